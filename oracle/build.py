@@ -1,0 +1,29 @@
+"""Compile the oracle's quad-precision operator builder (test infrastructure only).
+
+Produces ``oracle/liboracle_ops.so`` next to this file.  Plain gcc, no CUDA.
+"""
+import os
+import platform
+import subprocess
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(HERE, "ops_quad.c")
+LIB = os.path.join(HERE, "liboracle_ops.so")
+
+
+def build(force: bool = False) -> str:
+    if (not force and os.path.exists(LIB)
+            and os.path.getmtime(LIB) >= os.path.getmtime(SRC)):
+        return LIB
+    cmd = ["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+           SRC, "-o", LIB + ".tmp"]
+    if platform.machine() in ("x86_64", "AMD64"):
+        cmd.append("-lquadmath")
+    cmd.append("-lm")
+    subprocess.run(cmd, check=True)
+    os.replace(LIB + ".tmp", LIB)
+    return LIB
+
+
+if __name__ == "__main__":
+    print(build(force=True))

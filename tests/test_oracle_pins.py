@@ -1,0 +1,396 @@
+"""Pins of the CPU oracle to facts outside itself (closed forms, invariants,
+brute force, published values).  CPU only."""
+import os
+
+import numpy as np
+import pytest
+from numpy.polynomial import polynomial as P
+
+import dns_synth
+import oracle
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _read_golden(name):
+    rows = []
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                rows.append(line.split())
+    return rows
+
+
+# ------------------------------------------------------------------ grid
+
+@pytest.mark.parametrize("My", [9, 17, 33, 65])
+def test_nodes_are_flipped_gauss_lobatto(My):
+    y, _, _, _ = oracle.grid(My)
+    j = np.arange(My)
+    assert np.allclose(y, np.cos(np.pi * (My - 1 - j) / (My - 1)), atol=1e-15, rtol=0)
+    assert y[0] == -1.0 and y[-1] == 1.0 and np.all(np.diff(y) > 0)
+
+
+@pytest.mark.parametrize("My", [9, 17, 33, 65])
+def test_derivatives_exact_on_polynomials(My):
+    y, D1, D2, _ = oracle.grid(My)
+    for p in range(My):
+        c = np.zeros(p + 1); c[p] = 1.0
+        f = P.polyval(y, c)
+        d1 = P.polyval(y, P.polyder(c, 1))
+        d2 = P.polyval(y, P.polyder(c, 2))
+        tol1 = 1e-14 * My ** 2 * max(1.0, np.abs(d1).max())
+        tol2 = 1e-14 * My ** 4 * max(1.0, np.abs(d2).max())
+        assert np.abs(D1 @ f - d1).max() < tol1, p
+        assert np.abs(D2 @ f - d2).max() < tol2, p
+
+
+@pytest.mark.parametrize("My", [9, 17, 33, 49])
+def test_clamped_d4_exact_on_clamped_polynomials(My):
+    """D4c is exact on (1-y^2)^2 y^p for p <= My-3 (Weideman & Reddy clamped
+    fourth derivative cited in Sec. 2)."""
+    _, _, _, D4c = oracle.grid(My)
+    # nodes in extended precision, so the test data sit on the exact nodes
+    j = np.arange(1, My - 1, dtype=np.longdouble)
+    yi = -np.cos(np.pi * j / np.longdouble(My - 1))
+    D4l = D4c.astype(np.longdouble)
+    wpoly = np.array([1.0, 0.0, -2.0, 0.0, 1.0], dtype=np.longdouble)  # (1 - y^2)^2
+    for p in range(My - 2):
+        c = np.zeros(p + 1, dtype=np.longdouble); c[p] = 1.0
+        full = P.polymul(wpoly, c)
+        exact = P.polyval(yi, P.polyder(full, 4))
+        vals = ((1 - yi) * (1 + yi)) ** 2 * yi ** p   # factored: no cancellation at the walls
+        got = D4l @ vals          # extended-precision matvec: only D4c's own rounding remains
+        bound = 4 * np.finfo(float).eps * (np.abs(D4l) @ np.abs(vals)) + 1e-14 * np.abs(exact).max()
+        assert np.all(np.abs(got - exact) < bound), p
+
+
+@pytest.mark.parametrize("My", [9, 17, 33, 65])
+def test_clenshaw_curtis_exact(My):
+    y, _, _, _ = oracle.grid(My)
+    w = oracle.cc_weights(My)
+    for p in range(My):
+        exact = (1 - (-1) ** (p + 1)) / (p + 1)
+        assert abs(w @ y ** p - exact) < 1e-14
+
+
+def test_truncation_matches_paper_mode_counts():
+    """Dealiased mode counts of Table geometry3: 2K+1 = Nx with K = (M-1)//3."""
+    for mx, my, nx, ny in _read_golden("geometry3_modes.txt"):
+        K = dns_synth.truncation(int(mx))
+        assert 2 * K + 1 == int(nx)
+        assert int(my) - 2 == int(ny)
+
+
+# ------------------------------------------------------------- operators
+
+@pytest.mark.parametrize("My,k2,dt,re,h", [(17, 2.5, 0.01, 400.0, 0.5),
+                                          (33, 7.3, 0.01, 400.0, 1.0),
+                                          (33, 0.0, 0.005, 1650.0, 1.0)])
+def test_eta_operator_closed_form(My, k2, dt, re, h):
+    """(I - g Delta) P_eta = -h dt I on polynomials vanishing at the walls, and
+    M_eta = 2 (I - g Delta)^{-1} - I = -I - (2 / (h dt)) P_eta (Eq. CN2)."""
+    y, _, _, _ = oracle.grid(My)
+    yi = y[1:-1]
+    g = h * dt / (2 * re)
+    Mv, Pv, Me, Pe = oracle.cn_operators(My, [k2], dt, re, h)
+    for p in range(My - 3):
+        eta = P.polymul([1.0, 0.0, -1.0], np.eye(p + 1)[p])         # (1 - y^2) y^p
+        rhs = P.polyval(yi, eta) - g * (P.polyval(yi, P.polyder(eta, 2)) - k2 * P.polyval(yi, eta))
+        got = Pe[0] @ rhs
+        assert np.abs(got + h * dt * P.polyval(yi, eta)).max() < 1e-12 * h * dt, p
+    assert np.abs(Me[0] + np.eye(My - 2) + (2.0 / (h * dt)) * Pe[0]).max() < 1e-12
+
+
+@pytest.mark.parametrize("My,k2,dt,re,h", [(17, 2.5, 0.01, 400.0, 0.5),
+                                          (33, 7.3, 0.01, 400.0, 1.0),
+                                          (41, 1.0, 0.005, 1650.0, 0.5)])
+def test_v_operator_closed_form(My, k2, dt, re, h):
+    """For clamped polynomials v = (1-y^2)^2 y^p, (Delta - g Delta Delta) v is a
+    known polynomial and P_v maps it to -h dt v; and M_v = 2 A^{-1} Delta - I =
+    -I - (2/(h dt)) P_v Delta (Eq. CN1 multiplied through by Delta)."""
+    y, D1, D2, _ = oracle.grid(My)
+    yi = y[1:-1]
+    g = h * dt / (2 * re)
+    Mv, Pv, Me, Pe = oracle.cn_operators(My, [k2], dt, re, h)
+    for p in range(My - 5):
+        v = P.polymul([1.0, 0.0, -2.0, 0.0, 1.0], np.eye(p + 1)[p])
+        lap = P.polyval(yi, P.polyder(v, 2)) - k2 * P.polyval(yi, v)
+        bih = (P.polyval(yi, P.polyder(v, 4)) - 2 * k2 * P.polyval(yi, P.polyder(v, 2))
+               + k2 * k2 * P.polyval(yi, v))
+        rhs = lap - g * bih
+        got = Pv[0] @ rhs
+        assert np.abs(got + h * dt * P.polyval(yi, v)).max() < 1e-11 * h * dt, p
+    Delta = D2[1:-1, 1:-1] - k2 * np.eye(My - 2)
+    R = Mv[0] + np.eye(My - 2) + (2.0 / (h * dt)) * (Pv[0] @ Delta)
+    assert np.abs(R).max() < 1e-9
+
+
+def test_eta_operator_eigenvalues():
+    """M_eta has the CN amplification factors (1 + g mu)/(1 - g mu) of the
+    eigenvalues mu = lambda - k^2 of the Dirichlet Laplacian."""
+    My, k2, dt, re, h = 25, 3.0, 0.01, 300.0, 1.0
+    _, _, D2, _ = oracle.grid(My)
+    lam = np.linalg.eigvals(D2[1:-1, 1:-1]).real
+    g = h * dt / (2 * re)
+    mu = lam - k2
+    want = np.sort((1 + g * mu) / (1 - g * mu))
+    _, _, Me, _ = oracle.cn_operators(My, [k2], dt, re, h)
+    got = np.sort(np.linalg.eigvals(Me[0]).real)
+    assert np.abs(got - want).max() < 1e-10
+
+
+# ------------------------------------------------- transforms / products
+
+def _full_spectrum(c, Kx, Kz):
+    """Kept half-spectrum c[m+Kz, n] -> dict (n, m) -> coefficient, both signs of n,
+    the n = 0 column replaced by its Hermitian part."""
+    out = {}
+    for mi in range(2 * Kz + 1):
+        m = mi - Kz
+        for n in range(Kx + 1):
+            if n == 0:
+                val = 0.5 * (c[mi, 0] + np.conj(c[2 * Kz - mi, 0]))
+                out[(0, m)] = val
+            else:
+                out[(n, m)] = c[mi, n]
+                out[(-n, -m)] = np.conj(c[mi, n])
+    return out
+
+
+@pytest.mark.parametrize("mx,mz", [(4, 4), (7, 10), (10, 7), (16, 13)])
+def test_dealiased_product_equals_triad_sum(mx, mz):
+    """The pseudo-spectral product with 2/3-rule truncation equals the exact
+    convolution sum over kept triads (Orszag 1971's 2/3 rule, Sec. 3.2)."""
+    ch = oracle.Channel.__new__(oracle.Channel)
+    ch.mx, ch.mz = mx, mz
+    ch.Kx, ch.Kz = (mx - 1) // 3, (mz - 1) // 3
+    Kx, Kz = ch.Kx, ch.Kz
+    rng = np.random.default_rng(mx * 100 + mz)
+    a = rng.normal(size=(2 * Kz + 1, Kx + 1)) + 1j * rng.normal(size=(2 * Kz + 1, Kx + 1))
+    b = rng.normal(size=(2 * Kz + 1, Kx + 1)) + 1j * rng.normal(size=(2 * Kz + 1, Kx + 1))
+    got = ch.to_spectral(ch.to_physical(a) * ch.to_physical(b))
+    A = _full_spectrum(a, Kx, Kz)
+    B = _full_spectrum(b, Kx, Kz)
+    want = np.zeros_like(a)
+    for (n1, m1), va in A.items():
+        for (n2, m2), vb in B.items():
+            n, m = n1 + n2, m1 + m2
+            if 0 <= n <= Kx and abs(m) <= Kz:
+                want[m + Kz, n] += va * vb
+    assert np.abs(got - want).max() < 1e-13 * np.abs(want).max()
+
+
+def test_product_aliases_on_too_small_grid():
+    """Sensitivity check of the triad test: with M = 2K+1 < 3K+1 the same
+    comparison must fail (aliased triads fold back)."""
+    K = 3
+    ch = oracle.Channel.__new__(oracle.Channel)
+    ch.mx, ch.mz, ch.Kx, ch.Kz = 2 * K + 1, 1, K, 0
+    rng = np.random.default_rng(1)
+    a = (rng.normal(size=(1, K + 1)) + 1j * rng.normal(size=(1, K + 1)))
+    got = ch.to_spectral(ch.to_physical(a) * ch.to_physical(a))
+    A = _full_spectrum(a, K, 0)
+    want = np.zeros_like(a)
+    for (n1, _), va in A.items():
+        for (n2, _), vb in A.items():
+            if 0 <= n1 + n2 <= K:
+                want[0, n1 + n2] += va * vb
+    assert np.abs(got - want).max() > 1e-3
+
+
+# ----------------------------------------------------------- time scheme
+
+def _kutta_rk3(f, x, dt):
+    k1 = f(x)
+    k2 = f(x + 0.5 * dt * k1)
+    k3 = f(x - dt * k1 + 2.0 * dt * k2)
+    return x + dt * (k1 + 4.0 * k2 + k3) / 6.0
+
+
+def test_cn_rk3_without_viscosity_is_kutta():
+    """With the viscous operator off, the three CN/RK3 sub-steps of Sec. 3.1
+    reduce to Kutta's classical third-order method."""
+    f = lambda x: np.sin(x) + x * x
+    dt = 0.1
+    for x0 in (0.3, -1.1, 2.0):
+        got = oracle.cn_rk3(x0, lambda x: -f(x), lambda xt, Ft, h, s: xt - h * dt * Ft)
+        assert abs(got - _kutta_rk3(f, x0, dt)) < 1e-15
+
+
+def test_cn_rk3_third_order_in_dt():
+    f = lambda x: -x * x
+    exact = lambda t: 1.0 / (1.0 + t)       # x' = -x^2, x(0) = 1
+    errs = []
+    for nsteps in (10, 20, 40):
+        dt = 1.0 / nsteps
+        x = 1.0
+        for _ in range(nsteps):
+            x = oracle.cn_rk3(x, lambda x: -f(x), lambda xt, Ft, h, s: xt - h * dt * Ft)
+        errs.append(abs(x - exact(1.0)))
+    rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(rates > 2.8)
+
+
+# ------------------------------------------------------- whole-step pins
+
+def _state(st):
+    return tuple(st[k] for k in ("v", "eta", "U", "W"))
+
+
+def test_laminar_couette_is_steady():
+    ch = oracle.Channel(16, 33, 16, 1.75 * np.pi, 1.2 * np.pi, 400.0, 0.01, "couette")
+    x = _state(dns_synth.make_state(16, 33, 16, 1.75 * np.pi, 1.2 * np.pi, "couette", 1, 0, 0.0))
+    y = ch.step(x, 10)
+    assert np.abs(y[2] - x[2]).max() < 1e-14
+    assert np.abs(y[0]).max() == 0.0 and np.abs(y[3]).max() == 0.0
+    s = ch.stats(y)
+    assert abs(s["tau_bottom"][0] - 1.0) < 1e-13 and abs(s["tau_top"][0] - 1.0) < 1e-13
+
+
+def test_laminar_poiseuille_is_steady_with_gamma_two_over_re():
+    re = 1650.0
+    ch = oracle.Channel(16, 33, 16, 2 * np.pi, np.pi, re, 0.005, "poiseuille")
+    x = _state(dns_synth.make_state(16, 33, 16, 2 * np.pi, np.pi, "poiseuille", 1, 0, 0.0))
+    y = ch.step(x, 10)
+    assert np.abs(y[2] - x[2]).max() < 1e-14
+    assert abs(ch.last_gamma[0] - 2.0 / re) < 1e-15
+    assert abs(ch.stats(y)["bulk_flux"][0] - 4.0 / 3.0) < 1e-14
+
+
+@pytest.mark.parametrize("m", [1, 2])
+def test_viscous_streak_decays_by_closed_form_factor(m):
+    """A streamwise-uniform streak on laminar Couette has no nonlinear term
+    (v = w = 0, d/dx = 0), so one step multiplies eta by the h = 1 CN factor
+    (1 + g mu)/(1 - g mu), g = dt/(2 Re); for eta = cos(pi y / 2),
+    mu = -(pi/2)^2 - kz^2 (the Dirichlet eigenvalue on [-1, 1])."""
+    mx, my, mz, re, dt = 4, 33, 7, 400.0, 0.01
+    lx, lz = 2 * np.pi, 1.2 * np.pi
+    ch = oracle.Channel(mx, my, mz, lx, lz, re, dt, "couette")
+    x = _state(dns_synth.make_state(mx, my, mz, lx, lz, "couette", 1, 0, 0.0))
+    v, eta, U, W = (np.array(a) for a in x)
+    yi = ch.y[1:-1]
+    prof = 1e-3 * np.cos(np.pi * yi / 2)
+    eta[0, :, ch.Kz + m, 0] = prof * (0.3 + 0.7j)
+    eta[0, :, ch.Kz - m, 0] = prof * (0.3 - 0.7j)
+    y = ch.step((v, eta, U, W), 1)
+    kz = m * 2 * np.pi / lz
+    g = dt / (2 * re)
+    mu = -(np.pi / 2) ** 2 - kz ** 2
+    fac = (1 + g * mu) / (1 - g * mu)
+    assert np.abs(y[1] - fac * eta).max() < 1e-13 * np.abs(eta).max()
+    assert np.abs(y[0]).max() == 0.0
+    assert np.abs(y[2] - U).max() < 1e-15
+
+
+def test_orr_sommerfeld_mode_grows_at_linear_rate():
+    """An infinitesimal Tollmien-Schlichting wave (Re = 10^4, alpha = 1) in
+    Poiseuille flow grows and travels at the published Orr-Sommerfeld rate."""
+    g = dict((k, float(v)) for k, v in _read_golden("orr_sommerfeld_re1e4.txt"))
+    c_pub = g["c_r"] + 1j * g["c_i"]
+    scipy_linalg = pytest.importorskip("scipy.linalg")
+    re, dt, my = 1.0e4, 0.01, 81
+    ch = oracle.Channel(4, my, 1, 2 * np.pi, 1.0, re, dt, "poiseuille")
+    yi = ch.y[1:-1]
+    n = my - 2
+    # discrete Orr-Sommerfeld eigenproblem on the same D2_int / D4c:
+    # i alpha [(U - c)(D2 - a^2) - U''] v = (1/Re)(D2 - a^2)^2 v
+    a = 1.0
+    I = np.eye(n)
+    L = ch.D2[1:-1, 1:-1] - a * a * I
+    LL = ch.D4c - 2 * a * a * ch.D2[1:-1, 1:-1] + a ** 4 * I
+    U = np.diag(1 - yi ** 2)
+    A = 1j * a * (U @ L + 2.0 * I) - LL / re
+    B = 1j * a * L
+    ev, vec = scipy_linalg.eig(A, B)
+    k = np.argmax(ev.imag)
+    c_disc = ev[k]
+    assert abs(c_disc - c_pub) < 2e-7
+    vos = vec[:, k] / vec[np.argmax(np.abs(vec[:, k])), k]
+    st = _state(dns_synth.make_state(4, my, 1, 2 * np.pi, 1.0, "poiseuille", 1, 0, 0.0))
+    v, eta, Um, W = (np.array(s) for s in st)
+    v[0, :, 0, 1] = 1e-9 * vos
+    nsteps = 50
+    y = ch.step((v, eta, Um, W), nsteps)
+    ratio = np.vdot(vos, y[0][0, :, 0, 1]) / np.vdot(vos, v[0, :, 0, 1])
+    c_num = 1j * np.log(ratio) / (a * nsteps * dt)
+    assert abs(c_num - c_pub) < 2e-6
+    assert abs(c_num.imag - c_pub.imag) < 1e-6
+
+
+# ---------------------------------------------------------- invariants
+
+@pytest.fixture(scope="module")
+def couette_small():
+    ch = oracle.Channel(16, 33, 16, 1.75 * np.pi, 1.2 * np.pi, 400.0, 0.01, "couette")
+    st = dns_synth.make_state(16, 33, 16, 1.75 * np.pi, 1.2 * np.pi, "couette", 2, 1000, 5e-2)
+    return ch, _state(st)
+
+
+def test_divergence_free_and_hermitian(couette_small):
+    ch, x = couette_small
+    y = ch.step(x, 5)
+    s = ch.stats(y)
+    assert np.all(s["max_div"] < 1e-14)
+    for a in (y[0], y[1]):
+        col = a[:, :, :, 0]
+        assert np.abs(col - np.conj(col[:, :, ::-1])).max() < 1e-15 * np.abs(col).max() + 1e-300
+
+
+def test_poiseuille_flux_constant_under_perturbation():
+    ch = oracle.Channel(16, 33, 16, 2 * np.pi, np.pi, 1650.0, 0.005, "poiseuille")
+    x = _state(dns_synth.make_state(16, 33, 16, 2 * np.pi, np.pi, "poiseuille", 2, 2000, 5e-2,
+                                    n_max=4, m_max=4))
+    y = ch.step(x, 5)
+    assert np.abs(ch.stats(y)["bulk_flux"] - 4.0 / 3.0).max() < 1e-14
+    assert np.abs(y[2] - x[2]).max() > 1e-9    # the mean flow did respond
+
+
+def test_couette_shift_rotate_symmetry_is_preserved():
+    """(x, y, z) -> (-x, -y, z), (u, v, w) -> (-u, -v, w) maps plane Couette
+    flow onto itself; a symmetric state stays symmetric to round-off."""
+    ch = oracle.Channel(10, 25, 10, 1.75 * np.pi, 1.2 * np.pi, 400.0, 0.01, "couette")
+    st = dns_synth.make_state(10, 25, 10, 1.75 * np.pi, 1.2 * np.pi, "couette", 1, 7, 5e-2)
+
+    def symm(a):       # x_hat(n, m, y) = -conj x_hat(n, -m, -y)
+        return 0.5 * (a - np.conj(a[:, ::-1, ::-1, :]))
+
+    v, eta = symm(st["v"]), symm(st["eta"])
+    U = st["U"]
+    y = ch.step((v, eta, U, st["W"]), 5)
+    for a in (y[0], y[1]):
+        assert np.abs(a - symm(a)).max() < 1e-15 * max(1.0, np.abs(a).max()) * 50
+    assert np.abs(y[2] + y[2][:, ::-1]).max() < 1e-14
+    assert np.abs(y[0]).max() > 1e-4
+
+
+def test_members_are_independent(couette_small):
+    ch, x = couette_small
+    both = ch.step(x, 3)
+    alone = ch.step(tuple(a[1:2] for a in x), 3)
+    for a, b in zip(both, alone):   # BLAS may block differently per batch size
+        assert np.abs(a[1:2] - b).max() <= 1e-14 * max(np.abs(b).max(), 1e-300)
+
+
+def test_energy_budget_residual_is_second_order_in_dt():
+    """Kinetic-energy balance of plane Couette flow: dE/dt = wall work -
+    dissipation (the advection term only redistributes energy).  The discrete
+    residual of the central difference of E falls as O(dt^2) until it meets the
+    spatial floor (about 1e-8 here), so dt is taken in 0.08 .. 0.02."""
+    mx, my, mz, re = 16, 33, 16, 400.0
+    lx, lz = 1.75 * np.pi, 1.2 * np.pi
+    st = _state(dns_synth.make_state(mx, my, mz, lx, lz, "couette", 1, 11, 5e-2, n_max=3, m_max=3))
+    res = []
+    for dt in (0.08, 0.04, 0.02):
+        ch = oracle.Channel(mx, my, mz, lx, lz, re, dt, "couette")
+        xm = st
+        x0 = ch.step(xm, 1)
+        xp = ch.step(x0, 1)
+        E = [ch.stats(x)["e_total"][0] for x in (xm, x0, xp)]
+        s0 = ch.stats(x0)
+        dEdt = (E[2] - E[0]) / (2 * dt)
+        rhs = s0["wall_work"][0] - s0["dissipation"][0]
+        res.append(abs(dEdt - rhs))
+        assert abs(dEdt - rhs) < 1e-4 * abs(s0["dissipation"][0])
+    assert res[0] / res[1] > 3.5 and res[1] / res[2] > 3.5
