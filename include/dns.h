@@ -1,0 +1,182 @@
+/*
+ * dns.h -- C ABI of the ensemble channel DNS step library (libdns.so).
+ *
+ * The library advances whole ensembles of plane Couette / plane Poiseuille
+ * realisations by full Crank-Nicolson / 3rd-order Runge-Kutta time steps of the
+ * wall-normal velocity / vorticity (v-eta) formulation, Fourier (x, z) x
+ * Chebyshev (y) pseudo-spectral, on one CUDA GPU (sm_103a).
+ *
+ * Method (arXiv 2306.12739, "A vectorized Navier-Stokes ensemble direct
+ * numerical simulation code for plane parallel flows"):
+ *   - equations: Sec. 2, Eqs. (Dv), (eta), (U00), (W00) and the boundary
+ *     conditions v = dv/dy = eta = 0, U00(+-1) = +-U_w, W00(+-1) = 0;
+ *   - time scheme: Sec. 3.1 (three CN sub-steps of lengths h = 1/2, 1, 1 with
+ *     the nonlinear terms combined as F0, 2F1 - F0, (F0 + 4F1 + F2)/6, always
+ *     restarting from the state at t);
+ *   - implicit solves as precomputed matrices: Sec. 3.2, Eqs. CN1-CN4;
+ *   - 2/3-rule dealiasing and the u, w recovery from v, eta: Sec. 3.2.
+ *
+ * Conventions shared by every call
+ *   * Grid of a group: Mx x My x Mz collocation points; y_j = -cos(pi j/(My-1)),
+ *     j = 0..My-1 (ascending, walls at j = 0 and My-1); x_i = i Lx/Mx,
+ *     z_k = k Lz/Mz.  Retained modes: n = 0..Kx, m = -Kz..Kz with
+ *     Kx = (Mx-1)/3, Kz = (Mz-1)/3 (integer division), kx = n 2pi/Lx,
+ *     kz = m 2pi/Lz.  Supported Mx, Mz: 16, 32, 48, 64; 5 <= My <= 129.
+ *   * Host state layout (dns_set_state / dns_get_state):
+ *       v_hat, eta_hat : double complex, interleaved (re, im),
+ *                        [member][My-2 interior y][2 Kz + 1 (m + Kz)][Kx + 1 (n)]
+ *       U00, W00       : double [member][My] (all nodes, walls included)
+ *     The (n, m) = (0, 0) entries of v_hat and eta_hat are ignored (zero).
+ *   * Every call returns a dns_status (0 = success).  Nothing crosses the ABI as
+ *     an exception.  dns_last_error() gives a one-line reason for the last
+ *     failure on a handle.
+ *   * Ownership: the handle owns its host copies of the operators.  ALL device
+ *     memory is caller-owned: dns_workspace_size() says how much, the caller
+ *     allocates it (e.g. a torch uint8 tensor) and binds it with
+ *     dns_bind_workspace().  The CUDA stream is caller-owned too; every device
+ *     operation of a handle is enqueued on that stream.
+ *   * Asynchrony: dns_step() only enqueues work.  dns_get_state() and
+ *     dns_stats() synchronise the stream before they return host data.
+ */
+#ifndef DNS_H
+#define DNS_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    DNS_OK = 0,
+    DNS_ERR_INVALID = -1,     /* bad argument, bad configuration, unbound workspace */
+    DNS_ERR_CUDA = -2,        /* a CUDA runtime call failed (message in dns_last_error) */
+    DNS_ERR_NOMEM = -3,       /* workspace too small, host allocation failed */
+    DNS_ERR_TIMEOUT = -4,     /* reserved: a bounded device wait gave up */
+    DNS_ERR_NONFINITE = -5,   /* returned by dns_stats when any member holds NaN/Inf */
+    DNS_ERR_UNSUPPORTED = -6  /* valid request the library does not implement */
+} dns_status;
+
+typedef enum { DNS_COUETTE = 0, DNS_POISEUILLE = 1 } dns_flow;
+
+/* DNS_PREC_FP64: every stage in double precision (the comparator).
+ * DNS_PREC_MIXED: transforms and nonlinear products in single precision, the
+ * y-contractions and implicit applies in split precision, the boundary/mean-flow
+ * solves and the state accumulation in double precision. */
+typedef enum { DNS_PREC_FP64 = 0, DNS_PREC_MIXED = 1 } dns_precision;
+
+/* One group: members that share grid, box, Re and dt. */
+typedef struct {
+    dns_flow flow;
+    int mx, my, mz;        /* collocation points (x, y incl. both walls, z) */
+    double lx, lz;         /* box lengths; Ly = 2 is fixed */
+    double re;             /* Couette: half-gap wall speed; Poiseuille: laminar centreline speed */
+    double dt;             /* fixed time step (the paper's scheme has no adaptive dt) */
+    double u_wall;         /* Couette wall speed: U00(+-1) = +-u_wall (ignored for Poiseuille) */
+    double bulk_flux;      /* Poiseuille: prescribed int_{-1}^{1} U00 dy (4/3 for U = 1 - y^2) */
+    int members;           /* ensemble size of this group, >= 1 */
+} dns_group_desc;
+
+typedef struct {
+    int n_groups;                  /* >= 1 */
+    const dns_group_desc* groups;  /* n_groups entries, copied by dns_create */
+    dns_precision precision;
+    int use_graph;                 /* 1: capture one full step as a CUDA graph and replay it */
+    int persistent;                /* reserved, must be 0 */
+    unsigned long long barrier_timeout_ns;  /* reserved, 0 */
+    const char* autotune_cache;    /* reserved, may be NULL */
+} dns_config;
+
+/* One-point statistics of one member (paper Sec. 4), computed from the current
+ * state at time t:
+ *   e_total    volume-averaged kinetic energy (1/(2V)) int |u|^2 dV, mean flow included
+ *   e_pert     the same without the (0, 0) mode
+ *   tau_bottom, tau_top   dU00/dy at y = -1 and y = +1
+ *   bulk_flux  int_{-1}^{1} U00 dy (Clenshaw-Curtis)
+ *   gamma      Poiseuille pressure gradient of the last sub-step (0 for Couette)
+ *   max_div    max over interior nodes and modes of |i kx u + dv/dy + i kz w|
+ *   nonfinite  1 if any value of this member's state is NaN or Inf       */
+typedef struct {
+    double e_total, e_pert, tau_bottom, tau_top, bulk_flux, gamma, max_div;
+    int nonfinite;
+    int reserved;
+} dns_stats_t;
+
+typedef struct dns_handle dns_handle;
+
+/* Validate the configuration and build every operator on the host (Sec. 3.2,
+ * Listings 1 and 3: Chebyshev D, the clamped fourth derivative, and per
+ * wavenumber pair and sub-step length the CN matrices M = A^{-1} B and
+ * P = -h dt A^{-1} for v (Eq. CN1 multiplied through by Delta) and eta (Eq. CN2),
+ * plus the mean-flow operators of Eqs. CN3/CN4), in double-double precision,
+ * rounded once to double.  No device memory is touched.
+ * cuda_stream: a cudaStream_t (NULL = legacy default stream).
+ * Errors: DNS_ERR_INVALID (bad config, message in *out's last error when *out
+ * is returned, else none), DNS_ERR_UNSUPPORTED (grid size), DNS_ERR_NOMEM. */
+int dns_create(const dns_config* cfg, void* cuda_stream, dns_handle** out);
+
+/* Bytes of device memory the handle needs (operators, state, work arrays). */
+int dns_workspace_size(const dns_handle* h, size_t* bytes);
+
+/* Bind caller-owned device memory (>= dns_workspace_size bytes, 256-byte
+ * aligned) and upload the operators on the handle's stream.  The memory must
+ * stay valid until dns_destroy or the next bind.  Errors: DNS_ERR_NOMEM (too
+ * small), DNS_ERR_INVALID (misaligned / NULL), DNS_ERR_CUDA. */
+int dns_bind_workspace(dns_handle* h, void* dev_ptr, size_t bytes);
+
+/* Sizes of group `group`: n_kx = Kx + 1, n_kz = 2 Kz + 1, ny_int = My - 2, my = My. */
+int dns_state_shape(const dns_handle* h, int group, int* n_kx, int* n_kz, int* ny_int, int* my);
+
+/* Copy `count` members starting at `member0` of group `group` into the library
+ * (layout in the header comment).  ptr_kind: 0 = host pointers (pageable or
+ * pinned), 1 = device pointers.  The n = 0 column is replaced by its Hermitian
+ * part in m, x(0,m) := (x(0,m) + conj x(0,-m))/2 (the only part a real field
+ * carries), and the (0,0) entries are zeroed.  Host pointers are read before
+ * the call returns.  Errors: DNS_ERR_INVALID (range, NULL), DNS_ERR_CUDA. */
+int dns_set_state(dns_handle* h, int group, int member0, int count,
+                  const double* v_hat, const double* eta_hat,
+                  const double* U00, const double* W00, int ptr_kind);
+
+/* Copy members out (same layout).  Synchronises the stream. */
+int dns_get_state(const dns_handle* h, int group, int member0, int count,
+                  double* v_hat, double* eta_hat, double* U00, double* W00, int ptr_kind);
+
+/* Enqueue nsteps full CN/RK3 steps of every group on the handle's stream. */
+int dns_step(dns_handle* h, int nsteps);
+
+/* Statistics of every member of `group` at the current time (synchronises).
+ * per_member: [members] (required); ensemble_mean: arithmetic mean over the
+ * group's members (optional); profiles: optional host array
+ * [members][6][My] holding U00, W00, <u'u'>, <v'v'>, <w'w'>, <u'v'> (plane
+ * averages; the perturbation parts vanish on the walls).
+ * Returns DNS_ERR_NONFINITE (after filling the outputs) when any member of the
+ * group holds a NaN or Inf. */
+int dns_stats(dns_handle* h, int group, dns_stats_t* per_member, dns_stats_t* ensemble_mean,
+              double* profiles);
+
+/* Free the handle (not the caller's device memory).  Synchronises the stream. */
+int dns_destroy(dns_handle* h);
+
+/* Reason of the last failure on this handle ("" if none).  Valid until the
+ * next call on the handle. */
+const char* dns_last_error(const dns_handle* h);
+
+/* Number of kernel launches enqueued by the last dns_step call (all steps). */
+int dns_last_launch_count(const dns_handle* h);
+
+/* Host copies of what dns_create built, for inspection and tests; no device
+ * access, valid before a workspace is bound.
+ * dns_export_grid: y [My], D1 [My*My], D2 [My*My], D4c [(My-2)^2] and the
+ *   Clenshaw-Curtis weights ccw [My] (Sec. 2, Listing 1; any output may be NULL).
+ * dns_export_operators: the CN operators of Eqs. CN1/CN2 for sub-step length
+ *   h = 1/2 (h_index 0) or h = 1 (h_index 1) and wavenumber pair
+ *   pair = |m| (Kx + 1) + n, each (My-2)^2 doubles row-major (Listing 3). */
+int dns_export_grid(const dns_handle* h, int group, double* y, double* D1, double* D2,
+                    double* D4c, double* ccw);
+int dns_export_operators(const dns_handle* h, int group, int h_index, int pair,
+                         double* Mv, double* Pv, double* Me, double* Pe);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DNS_H */

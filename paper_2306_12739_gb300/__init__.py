@@ -1,0 +1,257 @@
+"""Python binding of libdns.so, the GB300 ensemble channel-DNS step library.
+
+Argument marshalling only: every step of the computation runs in the library's
+CUDA kernels.  PyTorch provides the device workspace and the CUDA stream.
+
+Functions named ``dns_*`` mirror the C ABI in ``include/dns.h`` one to one;
+``Ensemble`` is a convenience wrapper around them.  Importing this package
+raises ImportError if ``libdns.so`` has not been built (run
+``python -c "import __graft_entry__ as g; g.build()"``); there is no fallback.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdns.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError("libdns.so is not built at %s; build it with paper_2306_12739_gb300.build" % LIB_PATH)
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+DNS_OK = 0
+DNS_ERR_INVALID = -1
+DNS_ERR_CUDA = -2
+DNS_ERR_NOMEM = -3
+DNS_ERR_TIMEOUT = -4
+DNS_ERR_NONFINITE = -5
+DNS_ERR_UNSUPPORTED = -6
+DNS_COUETTE, DNS_POISEUILLE = 0, 1
+DNS_PREC_FP64, DNS_PREC_MIXED = 0, 1
+
+EXPORTED = ["dns_create", "dns_workspace_size", "dns_bind_workspace", "dns_state_shape",
+            "dns_set_state", "dns_get_state", "dns_step", "dns_stats", "dns_destroy",
+            "dns_last_error", "dns_last_launch_count", "dns_export_grid", "dns_export_operators"]
+
+
+class dns_group_desc(ctypes.Structure):
+    _fields_ = [("flow", ctypes.c_int), ("mx", ctypes.c_int), ("my", ctypes.c_int), ("mz", ctypes.c_int),
+                ("lx", ctypes.c_double), ("lz", ctypes.c_double), ("re", ctypes.c_double),
+                ("dt", ctypes.c_double), ("u_wall", ctypes.c_double), ("bulk_flux", ctypes.c_double),
+                ("members", ctypes.c_int)]
+
+
+class dns_config(ctypes.Structure):
+    _fields_ = [("n_groups", ctypes.c_int), ("groups", ctypes.POINTER(dns_group_desc)),
+                ("precision", ctypes.c_int), ("use_graph", ctypes.c_int), ("persistent", ctypes.c_int),
+                ("barrier_timeout_ns", ctypes.c_ulonglong), ("autotune_cache", ctypes.c_char_p)]
+
+
+class dns_stats_t(ctypes.Structure):
+    _fields_ = [("e_total", ctypes.c_double), ("e_pert", ctypes.c_double), ("tau_bottom", ctypes.c_double),
+                ("tau_top", ctypes.c_double), ("bulk_flux", ctypes.c_double), ("gamma", ctypes.c_double),
+                ("max_div", ctypes.c_double), ("nonfinite", ctypes.c_int), ("reserved", ctypes.c_int)]
+
+
+_H = ctypes.c_void_p
+_dp = ctypes.POINTER(ctypes.c_double)
+_vp = ctypes.c_void_p
+
+_lib.dns_create.argtypes = [ctypes.POINTER(dns_config), _vp, ctypes.POINTER(_H)]
+_lib.dns_workspace_size.argtypes = [_H, ctypes.POINTER(ctypes.c_size_t)]
+_lib.dns_bind_workspace.argtypes = [_H, _vp, ctypes.c_size_t]
+_lib.dns_state_shape.argtypes = [_H, ctypes.c_int] + [ctypes.POINTER(ctypes.c_int)] * 4
+_lib.dns_set_state.argtypes = [_H, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp, ctypes.c_int]
+_lib.dns_get_state.argtypes = [_H, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp, ctypes.c_int]
+_lib.dns_step.argtypes = [_H, ctypes.c_int]
+_lib.dns_stats.argtypes = [_H, ctypes.c_int, ctypes.POINTER(dns_stats_t), ctypes.POINTER(dns_stats_t), _dp]
+_lib.dns_destroy.argtypes = [_H]
+_lib.dns_last_error.argtypes = [_H]
+_lib.dns_last_error.restype = ctypes.c_char_p
+_lib.dns_last_launch_count.argtypes = [_H]
+_lib.dns_export_grid.argtypes = [_H, ctypes.c_int, _dp, _dp, _dp, _dp, _dp]
+_lib.dns_export_operators.argtypes = [_H, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp]
+
+
+class DnsError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("dns error %d: %s" % (code, msg))
+        self.code = code
+
+
+def _ck(h, rc):
+    if rc != DNS_OK:
+        msg = _lib.dns_last_error(h)
+        raise DnsError(rc, msg.decode() if msg else "")
+    return rc
+
+
+# ------------------------------------------------------------ C-ABI mirror
+
+def dns_create(cfg, stream=0):
+    h = _H()
+    rc = _lib.dns_create(ctypes.byref(cfg), _vp(stream), ctypes.byref(h))
+    if rc != DNS_OK:
+        msg = _lib.dns_last_error(h).decode() if h.value else ""
+        if h.value:
+            _lib.dns_destroy(h)
+        raise DnsError(rc, msg)
+    return h
+
+
+def dns_workspace_size(h):
+    n = ctypes.c_size_t()
+    _ck(h, _lib.dns_workspace_size(h, ctypes.byref(n)))
+    return n.value
+
+
+def dns_bind_workspace(h, ptr, nbytes):
+    return _ck(h, _lib.dns_bind_workspace(h, _vp(ptr), nbytes))
+
+
+def dns_state_shape(h, group):
+    a = [ctypes.c_int() for _ in range(4)]
+    _ck(h, _lib.dns_state_shape(h, group, *[ctypes.byref(x) for x in a]))
+    return tuple(x.value for x in a)
+
+
+def dns_set_state(h, group, member0, count, v, eta, U, W, ptr_kind):
+    return _ck(h, _lib.dns_set_state(h, group, member0, count, _vp(v), _vp(eta), _vp(U), _vp(W), ptr_kind))
+
+
+def dns_get_state(h, group, member0, count, v, eta, U, W, ptr_kind):
+    return _ck(h, _lib.dns_get_state(h, group, member0, count, _vp(v), _vp(eta), _vp(U), _vp(W), ptr_kind))
+
+
+def dns_step(h, nsteps):
+    return _ck(h, _lib.dns_step(h, nsteps))
+
+
+def dns_stats(h, group, members, profiles_ptr=None):
+    per = (dns_stats_t * members)()
+    mean = dns_stats_t()
+    rc = _lib.dns_stats(h, group, per, ctypes.byref(mean),
+                        ctypes.cast(profiles_ptr, _dp) if profiles_ptr else None)
+    if rc not in (DNS_OK, DNS_ERR_NONFINITE):
+        _ck(h, rc)
+    return rc, per, mean
+
+
+def dns_destroy(h):
+    return _lib.dns_destroy(h)
+
+
+def dns_last_error(h):
+    return _lib.dns_last_error(h).decode()
+
+
+def dns_last_launch_count(h):
+    return _lib.dns_last_launch_count(h)
+
+
+def dns_export_grid(h, group, my):
+    y = np.zeros(my); D1 = np.zeros((my, my)); D2 = np.zeros((my, my))
+    D4 = np.zeros((my - 2, my - 2)); w = np.zeros(my)
+    p = lambda a: a.ctypes.data_as(_dp)
+    _ck(h, _lib.dns_export_grid(h, group, p(y), p(D1), p(D2), p(D4), p(w)))
+    return y, D1, D2, D4, w
+
+
+def dns_export_operators(h, group, h_index, pair, ny):
+    out = [np.zeros((ny, ny)) for _ in range(4)]
+    _ck(h, _lib.dns_export_operators(h, group, h_index, pair, *[a.ctypes.data_as(_dp) for a in out]))
+    return out
+
+
+# ---------------------------------------------------------------- wrapper
+
+_FLOWS = {"couette": DNS_COUETTE, "poiseuille": DNS_POISEUILLE}
+_PRECS = {"fp64": DNS_PREC_FP64, "mixed": DNS_PREC_MIXED}
+
+
+def make_config(groups, precision="fp64", use_graph=False):
+    """groups: list of dicts with flow, mx, my, mz, lx, lz, re, dt, members,
+    optional u_wall (1.0) and bulk_flux (4/3)."""
+    arr = (dns_group_desc * len(groups))()
+    for i, g in enumerate(groups):
+        arr[i] = dns_group_desc(_FLOWS[g["flow"]], g["mx"], g["my"], g["mz"], g["lx"], g["lz"], g["re"],
+                                g["dt"], g.get("u_wall", 1.0), g.get("bulk_flux", 4.0 / 3.0), g["members"])
+    cfg = dns_config(len(groups), arr, _PRECS[precision], 1 if use_graph else 0, 0, 0, None)
+    cfg._keep = arr
+    return cfg
+
+
+class Ensemble:
+    """Owns a handle, its torch workspace and the stream it runs on."""
+
+    def __init__(self, groups, precision="fp64", use_graph=False, device="cuda:0", stream=None):
+        import torch
+        self.torch = torch
+        self.device = torch.device(device)
+        self.groups = [dict(g) for g in groups]
+        # a stream of its own: graph capture is not allowed on the legacy default stream
+        self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
+        self.cfg = make_config(groups, precision, use_graph)
+        self.h = dns_create(self.cfg, self.stream.cuda_stream)
+        nbytes = dns_workspace_size(self.h)
+        self.ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        base = self.ws.data_ptr()
+        self.ws_ptr = (base + 255) & ~255
+        dns_bind_workspace(self.h, self.ws_ptr, nbytes)
+        self.shapes = [dns_state_shape(self.h, i) for i in range(len(groups))]
+
+    def close(self):
+        if self.h is not None:
+            dns_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_state(self, group, v, eta, U, W, member0=0):
+        """v, eta complex128 [count][Ny][NKZ][NKX]; U, W float64 [count][My].
+        numpy arrays (host) or torch CUDA tensors (device, complex128/float64)."""
+        torch = self.torch
+        if isinstance(v, torch.Tensor):
+            ts = [t.contiguous() for t in (v, eta, U, W)]
+            count = ts[0].shape[0]
+            dns_set_state(self.h, group, member0, count, *[t.data_ptr() for t in ts], 1)
+            self._keep = ts
+        else:
+            arrs = [np.ascontiguousarray(v, dtype=np.complex128), np.ascontiguousarray(eta, dtype=np.complex128),
+                    np.ascontiguousarray(U, dtype=np.float64), np.ascontiguousarray(W, dtype=np.float64)]
+            count = arrs[0].shape[0]
+            dns_set_state(self.h, group, member0, count, *[a.ctypes.data for a in arrs], 0)
+
+    def get_state(self, group, member0=0, count=None):
+        nkx, nkz, ny, my = self.shapes[group]
+        if count is None:
+            count = self.groups[group]["members"] - member0
+        v = np.zeros((count, ny, nkz, nkx), dtype=np.complex128)
+        e = np.zeros_like(v)
+        U = np.zeros((count, my)); W = np.zeros((count, my))
+        dns_get_state(self.h, group, member0, count, v.ctypes.data, e.ctypes.data, U.ctypes.data,
+                      W.ctypes.data, 0)
+        return v, e, U, W
+
+    def step(self, nsteps=1):
+        dns_step(self.h, nsteps)
+
+    def launches(self):
+        return dns_last_launch_count(self.h)
+
+    def stats(self, group):
+        E = self.groups[group]["members"]
+        my = self.shapes[group][3]
+        prof = np.zeros((E, 6, my))
+        rc, per, mean = dns_stats(self.h, group, E, prof.ctypes.data)
+        keys = [k for k, _ in dns_stats_t._fields_ if k != "reserved"]
+        out = {k: np.array([getattr(per[i], k) for i in range(E)]) for k in keys}
+        out.update({"U": prof[:, 0], "W": prof[:, 1], "uu": prof[:, 2], "vv": prof[:, 3],
+                    "ww": prof[:, 4], "uv": prof[:, 5], "rc": rc})
+        return out

@@ -1,0 +1,499 @@
+// C ABI of the ensemble channel DNS library: configuration, host-side operator
+// build, workspace layout, state transfer and the CN/RK3 step orchestration
+// (paper Sec. 3.1: three sub-steps, each = nonlinear evaluation, forcing
+// combination, implicit per-wavenumber update, mean-flow update).
+#include "../../include/dns.h"
+#include "builder.hpp"
+#include "dns_internal.hpp"
+
+#include <cstdio>
+#include <cstring>
+#include <cstdarg>
+#include <string>
+#include <thread>
+#include <vector>
+
+using dnsk::GroupView;
+
+namespace {
+
+struct HostGroup {
+    dns_group_desc d;
+    GroupView v;
+    dnsb::GridOps grid;
+    dnsb::CnOps ops[2];
+    std::vector<double> kxt, kzt, k2t, k2inv, twx, twz, opsdev[2], mopsdev[2], D1i, D2i;
+    std::vector<float> kxtf, kztf, k2invf, twxf, twzf;
+    // byte offsets inside the workspace
+    struct Off { size_t off, bytes; };
+    std::vector<std::pair<void**, Off>> slots;
+};
+
+}  // namespace
+
+struct dns_handle {
+    dns_config cfg;
+    std::vector<dns_group_desc> descs;
+    std::vector<HostGroup> groups;
+    cudaStream_t stream = nullptr;
+    char* ws = nullptr;
+    size_t ws_bytes = 0;
+    size_t need = 0;
+    std::string err;
+    int launches = 0;
+    bool bound = false;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    int graph_launches = 0;
+};
+
+namespace {
+
+int fail(dns_handle* h, int code, const char* fmt, ...) {
+    if (h) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        h->err = buf;
+    }
+    return code;
+}
+
+bool make_plan(int N, dnsk::FftPlan* p) {
+    p->n = N;
+    p->nst = 0;
+    int n = N;
+    if (n % 3 == 0) { p->rad[p->nst++] = 3; n /= 3; }
+    while (n % 4 == 0 && p->nst < 5) { p->rad[p->nst++] = 4; n /= 4; }
+    if (n % 2 == 0 && p->nst < 5) { p->rad[p->nst++] = 2; n /= 2; }
+    return n == 1;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+bool precision_mixed(const dns_handle* h) { return h->cfg.precision == DNS_PREC_MIXED; }
+
+// Assign workspace offsets for every device array of group g (base = 0).
+size_t layout_group(dns_handle* h, HostGroup& G, size_t cur) {
+    GroupView& v = G.v;
+    G.slots.clear();
+    auto add = [&](void** ptr, size_t bytes) {
+        cur = align256(cur);
+        G.slots.push_back({ptr, {cur, bytes}});
+        cur += bytes;
+    };
+    const size_t S = (size_t)v.nmodes * v.ny * v.E;  // complex elements of one spectral field
+    const size_t nn = (size_t)v.ny * v.ny;
+    add((void**)&v.D1, sizeof(double) * v.my * v.my);
+    add((void**)&v.D1i, sizeof(double) * nn);
+    add((void**)&v.D2i, sizeof(double) * nn);
+    add((void**)&v.ccw, sizeof(double) * v.my);
+    add((void**)&v.kxt, sizeof(double) * v.nkx);
+    add((void**)&v.kzt, sizeof(double) * v.nkz);
+    add((void**)&v.k2t, sizeof(double) * v.nmodes);
+    add((void**)&v.k2inv, sizeof(double) * v.nmodes);
+    add((void**)&v.twx, sizeof(double2) * v.mx);
+    add((void**)&v.twz, sizeof(double2) * v.mz);
+    add((void**)&v.twxf, sizeof(float2) * v.mx);
+    add((void**)&v.twzf, sizeof(float2) * v.mz);
+    add((void**)&v.kxtf, sizeof(float) * v.nkx);
+    add((void**)&v.kztf, sizeof(float) * v.nkz);
+    add((void**)&v.k2invf, sizeof(float) * v.nmodes);
+    for (int hi = 0; hi < 2; ++hi) {
+        add((void**)&v.ops[hi], sizeof(double) * (size_t)v.npairs * 4 * nn);
+        add((void**)&v.mops[hi], sizeof(double) * (2 * nn + 3 * (size_t)v.ny));
+    }
+    double2** st[] = {&v.v_t, &v.e_t, &v.v_s, &v.e_s, &v.mx1_v, &v.mx1_e, &v.Fv, &v.Fe, &v.Av, &v.Ae};
+    for (auto p : st) add((void**)p, sizeof(double2) * S);
+    double** mf[] = {&v.U_t, &v.W_t, &v.U_s, &v.W_s, &v.dU, &v.dW, &v.uv, &v.wv};
+    for (auto p : mf) add((void**)p, sizeof(double) * (size_t)v.E * v.my);
+    add((void**)&v.AU, sizeof(double) * (size_t)v.E * v.ny);
+    add((void**)&v.AW, sizeof(double) * (size_t)v.E * v.ny);
+    add((void**)&v.gamma, sizeof(double) * v.E);
+    const size_t elem = precision_mixed(h) ? sizeof(float2) : sizeof(double2);
+    add(&v.P5, elem * 5 * S);
+    add(&v.N3, elem * 3 * S);
+    if (precision_mixed(h)) add((void**)&v.P5d, sizeof(double2) * 5 * S);
+    add((void**)&v.st_y, sizeof(double) * (size_t)v.E * v.ny * 6);
+    add((void**)&v.st_out, sizeof(double) * (size_t)v.E * 8);
+    add((void**)&v.prof, sizeof(double) * (size_t)v.E * 6 * v.my);
+    add((void**)&v.stage, sizeof(double2) * 2 * S);
+    return cur;
+}
+
+bool supported_m(int m) { return m == 16 || m == 32 || m == 48 || m == 64; }
+
+int check(dns_handle* h, cudaError_t e, const char* what) {
+    if (e != cudaSuccess) return fail(h, DNS_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+    return DNS_OK;
+}
+
+void enqueue_step(dns_handle* h) {
+    cudaStream_t st = h->stream;
+    for (auto& G : h->groups) {
+        const GroupView& g = G.v;
+        for (int s = 0; s < 3; ++s) {
+            const double2* cv = s == 0 ? g.v_t : g.v_s;
+            const double2* ce = s == 0 ? g.e_t : g.e_s;
+            const double* cU = s == 0 ? g.U_t : g.U_s;
+            const double* cW = s == 0 ? g.W_t : g.W_s;
+            dnsk::launch_mean_deriv(g, cU, cW, st);
+            if (precision_mixed(h)) {
+                dnsk::launch_yderiv<float>(g, cv, ce, g.P5, st);
+                dnsk::launch_plane_state<float>(g, cU, cW, st);
+                dnsk::launch_forcing<float>(g, s, st);
+            } else {
+                dnsk::launch_yderiv<double>(g, cv, ce, g.P5, st);
+                dnsk::launch_plane_state<double>(g, cU, cW, st);
+                dnsk::launch_forcing<double>(g, s, st);
+            }
+            dnsk::launch_helm(g, s, st);
+            dnsk::launch_mean(g, s, st);
+            h->launches += 6;
+        }
+    }
+}
+
+}  // namespace
+
+namespace dnsk {
+void set_attributes_spectral();
+void set_attributes_plane();
+}
+
+extern "C" {
+
+int dns_create(const dns_config* cfg, void* cuda_stream, dns_handle** out) {
+    if (!cfg || !out || cfg->n_groups < 1 || !cfg->groups) return DNS_ERR_INVALID;
+    *out = nullptr;
+    dns_handle* h = new (std::nothrow) dns_handle();
+    if (!h) return DNS_ERR_NOMEM;
+    h->cfg = *cfg;
+    h->descs.assign(cfg->groups, cfg->groups + cfg->n_groups);
+    h->cfg.groups = h->descs.data();
+    h->stream = (cudaStream_t)cuda_stream;
+    *out = h;
+    if (cfg->precision != DNS_PREC_FP64 && cfg->precision != DNS_PREC_MIXED)
+        return fail(h, DNS_ERR_INVALID, "unknown precision %d", (int)cfg->precision);
+    if (cfg->persistent != 0) return fail(h, DNS_ERR_UNSUPPORTED, "persistent launch not available");
+    h->groups.resize(cfg->n_groups);
+    int nthreads = (int)std::thread::hardware_concurrency();
+    if (nthreads < 1) nthreads = 1;
+    size_t cur = 0;
+    for (int gi = 0; gi < cfg->n_groups; ++gi) {
+        const dns_group_desc& d = h->descs[gi];
+        HostGroup& G = h->groups[gi];
+        G.d = d;
+        if (d.flow != DNS_COUETTE && d.flow != DNS_POISEUILLE)
+            return fail(h, DNS_ERR_INVALID, "group %d: unknown flow", gi);
+        if (!(d.re > 0) || !(d.dt > 0) || !(d.lx > 0) || !(d.lz > 0) || d.members < 1)
+            return fail(h, DNS_ERR_INVALID, "group %d: re, dt, lx, lz must be > 0 and members >= 1", gi);
+        if (d.my < 5 || d.my > 129) return fail(h, DNS_ERR_UNSUPPORTED, "group %d: My=%d outside 5..129", gi, d.my);
+        if (!supported_m(d.mx) || !supported_m(d.mz))
+            return fail(h, DNS_ERR_UNSUPPORTED, "group %d: Mx, Mz must be 16, 32, 48 or 64", gi);
+        GroupView& v = G.v;
+        memset(&v, 0, sizeof v);
+        v.mx = d.mx; v.my = d.my; v.mz = d.mz;
+        v.kx = (d.mx - 1) / 3; v.kz = (d.mz - 1) / 3;
+        v.nkx = v.kx + 1; v.nkz = 2 * v.kz + 1;
+        v.nmodes = v.nkx * v.nkz;
+        v.ny = d.my - 2;
+        v.E = d.members;
+        v.npairs = v.nkx * (v.kz + 1);
+        v.flow = d.flow == DNS_POISEUILLE ? 1 : 0;
+        v.re = d.re; v.dt = d.dt; v.u_wall = d.u_wall; v.bulk_flux = d.bulk_flux;
+        if (!make_plan(d.mx, &v.px) || !make_plan(d.mz, &v.pz))
+            return fail(h, DNS_ERR_UNSUPPORTED, "group %d: no radix plan", gi);
+        size_t smem = dnsk::plane_smem_bytes(v, precision_mixed(h) ? 4 : 8);
+        if (smem > 227 * 1024)
+            return fail(h, DNS_ERR_UNSUPPORTED, "group %d: plane stage needs %zu B of shared memory", gi, smem);
+        // operators
+        G.grid = dnsb::build_grid(d.my);
+        double a1 = dnsb::fundamental(d.lx), a3 = dnsb::fundamental(d.lz);
+        G.kxt.resize(v.nkx); G.kzt.resize(v.nkz);
+        for (int n = 0; n < v.nkx; ++n) G.kxt[n] = n * a1;
+        for (int mi = 0; mi < v.nkz; ++mi) G.kzt[mi] = (mi - v.kz) * a3;
+        G.k2t.resize(v.nmodes); G.k2inv.resize(v.nmodes);
+        for (int mi = 0; mi < v.nkz; ++mi)
+            for (int n = 0; n < v.nkx; ++n) {
+                int q = mi * v.nkx + n;
+                double kx = G.kxt[n], kz = G.kzt[mi];
+                double k2 = kx * kx + kz * kz;
+                G.k2t[q] = k2;
+                G.k2inv[q] = k2 > 0 ? 1.0 / k2 : 0.0;
+            }
+        std::vector<double> pk2(v.npairs);
+        for (int am = 0; am <= v.kz; ++am)
+            for (int n = 0; n < v.nkx; ++n) {
+                double kx = n * a1, kz = am * a3;
+                pk2[am * v.nkx + n] = kx * kx + kz * kz;
+            }
+        const double hs[2] = {0.5, 1.0};
+        const size_t nn = (size_t)v.ny * v.ny;
+        for (int hi = 0; hi < 2; ++hi) {
+            if (!dnsb::build_cn(G.grid, pk2, d.dt, d.re, hs[hi], &G.ops[hi], nthreads))
+                return fail(h, DNS_ERR_INVALID, "group %d: singular implicit operator", gi);
+            auto& od = G.opsdev[hi];
+            od.resize((size_t)v.npairs * 4 * nn);
+            for (int p = 0; p < v.npairs; ++p) {
+                memcpy(&od[((size_t)p * 4 + 0) * nn], &G.ops[hi].Mv[p * nn], nn * 8);
+                memcpy(&od[((size_t)p * 4 + 1) * nn], &G.ops[hi].Pv[p * nn], nn * 8);
+                memcpy(&od[((size_t)p * 4 + 2) * nn], &G.ops[hi].Me[p * nn], nn * 8);
+                memcpy(&od[((size_t)p * 4 + 3) * nn], &G.ops[hi].Pe[p * nn], nn * 8);
+            }
+            auto& md = G.mopsdev[hi];
+            md.clear();
+            md.insert(md.end(), G.ops[hi].MU.begin(), G.ops[hi].MU.end());
+            md.insert(md.end(), G.ops[hi].PU.begin(), G.ops[hi].PU.end());
+            md.insert(md.end(), G.ops[hi].bU.begin(), G.ops[hi].bU.end());
+            md.insert(md.end(), G.ops[hi].Ug.begin(), G.ops[hi].Ug.end());
+        }
+        G.D1i.resize(nn); G.D2i.resize(nn);
+        for (int i = 0; i < v.ny; ++i)
+            for (int j = 0; j < v.ny; ++j) {
+                G.D1i[(size_t)i * v.ny + j] = G.grid.D1[(size_t)(i + 1) * d.my + (j + 1)];
+                G.D2i[(size_t)i * v.ny + j] = G.grid.D2[(size_t)(i + 1) * d.my + (j + 1)];
+            }
+        G.twx = dnsb::twiddles(d.mx);
+        G.twz = dnsb::twiddles(d.mz);
+        G.twxf.assign(G.twx.begin(), G.twx.end());
+        G.twzf.assign(G.twz.begin(), G.twz.end());
+        G.kxtf.assign(G.kxt.begin(), G.kxt.end());
+        G.kztf.assign(G.kzt.begin(), G.kzt.end());
+        G.k2invf.assign(G.k2inv.begin(), G.k2inv.end());
+        cur = layout_group(h, G, cur);
+    }
+    h->need = align256(cur);
+    return DNS_OK;
+}
+
+int dns_workspace_size(const dns_handle* h, size_t* bytes) {
+    if (!h || !bytes) return DNS_ERR_INVALID;
+    *bytes = h->need;
+    return DNS_OK;
+}
+
+int dns_bind_workspace(dns_handle* h, void* dev_ptr, size_t bytes) {
+    if (!h) return DNS_ERR_INVALID;
+    if (!dev_ptr || ((uintptr_t)dev_ptr & 255)) return fail(h, DNS_ERR_INVALID, "workspace NULL or not 256-byte aligned");
+    if (bytes < h->need) return fail(h, DNS_ERR_NOMEM, "workspace has %zu bytes, needs %zu", bytes, h->need);
+    h->ws = (char*)dev_ptr;
+    h->ws_bytes = bytes;
+    if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
+    if (h->graph) { cudaGraphDestroy(h->graph); h->graph = nullptr; }
+    dnsk::set_attributes_spectral();
+    dnsk::set_attributes_plane();
+    cudaStream_t st = h->stream;
+    int rc = check(h, cudaMemsetAsync(dev_ptr, 0, h->need, st), "clear workspace");
+    if (rc) return rc;
+    for (auto& G : h->groups) {
+        for (auto& s : G.slots) *s.first = h->ws + s.second.off;
+        GroupView& v = G.v;
+        if (!precision_mixed(h)) v.P5d = (double2*)v.P5;
+        struct Up { const void* dst; const void* src; size_t bytes; };
+        const Up ups[] = {
+            {v.D1, G.grid.D1.data(), G.grid.D1.size() * 8},
+            {v.D1i, G.D1i.data(), G.D1i.size() * 8},
+            {v.D2i, G.D2i.data(), G.D2i.size() * 8},
+            {v.ccw, G.grid.ccw.data(), G.grid.ccw.size() * 8},
+            {v.kxt, G.kxt.data(), G.kxt.size() * 8},
+            {v.kzt, G.kzt.data(), G.kzt.size() * 8},
+            {v.k2t, G.k2t.data(), G.k2t.size() * 8},
+            {v.k2inv, G.k2inv.data(), G.k2inv.size() * 8},
+            {v.twx, G.twx.data(), G.twx.size() * 8},
+            {v.twz, G.twz.data(), G.twz.size() * 8},
+            {v.twxf, G.twxf.data(), G.twxf.size() * 4},
+            {v.twzf, G.twzf.data(), G.twzf.size() * 4},
+            {v.kxtf, G.kxtf.data(), G.kxtf.size() * 4},
+            {v.kztf, G.kztf.data(), G.kztf.size() * 4},
+            {v.k2invf, G.k2invf.data(), G.k2invf.size() * 4},
+            {v.ops[0], G.opsdev[0].data(), G.opsdev[0].size() * 8},
+            {v.ops[1], G.opsdev[1].data(), G.opsdev[1].size() * 8},
+            {v.mops[0], G.mopsdev[0].data(), G.mopsdev[0].size() * 8},
+            {v.mops[1], G.mopsdev[1].data(), G.mopsdev[1].size() * 8},
+        };
+        for (const auto& u : ups) {
+            rc = check(h, cudaMemcpyAsync((void*)u.dst, u.src, u.bytes, cudaMemcpyHostToDevice, st), "upload operators");
+            if (rc) return rc;
+        }
+    }
+    rc = check(h, cudaStreamSynchronize(st), "bind workspace");
+    if (rc) return rc;
+    h->bound = true;
+    return DNS_OK;
+}
+
+int dns_state_shape(const dns_handle* h, int group, int* n_kx, int* n_kz, int* ny_int, int* my) {
+    if (!h || group < 0 || group >= (int)h->groups.size()) return DNS_ERR_INVALID;
+    const GroupView& v = h->groups[group].v;
+    if (n_kx) *n_kx = v.nkx;
+    if (n_kz) *n_kz = v.nkz;
+    if (ny_int) *ny_int = v.ny;
+    if (my) *my = v.my;
+    return DNS_OK;
+}
+
+int dns_set_state(dns_handle* h, int group, int member0, int count, const double* v_hat,
+                  const double* eta_hat, const double* U00, const double* W00, int ptr_kind) {
+    if (!h) return DNS_ERR_INVALID;
+    if (!h->bound) return fail(h, DNS_ERR_INVALID, "workspace not bound");
+    if (group < 0 || group >= (int)h->groups.size()) return fail(h, DNS_ERR_INVALID, "bad group");
+    GroupView& v = h->groups[group].v;
+    if (member0 < 0 || count < 1 || member0 + count > v.E) return fail(h, DNS_ERR_INVALID, "member range");
+    if (!v_hat || !eta_hat || !U00 || !W00) return fail(h, DNS_ERR_INVALID, "NULL state pointer");
+    if (ptr_kind != 0 && ptr_kind != 1) return fail(h, DNS_ERR_INVALID, "ptr_kind must be 0 or 1");
+    cudaMemcpyKind k = ptr_kind ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    const size_t per = (size_t)count * v.ny * v.nmodes;
+    cudaStream_t st = h->stream;
+    int rc;
+    if ((rc = check(h, cudaMemcpyAsync(v.stage, v_hat, per * sizeof(double2), k, st), "set v"))) return rc;
+    if ((rc = check(h, cudaMemcpyAsync(v.stage + per, eta_hat, per * sizeof(double2), k, st), "set eta"))) return rc;
+    if ((rc = check(h, cudaMemcpyAsync(v.U_t + (size_t)member0 * v.my, U00, sizeof(double) * count * v.my, k, st), "set U")))
+        return rc;
+    if ((rc = check(h, cudaMemcpyAsync(v.W_t + (size_t)member0 * v.my, W00, sizeof(double) * count * v.my, k, st), "set W")))
+        return rc;
+    dnsk::launch_pack(v, member0, count, st);
+    if ((rc = check(h, cudaGetLastError(), "pack state"))) return rc;
+    // host buffers may be pageable and reused by the caller right away
+    if (ptr_kind == 0) return check(h, cudaStreamSynchronize(st), "set state");
+    return DNS_OK;
+}
+
+int dns_get_state(const dns_handle* hc, int group, int member0, int count, double* v_hat,
+                  double* eta_hat, double* U00, double* W00, int ptr_kind) {
+    dns_handle* h = const_cast<dns_handle*>(hc);
+    if (!h) return DNS_ERR_INVALID;
+    if (!h->bound) return fail(h, DNS_ERR_INVALID, "workspace not bound");
+    if (group < 0 || group >= (int)h->groups.size()) return fail(h, DNS_ERR_INVALID, "bad group");
+    GroupView& v = h->groups[group].v;
+    if (member0 < 0 || count < 1 || member0 + count > v.E) return fail(h, DNS_ERR_INVALID, "member range");
+    if (ptr_kind != 0 && ptr_kind != 1) return fail(h, DNS_ERR_INVALID, "ptr_kind must be 0 or 1");
+    cudaMemcpyKind k = ptr_kind ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    const size_t per = (size_t)count * v.ny * v.nmodes;
+    cudaStream_t st = h->stream;
+    dnsk::launch_unpack(v, member0, count, st);
+    int rc;
+    if ((rc = check(h, cudaGetLastError(), "unpack state"))) return rc;
+    if (v_hat && (rc = check(h, cudaMemcpyAsync(v_hat, v.stage, per * sizeof(double2), k, st), "get v"))) return rc;
+    if (eta_hat && (rc = check(h, cudaMemcpyAsync(eta_hat, v.stage + per, per * sizeof(double2), k, st), "get eta")))
+        return rc;
+    if (U00 && (rc = check(h, cudaMemcpyAsync(U00, v.U_t + (size_t)member0 * v.my, sizeof(double) * count * v.my, k, st),
+                           "get U")))
+        return rc;
+    if (W00 && (rc = check(h, cudaMemcpyAsync(W00, v.W_t + (size_t)member0 * v.my, sizeof(double) * count * v.my, k, st),
+                           "get W")))
+        return rc;
+    return check(h, cudaStreamSynchronize(st), "get state");
+}
+
+int dns_step(dns_handle* h, int nsteps) {
+    if (!h) return DNS_ERR_INVALID;
+    if (!h->bound) return fail(h, DNS_ERR_INVALID, "workspace not bound");
+    if (nsteps < 0) return fail(h, DNS_ERR_INVALID, "nsteps < 0");
+    h->launches = 0;
+    int rc;
+    if (h->cfg.use_graph) {
+        if (h->stream == nullptr)
+            return fail(h, DNS_ERR_INVALID, "graph capture needs a non-default stream (got the legacy NULL stream)");
+        if (!h->gexec) {
+            int before = h->launches;
+            if ((rc = check(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal), "begin capture")))
+                return rc;
+            enqueue_step(h);
+            cudaGraph_t gr = nullptr;
+            if ((rc = check(h, cudaStreamEndCapture(h->stream, &gr), "end capture"))) return rc;
+            h->graph = gr;
+            if ((rc = check(h, cudaGraphInstantiate(&h->gexec, gr, 0), "instantiate graph"))) return rc;
+            h->graph_launches = h->launches - before;
+            h->launches = 0;
+        }
+        for (int i = 0; i < nsteps; ++i) {
+            if ((rc = check(h, cudaGraphLaunch(h->gexec, h->stream), "graph launch"))) return rc;
+            h->launches += h->graph_launches;
+        }
+    } else {
+        for (int i = 0; i < nsteps; ++i) enqueue_step(h);
+    }
+    return check(h, cudaGetLastError(), "step launch");
+}
+
+int dns_stats(dns_handle* h, int group, dns_stats_t* per_member, dns_stats_t* ensemble_mean, double* profiles) {
+    if (!h) return DNS_ERR_INVALID;
+    if (!h->bound) return fail(h, DNS_ERR_INVALID, "workspace not bound");
+    if (group < 0 || group >= (int)h->groups.size()) return fail(h, DNS_ERR_INVALID, "bad group");
+    if (!per_member) return fail(h, DNS_ERR_INVALID, "per_member is NULL");
+    GroupView& v = h->groups[group].v;
+    cudaStream_t st = h->stream;
+    dnsk::launch_stats(v, st);
+    int rc;
+    if ((rc = check(h, cudaGetLastError(), "stats launch"))) return rc;
+    std::vector<double> out((size_t)v.E * 8);
+    if ((rc = check(h, cudaMemcpyAsync(out.data(), v.st_out, out.size() * 8, cudaMemcpyDeviceToHost, st), "stats copy")))
+        return rc;
+    if (profiles &&
+        (rc = check(h, cudaMemcpyAsync(profiles, v.prof, sizeof(double) * (size_t)v.E * 6 * v.my, cudaMemcpyDeviceToHost, st),
+                    "profile copy")))
+        return rc;
+    if ((rc = check(h, cudaStreamSynchronize(st), "stats"))) return rc;
+    bool any_nf = false;
+    dns_stats_t mean;
+    memset(&mean, 0, sizeof mean);
+    for (int e = 0; e < v.E; ++e) {
+        dns_stats_t& s = per_member[e];
+        const double* o = &out[(size_t)e * 8];
+        s.e_total = o[0]; s.e_pert = o[1]; s.tau_bottom = o[2]; s.tau_top = o[3];
+        s.bulk_flux = o[4]; s.gamma = o[5]; s.max_div = o[6];
+        s.nonfinite = o[7] != 0.0 ? 1 : 0;
+        s.reserved = 0;
+        any_nf = any_nf || s.nonfinite;
+        mean.e_total += s.e_total / v.E; mean.e_pert += s.e_pert / v.E;
+        mean.tau_bottom += s.tau_bottom / v.E; mean.tau_top += s.tau_top / v.E;
+        mean.bulk_flux += s.bulk_flux / v.E; mean.gamma += s.gamma / v.E;
+        mean.max_div = mean.max_div > s.max_div ? mean.max_div : s.max_div;
+        mean.nonfinite |= s.nonfinite;
+    }
+    if (ensemble_mean) *ensemble_mean = mean;
+    return any_nf ? DNS_ERR_NONFINITE : DNS_OK;
+}
+
+int dns_destroy(dns_handle* h) {
+    if (!h) return DNS_ERR_INVALID;
+    if (h->bound) cudaStreamSynchronize(h->stream);
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    if (h->graph) cudaGraphDestroy(h->graph);
+    delete h;
+    return DNS_OK;
+}
+
+const char* dns_last_error(const dns_handle* h) { return h ? h->err.c_str() : "NULL handle"; }
+
+int dns_last_launch_count(const dns_handle* h) { return h ? h->launches : 0; }
+
+int dns_export_grid(const dns_handle* h, int group, double* y, double* D1, double* D2, double* D4c, double* ccw) {
+    if (!h || group < 0 || group >= (int)h->groups.size()) return DNS_ERR_INVALID;
+    const dnsb::GridOps& g = h->groups[group].grid;
+    if (y) memcpy(y, g.y.data(), g.y.size() * 8);
+    if (D1) memcpy(D1, g.D1.data(), g.D1.size() * 8);
+    if (D2) memcpy(D2, g.D2.data(), g.D2.size() * 8);
+    if (D4c) memcpy(D4c, g.D4c.data(), g.D4c.size() * 8);
+    if (ccw) memcpy(ccw, g.ccw.data(), g.ccw.size() * 8);
+    return DNS_OK;
+}
+
+int dns_export_operators(const dns_handle* h, int group, int h_index, int pair, double* Mv, double* Pv,
+                         double* Me, double* Pe) {
+    if (!h || group < 0 || group >= (int)h->groups.size() || h_index < 0 || h_index > 1) return DNS_ERR_INVALID;
+    const HostGroup& G = h->groups[group];
+    if (pair < 0 || pair >= G.v.npairs) return DNS_ERR_INVALID;
+    const size_t nn = (size_t)G.v.ny * G.v.ny;
+    const dnsb::CnOps& o = G.ops[h_index];
+    if (Mv) memcpy(Mv, &o.Mv[pair * nn], nn * 8);
+    if (Pv) memcpy(Pv, &o.Pv[pair * nn], nn * 8);
+    if (Me) memcpy(Me, &o.Me[pair * nn], nn * 8);
+    if (Pe) memcpy(Pe, &o.Pe[pair * nn], nn * 8);
+    return DNS_OK;
+}
+
+}  // extern "C"

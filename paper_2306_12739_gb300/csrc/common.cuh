@@ -1,0 +1,146 @@
+// Device-side helpers shared by the DNS kernels: complex arithmetic and the
+// CTA-wide shared-memory FFT (Stockham autosort, mixed radix 2/3/4).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dnsk {
+
+template <typename T> struct C2;
+template <> struct C2<double> { typedef double2 type; };
+template <> struct C2<float> { typedef float2 type; };
+
+template <typename C>
+__device__ __forceinline__ C cadd(C a, C b) { C r; r.x = a.x + b.x; r.y = a.y + b.y; return r; }
+template <typename C>
+__device__ __forceinline__ C csub(C a, C b) { C r; r.x = a.x - b.x; r.y = a.y - b.y; return r; }
+template <typename C>
+__device__ __forceinline__ C cmul(C a, C b) {
+    C r; r.x = a.x * b.x - a.y * b.y; r.y = a.x * b.y + a.y * b.x; return r;
+}
+template <typename C, typename T>
+__device__ __forceinline__ C cscale(C a, T s) { C r; r.x = a.x * s; r.y = a.y * s; return r; }
+// i * a
+template <typename C>
+__device__ __forceinline__ C cmuli(C a) { C r; r.x = -a.y; r.y = a.x; return r; }
+template <typename C>
+__device__ __forceinline__ C cconj(C a) { C r; r.x = a.x; r.y = -a.y; return r; }
+template <typename C>
+__device__ __forceinline__ C czero() { C r; r.x = 0; r.y = 0; return r; }
+
+// Radix plan of one transform length N = 2^a 3^b <= 128.
+struct FftPlan {
+    int n;
+    int nst;
+    int rad[5];
+};
+
+// Radix-R DFT of v[0..R-1] in registers; SIGN = -1 forward, +1 inverse.
+template <typename C, int SIGN>
+__device__ __forceinline__ void butterfly(C* v, int R) {
+    if (R == 2) {
+        C a = v[0], b = v[1];
+        v[0] = cadd(a, b); v[1] = csub(a, b);
+    } else if (R == 4) {
+        C a = cadd(v[0], v[2]), b = csub(v[0], v[2]);
+        C c = cadd(v[1], v[3]), d = csub(v[1], v[3]);
+        C id = cmuli(d);
+        if (SIGN < 0) { id.x = -id.x; id.y = -id.y; }
+        v[0] = cadd(a, c); v[2] = csub(a, c);
+        v[1] = cadd(b, id); v[3] = csub(b, id);
+    } else {  // R == 3
+        typedef decltype(v[0].x) T;
+        const T h = (T)0.86602540378443864676;   // sqrt(3)/2
+        C t1 = cadd(v[1], v[2]), t2 = csub(v[1], v[2]);
+        C x0 = cadd(v[0], t1);
+        C m; m.x = v[0].x - (T)0.5 * t1.x; m.y = v[0].y - (T)0.5 * t1.y;
+        C s = cscale(cmuli(t2), (T)(SIGN) * h);
+        v[0] = x0; v[1] = cadd(m, s); v[2] = csub(m, s);
+    }
+}
+
+// CTA-wide Stockham FFT of nl lines of length p.n stored contiguously in b0
+// (line stride p.n); b1 is scratch of the same size.  tw holds the forward
+// twiddles exp(-2 pi i t / n), t < n.  Returns the buffer holding the result.
+// Must be called by every thread of the CTA; ends with a __syncthreads.
+template <typename C, int SIGN>
+__device__ C* fft_lines(C* b0, C* b1, int nl, const FftPlan& p, const C* tw) {
+    C* src = b0;
+    C* dst = b1;
+    const int N = p.n;
+    int Ns = 1;
+    for (int s = 0; s < p.nst; ++s) {
+        const int R = p.rad[s];
+        const int nb = N / R;
+        const int tstep = N / (Ns * R);
+        for (int idx = threadIdx.x; idx < nl * nb; idx += blockDim.x) {
+            int line = idx / nb;
+            int j = idx - line * nb;
+            const C* in = src + line * N;
+            C* out = dst + line * N;
+            int k = j % Ns;
+            C v[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+                if (r < R) v[r] = in[j + r * nb];
+            if (Ns > 1) {
+#pragma unroll
+                for (int r = 1; r < 4; ++r)
+                    if (r < R) {
+                        C w = tw[k * r * tstep];
+                        if (SIGN > 0) w.y = -w.y;
+                        v[r] = cmul(v[r], w);
+                    }
+            }
+            butterfly<C, SIGN>(v, R);
+            int base = (j / Ns) * Ns * R + k;
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+                if (r < R) out[base + r * Ns] = v[r];
+        }
+        __syncthreads();
+        C* t = src; src = dst; dst = t;
+        Ns *= R;
+    }
+    return src;
+}
+
+// Block-wide sum of a double (blockDim.x multiple of 32, <= 1024); result valid in
+// every thread.  red must hold 32 doubles.
+__device__ __forceinline__ double block_sum(double v, double* red) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) red[w] = v;
+    __syncthreads();
+    int nw = blockDim.x >> 5;
+    double t = (threadIdx.x < nw) ? red[threadIdx.x] : 0.0;
+    if (w == 0) {
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (l == 0) red[0] = t;
+    }
+    __syncthreads();
+    double r = red[0];
+    __syncthreads();
+    return r;
+}
+
+__device__ __forceinline__ double block_max(double v, double* red) {
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) red[w] = v;
+    __syncthreads();
+    int nw = blockDim.x >> 5;
+    double t = (threadIdx.x < nw) ? red[threadIdx.x] : 0.0;
+    if (w == 0) {
+        for (int o = 16; o > 0; o >>= 1) t = fmax(t, __shfl_xor_sync(0xffffffffu, t, o));
+        if (l == 0) red[0] = t;
+    }
+    __syncthreads();
+    double r = red[0];
+    __syncthreads();
+    return r;
+}
+
+}  // namespace dnsk

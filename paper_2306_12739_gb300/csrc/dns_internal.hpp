@@ -1,0 +1,76 @@
+// Internal structures shared by the host orchestration and the kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstddef>
+#include "common.cuh"
+
+namespace dnsk {
+
+// Device-side view of one group.  Spectral arrays use two layouts:
+//   H ("per-mode") layout  [q][y][e]  complex: the state, forcings and their
+//                          accumulators; the block of mode q is a contiguous
+//                          Ny x E complex matrix, i.e. the right-hand side of the
+//                          per-wavenumber operators.
+//   P ("per-plane") layout [y][e][q]  complex: inputs and outputs of the
+//                          physical-space stage, one contiguous run of all modes
+//                          per (plane, member).
+// with q = (m + Kz) * NKX + n, NKX = Kx + 1, y the interior index 0..Ny-1.
+struct GroupView {
+    int mx, my, mz, kx, kz, nkx, nkz, nmodes, ny, E, npairs;
+    int flow;             // 0 Couette, 1 Poiseuille
+    double re, dt, u_wall, bulk_flux;
+    FftPlan px, pz;
+    // constants
+    const double* D1;     // [My][My]
+    const double* D1i;    // [Ny][Ny]
+    const double* D2i;    // [Ny][Ny]
+    const double* ccw;    // [My]
+    const double* kxt;    // [NKX]
+    const double* kzt;    // [NKZ]
+    const double* k2t;    // [nmodes]
+    const double* k2inv;  // [nmodes], 0 at the mean mode
+    const double2* twx;   // [Mx]
+    const double2* twz;   // [Mz]
+    const float2* twxf;
+    const float2* twzf;
+    const float* kxtf;
+    const float* kztf;
+    const float* k2invf;
+    const double* ops[2];   // per h index: [npairs][4][Ny][Ny]  (Mv, Pv, Me, Pe)
+    const double* mops[2];  // per h index: MU [Ny][Ny], PU [Ny][Ny], bU [Ny][2], Ug [Ny]
+    // state, H layout
+    double2 *v_t, *e_t, *v_s, *e_s;
+    double2 *mx1_v, *mx1_e;       // M_1 x_t, shared by sub-steps 2 and 3
+    double2 *Fv, *Fe, *Av, *Ae;   // combined forcing of this sub-step; RK accumulators
+    double *U_t, *W_t, *U_s, *W_s;   // [E][My]
+    double *AU, *AW;                 // mean forcing accumulators [E][Ny]
+    double *dU, *dW;                 // [E][My] dU/dy, dW/dy of the sub-step state
+    double *uv, *wv;                 // [E][My] plane means <uv>, <wv>
+    double* gamma;                   // [E]
+    // P layout work arrays (element type by precision)
+    void* P5;    // 5 fields: v, Dv, D2v, eta, Deta
+    void* N3;    // 3 fields: Nu, Nv, Nw
+    double2* P5d;  // FP64 copy for statistics (== P5 in FP64 mode)
+    // statistics
+    double* st_y;    // [E][Ny][6]: uu, vv, ww, uv, maxdiv, nonfinite
+    double* st_out;  // [E][8] packed dns_stats_t doubles (+nonfinite as double)
+    double* prof;    // [E][6][My]
+    double2* stage;  // host-layout staging [E][Ny][nmodes] x 2 fields
+};
+
+void launch_mean_deriv(const GroupView& g, const double* U, const double* W, cudaStream_t st);
+template <typename T>
+void launch_yderiv(const GroupView& g, const double2* v, const double2* e, void* P5, cudaStream_t st);
+template <typename T>
+void launch_plane_state(const GroupView& g, const double* U, const double* W, cudaStream_t st);
+template <typename T>
+void launch_forcing(const GroupView& g, int s, cudaStream_t st);
+void launch_helm(const GroupView& g, int s, cudaStream_t st);
+void launch_mean(const GroupView& g, int s, cudaStream_t st);
+void launch_stats(const GroupView& g, cudaStream_t st);
+void launch_pack(const GroupView& g, int member0, int count, cudaStream_t st);
+void launch_unpack(const GroupView& g, int member0, int count, cudaStream_t st);
+size_t plane_smem_bytes(const GroupView& g, int elem_bytes);
+int plane_threads();
+
+}  // namespace dnsk

@@ -1,0 +1,490 @@
+// Spectral-space kernels of one CN/RK3 sub-step (paper Sec. 3):
+//   k_mean_deriv  dU00/dy, dW00/dy of the sub-step state
+//   k_yderiv      Dv, D2v, D eta on the interior nodes (y-contraction with the
+//                 shared Chebyshev operators, Sec. 3.1) and the H -> P relayout
+//   k_forcing     F = -k^2 Nv - D(i kx Nu + i kz Nw), G = i kz Nu - i kx Nw
+//                 (Eqs. Dv, eta) and the RK3 combination of Sec. 3.1
+//   k_helm        x_s = M_h x_t + P_h F~ per wavenumber pair (Eqs. CN1, CN2),
+//                 with M_1 x_t computed once and reused by sub-steps 2 and 3
+//   k_mean        U00, W00 update (Eqs. CN3, CN4) with the wall columns on the
+//                 right-hand side and the Poiseuille constant-flux gamma
+//   k_stats_*     one-point statistics (Sec. 4)
+//   k_pack/unpack host layout <-> H layout, Hermitian projection of n = 0
+#include "dns_internal.hpp"
+
+namespace dnsk {
+
+// ----------------------------------------------------------------- mean derivs
+
+__global__ void k_mean_deriv(const double* __restrict__ D1, const double* __restrict__ U,
+                             const double* __restrict__ W, double* __restrict__ dU,
+                             double* __restrict__ dW, int My) {
+    int e = blockIdx.x;
+    for (int i = threadIdx.x; i < My; i += blockDim.x) {
+        double su = 0.0, sw = 0.0;
+        for (int j = 0; j < My; ++j) {
+            double d = D1[i * My + j];
+            su += d * U[e * My + j];
+            sw += d * W[e * My + j];
+        }
+        dU[e * My + i] = su;
+        dW[e * My + i] = sw;
+    }
+}
+
+void launch_mean_deriv(const GroupView& g, const double* U, const double* W, cudaStream_t st) {
+    k_mean_deriv<<<g.E, 128, 0, st>>>(g.D1, U, W, g.dU, g.dW, g.my);
+}
+
+// ------------------------------------------------------------------ y-derivs
+
+constexpr int QB = 8;   // modes per tile
+constexpr int EB = 4;   // members per tile
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_yderiv(const double2* __restrict__ v, const double2* __restrict__ et,
+                                                const double* __restrict__ D1i, const double* __restrict__ D2i,
+                                                typename C2<T>::type* __restrict__ P5, int Ny, int E, int nmodes) {
+    typedef typename C2<T>::type C;
+    extern __shared__ __align__(16) unsigned char sm[];
+    double2* xv = (double2*)sm;                 // [QB][Ny][EB]
+    double2* xe = xv + QB * Ny * EB;
+    const int q0 = blockIdx.x * QB, e0 = blockIdx.y * EB;
+    const int tile = QB * Ny * EB;
+    for (int idx = threadIdx.x; idx < tile; idx += blockDim.x) {
+        int ee = idx % EB;
+        int y = (idx / EB) % Ny;
+        int qq = idx / (EB * Ny);
+        int q = q0 + qq, e = e0 + ee;
+        double2 a = make_double2(0.0, 0.0), b = a;
+        if (q < nmodes && e < E) {
+            size_t o = ((size_t)q * Ny + y) * E + e;
+            a = v[o];
+            b = et[o];
+        }
+        xv[idx] = a;
+        xe[idx] = b;
+    }
+    __syncthreads();
+    const size_t fs = (size_t)Ny * E * nmodes;
+    for (int idx = threadIdx.x; idx < tile; idx += blockDim.x) {
+        int qq = idx % QB;
+        int ee = (idx / QB) % EB;
+        int y = idx / (QB * EB);
+        int q = q0 + qq, e = e0 + ee;
+        double dvx = 0, dvy = 0, d2x = 0, d2y = 0, dex = 0, dey = 0;
+        const double* r1 = D1i + (size_t)y * Ny;
+        const double* r2 = D2i + (size_t)y * Ny;
+        for (int k = 0; k < Ny; ++k) {
+            double d1 = __ldg(r1 + k), d2 = __ldg(r2 + k);
+            double2 a = xv[(qq * Ny + k) * EB + ee];
+            double2 b = xe[(qq * Ny + k) * EB + ee];
+            dvx += d1 * a.x; dvy += d1 * a.y;
+            d2x += d2 * a.x; d2y += d2 * a.y;
+            dex += d1 * b.x; dey += d1 * b.y;
+        }
+        if (q < nmodes && e < E) {
+            size_t o = ((size_t)y * E + e) * nmodes + q;
+            double2 a = xv[(qq * Ny + y) * EB + ee];
+            double2 b = xe[(qq * Ny + y) * EB + ee];
+            C c;
+            c.x = (T)a.x; c.y = (T)a.y; P5[o] = c;
+            c.x = (T)dvx; c.y = (T)dvy; P5[fs + o] = c;
+            c.x = (T)d2x; c.y = (T)d2y; P5[2 * fs + o] = c;
+            c.x = (T)b.x; c.y = (T)b.y; P5[3 * fs + o] = c;
+            c.x = (T)dex; c.y = (T)dey; P5[4 * fs + o] = c;
+        }
+    }
+}
+
+template <typename T>
+void launch_yderiv(const GroupView& g, const double2* v, const double2* e, void* P5, cudaStream_t st) {
+    dim3 grid((g.nmodes + QB - 1) / QB, (g.E + EB - 1) / EB);
+    size_t smem = 2 * (size_t)QB * g.ny * EB * sizeof(double2);
+    k_yderiv<T><<<grid, 256, smem, st>>>(v, e, g.D1i, g.D2i, (typename C2<T>::type*)P5, g.ny, g.E, g.nmodes);
+}
+template void launch_yderiv<double>(const GroupView&, const double2*, const double2*, void*, cudaStream_t);
+template void launch_yderiv<float>(const GroupView&, const double2*, const double2*, void*, cudaStream_t);
+
+// ------------------------------------------------------------------- forcing
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_forcing(GroupView g, int s) {
+    typedef typename C2<T>::type C;
+    extern __shared__ __align__(16) unsigned char sm[];
+    double2* phi = (double2*)sm;   // [QB][Ny][EB]
+    const int Ny = g.ny, E = g.E, nmodes = g.nmodes, NKX = g.nkx;
+    const int q0 = blockIdx.x * QB, e0 = blockIdx.y * EB;
+    const int tile = QB * Ny * EB;
+    const size_t fs = (size_t)Ny * E * nmodes;
+    const C* N3 = (const C*)g.N3;
+    for (int idx = threadIdx.x; idx < tile; idx += blockDim.x) {
+        int qq = idx % QB;
+        int ee = (idx / QB) % EB;
+        int y = idx / (QB * EB);
+        int q = q0 + qq, e = e0 + ee;
+        double2 p = make_double2(0.0, 0.0);
+        if (q < nmodes && e < E) {
+            size_t o = ((size_t)y * E + e) * nmodes + q;
+            C nu = N3[o], nw = N3[2 * fs + o];
+            int mi = q / NKX, n = q - mi * NKX;
+            double kx = g.kxt[n], kz = g.kzt[mi];
+            // i kx Nu + i kz Nw
+            double ax = kx * (double)nu.x + kz * (double)nw.x;
+            double ay = kx * (double)nu.y + kz * (double)nw.y;
+            p = make_double2(-ay, ax);
+        }
+        phi[(qq * Ny + y) * EB + ee] = p;
+    }
+    __syncthreads();
+    const int q_mean = g.kz * NKX;
+    for (int idx = threadIdx.x; idx < tile; idx += blockDim.x) {
+        int ee = idx % EB;
+        int y = (idx / EB) % Ny;
+        int qq = idx / (EB * Ny);
+        int q = q0 + qq, e = e0 + ee;
+        if (q >= nmodes || e >= E) continue;
+        double sx = 0.0, sy = 0.0;
+        const double* r1 = g.D1i + (size_t)y * Ny;
+        for (int k = 0; k < Ny; ++k) {
+            double d = __ldg(r1 + k);
+            double2 p = phi[(qq * Ny + k) * EB + ee];
+            sx += d * p.x; sy += d * p.y;
+        }
+        size_t o = ((size_t)y * E + e) * nmodes + q;
+        C nu = N3[o], nv = N3[fs + o], nw = N3[2 * fs + o];
+        int mi = q / NKX, n = q - mi * NKX;
+        double kx = g.kxt[n], kz = g.kzt[mi], k2 = g.k2t[q];
+        double2 F, G;
+        F.x = -k2 * (double)nv.x - sx;
+        F.y = -k2 * (double)nv.y - sy;
+        // i kz Nu - i kx Nw
+        double bx = kz * (double)nu.x - kx * (double)nw.x;
+        double by = kz * (double)nu.y - kx * (double)nw.y;
+        G = make_double2(-by, bx);
+        if (q == q_mean) { F = make_double2(0.0, 0.0); G = F; }
+        size_t h = ((size_t)q * Ny + y) * E + e;
+        double2 Ft, Gt;
+        if (s == 0) {
+            Ft = F; Gt = G;
+            g.Av[h] = F; g.Ae[h] = G;
+        } else if (s == 1) {
+            double2 a = g.Av[h], b = g.Ae[h];
+            Ft = make_double2(2.0 * F.x - a.x, 2.0 * F.y - a.y);
+            Gt = make_double2(2.0 * G.x - b.x, 2.0 * G.y - b.y);
+            g.Av[h] = make_double2((1.0 / 6.0) * a.x + (4.0 / 6.0) * F.x, (1.0 / 6.0) * a.y + (4.0 / 6.0) * F.y);
+            g.Ae[h] = make_double2((1.0 / 6.0) * b.x + (4.0 / 6.0) * G.x, (1.0 / 6.0) * b.y + (4.0 / 6.0) * G.y);
+        } else {
+            double2 a = g.Av[h], b = g.Ae[h];
+            Ft = make_double2(a.x + (1.0 / 6.0) * F.x, a.y + (1.0 / 6.0) * F.y);
+            Gt = make_double2(b.x + (1.0 / 6.0) * G.x, b.y + (1.0 / 6.0) * G.y);
+        }
+        g.Fv[h] = Ft;
+        g.Fe[h] = Gt;
+    }
+}
+
+template <typename T>
+void launch_forcing(const GroupView& g, int s, cudaStream_t st) {
+    dim3 grid((g.nmodes + QB - 1) / QB, (g.E + EB - 1) / EB);
+    size_t smem = (size_t)QB * g.ny * EB * sizeof(double2);
+    k_forcing<T><<<grid, 256, smem, st>>>(g, s);
+}
+template void launch_forcing<double>(const GroupView&, int, cudaStream_t);
+template void launch_forcing<float>(const GroupView&, int, cudaStream_t);
+
+// --------------------------------------------------------------------- helm
+
+__global__ void __launch_bounds__(256) k_helm(GroupView g, int s) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    const int Ny = g.ny, E = g.E, NKX = g.nkx;
+    const int p = blockIdx.x, f = blockIdx.y;
+    const int n = p % NKX, am = p / NKX;
+    if (n == 0 && am == 0) return;
+    const int hi = (s == 0) ? 0 : 1;
+    const size_t nn = (size_t)Ny * Ny;
+    const double* Mg = g.ops[hi] + ((size_t)p * 4 + (f == 0 ? 0 : 2)) * nn;
+    const double* Pg = Mg + nn;
+    double* Ms = (double*)sm;
+    double* Ps = Ms + nn;
+    const bool needM = (s != 2);
+    for (size_t i = threadIdx.x; i < nn; i += blockDim.x) {
+        if (needM) Ms[i] = Mg[i];
+        Ps[i] = Pg[i];
+    }
+    __syncthreads();
+    const int nq = am > 0 ? 2 : 1;
+    const int q1 = (g.kz + am) * NKX + n, q2 = (g.kz - am) * NKX + n;
+    const double2* X = f == 0 ? g.v_t : g.e_t;
+    const double2* F = f == 0 ? g.Fv : g.Fe;
+    double2* M1 = f == 0 ? g.mx1_v : g.mx1_e;
+    double2* O = (s == 2) ? (f == 0 ? g.v_t : g.e_t) : (f == 0 ? g.v_s : g.e_s);
+    const int ncol = 2 * E;
+    const int per = Ny * ncol;
+    for (int idx = threadIdx.x; idx < nq * per; idx += blockDim.x) {
+        int which = idx / per;
+        int r = idx - which * per;
+        int y = r / ncol, c = r - y * ncol;
+        int q = which == 0 ? q1 : q2;
+        const double* xc = (const double*)(X + (size_t)q * Ny * E);
+        const double* fc = (const double*)(F + (size_t)q * Ny * E);
+        double* m1 = (double*)(M1 + (size_t)q * Ny * E);
+        double* oc = (double*)(O + (size_t)q * Ny * E);
+        double accP = 0.0;
+        const double* pr = Ps + (size_t)y * Ny;
+        for (int k = 0; k < Ny; ++k) accP += pr[k] * fc[k * ncol + c];
+        double out;
+        if (needM) {
+            double accM = 0.0;
+            const double* mr = Ms + (size_t)y * Ny;
+            for (int k = 0; k < Ny; ++k) accM += mr[k] * xc[k * ncol + c];
+            if (s == 1) m1[y * ncol + c] = accM;
+            out = accM + accP;
+        } else {
+            out = m1[y * ncol + c] + accP;
+        }
+        oc[y * ncol + c] = out;
+    }
+}
+
+void launch_helm(const GroupView& g, int s, cudaStream_t st) {
+    size_t smem = 2 * (size_t)g.ny * g.ny * sizeof(double);
+    k_helm<<<dim3(g.npairs, 2), 256, smem, st>>>(g, s);
+}
+
+// --------------------------------------------------------------------- mean
+
+__global__ void k_mean(GroupView g, int s) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    __shared__ double red[32];
+    const int Ny = g.ny, My = g.my, e = blockIdx.x;
+    double* fu = (double*)sm;     // [Ny] combined forcing
+    double* fw = fu + Ny;
+    double* ui = fw + Ny;         // new interior U
+    double* wi = ui + Ny;
+    const int hi = (s == 0) ? 0 : 1;
+    const double* MU = g.mops[hi];
+    const double* PU = MU + (size_t)Ny * Ny;
+    const double* bU = PU + (size_t)Ny * Ny;
+    const double* Ug = bU + 2 * (size_t)Ny;
+    const double* uv = g.uv + (size_t)e * My;
+    const double* wv = g.wv + (size_t)e * My;
+    for (int i = threadIdx.x; i < Ny; i += blockDim.x) {
+        double a = 0.0, b = 0.0;
+        for (int j = 0; j < My; ++j) {
+            double d = g.D1[(size_t)(i + 1) * My + j];
+            a += d * uv[j];
+            b += d * wv[j];
+        }
+        size_t o = (size_t)e * Ny + i;
+        double ft, gt;
+        if (s == 0) {
+            ft = a; gt = b; g.AU[o] = a; g.AW[o] = b;
+        } else if (s == 1) {
+            double pa = g.AU[o], pb = g.AW[o];
+            ft = 2.0 * a - pa; gt = 2.0 * b - pb;
+            g.AU[o] = (1.0 / 6.0) * pa + (4.0 / 6.0) * a;
+            g.AW[o] = (1.0 / 6.0) * pb + (4.0 / 6.0) * b;
+        } else {
+            ft = g.AU[o] + (1.0 / 6.0) * a;
+            gt = g.AW[o] + (1.0 / 6.0) * b;
+        }
+        fu[i] = ft;
+        fw[i] = gt;
+    }
+    __syncthreads();
+    const double* Ut = g.U_t + (size_t)e * My;
+    const double* Wt = g.W_t + (size_t)e * My;
+    double fl = 0.0, fg = 0.0;
+    for (int i = threadIdx.x; i < Ny; i += blockDim.x) {
+        double a = 0.0, b = 0.0, c = 0.0, d = 0.0;
+        for (int j = 0; j < Ny; ++j) {
+            a += MU[(size_t)i * Ny + j] * Ut[j + 1];
+            c += MU[(size_t)i * Ny + j] * Wt[j + 1];
+        }
+        double bu = bU[2 * i] * Ut[0] + bU[2 * i + 1] * Ut[My - 1];
+        double bw = bU[2 * i] * Wt[0] + bU[2 * i + 1] * Wt[My - 1];
+        for (int j = 0; j < Ny; ++j) {
+            b += PU[(size_t)i * Ny + j] * fu[j];
+            d += PU[(size_t)i * Ny + j] * fw[j];
+        }
+        ui[i] = a + bu + b;
+        wi[i] = c + bw + d;
+        fl += g.ccw[i + 1] * ui[i];
+        fg += g.ccw[i + 1] * Ug[i];
+    }
+    double gam = 0.0;
+    if (g.flow == 1) {
+        double f0 = block_sum(fl, red) + g.ccw[0] * Ut[0] + g.ccw[My - 1] * Ut[My - 1];
+        double f1 = block_sum(fg, red);
+        gam = (g.bulk_flux - f0) / f1;
+    } else {
+        __syncthreads();
+    }
+    double* Uo = (s == 2) ? (g.U_t + (size_t)e * My) : (g.U_s + (size_t)e * My);
+    double* Wo = (s == 2) ? (g.W_t + (size_t)e * My) : (g.W_s + (size_t)e * My);
+    double u0 = Ut[0], uN = Ut[My - 1], w0 = Wt[0], wN = Wt[My - 1];
+    __syncthreads();   // every read of U_t / W_t is done before an in-place write
+    for (int i = threadIdx.x; i < Ny; i += blockDim.x) {
+        Uo[i + 1] = ui[i] + gam * Ug[i];
+        Wo[i + 1] = wi[i];
+    }
+    if (threadIdx.x == 0) {
+        Uo[0] = u0; Uo[My - 1] = uN; Wo[0] = w0; Wo[My - 1] = wN;
+        g.gamma[e] = gam;
+    }
+}
+
+void launch_mean(const GroupView& g, int s, cudaStream_t st) {
+    size_t smem = 4 * (size_t)g.ny * sizeof(double);
+    k_mean<<<g.E, 128, smem, st>>>(g, s);
+}
+
+// -------------------------------------------------------------------- stats
+
+__global__ void __launch_bounds__(256) k_stats_plane(GroupView g) {
+    __shared__ double red[32];
+    const int y = blockIdx.x, e = blockIdx.y;
+    const int Ny = g.ny, E = g.E, nmodes = g.nmodes, NKX = g.nkx;
+    const size_t fs = (size_t)Ny * E * nmodes;
+    const double2* P = g.P5d + ((size_t)y * E + e) * nmodes;
+    double uu = 0, vv = 0, ww = 0, uv = 0, dmax = 0, nf = 0;
+    const int q_mean = g.kz * NKX;
+    for (int q = threadIdx.x; q < nmodes; q += blockDim.x) {
+        double2 v = P[q], dv = P[fs + q], et = P[3 * fs + q];
+        if (!isfinite(v.x) || !isfinite(v.y) || !isfinite(et.x) || !isfinite(et.y)) nf = 1.0;
+        if (q == q_mean) continue;
+        int mi = q / NKX, n = q - mi * NKX;
+        double kx = g.kxt[n], kz = g.kzt[mi], ki = g.k2inv[q];
+        // u = i (kx Dv - kz eta) / k^2, w = i (kz Dv + kx eta) / k^2
+        double ax = (kx * dv.x - kz * et.x) * ki, ay = (kx * dv.y - kz * et.y) * ki;
+        double bx = (kz * dv.x + kx * et.x) * ki, by = (kz * dv.y + kx * et.y) * ki;
+        double2 u = make_double2(-ay, ax), w = make_double2(-by, bx);
+        double c = (n == 0) ? 1.0 : 2.0;
+        uu += c * (u.x * u.x + u.y * u.y);
+        vv += c * (v.x * v.x + v.y * v.y);
+        ww += c * (w.x * w.x + w.y * w.y);
+        uv += c * (u.x * v.x + u.y * v.y);
+        // i kx u + Dv + i kz w
+        double rx = -kx * u.y + dv.x - kz * w.y;
+        double ry = kx * u.x + dv.y + kz * w.x;
+        dmax = fmax(dmax, sqrt(rx * rx + ry * ry));
+    }
+    uu = block_sum(uu, red); vv = block_sum(vv, red); ww = block_sum(ww, red);
+    uv = block_sum(uv, red); dmax = block_max(dmax, red); nf = block_max(nf, red);
+    if (threadIdx.x == 0) {
+        double* o = g.st_y + ((size_t)e * Ny + y) * 6;
+        o[0] = uu; o[1] = vv; o[2] = ww; o[3] = uv; o[4] = dmax; o[5] = nf;
+    }
+}
+
+__global__ void k_stats_final(GroupView g) {
+    __shared__ double red[32];
+    const int e = blockIdx.x, Ny = g.ny, My = g.my;
+    const double* U = g.U_t + (size_t)e * My;
+    const double* W = g.W_t + (size_t)e * My;
+    double* prof = g.prof + (size_t)e * 6 * My;
+    double ep = 0, em = 0, fl = 0, dm = 0, nf = 0;
+    for (int j = threadIdx.x; j < My; j += blockDim.x) {
+        double uu = 0, vv = 0, ww = 0, uv = 0;
+        if (j > 0 && j < My - 1) {
+            const double* s = g.st_y + ((size_t)e * Ny + (j - 1)) * 6;
+            uu = s[0]; vv = s[1]; ww = s[2]; uv = s[3];
+            dm = fmax(dm, s[4]);
+            nf = fmax(nf, s[5]);
+        }
+        if (!isfinite(U[j]) || !isfinite(W[j])) nf = 1.0;
+        prof[0 * My + j] = U[j];
+        prof[1 * My + j] = W[j];
+        prof[2 * My + j] = uu;
+        prof[3 * My + j] = vv;
+        prof[4 * My + j] = ww;
+        prof[5 * My + j] = uv;
+        double w = g.ccw[j];
+        ep += w * (uu + vv + ww);
+        em += w * (U[j] * U[j] + W[j] * W[j]);
+        fl += w * U[j];
+    }
+    ep = block_sum(ep, red); em = block_sum(em, red); fl = block_sum(fl, red);
+    dm = block_max(dm, red); nf = block_max(nf, red);
+    if (threadIdx.x == 0) {
+        double t0 = 0, t1 = 0;
+        for (int j = 0; j < My; ++j) {
+            t0 += g.D1[j] * U[j];
+            t1 += g.D1[(size_t)(My - 1) * My + j] * U[j];
+        }
+        double* o = g.st_out + (size_t)e * 8;
+        o[0] = 0.25 * (ep + em);
+        o[1] = 0.25 * ep;
+        o[2] = t0;
+        o[3] = t1;
+        o[4] = fl;
+        o[5] = g.gamma[e];
+        o[6] = dm;
+        o[7] = nf;
+    }
+}
+
+void launch_stats(const GroupView& g, cudaStream_t st) {
+    launch_yderiv<double>(g, g.v_t, g.e_t, g.P5d, st);
+    k_stats_plane<<<dim3(g.ny, g.E), 256, 0, st>>>(g);
+    k_stats_final<<<g.E, 128, 0, st>>>(g);
+}
+
+// --------------------------------------------------------------- pack/unpack
+
+// stage: v then eta, each [count][Ny][NKZ][NKX] complex (host layout)
+__global__ void k_pack(GroupView g, int member0, int count) {
+    const int Ny = g.ny, E = g.E, nmodes = g.nmodes, NKX = g.nkx, NKZ = g.nkz;
+    const size_t per = (size_t)count * Ny * nmodes;
+    const int q_mean = g.kz * NKX;
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < per; idx += (size_t)gridDim.x * blockDim.x) {
+        int q = (int)(idx % nmodes);
+        int y = (int)((idx / nmodes) % Ny);
+        int el = (int)(idx / ((size_t)nmodes * Ny));
+        int mi = q / NKX, n = q - mi * NKX;
+        double2 a = g.stage[idx], b = g.stage[per + idx];
+        if (n == 0) {
+            // Hermitian part of the n = 0 column: (x(m) + conj x(-m)) / 2
+            int qp = (NKZ - 1 - mi) * NKX;
+            size_t ip = ((size_t)el * Ny + y) * nmodes + qp;
+            double2 ap = g.stage[ip], bp = g.stage[per + ip];
+            a = make_double2(0.5 * (a.x + ap.x), 0.5 * (a.y - ap.y));
+            b = make_double2(0.5 * (b.x + bp.x), 0.5 * (b.y - bp.y));
+        }
+        if (q == q_mean) { a = make_double2(0.0, 0.0); b = a; }
+        size_t h = ((size_t)q * Ny + y) * E + member0 + el;
+        g.v_t[h] = a;
+        g.e_t[h] = b;
+    }
+}
+
+__global__ void k_unpack(GroupView g, int member0, int count) {
+    const int Ny = g.ny, E = g.E, nmodes = g.nmodes;
+    const size_t per = (size_t)count * Ny * nmodes;
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < per; idx += (size_t)gridDim.x * blockDim.x) {
+        int q = (int)(idx % nmodes);
+        int y = (int)((idx / nmodes) % Ny);
+        int el = (int)(idx / ((size_t)nmodes * Ny));
+        size_t h = ((size_t)q * Ny + y) * E + member0 + el;
+        g.stage[idx] = g.v_t[h];
+        g.stage[per + idx] = g.e_t[h];
+    }
+}
+
+void launch_pack(const GroupView& g, int member0, int count, cudaStream_t st) {
+    k_pack<<<1024, 256, 0, st>>>(g, member0, count);
+}
+void launch_unpack(const GroupView& g, int member0, int count, cudaStream_t st) {
+    k_unpack<<<1024, 256, 0, st>>>(g, member0, count);
+}
+
+void set_attributes_spectral() {
+    cudaFuncSetAttribute(k_yderiv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_yderiv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_forcing<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_forcing<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_helm, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+}
+
+}  // namespace dnsk

@@ -9,3 +9,10 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (sm_103a) and the built library")
     config.addinivalue_line("markers", "slow: long-running oracle case")
+
+
+def pytest_sessionstart(session):
+    # compile the library (and the oracle helper) once per session, so a fresh
+    # checkout or a fresh GPU machine can run the suite directly
+    import __graft_entry__
+    __graft_entry__.build()

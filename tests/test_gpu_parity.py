@@ -1,0 +1,162 @@
+"""GPU path vs the CPU oracle, through the C ABI (needs a GPU)."""
+import numpy as np
+import pytest
+
+import dns_synth
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_2306_12739_gb300 as dns  # noqa: E402
+
+FIELDS = ("v", "eta", "U", "W")
+
+
+def rel(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def group(flow, mx, my, mz, lx, lz, re, dt, members):
+    return dict(flow=flow, mx=mx, my=my, mz=mz, lx=lx, lz=lz, re=re, dt=dt, members=members)
+
+
+CFG1 = group("couette", 16, 33, 16, 1.75 * np.pi, 1.2 * np.pi, 400.0, 0.01, 1)
+CFG2 = group("poiseuille", 64, 65, 64, 2 * np.pi, np.pi, 1650.0, 0.005, 8)
+
+
+def _state(g, seed0, amp, **kw):
+    return dns_synth.make_state(g["mx"], g["my"], g["mz"], g["lx"], g["lz"], g["flow"], g["members"],
+                                seed0, amp, **kw)
+
+
+def _oracle(g):
+    return oracle.Channel(g["mx"], g["my"], g["mz"], g["lx"], g["lz"], g["re"], g["dt"], g["flow"])
+
+
+def _run(g, st, nsteps, precision="fp64", use_graph=False):
+    ens = dns.Ensemble([g], precision=precision, use_graph=use_graph)
+    ens.set_state(0, st["v"], st["eta"], st["U"], st["W"])
+    ens.step(nsteps)
+    out = ens.get_state(0)
+    ens.close()
+    return out
+
+
+def test_config1_fp64_matches_oracle_after_100_steps():
+    st = _state(CFG1, 1000, 1e-2, n_max=2, m_max=2)
+    ref = _oracle(CFG1).step(tuple(st[k] for k in FIELDS), 100)
+    got = _run(CFG1, st, 100)
+    for a, b, name in zip(got, ref, FIELDS):
+        assert rel(a, b) < 1e-11, (name, rel(a, b))
+
+
+@pytest.mark.parametrize("mx,my,mz,E", [(32, 49, 48, 3), (48, 21, 16, 5)])
+def test_ragged_grids_fp64_match_oracle(mx, my, mz, E):
+    g = group("couette", mx, my, mz, 1.75 * np.pi, 1.2 * np.pi, 500.0, 0.01, E)
+    st = _state(g, 3000, 5e-2)
+    ref = _oracle(g).step(tuple(st[k] for k in FIELDS), 5)
+    got = _run(g, st, 5)
+    for a, b, name in zip(got, ref, FIELDS):
+        assert rel(a, b) < 1e-12, (name, rel(a, b))
+
+
+def test_config2_fp64_matches_oracle_few_steps():
+    """Full size of the 64x65x64 Poiseuille ensemble (8 members), 3 steps."""
+    st = _state(CFG2, 2000, 5e-2, n_max=4, m_max=4)
+    ref = _oracle(CFG2).step(tuple(st[k] for k in FIELDS), 3)
+    got = _run(CFG2, st, 3)
+    for a, b, name in zip(got, ref, FIELDS):
+        assert rel(a, b) < 1e-12, (name, rel(a, b))
+
+
+def test_mixed_matches_fp64_over_50_steps():
+    g = group("couette", 32, 49, 32, 1.75 * np.pi, 1.2 * np.pi, 500.0, 0.01, 8)
+    st = _state(g, 3000, 5e-2, n_max=4, m_max=4)
+    a = _run(g, st, 50, "fp64")
+    b = _run(g, st, 50, "mixed")
+    for x, y, name in zip(b, a, FIELDS):
+        for e in range(g["members"]):
+            assert rel(x[e], y[e]) < 1e-6, (name, e, rel(x[e], y[e]))
+
+
+def test_graph_replay_is_bitwise_equal_to_eager():
+    g = group("poiseuille", 32, 33, 32, 2 * np.pi, np.pi, 1650.0, 0.005, 4)
+    st = _state(g, 77, 5e-2)
+    for prec in ("fp64", "mixed"):
+        a = _run(g, st, 4, prec, use_graph=False)
+        b = _run(g, st, 4, prec, use_graph=True)
+        for x, y in zip(a, b):
+            assert np.array_equal(x, y)
+
+
+def test_member_alone_equals_member_in_batch():
+    g = group("couette", 32, 33, 32, 1.75 * np.pi, 1.2 * np.pi, 400.0, 0.01, 6)
+    st = _state(g, 500, 5e-2)
+    full = _run(g, st, 3)
+    g1 = dict(g, members=1)
+    one = {k: st[k][4:5] for k in FIELDS}
+    alone = _run(g1, one, 3)
+    for a, b in zip(full, alone):
+        assert np.array_equal(a[4:5], b)
+
+
+def test_resume_is_bitwise():
+    g = group("poiseuille", 16, 33, 16, 2 * np.pi, np.pi, 1650.0, 0.005, 2)
+    st = _state(g, 9, 5e-2)
+    direct = _run(g, st, 6)
+    mid = _run(g, st, 3)
+    st2 = dict(zip(FIELDS, mid))
+    resumed = _run(g, st2, 3)
+    for a, b in zip(direct, resumed):
+        assert np.array_equal(a, b)
+
+
+def test_stats_match_oracle():
+    g = group("poiseuille", 32, 33, 32, 2 * np.pi, np.pi, 1650.0, 0.005, 3)
+    st = _state(g, 41, 5e-2)
+    ch = _oracle(g)
+    ref_state = ch.step(tuple(st[k] for k in FIELDS), 2)
+    ref = ch.stats(ref_state)
+    ens = dns.Ensemble([g], precision="fp64")
+    ens.set_state(0, st["v"], st["eta"], st["U"], st["W"])
+    ens.step(2)
+    s = ens.stats(0)
+    ens.close()
+    for k in ("e_total", "e_pert", "tau_bottom", "tau_top", "bulk_flux"):
+        assert np.abs(s[k] - ref[k]).max() <= 1e-12 * max(1.0, np.abs(ref[k]).max()), k
+    assert np.abs(s["gamma"] - ch.last_gamma).max() < 1e-14
+    assert np.all(s["max_div"] < 1e-13)
+    for k in ("uu", "vv", "ww", "uv"):
+        assert rel(s[k], ref[k]) < 1e-12, k
+    assert np.all(s["nonfinite"] == 0)
+
+
+def test_nonfinite_member_is_flagged_without_touching_others():
+    g = group("couette", 16, 33, 16, 1.75 * np.pi, 1.2 * np.pi, 400.0, 0.01, 3)
+    st = _state(g, 5, 1e-2)
+    st["v"][1, 3, 2, 1] = np.nan
+    ens = dns.Ensemble([g], precision="fp64")
+    ens.set_state(0, st["v"], st["eta"], st["U"], st["W"])
+    ens.step(2)
+    s = ens.stats(0)
+    got = ens.get_state(0)
+    ens.close()
+    assert s["rc"] == dns.DNS_ERR_NONFINITE
+    assert list(s["nonfinite"]) == [0, 1, 0]
+    clean = {k: st[k][[0, 2]] for k in FIELDS}
+    ref = _oracle(dict(g, members=2)).step(tuple(clean[k] for k in FIELDS), 2)
+    for a, b in zip(got, ref):
+        assert rel(a[[0, 2]], b) < 1e-12
+
+
+def test_laminar_states_stay_steady_on_gpu():
+    for flow in ("couette", "poiseuille"):
+        g = group(flow, 32, 33, 32, 2 * np.pi, np.pi, 1650.0, 0.005, 2)
+        st = _state(g, 0, 0.0)
+        got = _run(g, st, 20)
+        assert np.abs(got[2] - st["U"]).max() < 1e-13
+        assert np.abs(got[0]).max() == 0.0
