@@ -1,0 +1,386 @@
+#!/usr/bin/env python3
+"""Throughput of the ensemble channel-DNS step on one node.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp64]
+                  [--impl gpu|reference] [--no-cpu-baseline]
+
+One step = one full CN/RK3 step (three sub-steps: y-derivatives, transforms and
+advective products, forcing + RK combination, per-wavenumber implicit apply,
+mean flow) for every member of the ensemble.  Workload: plane Poiseuille flow
+at constant bulk flux, Re = 1650 (Re_tau ~ 100), box 2pi x 2 x pi, grid
+64 x 65 x 64, 8 members, dt = 0.005, seeded 5% noise in |n|, |m| <= 4.
+
+Prints one JSON line (rank 0).  With torchrun (N > 1) every rank advances its
+own independent ensemble (weak scaling, replicas: the step has no exchange
+between members); only a barrier and a max of the per-rank times cross ranks.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ensemble member-steps/s (and grid-pts*steps/s) mixed vs FP64 on 1 GB300 at stated err"
+UNIT = "member-steps/s"
+
+WORKLOAD = dict(flow="poiseuille", mx=64, my=65, mz=64, lx=2 * np.pi, lz=np.pi, re=1650.0, dt=0.005,
+                members=8)
+WORKLOAD_NAME = "Poiseuille constant-flux Re=1650 (Re_tau~100), 2pi x 2 x pi, 64x65x64, 8 members, dt=0.005"
+NOISE = dict(seed0=2000, amp=5e-2, n_max=4, m_max=4)
+
+FP32_PEAK_PER_SM_CLK = 128 * 2          # FP32 lanes x 2 flops (FMA) per SM per clock
+FP64_NOMINAL_TFLOPS = 1.25              # GB300 FP64 (nominal)
+N_SM = 152
+
+
+def initial_state(g, rank=0):
+    import dns_synth
+    return dns_synth.make_state(g["mx"], g["my"], g["mz"], g["lx"], g["lz"], g["flow"], g["members"],
+                                NOISE["seed0"] + 1000 * rank, NOISE["amp"], n_max=NOISE["n_max"],
+                                m_max=NOISE["m_max"])
+
+
+# ----------------------------------------------------------- distributed
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws <= 1:
+        return 0, 1, None
+    import torch
+    import torch.distributed as dist
+    rank = int(os.environ["RANK"])
+    local = int(os.environ.get("LOCAL_RANK", rank))
+    backend = "nccl" if torch.cuda.is_available() else "gloo"
+    if backend == "nccl":
+        torch.cuda.set_device(local)
+    dist.init_process_group(backend)
+    return rank, ws, dist
+
+
+def reduce_max(value, dist, device=None):
+    """Max of a float over ranks (host plumbing only)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate(member_steps_per_rank, seconds_per_rank, world):
+    """Whole-job throughput: all ranks' member-steps over the slowest rank's time."""
+    return member_steps_per_rank * world / seconds_per_rank
+
+
+# ----------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.th.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1])); smax.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, p[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# -------------------------------------------------------------- roofline
+
+def kernel_work(cls, g, precision):
+    """Algorithmic work of ONE launch of kernel class `cls` for group g:
+    (bound, amount, unit).  Counts per unit are in the design notes."""
+    ny, E = g["my"] - 2, g["members"]
+    nkx, nkz = (g["mx"] - 1) // 3 + 1, 2 * ((g["mz"] - 1) // 3) + 1
+    nmodes = nkx * nkz
+    S = nmodes * ny * E                      # complex values of one spectral field
+    MM = g["mx"] * g["mz"]
+    if cls == "plane":
+        per_plane = 15 * 2.5 * MM * np.log2(MM) + 9 * 2 * MM + 2 * 2 * MM
+        return "alu", E * ny * per_plane, "flop"
+    if cls == "yderiv":
+        return "alu", S * 3 * 2 * 2 * ny, "flop"
+    if cls == "forcing":
+        return "alu", S * 2 * 2 * ny, "flop"
+    if cls == "helm":
+        npairs = nkx * (nkz // 2 + 1)
+        return "alu", 2 * npairs * 2 * 2 * ny * ny * 4 * E, "flop"
+    return "alu", E * 4.0 * (g["my"]) ** 2, "flop"
+
+
+def alu_peak(precision_of_kernel, sm_mhz):
+    if precision_of_kernel == "f64":
+        return FP64_NOMINAL_TFLOPS
+    return N_SM * FP32_PEAK_PER_SM_CLK * sm_mhz * 1e6 / 1e12
+
+
+def kernel_precision(cls, precision):
+    if precision == "fp64":
+        return "f64"
+    return {"plane": "f32"}.get(cls, "f64")
+
+
+# ------------------------------------------------------------ cpu oracle
+
+CPU_SNIPPET = r"""
+import json, os, sys, time
+sys.path.insert(0, {root!r})
+import numpy as np
+import oracle, dns_synth
+g = {g!r}
+E = {members}
+ch = oracle.Channel(g['mx'], g['my'], g['mz'], g['lx'], g['lz'], g['re'], g['dt'], g['flow'])
+st = dns_synth.make_state(g['mx'], g['my'], g['mz'], g['lx'], g['lz'], g['flow'], E, {seed0}, {amp},
+                          n_max={n_max}, m_max={m_max})
+x = tuple(st[k] for k in ('v', 'eta', 'U', 'W'))
+for _ in range({warm}):
+    x = ch.step(x, 1)
+t = time.perf_counter()
+for _ in range({steps}):
+    x = ch.step(x, 1)
+dt = time.perf_counter() - t
+print(json.dumps(dict(seconds=dt, steps={steps}, members=E)))
+"""
+
+
+def run_oracle(g, members, steps, warm=0):
+    env = dict(os.environ)
+    for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS_STEP", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
+        env[k] = "1"
+    code = CPU_SNIPPET.format(root=ROOT, g=g, members=members, seed0=NOISE["seed0"], amp=NOISE["amp"],
+                              n_max=NOISE["n_max"], m_max=NOISE["m_max"], steps=steps, warm=warm)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
+    if r.returncode != 0:
+        raise RuntimeError("oracle run failed: " + r.stderr[-2000:])
+    out = json.loads(r.stdout.strip().splitlines()[-1])
+    return out
+
+
+def cpu_info():
+    model = "unknown"
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.lower().startswith(("model name", "cpu model")):
+                    model = ln.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return model, os.cpu_count()
+
+
+# ----------------------------------------------------------------- arms
+
+def reference_arm(args, rank, world):
+    if rank != 0:
+        return
+    g = WORKLOAD
+    out = run_oracle(g, g["members"], args.steps, warm=args.warmup)
+    value = out["members"] * out["steps"] / out["seconds"]
+    model, ncpu = cpu_info()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * out["seconds"] / out["steps"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded, dns_synth)",
+        "config": {"workload": WORKLOAD_NAME, "precision": "fp64", "l2": "n/a (CPU)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "%d steps x %d members of the workload (after %d warm-up steps), cpu %s, %d cores on host"
+                                   % (out["steps"], out["members"], args.warmup, model, ncpu)},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def gpu_arm(args, rank, world, dist):
+    import torch
+    import paper_2306_12739_gb300 as dns
+    dev = torch.device("cuda", torch.cuda.current_device())
+    g = dict(WORKLOAD)
+    st = initial_state(g, rank)
+    precision = args.precision
+
+    def timed_run(prec, nsteps, nwarm, flush):
+        ens = dns.Ensemble([g], precision=prec, use_graph=True, device=dev)
+        ens.set_state(0, st["v"], st["eta"], st["U"], st["W"])
+        stream = ens.stream
+        ens.step(nwarm)
+        torch.cuda.synchronize()
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(nsteps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(nsteps)]
+        launches = 0
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        sampler = ClockSampler(dev.index or 0)
+        sampler.start()
+        with torch.cuda.stream(stream):
+            for k in range(nsteps):
+                flush.zero_()                  # evict L2 between timed steps
+                starts[k].record(stream)
+                ens.step(1)
+                launches += ens.launches()
+                ends[k].record(stream)
+        torch.cuda.synchronize()
+        clocks = sampler.stop()
+        if dist is not None:
+            dist.barrier()
+        total_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+        return ens, total_ms, launches, clocks
+
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    ens, total_ms, launches, clocks = timed_run(precision, args.steps, args.warmup, flush)
+    total_ms = reduce_max(total_ms, dist, dev)
+    ms_step = total_ms / args.steps
+    value = aggregate(g["members"] * args.steps, total_ms / 1e3, world)
+    pts = g["mx"] * g["my"] * g["mz"]
+
+    # per-kernel device times (events around every launch), for the roofline
+    ens.set_state(0, st["v"], st["eta"], st["U"], st["W"])
+    kt = ens.step_timed(max(1, min(args.steps, 5)))
+    tot = sum(v[0] for v in kt.values())
+    shares = {k: (v[0] / tot if tot > 0 else 0.0) for k, v in kt.items()}
+    dom = max(kt, key=lambda k: kt[k][0])
+    avg_ms = kt[dom][0] / max(1, kt[dom][1])
+    bound, work, wunit = kernel_work(dom, g, precision)
+    kprec = kernel_precision(dom, precision)
+    sm_mhz = clocks["sm_mhz"] or 2070.0
+    peak = alu_peak(kprec, sm_mhz)
+    achieved = work / (avg_ms / 1e3) / 1e12
+    roofline = {"kernel": dom, "bound": bound, "precision": kprec, "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "peak_source": ("nominal GB300 FP64" if kprec == "f64" else
+                                "152 SM x 128 FP32 lanes x 2 x median sampled SM clock %.0f MHz" % sm_mhz),
+                "kernel_ms_per_launch": avg_ms,
+                "shares": {k: round(v, 4) for k, v in shares.items()}}
+
+    # end to end through the C ABI with host buffers: upload state, step, download state
+    v = np.ascontiguousarray(st["v"]); e = np.ascontiguousarray(st["eta"])
+    U = np.ascontiguousarray(st["U"]); W = np.ascontiguousarray(st["W"])
+    pin = [torch.from_numpy(a.view(np.float64)).pin_memory() for a in (v, e, U, W)]
+    h2d = sum(p.numel() * 8 for p in pin)
+    outs = [torch.empty_like(p).pin_memory() for p in pin]
+    d2h = sum(o.numel() * 8 for o in outs)
+    nkx, nkz, ny, my = ens.shapes[0]
+    E = g["members"]
+    e2e_steps = max(1, min(args.steps, 10))
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        dns.dns_set_state(ens.h, 0, 0, E, *[p.data_ptr() for p in pin], 0)
+        dns.dns_step(ens.h, 1)
+        dns.dns_get_state(ens.h, 0, 0, E, *[o.data_ptr() for o in outs], 0)
+    e2e_s = time.perf_counter() - t0
+    e2e_s = reduce_max(e2e_s, dist, dev)
+    e2e_value = aggregate(E * e2e_steps, e2e_s, world)
+    ens.close()
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64" if precision == "mixed" else "f64",
+        "data": "synthetic (seeded, dns_synth)",
+        "config": {"workload": WORKLOAD_NAME, "precision": precision, "graph": True,
+                   "l2": "flushed (256 MiB write) before every timed step", "parallelism": "replicas x%d" % world},
+        "grid_pts_steps_per_s": value * pts,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "steps": e2e_steps},
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "roofline": roofline,
+    }
+
+    if precision == "mixed" and not args.no_fp64:
+        n64 = max(1, min(args.steps, 5))
+        ens64, t64, _, _ = timed_run("fp64", n64, min(args.warmup, 3), flush)
+        ens64.close()
+        t64 = reduce_max(t64, dist, dev)
+        v64 = aggregate(g["members"] * n64, t64 / 1e3, world)
+        line["fp64"] = {"value": v64, "unit": UNIT, "ms_per_step": t64 / n64, "steps": n64}
+        line["mixed_over_fp64"] = value / v64
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out = run_oracle(g, 4, 2)
+        model, ncpu = cpu_info()
+        line["cpu_baseline"] = {"value": out["members"] * out["steps"] / out["seconds"], "unit": UNIT, "cores": 1,
+                                "kind": "oracle",
+                                "sample": "%d steps x %d members of the workload, single-threaded numpy, cpu %s (%d cores on host)"
+                                          % (out["steps"], out["members"], model, ncpu)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
+    ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparator run")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    rank, world, dist = dist_setup()
+    if args.impl == "reference":
+        reference_arm(args, rank, world)
+    else:
+        import __graft_entry__
+        __graft_entry__.build()
+        gpu_arm(args, rank, world, dist)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -164,6 +164,23 @@ const char* dns_last_error(const dns_handle* h);
 /* Number of kernel launches enqueued by the last dns_step call (all steps). */
 int dns_last_launch_count(const dns_handle* h);
 
+/* Kernel classes reported by dns_step_timed, in launch order within a sub-step. */
+enum {
+    DNS_K_MEAN_DERIV = 0,  /* dU00/dy, dW00/dy of the sub-step state */
+    DNS_K_YDERIV = 1,      /* Dv, D2v, D eta (shared Chebyshev operators) */
+    DNS_K_PLANE = 2,       /* transforms + advective products + plane means */
+    DNS_K_FORCING = 3,     /* F, G and the RK3 combination */
+    DNS_K_HELM = 4,        /* per-wavenumber implicit apply */
+    DNS_K_MEAN = 5,        /* mean flow + constant-flux gamma */
+    DNS_K_NCLASS = 6
+};
+
+/* Like dns_step (never through a graph), with a CUDA event pair recorded on
+ * the handle's stream around every kernel launch; synchronises, then returns
+ * the summed device time in ms (ms[DNS_K_NCLASS]) and the number of launches
+ * (launches[DNS_K_NCLASS]) of each kernel class over the nsteps steps. */
+int dns_step_timed(dns_handle* h, int nsteps, double* ms, int* launches);
+
 /* Host copies of what dns_create built, for inspection and tests; no device
  * access, valid before a workspace is bound.
  * dns_export_grid: y [My], D1 [My*My], D2 [My*My], D4c [(My-2)^2] and the

@@ -11,6 +11,20 @@ SRC = os.path.join(HERE, "ops_quad.c")
 LIB = os.path.join(HERE, "liboracle_ops.so")
 
 
+def _locked(fn):
+    """Serialise concurrent builds (several ranks on one node) with a file lock."""
+    def wrap(*a, **k):
+        import fcntl
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), ".build.lock"), "w") as lk:
+            fcntl.flock(lk, fcntl.LOCK_EX)
+            try:
+                return fn(*a, **k)
+            finally:
+                fcntl.flock(lk, fcntl.LOCK_UN)
+    return wrap
+
+
+@_locked
 def build(force: bool = False) -> str:
     if (not force and os.path.exists(LIB)
             and os.path.getmtime(LIB) >= os.path.getmtime(SRC)):

@@ -304,8 +304,16 @@ class Channel:
         def corr(a, b):
             return np.sum(np.real(a * np.conj(b)) * cn * pert, axis=(-2, -1))
 
-        uu = corr(f["u"], f["u"]); vv = corr(f["v"], f["v"]); ww = corr(f["w"], f["w"])
-        uv = corr(f["u"], f["v"])
+        def corr_int(a, b):
+            # perturbation correlations on the interior nodes; the no-slip walls
+            # carry none (the discrete Dv there is not part of the solution)
+            c = corr(a, b)
+            c[:, 0] = 0.0
+            c[:, -1] = 0.0
+            return c
+
+        uu = corr_int(f["u"], f["u"]); vv = corr_int(f["v"], f["v"]); ww = corr_int(f["w"], f["w"])
+        uv = corr_int(f["u"], f["v"])
         e_pert = 0.25 * ((uu + vv + ww) @ self.w)
         e_mean = 0.25 * ((U ** 2 + W ** 2) @ self.w)
         dU = U @ self.D1.T

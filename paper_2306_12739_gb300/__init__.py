@@ -33,7 +33,9 @@ DNS_PREC_FP64, DNS_PREC_MIXED = 0, 1
 
 EXPORTED = ["dns_create", "dns_workspace_size", "dns_bind_workspace", "dns_state_shape",
             "dns_set_state", "dns_get_state", "dns_step", "dns_stats", "dns_destroy",
-            "dns_last_error", "dns_last_launch_count", "dns_export_grid", "dns_export_operators"]
+            "dns_last_error", "dns_last_launch_count", "dns_export_grid", "dns_export_operators",
+            "dns_step_timed"]
+KERNEL_CLASSES = ["mean_deriv", "yderiv", "plane", "forcing", "helm", "mean"]
 
 
 class dns_group_desc(ctypes.Structure):
@@ -71,6 +73,7 @@ _lib.dns_destroy.argtypes = [_H]
 _lib.dns_last_error.argtypes = [_H]
 _lib.dns_last_error.restype = ctypes.c_char_p
 _lib.dns_last_launch_count.argtypes = [_H]
+_lib.dns_step_timed.argtypes = [_H, ctypes.c_int, _dp, ctypes.POINTER(ctypes.c_int)]
 _lib.dns_export_grid.argtypes = [_H, ctypes.c_int, _dp, _dp, _dp, _dp, _dp]
 _lib.dns_export_operators.argtypes = [_H, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp]
 
@@ -127,6 +130,14 @@ def dns_get_state(h, group, member0, count, v, eta, U, W, ptr_kind):
 
 def dns_step(h, nsteps):
     return _ck(h, _lib.dns_step(h, nsteps))
+
+
+def dns_step_timed(h, nsteps):
+    """Returns {kernel class: (total ms, launches)} over nsteps eager steps."""
+    ms = (ctypes.c_double * len(KERNEL_CLASSES))()
+    n = (ctypes.c_int * len(KERNEL_CLASSES))()
+    _ck(h, _lib.dns_step_timed(h, nsteps, ms, n))
+    return {k: (ms[i], n[i]) for i, k in enumerate(KERNEL_CLASSES)}
 
 
 def dns_stats(h, group, members, profiles_ptr=None):
@@ -241,6 +252,9 @@ class Ensemble:
 
     def step(self, nsteps=1):
         dns_step(self.h, nsteps)
+
+    def step_timed(self, nsteps=1):
+        return dns_step_timed(self.h, nsteps)
 
     def launches(self):
         return dns_last_launch_count(self.h)

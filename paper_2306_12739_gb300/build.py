@@ -44,6 +44,20 @@ def _compile(src, extra=()):
     return obj, r.stderr
 
 
+def _locked(fn):
+    """Serialise concurrent builds (several ranks on one node) with a file lock."""
+    def wrap(*a, **k):
+        import fcntl
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), ".build.lock"), "w") as lk:
+            fcntl.flock(lk, fcntl.LOCK_EX)
+            try:
+                return fn(*a, **k)
+            finally:
+                fcntl.flock(lk, fcntl.LOCK_UN)
+    return wrap
+
+
+@_locked
 def build(force=False, verbose=False, extra_nvcc=()):
     if (not force and os.path.exists(LIB)
             and os.path.getmtime(LIB) >= max(os.path.getmtime(p) for p in _deps())):

@@ -130,8 +130,22 @@ int check(dns_handle* h, cudaError_t e, const char* what) {
     return DNS_OK;
 }
 
-void enqueue_step(dns_handle* h) {
+// Optional per-launch event recording (dns_step_timed).
+struct Timer {
+    std::vector<cudaEvent_t> ev;
+    std::vector<int> cls;
+};
+
+void enqueue_step(dns_handle* h, Timer* tm = nullptr) {
     cudaStream_t st = h->stream;
+    auto mark = [&](int c) {
+        if (!tm) return;
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        cudaEventRecord(e, st);
+        tm->ev.push_back(e);
+        tm->cls.push_back(c);
+    };
     for (auto& G : h->groups) {
         const GroupView& g = G.v;
         for (int s = 0; s < 3; ++s) {
@@ -139,18 +153,27 @@ void enqueue_step(dns_handle* h) {
             const double2* ce = s == 0 ? g.e_t : g.e_s;
             const double* cU = s == 0 ? g.U_t : g.U_s;
             const double* cW = s == 0 ? g.W_t : g.W_s;
+            mark(-1);
             dnsk::launch_mean_deriv(g, cU, cW, st);
+            mark(DNS_K_MEAN_DERIV);
             if (precision_mixed(h)) {
                 dnsk::launch_yderiv<float>(g, cv, ce, g.P5, st);
+                mark(DNS_K_YDERIV);
                 dnsk::launch_plane_state<float>(g, cU, cW, st);
+                mark(DNS_K_PLANE);
                 dnsk::launch_forcing<float>(g, s, st);
             } else {
                 dnsk::launch_yderiv<double>(g, cv, ce, g.P5, st);
+                mark(DNS_K_YDERIV);
                 dnsk::launch_plane_state<double>(g, cU, cW, st);
+                mark(DNS_K_PLANE);
                 dnsk::launch_forcing<double>(g, s, st);
             }
+            mark(DNS_K_FORCING);
             dnsk::launch_helm(g, s, st);
+            mark(DNS_K_HELM);
             dnsk::launch_mean(g, s, st);
+            mark(DNS_K_MEAN);
             h->launches += 6;
         }
     }
@@ -417,6 +440,30 @@ int dns_step(dns_handle* h, int nsteps) {
         for (int i = 0; i < nsteps; ++i) enqueue_step(h);
     }
     return check(h, cudaGetLastError(), "step launch");
+}
+
+int dns_step_timed(dns_handle* h, int nsteps, double* ms, int* launches) {
+    if (!h || !ms || !launches) return DNS_ERR_INVALID;
+    if (!h->bound) return fail(h, DNS_ERR_INVALID, "workspace not bound");
+    if (nsteps < 0) return fail(h, DNS_ERR_INVALID, "nsteps < 0");
+    for (int c = 0; c < DNS_K_NCLASS; ++c) { ms[c] = 0.0; launches[c] = 0; }
+    h->launches = 0;
+    int rc = DNS_OK;
+    for (int i = 0; i < nsteps && rc == DNS_OK; ++i) {
+        Timer tm;
+        enqueue_step(h, &tm);
+        rc = check(h, cudaStreamSynchronize(h->stream), "timed step");
+        for (size_t k = 1; k < tm.ev.size() && rc == DNS_OK; ++k) {
+            if (tm.cls[k] < 0) continue;
+            float t = 0.f;
+            rc = check(h, cudaEventElapsedTime(&t, tm.ev[k - 1], tm.ev[k]), "event time");
+            ms[tm.cls[k]] += t;
+            launches[tm.cls[k]] += 1;
+        }
+        for (auto e : tm.ev) cudaEventDestroy(e);
+    }
+    if (rc) return rc;
+    return check(h, cudaGetLastError(), "timed step launch");
 }
 
 int dns_stats(dns_handle* h, int group, dns_stats_t* per_member, dns_stats_t* ensemble_mean, double* profiles) {
