@@ -23,7 +23,7 @@ struct HostGroup {
     dnsb::GridOps grid;
     dnsb::CnOps ops[2];
     std::vector<double> kxt, kzt, k2t, k2inv, twx, twz, opsdev[2], mopsdev[2], D1i, D2i;
-    std::vector<float> kxtf, kztf, k2invf, twxf, twzf;
+    std::vector<float> kxtf, kztf, k2invf, twxf, twzf, opsf[2], D1if, D2if;
     // byte offsets inside the workspace
     struct Off { size_t off, bytes; };
     std::vector<std::pair<void**, Off>> slots;
@@ -89,6 +89,8 @@ size_t layout_group(dns_handle* h, HostGroup& G, size_t cur) {
     add((void**)&v.D1, sizeof(double) * v.my * v.my);
     add((void**)&v.D1i, sizeof(double) * nn);
     add((void**)&v.D2i, sizeof(double) * nn);
+    add((void**)&v.D1if, sizeof(float) * nn);
+    add((void**)&v.D2if, sizeof(float) * nn);
     add((void**)&v.ccw, sizeof(double) * v.my);
     add((void**)&v.kxt, sizeof(double) * v.nkx);
     add((void**)&v.kzt, sizeof(double) * v.nkz);
@@ -103,6 +105,7 @@ size_t layout_group(dns_handle* h, HostGroup& G, size_t cur) {
     add((void**)&v.k2invf, sizeof(float) * v.nmodes);
     for (int hi = 0; hi < 2; ++hi) {
         add((void**)&v.ops[hi], sizeof(double) * (size_t)v.npairs * 4 * nn);
+        if (precision_mixed(h)) add((void**)&v.opsf[hi], sizeof(float) * (size_t)v.npairs * 4 * nn);
         add((void**)&v.mops[hi], sizeof(double) * (2 * nn + 3 * (size_t)v.ny));
     }
     double2** st[] = {&v.v_t, &v.e_t, &v.v_s, &v.e_s, &v.mx1_v, &v.mx1_e, &v.Fv, &v.Fe, &v.Av, &v.Ae};
@@ -159,7 +162,7 @@ void enqueue_step(dns_handle* h, Timer* tm = nullptr) {
             if (precision_mixed(h)) {
                 dnsk::launch_yderiv<float>(g, cv, ce, g.P5, st);
                 mark(DNS_K_YDERIV);
-                dnsk::launch_plane_state<float>(g, cU, cW, st);
+                dnsk::launch_plane_f32(g, cU, cW, st);
                 mark(DNS_K_PLANE);
                 dnsk::launch_forcing<float>(g, s, st);
             } else {
@@ -170,7 +173,8 @@ void enqueue_step(dns_handle* h, Timer* tm = nullptr) {
                 dnsk::launch_forcing<double>(g, s, st);
             }
             mark(DNS_K_FORCING);
-            dnsk::launch_helm(g, s, st);
+            if (precision_mixed(h)) dnsk::launch_helm_mixed(g, s, st);
+            else dnsk::launch_helm(g, s, st);
             mark(DNS_K_HELM);
             dnsk::launch_mean(g, s, st);
             mark(DNS_K_MEAN);
@@ -229,8 +233,8 @@ int dns_create(const dns_config* cfg, void* cuda_stream, dns_handle** out) {
         v.re = d.re; v.dt = d.dt; v.u_wall = d.u_wall; v.bulk_flux = d.bulk_flux;
         if (!make_plan(d.mx, &v.px) || !make_plan(d.mz, &v.pz))
             return fail(h, DNS_ERR_UNSUPPORTED, "group %d: no radix plan", gi);
-        size_t smem = dnsk::plane_smem_bytes(v, precision_mixed(h) ? 4 : 8);
-        if (smem > 227 * 1024)
+        size_t smem = precision_mixed(h) ? dnsk::plane_f32_smem_bytes(d.mx, d.mz) : dnsk::plane_smem_bytes(v, 8);
+        if (smem == 0 || smem > 227 * 1024)
             return fail(h, DNS_ERR_UNSUPPORTED, "group %d: plane stage needs %zu B of shared memory", gi, smem);
         // operators
         G.grid = dnsb::build_grid(d.my);
@@ -266,6 +270,21 @@ int dns_create(const dns_config* cfg, void* cuda_stream, dns_handle** out) {
                 memcpy(&od[((size_t)p * 4 + 2) * nn], &G.ops[hi].Me[p * nn], nn * 8);
                 memcpy(&od[((size_t)p * 4 + 3) * nn], &G.ops[hi].Pe[p * nn], nn * 8);
             }
+            if (precision_mixed(h)) {
+                // single-precision copies for the increment form: M - I and P
+                auto& of = G.opsf[hi];
+                of.resize(od.size());
+                for (int p = 0; p < v.npairs; ++p)
+                    for (int k = 0; k < 4; ++k) {
+                        const double* src = &od[((size_t)p * 4 + k) * nn];
+                        float* dst = &of[((size_t)p * 4 + k) * nn];
+                        for (size_t i = 0; i < nn; ++i) {
+                            double val = src[i];
+                            if ((k == 0 || k == 2) && (i % (v.ny + 1) == 0)) val -= 1.0;
+                            dst[i] = (float)val;
+                        }
+                    }
+            }
             auto& md = G.mopsdev[hi];
             md.clear();
             md.insert(md.end(), G.ops[hi].MU.begin(), G.ops[hi].MU.end());
@@ -279,6 +298,8 @@ int dns_create(const dns_config* cfg, void* cuda_stream, dns_handle** out) {
                 G.D1i[(size_t)i * v.ny + j] = G.grid.D1[(size_t)(i + 1) * d.my + (j + 1)];
                 G.D2i[(size_t)i * v.ny + j] = G.grid.D2[(size_t)(i + 1) * d.my + (j + 1)];
             }
+        G.D1if.assign(G.D1i.begin(), G.D1i.end());
+        G.D2if.assign(G.D2i.begin(), G.D2i.end());
         G.twx = dnsb::twiddles(d.mx);
         G.twz = dnsb::twiddles(d.mz);
         G.twxf.assign(G.twx.begin(), G.twx.end());
@@ -308,6 +329,7 @@ int dns_bind_workspace(dns_handle* h, void* dev_ptr, size_t bytes) {
     if (h->graph) { cudaGraphDestroy(h->graph); h->graph = nullptr; }
     dnsk::set_attributes_spectral();
     dnsk::set_attributes_plane();
+    dnsk::set_attributes_plane_f32();
     cudaStream_t st = h->stream;
     int rc = check(h, cudaMemsetAsync(dev_ptr, 0, h->need, st), "clear workspace");
     if (rc) return rc;
@@ -320,6 +342,8 @@ int dns_bind_workspace(dns_handle* h, void* dev_ptr, size_t bytes) {
             {v.D1, G.grid.D1.data(), G.grid.D1.size() * 8},
             {v.D1i, G.D1i.data(), G.D1i.size() * 8},
             {v.D2i, G.D2i.data(), G.D2i.size() * 8},
+            {v.D1if, G.D1if.data(), G.D1if.size() * 4},
+            {v.D2if, G.D2if.data(), G.D2if.size() * 4},
             {v.ccw, G.grid.ccw.data(), G.grid.ccw.size() * 8},
             {v.kxt, G.kxt.data(), G.kxt.size() * 8},
             {v.kzt, G.kzt.data(), G.kzt.size() * 8},
@@ -334,10 +358,13 @@ int dns_bind_workspace(dns_handle* h, void* dev_ptr, size_t bytes) {
             {v.k2invf, G.k2invf.data(), G.k2invf.size() * 4},
             {v.ops[0], G.opsdev[0].data(), G.opsdev[0].size() * 8},
             {v.ops[1], G.opsdev[1].data(), G.opsdev[1].size() * 8},
+            {v.opsf[0], G.opsf[0].data(), G.opsf[0].size() * 4},
+            {v.opsf[1], G.opsf[1].data(), G.opsf[1].size() * 4},
             {v.mops[0], G.mopsdev[0].data(), G.mopsdev[0].size() * 8},
             {v.mops[1], G.mopsdev[1].data(), G.mopsdev[1].size() * 8},
         };
         for (const auto& u : ups) {
+            if (u.bytes == 0 || u.dst == nullptr) continue;
             rc = check(h, cudaMemcpyAsync((void*)u.dst, u.src, u.bytes, cudaMemcpyHostToDevice, st), "upload operators");
             if (rc) return rc;
         }

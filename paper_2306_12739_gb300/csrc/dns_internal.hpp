@@ -24,6 +24,8 @@ struct GroupView {
     const double* D1;     // [My][My]
     const double* D1i;    // [Ny][Ny]
     const double* D2i;    // [Ny][Ny]
+    const float* D1if;    // float copies for the mixed path
+    const float* D2if;
     const double* ccw;    // [My]
     const double* kxt;    // [NKX]
     const double* kzt;    // [NKZ]
@@ -37,6 +39,7 @@ struct GroupView {
     const float* kztf;
     const float* k2invf;
     const double* ops[2];   // per h index: [npairs][4][Ny][Ny]  (Mv, Pv, Me, Pe)
+    const float* opsf[2];   // mixed path, per h index: [npairs][4][Ny][Ny]  (Mv - I, Pv, Me - I, Pe)
     const double* mops[2];  // per h index: MU [Ny][Ny], PU [Ny][Ny], bU [Ny][2], Ug [Ny]
     // state, H layout
     double2 *v_t, *e_t, *v_s, *e_s;
@@ -66,11 +69,15 @@ void launch_plane_state(const GroupView& g, const double* U, const double* W, cu
 template <typename T>
 void launch_forcing(const GroupView& g, int s, cudaStream_t st);
 void launch_helm(const GroupView& g, int s, cudaStream_t st);
+void launch_helm_mixed(const GroupView& g, int s, cudaStream_t st);
 void launch_mean(const GroupView& g, int s, cudaStream_t st);
 void launch_stats(const GroupView& g, cudaStream_t st);
 void launch_pack(const GroupView& g, int member0, int count, cudaStream_t st);
 void launch_unpack(const GroupView& g, int member0, int count, cudaStream_t st);
 size_t plane_smem_bytes(const GroupView& g, int elem_bytes);
+bool launch_plane_f32(const GroupView& g, const double* U, const double* W, cudaStream_t st);
+size_t plane_f32_smem_bytes(int mx, int mz);
+void set_attributes_plane_f32();
 int plane_threads();
 
 }  // namespace dnsk

@@ -41,14 +41,16 @@ void launch_mean_deriv(const GroupView& g, const double* U, const double* W, cud
 constexpr int QB = 8;   // modes per tile
 constexpr int EB = 4;   // members per tile
 
+// T is the arithmetic (and output) type: double for the FP64 path, float for
+// the mixed path (the FP64 state is rounded to float on load).
 template <typename T>
 __global__ void __launch_bounds__(256) k_yderiv(const double2* __restrict__ v, const double2* __restrict__ et,
-                                                const double* __restrict__ D1i, const double* __restrict__ D2i,
+                                                const T* __restrict__ D1i, const T* __restrict__ D2i,
                                                 typename C2<T>::type* __restrict__ P5, int Ny, int E, int nmodes) {
     typedef typename C2<T>::type C;
     extern __shared__ __align__(16) unsigned char sm[];
-    double2* xv = (double2*)sm;                 // [QB][Ny][EB]
-    double2* xe = xv + QB * Ny * EB;
+    C* xv = (C*)sm;                 // [QB][Ny][EB]
+    C* xe = xv + QB * Ny * EB;
     const int q0 = blockIdx.x * QB, e0 = blockIdx.y * EB;
     const int tile = QB * Ny * EB;
     for (int idx = threadIdx.x; idx < tile; idx += blockDim.x) {
@@ -56,11 +58,12 @@ __global__ void __launch_bounds__(256) k_yderiv(const double2* __restrict__ v, c
         int y = (idx / EB) % Ny;
         int qq = idx / (EB * Ny);
         int q = q0 + qq, e = e0 + ee;
-        double2 a = make_double2(0.0, 0.0), b = a;
+        C a = czero<C>(), b = a;
         if (q < nmodes && e < E) {
             size_t o = ((size_t)q * Ny + y) * E + e;
-            a = v[o];
-            b = et[o];
+            double2 va = v[o], vb = et[o];
+            a.x = (T)va.x; a.y = (T)va.y;
+            b.x = (T)vb.x; b.y = (T)vb.y;
         }
         xv[idx] = a;
         xe[idx] = b;
@@ -72,36 +75,44 @@ __global__ void __launch_bounds__(256) k_yderiv(const double2* __restrict__ v, c
         int ee = (idx / QB) % EB;
         int y = idx / (QB * EB);
         int q = q0 + qq, e = e0 + ee;
-        double dvx = 0, dvy = 0, d2x = 0, d2y = 0, dex = 0, dey = 0;
-        const double* r1 = D1i + (size_t)y * Ny;
-        const double* r2 = D2i + (size_t)y * Ny;
+        T dvx = 0, dvy = 0, d2x = 0, d2y = 0, dex = 0, dey = 0;
+        const T* r1 = D1i + (size_t)y * Ny;
+        const T* r2 = D2i + (size_t)y * Ny;
         for (int k = 0; k < Ny; ++k) {
-            double d1 = __ldg(r1 + k), d2 = __ldg(r2 + k);
-            double2 a = xv[(qq * Ny + k) * EB + ee];
-            double2 b = xe[(qq * Ny + k) * EB + ee];
+            T d1 = __ldg(r1 + k), d2 = __ldg(r2 + k);
+            C a = xv[(qq * Ny + k) * EB + ee];
+            C b = xe[(qq * Ny + k) * EB + ee];
             dvx += d1 * a.x; dvy += d1 * a.y;
             d2x += d2 * a.x; d2y += d2 * a.y;
             dex += d1 * b.x; dey += d1 * b.y;
         }
         if (q < nmodes && e < E) {
             size_t o = ((size_t)y * E + e) * nmodes + q;
-            double2 a = xv[(qq * Ny + y) * EB + ee];
-            double2 b = xe[(qq * Ny + y) * EB + ee];
+            C a = xv[(qq * Ny + y) * EB + ee];
+            C b = xe[(qq * Ny + y) * EB + ee];
             C c;
-            c.x = (T)a.x; c.y = (T)a.y; P5[o] = c;
-            c.x = (T)dvx; c.y = (T)dvy; P5[fs + o] = c;
-            c.x = (T)d2x; c.y = (T)d2y; P5[2 * fs + o] = c;
-            c.x = (T)b.x; c.y = (T)b.y; P5[3 * fs + o] = c;
-            c.x = (T)dex; c.y = (T)dey; P5[4 * fs + o] = c;
+            P5[o] = a;
+            c.x = dvx; c.y = dvy; P5[fs + o] = c;
+            c.x = d2x; c.y = d2y; P5[2 * fs + o] = c;
+            P5[3 * fs + o] = b;
+            c.x = dex; c.y = dey; P5[4 * fs + o] = c;
         }
     }
 }
 
+template <typename T> __host__ __device__ const T* d1i_of(const GroupView& g);
+template <> __host__ __device__ const double* d1i_of<double>(const GroupView& g) { return g.D1i; }
+template <> __host__ __device__ const float* d1i_of<float>(const GroupView& g) { return g.D1if; }
+template <typename T> __host__ __device__ const T* d2i_of(const GroupView& g);
+template <> __host__ __device__ const double* d2i_of<double>(const GroupView& g) { return g.D2i; }
+template <> __host__ __device__ const float* d2i_of<float>(const GroupView& g) { return g.D2if; }
+
 template <typename T>
 void launch_yderiv(const GroupView& g, const double2* v, const double2* e, void* P5, cudaStream_t st) {
     dim3 grid((g.nmodes + QB - 1) / QB, (g.E + EB - 1) / EB);
-    size_t smem = 2 * (size_t)QB * g.ny * EB * sizeof(double2);
-    k_yderiv<T><<<grid, 256, smem, st>>>(v, e, g.D1i, g.D2i, (typename C2<T>::type*)P5, g.ny, g.E, g.nmodes);
+    size_t smem = 2 * (size_t)QB * g.ny * EB * sizeof(typename C2<T>::type);
+    k_yderiv<T><<<grid, 256, smem, st>>>(v, e, d1i_of<T>(g), d2i_of<T>(g), (typename C2<T>::type*)P5, g.ny, g.E,
+                                         g.nmodes);
 }
 template void launch_yderiv<double>(const GroupView&, const double2*, const double2*, void*, cudaStream_t);
 template void launch_yderiv<float>(const GroupView&, const double2*, const double2*, void*, cudaStream_t);
@@ -112,7 +123,8 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_forcing(GroupView g, int s) {
     typedef typename C2<T>::type C;
     extern __shared__ __align__(16) unsigned char sm[];
-    double2* phi = (double2*)sm;   // [QB][Ny][EB]
+    C* phi = (C*)sm;   // [QB][Ny][EB], i kx Nu + i kz Nw in the arithmetic type T
+    const T* D1 = d1i_of<T>(g);
     const int Ny = g.ny, E = g.E, nmodes = g.nmodes, NKX = g.nkx;
     const int q0 = blockIdx.x * QB, e0 = blockIdx.y * EB;
     const int tile = QB * Ny * EB;
@@ -123,16 +135,16 @@ __global__ void __launch_bounds__(256) k_forcing(GroupView g, int s) {
         int ee = (idx / QB) % EB;
         int y = idx / (QB * EB);
         int q = q0 + qq, e = e0 + ee;
-        double2 p = make_double2(0.0, 0.0);
+        C p = czero<C>();
         if (q < nmodes && e < E) {
             size_t o = ((size_t)y * E + e) * nmodes + q;
             C nu = N3[o], nw = N3[2 * fs + o];
             int mi = q / NKX, n = q - mi * NKX;
-            double kx = g.kxt[n], kz = g.kzt[mi];
+            T kx = (T)g.kxt[n], kz = (T)g.kzt[mi];
             // i kx Nu + i kz Nw
-            double ax = kx * (double)nu.x + kz * (double)nw.x;
-            double ay = kx * (double)nu.y + kz * (double)nw.y;
-            p = make_double2(-ay, ax);
+            T ax = kx * nu.x + kz * nw.x;
+            T ay = kx * nu.y + kz * nw.y;
+            p.x = -ay; p.y = ax;
         }
         phi[(qq * Ny + y) * EB + ee] = p;
     }
@@ -144,13 +156,14 @@ __global__ void __launch_bounds__(256) k_forcing(GroupView g, int s) {
         int qq = idx / (EB * Ny);
         int q = q0 + qq, e = e0 + ee;
         if (q >= nmodes || e >= E) continue;
-        double sx = 0.0, sy = 0.0;
-        const double* r1 = g.D1i + (size_t)y * Ny;
+        T tx = 0, ty = 0;
+        const T* r1 = D1 + (size_t)y * Ny;
         for (int k = 0; k < Ny; ++k) {
-            double d = __ldg(r1 + k);
-            double2 p = phi[(qq * Ny + k) * EB + ee];
-            sx += d * p.x; sy += d * p.y;
+            T d = __ldg(r1 + k);
+            C p = phi[(qq * Ny + k) * EB + ee];
+            tx += d * p.x; ty += d * p.y;
         }
+        const double sx = (double)tx, sy = (double)ty;
         size_t o = ((size_t)y * E + e) * nmodes + q;
         C nu = N3[o], nv = N3[fs + o], nw = N3[2 * fs + o];
         int mi = q / NKX, n = q - mi * NKX;
@@ -187,7 +200,7 @@ __global__ void __launch_bounds__(256) k_forcing(GroupView g, int s) {
 template <typename T>
 void launch_forcing(const GroupView& g, int s, cudaStream_t st) {
     dim3 grid((g.nmodes + QB - 1) / QB, (g.E + EB - 1) / EB);
-    size_t smem = (size_t)QB * g.ny * EB * sizeof(double2);
+    size_t smem = (size_t)QB * g.ny * EB * sizeof(typename C2<T>::type);
     k_forcing<T><<<grid, 256, smem, st>>>(g, s);
 }
 template void launch_forcing<double>(const GroupView&, int, cudaStream_t);
@@ -250,6 +263,79 @@ __global__ void __launch_bounds__(256) k_helm(GroupView g, int s) {
 void launch_helm(const GroupView& g, int s, cudaStream_t st) {
     size_t smem = 2 * (size_t)g.ny * g.ny * sizeof(double);
     k_helm<<<dim3(g.npairs, 2), 256, smem, st>>>(g, s);
+}
+
+// Mixed path: x_s = x_t + [(M_h - I) x_t] + [P_h F~] with both brackets in
+// single precision (operators rounded once from double) and the sums in double.
+// (M - I) x_t is O(dt/Re) x_t for the resolved modes, so its single-precision
+// rounding error is tiny against x_t (increment form of Eqs. CN1, CN2).
+__global__ void __launch_bounds__(256) k_helm_mixed(GroupView g, int s) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    const int Ny = g.ny, E = g.E, NKX = g.nkx;
+    const int p = blockIdx.x, f = blockIdx.y;
+    const int n = p % NKX, am = p / NKX;
+    if (n == 0 && am == 0) return;
+    const int hi = (s == 0) ? 0 : 1;
+    const size_t nn = (size_t)Ny * Ny;
+    const float* Mg = g.opsf[hi] + ((size_t)p * 4 + (f == 0 ? 0 : 2)) * nn;
+    const float* Pg = Mg + nn;
+    const int ncol = 2 * E;
+    const int nq = am > 0 ? 2 : 1;
+    const int q1 = (g.kz + am) * NKX + n, q2 = (g.kz - am) * NKX + n;
+    float* Ms = (float*)sm;
+    float* Ps = Ms + nn;
+    float* xs = Ps + nn;                 // [nq][Ny][ncol]
+    float* fs = xs + (size_t)2 * Ny * ncol;
+    const bool needM = (s != 2);
+    const double2* X = f == 0 ? g.v_t : g.e_t;
+    const double2* F = f == 0 ? g.Fv : g.Fe;
+    for (size_t i = threadIdx.x; i < nn; i += blockDim.x) {
+        if (needM) Ms[i] = Mg[i];
+        Ps[i] = Pg[i];
+    }
+    const int per = Ny * ncol;
+    for (int idx = threadIdx.x; idx < nq * per; idx += blockDim.x) {
+        int which = idx / per, r = idx - which * per;
+        int q = which == 0 ? q1 : q2;
+        const double* xc = (const double*)(X + (size_t)q * Ny * E);
+        const double* fc = (const double*)(F + (size_t)q * Ny * E);
+        if (needM) xs[idx] = (float)xc[r];
+        fs[idx] = (float)fc[r];
+    }
+    __syncthreads();
+    double2* M1 = f == 0 ? g.mx1_v : g.mx1_e;
+    double2* O = (s == 2) ? (f == 0 ? g.v_t : g.e_t) : (f == 0 ? g.v_s : g.e_s);
+    for (int idx = threadIdx.x; idx < nq * per; idx += blockDim.x) {
+        int which = idx / per;
+        int r = idx - which * per;
+        int y = r / ncol, c = r - y * ncol;
+        int q = which == 0 ? q1 : q2;
+        const float* xcol = xs + (size_t)which * per + c;
+        const float* fcol = fs + (size_t)which * per + c;
+        float accP = 0.f;
+        const float* pr = Ps + (size_t)y * Ny;
+        for (int k = 0; k < Ny; ++k) accP += pr[k] * fcol[k * ncol];
+        double* m1 = (double*)(M1 + (size_t)q * Ny * E);
+        double* oc = (double*)(O + (size_t)q * Ny * E);
+        double out;
+        if (needM) {
+            float accM = 0.f;
+            const float* mr = Ms + (size_t)y * Ny;
+            for (int k = 0; k < Ny; ++k) accM += mr[k] * xcol[k * ncol];
+            const double* xc = (const double*)(X + (size_t)q * Ny * E);
+            double base = xc[r] + (double)accM;
+            if (s == 1) m1[r] = base;
+            out = base + (double)accP;
+        } else {
+            out = m1[r] + (double)accP;
+        }
+        oc[r] = out;
+    }
+}
+
+void launch_helm_mixed(const GroupView& g, int s, cudaStream_t st) {
+    size_t smem = (2 * (size_t)g.ny * g.ny + 4 * (size_t)g.ny * 2 * g.E) * sizeof(float);
+    k_helm_mixed<<<dim3(g.npairs, 2), 256, smem, st>>>(g, s);
 }
 
 // --------------------------------------------------------------------- mean
@@ -485,6 +571,7 @@ void set_attributes_spectral() {
     cudaFuncSetAttribute(k_forcing<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_forcing<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_helm, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    cudaFuncSetAttribute(k_helm_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
 }
 
 }  // namespace dnsk
