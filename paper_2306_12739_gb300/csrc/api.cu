@@ -106,14 +106,14 @@ size_t layout_group(dns_handle* h, HostGroup& G, size_t cur) {
     for (int hi = 0; hi < 2; ++hi) {
         add((void**)&v.ops[hi], sizeof(double) * (size_t)v.npairs * 4 * nn);
         if (precision_mixed(h)) add((void**)&v.opsf[hi], sizeof(float) * (size_t)v.npairs * 4 * nn);
-        add((void**)&v.mops[hi], sizeof(double) * (2 * nn + 3 * (size_t)v.ny));
+        add((void**)&v.mops[hi], sizeof(double) * (2 * nn + 3 * (size_t)v.ny + (size_t)v.ny * v.my));
     }
     double2** st[] = {&v.v_t, &v.e_t, &v.v_s, &v.e_s, &v.mx1_v, &v.mx1_e, &v.Fv, &v.Fe, &v.Av, &v.Ae};
     for (auto p : st) add((void**)p, sizeof(double2) * S);
     double** mf[] = {&v.U_t, &v.W_t, &v.U_s, &v.W_s, &v.dU, &v.dW, &v.uv, &v.wv};
     for (auto p : mf) add((void**)p, sizeof(double) * (size_t)v.E * v.my);
-    add((void**)&v.AU, sizeof(double) * (size_t)v.E * v.ny);
-    add((void**)&v.AW, sizeof(double) * (size_t)v.E * v.ny);
+    add((void**)&v.AU, sizeof(double) * (size_t)v.E * v.my);
+    add((void**)&v.AW, sizeof(double) * (size_t)v.E * v.my);
     add((void**)&v.gamma, sizeof(double) * v.E);
     const size_t elem = precision_mixed(h) ? sizeof(float2) : sizeof(double2);
     add(&v.P5, elem * 5 * S);
@@ -157,8 +157,6 @@ void enqueue_step(dns_handle* h, Timer* tm = nullptr) {
             const double* cU = s == 0 ? g.U_t : g.U_s;
             const double* cW = s == 0 ? g.W_t : g.W_s;
             mark(-1);
-            dnsk::launch_mean_deriv(g, cU, cW, st);
-            mark(DNS_K_MEAN_DERIV);
             if (precision_mixed(h)) {
                 dnsk::launch_yderiv<float>(g, cv, ce, g.P5, st);
                 mark(DNS_K_YDERIV);
@@ -173,12 +171,12 @@ void enqueue_step(dns_handle* h, Timer* tm = nullptr) {
                 dnsk::launch_forcing<double>(g, s, st);
             }
             mark(DNS_K_FORCING);
+            // per-wavenumber implicit apply; the same launch carries the mean-flow
+            // update as E extra CTAs (independent work that overlaps with it)
             if (precision_mixed(h)) dnsk::launch_helm_mixed(g, s, st);
             else dnsk::launch_helm(g, s, st);
             mark(DNS_K_HELM);
-            dnsk::launch_mean(g, s, st);
-            mark(DNS_K_MEAN);
-            h->launches += 6;
+            h->launches += 4;
         }
     }
 }
@@ -291,6 +289,7 @@ int dns_create(const dns_config* cfg, void* cuda_stream, dns_handle** out) {
             md.insert(md.end(), G.ops[hi].PU.begin(), G.ops[hi].PU.end());
             md.insert(md.end(), G.ops[hi].bU.begin(), G.ops[hi].bU.end());
             md.insert(md.end(), G.ops[hi].Ug.begin(), G.ops[hi].Ug.end());
+            md.insert(md.end(), G.ops[hi].PD.begin(), G.ops[hi].PD.end());
         }
         G.D1i.resize(nn); G.D2i.resize(nn);
         for (int i = 0; i < v.ny; ++i)

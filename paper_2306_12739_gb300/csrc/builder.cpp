@@ -314,6 +314,15 @@ bool build_cn(const GridOps& go, const std::vector<double>& k2, double dt, doubl
             out->bU[(size_t)i * 2 + 1] = (double)B[(size_t)i * m + 2 * n + 1];
             out->Ug[i] = (double)B[(size_t)i * m + 2 * n + 2];
         }
+        // PD = PU D1[1..My-2, :]: the mean forcing d/dy <uv> folded into the solve,
+        // so that PU (D1 uv) = PD uv (uv vanishes on the walls)
+        out->PD.assign((size_t)n * My, 0.0);
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < My; ++j) {
+                dd acc;
+                for (int k = 0; k < n; ++k) acc += B[(size_t)i * m + n + k] * g.D1[(size_t)(k + 1) * My + j];
+                out->PD[(size_t)i * My + j] = (double)acc;
+            }
     }
     return true;
 }

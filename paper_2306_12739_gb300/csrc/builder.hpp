@@ -18,6 +18,7 @@ struct GridOps {
 struct CnOps {
     std::vector<double> Mv, Pv, Me, Pe;  // [npairs][Ny][Ny] each, Ny = My - 2
     std::vector<double> MU, PU, bU, Ug;  // mean flow: [Ny][Ny], [Ny][Ny], [Ny][2], [Ny]
+    std::vector<double> PD;              // PU * D1[interior rows, all nodes]: [Ny][My]
 };
 
 GridOps build_grid(int My);

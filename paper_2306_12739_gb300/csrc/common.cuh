@@ -143,4 +143,19 @@ __device__ __forceinline__ double block_max(double v, double* red) {
     return r;
 }
 
+// dU00/dy and dW00/dy at node row `row` (warp 0 of the CTA; result in out[0..1],
+// valid after the caller's next __syncthreads).
+__device__ __forceinline__ void mean_dy_row(const double* __restrict__ D1, const double* __restrict__ U,
+                                            const double* __restrict__ W, int My, int row, double* out) {
+    if (threadIdx.x >= 32) return;
+    const double* d = D1 + (size_t)row * My;
+    double a = 0.0, b = 0.0;
+    for (int j = threadIdx.x; j < My; j += 32) { a += d[j] * U[j]; b += d[j] * W[j]; }
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    if (threadIdx.x == 0) { out[0] = a; out[1] = b; }
+}
+
 }  // namespace dnsk

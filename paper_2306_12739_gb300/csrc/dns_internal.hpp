@@ -40,14 +40,14 @@ struct GroupView {
     const float* k2invf;
     const double* ops[2];   // per h index: [npairs][4][Ny][Ny]  (Mv, Pv, Me, Pe)
     const float* opsf[2];   // mixed path, per h index: [npairs][4][Ny][Ny]  (Mv - I, Pv, Me - I, Pe)
-    const double* mops[2];  // per h index: MU [Ny][Ny], PU [Ny][Ny], bU [Ny][2], Ug [Ny]
+    const double* mops[2];  // per h index: MU [Ny][Ny], PU [Ny][Ny], bU [Ny][2], Ug [Ny], PD [Ny][My]
     // state, H layout
     double2 *v_t, *e_t, *v_s, *e_s;
     double2 *mx1_v, *mx1_e;       // M_1 x_t, shared by sub-steps 2 and 3
     double2 *Fv, *Fe, *Av, *Ae;   // combined forcing of this sub-step; RK accumulators
     double *U_t, *W_t, *U_s, *W_s;   // [E][My]
-    double *AU, *AW;                 // mean forcing accumulators [E][Ny]
-    double *dU, *dW;                 // [E][My] dU/dy, dW/dy of the sub-step state
+    double *AU, *AW;                 // RK accumulators of <uv>, <wv> [E][My]
+    double *dU, *dW;                 // [E][My] (unused by the step)
     double *uv, *wv;                 // [E][My] plane means <uv>, <wv>
     double* gamma;                   // [E]
     // P layout work arrays (element type by precision)
@@ -70,7 +70,7 @@ template <typename T>
 void launch_forcing(const GroupView& g, int s, cudaStream_t st);
 void launch_helm(const GroupView& g, int s, cudaStream_t st);
 void launch_helm_mixed(const GroupView& g, int s, cudaStream_t st);
-void launch_mean(const GroupView& g, int s, cudaStream_t st);
+size_t mean_smem_bytes(const GroupView& g);
 void launch_stats(const GroupView& g, cudaStream_t st);
 void launch_pack(const GroupView& g, int member0, int count, cudaStream_t st);
 void launch_unpack(const GroupView& g, int member0, int count, cudaStream_t st);

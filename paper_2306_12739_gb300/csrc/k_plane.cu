@@ -73,8 +73,11 @@ __global__ void __launch_bounds__(PLANE_THREADS) k_plane(GroupView g, const doub
     const int q_mean = Kz * NKX;
     const T Um = (T)Ucur[(size_t)e * My + y + 1];
     const T Wm = (T)Wcur[(size_t)e * My + y + 1];
-    const T dUm = (T)g.dU[(size_t)e * My + y + 1];
-    const T dWm = (T)g.dW[(size_t)e * My + y + 1];
+    mean_dy_row(g.D1, Ucur + (size_t)e * My, Wcur + (size_t)e * My, My, y + 1, red);
+    __syncthreads();
+    const T dUm = (T)red[0];
+    const T dWm = (T)red[1];
+    __syncthreads();
 
     // spectral value of field `which` at mode q:
     //   0 u, 1 v, 2 w, 3 + 3 i + j: d u_i / d x_j (i: u v w, j: x y z)

@@ -93,23 +93,26 @@ template <int MX, int MZ>
 struct Cfg {
     static constexpr int KX = (MX - 1) / 3, KZ = (MZ - 1) / 3;
     static constexpr int NKX = KX + 1, NKZ = 2 * KZ + 1, NM = NKX * NKZ;
+    static constexpr int NKXP = NKX | 1;          // odd row stride: conflict-free 8-byte columns
     static constexpr int X1 = Split<MX>::N1, X2 = Split<MX>::N2;
     static constexpr int Z1 = Split<MZ>::N1, Z2 = Split<MZ>::N2;
     static constexpr int HP = MZ / 2;             // line pairs of the x transforms
     static constexpr int PLANE = MX * MZ;
     static constexpr int NF = 3;                  // fields transformed together
-    // per-field scratch: z-stage exchange [NKX][Z1][Z2+1] / x-stage [HP][X1][X2+1]
-    static constexpr int SZ = NKX * Z1 * (Z2 + 1);
-    static constexpr int SX = HP * X1 * (X2 + 1);
-    static constexpr int SS = SZ > SX ? SZ : SX;
-    static constexpr int SSP = SS > HP * MX ? SS : HP * MX;   // also holds one output plane
+    // Layouts (consecutive threads always touch consecutive words):
+    //   physical planes [x][z];  A (z-transformed columns) [z][n] stride NKXP;
+    //   z exchange [k1][n2][n] stride NKXP;  x exchange [k1][n2][p];  x output [x][p]
+    static constexpr int SZ = Z1 * Z2 * NKXP;
+    static constexpr int SX = X1 * X2 * HP;
+    static constexpr int SSP = SZ > SX ? SZ : SX;   // = also MX * HP (one output plane)
+    static constexpr int AS = MZ * NKXP;
     static constexpr int NT0 = NF * HP * X2;
     static constexpr int NT = ((NT0 + 31) / 32) * 32 > 1024 ? 1024 : ((NT0 + 31) / 32) * 32;
     // shared-memory layout (bytes)
     static constexpr size_t B_BASE = 0;                                   // float2 [5][NM]
     static constexpr size_t B_PLN = B_BASE + sizeof(float2) * 5 * NM;     // float  [4][PLANE]
-    static constexpr size_t B_A = B_PLN + sizeof(float) * 4 * PLANE;      // float2 [NF][NKX*MZ]
-    static constexpr size_t B_S = B_A + sizeof(float2) * NF * NKX * MZ;   // float2 [NF][SSP]
+    static constexpr size_t B_A = B_PLN + sizeof(float) * 4 * PLANE;      // float2 [NF][AS]
+    static constexpr size_t B_S = B_A + sizeof(float2) * NF * AS;         // float2 [NF][SSP]
     static constexpr size_t B_TW = B_S + sizeof(float2) * NF * SSP;       // float2 [MX + MZ]
     static constexpr size_t B_K = B_TW + sizeof(float2) * (MX + MZ);      // float [NKX + NKZ + NM]
     static constexpr size_t B_RED = ((B_K + sizeof(float) * (NKX + NKZ + NM)) + 15) / 16 * 16;
@@ -160,14 +163,16 @@ k_plane_f32(GroupView g, const double* __restrict__ Ucur, const double* __restri
     }
     const float Um = (float)Ucur[(size_t)e * My + y + 1];
     const float Wm = (float)Wcur[(size_t)e * My + y + 1];
-    const float dUm = (float)g.dU[(size_t)e * My + y + 1];
-    const float dWm = (float)g.dW[(size_t)e * My + y + 1];
+    mean_dy_row(g.D1, Ucur + (size_t)e * My, Wcur + (size_t)e * My, My, y + 1, red);
     const float2* Bv = base;
     const float2* BDv = base + NM;
     const float2* BD2v = base + 2 * NM;
     const float2* Be = base + 3 * NM;
     const float2* BDe = base + 4 * NM;
     constexpr int QMEAN = KZ * NKX;
+    __syncthreads();
+    const float dUm = (float)red[0];
+    const float dWm = (float)red[1];
     __syncthreads();
 
     // spectral value of field `which` at mode (mi, n): 0 u, 1 v, 2 w,
@@ -205,11 +210,12 @@ k_plane_f32(GroupView g, const double* __restrict__ Ucur, const double* __restri
     };
 
     // ---- inverse transforms of three fields; mode 0: into PU/PV/PW,
-    // mode 1: into the per-field scratch as planes (complex line-pair form)
+    // mode 1: into the per-field scratch as [x][p] line-pair planes
+    constexpr int NKXP = K::NKXP, AS = K::AS, SSP = K::SSP;
     auto inverse3 = [&](int w0, int w1, int w2, int mode) {
-        // z-stage, step A: tasks (f, n, n2)
+        // z-stage, step A: tasks (f, n2, n), n fastest
         for (int t = tid; t < NF * NKX * Z2; t += NT) {
-            const int f = t / (NKX * Z2), r = t - f * (NKX * Z2), n = r / Z2, n2 = r - n * Z2;
+            const int n = t % NKX, r = t / NKX, n2 = r % Z2, f = r / Z2;
             const int which = f == 0 ? w0 : (f == 1 ? w1 : w2);
             float2 v[Z1];
 #pragma unroll
@@ -221,85 +227,86 @@ k_plane_f32(GroupView g, const double* __restrict__ Ucur, const double* __restri
                 v[n1] = mi >= 0 ? gen(which, mi, n) : f2(0.f, 0.f);
             }
             Dft<Z1, +1>::run(v);
-            float2* S = Sb + f * K::SSP + n * (Z1 * (Z2 + 1));
+            float2* S = Sb + f * SSP + n2 * NKXP + n;
 #pragma unroll
             for (int k1 = 0; k1 < Z1; ++k1) {
                 float2 w = twz[n2 * k1];
-                S[k1 * (Z2 + 1) + n2] = k1 == 0 ? v[0] : mul(v[k1], f2(w.x, -w.y));
+                S[k1 * (Z2 * NKXP)] = k1 == 0 ? v[0] : mul(v[k1], f2(w.x, -w.y));
             }
         }
         __syncthreads();
-        // z-stage, step C: tasks (f, n, k1) -> A[f][n][z]
+        // z-stage, step C: tasks (f, k1, n) -> A[f][z][n]
         for (int t = tid; t < NF * NKX * Z1; t += NT) {
-            const int f = t / (NKX * Z1), r = t - f * (NKX * Z1), n = r / Z1, k1 = r - n * Z1;
-            const float2* S = Sb + f * K::SSP + n * (Z1 * (Z2 + 1)) + k1 * (Z2 + 1);
+            const int n = t % NKX, r = t / NKX, k1 = r % Z1, f = r / Z1;
+            const float2* S = Sb + f * SSP + k1 * (Z2 * NKXP) + n;
             float2 v[Z2];
 #pragma unroll
-            for (int n2 = 0; n2 < Z2; ++n2) v[n2] = S[n2];
+            for (int n2 = 0; n2 < Z2; ++n2) v[n2] = S[n2 * NKXP];
             Dft<Z2, +1>::run(v);
-            float2* A = Ab + f * (NKX * MZ) + n * MZ;
+            float2* A = Ab + f * AS + n;
 #pragma unroll
-            for (int k2 = 0; k2 < Z2; ++k2) A[k1 + Z1 * k2] = v[k2];
+            for (int k2 = 0; k2 < Z2; ++k2) A[(k1 + Z1 * k2) * NKXP] = v[k2];
         }
         __syncthreads();
-        // x-stage, step A: tasks (f, p, n2); line p carries rows p and p + HP
+        // x-stage, step A: tasks (f, n2, p), p fastest; line p carries rows p, p + HP
         for (int t = tid; t < NF * HP * X2; t += NT) {
-            const int f = t / (HP * X2), r = t - f * (HP * X2), p = r / X2, n2 = r - p * X2;
-            const float2* A = Ab + f * (NKX * MZ);
+            const int p = t % HP, r = t / HP, n2 = r % X2, f = r / X2;
+            const float2* A0 = Ab + f * AS + p * NKXP;
+            const float2* A1 = A0 + HP * NKXP;
             float2 v[X1];
 #pragma unroll
             for (int n1 = 0; n1 < X1; ++n1) {
                 const int k = X2 * n1 + n2;
                 float2 Z = f2(0.f, 0.f);
                 if (k == 0) {
-                    Z = f2(A[p].x, A[p + HP].x);             // Hermitian part of the n = 0 column
+                    Z = f2(A0[0].x, A1[0].x);                 // Hermitian part of the n = 0 column
                 } else if (k <= KX) {
-                    float2 a = A[k * MZ + p], b = A[k * MZ + p + HP];
-                    Z = f2(a.x - b.y, a.y + b.x);            // a + i b
+                    float2 a = A0[k], b = A1[k];
+                    Z = f2(a.x - b.y, a.y + b.x);             // a + i b
                 } else if (k >= MX - KX) {
-                    float2 a = A[(MX - k) * MZ + p], b = A[(MX - k) * MZ + p + HP];
-                    Z = f2(a.x + b.y, b.x - a.y);            // conj(a) + i conj(b)
+                    float2 a = A0[MX - k], b = A1[MX - k];
+                    Z = f2(a.x + b.y, b.x - a.y);             // conj(a) + i conj(b)
                 }
                 v[n1] = Z;
             }
             Dft<X1, +1>::run(v);
-            float2* S = Sb + f * K::SSP + p * (X1 * (X2 + 1));
+            float2* S = Sb + f * SSP + n2 * HP + p;
 #pragma unroll
             for (int k1 = 0; k1 < X1; ++k1) {
                 float2 w = twx[n2 * k1];
-                S[k1 * (X2 + 1) + n2] = k1 == 0 ? v[0] : mul(v[k1], f2(w.x, -w.y));
+                S[k1 * (X2 * HP)] = k1 == 0 ? v[0] : mul(v[k1], f2(w.x, -w.y));
             }
         }
         __syncthreads();
-        // x-stage, step C: one task (f, p, k1) per thread
+        // x-stage, step C: one task (f, k1, p) per thread
         static_assert(NF * HP * X1 <= NT, "one x-stage step-C task per thread");
         float2 out[X2];
         const bool active = tid < NF * HP * X1;
         int cf = 0, cp = 0, ck1 = 0;
         if (active) {
-            cf = tid / (HP * X1);
-            const int r = tid - cf * (HP * X1);
-            cp = r / X1;
-            ck1 = r - cp * X1;
-            const float2* S = Sb + cf * K::SSP + cp * (X1 * (X2 + 1)) + ck1 * (X2 + 1);
+            cp = tid % HP;
+            const int r = tid / HP;
+            ck1 = r % X1;
+            cf = r / X1;
+            const float2* S = Sb + cf * SSP + ck1 * (X2 * HP) + cp;
 #pragma unroll
-            for (int n2 = 0; n2 < X2; ++n2) out[n2] = S[n2];
+            for (int n2 = 0; n2 < X2; ++n2) out[n2] = S[n2 * HP];
             Dft<X2, +1>::run(out);
         }
         if (mode == 1) __syncthreads();     // the scratch is overwritten below
         if (active) {
             if (mode == 0) {
-                float* dst = pl + cf * PLANE;
+                float* dst = pl + cf * PLANE + cp;
 #pragma unroll
                 for (int k2 = 0; k2 < X2; ++k2) {
                     const int x = ck1 + X1 * k2;
-                    dst[cp * MX + x] = out[k2].x;
-                    dst[(cp + HP) * MX + x] = out[k2].y;
+                    dst[x * MZ] = out[k2].x;
+                    dst[x * MZ + HP] = out[k2].y;
                 }
             } else {
-                float2* dst = Sb + cf * K::SSP + cp * MX;
+                float2* dst = Sb + cf * SSP + cp;
 #pragma unroll
-                for (int k2 = 0; k2 < X2; ++k2) dst[ck1 + X1 * k2] = out[k2];
+                for (int k2 = 0; k2 < X2; ++k2) dst[(ck1 + X1 * k2) * HP] = out[k2];
             }
         }
         __syncthreads();
@@ -307,67 +314,67 @@ k_plane_f32(GroupView g, const double* __restrict__ Ucur, const double* __restri
 
     // ---- forward transform of ACC, kept modes to global
     auto forward = [&](float2* __restrict__ gout) {
-        // x-stage, step A: tasks (p, n2)
+        // x-stage, step A: tasks (n2, p), p fastest
         for (int t = tid; t < HP * X2; t += NT) {
-            const int p = t / X2, n2 = t - p * X2;
+            const int p = t % HP, n2 = t / HP;
             float2 v[X1];
 #pragma unroll
             for (int n1 = 0; n1 < X1; ++n1) {
                 const int x = X2 * n1 + n2;
-                v[n1] = f2(ACC[p * MX + x], ACC[(p + HP) * MX + x]);
+                v[n1] = f2(ACC[x * MZ + p], ACC[x * MZ + p + HP]);
             }
             Dft<X1, -1>::run(v);
-            float2* S = Sb + p * (X1 * (X2 + 1));
+            float2* S = Sb + n2 * HP + p;
 #pragma unroll
-            for (int k1 = 0; k1 < X1; ++k1) S[k1 * (X2 + 1) + n2] = k1 == 0 ? v[0] : mul(v[k1], twx[n2 * k1]);
+            for (int k1 = 0; k1 < X1; ++k1) S[k1 * (X2 * HP)] = k1 == 0 ? v[0] : mul(v[k1], twx[n2 * k1]);
         }
         __syncthreads();
-        // x-stage, step C: tasks (p, k1), outputs into slot-1 scratch [HP][MX]
+        // x-stage, step C: tasks (k1, p), outputs [x][p] into slot 1
         for (int t = tid; t < HP * X1; t += NT) {
-            const int p = t / X1, k1 = t - p * X1;
-            const float2* S = Sb + p * (X1 * (X2 + 1)) + k1 * (X2 + 1);
+            const int p = t % HP, k1 = t / HP;
+            const float2* S = Sb + k1 * (X2 * HP) + p;
             float2 v[X2];
 #pragma unroll
-            for (int n2 = 0; n2 < X2; ++n2) v[n2] = S[n2];
+            for (int n2 = 0; n2 < X2; ++n2) v[n2] = S[n2 * HP];
             Dft<X2, -1>::run(v);
-            float2* O = Sb + K::SSP + p * MX;
+            float2* O = Sb + SSP + p;
 #pragma unroll
-            for (int k2 = 0; k2 < X2; ++k2) O[k1 + X1 * k2] = v[k2];
+            for (int k2 = 0; k2 < X2; ++k2) O[(k1 + X1 * k2) * HP] = v[k2];
         }
         __syncthreads();
-        // split the two real rows, keep n <= KX, scale 1/MX -> A[0][n][z]
+        // split the two real rows, keep n <= KX, scale 1/MX -> A[0][z][n]
         const float sx = 1.0f / MX;
         for (int t = tid; t < HP * NKX; t += NT) {
-            const int p = t / NKX, n = t - p * NKX;
-            const float2* O = Sb + K::SSP + p * MX;
-            float2 Zn = O[n], Zc = O[(MX - n) % MX];
+            const int p = t % HP, n = t / HP;
+            const float2* O = Sb + SSP + p;
+            float2 Zn = O[n * HP], Zc = O[((MX - n) % MX) * HP];
             float2 xa = f2(0.5f * (Zn.x + Zc.x) * sx, 0.5f * (Zn.y - Zc.y) * sx);
             float2 xb = f2(0.5f * (Zn.y + Zc.y) * sx, 0.5f * (Zc.x - Zn.x) * sx);
-            Ab[n * MZ + p] = xa;
-            Ab[n * MZ + p + HP] = xb;
+            Ab[p * NKXP + n] = xa;
+            Ab[(p + HP) * NKXP + n] = xb;
         }
         __syncthreads();
-        // z-stage, step A: tasks (n, n2)
+        // z-stage, step A: tasks (n2, n), n fastest
         for (int t = tid; t < NKX * Z2; t += NT) {
-            const int n = t / Z2, n2 = t - n * Z2;
+            const int n = t % NKX, n2 = t / NKX;
             float2 v[Z1];
 #pragma unroll
-            for (int n1 = 0; n1 < Z1; ++n1) v[n1] = Ab[n * MZ + Z2 * n1 + n2];
+            for (int n1 = 0; n1 < Z1; ++n1) v[n1] = Ab[(Z2 * n1 + n2) * NKXP + n];
             Dft<Z1, -1>::run(v);
-            float2* S = Sb + n * (Z1 * (Z2 + 1));
+            float2* S = Sb + n2 * NKXP + n;
 #pragma unroll
-            for (int k1 = 0; k1 < Z1; ++k1) S[k1 * (Z2 + 1) + n2] = k1 == 0 ? v[0] : mul(v[k1], twz[n2 * k1]);
+            for (int k1 = 0; k1 < Z1; ++k1) S[k1 * (Z2 * NKXP)] = k1 == 0 ? v[0] : mul(v[k1], twz[n2 * k1]);
         }
         __syncthreads();
-        // z-stage, step C: tasks (n, k1); keep |m| <= KZ, scale 1/MZ -> staging [NM]
-        float2* stage = Sb + 2 * K::SSP;
+        // z-stage, step C: tasks (k1, n); keep |m| <= KZ, scale 1/MZ -> staging [NM]
+        float2* stage = Sb + 2 * SSP;
         const float sz = 1.0f / MZ;
         for (int t = tid; t < NKX * Z1; t += NT) {
-            const int n = t / Z1, k1 = t - n * Z1;
-            const float2* S = Sb + n * (Z1 * (Z2 + 1)) + k1 * (Z2 + 1);
+            const int n = t % NKX, k1 = t / NKX;
+            const float2* S = Sb + k1 * (Z2 * NKXP) + n;
             float2 v[Z2];
 #pragma unroll
-            for (int n2 = 0; n2 < Z2; ++n2) v[n2] = S[n2];
+            for (int n2 = 0; n2 < Z2; ++n2) v[n2] = S[n2 * NKXP];
             Dft<Z2, -1>::run(v);
 #pragma unroll
             for (int k2 = 0; k2 < Z2; ++k2) {
@@ -404,12 +411,12 @@ k_plane_f32(GroupView g, const double* __restrict__ Ucur, const double* __restri
         inverse3(3 + 3 * i, 4 + 3 * i, 5 + 3 * i, 1);
         // N_i = u d_x u_i + v d_y u_i + w d_z u_i, in this order
         const float2* G0 = Sb;
-        const float2* G1 = Sb + K::SSP;
-        const float2* G2 = Sb + 2 * K::SSP;
+        const float2* G1 = Sb + SSP;
+        const float2* G2 = Sb + 2 * SSP;
         for (int t = tid; t < HP * MX; t += NT) {
-            const int p = t / MX, x = t - p * MX;
+            const int p = t % HP, x = t / HP;
             float2 a = G0[t], b = G1[t], c = G2[t];
-            const int i0 = p * MX + x, i1 = (p + HP) * MX + x;
+            const int i0 = x * MZ + p, i1 = i0 + HP;
             ACC[i0] = PU[i0] * a.x + PV[i0] * b.x + PW[i0] * c.x;
             ACC[i1] = PU[i1] * a.y + PV[i1] * b.y + PW[i1] * c.y;
         }

@@ -19,21 +19,25 @@ namespace dnsk {
 __global__ void k_mean_deriv(const double* __restrict__ D1, const double* __restrict__ U,
                              const double* __restrict__ W, double* __restrict__ dU,
                              double* __restrict__ dW, int My) {
-    int e = blockIdx.x;
-    for (int i = threadIdx.x; i < My; i += blockDim.x) {
+    const int e = blockIdx.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int i = warp; i < My; i += nw) {
         double su = 0.0, sw = 0.0;
-        for (int j = 0; j < My; ++j) {
-            double d = D1[i * My + j];
-            su += d * U[e * My + j];
-            sw += d * W[e * My + j];
+        for (int j = lane; j < My; j += 32) {
+            double d = D1[(size_t)i * My + j];
+            su += d * U[(size_t)e * My + j];
+            sw += d * W[(size_t)e * My + j];
         }
-        dU[e * My + i] = su;
-        dW[e * My + i] = sw;
+        for (int o = 16; o > 0; o >>= 1) {
+            su += __shfl_xor_sync(0xffffffffu, su, o);
+            sw += __shfl_xor_sync(0xffffffffu, sw, o);
+        }
+        if (lane == 0) { dU[(size_t)e * My + i] = su; dW[(size_t)e * My + i] = sw; }
     }
 }
 
 void launch_mean_deriv(const GroupView& g, const double* U, const double* W, cudaStream_t st) {
-    k_mean_deriv<<<g.E, 128, 0, st>>>(g.D1, U, W, g.dU, g.dW, g.my);
+    k_mean_deriv<<<g.E, 256, 0, st>>>(g.D1, U, W, g.dU, g.dW, g.my);
 }
 
 // ------------------------------------------------------------------ y-derivs
@@ -206,12 +210,100 @@ void launch_forcing(const GroupView& g, int s, cudaStream_t st) {
 template void launch_forcing<double>(const GroupView&, int, cudaStream_t);
 template void launch_forcing<float>(const GroupView&, int, cudaStream_t);
 
+// --------------------------------------------------------------------- mean
+
+// Mean-flow update of member e (Eqs. CN3, CN4), run by one 256-thread CTA of
+// the implicit-apply launch.  The forcing d/dy <uv> is folded into the solve
+// (PD = PU D1), so the RK3 combination acts on the plane means themselves:
+//   U_int = MU U_int + PD <uv>~ + bU [U(-1), U(+1)] (+ gamma Ug, Poiseuille),
+// each row one warp with a lane-strided sum and a fixed shuffle tree.
+__device__ __forceinline__ double warp_sum(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+size_t mean_smem_bytes(const GroupView& g) { return (8 * (size_t)g.my + 32) * sizeof(double); }
+
+__device__ void mean_cta(const GroupView& g, int s, int e, unsigned char* sm) {
+    const int Ny = g.ny, My = g.my;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    double* red = (double*)sm;     // [32]
+    double* uvs = red + 32;        // [My] each below
+    double* wvs = uvs + My;
+    double* Ut = wvs + My;
+    double* Wt = Ut + My;
+    double* cu = Wt + My;
+    double* cw = cu + My;
+    double* Un = cw + My;
+    double* Wn = Un + My;
+    const int hi = (s == 0) ? 0 : 1;
+    const double* MU = g.mops[hi];
+    const double* PU = MU + (size_t)Ny * Ny;
+    const double* bU = PU + (size_t)Ny * Ny;
+    const double* Ug = bU + 2 * (size_t)Ny;
+    const double* PD = Ug + Ny;
+    for (int j = threadIdx.x; j < My; j += blockDim.x) {
+        const size_t o = (size_t)e * My + j;
+        const double a = g.uv[o], b = g.wv[o];
+        Ut[j] = g.U_t[o];
+        Wt[j] = g.W_t[o];
+        double ca, cb;
+        if (s == 0) {
+            ca = a; cb = b; g.AU[o] = a; g.AW[o] = b;
+        } else if (s == 1) {
+            const double pa = g.AU[o], pb = g.AW[o];
+            ca = 2.0 * a - pa; cb = 2.0 * b - pb;
+            g.AU[o] = (1.0 / 6.0) * pa + (4.0 / 6.0) * a;
+            g.AW[o] = (1.0 / 6.0) * pb + (4.0 / 6.0) * b;
+        } else {
+            ca = g.AU[o] + (1.0 / 6.0) * a;
+            cb = g.AW[o] + (1.0 / 6.0) * b;
+        }
+        cu[j] = ca;
+        cw[j] = cb;
+    }
+    __syncthreads();
+    for (int i = warp; i < Ny; i += nw) {
+        const double* mr = MU + (size_t)i * Ny;
+        const double* pr = PD + (size_t)i * My;
+        double a = 0.0, c = 0.0;
+        for (int j = lane; j < Ny; j += 32) { a += mr[j] * Ut[j + 1]; c += mr[j] * Wt[j + 1]; }
+        for (int j = lane; j < My; j += 32) { a += pr[j] * cu[j]; c += pr[j] * cw[j]; }
+        a = warp_sum(a);
+        c = warp_sum(c);
+        if (lane == 0) {
+            Un[i + 1] = a + (bU[2 * i] * Ut[0] + bU[2 * i + 1] * Ut[My - 1]);
+            Wn[i + 1] = c + (bU[2 * i] * Wt[0] + bU[2 * i + 1] * Wt[My - 1]);
+        }
+    }
+    if (threadIdx.x == 0) { Un[0] = Ut[0]; Un[My - 1] = Ut[My - 1]; Wn[0] = Wt[0]; Wn[My - 1] = Wt[My - 1]; }
+    __syncthreads();
+    double gam = 0.0;
+    if (g.flow == 1) {
+        double fl = 0.0, fg = 0.0;
+        for (int j = threadIdx.x; j < My; j += blockDim.x) fl += g.ccw[j] * Un[j];
+        for (int i = threadIdx.x; i < Ny; i += blockDim.x) fg += g.ccw[i + 1] * Ug[i];
+        fl = block_sum(fl, red);
+        fg = block_sum(fg, red);
+        gam = (g.bulk_flux - fl) / fg;
+    }
+    double* Uo = (s == 2) ? (g.U_t + (size_t)e * My) : (g.U_s + (size_t)e * My);
+    double* Wo = (s == 2) ? (g.W_t + (size_t)e * My) : (g.W_s + (size_t)e * My);
+    for (int j = threadIdx.x; j < My; j += blockDim.x) {
+        Uo[j] = (j > 0 && j < My - 1) ? Un[j] + gam * Ug[j - 1] : Un[j];
+        Wo[j] = Wn[j];
+    }
+    if (threadIdx.x == 0) g.gamma[e] = gam;
+}
+
 // --------------------------------------------------------------------- helm
 
 __global__ void __launch_bounds__(256) k_helm(GroupView g, int s) {
     extern __shared__ __align__(16) unsigned char sm[];
     const int Ny = g.ny, E = g.E, NKX = g.nkx;
-    const int p = blockIdx.x, f = blockIdx.y;
+    if ((int)blockIdx.x < E) { mean_cta(g, s, blockIdx.x, sm); return; }
+    const int b = blockIdx.x - E;
+    const int p = b % g.npairs, f = b / g.npairs;
     const int n = p % NKX, am = p / NKX;
     if (n == 0 && am == 0) return;
     const int hi = (s == 0) ? 0 : 1;
@@ -262,7 +354,8 @@ __global__ void __launch_bounds__(256) k_helm(GroupView g, int s) {
 
 void launch_helm(const GroupView& g, int s, cudaStream_t st) {
     size_t smem = 2 * (size_t)g.ny * g.ny * sizeof(double);
-    k_helm<<<dim3(g.npairs, 2), 256, smem, st>>>(g, s);
+    if (smem < mean_smem_bytes(g)) smem = mean_smem_bytes(g);
+    k_helm<<<g.E + 2 * g.npairs, 256, smem, st>>>(g, s);
 }
 
 // Mixed path: x_s = x_t + [(M_h - I) x_t] + [P_h F~] with both brackets in
@@ -272,7 +365,9 @@ void launch_helm(const GroupView& g, int s, cudaStream_t st) {
 __global__ void __launch_bounds__(256) k_helm_mixed(GroupView g, int s) {
     extern __shared__ __align__(16) unsigned char sm[];
     const int Ny = g.ny, E = g.E, NKX = g.nkx;
-    const int p = blockIdx.x, f = blockIdx.y;
+    if ((int)blockIdx.x < E) { mean_cta(g, s, blockIdx.x, sm); return; }
+    const int b = blockIdx.x - E;
+    const int p = b % g.npairs, f = b / g.npairs;
     const int n = p % NKX, am = p / NKX;
     if (n == 0 && am == 0) return;
     const int hi = (s == 0) ? 0 : 1;
@@ -335,96 +430,11 @@ __global__ void __launch_bounds__(256) k_helm_mixed(GroupView g, int s) {
 
 void launch_helm_mixed(const GroupView& g, int s, cudaStream_t st) {
     size_t smem = (2 * (size_t)g.ny * g.ny + 4 * (size_t)g.ny * 2 * g.E) * sizeof(float);
-    k_helm_mixed<<<dim3(g.npairs, 2), 256, smem, st>>>(g, s);
+    if (smem < mean_smem_bytes(g)) smem = mean_smem_bytes(g);
+    k_helm_mixed<<<g.E + 2 * g.npairs, 256, smem, st>>>(g, s);
 }
 
 // --------------------------------------------------------------------- mean
-
-__global__ void k_mean(GroupView g, int s) {
-    extern __shared__ __align__(16) unsigned char sm[];
-    __shared__ double red[32];
-    const int Ny = g.ny, My = g.my, e = blockIdx.x;
-    double* fu = (double*)sm;     // [Ny] combined forcing
-    double* fw = fu + Ny;
-    double* ui = fw + Ny;         // new interior U
-    double* wi = ui + Ny;
-    const int hi = (s == 0) ? 0 : 1;
-    const double* MU = g.mops[hi];
-    const double* PU = MU + (size_t)Ny * Ny;
-    const double* bU = PU + (size_t)Ny * Ny;
-    const double* Ug = bU + 2 * (size_t)Ny;
-    const double* uv = g.uv + (size_t)e * My;
-    const double* wv = g.wv + (size_t)e * My;
-    for (int i = threadIdx.x; i < Ny; i += blockDim.x) {
-        double a = 0.0, b = 0.0;
-        for (int j = 0; j < My; ++j) {
-            double d = g.D1[(size_t)(i + 1) * My + j];
-            a += d * uv[j];
-            b += d * wv[j];
-        }
-        size_t o = (size_t)e * Ny + i;
-        double ft, gt;
-        if (s == 0) {
-            ft = a; gt = b; g.AU[o] = a; g.AW[o] = b;
-        } else if (s == 1) {
-            double pa = g.AU[o], pb = g.AW[o];
-            ft = 2.0 * a - pa; gt = 2.0 * b - pb;
-            g.AU[o] = (1.0 / 6.0) * pa + (4.0 / 6.0) * a;
-            g.AW[o] = (1.0 / 6.0) * pb + (4.0 / 6.0) * b;
-        } else {
-            ft = g.AU[o] + (1.0 / 6.0) * a;
-            gt = g.AW[o] + (1.0 / 6.0) * b;
-        }
-        fu[i] = ft;
-        fw[i] = gt;
-    }
-    __syncthreads();
-    const double* Ut = g.U_t + (size_t)e * My;
-    const double* Wt = g.W_t + (size_t)e * My;
-    double fl = 0.0, fg = 0.0;
-    for (int i = threadIdx.x; i < Ny; i += blockDim.x) {
-        double a = 0.0, b = 0.0, c = 0.0, d = 0.0;
-        for (int j = 0; j < Ny; ++j) {
-            a += MU[(size_t)i * Ny + j] * Ut[j + 1];
-            c += MU[(size_t)i * Ny + j] * Wt[j + 1];
-        }
-        double bu = bU[2 * i] * Ut[0] + bU[2 * i + 1] * Ut[My - 1];
-        double bw = bU[2 * i] * Wt[0] + bU[2 * i + 1] * Wt[My - 1];
-        for (int j = 0; j < Ny; ++j) {
-            b += PU[(size_t)i * Ny + j] * fu[j];
-            d += PU[(size_t)i * Ny + j] * fw[j];
-        }
-        ui[i] = a + bu + b;
-        wi[i] = c + bw + d;
-        fl += g.ccw[i + 1] * ui[i];
-        fg += g.ccw[i + 1] * Ug[i];
-    }
-    double gam = 0.0;
-    if (g.flow == 1) {
-        double f0 = block_sum(fl, red) + g.ccw[0] * Ut[0] + g.ccw[My - 1] * Ut[My - 1];
-        double f1 = block_sum(fg, red);
-        gam = (g.bulk_flux - f0) / f1;
-    } else {
-        __syncthreads();
-    }
-    double* Uo = (s == 2) ? (g.U_t + (size_t)e * My) : (g.U_s + (size_t)e * My);
-    double* Wo = (s == 2) ? (g.W_t + (size_t)e * My) : (g.W_s + (size_t)e * My);
-    double u0 = Ut[0], uN = Ut[My - 1], w0 = Wt[0], wN = Wt[My - 1];
-    __syncthreads();   // every read of U_t / W_t is done before an in-place write
-    for (int i = threadIdx.x; i < Ny; i += blockDim.x) {
-        Uo[i + 1] = ui[i] + gam * Ug[i];
-        Wo[i + 1] = wi[i];
-    }
-    if (threadIdx.x == 0) {
-        Uo[0] = u0; Uo[My - 1] = uN; Wo[0] = w0; Wo[My - 1] = wN;
-        g.gamma[e] = gam;
-    }
-}
-
-void launch_mean(const GroupView& g, int s, cudaStream_t st) {
-    size_t smem = 4 * (size_t)g.ny * sizeof(double);
-    k_mean<<<g.E, 128, smem, st>>>(g, s);
-}
 
 // -------------------------------------------------------------------- stats
 
