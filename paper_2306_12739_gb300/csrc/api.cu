@@ -23,7 +23,7 @@ struct HostGroup {
     dnsb::GridOps grid;
     dnsb::CnOps ops[2];
     std::vector<double> kxt, kzt, k2t, k2inv, twx, twz, opsdev[2], mopsdev[2], D1i, D2i;
-    std::vector<float> kxtf, kztf, k2invf, twxf, twzf, opsf[2], D1if, D2if;
+    std::vector<float> kxtf, kztf, k2invf, twxf, twzf, opsf[2], opsfT[2], D1if, D2if, D1T, D2T;
     // byte offsets inside the workspace
     struct Off { size_t off, bytes; };
     std::vector<std::pair<void**, Off>> slots;
@@ -91,6 +91,9 @@ size_t layout_group(dns_handle* h, HostGroup& G, size_t cur) {
     add((void**)&v.D2i, sizeof(double) * nn);
     add((void**)&v.D1if, sizeof(float) * nn);
     add((void**)&v.D2if, sizeof(float) * nn);
+    add((void**)&v.D1T, sizeof(float) * (size_t)v.ny * v.rp);
+    add((void**)&v.D2T, sizeof(float) * (size_t)v.ny * v.rp);
+    add((void**)&v.status, 256);
     add((void**)&v.ccw, sizeof(double) * v.my);
     add((void**)&v.kxt, sizeof(double) * v.nkx);
     add((void**)&v.kzt, sizeof(double) * v.nkz);
@@ -105,7 +108,10 @@ size_t layout_group(dns_handle* h, HostGroup& G, size_t cur) {
     add((void**)&v.k2invf, sizeof(float) * v.nmodes);
     for (int hi = 0; hi < 2; ++hi) {
         add((void**)&v.ops[hi], sizeof(double) * (size_t)v.npairs * 4 * nn);
-        if (precision_mixed(h)) add((void**)&v.opsf[hi], sizeof(float) * (size_t)v.npairs * 4 * nn);
+        if (precision_mixed(h)) {
+            add((void**)&v.opsf[hi], sizeof(float) * (size_t)v.npairs * 4 * nn);
+            add((void**)&v.opsfT[hi], sizeof(float) * (size_t)v.npairs * 4 * v.ny * v.rp);
+        }
         add((void**)&v.mops[hi], sizeof(double) * (2 * nn + 3 * (size_t)v.ny + (size_t)v.ny * v.my));
     }
     double2** st[] = {&v.v_t, &v.e_t, &v.v_s, &v.e_s, &v.mx1_v, &v.mx1_e, &v.Fv, &v.Fe, &v.Av, &v.Ae};
@@ -158,11 +164,11 @@ void enqueue_step(dns_handle* h, Timer* tm = nullptr) {
             const double* cW = s == 0 ? g.W_t : g.W_s;
             mark(-1);
             if (precision_mixed(h)) {
-                dnsk::launch_yderiv<float>(g, cv, ce, g.P5, st);
+                dnsk::launch_yderiv_t(g, cv, ce, st);
                 mark(DNS_K_YDERIV);
                 dnsk::launch_plane_f32(g, cU, cW, st);
                 mark(DNS_K_PLANE);
-                dnsk::launch_forcing<float>(g, s, st);
+                dnsk::launch_forcing_t(g, s, st);
             } else {
                 dnsk::launch_yderiv<double>(g, cv, ce, g.P5, st);
                 mark(DNS_K_YDERIV);
@@ -173,7 +179,7 @@ void enqueue_step(dns_handle* h, Timer* tm = nullptr) {
             mark(DNS_K_FORCING);
             // per-wavenumber implicit apply; the same launch carries the mean-flow
             // update as E extra CTAs (independent work that overlaps with it)
-            if (precision_mixed(h)) dnsk::launch_helm_mixed(g, s, st);
+            if (precision_mixed(h)) dnsk::launch_helm_t(g, s, st);
             else dnsk::launch_helm(g, s, st);
             mark(DNS_K_HELM);
             h->launches += 4;
@@ -227,6 +233,7 @@ int dns_create(const dns_config* cfg, void* cuda_stream, dns_handle** out) {
         v.ny = d.my - 2;
         v.E = d.members;
         v.npairs = v.nkx * (v.kz + 1);
+        v.rp = (v.ny + 3) / 4 * 4;
         v.flow = d.flow == DNS_POISEUILLE ? 1 : 0;
         v.re = d.re; v.dt = d.dt; v.u_wall = d.u_wall; v.bulk_flux = d.bulk_flux;
         if (!make_plan(d.mx, &v.px) || !make_plan(d.mz, &v.pz))
@@ -234,6 +241,13 @@ int dns_create(const dns_config* cfg, void* cuda_stream, dns_handle** out) {
         size_t smem = precision_mixed(h) ? dnsk::plane_f32_smem_bytes(d.mx, d.mz) : dnsk::plane_smem_bytes(v, 8);
         if (smem == 0 || smem > 227 * 1024)
             return fail(h, DNS_ERR_UNSUPPORTED, "group %d: plane stage needs %zu B of shared memory", gi, smem);
+        if (precision_mixed(h)) {
+            size_t m1 = dnsk::helm_t_smem_bytes(v), m2 = dnsk::yderiv_t_smem_bytes(v), m3 = dnsk::forcing_t_smem_bytes(v);
+            size_t mm = m1 > m2 ? m1 : m2;
+            mm = mm > m3 ? mm : m3;
+            if (mm > 227 * 1024)
+                return fail(h, DNS_ERR_UNSUPPORTED, "group %d: spectral stage needs %zu B of shared memory", gi, mm);
+        }
         // operators
         G.grid = dnsb::build_grid(d.my);
         double a1 = dnsb::fundamental(d.lx), a3 = dnsb::fundamental(d.lz);
@@ -282,6 +296,13 @@ int dns_create(const dns_config* cfg, void* cuda_stream, dns_handle** out) {
                             dst[i] = (float)val;
                         }
                     }
+                auto& ot = G.opsfT[hi];
+                const size_t mt = (size_t)v.ny * v.rp;
+                ot.assign((size_t)v.npairs * 4 * mt, 0.f);
+                for (size_t blk = 0; blk < (size_t)v.npairs * 4; ++blk)
+                    for (int r = 0; r < v.ny; ++r)
+                        for (int k = 0; k < v.ny; ++k)
+                            ot[blk * mt + (size_t)k * v.rp + r] = of[blk * nn + (size_t)r * v.ny + k];
             }
             auto& md = G.mopsdev[hi];
             md.clear();
@@ -299,6 +320,13 @@ int dns_create(const dns_config* cfg, void* cuda_stream, dns_handle** out) {
             }
         G.D1if.assign(G.D1i.begin(), G.D1i.end());
         G.D2if.assign(G.D2i.begin(), G.D2i.end());
+        G.D1T.assign((size_t)v.ny * v.rp, 0.f);
+        G.D2T.assign((size_t)v.ny * v.rp, 0.f);
+        for (int r = 0; r < v.ny; ++r)
+            for (int k = 0; k < v.ny; ++k) {
+                G.D1T[(size_t)k * v.rp + r] = (float)G.D1i[(size_t)r * v.ny + k];
+                G.D2T[(size_t)k * v.rp + r] = (float)G.D2i[(size_t)r * v.ny + k];
+            }
         G.twx = dnsb::twiddles(d.mx);
         G.twz = dnsb::twiddles(d.mz);
         G.twxf.assign(G.twx.begin(), G.twx.end());
@@ -329,6 +357,7 @@ int dns_bind_workspace(dns_handle* h, void* dev_ptr, size_t bytes) {
     dnsk::set_attributes_spectral();
     dnsk::set_attributes_plane();
     dnsk::set_attributes_plane_f32();
+    dnsk::set_attributes_gemm_t();
     cudaStream_t st = h->stream;
     int rc = check(h, cudaMemsetAsync(dev_ptr, 0, h->need, st), "clear workspace");
     if (rc) return rc;
@@ -359,6 +388,10 @@ int dns_bind_workspace(dns_handle* h, void* dev_ptr, size_t bytes) {
             {v.ops[1], G.opsdev[1].data(), G.opsdev[1].size() * 8},
             {v.opsf[0], G.opsf[0].data(), G.opsf[0].size() * 4},
             {v.opsf[1], G.opsf[1].data(), G.opsf[1].size() * 4},
+            {v.opsfT[0], G.opsfT[0].data(), G.opsfT[0].size() * 4},
+            {v.opsfT[1], G.opsfT[1].data(), G.opsfT[1].size() * 4},
+            {v.D1T, G.D1T.data(), G.D1T.size() * 4},
+            {v.D2T, G.D2T.data(), G.D2T.size() * 4},
             {v.mops[0], G.mopsdev[0].data(), G.mopsdev[0].size() * 8},
             {v.mops[1], G.mopsdev[1].data(), G.mopsdev[1].size() * 8},
         };

@@ -17,6 +17,8 @@ namespace dnsk {
 // with q = (m + Kz) * NKX + n, NKX = Kx + 1, y the interior index 0..Ny-1.
 struct GroupView {
     int mx, my, mz, kx, kz, nkx, nkz, nmodes, ny, E, npairs;
+    int rp;               // Ny rounded up to a multiple of 4 (row padding of transposed operators)
+    int* status;          // device error word (1: a bounded wait gave up)
     int flow;             // 0 Couette, 1 Poiseuille
     double re, dt, u_wall, bulk_flux;
     FftPlan px, pz;
@@ -26,6 +28,8 @@ struct GroupView {
     const double* D2i;    // [Ny][Ny]
     const float* D1if;    // float copies for the mixed path
     const float* D2if;
+    const float* D1T;     // mixed path, transposed and row-padded: D1T[k][r] = D1i[r][k], [Ny][rp]
+    const float* D2T;
     const double* ccw;    // [My]
     const double* kxt;    // [NKX]
     const double* kzt;    // [NKZ]
@@ -40,6 +44,7 @@ struct GroupView {
     const float* k2invf;
     const double* ops[2];   // per h index: [npairs][4][Ny][Ny]  (Mv, Pv, Me, Pe)
     const float* opsf[2];   // mixed path, per h index: [npairs][4][Ny][Ny]  (Mv - I, Pv, Me - I, Pe)
+    const float* opsfT[2];  // the same transposed and row-padded: [npairs][4][Ny][rp]
     const double* mops[2];  // per h index: MU [Ny][Ny], PU [Ny][Ny], bU [Ny][2], Ug [Ny], PD [Ny][My]
     // state, H layout
     double2 *v_t, *e_t, *v_s, *e_s;
@@ -70,7 +75,14 @@ template <typename T>
 void launch_forcing(const GroupView& g, int s, cudaStream_t st);
 void launch_helm(const GroupView& g, int s, cudaStream_t st);
 void launch_helm_mixed(const GroupView& g, int s, cudaStream_t st);
-size_t mean_smem_bytes(const GroupView& g);
+inline size_t mean_smem_bytes(const GroupView& g) { return (8 * (size_t)g.my + 32) * sizeof(double); }
+size_t helm_t_smem_bytes(const GroupView& g);
+size_t yderiv_t_smem_bytes(const GroupView& g);
+size_t forcing_t_smem_bytes(const GroupView& g);
+void launch_yderiv_t(const GroupView& g, const double2* v, const double2* e, cudaStream_t st);
+void launch_forcing_t(const GroupView& g, int s, cudaStream_t st);
+void launch_helm_t(const GroupView& g, int s, cudaStream_t st);
+void set_attributes_gemm_t();
 void launch_stats(const GroupView& g, cudaStream_t st);
 void launch_pack(const GroupView& g, int member0, int count, cudaStream_t st);
 void launch_unpack(const GroupView& g, int member0, int count, cudaStream_t st);

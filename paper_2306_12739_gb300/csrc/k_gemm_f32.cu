@@ -1,0 +1,366 @@
+// Single-precision y-contractions of the mixed path, register-tiled (each
+// thread owns a 4-row x 1-complex-column micro-tile; operators are stored
+// transposed and row-padded, [k][r] with r padded to RP = 4 ceil(Ny/4), so one
+// 16-byte shared load feeds four rows).
+//   k_yderiv_t  Dv, D2v, D eta with the shared Chebyshev operators (Sec. 3.1),
+//               H layout in, P layout out
+//   k_forcing_t F = -k^2 Nv - D1 (i kx Nu + i kz Nw), G = i kz Nu - i kx Nw
+//               (Eqs. Dv, eta) and the RK3 combination, P layout in, H out
+//   k_helm_t    x_s = x_t + (M_h - I) x_t + P_h F~ per wavenumber pair
+//               (increment form of Eqs. CN1, CN2); the pair's operators arrive
+//               by one TMA bulk copy (cp.async.bulk + mbarrier) per CTA.
+#include "dns_internal.hpp"
+#include "mean.cuh"
+
+namespace dnsk {
+
+namespace gt {
+
+constexpr int THREADS = 256;
+
+// Column tile: QT consecutive modes x EBT consecutive members (complex columns).
+struct Tile {
+    int QT, EBT, NC;   // NC = QT * EBT complex columns
+};
+
+__host__ __device__ inline Tile tile_of(int E, int ny) {
+    const int cap = ny <= 96 ? 64 : 32;    // complex columns per tile
+    Tile t;
+    t.EBT = E < cap ? E : cap;
+    t.QT = cap / t.EBT;
+    if (t.QT < 1) t.QT = 1;
+    t.NC = t.QT * t.EBT;
+    return t;
+}
+
+// --------------------------------------------------------------- y-derivs
+
+__global__ void __launch_bounds__(THREADS) k_yderiv_t(GroupView g, const double2* __restrict__ V,
+                                                     const double2* __restrict__ H) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    const int Ny = g.ny, RP = g.rp, E = g.E, NM = g.nmodes;
+    const Tile T = tile_of(E, Ny);
+    const int q0 = blockIdx.x * T.QT, e0 = blockIdx.y * T.EBT;
+    const int NCR = 2 * T.NC;                       // real columns
+    float* D1 = (float*)sm;                         // [Ny][RP]
+    float* D2 = D1 + Ny * RP;
+    float* Xv = D2 + Ny * RP;                       // [Ny][NCR], column = 2 (el QT + qq) + c
+    float* Xe = Xv + Ny * NCR;
+    {
+        const float4* s1 = (const float4*)g.D1T;
+        const float4* s2 = (const float4*)g.D2T;
+        for (int i = threadIdx.x; i < Ny * RP / 4; i += THREADS) {
+            ((float4*)D1)[i] = s1[i];
+            ((float4*)D2)[i] = s2[i];
+        }
+        // state tile, read in H order [q][y][e], written [y][(el QT + qq)]
+        const int per_q = Ny * T.EBT;
+        for (int i = threadIdx.x; i < T.QT * per_q; i += THREADS) {
+            const int qq = i / per_q, r = i - qq * per_q, k = r / T.EBT, el = r - k * T.EBT;
+            const int q = q0 + qq, e = e0 + el;
+            double2 a = make_double2(0.0, 0.0), b = a;
+            if (q < NM && e < E) {
+                const size_t o = ((size_t)q * Ny + k) * E + e;
+                a = V[o];
+                b = H[o];
+            }
+            const int c = 2 * (el * T.QT + qq);
+            *(float2*)&Xv[k * NCR + c] = make_float2((float)a.x, (float)a.y);
+            *(float2*)&Xe[k * NCR + c] = make_float2((float)b.x, (float)b.y);
+        }
+    }
+    __syncthreads();
+    const size_t fs = (size_t)Ny * E * NM;
+    float2* P = (float2*)g.P5;
+    const int RB = RP / 4;
+    for (int m = threadIdx.x; m < RB * T.NC; m += THREADS) {
+        const int j = m % T.NC, rb = m / T.NC;       // consecutive threads: consecutive q
+        const int r0 = 4 * rb;
+        float4 av[2] = {make_float4(0, 0, 0, 0), make_float4(0, 0, 0, 0)};   // D1 v: re, im
+        float4 bv[2] = {make_float4(0, 0, 0, 0), make_float4(0, 0, 0, 0)};   // D2 v
+        float4 ae[2] = {make_float4(0, 0, 0, 0), make_float4(0, 0, 0, 0)};   // D1 eta
+#pragma unroll 4
+        for (int k = 0; k < Ny; ++k) {
+            const float4 d1 = *(const float4*)&D1[k * RP + r0];
+            const float4 d2 = *(const float4*)&D2[k * RP + r0];
+            const float2 x = *(const float2*)&Xv[k * NCR + 2 * j];
+            const float2 h = *(const float2*)&Xe[k * NCR + 2 * j];
+            av[0].x += d1.x * x.x; av[0].y += d1.y * x.x; av[0].z += d1.z * x.x; av[0].w += d1.w * x.x;
+            av[1].x += d1.x * x.y; av[1].y += d1.y * x.y; av[1].z += d1.z * x.y; av[1].w += d1.w * x.y;
+            bv[0].x += d2.x * x.x; bv[0].y += d2.y * x.x; bv[0].z += d2.z * x.x; bv[0].w += d2.w * x.x;
+            bv[1].x += d2.x * x.y; bv[1].y += d2.y * x.y; bv[1].z += d2.z * x.y; bv[1].w += d2.w * x.y;
+            ae[0].x += d1.x * h.x; ae[0].y += d1.y * h.x; ae[0].z += d1.z * h.x; ae[0].w += d1.w * h.x;
+            ae[1].x += d1.x * h.y; ae[1].y += d1.y * h.y; ae[1].z += d1.z * h.y; ae[1].w += d1.w * h.y;
+        }
+        const int el = j / T.QT, qq = j - el * T.QT;
+        const int q = q0 + qq, e = e0 + el;
+        if (q >= NM || e >= E) continue;
+        const float r_av[2][4] = {{av[0].x, av[0].y, av[0].z, av[0].w}, {av[1].x, av[1].y, av[1].z, av[1].w}};
+        const float r_bv[2][4] = {{bv[0].x, bv[0].y, bv[0].z, bv[0].w}, {bv[1].x, bv[1].y, bv[1].z, bv[1].w}};
+        const float r_ae[2][4] = {{ae[0].x, ae[0].y, ae[0].z, ae[0].w}, {ae[1].x, ae[1].y, ae[1].z, ae[1].w}};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int y = r0 + i;
+            if (y >= Ny) break;
+            const size_t o = ((size_t)y * E + e) * NM + q;
+            P[o] = *(const float2*)&Xv[y * NCR + 2 * j];
+            P[fs + o] = make_float2(r_av[0][i], r_av[1][i]);
+            P[2 * fs + o] = make_float2(r_bv[0][i], r_bv[1][i]);
+            P[3 * fs + o] = *(const float2*)&Xe[y * NCR + 2 * j];
+            P[4 * fs + o] = make_float2(r_ae[0][i], r_ae[1][i]);
+        }
+    }
+}
+
+// ---------------------------------------------------------------- forcing
+
+__global__ void __launch_bounds__(THREADS) k_forcing_t(GroupView g, int s) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    const int Ny = g.ny, RP = g.rp, E = g.E, NM = g.nmodes, NKX = g.nkx;
+    const Tile T = tile_of(E, Ny);
+    const int q0 = blockIdx.x * T.QT, e0 = blockIdx.y * T.EBT;
+    const int NCR = 2 * T.NC;
+    float* D1 = (float*)sm;              // [Ny][RP]
+    float* PH = D1 + Ny * RP;            // phi    [Ny][NCR], column 2 (el QT + qq) + c
+    float* GG = PH + Ny * NCR;           // G      [Ny][NCR]
+    float* KV = GG + Ny * NCR;           // -k^2 Nv [Ny][NCR]
+    const size_t fs = (size_t)Ny * E * NM;
+    const float2* N3 = (const float2*)g.N3;
+    {
+        const float4* s1 = (const float4*)g.D1T;
+        for (int i = threadIdx.x; i < Ny * RP / 4; i += THREADS) ((float4*)D1)[i] = s1[i];
+        // P layout [y][e][q]: consecutive threads read consecutive q
+        const int per_y = T.EBT * T.QT;
+        for (int i = threadIdx.x; i < Ny * per_y; i += THREADS) {
+            const int k = i / per_y, r = i - k * per_y, el = r / T.QT, qq = r - el * T.QT;
+            const int q = q0 + qq, e = e0 + el;
+            float2 ph = make_float2(0.f, 0.f), gg = ph, kv = ph;
+            if (q < NM && e < E) {
+                const size_t o = ((size_t)k * E + e) * NM + q;
+                const float2 nu = N3[o], nv = N3[fs + o], nw = N3[2 * fs + o];
+                const int mi = q / NKX, n = q - mi * NKX;
+                const float kx = g.kxtf[n], kz = g.kztf[mi];
+                const float k2 = (float)g.k2t[q];
+                const float ax = kx * nu.x + kz * nw.x, ay = kx * nu.y + kz * nw.y;   // i kx Nu + i kz Nw
+                ph = make_float2(-ay, ax);
+                const float bx = kz * nu.x - kx * nw.x, by = kz * nu.y - kx * nw.y;   // i kz Nu - i kx Nw
+                gg = make_float2(-by, bx);
+                kv = make_float2(-k2 * nv.x, -k2 * nv.y);
+            }
+            const int c = 2 * (el * T.QT + qq);
+            *(float2*)&PH[k * NCR + c] = ph;
+            *(float2*)&GG[k * NCR + c] = gg;
+            *(float2*)&KV[k * NCR + c] = kv;
+        }
+    }
+    __syncthreads();
+    const int RB = RP / 4;
+    const int q_mean = g.kz * NKX;
+    for (int m = threadIdx.x; m < RB * T.NC; m += THREADS) {
+        // consecutive threads: consecutive members (the H layout's fastest index)
+        const int el = m % T.EBT, r = m / T.EBT, qq = r % T.QT, rb = r / T.QT;
+        const int j = el * T.QT + qq;
+        const int r0 = 4 * rb;
+        float4 ax = make_float4(0, 0, 0, 0), ay = ax;
+#pragma unroll 4
+        for (int k = 0; k < Ny; ++k) {
+            const float4 d = *(const float4*)&D1[k * RP + r0];
+            const float2 p = *(const float2*)&PH[k * NCR + 2 * j];
+            ax.x += d.x * p.x; ax.y += d.y * p.x; ax.z += d.z * p.x; ax.w += d.w * p.x;
+            ay.x += d.x * p.y; ay.y += d.y * p.y; ay.z += d.z * p.y; ay.w += d.w * p.y;
+        }
+        const int q = q0 + qq, e = e0 + el;
+        if (q >= NM || e >= E) continue;
+        const float rx[4] = {ax.x, ax.y, ax.z, ax.w}, ry[4] = {ay.x, ay.y, ay.z, ay.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int y = r0 + i;
+            if (y >= Ny) break;
+            const float2 kv = *(const float2*)&KV[y * NCR + 2 * j];
+            const float2 gg = *(const float2*)&GG[y * NCR + 2 * j];
+            double2 F = make_double2((double)kv.x - (double)rx[i], (double)kv.y - (double)ry[i]);
+            double2 G = make_double2((double)gg.x, (double)gg.y);
+            if (q == q_mean) { F = make_double2(0.0, 0.0); G = F; }
+            const size_t h = ((size_t)q * Ny + y) * E + e;
+            double2 Ft, Gt;
+            if (s == 0) {
+                Ft = F; Gt = G;
+                g.Av[h] = F; g.Ae[h] = G;
+            } else if (s == 1) {
+                const double2 a = g.Av[h], b = g.Ae[h];
+                Ft = make_double2(2.0 * F.x - a.x, 2.0 * F.y - a.y);
+                Gt = make_double2(2.0 * G.x - b.x, 2.0 * G.y - b.y);
+                g.Av[h] = make_double2((1.0 / 6.0) * a.x + (4.0 / 6.0) * F.x, (1.0 / 6.0) * a.y + (4.0 / 6.0) * F.y);
+                g.Ae[h] = make_double2((1.0 / 6.0) * b.x + (4.0 / 6.0) * G.x, (1.0 / 6.0) * b.y + (4.0 / 6.0) * G.y);
+            } else {
+                const double2 a = g.Av[h], b = g.Ae[h];
+                Ft = make_double2(a.x + (1.0 / 6.0) * F.x, a.y + (1.0 / 6.0) * F.y);
+                Gt = make_double2(b.x + (1.0 / 6.0) * G.x, b.y + (1.0 / 6.0) * G.y);
+            }
+            g.Fv[h] = Ft;
+            g.Fe[h] = Gt;
+        }
+    }
+}
+
+// ------------------------------------------------------------------- helm
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+// Bounded wait on phase 0 of an mbarrier; false if it did not complete.
+__device__ __forceinline__ bool mbar_wait0(unsigned bar) {
+    for (int it = 0; it < (1 << 22); ++it) {
+        unsigned done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done) : "r"(bar), "r"(0) : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__global__ void __launch_bounds__(THREADS) k_helm_t(GroupView g, int s) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    const int Ny = g.ny, RP = g.rp, E = g.E, NKX = g.nkx;
+    if ((int)blockIdx.x < E) { mean_cta(g, s, blockIdx.x, sm); return; }
+    const int b = blockIdx.x - E;
+    const int p = b % g.npairs, f = b / g.npairs;
+    const int n = p % NKX, am = p / NKX;
+    if (n == 0 && am == 0) return;
+    const int hi = (s == 0) ? 0 : 1;
+    const bool needM = (s != 2);
+    const int nq = am > 0 ? 2 : 1;
+    const int q1 = (g.kz + am) * NKX + n, q2 = (g.kz - am) * NKX + n;
+    const int NC = nq * 2 * E;                    // real columns
+    const size_t mat = (size_t)Ny * RP;           // floats per transposed operator
+    float* MT = (float*)sm;                       // [Ny][RP]  (M - I)^T
+    float* PT = MT + mat;                         // [Ny][RP]  P^T
+    float* Xs = PT + mat;                         // [Ny][NC]
+    float* Fs = Xs + (size_t)Ny * NC;             // [Ny][NC]
+    unsigned long long* bar = (unsigned long long*)(Fs + (size_t)Ny * NC + 2);
+    const float* src = g.opsfT[hi] + ((size_t)p * 4 + 2 * f) * mat;   // M^T then P^T, contiguous
+    const unsigned bar_a = smem_u32(bar);
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_a) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        // TMA bulk copy of the operators of this pair and field
+        const unsigned bytes = (unsigned)((needM ? 2 : 1) * mat * sizeof(float));
+        const float* from = needM ? src : src + mat;
+        float* to = needM ? MT : PT;
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_a), "r"(bytes) : "memory");
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                     ::"r"(smem_u32(to)), "l"(from), "r"(bytes), "r"(bar_a) : "memory");
+    }
+    const double2* X = f == 0 ? g.v_t : g.e_t;
+    const double2* F = f == 0 ? g.Fv : g.Fe;
+    const int per = Ny * 2 * E;
+    for (int i = threadIdx.x; i < nq * per; i += THREADS) {
+        const int which = i / per, r = i - which * per;
+        const int k = r / (2 * E), c = r - k * (2 * E);
+        const int q = which == 0 ? q1 : q2;
+        const size_t o = (size_t)q * per + r;
+        if (needM) Xs[k * NC + which * 2 * E + c] = (float)((const double*)X)[o];
+        Fs[k * NC + which * 2 * E + c] = (float)((const double*)F)[o];
+    }
+    __syncthreads();
+    if (!mbar_wait0(bar_a)) {
+        // the operator copy did not land: flag it, give the copy one more bounded
+        // wait so no write into this CTA's shared memory is left in flight, leave
+        if (threadIdx.x == 0) atomicExch(g.status, 1);
+        mbar_wait0(bar_a);
+        return;
+    }
+    double2* M1 = f == 0 ? g.mx1_v : g.mx1_e;
+    double2* O = (s == 2) ? (f == 0 ? g.v_t : g.e_t) : (f == 0 ? g.v_s : g.e_s);
+    const int RB = RP / 4, CB = NC / 2;
+    for (int m = threadIdx.x; m < RB * CB; m += THREADS) {
+        const int cb = m % CB, rb = m / CB;
+        const int r0 = 4 * rb, c0 = 2 * cb;
+        float4 pa = make_float4(0, 0, 0, 0), pb = pa, ma = pa, mb = pa;   // columns c0, c0+1
+#pragma unroll 4
+        for (int k = 0; k < Ny; ++k) {
+            const float4 pk = *(const float4*)&PT[k * RP + r0];
+            const float2 fk = *(const float2*)&Fs[k * NC + c0];
+            pa.x += pk.x * fk.x; pa.y += pk.y * fk.x; pa.z += pk.z * fk.x; pa.w += pk.w * fk.x;
+            pb.x += pk.x * fk.y; pb.y += pk.y * fk.y; pb.z += pk.z * fk.y; pb.w += pk.w * fk.y;
+            if (needM) {
+                const float4 mk = *(const float4*)&MT[k * RP + r0];
+                const float2 xk = *(const float2*)&Xs[k * NC + c0];
+                ma.x += mk.x * xk.x; ma.y += mk.y * xk.x; ma.z += mk.z * xk.x; ma.w += mk.w * xk.x;
+                mb.x += mk.x * xk.y; mb.y += mk.y * xk.y; mb.z += mk.z * xk.y; mb.w += mk.w * xk.y;
+            }
+        }
+        const int which = c0 / (2 * E), cl = c0 - which * 2 * E;
+        const int q = which == 0 ? q1 : q2;
+        const float rp[2][4] = {{pa.x, pa.y, pa.z, pa.w}, {pb.x, pb.y, pb.z, pb.w}};
+        const float rm[2][4] = {{ma.x, ma.y, ma.z, ma.w}, {mb.x, mb.y, mb.z, mb.w}};
+        const double* xg = (const double*)(X + (size_t)q * Ny * E);
+        double* m1 = (double*)(M1 + (size_t)q * Ny * E);
+        double* og = (double*)(O + (size_t)q * Ny * E);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int y = r0 + i;
+            if (y >= Ny) break;
+            const int o = y * 2 * E + cl;
+            double base0, base1;
+            if (needM) {
+                base0 = xg[o] + (double)rm[0][i];
+                base1 = xg[o + 1] + (double)rm[1][i];
+                if (s == 1) { m1[o] = base0; m1[o + 1] = base1; }
+            } else {
+                base0 = m1[o];
+                base1 = m1[o + 1];
+            }
+            og[o] = base0 + (double)rp[0][i];
+            og[o + 1] = base1 + (double)rp[1][i];
+        }
+    }
+}
+
+}  // namespace gt
+
+size_t helm_t_smem_bytes(const GroupView& g) {
+    const int nc = 2 * 2 * g.E;
+    size_t b = (2 * (size_t)g.ny * g.rp + 2 * (size_t)g.ny * nc + 2) * sizeof(float) + 16;
+    size_t m = mean_smem_bytes(g);
+    return b > m ? b : m;
+}
+
+size_t yderiv_t_smem_bytes(const GroupView& g) {
+    gt::Tile t = gt::tile_of(g.E, g.ny);
+    return (2 * (size_t)g.ny * g.rp + 2 * (size_t)g.ny * 2 * t.NC) * sizeof(float);
+}
+
+size_t forcing_t_smem_bytes(const GroupView& g) {
+    gt::Tile t = gt::tile_of(g.E, g.ny);
+    return ((size_t)g.ny * g.rp + 3 * (size_t)g.ny * 2 * t.NC) * sizeof(float);
+}
+
+void launch_yderiv_t(const GroupView& g, const double2* v, const double2* e, cudaStream_t st) {
+    gt::Tile t = gt::tile_of(g.E, g.ny);
+    dim3 grid((g.nmodes + t.QT - 1) / t.QT, (g.E + t.EBT - 1) / t.EBT);
+    gt::k_yderiv_t<<<grid, gt::THREADS, yderiv_t_smem_bytes(g), st>>>(g, v, e);
+}
+
+void launch_forcing_t(const GroupView& g, int s, cudaStream_t st) {
+    gt::Tile t = gt::tile_of(g.E, g.ny);
+    dim3 grid((g.nmodes + t.QT - 1) / t.QT, (g.E + t.EBT - 1) / t.EBT);
+    gt::k_forcing_t<<<grid, gt::THREADS, forcing_t_smem_bytes(g), st>>>(g, s);
+}
+
+void launch_helm_t(const GroupView& g, int s, cudaStream_t st) {
+    gt::k_helm_t<<<g.E + 2 * g.npairs, gt::THREADS, helm_t_smem_bytes(g), st>>>(g, s);
+}
+
+void set_attributes_gemm_t() {
+    cudaFuncSetAttribute(gt::k_yderiv_t, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaFuncSetAttribute(gt::k_forcing_t, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaFuncSetAttribute(gt::k_helm_t, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+}
+
+}  // namespace dnsk
