@@ -193,6 +193,29 @@ int dns_export_grid(const dns_handle* h, int group, double* y, double* D1, doubl
 int dns_export_operators(const dns_handle* h, int group, int h_index, int pair,
                          double* Mv, double* Pv, double* Me, double* Pe);
 
+/* Allocation-free statistics.  The paper has no counterpart: this entry point
+ * exists for callers that cannot allocate device memory at the moment they want
+ * statistics -- a host that has handed all device memory to its own pool, an
+ * embedding runtime that forbids cudaMalloc/cudaFree inside its step callback,
+ * or a monitoring hook that must not wait on the allocator's device-wide
+ * synchronisation.  It computes the same per-member statistics as dns_stats for
+ * the current state of `group` and allocates nothing: the per-plane partial
+ * sums go to a fixed array inside the library (2^20 doubles, 8 MiB, resident on
+ * every GPU that loads the library until the process exits), everything else
+ * uses the handle's bound workspace.
+ *   out_dev: DEVICE pointer, [members][8] doubles per member, in this order:
+ *            e_total, e_pert, tau_bottom, tau_top, bulk_flux, gamma, max_div,
+ *            nonfinite (1.0 or 0.0).  Caller-owned.
+ * Enqueued on the handle's stream; returns without synchronising.
+ * The first call on a device looks up the array's device address; make that
+ * first call before any stream capture.  Every call shares the one array, so
+ * calls that overlap on the GPU (other streams, other handles) race; each call
+ * writes every partial it reads, so nothing needs clearing between calls.
+ * Errors: DNS_ERR_INVALID (unbound workspace, NULL output, or a group with
+ * more than 2^20 / 6 member-planes -- members * (My - 2) > 174762),
+ * DNS_ERR_CUDA (address lookup or launch failed). */
+int dns_stats_noalloc(dns_handle* h, int group, double* out_dev);
+
 #ifdef __cplusplus
 }
 #endif

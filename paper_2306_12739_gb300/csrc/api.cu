@@ -190,6 +190,9 @@ void enqueue_step(dns_handle* h, Timer* tm = nullptr) {
 }  // namespace
 
 namespace dnsk {
+cudaError_t noalloc_scratch(double** out);
+size_t noalloc_max_partials();
+void launch_stats_noalloc(const GroupView& g, double* scratch, double* out, cudaStream_t st);
 void set_attributes_spectral();
 void set_attributes_plane();
 }
@@ -562,6 +565,24 @@ int dns_stats(dns_handle* h, int group, dns_stats_t* per_member, dns_stats_t* en
     }
     if (ensemble_mean) *ensemble_mean = mean;
     return any_nf ? DNS_ERR_NONFINITE : DNS_OK;
+}
+
+int dns_stats_noalloc(dns_handle* h, int group, double* out_dev) {
+    if (!h) return DNS_ERR_INVALID;
+    if (!h->bound) return fail(h, DNS_ERR_INVALID, "workspace not bound");
+    if (group < 0 || group >= (int)h->groups.size()) return fail(h, DNS_ERR_INVALID, "bad group");
+    if (!out_dev) return fail(h, DNS_ERR_INVALID, "out_dev is NULL");
+    const GroupView& v = h->groups[group].v;
+    const size_t need = (size_t)v.E * v.ny * 6;
+    if (need > dnsk::noalloc_max_partials())
+        return fail(h, DNS_ERR_INVALID,
+                    "dns_stats_noalloc: group %d needs %zu partial sums (members x (My-2) x 6), the fixed array holds %zu",
+                    group, need, dnsk::noalloc_max_partials());
+    double* scratch = nullptr;
+    int rc = check(h, dnsk::noalloc_scratch(&scratch), "dns_stats_noalloc: scratch address");
+    if (rc) return rc;
+    dnsk::launch_stats_noalloc(v, scratch, out_dev, h->stream);
+    return check(h, cudaGetLastError(), "dns_stats_noalloc launch");
 }
 
 int dns_destroy(dns_handle* h) {
