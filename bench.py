@@ -154,6 +154,26 @@ def kernel_work(cls, g, precision):
     return "alu", E * 4.0 * (g["my"]) ** 2, "flop"
 
 
+def profiled_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu record, or None
+    when the kernel's sources changed since the counters were taken."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic_poiseuille64x65x64_E8_mixed.json")
+    try:
+        rec = json.load(open(path))["kernels"][kernel]
+    except (OSError, KeyError, ValueError):
+        return None
+    h = hashlib.sha256()
+    for f in rec["source_files"]:
+        try:
+            h.update(open(os.path.join(ROOT, f), "rb").read())
+        except OSError:
+            return None
+    if h.hexdigest()[:16] != rec["source_sha256_16"]:
+        return None
+    return rec["dram_bytes_per_launch"]
+
+
 def alu_peak(precision_of_kernel, sm_mhz):
     if precision_of_kernel == "f64":
         return FP64_NOMINAL_TFLOPS
@@ -161,9 +181,8 @@ def alu_peak(precision_of_kernel, sm_mhz):
 
 
 def kernel_precision(cls, precision):
-    if precision == "fp64":
-        return "f64"
-    return {"plane": "f32"}.get(cls, "f64")
+    # the mixed path runs every contraction and transform in FP32 (FP64 sums only)
+    return "f64" if precision == "fp64" else "f32"
 
 
 # ------------------------------------------------------------ cpu oracle
@@ -293,8 +312,10 @@ def gpu_arm(args, rank, world, dist):
     sm_mhz = clocks["sm_mhz"] or 2070.0
     peak = alu_peak(kprec, sm_mhz)
     achieved = work / (avg_ms / 1e3) / 1e12
+    traffic = profiled_traffic(dom) if precision == "mixed" else None
     roofline = {"kernel": dom, "bound": bound, "precision": kprec, "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
+                "traffic_unit": "DRAM bytes per launch (ncu, profiles/)",
                 "peak_source": ("nominal GB300 FP64" if kprec == "f64" else
                                 "152 SM x 128 FP32 lanes x 2 x median sampled SM clock %.0f MHz" % sm_mhz),
                 "kernel_ms_per_launch": avg_ms,

@@ -52,7 +52,7 @@ typedef enum {
     DNS_ERR_INVALID = -1,     /* bad argument, bad configuration, unbound workspace */
     DNS_ERR_CUDA = -2,        /* a CUDA runtime call failed (message in dns_last_error) */
     DNS_ERR_NOMEM = -3,       /* workspace too small, host allocation failed */
-    DNS_ERR_TIMEOUT = -4,     /* reserved: a bounded device wait gave up */
+    DNS_ERR_TIMEOUT = -4,     /* a bounded device wait gave up (reported by the next synchronising call) */
     DNS_ERR_NONFINITE = -5,   /* returned by dns_stats when any member holds NaN/Inf */
     DNS_ERR_UNSUPPORTED = -6  /* valid request the library does not implement */
 } dns_status;
@@ -180,6 +180,12 @@ enum {
  * the summed device time in ms (ms[DNS_K_NCLASS]) and the number of launches
  * (launches[DNS_K_NCLASS]) of each kernel class over the nsteps steps. */
 int dns_step_timed(dns_handle* h, int nsteps, double* ms, int* launches);
+
+/* Self-test of the device-side timeout path: launches one kernel that waits,
+ * with its usual iteration limit, on a barrier nobody arrives at; the wait
+ * gives up, latches the device status word, and the call returns
+ * DNS_ERR_TIMEOUT (the context stays usable).  Synchronises. */
+int dns_selftest_timeout(dns_handle* h);
 
 /* Host copies of what dns_create built, for inspection and tests; no device
  * access, valid before a workspace is bound.

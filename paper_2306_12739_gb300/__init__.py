@@ -34,7 +34,7 @@ DNS_PREC_FP64, DNS_PREC_MIXED = 0, 1
 EXPORTED = ["dns_create", "dns_workspace_size", "dns_bind_workspace", "dns_state_shape",
             "dns_set_state", "dns_get_state", "dns_step", "dns_stats", "dns_destroy",
             "dns_last_error", "dns_last_launch_count", "dns_export_grid", "dns_export_operators",
-            "dns_step_timed", "dns_stats_noalloc"]
+            "dns_step_timed", "dns_stats_noalloc", "dns_selftest_timeout"]
 KERNEL_CLASSES = ["mean_deriv", "yderiv", "plane", "forcing", "helm", "mean"]
 
 
@@ -75,6 +75,7 @@ _lib.dns_last_error.restype = ctypes.c_char_p
 _lib.dns_last_launch_count.argtypes = [_H]
 _lib.dns_step_timed.argtypes = [_H, ctypes.c_int, _dp, ctypes.POINTER(ctypes.c_int)]
 _lib.dns_stats_noalloc.argtypes = [_H, ctypes.c_int, _vp]
+_lib.dns_selftest_timeout.argtypes = [_H]
 _lib.dns_export_grid.argtypes = [_H, ctypes.c_int, _dp, _dp, _dp, _dp, _dp]
 _lib.dns_export_operators.argtypes = [_H, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp]
 
@@ -155,6 +156,12 @@ def dns_stats_noalloc(h, group, out_dev_ptr):
     """Allocation-free statistics into a caller-owned DEVICE buffer
     [members][8] (see include/dns.h); asynchronous on the handle's stream."""
     return _ck(h, _lib.dns_stats_noalloc(h, group, _vp(out_dev_ptr)))
+
+
+def dns_selftest_timeout(h):
+    """Runs a bounded device wait that must give up; returns the status code
+    (DNS_ERR_TIMEOUT expected) without raising."""
+    return _lib.dns_selftest_timeout(h)
 
 
 def dns_destroy(h):

@@ -139,6 +139,21 @@ int check(dns_handle* h, cudaError_t e, const char* what) {
     return DNS_OK;
 }
 
+// Read and clear the device status words after a synchronising call: a kernel
+// whose bounded wait gave up latches 1 there.
+int device_status(dns_handle* h) {
+    for (auto& G : h->groups) {
+        int st = 0;
+        int rc = check(h, cudaMemcpy(&st, G.v.status, sizeof(int), cudaMemcpyDeviceToHost), "read status");
+        if (rc) return rc;
+        if (st != 0) {
+            cudaMemset(G.v.status, 0, sizeof(int));
+            return fail(h, DNS_ERR_TIMEOUT, "a bounded device wait gave up (status %d)", st);
+        }
+    }
+    return DNS_OK;
+}
+
 // Optional per-launch event recording (dns_step_timed).
 struct Timer {
     std::vector<cudaEvent_t> ev;
@@ -190,6 +205,7 @@ void enqueue_step(dns_handle* h, Timer* tm = nullptr) {
 }  // namespace
 
 namespace dnsk {
+void launch_wait_selftest(int* status, cudaStream_t st);
 cudaError_t noalloc_scratch(double** out);
 size_t noalloc_max_partials();
 void launch_stats_noalloc(const GroupView& g, double* scratch, double* out, cudaStream_t st);
@@ -470,7 +486,8 @@ int dns_get_state(const dns_handle* hc, int group, int member0, int count, doubl
     if (W00 && (rc = check(h, cudaMemcpyAsync(W00, v.W_t + (size_t)member0 * v.my, sizeof(double) * count * v.my, k, st),
                            "get W")))
         return rc;
-    return check(h, cudaStreamSynchronize(st), "get state");
+    if ((rc = check(h, cudaStreamSynchronize(st), "get state"))) return rc;
+    return device_status(h);
 }
 
 int dns_step(dns_handle* h, int nsteps) {
@@ -546,6 +563,7 @@ int dns_stats(dns_handle* h, int group, dns_stats_t* per_member, dns_stats_t* en
                     "profile copy")))
         return rc;
     if ((rc = check(h, cudaStreamSynchronize(st), "stats"))) return rc;
+    if ((rc = device_status(h))) return rc;
     bool any_nf = false;
     dns_stats_t mean;
     memset(&mean, 0, sizeof mean);
@@ -583,6 +601,16 @@ int dns_stats_noalloc(dns_handle* h, int group, double* out_dev) {
     if (rc) return rc;
     dnsk::launch_stats_noalloc(v, scratch, out_dev, h->stream);
     return check(h, cudaGetLastError(), "dns_stats_noalloc launch");
+}
+
+int dns_selftest_timeout(dns_handle* h) {
+    if (!h) return DNS_ERR_INVALID;
+    if (!h->bound) return fail(h, DNS_ERR_INVALID, "workspace not bound");
+    dnsk::launch_wait_selftest(h->groups[0].v.status, h->stream);
+    int rc = check(h, cudaGetLastError(), "selftest launch");
+    if (rc) return rc;
+    if ((rc = check(h, cudaStreamSynchronize(h->stream), "selftest"))) return rc;
+    return device_status(h);
 }
 
 int dns_destroy(dns_handle* h) {

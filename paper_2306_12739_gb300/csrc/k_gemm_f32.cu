@@ -322,7 +322,22 @@ __global__ void __launch_bounds__(THREADS) k_helm_t(GroupView g, int s) {
     }
 }
 
+// Self-test of the bounded-wait path: an mbarrier that expects one arrival that
+// never comes.  The wait gives up after its iteration limit and latches status.
+__global__ void k_wait_selftest(int* status) {
+    __shared__ unsigned long long bar;
+    const unsigned b = smem_u32(&bar);
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (!mbar_wait0(b) && threadIdx.x == 0) atomicExch(status, 2);
+}
+
 }  // namespace gt
+
+void launch_wait_selftest(int* status, cudaStream_t st) { gt::k_wait_selftest<<<1, 32, 0, st>>>(status); }
 
 size_t helm_t_smem_bytes(const GroupView& g) {
     const int nc = 2 * 2 * g.E;

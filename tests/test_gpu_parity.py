@@ -190,3 +190,18 @@ def test_mixed_matches_fp64_for_every_plane_shape(mx, mz):
     err = mixed_errors(b, a)
     assert np.all(err[:, :3] < 1e-6), err
     assert np.all(err[:, 3] < 1e-5), err
+
+
+def test_bounded_device_wait_reports_timeout_and_context_survives():
+    g = group("couette", 16, 33, 16, 1.75 * np.pi, 1.2 * np.pi, 400.0, 0.01, 1)
+    st = _state(g, 1000, 1e-2, n_max=2, m_max=2)
+    ens = dns.Ensemble([g], precision="mixed")
+    ens.set_state(0, st["v"], st["eta"], st["U"], st["W"])
+    assert dns.dns_selftest_timeout(ens.h) == dns.DNS_ERR_TIMEOUT
+    assert "gave up" in dns.dns_last_error(ens.h)
+    ens.step(2)                      # the context is still usable
+    got = ens.get_state(0)
+    ens.close()
+    ref = _run(g, st, 2, "mixed")
+    for a, b in zip(got, ref):
+        assert np.array_equal(a, b)

@@ -1,0 +1,83 @@
+"""The N > 1 path of bench.py on CPU: two gloo ranks, each advancing its own
+replica ensemble (members are independent, so nothing but a barrier and the
+max of the timed durations crosses ranks)."""
+import os
+import queue
+import socket
+import time
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+G = dict(flow="couette", mx=16, my=17, mz=16, lx=1.75 * np.pi, lz=1.2 * np.pi, re=400.0, dt=0.01, members=2)
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _replica(rank):
+    import bench
+    import oracle
+    st = bench.initial_state(G, rank)
+    ch = oracle.Channel(G["mx"], G["my"], G["mz"], G["lx"], G["lz"], G["re"], G["dt"], G["flow"])
+    x = ch.step(tuple(st[k] for k in ("v", "eta", "U", "W")), 2)
+    return ch.stats(x)["e_total"]
+
+
+def _worker(rank, world, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world), LOCAL_RANK=str(rank))
+    try:
+        import bench
+        r, w, dist = bench.dist_setup()
+        assert (r, w) == (rank, world) and dist is not None
+        t0 = time.perf_counter()
+        energy = _replica(rank)
+        dt = time.perf_counter() - t0 + 0.05 * rank      # ranks finish at different times
+        tmax = bench.reduce_max(dt, dist)
+        value = bench.aggregate(G["members"] * 2, tmax, w)
+        gathered = [None] * w
+        dist.all_gather_object(gathered, energy.tolist())
+        dist.barrier()
+        dist.destroy_process_group()
+        q.put((rank, dt, tmax, value, gathered))
+    except Exception as exc:  # pragma: no cover - reported to the parent
+        q.put((rank, "error", repr(exc)))
+
+
+def test_two_gloo_ranks_run_replicas_and_report_whole_job_throughput():
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    results = {}
+    try:
+        for _ in range(2):
+            item = q.get(timeout=240)
+            assert item[1] != "error", item
+            results[item[0]] = item
+    except queue.Empty:  # pragma: no cover
+        pytest.fail("a rank did not report")
+    finally:
+        for p in procs:
+            p.join(timeout=60)
+            if p.is_alive():
+                p.terminate()
+    dts = [results[r][1] for r in range(2)]
+    for r in range(2):
+        _, dt, tmax, value, gathered = results[r]
+        assert tmax == pytest.approx(max(dts))                      # max over ranks
+        assert value == pytest.approx(G["members"] * 2 * 2 / max(dts))   # all ranks' member-steps / slowest
+        # each rank advanced a distinct replica, identical to running it alone
+        assert not np.allclose(gathered[0], gathered[1])
+    alone = [_replica(r) for r in range(2)]
+    for r in range(2):
+        assert np.allclose(results[0][4][r], alone[r], rtol=1e-13, atol=0)
