@@ -85,6 +85,10 @@ typedef struct {
     int persistent;                /* reserved, must be 0 */
     unsigned long long barrier_timeout_ns;  /* reserved, 0 */
     const char* autotune_cache;    /* reserved, may be NULL */
+    int ygemm;                     /* mixed path y-derivatives: 0 default (register-tiled FP32),
+                                      1 register-tiled FP32, 2 tcgen05 tensor cores with
+                                      split-BF16 operands (groups with My <= 66 and <= 64
+                                      members; others fall back to 1) */
 } dns_config;
 
 /* One-point statistics of one member (paper Sec. 4), computed from the current

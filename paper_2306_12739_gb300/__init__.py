@@ -48,7 +48,8 @@ class dns_group_desc(ctypes.Structure):
 class dns_config(ctypes.Structure):
     _fields_ = [("n_groups", ctypes.c_int), ("groups", ctypes.POINTER(dns_group_desc)),
                 ("precision", ctypes.c_int), ("use_graph", ctypes.c_int), ("persistent", ctypes.c_int),
-                ("barrier_timeout_ns", ctypes.c_ulonglong), ("autotune_cache", ctypes.c_char_p)]
+                ("barrier_timeout_ns", ctypes.c_ulonglong), ("autotune_cache", ctypes.c_char_p),
+                ("ygemm", ctypes.c_int)]
 
 
 class dns_stats_t(ctypes.Structure):
@@ -196,14 +197,17 @@ _FLOWS = {"couette": DNS_COUETTE, "poiseuille": DNS_POISEUILLE}
 _PRECS = {"fp64": DNS_PREC_FP64, "mixed": DNS_PREC_MIXED}
 
 
-def make_config(groups, precision="fp64", use_graph=False):
+_YGEMM = {"default": 0, "simt": 1, "tc": 2}
+
+
+def make_config(groups, precision="fp64", use_graph=False, ygemm="default"):
     """groups: list of dicts with flow, mx, my, mz, lx, lz, re, dt, members,
     optional u_wall (1.0) and bulk_flux (4/3)."""
     arr = (dns_group_desc * len(groups))()
     for i, g in enumerate(groups):
         arr[i] = dns_group_desc(_FLOWS[g["flow"]], g["mx"], g["my"], g["mz"], g["lx"], g["lz"], g["re"],
                                 g["dt"], g.get("u_wall", 1.0), g.get("bulk_flux", 4.0 / 3.0), g["members"])
-    cfg = dns_config(len(groups), arr, _PRECS[precision], 1 if use_graph else 0, 0, 0, None)
+    cfg = dns_config(len(groups), arr, _PRECS[precision], 1 if use_graph else 0, 0, 0, None, _YGEMM[ygemm])
     cfg._keep = arr
     return cfg
 
@@ -211,14 +215,14 @@ def make_config(groups, precision="fp64", use_graph=False):
 class Ensemble:
     """Owns a handle, its torch workspace and the stream it runs on."""
 
-    def __init__(self, groups, precision="fp64", use_graph=False, device="cuda:0", stream=None):
+    def __init__(self, groups, precision="fp64", use_graph=False, device="cuda:0", stream=None, ygemm="default"):
         import torch
         self.torch = torch
         self.device = torch.device(device)
         self.groups = [dict(g) for g in groups]
         # a stream of its own: graph capture is not allowed on the legacy default stream
         self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
-        self.cfg = make_config(groups, precision, use_graph)
+        self.cfg = make_config(groups, precision, use_graph, ygemm)
         self.h = dns_create(self.cfg, self.stream.cuda_stream)
         nbytes = dns_workspace_size(self.h)
         self.ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)

@@ -24,6 +24,7 @@ struct HostGroup {
     dnsb::CnOps ops[2];
     std::vector<double> kxt, kzt, k2t, k2inv, twx, twz, opsdev[2], mopsdev[2], D1i, D2i;
     std::vector<float> kxtf, kztf, k2invf, twxf, twzf, opsf[2], opsfT[2], D1if, D2if, D1T, D2T;
+    std::vector<uint16_t> Atc;
     // byte offsets inside the workspace
     struct Off { size_t off, bytes; };
     std::vector<std::pair<void**, Off>> slots;
@@ -94,6 +95,7 @@ size_t layout_group(dns_handle* h, HostGroup& G, size_t cur) {
     add((void**)&v.D1T, sizeof(float) * (size_t)v.ny * v.rp);
     add((void**)&v.D2T, sizeof(float) * (size_t)v.ny * v.rp);
     add((void**)&v.status, 256);
+    if (v.ygemm == 2) add((void**)&v.Atc, 3 * 128 * (size_t)v.kp * sizeof(uint16_t));
     add((void**)&v.ccw, sizeof(double) * v.my);
     add((void**)&v.kxt, sizeof(double) * v.nkx);
     add((void**)&v.kzt, sizeof(double) * v.nkz);
@@ -179,7 +181,8 @@ void enqueue_step(dns_handle* h, Timer* tm = nullptr) {
             const double* cW = s == 0 ? g.W_t : g.W_s;
             mark(-1);
             if (precision_mixed(h)) {
-                dnsk::launch_yderiv_t(g, cv, ce, st);
+                if (g.ygemm == 2) dnsk::launch_yderiv_tc(g, cv, ce, st);
+                else dnsk::launch_yderiv_t(g, cv, ce, st);
                 mark(DNS_K_YDERIV);
                 dnsk::launch_plane_f32(g, cU, cW, st);
                 mark(DNS_K_PLANE);
@@ -205,6 +208,7 @@ void enqueue_step(dns_handle* h, Timer* tm = nullptr) {
 }  // namespace
 
 namespace dnsk {
+std::vector<uint16_t> yderiv_tc_a_image(const std::vector<double>& D1i, const std::vector<double>& D2i, int ny, int kp);
 void launch_wait_selftest(int* status, cudaStream_t st);
 cudaError_t noalloc_scratch(double** out);
 size_t noalloc_max_partials();
@@ -253,6 +257,9 @@ int dns_create(const dns_config* cfg, void* cuda_stream, dns_handle** out) {
         v.E = d.members;
         v.npairs = v.nkx * (v.kz + 1);
         v.rp = (v.ny + 3) / 4 * 4;
+        v.kp = (v.ny + 15) / 16 * 16;
+        v.ygemm = 1;
+        if (precision_mixed(h) && cfg->ygemm == 2 && dnsk::yderiv_tc_supported(v)) v.ygemm = 2;
         v.flow = d.flow == DNS_POISEUILLE ? 1 : 0;
         v.re = d.re; v.dt = d.dt; v.u_wall = d.u_wall; v.bulk_flux = d.bulk_flux;
         if (!make_plan(d.mx, &v.px) || !make_plan(d.mz, &v.pz))
@@ -346,6 +353,7 @@ int dns_create(const dns_config* cfg, void* cuda_stream, dns_handle** out) {
                 G.D1T[(size_t)k * v.rp + r] = (float)G.D1i[(size_t)r * v.ny + k];
                 G.D2T[(size_t)k * v.rp + r] = (float)G.D2i[(size_t)r * v.ny + k];
             }
+        if (v.ygemm == 2) G.Atc = dnsk::yderiv_tc_a_image(G.D1i, G.D2i, v.ny, v.kp);
         G.twx = dnsb::twiddles(d.mx);
         G.twz = dnsb::twiddles(d.mz);
         G.twxf.assign(G.twx.begin(), G.twx.end());
@@ -377,6 +385,11 @@ int dns_bind_workspace(dns_handle* h, void* dev_ptr, size_t bytes) {
     dnsk::set_attributes_plane();
     dnsk::set_attributes_plane_f32();
     dnsk::set_attributes_gemm_t();
+    dnsk::set_attributes_yderiv_tc();
+    {
+        int rc0 = check(h, cudaGetLastError(), "kernel attributes");
+        if (rc0) return rc0;
+    }
     cudaStream_t st = h->stream;
     int rc = check(h, cudaMemsetAsync(dev_ptr, 0, h->need, st), "clear workspace");
     if (rc) return rc;
@@ -410,6 +423,7 @@ int dns_bind_workspace(dns_handle* h, void* dev_ptr, size_t bytes) {
             {v.opsfT[0], G.opsfT[0].data(), G.opsfT[0].size() * 4},
             {v.opsfT[1], G.opsfT[1].data(), G.opsfT[1].size() * 4},
             {v.D1T, G.D1T.data(), G.D1T.size() * 4},
+            {v.Atc, G.Atc.data(), G.Atc.size() * 2},
             {v.D2T, G.D2T.data(), G.D2T.size() * 4},
             {v.mops[0], G.mopsdev[0].data(), G.mopsdev[0].size() * 8},
             {v.mops[1], G.mopsdev[1].data(), G.mopsdev[1].size() * 8},

@@ -158,4 +158,16 @@ __device__ __forceinline__ void mean_dy_row(const double* __restrict__ D1, const
     if (threadIdx.x == 0) { out[0] = a; out[1] = b; }
 }
 
+// Allow a kernel the largest dynamic shared memory the SM offers next to its
+// static shared memory (227 KB per block on sm_103).
+template <typename F>
+inline cudaError_t allow_max_dynamic_smem(F* func) {
+    cudaFuncAttributes a;
+    cudaError_t e = cudaFuncGetAttributes(&a, (const void*)func);
+    if (e != cudaSuccess) return e;
+    const int total = 227 * 1024;
+    return cudaFuncSetAttribute((const void*)func, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                total - (int)a.sharedSizeBytes);
+}
+
 }  // namespace dnsk

@@ -18,6 +18,9 @@ namespace dnsk {
 struct GroupView {
     int mx, my, mz, kx, kz, nkx, nkz, nmodes, ny, E, npairs;
     int rp;               // Ny rounded up to a multiple of 4 (row padding of transposed operators)
+    int kp;               // Ny rounded up to a multiple of 16 (K of the tensor-core y-contraction)
+    int ygemm;            // mixed path y-derivatives: 1 register-tiled FP32, 2 tcgen05 split-BF16
+    const void* Atc;      // tensor-core A image: [D1_int; D2_int] in 3 BF16 pieces
     int* status;          // device error word (1: a bounded wait gave up)
     int flow;             // 0 Couette, 1 Poiseuille
     double re, dt, u_wall, bulk_flux;
@@ -83,6 +86,10 @@ void launch_yderiv_t(const GroupView& g, const double2* v, const double2* e, cud
 void launch_forcing_t(const GroupView& g, int s, cudaStream_t st);
 void launch_helm_t(const GroupView& g, int s, cudaStream_t st);
 void set_attributes_gemm_t();
+bool yderiv_tc_supported(const GroupView& g);
+size_t yderiv_tc_smem_bytes(const GroupView& g);
+void launch_yderiv_tc(const GroupView& g, const double2* v, const double2* e, cudaStream_t st);
+void set_attributes_yderiv_tc();
 void launch_stats(const GroupView& g, cudaStream_t st);
 void launch_pack(const GroupView& g, int member0, int count, cudaStream_t st);
 void launch_unpack(const GroupView& g, int member0, int count, cudaStream_t st);

@@ -373,9 +373,9 @@ void launch_helm_t(const GroupView& g, int s, cudaStream_t st) {
 }
 
 void set_attributes_gemm_t() {
-    cudaFuncSetAttribute(gt::k_yderiv_t, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    cudaFuncSetAttribute(gt::k_forcing_t, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    cudaFuncSetAttribute(gt::k_helm_t, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    allow_max_dynamic_smem(gt::k_yderiv_t);
+    allow_max_dynamic_smem(gt::k_forcing_t);
+    allow_max_dynamic_smem(gt::k_helm_t);
 }
 
 }  // namespace dnsk

@@ -253,8 +253,8 @@ template void launch_plane_state<double>(const GroupView&, const double*, const 
 template void launch_plane_state<float>(const GroupView&, const double*, const double*, cudaStream_t);
 
 void set_attributes_plane() {
-    cudaFuncSetAttribute(k_plane<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    cudaFuncSetAttribute(k_plane<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    allow_max_dynamic_smem(k_plane<double>);
+    allow_max_dynamic_smem(k_plane<float>);
 }
 
 }  // namespace dnsk

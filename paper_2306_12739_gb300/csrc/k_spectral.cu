@@ -493,12 +493,12 @@ void launch_unpack(const GroupView& g, int member0, int count, cudaStream_t st) 
 }
 
 void set_attributes_spectral() {
-    cudaFuncSetAttribute(k_yderiv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(k_yderiv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(k_forcing<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(k_forcing<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(k_helm, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-    cudaFuncSetAttribute(k_helm_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    allow_max_dynamic_smem(k_yderiv<double>);
+    allow_max_dynamic_smem(k_yderiv<float>);
+    allow_max_dynamic_smem(k_forcing<double>);
+    allow_max_dynamic_smem(k_forcing<float>);
+    allow_max_dynamic_smem(k_helm);
+    allow_max_dynamic_smem(k_helm_mixed);
 }
 
 }  // namespace dnsk

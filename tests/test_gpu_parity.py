@@ -37,8 +37,8 @@ def _oracle(g):
     return oracle.Channel(g["mx"], g["my"], g["mz"], g["lx"], g["lz"], g["re"], g["dt"], g["flow"])
 
 
-def _run(g, st, nsteps, precision="fp64", use_graph=False):
-    ens = dns.Ensemble([g], precision=precision, use_graph=use_graph)
+def _run(g, st, nsteps, precision="fp64", use_graph=False, ygemm="default"):
+    ens = dns.Ensemble([g], precision=precision, use_graph=use_graph, ygemm=ygemm)
     ens.set_state(0, st["v"], st["eta"], st["U"], st["W"])
     ens.step(nsteps)
     out = ens.get_state(0)
@@ -90,11 +90,12 @@ def mixed_errors(mixed, ref):
     return np.array(out)
 
 
-def test_mixed_matches_fp64_over_50_steps():
+@pytest.mark.parametrize("ygemm", ["simt", "tc"])
+def test_mixed_matches_fp64_over_50_steps(ygemm):
     g = group("couette", 32, 49, 32, 1.75 * np.pi, 1.2 * np.pi, 500.0, 0.01, 8)
     st = _state(g, 3000, 5e-2, n_max=4, m_max=4)
     a = _run(g, st, 50, "fp64")
-    b = _run(g, st, 50, "mixed")
+    b = _run(g, st, 50, "mixed", ygemm=ygemm)
     err = mixed_errors(b, a)
     assert np.all(err[:, :3] < 1e-6), err
     assert np.all(err[:, 3] < 1e-5), err
@@ -205,3 +206,16 @@ def test_bounded_device_wait_reports_timeout_and_context_survives():
     ref = _run(g, st, 2, "mixed")
     for a, b in zip(got, ref):
         assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("mx,my,mz,E", [(64, 65, 64, 8), (32, 33, 32, 5), (16, 21, 48, 64), (32, 49, 16, 1)])
+def test_tensor_core_y_derivatives_match_fp64(mx, my, mz, E):
+    """tcgen05 split-BF16 y-contraction and the register-tiled FP32 one, each
+    against the FP64 step: both inside the 1e-6 budget (ragged grids, 1 to 64
+    members)."""
+    g = group("poiseuille", mx, my, mz, 2 * np.pi, np.pi, 1650.0, 0.005, E)
+    st = _state(g, 71, 5e-2)
+    ref = _run(g, st, 5, "fp64")
+    for ygemm in ("simt", "tc"):
+        err = mixed_errors(_run(g, st, 5, "mixed", ygemm=ygemm), ref)
+        assert np.all(err[:, :3] < 1e-6), (ygemm, err)
