@@ -266,7 +266,7 @@ def gpu_arm(args, rank, world, dist):
     precision = args.precision
 
     def timed_run(prec, nsteps, nwarm, flush):
-        ens = dns.Ensemble([g], precision=prec, use_graph=True, device=dev)
+        ens = dns.Ensemble([g], precision=prec, use_graph=True, device=dev, ygemm=args.ygemm)
         ens.set_state(0, st["v"], st["eta"], st["U"], st["W"])
         stream = ens.stream
         ens.step(nwarm)
@@ -295,6 +295,7 @@ def gpu_arm(args, rank, world, dist):
 
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
     ens, total_ms, launches, clocks = timed_run(precision, args.steps, args.warmup, flush)
+    ygemm_used = dns.dns_kernel_choice(ens.h, 0)
     total_ms = reduce_max(total_ms, dist, dev)
     ms_step = total_ms / args.steps
     value = aggregate(g["members"] * args.steps, total_ms / 1e3, world)
@@ -350,6 +351,7 @@ def gpu_arm(args, rank, world, dist):
         "vs_baseline": None, "dtype": "f32+f64" if precision == "mixed" else "f64",
         "data": "synthetic (seeded, dns_synth)",
         "config": {"workload": WORKLOAD_NAME, "precision": precision, "graph": True,
+                   "ygemm": "%s (%s)" % (ygemm_used, args.ygemm),
                    "l2": "flushed (256 MiB write) before every timed step", "parallelism": "replicas x%d" % world},
         "grid_pts_steps_per_s": value * pts,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
@@ -388,6 +390,8 @@ def main():
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparator run")
+    ap.add_argument("--ygemm", choices=["default", "simt", "tc"], default="default",
+                    help="y-contraction variant of the mixed path")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

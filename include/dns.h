@@ -84,11 +84,13 @@ typedef struct {
     int use_graph;                 /* 1: capture one full step as a CUDA graph and replay it */
     int persistent;                /* reserved, must be 0 */
     unsigned long long barrier_timeout_ns;  /* reserved, 0 */
-    const char* autotune_cache;    /* reserved, may be NULL */
-    int ygemm;                     /* mixed path y-derivatives: 0 default (register-tiled FP32),
-                                      1 register-tiled FP32, 2 tcgen05 tensor cores with
+    const char* autotune_cache;    /* optional text file: autotuner decisions are read from it
+                                      and appended to it ("ygemm Mx My Mz E choice"); NULL = none */
+    int ygemm;                     /* mixed path y-derivatives: 0 autotuned at dns_bind_workspace
+                                      (both variants timed on the bound workspace, the faster
+                                      kept), 1 register-tiled FP32, 2 tcgen05 tensor cores with
                                       split-BF16 operands (groups with My <= 66 and <= 64
-                                      members; others fall back to 1) */
+                                      members; others always use 1) */
 } dns_config;
 
 /* One-point statistics of one member (paper Sec. 4), computed from the current
@@ -164,6 +166,10 @@ int dns_destroy(dns_handle* h);
 /* Reason of the last failure on this handle ("" if none).  Valid until the
  * next call on the handle. */
 const char* dns_last_error(const dns_handle* h);
+
+/* Variant the y-contraction of `group` uses (1 register-tiled FP32, 2 tcgen05),
+ * after the autotuner ran (i.e. after dns_bind_workspace). */
+int dns_kernel_choice(const dns_handle* h, int group, int* ygemm);
 
 /* Number of kernel launches enqueued by the last dns_step call (all steps). */
 int dns_last_launch_count(const dns_handle* h);

@@ -34,7 +34,7 @@ DNS_PREC_FP64, DNS_PREC_MIXED = 0, 1
 EXPORTED = ["dns_create", "dns_workspace_size", "dns_bind_workspace", "dns_state_shape",
             "dns_set_state", "dns_get_state", "dns_step", "dns_stats", "dns_destroy",
             "dns_last_error", "dns_last_launch_count", "dns_export_grid", "dns_export_operators",
-            "dns_step_timed", "dns_stats_noalloc", "dns_selftest_timeout"]
+            "dns_step_timed", "dns_stats_noalloc", "dns_selftest_timeout", "dns_kernel_choice"]
 KERNEL_CLASSES = ["mean_deriv", "yderiv", "plane", "forcing", "helm", "mean"]
 
 
@@ -77,6 +77,7 @@ _lib.dns_last_launch_count.argtypes = [_H]
 _lib.dns_step_timed.argtypes = [_H, ctypes.c_int, _dp, ctypes.POINTER(ctypes.c_int)]
 _lib.dns_stats_noalloc.argtypes = [_H, ctypes.c_int, _vp]
 _lib.dns_selftest_timeout.argtypes = [_H]
+_lib.dns_kernel_choice.argtypes = [_H, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
 _lib.dns_export_grid.argtypes = [_H, ctypes.c_int, _dp, _dp, _dp, _dp, _dp]
 _lib.dns_export_operators.argtypes = [_H, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp]
 
@@ -165,6 +166,12 @@ def dns_selftest_timeout(h):
     return _lib.dns_selftest_timeout(h)
 
 
+def dns_kernel_choice(h, group):
+    c = ctypes.c_int()
+    _ck(h, _lib.dns_kernel_choice(h, group, ctypes.byref(c)))
+    return {1: "simt", 2: "tc"}.get(c.value, c.value)
+
+
 def dns_destroy(h):
     return _lib.dns_destroy(h)
 
@@ -197,32 +204,34 @@ _FLOWS = {"couette": DNS_COUETTE, "poiseuille": DNS_POISEUILLE}
 _PRECS = {"fp64": DNS_PREC_FP64, "mixed": DNS_PREC_MIXED}
 
 
-_YGEMM = {"default": 0, "simt": 1, "tc": 2}
+_YGEMM = {"default": 0, "auto": 0, "simt": 1, "tc": 2}
 
 
-def make_config(groups, precision="fp64", use_graph=False, ygemm="default"):
+def make_config(groups, precision="fp64", use_graph=False, ygemm="default", autotune_cache=None):
     """groups: list of dicts with flow, mx, my, mz, lx, lz, re, dt, members,
     optional u_wall (1.0) and bulk_flux (4/3)."""
     arr = (dns_group_desc * len(groups))()
     for i, g in enumerate(groups):
         arr[i] = dns_group_desc(_FLOWS[g["flow"]], g["mx"], g["my"], g["mz"], g["lx"], g["lz"], g["re"],
                                 g["dt"], g.get("u_wall", 1.0), g.get("bulk_flux", 4.0 / 3.0), g["members"])
-    cfg = dns_config(len(groups), arr, _PRECS[precision], 1 if use_graph else 0, 0, 0, None, _YGEMM[ygemm])
-    cfg._keep = arr
+    cache = autotune_cache.encode() if autotune_cache else None
+    cfg = dns_config(len(groups), arr, _PRECS[precision], 1 if use_graph else 0, 0, 0, cache, _YGEMM[ygemm])
+    cfg._keep = (arr, cache)
     return cfg
 
 
 class Ensemble:
     """Owns a handle, its torch workspace and the stream it runs on."""
 
-    def __init__(self, groups, precision="fp64", use_graph=False, device="cuda:0", stream=None, ygemm="default"):
+    def __init__(self, groups, precision="fp64", use_graph=False, device="cuda:0", stream=None, ygemm="default",
+                 autotune_cache=None):
         import torch
         self.torch = torch
         self.device = torch.device(device)
         self.groups = [dict(g) for g in groups]
         # a stream of its own: graph capture is not allowed on the legacy default stream
         self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
-        self.cfg = make_config(groups, precision, use_graph, ygemm)
+        self.cfg = make_config(groups, precision, use_graph, ygemm, autotune_cache)
         self.h = dns_create(self.cfg, self.stream.cuda_stream)
         nbytes = dns_workspace_size(self.h)
         self.ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)

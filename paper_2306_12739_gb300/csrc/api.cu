@@ -35,6 +35,7 @@ struct HostGroup {
 struct dns_handle {
     dns_config cfg;
     std::vector<dns_group_desc> descs;
+    std::string cache_path;
     std::vector<HostGroup> groups;
     cudaStream_t stream = nullptr;
     char* ws = nullptr;
@@ -95,7 +96,7 @@ size_t layout_group(dns_handle* h, HostGroup& G, size_t cur) {
     add((void**)&v.D1T, sizeof(float) * (size_t)v.ny * v.rp);
     add((void**)&v.D2T, sizeof(float) * (size_t)v.ny * v.rp);
     add((void**)&v.status, 256);
-    if (v.ygemm == 2) add((void**)&v.Atc, 3 * 128 * (size_t)v.kp * sizeof(uint16_t));
+    if (v.ygemm != 1) add((void**)&v.Atc, 3 * 128 * (size_t)v.kp * sizeof(uint16_t));
     add((void**)&v.ccw, sizeof(double) * v.my);
     add((void**)&v.kxt, sizeof(double) * v.nkx);
     add((void**)&v.kzt, sizeof(double) * v.nkz);
@@ -205,6 +206,39 @@ void enqueue_step(dns_handle* h, Timer* tm = nullptr) {
     }
 }
 
+// ---- autotuner: per group, time the y-contraction variants on the bound
+// workspace (the work is data independent) and keep the faster one.
+std::string tune_key(const GroupView& v) {
+    char b[128];
+    snprintf(b, sizeof b, "ygemm %d %d %d %d", v.mx, v.my, v.mz, v.E);
+    return b;
+}
+
+int cache_lookup(const char* path, const std::string& key) {
+    if (!path) return 0;
+    FILE* f = fopen(path, "r");
+    if (!f) return 0;
+    char line[256];
+    int found = 0;
+    while (fgets(line, sizeof line, f)) {
+        std::string ln(line);
+        if (ln.compare(0, key.size(), key) == 0 && ln.size() > key.size() + 1) {
+            int c = atoi(ln.c_str() + key.size() + 1);
+            if (c == 1 || c == 2) found = c;
+        }
+    }
+    fclose(f);
+    return found;
+}
+
+void cache_store(const char* path, const std::string& key, int choice, float ms1, float ms2) {
+    if (!path) return;
+    FILE* f = fopen(path, "a");
+    if (!f) return;
+    fprintf(f, "%s %d   # simt %.4f ms, tc %.4f ms\n", key.c_str(), choice, ms1, ms2);
+    fclose(f);
+}
+
 }  // namespace
 
 namespace dnsk {
@@ -227,6 +261,10 @@ int dns_create(const dns_config* cfg, void* cuda_stream, dns_handle** out) {
     h->cfg = *cfg;
     h->descs.assign(cfg->groups, cfg->groups + cfg->n_groups);
     h->cfg.groups = h->descs.data();
+    if (cfg->autotune_cache) {
+        h->cache_path = cfg->autotune_cache;
+        h->cfg.autotune_cache = h->cache_path.c_str();
+    }
     h->stream = (cudaStream_t)cuda_stream;
     *out = h;
     if (cfg->precision != DNS_PREC_FP64 && cfg->precision != DNS_PREC_MIXED)
@@ -258,8 +296,13 @@ int dns_create(const dns_config* cfg, void* cuda_stream, dns_handle** out) {
         v.npairs = v.nkx * (v.kz + 1);
         v.rp = (v.ny + 3) / 4 * 4;
         v.kp = (v.ny + 15) / 16 * 16;
+        // y-contraction variant: 1 register-tiled FP32, 2 tcgen05; 0 = decided by the
+        // autotuner when the workspace is bound
         v.ygemm = 1;
-        if (precision_mixed(h) && cfg->ygemm == 2 && dnsk::yderiv_tc_supported(v)) v.ygemm = 2;
+        if (precision_mixed(h) && dnsk::yderiv_tc_supported(v)) {
+            if (cfg->ygemm == 2) v.ygemm = 2;
+            else if (cfg->ygemm == 0) v.ygemm = 0;
+        }
         v.flow = d.flow == DNS_POISEUILLE ? 1 : 0;
         v.re = d.re; v.dt = d.dt; v.u_wall = d.u_wall; v.bulk_flux = d.bulk_flux;
         if (!make_plan(d.mx, &v.px) || !make_plan(d.mz, &v.pz))
@@ -353,7 +396,7 @@ int dns_create(const dns_config* cfg, void* cuda_stream, dns_handle** out) {
                 G.D1T[(size_t)k * v.rp + r] = (float)G.D1i[(size_t)r * v.ny + k];
                 G.D2T[(size_t)k * v.rp + r] = (float)G.D2i[(size_t)r * v.ny + k];
             }
-        if (v.ygemm == 2) G.Atc = dnsk::yderiv_tc_a_image(G.D1i, G.D2i, v.ny, v.kp);
+        if (v.ygemm != 1) G.Atc = dnsk::yderiv_tc_a_image(G.D1i, G.D2i, v.ny, v.kp);
         G.twx = dnsb::twiddles(d.mx);
         G.twz = dnsb::twiddles(d.mz);
         G.twxf.assign(G.twx.begin(), G.twx.end());
@@ -436,6 +479,39 @@ int dns_bind_workspace(dns_handle* h, void* dev_ptr, size_t bytes) {
     }
     rc = check(h, cudaStreamSynchronize(st), "bind workspace");
     if (rc) return rc;
+    for (auto& G : h->groups) {
+        GroupView& v = G.v;
+        if (v.ygemm != 0) continue;
+        const std::string key = tune_key(v);
+        int choice = cache_lookup(h->cfg.autotune_cache, key);
+        if (!choice) {
+            float best[3] = {0.f, 0.f, 0.f};
+            cudaEvent_t e0, e1;
+            cudaEventCreate(&e0);
+            cudaEventCreate(&e1);
+            for (int cand = 1; cand <= 2; ++cand) {
+                auto run = [&]() {
+                    if (cand == 2) dnsk::launch_yderiv_tc(v, v.v_t, v.e_t, st);
+                    else dnsk::launch_yderiv_t(v, v.v_t, v.e_t, st);
+                };
+                for (int w = 0; w < 2; ++w) run();
+                cudaEventRecord(e0, st);
+                for (int r = 0; r < 5; ++r) run();
+                cudaEventRecord(e1, st);
+                rc = check(h, cudaEventSynchronize(e1), "autotune");
+                if (rc) break;
+                cudaEventElapsedTime(&best[cand], e0, e1);
+                best[cand] /= 5.f;
+            }
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            if (rc) return rc;
+            if ((rc = device_status(h))) return rc;
+            choice = best[2] < best[1] ? 2 : 1;
+            cache_store(h->cfg.autotune_cache, key, choice, best[1], best[2]);
+        }
+        v.ygemm = choice;
+    }
     h->bound = true;
     return DNS_OK;
 }
@@ -637,6 +713,12 @@ int dns_destroy(dns_handle* h) {
 }
 
 const char* dns_last_error(const dns_handle* h) { return h ? h->err.c_str() : "NULL handle"; }
+
+int dns_kernel_choice(const dns_handle* h, int group, int* ygemm) {
+    if (!h || !ygemm || group < 0 || group >= (int)h->groups.size()) return DNS_ERR_INVALID;
+    *ygemm = h->groups[group].v.ygemm;
+    return DNS_OK;
+}
 
 int dns_last_launch_count(const dns_handle* h) { return h ? h->launches : 0; }
 

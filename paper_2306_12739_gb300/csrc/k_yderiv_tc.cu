@@ -24,8 +24,9 @@ namespace dnsk {
 
 namespace tc {
 
-constexpr int THREADS = 128;          // 4 warps: one per 32-lane TMEM slice in the epilogue
-constexpr int NCOL = 256;             // tile width (real columns) = TMEM columns
+constexpr int THREADS = 256;          // 8 warps; warp w reads TMEM lanes 32 (w % 4) in the epilogue
+constexpr int NCOL = 128;             // tile width (real columns) = TMEM columns: 64 of v, 64 of eta
+constexpr int JT = NCOL / 4;          // complex columns per field in a tile
 constexpr int MROWS = 128;
 
 __device__ __forceinline__ unsigned su32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -77,13 +78,15 @@ __device__ __forceinline__ void ld16(unsigned taddr, float* v) {
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// Split x into three BF16 pieces x ~ h + m + l (each the rounding of what is left).
-__device__ __forceinline__ void split3(double x, __nv_bfloat16& h, __nv_bfloat16& m, __nv_bfloat16& l) {
-    h = __float2bfloat16_rn((float)x);
-    const double r1 = x - (double)__bfloat162float(h);
-    m = __float2bfloat16_rn((float)r1);
-    const double r2 = r1 - (double)__bfloat162float(m);
-    l = __float2bfloat16_rn((float)r2);
+// Split x into three BF16 pieces x ~ h + m + l (each the rounding of what is
+// left).  The state is rounded to float once; three 8-bit pieces then hold its
+// 24-bit significand exactly, and the remainders are exact in float.
+__device__ __forceinline__ void split3(float x, __nv_bfloat16& h, __nv_bfloat16& m, __nv_bfloat16& l) {
+    h = __float2bfloat16_rn(x);
+    const float r1 = x - __bfloat162float(h);
+    m = __float2bfloat16_rn(r1);
+    const float r2 = r1 - __bfloat162float(m);
+    l = __float2bfloat16_rn(r2);
 }
 
 struct Tile {
@@ -92,22 +95,23 @@ struct Tile {
 
 __host__ __device__ inline Tile tile_of(int E) {
     Tile t;
-    t.EBT = E < 64 ? E : 64;
-    t.QT = 64 / t.EBT;
+    t.EBT = E < JT ? E : JT;
+    t.QT = JT / t.EBT;
     return t;
 }
 
-// Shared memory: A pieces [3][128 x KP] bf16 | B pieces [3][256 x KP] bf16 (reused
-// as the output staging [3][64][65] float2) | tmem slot | 2 mbarriers.
+// Shared memory: A pieces [3][128 x KP] bf16 | B pieces [3][NCOL x KP] bf16 (reused
+// as the output staging [3][64][JT+1] float2) | tmem slot | 2 mbarriers.
+constexpr int SROW = JT + 1;          // staging row stride (odd: conflict-free column writes)
 __host__ __device__ inline size_t smem_a(int KP) { return (size_t)3 * MROWS * KP * 2; }
 __host__ __device__ inline size_t smem_b(int KP) {
     size_t b = (size_t)3 * NCOL * KP * 2;
-    size_t st = (size_t)3 * 64 * 65 * 8;
+    size_t st = (size_t)3 * 64 * SROW * 8;
     return b > st ? b : st;
 }
 __host__ __device__ inline size_t smem_total(int KP) { return smem_a(KP) + smem_b(KP) + 64; }
 
-__global__ void __launch_bounds__(THREADS, 1) k_yderiv_tc(GroupView g, const double2* __restrict__ V,
+__global__ void __launch_bounds__(THREADS, 2) k_yderiv_tc(GroupView g, const double2* __restrict__ V,
                                                           const double2* __restrict__ H) {
     extern __shared__ __align__(1024) unsigned char sm[];
     const int Ny = g.ny, KP = g.kp, E = g.E, NM = g.nmodes;
@@ -139,11 +143,11 @@ __global__ void __launch_bounds__(THREADS, 1) k_yderiv_tc(GroupView g, const dou
         asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
                      ::"r"(su32(A)), "l"(g.Atc), "r"(bytes), "r"(bar_a) : "memory");
     }
-    // B: column n = f*128 + 2 j + c, j = qq*EBT + el (H order), rows k (interior y)
+    // B: column n = f*(NCOL/2) + 2 j + c, j = qq*EBT + el (H order), rows k (interior y)
     const int KC = KP / 8;
     for (int i = threadIdx.x; i < NCOL * KC; i += THREADS) {
         const int n = i % NCOL, kc = i / NCOL;
-        const int f = n >> 7, r = n & 127, j = r >> 1, c = r & 1;
+        const int f = n / (NCOL / 2), r = n % (NCOL / 2), j = r >> 1, c = r & 1;
         const int qq = j / T.EBT, el = j - qq * T.EBT;
         const int q = q0 + qq, e = e0 + el;
         const bool ok = (qq < T.QT) && (q < NM) && (e < E);
@@ -152,8 +156,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_yderiv_tc(GroupView g, const dou
 #pragma unroll
         for (int t = 0; t < 8; ++t) {
             const int k = kc * 8 + t;
-            double x = 0.0;
-            if (ok && k < Ny) x = src[(((size_t)q * Ny + k) * E + e) * 2 + c];
+            float x = 0.f;
+            if (ok && k < Ny) x = (float)src[(((size_t)q * Ny + k) * E + e) * 2 + c];
             split3(x, hv[t], mv[t], lv[t]);
         }
         const size_t off = (size_t)(n >> 3) * SBO + (size_t)kc * LBO + (size_t)(n & 7) * 16;
@@ -195,22 +199,25 @@ __global__ void __launch_bounds__(THREADS, 1) k_yderiv_tc(GroupView g, const dou
     }
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (ok) {
-        // epilogue: warp w owns TMEM lanes 32w..32w+31 = output rows m
-        float2* stage = (float2*)B;    // [3][64][65]: Dv, D2v, D eta
-        const int m = 32 * warp + lane;
-        const unsigned trow = tmem + ((unsigned)(32 * warp) << 16);
-        for (int c0 = 0; c0 < NCOL; c0 += 16) {
-            float v[16];
-            ld16(trow + c0, v);
-            const int f = c0 >> 7;
-            int fld;
-            if (m < 64) fld = (f == 0) ? 0 : 2;
-            else fld = (f == 0) ? 1 : -1;
-            if (fld < 0) continue;
+        // epilogue: warp w reads TMEM lanes 32 (w % 4).. (output rows m) and the
+        // column half w / 4 (v or eta)
+        float2* stage = (float2*)B;    // [3][64][SROW]: Dv, D2v, D eta
+        const int m = 32 * (warp & 3) + lane;
+        const int f = warp >> 2;
+        const unsigned trow = tmem + ((unsigned)(32 * (warp & 3)) << 16);
+        int fld;
+        if (m < 64) fld = (f == 0) ? 0 : 2;
+        else fld = (f == 0) ? 1 : -1;
+        if (fld >= 0) {
             const int y = m & 63;
-            const int j0 = (c0 & 127) >> 1;
+            for (int c0 = f * (NCOL / 2); c0 < (f + 1) * (NCOL / 2); c0 += 16) {
+                float v[16];
+                ld16(trow + c0, v);
+                const int j0 = (c0 % (NCOL / 2)) >> 1;
 #pragma unroll
-            for (int t = 0; t < 8; ++t) stage[((size_t)fld * 64 + y) * 65 + j0 + t] = make_float2(v[2 * t], v[2 * t + 1]);
+                for (int t = 0; t < 8; ++t)
+                    stage[((size_t)fld * 64 + y) * SROW + j0 + t] = make_float2(v[2 * t], v[2 * t + 1]);
+            }
         }
     } else {
         atomicExch(g.status, 3);
@@ -231,7 +238,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_yderiv_tc(GroupView g, const dou
         const int q = q0 + qq, e = e0 + el;
         if (q >= NM || e >= E) continue;
         const int dst_field = fld == 0 ? 1 : (fld == 1 ? 2 : 4);
-        P[dst_field * fs + ((size_t)y * E + e) * NM + q] = stage[((size_t)fld * 64 + y) * 65 + qq * T.EBT + el];
+        P[dst_field * fs + ((size_t)y * E + e) * NM + q] = stage[((size_t)fld * 64 + y) * SROW + qq * T.EBT + el];
     }
     // the fields themselves (rounded to float) in the same layout
     for (int i = threadIdx.x; i < Ny * per; i += THREADS) {

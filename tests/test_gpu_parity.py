@@ -219,3 +219,25 @@ def test_tensor_core_y_derivatives_match_fp64(mx, my, mz, E):
     for ygemm in ("simt", "tc"):
         err = mixed_errors(_run(g, st, 5, "mixed", ygemm=ygemm), ref)
         assert np.all(err[:, :3] < 1e-6), (ygemm, err)
+
+
+def test_autotuner_picks_a_variant_caches_it_and_matches_that_variant(tmp_path):
+    g = group("poiseuille", 32, 33, 32, 2 * np.pi, np.pi, 1650.0, 0.005, 8)
+    st = _state(g, 5, 5e-2)
+    cache = str(tmp_path / "tune.txt")
+    ens = dns.Ensemble([g], precision="mixed", autotune_cache=cache)
+    choice = dns.dns_kernel_choice(ens.h, 0)
+    assert choice in ("simt", "tc")
+    ens.set_state(0, st["v"], st["eta"], st["U"], st["W"])
+    ens.step(3)
+    got = ens.get_state(0)
+    ens.close()
+    lines = [ln for ln in open(cache) if ln.strip()]
+    assert len(lines) == 1 and lines[0].startswith("ygemm 32 33 32 8 ")
+    ens2 = dns.Ensemble([g], precision="mixed", autotune_cache=cache)   # read back, no new timing
+    assert dns.dns_kernel_choice(ens2.h, 0) == choice
+    ens2.close()
+    assert len([ln for ln in open(cache) if ln.strip()]) == 1
+    ref = _run(g, st, 3, "mixed", ygemm=choice)
+    for a, b in zip(got, ref):
+        assert np.array_equal(a, b)
