@@ -23,7 +23,7 @@ struct HostGroup {
     dnsb::GridOps grid;
     dnsb::CnOps ops[2];
     std::vector<double> kxt, kzt, k2t, k2inv, twx, twz, opsdev[2], mopsdev[2], D1i, D2i;
-    std::vector<float> kxtf, kztf, k2invf, twxf, twzf, opsf[2], opsfT[2], D1if, D2if, D1T, D2T;
+    std::vector<float> kxtf, kztf, k2invf, twxf, twzf, opsf[2], opsfT[2], D1T, D2T;
     std::vector<uint16_t> Atc;
     // byte offsets inside the workspace
     struct Off { size_t off, bytes; };
@@ -91,8 +91,6 @@ size_t layout_group(dns_handle* h, HostGroup& G, size_t cur) {
     add((void**)&v.D1, sizeof(double) * v.my * v.my);
     add((void**)&v.D1i, sizeof(double) * nn);
     add((void**)&v.D2i, sizeof(double) * nn);
-    add((void**)&v.D1if, sizeof(float) * nn);
-    add((void**)&v.D2if, sizeof(float) * nn);
     add((void**)&v.D1T, sizeof(float) * (size_t)v.ny * v.rp);
     add((void**)&v.D2T, sizeof(float) * (size_t)v.ny * v.rp);
     add((void**)&v.status, 256);
@@ -112,7 +110,6 @@ size_t layout_group(dns_handle* h, HostGroup& G, size_t cur) {
     for (int hi = 0; hi < 2; ++hi) {
         add((void**)&v.ops[hi], sizeof(double) * (size_t)v.npairs * 4 * nn);
         if (precision_mixed(h)) {
-            add((void**)&v.opsf[hi], sizeof(float) * (size_t)v.npairs * 4 * nn);
             add((void**)&v.opsfT[hi], sizeof(float) * (size_t)v.npairs * 4 * v.ny * v.rp);
         }
         add((void**)&v.mops[hi], sizeof(double) * (2 * nn + 3 * (size_t)v.ny + (size_t)v.ny * v.my));
@@ -372,6 +369,7 @@ int dns_create(const dns_config* cfg, void* cuda_stream, dns_handle** out) {
                     for (int r = 0; r < v.ny; ++r)
                         for (int k = 0; k < v.ny; ++k)
                             ot[blk * mt + (size_t)k * v.rp + r] = of[blk * nn + (size_t)r * v.ny + k];
+                std::vector<float>().swap(of);
             }
             auto& md = G.mopsdev[hi];
             md.clear();
@@ -387,8 +385,6 @@ int dns_create(const dns_config* cfg, void* cuda_stream, dns_handle** out) {
                 G.D1i[(size_t)i * v.ny + j] = G.grid.D1[(size_t)(i + 1) * d.my + (j + 1)];
                 G.D2i[(size_t)i * v.ny + j] = G.grid.D2[(size_t)(i + 1) * d.my + (j + 1)];
             }
-        G.D1if.assign(G.D1i.begin(), G.D1i.end());
-        G.D2if.assign(G.D2i.begin(), G.D2i.end());
         G.D1T.assign((size_t)v.ny * v.rp, 0.f);
         G.D2T.assign((size_t)v.ny * v.rp, 0.f);
         for (int r = 0; r < v.ny; ++r)
@@ -445,8 +441,6 @@ int dns_bind_workspace(dns_handle* h, void* dev_ptr, size_t bytes) {
             {v.D1, G.grid.D1.data(), G.grid.D1.size() * 8},
             {v.D1i, G.D1i.data(), G.D1i.size() * 8},
             {v.D2i, G.D2i.data(), G.D2i.size() * 8},
-            {v.D1if, G.D1if.data(), G.D1if.size() * 4},
-            {v.D2if, G.D2if.data(), G.D2if.size() * 4},
             {v.ccw, G.grid.ccw.data(), G.grid.ccw.size() * 8},
             {v.kxt, G.kxt.data(), G.kxt.size() * 8},
             {v.kzt, G.kzt.data(), G.kzt.size() * 8},
@@ -461,8 +455,6 @@ int dns_bind_workspace(dns_handle* h, void* dev_ptr, size_t bytes) {
             {v.k2invf, G.k2invf.data(), G.k2invf.size() * 4},
             {v.ops[0], G.opsdev[0].data(), G.opsdev[0].size() * 8},
             {v.ops[1], G.opsdev[1].data(), G.opsdev[1].size() * 8},
-            {v.opsf[0], G.opsf[0].data(), G.opsf[0].size() * 4},
-            {v.opsf[1], G.opsf[1].data(), G.opsf[1].size() * 4},
             {v.opsfT[0], G.opsfT[0].data(), G.opsfT[0].size() * 4},
             {v.opsfT[1], G.opsfT[1].data(), G.opsfT[1].size() * 4},
             {v.D1T, G.D1T.data(), G.D1T.size() * 4},

@@ -29,8 +29,6 @@ struct GroupView {
     const double* D1;     // [My][My]
     const double* D1i;    // [Ny][Ny]
     const double* D2i;    // [Ny][Ny]
-    const float* D1if;    // float copies for the mixed path
-    const float* D2if;
     const float* D1T;     // mixed path, transposed and row-padded: D1T[k][r] = D1i[r][k], [Ny][rp]
     const float* D2T;
     const double* ccw;    // [My]
@@ -46,8 +44,8 @@ struct GroupView {
     const float* kztf;
     const float* k2invf;
     const double* ops[2];   // per h index: [npairs][4][Ny][Ny]  (Mv, Pv, Me, Pe)
-    const float* opsf[2];   // mixed path, per h index: [npairs][4][Ny][Ny]  (Mv - I, Pv, Me - I, Pe)
-    const float* opsfT[2];  // the same transposed and row-padded: [npairs][4][Ny][rp]
+    const float* opsfT[2];  // mixed path, per h index: [npairs][4][Ny][rp], transposed and row-padded
+                            // single-precision (Mv - I), Pv, (Me - I), Pe
     const double* mops[2];  // per h index: MU [Ny][Ny], PU [Ny][Ny], bU [Ny][2], Ug [Ny], PD [Ny][My]
     // state, H layout
     double2 *v_t, *e_t, *v_s, *e_s;
@@ -77,7 +75,6 @@ void launch_plane_state(const GroupView& g, const double* U, const double* W, cu
 template <typename T>
 void launch_forcing(const GroupView& g, int s, cudaStream_t st);
 void launch_helm(const GroupView& g, int s, cudaStream_t st);
-void launch_helm_mixed(const GroupView& g, int s, cudaStream_t st);
 inline size_t mean_smem_bytes(const GroupView& g) { return (8 * (size_t)g.my + 32) * sizeof(double); }
 size_t helm_t_smem_bytes(const GroupView& g);
 size_t yderiv_t_smem_bytes(const GroupView& g);

@@ -178,27 +178,32 @@ __global__ void __launch_bounds__(THREADS) k_forcing_t(GroupView g, int s) {
             if (y >= Ny) break;
             const float2 kv = *(const float2*)&KV[y * NCR + 2 * j];
             const float2 gg = *(const float2*)&GG[y * NCR + 2 * j];
-            double2 F = make_double2((double)kv.x - (double)rx[i], (double)kv.y - (double)ry[i]);
-            double2 G = make_double2((double)gg.x, (double)gg.y);
-            if (q == q_mean) { F = make_double2(0.0, 0.0); G = F; }
+            // F~, G~ and their RK3 accumulators in single precision: they carry the
+            // accuracy of the single-precision nonlinear terms; the state itself is
+            // accumulated in double by the implicit apply
+            float2 F = make_float2(kv.x - rx[i], kv.y - ry[i]);
+            float2 G = gg;
+            if (q == q_mean) { F = make_float2(0.f, 0.f); G = F; }
             const size_t h = ((size_t)q * Ny + y) * E + e;
-            double2 Ft, Gt;
+            float2* Av = (float2*)g.Av;
+            float2* Ae = (float2*)g.Ae;
+            float2 Ft, Gt;
             if (s == 0) {
                 Ft = F; Gt = G;
-                g.Av[h] = F; g.Ae[h] = G;
+                Av[h] = F; Ae[h] = G;
             } else if (s == 1) {
-                const double2 a = g.Av[h], b = g.Ae[h];
-                Ft = make_double2(2.0 * F.x - a.x, 2.0 * F.y - a.y);
-                Gt = make_double2(2.0 * G.x - b.x, 2.0 * G.y - b.y);
-                g.Av[h] = make_double2((1.0 / 6.0) * a.x + (4.0 / 6.0) * F.x, (1.0 / 6.0) * a.y + (4.0 / 6.0) * F.y);
-                g.Ae[h] = make_double2((1.0 / 6.0) * b.x + (4.0 / 6.0) * G.x, (1.0 / 6.0) * b.y + (4.0 / 6.0) * G.y);
+                const float2 a = Av[h], b = Ae[h];
+                Ft = make_float2(2.f * F.x - a.x, 2.f * F.y - a.y);
+                Gt = make_float2(2.f * G.x - b.x, 2.f * G.y - b.y);
+                Av[h] = make_float2((1.f / 6.f) * a.x + (4.f / 6.f) * F.x, (1.f / 6.f) * a.y + (4.f / 6.f) * F.y);
+                Ae[h] = make_float2((1.f / 6.f) * b.x + (4.f / 6.f) * G.x, (1.f / 6.f) * b.y + (4.f / 6.f) * G.y);
             } else {
-                const double2 a = g.Av[h], b = g.Ae[h];
-                Ft = make_double2(a.x + (1.0 / 6.0) * F.x, a.y + (1.0 / 6.0) * F.y);
-                Gt = make_double2(b.x + (1.0 / 6.0) * G.x, b.y + (1.0 / 6.0) * G.y);
+                const float2 a = Av[h], b = Ae[h];
+                Ft = make_float2(a.x + (1.f / 6.f) * F.x, a.y + (1.f / 6.f) * F.y);
+                Gt = make_float2(b.x + (1.f / 6.f) * G.x, b.y + (1.f / 6.f) * G.y);
             }
-            g.Fv[h] = Ft;
-            g.Fe[h] = Gt;
+            ((float2*)g.Fv)[h] = Ft;
+            ((float2*)g.Fe)[h] = Gt;
         }
     }
 }
@@ -257,7 +262,7 @@ __global__ void __launch_bounds__(THREADS) k_helm_t(GroupView g, int s) {
                      ::"r"(smem_u32(to)), "l"(from), "r"(bytes), "r"(bar_a) : "memory");
     }
     const double2* X = f == 0 ? g.v_t : g.e_t;
-    const double2* F = f == 0 ? g.Fv : g.Fe;
+    const float* F = (const float*)(f == 0 ? g.Fv : g.Fe);     // single-precision F~ (mixed path)
     const int per = Ny * 2 * E;
     for (int i = threadIdx.x; i < nq * per; i += THREADS) {
         const int which = i / per, r = i - which * per;
@@ -265,7 +270,7 @@ __global__ void __launch_bounds__(THREADS) k_helm_t(GroupView g, int s) {
         const int q = which == 0 ? q1 : q2;
         const size_t o = (size_t)q * per + r;
         if (needM) Xs[k * NC + which * 2 * E + c] = (float)((const double*)X)[o];
-        Fs[k * NC + which * 2 * E + c] = (float)((const double*)F)[o];
+        Fs[k * NC + which * 2 * E + c] = F[o];
     }
     __syncthreads();
     if (!mbar_wait0(bar_a)) {

@@ -250,11 +250,9 @@ void launch_plane_state(const GroupView& g, const double* U, const double* W, cu
     k_plane<T><<<dim3(g.ny, g.E), PLANE_THREADS, smem, st>>>(g, U, W);
 }
 template void launch_plane_state<double>(const GroupView&, const double*, const double*, cudaStream_t);
-template void launch_plane_state<float>(const GroupView&, const double*, const double*, cudaStream_t);
 
 void set_attributes_plane() {
     allow_max_dynamic_smem(k_plane<double>);
-    allow_max_dynamic_smem(k_plane<float>);
 }
 
 }  // namespace dnsk

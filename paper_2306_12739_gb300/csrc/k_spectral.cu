@@ -107,10 +107,8 @@ __global__ void __launch_bounds__(256) k_yderiv(const double2* __restrict__ v, c
 
 template <typename T> __host__ __device__ const T* d1i_of(const GroupView& g);
 template <> __host__ __device__ const double* d1i_of<double>(const GroupView& g) { return g.D1i; }
-template <> __host__ __device__ const float* d1i_of<float>(const GroupView& g) { return g.D1if; }
 template <typename T> __host__ __device__ const T* d2i_of(const GroupView& g);
 template <> __host__ __device__ const double* d2i_of<double>(const GroupView& g) { return g.D2i; }
-template <> __host__ __device__ const float* d2i_of<float>(const GroupView& g) { return g.D2if; }
 
 template <typename T>
 void launch_yderiv(const GroupView& g, const double2* v, const double2* e, void* P5, cudaStream_t st) {
@@ -120,7 +118,6 @@ void launch_yderiv(const GroupView& g, const double2* v, const double2* e, void*
                                          g.nmodes);
 }
 template void launch_yderiv<double>(const GroupView&, const double2*, const double2*, void*, cudaStream_t);
-template void launch_yderiv<float>(const GroupView&, const double2*, const double2*, void*, cudaStream_t);
 
 // ------------------------------------------------------------------- forcing
 
@@ -209,7 +206,6 @@ void launch_forcing(const GroupView& g, int s, cudaStream_t st) {
     k_forcing<T><<<grid, 256, smem, st>>>(g, s);
 }
 template void launch_forcing<double>(const GroupView&, int, cudaStream_t);
-template void launch_forcing<float>(const GroupView&, int, cudaStream_t);
 
 // --------------------------------------------------------------------- mean
 
@@ -275,81 +271,6 @@ void launch_helm(const GroupView& g, int s, cudaStream_t st) {
     k_helm<<<g.E + 2 * g.npairs, 256, smem, st>>>(g, s);
 }
 
-// Mixed path: x_s = x_t + [(M_h - I) x_t] + [P_h F~] with both brackets in
-// single precision (operators rounded once from double) and the sums in double.
-// (M - I) x_t is O(dt/Re) x_t for the resolved modes, so its single-precision
-// rounding error is tiny against x_t (increment form of Eqs. CN1, CN2).
-__global__ void __launch_bounds__(256) k_helm_mixed(GroupView g, int s) {
-    extern __shared__ __align__(16) unsigned char sm[];
-    const int Ny = g.ny, E = g.E, NKX = g.nkx;
-    if ((int)blockIdx.x < E) { mean_cta(g, s, blockIdx.x, sm); return; }
-    const int b = blockIdx.x - E;
-    const int p = b % g.npairs, f = b / g.npairs;
-    const int n = p % NKX, am = p / NKX;
-    if (n == 0 && am == 0) return;
-    const int hi = (s == 0) ? 0 : 1;
-    const size_t nn = (size_t)Ny * Ny;
-    const float* Mg = g.opsf[hi] + ((size_t)p * 4 + (f == 0 ? 0 : 2)) * nn;
-    const float* Pg = Mg + nn;
-    const int ncol = 2 * E;
-    const int nq = am > 0 ? 2 : 1;
-    const int q1 = (g.kz + am) * NKX + n, q2 = (g.kz - am) * NKX + n;
-    float* Ms = (float*)sm;
-    float* Ps = Ms + nn;
-    float* xs = Ps + nn;                 // [nq][Ny][ncol]
-    float* fs = xs + (size_t)2 * Ny * ncol;
-    const bool needM = (s != 2);
-    const double2* X = f == 0 ? g.v_t : g.e_t;
-    const double2* F = f == 0 ? g.Fv : g.Fe;
-    for (size_t i = threadIdx.x; i < nn; i += blockDim.x) {
-        if (needM) Ms[i] = Mg[i];
-        Ps[i] = Pg[i];
-    }
-    const int per = Ny * ncol;
-    for (int idx = threadIdx.x; idx < nq * per; idx += blockDim.x) {
-        int which = idx / per, r = idx - which * per;
-        int q = which == 0 ? q1 : q2;
-        const double* xc = (const double*)(X + (size_t)q * Ny * E);
-        const double* fc = (const double*)(F + (size_t)q * Ny * E);
-        if (needM) xs[idx] = (float)xc[r];
-        fs[idx] = (float)fc[r];
-    }
-    __syncthreads();
-    double2* M1 = f == 0 ? g.mx1_v : g.mx1_e;
-    double2* O = (s == 2) ? (f == 0 ? g.v_t : g.e_t) : (f == 0 ? g.v_s : g.e_s);
-    for (int idx = threadIdx.x; idx < nq * per; idx += blockDim.x) {
-        int which = idx / per;
-        int r = idx - which * per;
-        int y = r / ncol, c = r - y * ncol;
-        int q = which == 0 ? q1 : q2;
-        const float* xcol = xs + (size_t)which * per + c;
-        const float* fcol = fs + (size_t)which * per + c;
-        float accP = 0.f;
-        const float* pr = Ps + (size_t)y * Ny;
-        for (int k = 0; k < Ny; ++k) accP += pr[k] * fcol[k * ncol];
-        double* m1 = (double*)(M1 + (size_t)q * Ny * E);
-        double* oc = (double*)(O + (size_t)q * Ny * E);
-        double out;
-        if (needM) {
-            float accM = 0.f;
-            const float* mr = Ms + (size_t)y * Ny;
-            for (int k = 0; k < Ny; ++k) accM += mr[k] * xcol[k * ncol];
-            const double* xc = (const double*)(X + (size_t)q * Ny * E);
-            double base = xc[r] + (double)accM;
-            if (s == 1) m1[r] = base;
-            out = base + (double)accP;
-        } else {
-            out = m1[r] + (double)accP;
-        }
-        oc[r] = out;
-    }
-}
-
-void launch_helm_mixed(const GroupView& g, int s, cudaStream_t st) {
-    size_t smem = (2 * (size_t)g.ny * g.ny + 4 * (size_t)g.ny * 2 * g.E) * sizeof(float);
-    if (smem < mean_smem_bytes(g)) smem = mean_smem_bytes(g);
-    k_helm_mixed<<<g.E + 2 * g.npairs, 256, smem, st>>>(g, s);
-}
 
 // --------------------------------------------------------------------- mean
 
@@ -494,11 +415,8 @@ void launch_unpack(const GroupView& g, int member0, int count, cudaStream_t st) 
 
 void set_attributes_spectral() {
     allow_max_dynamic_smem(k_yderiv<double>);
-    allow_max_dynamic_smem(k_yderiv<float>);
     allow_max_dynamic_smem(k_forcing<double>);
-    allow_max_dynamic_smem(k_forcing<float>);
     allow_max_dynamic_smem(k_helm);
-    allow_max_dynamic_smem(k_helm_mixed);
 }
 
 }  // namespace dnsk
