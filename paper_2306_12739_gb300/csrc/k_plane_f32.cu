@@ -110,9 +110,9 @@ struct Cfg {
     static constexpr int NT = ((NT0 + 31) / 32) * 32 > 1024 ? 1024 : ((NT0 + 31) / 32) * 32;
     // shared-memory layout (bytes)
     static constexpr size_t B_BASE = 0;                                   // float2 [5][NM]
-    static constexpr size_t B_PLN = B_BASE + sizeof(float2) * 5 * NM;     // float  [4][PLANE]
-    static constexpr size_t B_A = B_PLN + sizeof(float) * 4 * PLANE;      // float2 [NF][AS]
-    static constexpr size_t B_S = B_A + sizeof(float2) * NF * AS;         // float2 [NF][SSP]
+    static constexpr size_t B_PLN = B_BASE + sizeof(float2) * 5 * NM;     // float  [3][PLANE]: u, v, w
+    static constexpr size_t B_A = B_PLN + sizeof(float) * 3 * PLANE;      // float2 [2 NF][AS]: working + u, v, w
+    static constexpr size_t B_S = B_A + sizeof(float2) * 2 * NF * AS;     // float2 [NF][SSP]
     static constexpr size_t B_TW = B_S + sizeof(float2) * NF * SSP;       // float2 [MX + MZ]
     static constexpr size_t B_K = B_TW + sizeof(float2) * (MX + MZ);      // float [NKX + NKZ + NM]
     static constexpr size_t B_RED = ((B_K + sizeof(float) * (NKX + NKZ + NM)) + 15) / 16 * 16;
@@ -132,7 +132,6 @@ k_plane_f32(GroupView g, const double* __restrict__ Ucur, const double* __restri
     float* PU = pl;
     float* PV = pl + PLANE;
     float* PW = pl + 2 * PLANE;
-    float* ACC = pl + 3 * PLANE;
     float2* Ab = (float2*)(smem + K::B_A);
     float2* Sb = (float2*)(smem + K::B_S);
     float2* twx = (float2*)(smem + K::B_TW);
@@ -209,13 +208,19 @@ k_plane_f32(GroupView g, const double* __restrict__ Ucur, const double* __restri
         return f2(-k * b.y, k * b.x);
     };
 
-    // ---- inverse transforms of three fields; mode 0: into PU/PV/PW,
-    // mode 1: into the per-field scratch as [x][p] line-pair planes
+    // ---- inverse transforms of three fields; mode 0 (u, v, w): into PU/PV/PW,
+    // their z-transformed columns kept in A slots 3..5; mode 1 (the three
+    // derivatives of component xc): into the per-field scratch as [x][p]
+    // line-pair planes.  The x derivative needs no z-stage of its own: the
+    // z transform commutes with the factor i kx, so its x-stage reads the
+    // kept columns of u_xc times i kx.
     constexpr int NKXP = K::NKXP, AS = K::AS, SSP = K::SSP;
-    auto inverse3 = [&](int w0, int w1, int w2, int mode) {
+    auto inverse3 = [&](int w0, int w1, int w2, int mode, int xc) {
+        const int f_lo = (mode == 1) ? 1 : 0;      // the x derivative skips the z-stage
+        auto aslot = [&](int f) -> float2* { return Ab + (mode == 0 ? 3 + f : f) * AS; };
         // z-stage, step A: tasks (f, n2, n), n fastest
-        for (int t = tid; t < NF * NKX * Z2; t += NT) {
-            const int n = t % NKX, r = t / NKX, n2 = r % Z2, f = r / Z2;
+        for (int t = tid; t < (NF - f_lo) * NKX * Z2; t += NT) {
+            const int n = t % NKX, r = t / NKX, n2 = r % Z2, f = f_lo + r / Z2;
             const int which = f == 0 ? w0 : (f == 1 ? w1 : w2);
             float2 v[Z1];
 #pragma unroll
@@ -236,14 +241,14 @@ k_plane_f32(GroupView g, const double* __restrict__ Ucur, const double* __restri
         }
         __syncthreads();
         // z-stage, step C: tasks (f, k1, n) -> A[f][z][n]
-        for (int t = tid; t < NF * NKX * Z1; t += NT) {
-            const int n = t % NKX, r = t / NKX, k1 = r % Z1, f = r / Z1;
+        for (int t = tid; t < (NF - f_lo) * NKX * Z1; t += NT) {
+            const int n = t % NKX, r = t / NKX, k1 = r % Z1, f = f_lo + r / Z1;
             const float2* S = Sb + f * SSP + k1 * (Z2 * NKXP) + n;
             float2 v[Z2];
 #pragma unroll
             for (int n2 = 0; n2 < Z2; ++n2) v[n2] = S[n2 * NKXP];
             Dft<Z2, +1>::run(v);
-            float2* A = Ab + f * AS + n;
+            float2* A = aslot(f) + n;
 #pragma unroll
             for (int k2 = 0; k2 < Z2; ++k2) A[(k1 + Z1 * k2) * NKXP] = v[k2];
         }
@@ -251,7 +256,8 @@ k_plane_f32(GroupView g, const double* __restrict__ Ucur, const double* __restri
         // x-stage, step A: tasks (f, n2, p), p fastest; line p carries rows p, p + HP
         for (int t = tid; t < NF * HP * X2; t += NT) {
             const int p = t % HP, r = t / HP, n2 = r % X2, f = r / X2;
-            const float2* A0 = Ab + f * AS + p * NKXP;
+            const bool dx = (f == 0 && mode == 1);          // x derivative of u_xc
+            const float2* A0 = (dx ? Ab + (3 + xc) * AS : aslot(f)) + p * NKXP;
             const float2* A1 = A0 + HP * NKXP;
             float2 v[X1];
 #pragma unroll
@@ -259,12 +265,14 @@ k_plane_f32(GroupView g, const double* __restrict__ Ucur, const double* __restri
                 const int k = X2 * n1 + n2;
                 float2 Z = f2(0.f, 0.f);
                 if (k == 0) {
-                    Z = f2(A0[0].x, A1[0].x);                 // Hermitian part of the n = 0 column
+                    if (!dx) Z = f2(A0[0].x, A1[0].x);        // Hermitian part of the n = 0 column
                 } else if (k <= KX) {
                     float2 a = A0[k], b = A1[k];
+                    if (dx) { const float kx = kxs[k]; a = f2(-kx * a.y, kx * a.x); b = f2(-kx * b.y, kx * b.x); }
                     Z = f2(a.x - b.y, a.y + b.x);             // a + i b
                 } else if (k >= MX - KX) {
                     float2 a = A0[MX - k], b = A1[MX - k];
+                    if (dx) { const float kx = kxs[MX - k]; a = f2(-kx * a.y, kx * a.x); b = f2(-kx * b.y, kx * b.x); }
                     Z = f2(a.x + b.y, b.x - a.y);             // conj(a) + i conj(b)
                 }
                 v[n1] = Z;
@@ -312,32 +320,30 @@ k_plane_f32(GroupView g, const double* __restrict__ Ucur, const double* __restri
         __syncthreads();
     };
 
-    // ---- forward transform of ACC, kept modes to global
+    // ---- forward transform of the advective sum, held in slot 0 as packed
+    // line pairs [x][p] (row p in .x, row p + HP in .y); kept modes to global
     auto forward = [&](float2* __restrict__ gout) {
-        // x-stage, step A: tasks (n2, p), p fastest
+        // x-stage, step A: tasks (n2, p), p fastest; exchange in slot 1
         for (int t = tid; t < HP * X2; t += NT) {
             const int p = t % HP, n2 = t / HP;
             float2 v[X1];
 #pragma unroll
-            for (int n1 = 0; n1 < X1; ++n1) {
-                const int x = X2 * n1 + n2;
-                v[n1] = f2(ACC[x * MZ + p], ACC[x * MZ + p + HP]);
-            }
+            for (int n1 = 0; n1 < X1; ++n1) v[n1] = Sb[(X2 * n1 + n2) * HP + p];
             Dft<X1, -1>::run(v);
-            float2* S = Sb + n2 * HP + p;
+            float2* S = Sb + SSP + n2 * HP + p;
 #pragma unroll
             for (int k1 = 0; k1 < X1; ++k1) S[k1 * (X2 * HP)] = k1 == 0 ? v[0] : mul(v[k1], twx[n2 * k1]);
         }
         __syncthreads();
-        // x-stage, step C: tasks (k1, p), outputs [x][p] into slot 1
+        // x-stage, step C: tasks (k1, p), outputs [x][p] into slot 2
         for (int t = tid; t < HP * X1; t += NT) {
             const int p = t % HP, k1 = t / HP;
-            const float2* S = Sb + k1 * (X2 * HP) + p;
+            const float2* S = Sb + SSP + k1 * (X2 * HP) + p;
             float2 v[X2];
 #pragma unroll
             for (int n2 = 0; n2 < X2; ++n2) v[n2] = S[n2 * HP];
             Dft<X2, -1>::run(v);
-            float2* O = Sb + SSP + p;
+            float2* O = Sb + 2 * SSP + p;
 #pragma unroll
             for (int k2 = 0; k2 < X2; ++k2) O[(k1 + X1 * k2) * HP] = v[k2];
         }
@@ -346,7 +352,7 @@ k_plane_f32(GroupView g, const double* __restrict__ Ucur, const double* __restri
         const float sx = 1.0f / MX;
         for (int t = tid; t < HP * NKX; t += NT) {
             const int p = t % HP, n = t / HP;
-            const float2* O = Sb + SSP + p;
+            const float2* O = Sb + 2 * SSP + p;
             float2 Zn = O[n * HP], Zc = O[((MX - n) % MX) * HP];
             float2 xa = f2(0.5f * (Zn.x + Zc.x) * sx, 0.5f * (Zn.y - Zc.y) * sx);
             float2 xb = f2(0.5f * (Zn.y + Zc.y) * sx, 0.5f * (Zc.x - Zn.x) * sx);
@@ -367,7 +373,7 @@ k_plane_f32(GroupView g, const double* __restrict__ Ucur, const double* __restri
         }
         __syncthreads();
         // z-stage, step C: tasks (k1, n); keep |m| <= KZ, scale 1/MZ -> staging [NM]
-        float2* stage = Sb + 2 * SSP;
+        float2* stage = Sb + SSP;
         const float sz = 1.0f / MZ;
         for (int t = tid; t < NKX * Z1; t += NT) {
             const int n = t % NKX, k1 = t / NKX;
@@ -391,7 +397,7 @@ k_plane_f32(GroupView g, const double* __restrict__ Ucur, const double* __restri
     };
 
     // velocities
-    inverse3(0, 1, 2, 0);
+    inverse3(0, 1, 2, 0, -1);
     // plane means <uv>, <wv>
     {
         double s1 = 0.0, s2 = 0.0;
@@ -408,17 +414,17 @@ k_plane_f32(GroupView g, const double* __restrict__ Ucur, const double* __restri
     }
     float2* N3 = (float2*)g.N3;
     for (int i = 0; i < 3; ++i) {
-        inverse3(3 + 3 * i, 4 + 3 * i, 5 + 3 * i, 1);
-        // N_i = u d_x u_i + v d_y u_i + w d_z u_i, in this order
-        const float2* G0 = Sb;
+        inverse3(3 + 3 * i, 4 + 3 * i, 5 + 3 * i, 1, i);
+        // N_i = u d_x u_i + v d_y u_i + w d_z u_i, in this order, written over
+        // the d_x plane in the same packed line-pair form
+        float2* G0 = Sb;
         const float2* G1 = Sb + SSP;
         const float2* G2 = Sb + 2 * SSP;
         for (int t = tid; t < HP * MX; t += NT) {
             const int p = t % HP, x = t / HP;
-            float2 a = G0[t], b = G1[t], c = G2[t];
+            const float2 a = G0[t], b = G1[t], c = G2[t];
             const int i0 = x * MZ + p, i1 = i0 + HP;
-            ACC[i0] = PU[i0] * a.x + PV[i0] * b.x + PW[i0] * c.x;
-            ACC[i1] = PU[i1] * a.y + PV[i1] * b.y + PW[i1] * c.y;
+            G0[t] = f2(PU[i0] * a.x + PV[i0] * b.x + PW[i0] * c.x, PU[i1] * a.y + PV[i1] * b.y + PW[i1] * c.y);
         }
         __syncthreads();
         forward(N3 + (size_t)i * fs + off0);
