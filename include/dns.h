@@ -21,7 +21,8 @@
  *     j = 0..My-1 (ascending, walls at j = 0 and My-1); x_i = i Lx/Mx,
  *     z_k = k Lz/Mz.  Retained modes: n = 0..Kx, m = -Kz..Kz with
  *     Kx = (Mx-1)/3, Kz = (Mz-1)/3 (integer division), kx = n 2pi/Lx,
- *     kz = m 2pi/Lz.  Supported Mx, Mz: 16, 32, 48, 64; 5 <= My <= 129.
+ *     kz = m 2pi/Lz.  Supported Mx, Mz: 16, 32, 48, 64, 128 (128 with 64 or 128
+ *     only); 5 <= My <= 129.
  *   * Host state layout (dns_set_state / dns_get_state):
  *       v_hat, eta_hat : double complex, interleaved (re, im),
  *                        [member][My-2 interior y][2 Kz + 1 (m + Kz)][Kx + 1 (n)]
@@ -91,6 +92,10 @@ typedef struct {
                                       kept), 1 register-tiled FP32, 2 tcgen05 tensor cores with
                                       split-BF16 operands (groups with My <= 66 and <= 64
                                       members; others always use 1) */
+    int plane;                     /* plane stage: 0 autotuned where two kernels exist (else the
+                                      only one), 1 one CTA per plane (sizes <= 64), 2 a
+                                      thread-block cluster per plane (64x64 single precision,
+                                      and every size with a 128) */
 } dns_config;
 
 /* One-point statistics of one member (paper Sec. 4), computed from the current
@@ -167,9 +172,11 @@ int dns_destroy(dns_handle* h);
  * next call on the handle. */
 const char* dns_last_error(const dns_handle* h);
 
-/* Variant the y-contraction of `group` uses (1 register-tiled FP32, 2 tcgen05),
- * after the autotuner ran (i.e. after dns_bind_workspace). */
-int dns_kernel_choice(const dns_handle* h, int group, int* ygemm);
+/* Kernel variants `group` uses, after the autotuner ran (i.e. after
+ * dns_bind_workspace): ygemm 1 register-tiled FP32 / 2 tcgen05 y-contraction;
+ * plane 1 one CTA per plane / 2 a thread-block cluster per plane.  Either
+ * output may be NULL. */
+int dns_kernel_choice(const dns_handle* h, int group, int* ygemm, int* plane);
 
 /* Number of kernel launches enqueued by the last dns_step call (all steps). */
 int dns_last_launch_count(const dns_handle* h);

@@ -132,7 +132,7 @@ size_t layout_group(dns_handle* h, HostGroup& G, size_t cur) {
     return cur;
 }
 
-bool supported_m(int m) { return m == 16 || m == 32 || m == 48 || m == 64; }
+bool supported_m(int m) { return m == 16 || m == 32 || m == 48 || m == 64 || m == 128; }
 
 int check(dns_handle* h, cudaError_t e, const char* what) {
     if (e != cudaSuccess) return fail(h, DNS_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
@@ -182,13 +182,15 @@ void enqueue_step(dns_handle* h, Timer* tm = nullptr) {
                 if (g.ygemm == 2) dnsk::launch_yderiv_tc(g, cv, ce, st);
                 else dnsk::launch_yderiv_t(g, cv, ce, st);
                 mark(DNS_K_YDERIV);
-                dnsk::launch_plane_f32(g, cU, cW, st);
+                if (g.plane == 2) dnsk::launch_plane_cl(g, false, cU, cW, st);
+                else dnsk::launch_plane_f32(g, cU, cW, st);
                 mark(DNS_K_PLANE);
                 dnsk::launch_forcing_t(g, s, st);
             } else {
                 dnsk::launch_yderiv<double>(g, cv, ce, g.P5, st);
                 mark(DNS_K_YDERIV);
-                dnsk::launch_plane_state<double>(g, cU, cW, st);
+                if (g.plane == 2) dnsk::launch_plane_cl(g, true, cU, cW, st);
+                else dnsk::launch_plane_state<double>(g, cU, cW, st);
                 mark(DNS_K_PLANE);
                 dnsk::launch_forcing<double>(g, s, st);
             }
@@ -208,6 +210,12 @@ void enqueue_step(dns_handle* h, Timer* tm = nullptr) {
 std::string tune_key(const GroupView& v) {
     char b[128];
     snprintf(b, sizeof b, "ygemm %d %d %d %d", v.mx, v.my, v.mz, v.E);
+    return b;
+}
+
+std::string tune_plane_key(const GroupView& v) {
+    char b[128];
+    snprintf(b, sizeof b, "plane %d %d %d %d", v.mx, v.my, v.mz, v.E);
     return b;
 }
 
@@ -232,7 +240,7 @@ void cache_store(const char* path, const std::string& key, int choice, float ms1
     if (!path) return;
     FILE* f = fopen(path, "a");
     if (!f) return;
-    fprintf(f, "%s %d   # simt %.4f ms, tc %.4f ms\n", key.c_str(), choice, ms1, ms2);
+    fprintf(f, "%s %d   # variant 1 %.4f ms, variant 2 %.4f ms\n", key.c_str(), choice, ms1, ms2);
     fclose(f);
 }
 
@@ -304,9 +312,18 @@ int dns_create(const dns_config* cfg, void* cuda_stream, dns_handle** out) {
         v.re = d.re; v.dt = d.dt; v.u_wall = d.u_wall; v.bulk_flux = d.bulk_flux;
         if (!make_plan(d.mx, &v.px) || !make_plan(d.mz, &v.pz))
             return fail(h, DNS_ERR_UNSUPPORTED, "group %d: no radix plan", gi);
-        size_t smem = precision_mixed(h) ? dnsk::plane_f32_smem_bytes(d.mx, d.mz) : dnsk::plane_smem_bytes(v, 8);
-        if (smem == 0 || smem > 227 * 1024)
-            return fail(h, DNS_ERR_UNSUPPORTED, "group %d: plane stage needs %zu B of shared memory", gi, smem);
+        // plane-stage kernel: single CTA per plane where it fits, a thread-block
+        // cluster (distributed shared memory) where it does not; where both exist
+        // the autotuner decides at bind time
+        const bool mixed = precision_mixed(h);
+        const size_t s1 = mixed ? dnsk::plane_f32_smem_bytes(d.mx, d.mz) : dnsk::plane_smem_bytes(v, 8);
+        const size_t s2 = dnsk::plane_cl_smem_bytes(d.mx, d.mz, !mixed);
+        const bool ok1 = (mixed ? s1 > 0 : (d.mx <= 64 && d.mz <= 64)) && s1 <= 227 * 1024;
+        const bool ok2 = s2 > 0 && s2 <= 227 * 1024;
+        if (!ok1 && !ok2)
+            return fail(h, DNS_ERR_UNSUPPORTED, "group %d: no plane-stage kernel for %dx%d", gi, d.mx, d.mz);
+        v.plane = ok1 && ok2 ? (mixed ? 0 : 1) : (ok1 ? 1 : 2);
+        if (ok1 && ok2 && (cfg->plane == 1 || cfg->plane == 2)) v.plane = cfg->plane;
         if (precision_mixed(h)) {
             size_t m1 = dnsk::helm_t_smem_bytes(v), m2 = dnsk::yderiv_t_smem_bytes(v), m3 = dnsk::forcing_t_smem_bytes(v);
             size_t mm = m1 > m2 ? m1 : m2;
@@ -425,6 +442,7 @@ int dns_bind_workspace(dns_handle* h, void* dev_ptr, size_t bytes) {
     dnsk::set_attributes_plane_f32();
     dnsk::set_attributes_gemm_t();
     dnsk::set_attributes_yderiv_tc();
+    dnsk::set_attributes_plane_cl();
     {
         int rc0 = check(h, cudaGetLastError(), "kernel attributes");
         if (rc0) return rc0;
@@ -471,6 +489,38 @@ int dns_bind_workspace(dns_handle* h, void* dev_ptr, size_t bytes) {
     }
     rc = check(h, cudaStreamSynchronize(st), "bind workspace");
     if (rc) return rc;
+    for (auto& G : h->groups) {
+        GroupView& v = G.v;
+        if (v.plane != 0) continue;
+        const std::string key = tune_plane_key(v);
+        int choice = cache_lookup(h->cfg.autotune_cache, key);
+        if (!choice) {
+            float best[3] = {0.f, 0.f, 0.f};
+            cudaEvent_t e0, e1;
+            cudaEventCreate(&e0);
+            cudaEventCreate(&e1);
+            for (int cand = 1; cand <= 2; ++cand) {
+                auto run = [&]() {
+                    if (cand == 2) dnsk::launch_plane_cl(v, false, v.U_t, v.W_t, st);
+                    else dnsk::launch_plane_f32(v, v.U_t, v.W_t, st);
+                };
+                for (int w = 0; w < 2; ++w) run();
+                cudaEventRecord(e0, st);
+                for (int r = 0; r < 5; ++r) run();
+                cudaEventRecord(e1, st);
+                rc = check(h, cudaEventSynchronize(e1), "autotune plane");
+                if (rc) break;
+                cudaEventElapsedTime(&best[cand], e0, e1);
+                best[cand] /= 5.f;
+            }
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            if (rc) return rc;
+            choice = best[2] < best[1] ? 2 : 1;
+            cache_store(h->cfg.autotune_cache, key, choice, best[1], best[2]);
+        }
+        v.plane = choice;
+    }
     for (auto& G : h->groups) {
         GroupView& v = G.v;
         if (v.ygemm != 0) continue;
@@ -706,9 +756,10 @@ int dns_destroy(dns_handle* h) {
 
 const char* dns_last_error(const dns_handle* h) { return h ? h->err.c_str() : "NULL handle"; }
 
-int dns_kernel_choice(const dns_handle* h, int group, int* ygemm) {
-    if (!h || !ygemm || group < 0 || group >= (int)h->groups.size()) return DNS_ERR_INVALID;
-    *ygemm = h->groups[group].v.ygemm;
+int dns_kernel_choice(const dns_handle* h, int group, int* ygemm, int* plane) {
+    if (!h || group < 0 || group >= (int)h->groups.size()) return DNS_ERR_INVALID;
+    if (ygemm) *ygemm = h->groups[group].v.ygemm;
+    if (plane) *plane = h->groups[group].v.plane;
     return DNS_OK;
 }
 

@@ -20,6 +20,7 @@ struct GroupView {
     int rp;               // Ny rounded up to a multiple of 4 (row padding of transposed operators)
     int kp;               // Ny rounded up to a multiple of 16 (K of the tensor-core y-contraction)
     int ygemm;            // mixed path y-derivatives: 1 register-tiled FP32, 2 tcgen05 split-BF16
+    int plane;            // plane stage: 1 single-CTA kernel, 2 cluster kernel (0 = autotune)
     const void* Atc;      // tensor-core A image: [D1_int; D2_int] in 3 BF16 pieces
     int* status;          // device error word (1: a bounded wait gave up)
     int flow;             // 0 Couette, 1 Poiseuille
@@ -87,6 +88,9 @@ bool yderiv_tc_supported(const GroupView& g);
 size_t yderiv_tc_smem_bytes(const GroupView& g);
 void launch_yderiv_tc(const GroupView& g, const double2* v, const double2* e, cudaStream_t st);
 void set_attributes_yderiv_tc();
+bool launch_plane_cl(const GroupView& g, bool fp64, const double* U, const double* W, cudaStream_t st);
+size_t plane_cl_smem_bytes(int mx, int mz, bool fp64);
+void set_attributes_plane_cl();
 void launch_stats(const GroupView& g, cudaStream_t st);
 void launch_pack(const GroupView& g, int member0, int count, cudaStream_t st);
 void launch_unpack(const GroupView& g, int member0, int count, cudaStream_t st);

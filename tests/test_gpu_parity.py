@@ -37,8 +37,8 @@ def _oracle(g):
     return oracle.Channel(g["mx"], g["my"], g["mz"], g["lx"], g["lz"], g["re"], g["dt"], g["flow"])
 
 
-def _run(g, st, nsteps, precision="fp64", use_graph=False, ygemm="default"):
-    ens = dns.Ensemble([g], precision=precision, use_graph=use_graph, ygemm=ygemm)
+def _run(g, st, nsteps, precision="fp64", use_graph=False, ygemm="default", plane="default"):
+    ens = dns.Ensemble([g], precision=precision, use_graph=use_graph, ygemm=ygemm, plane=plane)
     ens.set_state(0, st["v"], st["eta"], st["U"], st["W"])
     ens.step(nsteps)
     out = ens.get_state(0)
@@ -241,3 +241,31 @@ def test_autotuner_picks_a_variant_caches_it_and_matches_that_variant(tmp_path):
     ref = _run(g, st, 3, "mixed", ygemm=choice)
     for a, b in zip(got, ref):
         assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("mx,mz", [(128, 128), (128, 64), (64, 128)])
+def test_fp64_cluster_plane_kernel_matches_oracle_on_128_grids(mx, mz):
+    g = group("couette", mx, 25, mz, 1.75 * np.pi, 1.2 * np.pi, 500.0, 0.01, 2)
+    st = _state(g, 4000, 5e-2, n_max=6, m_max=6)
+    ref = _oracle(g).step(tuple(st[k] for k in FIELDS), 2)
+    got = _run(g, st, 2)
+    for a, b, name in zip(got, ref, FIELDS):
+        assert rel(a, b) < 1e-12, (name, rel(a, b))
+
+
+@pytest.mark.parametrize("plane", ["cta", "cluster"])
+def test_both_64x64_plane_kernels_match_fp64(plane):
+    g = group("poiseuille", 64, 33, 64, 2 * np.pi, np.pi, 1650.0, 0.005, 3)
+    st = _state(g, 17, 5e-2)
+    ref = _run(g, st, 5, "fp64")
+    err = mixed_errors(_run(g, st, 5, "mixed", plane=plane), ref)
+    assert np.all(err[:, :3] < 1e-6), err
+
+
+def test_channel_128x97x128_mixed_matches_fp64():
+    """Re_tau ~ 180 Poiseuille ensemble at full size (16 members, k^-5/3 noise)."""
+    g = group("poiseuille", 128, 97, 128, 4 * np.pi, 4 * np.pi / 3, 3250.0, 0.002, 16)
+    st = dns_synth.make_state(128, 97, 128, g["lx"], g["lz"], "poiseuille", 16, 5000, 1e-1, spectrum="kolmogorov")
+    ref = _run(g, st, 10, "fp64")
+    err = mixed_errors(_run(g, st, 10, "mixed"), ref)
+    assert np.all(err[:, :3] < 1e-6), err
