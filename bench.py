@@ -30,21 +30,52 @@ sys.path.insert(0, ROOT)
 METRIC = "ensemble member-steps/s (and grid-pts*steps/s) mixed vs FP64 on 1 GB300 at stated err"
 UNIT = "member-steps/s"
 
-WORKLOAD = dict(flow="poiseuille", mx=64, my=65, mz=64, lx=2 * np.pi, lz=np.pi, re=1650.0, dt=0.005,
-                members=8)
-WORKLOAD_NAME = "Poiseuille constant-flux Re=1650 (Re_tau~100), 2pi x 2 x pi, 64x65x64, 8 members, dt=0.005"
-NOISE = dict(seed0=2000, amp=5e-2, n_max=4, m_max=4)
+# The default workload (the headline) and the other ensemble configurations.
+WORKLOADS = {
+    "poiseuille64": dict(
+        groups=[dict(flow="poiseuille", mx=64, my=65, mz=64, lx=2 * np.pi, lz=np.pi, re=1650.0, dt=0.005, members=8)],
+        name="Poiseuille constant-flux Re=1650 (Re_tau~100), 2pi x 2 x pi, 64x65x64, 8 members, dt=0.005",
+        noise=[dict(seed0=2000, amp=5e-2, n_max=4, m_max=4)]),
+    "couette32": dict(
+        groups=[dict(flow="couette", mx=32, my=49, mz=32, lx=1.75 * np.pi, lz=1.2 * np.pi, re=500.0, dt=0.01,
+                     members=64)],
+        name="Couette Re=500 (Re_tau~40 minimal box), 1.75pi x 2 x 1.2pi, 32x49x32, 64 members, dt=0.01",
+        noise=[dict(seed0=3000, amp=5e-2, n_max=4, m_max=4)]),
+    "uneven": dict(
+        groups=[dict(flow="couette", mx=32, my=33, mz=32, lx=1.75 * np.pi, lz=1.2 * np.pi, re=400.0, dt=0.005,
+                     members=64),
+                dict(flow="couette", mx=48, my=49, mz=48, lx=1.75 * np.pi, lz=1.2 * np.pi, re=800.0, dt=0.005,
+                     members=32),
+                dict(flow="poiseuille", mx=64, my=65, mz=64, lx=2 * np.pi, lz=np.pi, re=1650.0, dt=0.005,
+                     members=32)],
+        name="uneven batch, 128 members in one graph: 64 x Couette 32x33x32 Re=400, 32 x Couette 48x49x48 Re=800, "
+             "32 x Poiseuille 64x65x64 Re=1650, dt=0.005",
+        noise=[dict(seed0=4000, amp=(1e-2, 5e-2), n_max=4, m_max=4), dict(seed0=4100, amp=(1e-2, 5e-2), n_max=4, m_max=4),
+               dict(seed0=4200, amp=(1e-2, 5e-2), n_max=4, m_max=4)]),
+    "channel128": dict(
+        groups=[dict(flow="poiseuille", mx=128, my=97, mz=128, lx=4 * np.pi, lz=4 * np.pi / 3, re=3250.0, dt=0.002,
+                     members=16)],
+        name="Poiseuille constant-flux Re=3250 (Re_tau~180), 4pi x 2 x 4pi/3, 128x97x128, 16 members, dt=0.002",
+        noise=[dict(seed0=5000, amp=1e-1, spectrum="kolmogorov")]),
+}
+WORKLOAD = WORKLOADS["poiseuille64"]["groups"][0]
+WORKLOAD_NAME = WORKLOADS["poiseuille64"]["name"]
+NOISE = WORKLOADS["poiseuille64"]["noise"][0]
 
 FP32_PEAK_PER_SM_CLK = 128 * 2          # FP32 lanes x 2 flops (FMA) per SM per clock
 FP64_NOMINAL_TFLOPS = 1.25              # GB300 FP64 (nominal)
 N_SM = 152
 
 
-def initial_state(g, rank=0):
+def initial_state(g, rank=0, noise=None):
     import dns_synth
+    nz = dict(NOISE if noise is None else noise)
+    amp = nz.get("amp", 5e-2)
+    if isinstance(amp, tuple):     # amplitude ramp across members
+        amp = np.linspace(amp[0], amp[1], g["members"])
     return dns_synth.make_state(g["mx"], g["my"], g["mz"], g["lx"], g["lz"], g["flow"], g["members"],
-                                NOISE["seed0"] + 1000 * rank, NOISE["amp"], n_max=NOISE["n_max"],
-                                m_max=NOISE["m_max"])
+                                nz["seed0"] + 1000 * rank, amp, n_max=nz.get("n_max"), m_max=nz.get("m_max"),
+                                spectrum=nz.get("spectrum", "flat"))
 
 
 # ----------------------------------------------------------- distributed
@@ -261,13 +292,20 @@ def gpu_arm(args, rank, world, dist):
     import torch
     import paper_2306_12739_gb300 as dns
     dev = torch.device("cuda", torch.cuda.current_device())
-    g = dict(WORKLOAD)
-    st = initial_state(g, rank)
+    wl = WORKLOADS[args.workload]
+    groups = [dict(g) for g in wl["groups"]]
+    states = [initial_state(g, rank, nz) for g, nz in zip(groups, wl["noise"])]
+    members = sum(g["members"] for g in groups)
+    pts = sum(g["members"] * g["mx"] * g["my"] * g["mz"] for g in groups)   # member grid points
     precision = args.precision
 
+    def load(ens):
+        for gi, st in enumerate(states):
+            ens.set_state(gi, st["v"], st["eta"], st["U"], st["W"])
+
     def timed_run(prec, nsteps, nwarm, flush):
-        ens = dns.Ensemble([g], precision=prec, use_graph=True, device=dev, ygemm=args.ygemm)
-        ens.set_state(0, st["v"], st["eta"], st["U"], st["W"])
+        ens = dns.Ensemble(groups, precision=prec, use_graph=True, device=dev, ygemm=args.ygemm)
+        load(ens)
         stream = ens.stream
         ens.step(nwarm)
         torch.cuda.synchronize()
@@ -295,25 +333,27 @@ def gpu_arm(args, rank, world, dist):
 
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
     ens, total_ms, launches, clocks = timed_run(precision, args.steps, args.warmup, flush)
-    ygemm_used = dns.dns_kernel_choice(ens.h, 0)
+    choices = [dict(ygemm=dns.dns_kernel_choice(ens.h, gi, "ygemm"), plane=dns.dns_kernel_choice(ens.h, gi, "plane"))
+               for gi in range(len(groups))]
     total_ms = reduce_max(total_ms, dist, dev)
     ms_step = total_ms / args.steps
-    value = aggregate(g["members"] * args.steps, total_ms / 1e3, world)
-    pts = g["mx"] * g["my"] * g["mz"]
+    value = aggregate(members * args.steps, total_ms / 1e3, world)
 
     # per-kernel device times (events around every launch), for the roofline
-    ens.set_state(0, st["v"], st["eta"], st["U"], st["W"])
+    load(ens)
     kt = ens.step_timed(max(1, min(args.steps, 5)))
     tot = sum(v[0] for v in kt.values())
     shares = {k: (v[0] / tot if tot > 0 else 0.0) for k, v in kt.items()}
     dom = max(kt, key=lambda k: kt[k][0])
+    per_group_launches = kt[dom][1] / len(groups)
+    work = sum(kernel_work(dom, g, precision)[1] for g in groups) * per_group_launches
+    bound = kernel_work(dom, groups[0], precision)[0]
     avg_ms = kt[dom][0] / max(1, kt[dom][1])
-    bound, work, wunit = kernel_work(dom, g, precision)
     kprec = kernel_precision(dom, precision)
     sm_mhz = clocks["sm_mhz"] or 2070.0
     peak = alu_peak(kprec, sm_mhz)
-    achieved = work / (avg_ms / 1e3) / 1e12
-    traffic = profiled_traffic(dom) if precision == "mixed" else None
+    achieved = work / (kt[dom][0] / 1e3) / 1e12
+    traffic = profiled_traffic(dom) if (precision == "mixed" and args.workload == "poiseuille64") else None
     roofline = {"kernel": dom, "bound": bound, "precision": kprec, "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
                 "traffic_unit": "DRAM bytes per launch (ncu, profiles/)",
@@ -323,26 +363,28 @@ def gpu_arm(args, rank, world, dist):
                 "shares": {k: round(v, 4) for k, v in shares.items()}}
 
     # end to end through the C ABI with host buffers: upload state, step, download state
-    v = np.ascontiguousarray(st["v"]); e = np.ascontiguousarray(st["eta"])
-    U = np.ascontiguousarray(st["U"]); W = np.ascontiguousarray(st["W"])
-    pin = [torch.from_numpy(a.view(np.float64)).pin_memory() for a in (v, e, U, W)]
-    h2d = sum(p.numel() * 8 for p in pin)
-    outs = [torch.empty_like(p).pin_memory() for p in pin]
-    d2h = sum(o.numel() * 8 for o in outs)
-    nkx, nkz, ny, my = ens.shapes[0]
-    E = g["members"]
+    pins, outs = [], []
+    for st in states:
+        pin = [torch.from_numpy(np.ascontiguousarray(st[k]).view(np.float64)).pin_memory()
+               for k in ("v", "eta", "U", "W")]
+        pins.append(pin)
+        outs.append([torch.empty_like(p).pin_memory() for p in pin])
+    h2d = sum(p.numel() * 8 for pin in pins for p in pin)
+    d2h = sum(o.numel() * 8 for out in outs for o in out)
     e2e_steps = max(1, min(args.steps, 10))
     torch.cuda.synchronize()
     if dist is not None:
         dist.barrier()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        dns.dns_set_state(ens.h, 0, 0, E, *[p.data_ptr() for p in pin], 0)
+        for gi, g in enumerate(groups):
+            dns.dns_set_state(ens.h, gi, 0, g["members"], *[p.data_ptr() for p in pins[gi]], 0)
         dns.dns_step(ens.h, 1)
-        dns.dns_get_state(ens.h, 0, 0, E, *[o.data_ptr() for o in outs], 0)
+        for gi, g in enumerate(groups):
+            dns.dns_get_state(ens.h, gi, 0, g["members"], *[o.data_ptr() for o in outs[gi]], 0)
     e2e_s = time.perf_counter() - t0
     e2e_s = reduce_max(e2e_s, dist, dev)
-    e2e_value = aggregate(E * e2e_steps, e2e_s, world)
+    e2e_value = aggregate(members * e2e_steps, e2e_s, world)
     ens.close()
 
     line = {
@@ -350,10 +392,10 @@ def gpu_arm(args, rank, world, dist):
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64" if precision == "mixed" else "f64",
         "data": "synthetic (seeded, dns_synth)",
-        "config": {"workload": WORKLOAD_NAME, "precision": precision, "graph": True,
-                   "ygemm": "%s (%s)" % (ygemm_used, args.ygemm),
+        "config": {"workload": wl["name"], "precision": precision, "graph": True,
+                   "kernels": choices, "ygemm_request": args.ygemm,
                    "l2": "flushed (256 MiB write) before every timed step", "parallelism": "replicas x%d" % world},
-        "grid_pts_steps_per_s": value * pts,
+        "grid_pts_steps_per_s": aggregate(pts * args.steps, total_ms / 1e3, world),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "steps": e2e_steps},
         "gpu_launches": launches,
@@ -366,17 +408,18 @@ def gpu_arm(args, rank, world, dist):
         ens64, t64, _, _ = timed_run("fp64", n64, min(args.warmup, 3), flush)
         ens64.close()
         t64 = reduce_max(t64, dist, dev)
-        v64 = aggregate(g["members"] * n64, t64 / 1e3, world)
+        v64 = aggregate(members * n64, t64 / 1e3, world)
         line["fp64"] = {"value": v64, "unit": UNIT, "ms_per_step": t64 / n64, "steps": n64}
         line["mixed_over_fp64"] = value / v64
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        out = run_oracle(g, 4, 2)
+        g0 = groups[0]
+        out = run_oracle(g0, min(g0["members"], 4), 2)
         model, ncpu = cpu_info()
         line["cpu_baseline"] = {"value": out["members"] * out["steps"] / out["seconds"], "unit": UNIT, "cores": 1,
                                 "kind": "oracle",
-                                "sample": "%d steps x %d members of the workload, single-threaded numpy, cpu %s (%d cores on host)"
-                                          % (out["steps"], out["members"], model, ncpu)}
+                                "sample": "%d steps x %d members of the workload's first group, single-threaded numpy, "
+                                          "cpu %s (%d cores on host)" % (out["steps"], out["members"], model, ncpu)}
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -392,6 +435,8 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparator run")
     ap.add_argument("--ygemm", choices=["default", "simt", "tc"], default="default",
                     help="y-contraction variant of the mixed path")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="poiseuille64",
+                    help="ensemble configuration (default: the headline 64x65x64 Poiseuille ensemble)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -269,3 +269,23 @@ def test_channel_128x97x128_mixed_matches_fp64():
     ref = _run(g, st, 10, "fp64")
     err = mixed_errors(_run(g, st, 10, "mixed"), ref)
     assert np.all(err[:, :3] < 1e-6), err
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_uneven_batch_groups_match_each_group_run_alone(precision):
+    """Three grids / Reynolds numbers / flows in one handle and one graph: each
+    group's trajectory is bit-identical to the same group run on its own."""
+    gs = [group("couette", 32, 33, 32, 1.75 * np.pi, 1.2 * np.pi, 400.0, 0.005, 3),
+          group("couette", 48, 49, 48, 1.75 * np.pi, 1.2 * np.pi, 800.0, 0.005, 2),
+          group("poiseuille", 64, 65, 64, 2 * np.pi, np.pi, 1650.0, 0.005, 2)]
+    sts = [_state(g, 4000 + 100 * i, np.linspace(1e-2, 5e-2, g["members"])) for i, g in enumerate(gs)]
+    ens = dns.Ensemble(gs, precision=precision, use_graph=True, ygemm="simt", plane="cta")
+    for i, st in enumerate(sts):
+        ens.set_state(i, st["v"], st["eta"], st["U"], st["W"])
+    ens.step(3)
+    together = [ens.get_state(i) for i in range(len(gs))]
+    ens.close()
+    for g, st, tog in zip(gs, sts, together):
+        alone = _run(g, st, 3, precision, use_graph=True, ygemm="simt", plane="cta")
+        for a, b in zip(tog, alone):
+            assert np.array_equal(a, b)
