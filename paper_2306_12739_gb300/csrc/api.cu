@@ -47,6 +47,11 @@ struct dns_handle {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
     int graph_launches = 0;
+    // multi-group handles: one stream per group, forked from and joined back to
+    // the caller's stream every step (independent branches of one graph)
+    std::vector<cudaStream_t> gstreams;
+    std::vector<cudaEvent_t> gevents;
+    cudaEvent_t fork_ev = nullptr;
 };
 
 namespace {
@@ -160,8 +165,7 @@ struct Timer {
     std::vector<int> cls;
 };
 
-void enqueue_step(dns_handle* h, Timer* tm = nullptr) {
-    cudaStream_t st = h->stream;
+void enqueue_group(dns_handle* h, HostGroup& G, cudaStream_t st, Timer* tm) {
     auto mark = [&](int c) {
         if (!tm) return;
         cudaEvent_t e;
@@ -170,39 +174,55 @@ void enqueue_step(dns_handle* h, Timer* tm = nullptr) {
         tm->ev.push_back(e);
         tm->cls.push_back(c);
     };
-    for (auto& G : h->groups) {
-        const GroupView& g = G.v;
-        for (int s = 0; s < 3; ++s) {
-            const double2* cv = s == 0 ? g.v_t : g.v_s;
-            const double2* ce = s == 0 ? g.e_t : g.e_s;
-            const double* cU = s == 0 ? g.U_t : g.U_s;
-            const double* cW = s == 0 ? g.W_t : g.W_s;
-            mark(-1);
-            if (precision_mixed(h)) {
-                if (g.ygemm == 2) dnsk::launch_yderiv_tc(g, cv, ce, st);
-                else dnsk::launch_yderiv_t(g, cv, ce, st);
-                mark(DNS_K_YDERIV);
-                if (g.plane == 2) dnsk::launch_plane_cl(g, false, cU, cW, st);
-                else dnsk::launch_plane_f32(g, cU, cW, st);
-                mark(DNS_K_PLANE);
-                dnsk::launch_forcing_t(g, s, st);
-            } else {
-                dnsk::launch_yderiv<double>(g, cv, ce, g.P5, st);
-                mark(DNS_K_YDERIV);
-                if (g.plane == 2) dnsk::launch_plane_cl(g, true, cU, cW, st);
-                else dnsk::launch_plane_state<double>(g, cU, cW, st);
-                mark(DNS_K_PLANE);
-                dnsk::launch_forcing<double>(g, s, st);
-            }
-            mark(DNS_K_FORCING);
-            // per-wavenumber implicit apply; the same launch carries the mean-flow
-            // update as E extra CTAs (independent work that overlaps with it)
-            if (precision_mixed(h)) dnsk::launch_helm_t(g, s, st);
-            else dnsk::launch_helm(g, s, st);
-            mark(DNS_K_HELM);
-            h->launches += 4;
+    const GroupView& g = G.v;
+    for (int s = 0; s < 3; ++s) {
+        const double2* cv = s == 0 ? g.v_t : g.v_s;
+        const double2* ce = s == 0 ? g.e_t : g.e_s;
+        const double* cU = s == 0 ? g.U_t : g.U_s;
+        const double* cW = s == 0 ? g.W_t : g.W_s;
+        mark(-1);
+        if (precision_mixed(h)) {
+            if (g.ygemm == 2) dnsk::launch_yderiv_tc(g, cv, ce, st);
+            else dnsk::launch_yderiv_t(g, cv, ce, st);
+            mark(DNS_K_YDERIV);
+            if (g.plane == 2) dnsk::launch_plane_cl(g, false, cU, cW, st);
+            else dnsk::launch_plane_f32(g, cU, cW, st);
+            mark(DNS_K_PLANE);
+            dnsk::launch_forcing_t(g, s, st);
+        } else {
+            dnsk::launch_yderiv<double>(g, cv, ce, g.P5, st);
+            mark(DNS_K_YDERIV);
+            if (g.plane == 2) dnsk::launch_plane_cl(g, true, cU, cW, st);
+            else dnsk::launch_plane_state<double>(g, cU, cW, st);
+            mark(DNS_K_PLANE);
+            dnsk::launch_forcing<double>(g, s, st);
         }
+        mark(DNS_K_FORCING);
+        // per-wavenumber implicit apply; the same launch carries the mean-flow
+        // update as E extra CTAs (independent work that overlaps with it)
+        if (precision_mixed(h)) dnsk::launch_helm_t(g, s, st);
+        else dnsk::launch_helm(g, s, st);
+        mark(DNS_K_HELM);
+        h->launches += 4;
     }
+}
+
+// One full step of every group.  With several groups (and no per-launch
+// timing) each group runs on its own stream, forked from and joined back to
+// the caller's stream, so the groups of an uneven batch proceed concurrently
+// (and a captured graph holds one independent branch per group).
+void enqueue_step(dns_handle* h, Timer* tm = nullptr) {
+    if (tm || h->groups.size() == 1 || h->gstreams.empty()) {
+        for (auto& G : h->groups) enqueue_group(h, G, h->stream, tm);
+        return;
+    }
+    cudaEventRecord(h->fork_ev, h->stream);
+    for (size_t gi = 0; gi < h->groups.size(); ++gi) {
+        cudaStreamWaitEvent(h->gstreams[gi], h->fork_ev, 0);
+        enqueue_group(h, h->groups[gi], h->gstreams[gi], nullptr);
+        cudaEventRecord(h->gevents[gi], h->gstreams[gi]);
+    }
+    for (size_t gi = 0; gi < h->groups.size(); ++gi) cudaStreamWaitEvent(h->stream, h->gevents[gi], 0);
 }
 
 // ---- autotuner: per group, time the y-contraction variants on the bound
@@ -243,6 +263,7 @@ void cache_store(const char* path, const std::string& key, int choice, float ms1
     fprintf(f, "%s %d   # variant 1 %.4f ms, variant 2 %.4f ms\n", key.c_str(), choice, ms1, ms2);
     fclose(f);
 }
+
 
 }  // namespace
 
@@ -437,6 +458,18 @@ int dns_bind_workspace(dns_handle* h, void* dev_ptr, size_t bytes) {
     h->ws_bytes = bytes;
     if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
     if (h->graph) { cudaGraphDestroy(h->graph); h->graph = nullptr; }
+    if (h->groups.size() > 1 && h->gstreams.empty()) {
+        int rc0 = check(h, cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming), "fork event");
+        if (rc0) return rc0;
+        for (size_t gi = 0; gi < h->groups.size(); ++gi) {
+            cudaStream_t s2;
+            cudaEvent_t e2;
+            if ((rc0 = check(h, cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking), "group stream"))) return rc0;
+            if ((rc0 = check(h, cudaEventCreateWithFlags(&e2, cudaEventDisableTiming), "group event"))) return rc0;
+            h->gstreams.push_back(s2);
+            h->gevents.push_back(e2);
+        }
+    }
     dnsk::set_attributes_spectral();
     dnsk::set_attributes_plane();
     dnsk::set_attributes_plane_f32();
@@ -750,6 +783,9 @@ int dns_destroy(dns_handle* h) {
     if (h->bound) cudaStreamSynchronize(h->stream);
     if (h->gexec) cudaGraphExecDestroy(h->gexec);
     if (h->graph) cudaGraphDestroy(h->graph);
+    for (auto s2 : h->gstreams) cudaStreamDestroy(s2);
+    for (auto e2 : h->gevents) cudaEventDestroy(e2);
+    if (h->fork_ev) cudaEventDestroy(h->fork_ev);
     delete h;
     return DNS_OK;
 }

@@ -271,15 +271,17 @@ def test_channel_128x97x128_mixed_matches_fp64():
     assert np.all(err[:, :3] < 1e-6), err
 
 
+@pytest.mark.parametrize("use_graph", [True, False])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_uneven_batch_groups_match_each_group_run_alone(precision):
-    """Three grids / Reynolds numbers / flows in one handle and one graph: each
+def test_uneven_batch_groups_match_each_group_run_alone(precision, use_graph):
+    """Three grids / Reynolds numbers / flows in one handle (the groups run as
+    concurrent branches, captured in one graph or launched eagerly): each
     group's trajectory is bit-identical to the same group run on its own."""
     gs = [group("couette", 32, 33, 32, 1.75 * np.pi, 1.2 * np.pi, 400.0, 0.005, 3),
           group("couette", 48, 49, 48, 1.75 * np.pi, 1.2 * np.pi, 800.0, 0.005, 2),
           group("poiseuille", 64, 65, 64, 2 * np.pi, np.pi, 1650.0, 0.005, 2)]
     sts = [_state(g, 4000 + 100 * i, np.linspace(1e-2, 5e-2, g["members"])) for i, g in enumerate(gs)]
-    ens = dns.Ensemble(gs, precision=precision, use_graph=True, ygemm="simt", plane="cta")
+    ens = dns.Ensemble(gs, precision=precision, use_graph=use_graph, ygemm="simt", plane="cta")
     for i, st in enumerate(sts):
         ens.set_state(i, st["v"], st["eta"], st["U"], st["W"])
     ens.step(3)
