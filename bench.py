@@ -304,7 +304,7 @@ def gpu_arm(args, rank, world, dist):
             ens.set_state(gi, st["v"], st["eta"], st["U"], st["W"])
 
     def timed_run(prec, nsteps, nwarm, flush):
-        ens = dns.Ensemble(groups, precision=prec, use_graph=True, device=dev, ygemm=args.ygemm)
+        ens = dns.Ensemble(groups, precision=prec, use_graph=True, device=dev, ygemm=args.ygemm, plane=args.plane)
         load(ens)
         stream = ens.stream
         ens.step(nwarm)
@@ -393,7 +393,7 @@ def gpu_arm(args, rank, world, dist):
         "vs_baseline": None, "dtype": "f32+f64" if precision == "mixed" else "f64",
         "data": "synthetic (seeded, dns_synth)",
         "config": {"workload": wl["name"], "precision": precision, "graph": True,
-                   "kernels": choices, "ygemm_request": args.ygemm,
+                   "kernels": choices, "ygemm_request": args.ygemm, "plane_request": args.plane,
                    "l2": "flushed (256 MiB write) before every timed step", "parallelism": "replicas x%d" % world},
         "grid_pts_steps_per_s": aggregate(pts * args.steps, total_ms / 1e3, world),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
@@ -433,6 +433,8 @@ def main():
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparator run")
+    ap.add_argument("--plane", choices=["default", "cta", "cluster", "lines"], default="default",
+                    help="plane-stage kernel (default: autotuned among those the grid supports)")
     ap.add_argument("--ygemm", choices=["default", "simt", "tc"], default="default",
                     help="y-contraction variant of the mixed path")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="poiseuille64",

@@ -92,10 +92,13 @@ typedef struct {
                                       kept), 1 register-tiled FP32, 2 tcgen05 tensor cores with
                                       split-BF16 operands (groups with My <= 66 and <= 64
                                       members; others always use 1) */
-    int plane;                     /* plane stage: 0 autotuned where two kernels exist (else the
-                                      only one), 1 one CTA per plane (sizes <= 64), 2 a
-                                      thread-block cluster per plane (64x64 single precision,
-                                      and every size with a 128) */
+    int plane;                     /* plane stage: 0 autotuned where several kernels exist (else
+                                      the only one; FP64 defaults to 1), 1 one CTA per plane
+                                      (sizes <= 64), 2 a thread-block cluster per plane (64x64
+                                      single precision, and every size with a 128), 3 one CTA
+                                      per plane with each 1-D transform owned by one group of
+                                      threads (mixed precision, sizes <= 64); a request for a
+                                      variant the group's size lacks is ignored */
 } dns_config;
 
 /* One-point statistics of one member (paper Sec. 4), computed from the current
@@ -174,7 +177,8 @@ const char* dns_last_error(const dns_handle* h);
 
 /* Kernel variants `group` uses, after the autotuner ran (i.e. after
  * dns_bind_workspace): ygemm 1 register-tiled FP32 / 2 tcgen05 y-contraction;
- * plane 1 one CTA per plane / 2 a thread-block cluster per plane.  Either
+ * plane 1 one CTA per plane / 2 a thread-block cluster per plane / 3 line-owned
+ * single CTA per plane.  Either
  * output may be NULL. */
 int dns_kernel_choice(const dns_handle* h, int group, int* ygemm, int* plane);
 

@@ -167,11 +167,11 @@ def dns_selftest_timeout(h):
 
 
 def dns_kernel_choice(h, group, which="ygemm"):
-    """'ygemm' -> 'simt' | 'tc'; 'plane' -> 'cta' | 'cluster'."""
+    """'ygemm' -> 'simt' | 'tc'; 'plane' -> 'cta' | 'cluster' | 'lines'."""
     c, p = ctypes.c_int(), ctypes.c_int()
     _ck(h, _lib.dns_kernel_choice(h, group, ctypes.byref(c), ctypes.byref(p)))
     if which == "plane":
-        return {1: "cta", 2: "cluster"}.get(p.value, p.value)
+        return {1: "cta", 2: "cluster", 3: "lines"}.get(p.value, p.value)
     return {1: "simt", 2: "tc"}.get(c.value, c.value)
 
 
@@ -210,7 +210,7 @@ _PRECS = {"fp64": DNS_PREC_FP64, "mixed": DNS_PREC_MIXED}
 _YGEMM = {"default": 0, "auto": 0, "simt": 1, "tc": 2}
 
 
-_PLANE = {"default": 0, "auto": 0, "cta": 1, "cluster": 2}
+_PLANE = {"default": 0, "auto": 0, "cta": 1, "cluster": 2, "lines": 3}
 
 
 def make_config(groups, precision="fp64", use_graph=False, ygemm="default", autotune_cache=None, plane="default"):

@@ -186,6 +186,7 @@ void enqueue_group(dns_handle* h, HostGroup& G, cudaStream_t st, Timer* tm) {
             else dnsk::launch_yderiv_t(g, cv, ce, st);
             mark(DNS_K_YDERIV);
             if (g.plane == 2) dnsk::launch_plane_cl(g, false, cU, cW, st);
+            else if (g.plane == 3) dnsk::launch_plane_lines(g, cU, cW, st);
             else dnsk::launch_plane_f32(g, cU, cW, st);
             mark(DNS_K_PLANE);
             dnsk::launch_forcing_t(g, s, st);
@@ -233,6 +234,25 @@ std::string tune_key(const GroupView& v) {
     return b;
 }
 
+// plane-stage variants: 1 one CTA per plane, 2 a thread-block cluster per
+// plane, 3 line-owned single CTA (single precision only)
+bool plane_variant_ok(bool mixed, const GroupView& v, int c) {
+    const size_t lim = 227 * 1024;
+    if (c == 1) {
+        const size_t b = mixed ? dnsk::plane_f32_smem_bytes(v.mx, v.mz) : dnsk::plane_smem_bytes(v, 8);
+        return (mixed ? b > 0 : (v.mx <= 64 && v.mz <= 64)) && b <= lim;
+    }
+    if (c == 2) {
+        const size_t b = dnsk::plane_cl_smem_bytes(v.mx, v.mz, !mixed);
+        return b > 0 && b <= lim;
+    }
+    if (c == 3) {
+        const size_t b = mixed ? dnsk::plane_lines_smem_bytes(v.mx, v.mz) : 0;
+        return b > 0 && b <= lim;
+    }
+    return false;
+}
+
 std::string tune_plane_key(const GroupView& v) {
     char b[128];
     snprintf(b, sizeof b, "plane %d %d %d %d", v.mx, v.my, v.mz, v.E);
@@ -249,18 +269,23 @@ int cache_lookup(const char* path, const std::string& key) {
         std::string ln(line);
         if (ln.compare(0, key.size(), key) == 0 && ln.size() > key.size() + 1) {
             int c = atoi(ln.c_str() + key.size() + 1);
-            if (c == 1 || c == 2) found = c;
+            if (c >= 1 && c <= 3) found = c;
         }
     }
     fclose(f);
     return found;
 }
 
-void cache_store(const char* path, const std::string& key, int choice, float ms1, float ms2) {
+void cache_store(const char* path, const std::string& key, int choice, const float* ms, int nvar) {
     if (!path) return;
     FILE* f = fopen(path, "a");
     if (!f) return;
-    fprintf(f, "%s %d   # variant 1 %.4f ms, variant 2 %.4f ms\n", key.c_str(), choice, ms1, ms2);
+    fprintf(f, "%s %d   #", key.c_str(), choice);
+    for (int c = 1; c <= nvar; ++c) {
+        if (ms[c] > 0.f) fprintf(f, " variant %d %.4f ms", c, ms[c]);
+        else fprintf(f, " variant %d n/a", c);
+    }
+    fprintf(f, "\n");
     fclose(f);
 }
 
@@ -337,14 +362,13 @@ int dns_create(const dns_config* cfg, void* cuda_stream, dns_handle** out) {
         // cluster (distributed shared memory) where it does not; where both exist
         // the autotuner decides at bind time
         const bool mixed = precision_mixed(h);
-        const size_t s1 = mixed ? dnsk::plane_f32_smem_bytes(d.mx, d.mz) : dnsk::plane_smem_bytes(v, 8);
-        const size_t s2 = dnsk::plane_cl_smem_bytes(d.mx, d.mz, !mixed);
-        const bool ok1 = (mixed ? s1 > 0 : (d.mx <= 64 && d.mz <= 64)) && s1 <= 227 * 1024;
-        const bool ok2 = s2 > 0 && s2 <= 227 * 1024;
-        if (!ok1 && !ok2)
+        const bool ok[4] = {false, plane_variant_ok(mixed, v, 1), plane_variant_ok(mixed, v, 2),
+                            plane_variant_ok(mixed, v, 3)};
+        const int navail = ok[1] + ok[2] + ok[3];
+        if (navail == 0)
             return fail(h, DNS_ERR_UNSUPPORTED, "group %d: no plane-stage kernel for %dx%d", gi, d.mx, d.mz);
-        v.plane = ok1 && ok2 ? (mixed ? 0 : 1) : (ok1 ? 1 : 2);
-        if (ok1 && ok2 && (cfg->plane == 1 || cfg->plane == 2)) v.plane = cfg->plane;
+        v.plane = navail == 1 ? (ok[1] ? 1 : ok[2] ? 2 : 3) : (mixed ? 0 : 1);
+        if (navail > 1 && cfg->plane >= 1 && cfg->plane <= 3 && ok[cfg->plane]) v.plane = cfg->plane;
         if (precision_mixed(h)) {
             size_t m1 = dnsk::helm_t_smem_bytes(v), m2 = dnsk::yderiv_t_smem_bytes(v), m3 = dnsk::forcing_t_smem_bytes(v);
             size_t mm = m1 > m2 ? m1 : m2;
@@ -476,6 +500,7 @@ int dns_bind_workspace(dns_handle* h, void* dev_ptr, size_t bytes) {
     dnsk::set_attributes_gemm_t();
     dnsk::set_attributes_yderiv_tc();
     dnsk::set_attributes_plane_cl();
+    dnsk::set_attributes_plane_lines();
     {
         int rc0 = check(h, cudaGetLastError(), "kernel attributes");
         if (rc0) return rc0;
@@ -528,13 +553,15 @@ int dns_bind_workspace(dns_handle* h, void* dev_ptr, size_t bytes) {
         const std::string key = tune_plane_key(v);
         int choice = cache_lookup(h->cfg.autotune_cache, key);
         if (!choice) {
-            float best[3] = {0.f, 0.f, 0.f};
+            float best[4] = {0.f, 0.f, 0.f, 0.f};
             cudaEvent_t e0, e1;
             cudaEventCreate(&e0);
             cudaEventCreate(&e1);
-            for (int cand = 1; cand <= 2; ++cand) {
+            for (int cand = 1; cand <= 3; ++cand) {
+                if (!plane_variant_ok(true, v, cand)) continue;
                 auto run = [&]() {
                     if (cand == 2) dnsk::launch_plane_cl(v, false, v.U_t, v.W_t, st);
+                    else if (cand == 3) dnsk::launch_plane_lines(v, v.U_t, v.W_t, st);
                     else dnsk::launch_plane_f32(v, v.U_t, v.W_t, st);
                 };
                 for (int w = 0; w < 2; ++w) run();
@@ -549,8 +576,10 @@ int dns_bind_workspace(dns_handle* h, void* dev_ptr, size_t bytes) {
             cudaEventDestroy(e0);
             cudaEventDestroy(e1);
             if (rc) return rc;
-            choice = best[2] < best[1] ? 2 : 1;
-            cache_store(h->cfg.autotune_cache, key, choice, best[1], best[2]);
+            choice = 0;
+            for (int cand = 1; cand <= 3; ++cand)
+                if (best[cand] > 0.f && (choice == 0 || best[cand] < best[choice])) choice = cand;
+            cache_store(h->cfg.autotune_cache, key, choice, best, 3);
         }
         v.plane = choice;
     }
@@ -583,7 +612,7 @@ int dns_bind_workspace(dns_handle* h, void* dev_ptr, size_t bytes) {
             if (rc) return rc;
             if ((rc = device_status(h))) return rc;
             choice = best[2] < best[1] ? 2 : 1;
-            cache_store(h->cfg.autotune_cache, key, choice, best[1], best[2]);
+            cache_store(h->cfg.autotune_cache, key, choice, best, 2);
         }
         v.ygemm = choice;
     }

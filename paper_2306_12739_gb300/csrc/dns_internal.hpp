@@ -20,7 +20,8 @@ struct GroupView {
     int rp;               // Ny rounded up to a multiple of 4 (row padding of transposed operators)
     int kp;               // Ny rounded up to a multiple of 16 (K of the tensor-core y-contraction)
     int ygemm;            // mixed path y-derivatives: 1 register-tiled FP32, 2 tcgen05 split-BF16
-    int plane;            // plane stage: 1 single-CTA kernel, 2 cluster kernel (0 = autotune)
+    int plane;            // plane stage: 1 single-CTA kernel, 2 cluster kernel, 3 line-owned
+                          // single-CTA kernel (mixed path); 0 = autotune
     const void* Atc;      // tensor-core A image: [D1_int; D2_int] in 3 BF16 pieces
     int* status;          // device error word (1: a bounded wait gave up)
     int flow;             // 0 Couette, 1 Poiseuille
@@ -98,6 +99,9 @@ size_t plane_smem_bytes(const GroupView& g, int elem_bytes);
 bool launch_plane_f32(const GroupView& g, const double* U, const double* W, cudaStream_t st);
 size_t plane_f32_smem_bytes(int mx, int mz);
 void set_attributes_plane_f32();
+bool launch_plane_lines(const GroupView& g, const double* U, const double* W, cudaStream_t st);
+size_t plane_lines_smem_bytes(int mx, int mz);
+void set_attributes_plane_lines();
 int plane_threads();
 
 }  // namespace dnsk

@@ -90,12 +90,12 @@ def mixed_errors(mixed, ref):
     return np.array(out)
 
 
-@pytest.mark.parametrize("ygemm", ["simt", "tc"])
-def test_mixed_matches_fp64_over_50_steps(ygemm):
+@pytest.mark.parametrize("ygemm,plane", [("simt", "cta"), ("tc", "cta"), ("tc", "lines")])
+def test_mixed_matches_fp64_over_50_steps(ygemm, plane):
     g = group("couette", 32, 49, 32, 1.75 * np.pi, 1.2 * np.pi, 500.0, 0.01, 8)
     st = _state(g, 3000, 5e-2, n_max=4, m_max=4)
     a = _run(g, st, 50, "fp64")
-    b = _run(g, st, 50, "mixed", ygemm=ygemm)
+    b = _run(g, st, 50, "mixed", ygemm=ygemm, plane=plane)
     err = mixed_errors(b, a)
     assert np.all(err[:, :3] < 1e-6), err
     assert np.all(err[:, 3] < 1e-5), err
@@ -182,12 +182,13 @@ def test_laminar_states_stay_steady_on_gpu():
         assert np.abs(got[0]).max() == 0.0
 
 
-@pytest.mark.parametrize("mx,mz", [(16, 16), (16, 64), (64, 16), (48, 32), (32, 48), (64, 64), (48, 48)])
-def test_mixed_matches_fp64_for_every_plane_shape(mx, mz):
+@pytest.mark.parametrize("plane", ["cta", "lines"])
+@pytest.mark.parametrize("mx,mz", [(a, b) for a in (16, 32, 48, 64) for b in (16, 32, 48, 64)])
+def test_mixed_matches_fp64_for_every_plane_shape(mx, mz, plane):
     g = group("poiseuille", mx, 33, mz, 2 * np.pi, np.pi, 1650.0, 0.005, 3)
     st = _state(g, 31, 5e-2)
     a = _run(g, st, 10, "fp64")
-    b = _run(g, st, 10, "mixed")
+    b = _run(g, st, 10, "mixed", plane=plane)
     err = mixed_errors(b, a)
     assert np.all(err[:, :3] < 1e-6), err
     assert np.all(err[:, 3] < 1e-5), err
@@ -253,8 +254,8 @@ def test_fp64_cluster_plane_kernel_matches_oracle_on_128_grids(mx, mz):
         assert rel(a, b) < 1e-12, (name, rel(a, b))
 
 
-@pytest.mark.parametrize("plane", ["cta", "cluster"])
-def test_both_64x64_plane_kernels_match_fp64(plane):
+@pytest.mark.parametrize("plane", ["cta", "cluster", "lines"])
+def test_every_64x64_plane_kernel_matches_fp64(plane):
     g = group("poiseuille", 64, 33, 64, 2 * np.pi, np.pi, 1650.0, 0.005, 3)
     st = _state(g, 17, 5e-2)
     ref = _run(g, st, 5, "fp64")
