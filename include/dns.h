@@ -208,6 +208,15 @@ int dns_step_timed(dns_handle* h, int nsteps, double* ms, int* launches);
  * DNS_ERR_TIMEOUT (the context stays usable).  Synchronises. */
 int dns_selftest_timeout(dns_handle* h);
 
+/* Host run of the integer-operation binary64 <-> binary32 conversions the
+ * mixed-precision kernels apply to the FP64 state (the same source code the
+ * device compiles): f_out[i] = d_in[i] rounded to nearest even (magnitudes
+ * below 2^-126 give a signed zero), d_out[i] = f_in[i] exactly (binary32
+ * subnormals give a signed zero).  Host pointers, n >= 0 elements each; no
+ * handle, no device access.  No counterpart in the paper: it exists so the
+ * conversions can be checked without a GPU. */
+int dns_convert_selftest(const double* d_in, float* f_out, const float* f_in, double* d_out, long long n);
+
 /* Host copies of what dns_create built, for inspection and tests; no device
  * access, valid before a workspace is bound.
  * dns_export_grid: y [My], D1 [My*My], D2 [My*My], D4c [(My-2)^2] and the

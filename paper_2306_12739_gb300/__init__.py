@@ -34,7 +34,8 @@ DNS_PREC_FP64, DNS_PREC_MIXED = 0, 1
 EXPORTED = ["dns_create", "dns_workspace_size", "dns_bind_workspace", "dns_state_shape",
             "dns_set_state", "dns_get_state", "dns_step", "dns_stats", "dns_destroy",
             "dns_last_error", "dns_last_launch_count", "dns_export_grid", "dns_export_operators",
-            "dns_step_timed", "dns_stats_noalloc", "dns_selftest_timeout", "dns_kernel_choice"]
+            "dns_step_timed", "dns_stats_noalloc", "dns_selftest_timeout", "dns_kernel_choice",
+            "dns_convert_selftest"]
 KERNEL_CLASSES = ["mean_deriv", "yderiv", "plane", "forcing", "helm", "mean"]
 
 
@@ -77,6 +78,7 @@ _lib.dns_last_launch_count.argtypes = [_H]
 _lib.dns_step_timed.argtypes = [_H, ctypes.c_int, _dp, ctypes.POINTER(ctypes.c_int)]
 _lib.dns_stats_noalloc.argtypes = [_H, ctypes.c_int, _vp]
 _lib.dns_selftest_timeout.argtypes = [_H]
+_lib.dns_convert_selftest.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_longlong]
 _lib.dns_kernel_choice.argtypes = [_H, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
 _lib.dns_export_grid.argtypes = [_H, ctypes.c_int, _dp, _dp, _dp, _dp, _dp]
 _lib.dns_export_operators.argtypes = [_H, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp]
@@ -164,6 +166,22 @@ def dns_selftest_timeout(h):
     """Runs a bounded device wait that must give up; returns the status code
     (DNS_ERR_TIMEOUT expected) without raising."""
     return _lib.dns_selftest_timeout(h)
+
+
+def convert_selftest(d_in, f_in):
+    """Host run of the library's integer binary64 -> binary32 (round to nearest
+    even) and binary32 -> binary64 conversions; returns (f_out, d_out)."""
+    import numpy as np
+    d_in = np.ascontiguousarray(d_in, dtype=np.float64)
+    f_in = np.ascontiguousarray(f_in, dtype=np.float32)
+    assert d_in.shape == f_in.shape
+    f_out = np.empty_like(f_in)
+    d_out = np.empty_like(d_in)
+    rc = _lib.dns_convert_selftest(d_in.ctypes.data, f_out.ctypes.data, f_in.ctypes.data, d_out.ctypes.data,
+                                   d_in.size)
+    if rc != DNS_OK:
+        raise DnsError(rc, "dns_convert_selftest")
+    return f_out, d_out
 
 
 def dns_kernel_choice(h, group, which="ygemm"):

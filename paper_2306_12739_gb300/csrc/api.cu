@@ -5,6 +5,7 @@
 #include "../../include/dns.h"
 #include "builder.hpp"
 #include "dns_internal.hpp"
+#include "cvt.cuh"
 
 #include <cstdio>
 #include <cstring>
@@ -805,6 +806,22 @@ int dns_selftest_timeout(dns_handle* h) {
     if (rc) return rc;
     if ((rc = check(h, cudaStreamSynchronize(h->stream), "selftest"))) return rc;
     return device_status(h);
+}
+
+int dns_convert_selftest(const double* d_in, float* f_out, const float* f_in, double* d_out, long long n) {
+    if (n < 0 || (n > 0 && (!d_in || !f_out || !f_in || !d_out))) return DNS_ERR_INVALID;
+    for (long long i = 0; i < n; ++i) {
+        unsigned long long b;
+        std::memcpy(&b, &d_in[i], 8);
+        const unsigned fb = dnsk::d2f_bits((unsigned)(b >> 32), (unsigned)b);
+        std::memcpy(&f_out[i], &fb, 4);
+        unsigned fi, hi, lo;
+        std::memcpy(&fi, &f_in[i], 4);
+        dnsk::f2d_bits(fi, &hi, &lo);
+        b = ((unsigned long long)hi << 32) | lo;
+        std::memcpy(&d_out[i], &b, 8);
+    }
+    return DNS_OK;
 }
 
 int dns_destroy(dns_handle* h) {

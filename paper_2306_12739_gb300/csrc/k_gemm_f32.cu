@@ -10,6 +10,7 @@
 //               (increment form of Eqs. CN1, CN2); the pair's operators arrive
 //               by one TMA bulk copy (cp.async.bulk + mbarrier) per CTA.
 #include "dns_internal.hpp"
+#include "cvt.cuh"
 #include "mean.cuh"
 
 namespace dnsk {
@@ -23,13 +24,21 @@ struct Tile {
     int QT, EBT, NC;   // NC = QT * EBT complex columns
 };
 
-__host__ __device__ inline Tile tile_of(int E, int ny) {
-    const int cap = ny <= 96 ? 64 : 32;    // complex columns per tile
+// Up to 64 complex columns per tile (32 for tall operators), halved down to 16
+// while the grid would hold fewer than three CTAs per SM (152 SMs) and a tile
+// still spans several modes (member runs are not split).
+__host__ __device__ inline Tile tile_of(int E, int ny, int nm) {
+    int cap = ny <= 96 ? 64 : 32;
     Tile t;
-    t.EBT = E < cap ? E : cap;
-    t.QT = cap / t.EBT;
-    if (t.QT < 1) t.QT = 1;
-    t.NC = t.QT * t.EBT;
+    for (;;) {
+        t.EBT = E < cap ? E : cap;
+        t.QT = cap / t.EBT;
+        if (t.QT < 1) t.QT = 1;
+        t.NC = t.QT * t.EBT;
+        const long long ctas = (long long)((nm + t.QT - 1) / t.QT) * ((E + t.EBT - 1) / t.EBT);
+        if (cap <= 16 || ctas >= 3 * 152 || t.QT < 2) break;
+        cap /= 2;
+    }
     return t;
 }
 
@@ -39,7 +48,7 @@ __global__ void __launch_bounds__(THREADS) k_yderiv_t(GroupView g, const double2
                                                      const double2* __restrict__ H) {
     extern __shared__ __align__(16) unsigned char sm[];
     const int Ny = g.ny, RP = g.rp, E = g.E, NM = g.nmodes;
-    const Tile T = tile_of(E, Ny);
+    const Tile T = tile_of(E, Ny, NM);
     const int q0 = blockIdx.x * T.QT, e0 = blockIdx.y * T.EBT;
     const int NCR = 2 * T.NC;                       // real columns
     float* D1 = (float*)sm;                         // [Ny][RP]
@@ -117,7 +126,7 @@ __global__ void __launch_bounds__(THREADS) k_yderiv_t(GroupView g, const double2
 __global__ void __launch_bounds__(THREADS) k_forcing_t(GroupView g, int s) {
     extern __shared__ __align__(16) unsigned char sm[];
     const int Ny = g.ny, RP = g.rp, E = g.E, NM = g.nmodes, NKX = g.nkx;
-    const Tile T = tile_of(E, Ny);
+    const Tile T = tile_of(E, Ny, NM);
     const int q0 = blockIdx.x * T.QT, e0 = blockIdx.y * T.EBT;
     const int NCR = 2 * T.NC;
     float* D1 = (float*)sm;              // [Ny][RP]
@@ -140,7 +149,7 @@ __global__ void __launch_bounds__(THREADS) k_forcing_t(GroupView g, int s) {
                 const float2 nu = N3[o], nv = N3[fs + o], nw = N3[2 * fs + o];
                 const int mi = q / NKX, n = q - mi * NKX;
                 const float kx = g.kxtf[n], kz = g.kztf[mi];
-                const float k2 = (float)g.k2t[q];
+                const float k2 = kx * kx + kz * kz;
                 const float ax = kx * nu.x + kz * nw.x, ay = kx * nu.y + kz * nw.y;   // i kx Nu + i kz Nw
                 ph = make_float2(-ay, ax);
                 const float bx = kz * nu.x - kx * nw.x, by = kz * nu.y - kx * nw.y;   // i kz Nu - i kx Nw
@@ -269,7 +278,7 @@ __global__ void __launch_bounds__(THREADS) k_helm_t(GroupView g, int s) {
         const int k = r / (2 * E), c = r - k * (2 * E);
         const int q = which == 0 ? q1 : q2;
         const size_t o = (size_t)q * per + r;
-        if (needM) Xs[k * NC + which * 2 * E + c] = (float)((const double*)X)[o];
+        if (needM) Xs[k * NC + which * 2 * E + c] = d2f(((const double*)X)[o]);
         Fs[k * NC + which * 2 * E + c] = F[o];
     }
     __syncthreads();
@@ -304,25 +313,28 @@ __global__ void __launch_bounds__(THREADS) k_helm_t(GroupView g, int s) {
         const int q = which == 0 ? q1 : q2;
         const float rp[2][4] = {{pa.x, pa.y, pa.z, pa.w}, {pb.x, pb.y, pb.z, pb.w}};
         const float rm[2][4] = {{ma.x, ma.y, ma.z, ma.w}, {mb.x, mb.y, mb.z, mb.w}};
+        // x+ = x_t + ((M - I) x_t + P F~): the increment in single precision, one
+        // double add; (M_1 - I) x_t of sub-step 2 is kept (single precision) for
+        // sub-step 3.  In sub-step 3 the output overwrites x_t element by element.
         const double* xg = (const double*)(X + (size_t)q * Ny * E);
-        double* m1 = (double*)(M1 + (size_t)q * Ny * E);
+        float* m1 = (float*)(M1 + (size_t)q * Ny * E);
         double* og = (double*)(O + (size_t)q * Ny * E);
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const int y = r0 + i;
             if (y >= Ny) break;
             const int o = y * 2 * E + cl;
-            double base0, base1;
+            float d0, d1;
             if (needM) {
-                base0 = xg[o] + (double)rm[0][i];
-                base1 = xg[o + 1] + (double)rm[1][i];
-                if (s == 1) { m1[o] = base0; m1[o + 1] = base1; }
+                d0 = rm[0][i];
+                d1 = rm[1][i];
+                if (s == 1) { m1[o] = d0; m1[o + 1] = d1; }
             } else {
-                base0 = m1[o];
-                base1 = m1[o + 1];
+                d0 = m1[o];
+                d1 = m1[o + 1];
             }
-            og[o] = base0 + (double)rp[0][i];
-            og[o + 1] = base1 + (double)rp[1][i];
+            og[o] = xg[o] + f2d(d0 + rp[0][i]);
+            og[o + 1] = xg[o + 1] + f2d(d1 + rp[1][i]);
         }
     }
 }
@@ -352,23 +364,23 @@ size_t helm_t_smem_bytes(const GroupView& g) {
 }
 
 size_t yderiv_t_smem_bytes(const GroupView& g) {
-    gt::Tile t = gt::tile_of(g.E, g.ny);
+    gt::Tile t = gt::tile_of(g.E, g.ny, g.nmodes);
     return (2 * (size_t)g.ny * g.rp + 2 * (size_t)g.ny * 2 * t.NC) * sizeof(float);
 }
 
 size_t forcing_t_smem_bytes(const GroupView& g) {
-    gt::Tile t = gt::tile_of(g.E, g.ny);
+    gt::Tile t = gt::tile_of(g.E, g.ny, g.nmodes);
     return ((size_t)g.ny * g.rp + 3 * (size_t)g.ny * 2 * t.NC) * sizeof(float);
 }
 
 void launch_yderiv_t(const GroupView& g, const double2* v, const double2* e, cudaStream_t st) {
-    gt::Tile t = gt::tile_of(g.E, g.ny);
+    gt::Tile t = gt::tile_of(g.E, g.ny, g.nmodes);
     dim3 grid((g.nmodes + t.QT - 1) / t.QT, (g.E + t.EBT - 1) / t.EBT);
     gt::k_yderiv_t<<<grid, gt::THREADS, yderiv_t_smem_bytes(g), st>>>(g, v, e);
 }
 
 void launch_forcing_t(const GroupView& g, int s, cudaStream_t st) {
-    gt::Tile t = gt::tile_of(g.E, g.ny);
+    gt::Tile t = gt::tile_of(g.E, g.ny, g.nmodes);
     dim3 grid((g.nmodes + t.QT - 1) / t.QT, (g.E + t.EBT - 1) / t.EBT);
     gt::k_forcing_t<<<grid, gt::THREADS, forcing_t_smem_bytes(g), st>>>(g, s);
 }

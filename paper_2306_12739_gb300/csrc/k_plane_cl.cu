@@ -18,6 +18,8 @@
 // atomics: the plane means are combined in a fixed order by rank 0.
 #include "dns_internal.hpp"
 #include "dft.cuh"
+#include "ff.cuh"
+#include <type_traits>
 #include <cooperative_groups.h>
 
 namespace cg = cooperative_groups;
@@ -57,8 +59,8 @@ struct Cfg {
     static constexpr size_t B_S = B_F + CB * AF;                         // C [NF][SSP]
     static constexpr size_t B_TW = B_S + CB * NF * SSP;                  // C [MX + MZ]
     static constexpr size_t B_K = B_TW + CB * (MX + MZ);                 // T [NKX + NKZ + NKZ*NKL]
-    static constexpr size_t B_RED = ((B_K + TB * (NKX + NKZ + NKZ * NKL)) + 15) / 16 * 16;  // double [32 + 2 CL]
-    static constexpr size_t BYTES = B_RED + sizeof(double) * (32 + 2 * CL);
+    static constexpr size_t B_RED = ((B_K + TB * (NKX + NKZ + NKZ * NKL)) + 15) / 16 * 16;  // double [64 + 2 CL]
+    static constexpr size_t BYTES = B_RED + sizeof(double) * (64 + 2 * CL);
     // two CTAs per SM where shared memory allows it (registers capped to match)
     static constexpr int MINB = (2 * BYTES <= 227 * 1024 && NT <= 512) ? 2 : 1;
     static_assert(HP % CL == 0, "line pairs must split evenly over the cluster");
@@ -98,7 +100,7 @@ k_plane_cl(GroupView g, const double* __restrict__ Ucur, const double* __restric
     T* kxs = (T*)(smem + K::B_K);
     T* kzs = kxs + NKX;
     T* k2s = kzs + NKZ;                       // [NKZ][NKL]
-    double* red = (double*)(smem + K::B_RED); // [32] block reductions, then [2 CL] cluster partials
+    double* red = (double*)(smem + K::B_RED); // [64] block reductions, then [2 CL] cluster partials
 
     // ---- stage the owned columns of the five spectral inputs and the tables
     {
@@ -368,21 +370,31 @@ k_plane_cl(GroupView g, const double* __restrict__ Ucur, const double* __restric
     // plane means <uv>, <wv>: per-rank partial sums, combined by rank 0 in rank order
     {
         double s1 = 0.0, s2 = 0.0;
-        for (int i = tid; i < PL; i += NT) {
-            s1 += (double)PU[i] * (double)PV[i];
-            s2 += (double)PW[i] * (double)PV[i];
+        if constexpr (std::is_same<T, float>::value) {
+            // single precision: float-float sums (the FP64 pipe is slow)
+            float h1 = 0.f, l1 = 0.f, h2 = 0.f, l2 = 0.f;
+            for (int i = tid; i < PL; i += NT) {
+                ff_add_prod(h1, l1, PU[i], PV[i]);
+                ff_add_prod(h2, l2, PW[i], PV[i]);
+            }
+            ff_block_sum2(h1, l1, h2, l2, (float*)red, &s1, &s2);
+        } else {
+            for (int i = tid; i < PL; i += NT) {
+                s1 += (double)PU[i] * (double)PV[i];
+                s2 += (double)PW[i] * (double)PV[i];
+            }
+            s1 = block_sum(s1, red);
+            s2 = block_sum(s2, red);
         }
-        s1 = block_sum(s1, red);
-        s2 = block_sum(s2, red);
         if (tid == 0) {
-            double* dst = cluster.map_shared_rank(red + 32, 0);
+            double* dst = cluster.map_shared_rank(red + 64, 0);
             dst[2 * rk] = s1;
             dst[2 * rk + 1] = s2;
         }
         cluster.sync();
         if (rk == 0 && tid == 0) {
             double a = 0.0, b = 0.0;
-            for (int r = 0; r < CL; ++r) { a += red[32 + 2 * r]; b += red[32 + 2 * r + 1]; }
+            for (int r = 0; r < CL; ++r) { a += red[64 + 2 * r]; b += red[64 + 2 * r + 1]; }
             g.uv[(size_t)e * My + y + 1] = a / (double)(MX * MZ);
             g.wv[(size_t)e * My + y + 1] = b / (double)(MX * MZ);
         }

@@ -11,6 +11,7 @@
 //     transformed together, and the three derivative planes are folded into the
 //     advective sum in one elementwise pass in a fixed order (deterministic).
 #include "dns_internal.hpp"
+#include "ff.cuh"
 
 namespace dnsk {
 
@@ -116,7 +117,7 @@ struct Cfg {
     static constexpr size_t B_TW = B_S + sizeof(float2) * NF * SSP;       // float2 [MX + MZ]
     static constexpr size_t B_K = B_TW + sizeof(float2) * (MX + MZ);      // float [NKX + NKZ + NM]
     static constexpr size_t B_RED = ((B_K + sizeof(float) * (NKX + NKZ + NM)) + 15) / 16 * 16;
-    static constexpr size_t BYTES = B_RED + 32 * sizeof(double);
+    static constexpr size_t BYTES = B_RED + 64 * sizeof(double);
 };
 
 template <int MX, int MZ>
@@ -400,13 +401,14 @@ k_plane_f32(GroupView g, const double* __restrict__ Ucur, const double* __restri
     inverse3(0, 1, 2, 0, -1);
     // plane means <uv>, <wv>
     {
-        double s1 = 0.0, s2 = 0.0;
+        // float-float sums (the FP64 pipe is slow)
+        float h1 = 0.f, l1 = 0.f, h2 = 0.f, l2 = 0.f;
         for (int i = tid; i < PLANE; i += NT) {
-            s1 += (double)PU[i] * (double)PV[i];
-            s2 += (double)PW[i] * (double)PV[i];
+            ff_add_prod(h1, l1, PU[i], PV[i]);
+            ff_add_prod(h2, l2, PW[i], PV[i]);
         }
-        s1 = block_sum(s1, red);
-        s2 = block_sum(s2, red);
+        double s1 = 0.0, s2 = 0.0;
+        ff_block_sum2(h1, l1, h2, l2, (float*)red, &s1, &s2);
         if (tid == 0) {
             g.uv[(size_t)e * My + y + 1] = s1 / (double)PLANE;
             g.wv[(size_t)e * My + y + 1] = s2 / (double)PLANE;

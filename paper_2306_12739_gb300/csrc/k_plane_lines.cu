@@ -23,6 +23,9 @@
 // rows are chosen so that a warp's shared accesses fall in distinct banks.
 #include "dns_internal.hpp"
 #include "dft.cuh"
+#include "ff.cuh"
+#include <type_traits>
+
 
 namespace dnsk {
 
@@ -33,6 +36,28 @@ typedef float2 C;
 
 __device__ __forceinline__ C f2(float a, float b) { return make_float2(a, b); }
 __device__ __forceinline__ C conjf2(C a) { return make_float2(a.x, -a.y); }
+
+// compile-time loop: f(std::integral_constant<int, I>) for I = B .. E-1
+template <int B, int E> struct SFor {
+    template <typename F> __device__ __forceinline__ static void run(F& f) {
+        f(std::integral_constant<int, B>());
+        SFor<B + 1, E>::run(f);
+    }
+};
+template <int E> struct SFor<E, E> {
+    template <typename F> __device__ __forceinline__ static void run(F&) {}
+};
+
+// asynchronous global -> shared copies (completion awaited with cp_async_wait)
+__device__ __forceinline__ void cp_async8(void* sdst, const void* gsrc) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* sdst, const void* gsrc) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 constexpr int rup(int a, int b) { return (a + b - 1) / b * b; }
 // smallest v >= a with v % m == r
@@ -89,6 +114,7 @@ struct LCfg {
     static constexpr size_t BYTES = B_RED + (2 + 2 * 32) * sizeof(double);
     static constexpr int MINB = (2 * (BYTES + 1024) <= 228 * 1024 && NT * 2 * 64 <= 65536) ? 2 : 1;
     static_assert(MZ % 8 == 0, "z-row permutation works in blocks of eight");
+    static_assert(X2 - 1 <= KX && Z2 - 1 <= KZ, "first DFT slot lies in the kept band");
 };
 
 template <int MX, int MZ>
@@ -125,61 +151,54 @@ k_plane_lines(GroupView g, const double* __restrict__ Ucur, const double* __rest
     const size_t fs = (size_t)Ny * E * NM;
     const size_t off0 = ((size_t)y * E + e) * NM;
 
-    // ---- stage inputs [f][m][n] (padded rows) and tables
+    // ---- stage inputs [f][m][n] (padded rows) and tables, all copies in flight at once
     {
         const C* P = (const C*)g.P5;
         for (int i = tid; i < 5 * NM; i += NT) {
             const int f = i / NM, q = i - f * NM, mi = q / NKX, n = q - mi * NKX;
-            BASE[f * FSB + mi * NKXB + n] = P[f * fs + off0 + q];
+            cp_async8(BASE + f * FSB + mi * NKXB + n, P + f * fs + off0 + q);
         }
-        for (int i = tid; i < MX; i += NT) twx[i] = g.twxf[i];
-        for (int i = tid; i < MZ; i += NT) twz[i] = g.twzf[i];
-        for (int i = tid; i < NKX; i += NT) kxs[i] = g.kxtf[i];
-        for (int i = tid; i < NKZ; i += NT) kzs[i] = g.kztf[i];
+        for (int i = tid; i < MX; i += NT) cp_async8(twx + i, g.twxf + i);
+        for (int i = tid; i < MZ; i += NT) cp_async8(twz + i, g.twzf + i);
+        for (int i = tid; i < NKX; i += NT) cp_async4(kxs + i, g.kxtf + i);
+        for (int i = tid; i < NKZ; i += NT) cp_async4(kzs + i, g.kztf + i);
         for (int q = tid; q < NM; q += NT) {
             const int mi = q / NKX;
-            k2s[mi * NKXB + q - mi * NKX] = g.k2invf[q];
+            cp_async4(k2s + mi * NKXB + q - mi * NKX, g.k2invf + q);
         }
     }
     const float Um = (float)Ucur[(size_t)e * My + y + 1];
     const float Wm = (float)Wcur[(size_t)e * My + y + 1];
     mean_dy_row(g.D1, Ucur + (size_t)e * My, Wcur + (size_t)e * My, My, y + 1, red);
+    cp_async_wait();
     __syncthreads();
     const float dUm = (float)red[0];
     const float dWm = (float)red[1];
 
     // spectral value at mode (mi, n) of u_comp (kind 0), d_y u_comp (kind 1)
     // or d_z u_comp (kind 2); u, w from v, eta as u = i (kx Dv - kz eta) / k^2,
-    // w = i (kz Dv + kx eta) / k^2, the (0, 0) mode from the mean flow
+    // w = i (kz Dv + kx eta) / k^2 (d_y: D2v, D eta in place of Dv, eta), the
+    // (0, 0) mode from the mean flow.  Loads and selects only, no divergence
+    // on the mode.
     auto gen = [&](int kind, int comp, int mi, int n) -> C {
         const C* B = BASE + mi * NKXB + n;
-        const bool mean = (mi == KZ && n == 0);
-        if (kind == 1) {
-            if (comp == 1) return B[FSB];
-            if (mean) return f2(comp == 0 ? dUm : dWm, 0.f);
-            const float kx = kxs[n], kz = kzs[mi], ki = k2s[mi * NKXB + n];
-            const C d2 = B[2 * FSB], de = B[4 * FSB];
-            float ax, ay;
-            if (comp == 0) { ax = (kx * d2.x - kz * de.x) * ki; ay = (kx * d2.y - kz * de.y) * ki; }
-            else { ax = (kz * d2.x + kx * de.x) * ki; ay = (kz * d2.y + kx * de.y) * ki; }
-            return f2(-ay, ax);
-        }
-        C b;
-        if (comp == 1) {
-            b = B[0];
-        } else if (mean) {
-            b = f2(comp == 0 ? Um : Wm, 0.f);
-        } else {
-            const float kx = kxs[n], kz = kzs[mi], ki = k2s[mi * NKXB + n];
-            const C dv = B[FSB], et = B[3 * FSB];
-            float ax, ay;
-            if (comp == 0) { ax = (kx * dv.x - kz * et.x) * ki; ay = (kx * dv.y - kz * et.y) * ki; }
-            else { ax = (kz * dv.x + kx * et.x) * ki; ay = (kz * dv.y + kx * et.y) * ki; }
-            b = f2(-ay, ax);
-        }
-        if (kind == 0) return b;
         const float kz = kzs[mi];
-        return f2(-kz * b.y, kz * b.x);
+        C r;
+        if (comp == 1) {
+            r = kind == 1 ? B[FSB] : B[0];
+        } else {
+            const float kx = kxs[n], ki = k2s[mi * NKXB + n];
+            const C a = kind == 1 ? B[2 * FSB] : B[FSB];
+            const C b = kind == 1 ? B[4 * FSB] : B[3 * FSB];
+            float ax, ay;
+            if (comp == 0) { ax = (kx * a.x - kz * b.x) * ki; ay = (kx * a.y - kz * b.y) * ki; }
+            else { ax = (kz * a.x + kx * b.x) * ki; ay = (kz * a.y + kx * b.y) * ki; }
+            r = f2(-ay, ax);
+            const float mv = kind == 1 ? (comp == 0 ? dUm : dWm) : (comp == 0 ? Um : Wm);
+            if (mi == KZ && n == 0) r = f2(mv, 0.f);
+        }
+        if (kind == 2) r = f2(-kz * r.y, kz * r.x);
+        return r;
     };
 
     // ---- phase 1: z transforms, line (f, n), f = 3 kind + comp
@@ -193,12 +212,23 @@ k_plane_lines(GroupView g, const double* __restrict__ Ucur, const double* __rest
             const int kind = f / 3, comp = f - 3 * kind;
             if (act && t < Z2) {
                 C v[Z1];
-#pragma unroll
-                for (int n1 = 0; n1 < Z1; ++n1) {
-                    const int z = Z2 * n1 + t;
-                    const int mi = z <= KZ ? z + KZ : (z >= MZ - KZ ? z - MZ + KZ : -1);
-                    v[n1] = mi >= 0 ? gen(kind, comp, mi, n) : f2(0.f, 0.f);
-                }
+                // slot n1 holds z = Z2 n1 + t: blocks of slots wholly inside the
+                // kept band or the padding are resolved at compile time
+                auto ld = [&](auto ic) {
+                    constexpr int n1 = decltype(ic)::value, z0 = Z2 * n1, z1 = z0 + Z2 - 1;
+                    constexpr bool lo = z1 <= KZ, hi = z0 >= MZ - KZ, pad = z0 > KZ && z1 < MZ - KZ;
+                    if constexpr (pad) {
+                        v[n1] = f2(0.f, 0.f);
+                    } else {
+                        const int z = z0 + t;
+                        const bool in_lo = lo || (!hi && z <= KZ);
+                        const bool keep = lo || hi || z <= KZ || z >= MZ - KZ;
+                        const int mi = keep ? (in_lo ? z + KZ : z - MZ + KZ) : KZ;
+                        const C r = gen(kind, comp, mi, n);
+                        v[n1] = keep ? r : f2(0.f, 0.f);
+                    }
+                };
+                SFor<0, Z1>::run(ld);
                 Dft<Z1, +1, C>::run(v);
 #pragma unroll
                 for (int k1 = 0; k1 < Z1; ++k1) X[k1 * ZR + t] = k1 == 0 ? v[0] : mul(v[k1], conjf2(twz[t * k1]));
@@ -226,23 +256,27 @@ k_plane_lines(GroupView g, const double* __restrict__ Ucur, const double* __rest
         const C* A1 = src + zrow<MX, MZ>(p + HP) * S;
         if (act && t < X2) {
             C v[X1];
-#pragma unroll
-            for (int n1 = 0; n1 < X1; ++n1) {
-                const int k = X2 * n1 + t;
-                C Z = f2(0.f, 0.f);
-                if (k == 0) {
-                    if (!dx) Z = f2(A0[0].x, A1[0].x);          // Hermitian part of the kx = 0 column
-                } else if (k <= KX) {
-                    C a = A0[k], b = A1[k];
-                    if (dx) { const float kx = kxs[k]; a = f2(-kx * a.y, kx * a.x); b = f2(-kx * b.y, kx * b.x); }
-                    Z = f2(a.x - b.y, a.y + b.x);               // a + i b
-                } else if (k >= MX - KX) {
-                    C a = A0[MX - k], b = A1[MX - k];
-                    if (dx) { const float kx = kxs[MX - k]; a = f2(-kx * a.y, kx * a.x); b = f2(-kx * b.y, kx * b.x); }
-                    Z = f2(a.x + b.y, b.x - a.y);               // conj(a) + i conj(b)
+            // slot n1 holds k = X2 n1 + t; the line is a + i b with a, b the two
+            // rows: a_k + i b_k for k <= Kx, conj(a) + i conj(b) at Mx - k, the
+            // Hermitian part (Re a_0, Re b_0) at k = 0 (and 0 for d_x)
+            auto ld = [&](auto ic) {
+                constexpr int n1 = decltype(ic)::value, k0 = X2 * n1, k1 = k0 + X2 - 1;
+                constexpr bool lo = k1 <= KX, hi = k0 >= MX - KX, pad = k0 > KX && k1 < MX - KX;
+                if constexpr (pad) {
+                    v[n1] = f2(0.f, 0.f);
+                } else {
+                    const int k = k0 + t;
+                    const bool in_lo = lo || (!hi && k <= KX);
+                    const bool keep = lo || hi || k <= KX || k >= MX - KX;
+                    const int kc = keep ? (in_lo ? k : MX - k) : 0;
+                    C a = A0[kc], b = A1[kc];
+                    if (dx) { const float kx = kxs[kc]; a = f2(-kx * a.y, kx * a.x); b = f2(-kx * b.y, kx * b.x); }
+                    C Z = in_lo ? f2(a.x - b.y, a.y + b.x) : f2(a.x + b.y, b.x - a.y);
+                    if (n1 == 0 && t == 0) Z = f2(a.x, b.x);
+                    v[n1] = keep ? Z : f2(0.f, 0.f);
                 }
-                v[n1] = Z;
-            }
+            };
+            SFor<0, X1>::run(ld);
             Dft<X1, +1, C>::run(v);
 #pragma unroll
             for (int k1 = 0; k1 < X1; ++k1) X[k1 * XR + t] = k1 == 0 ? v[0] : mul(v[k1], conjf2(twx[t * k1]));
@@ -278,8 +312,9 @@ k_plane_lines(GroupView g, const double* __restrict__ Ucur, const double* __rest
     }
     __syncthreads();
 
-    // ---- phase 2b: products and forward x transforms, line pair (i, p)
-    double s_uv = 0.0, s_wv = 0.0;
+    // ---- phase 2b: products and forward x transforms, line pair (i, p); the
+    // groups of component 0 also sum u v, those of component 2 w v (float-float)
+    float uv_hi = 0.f, uv_lo = 0.f, wv_hi = 0.f, wv_lo = 0.f;
     const float sx = 1.0f / MX;
     for (int u0 = warp * UX; u0 < K::NU2; u0 += K::NSX) {
         const int u = u0 + gx;
@@ -302,15 +337,19 @@ k_plane_lines(GroupView g, const double* __restrict__ Ucur, const double* __rest
                 }
             }
         }
-        if (act && tx < X1 && i == 0) {
-            const float* pu = PLN + p;
-            const float* pv = pu + MX * MZP;
-            const float* pw = pv + MX * MZP;
+        if (act && tx < X1 && i != 1) {
+            const float* pa = PLN + i * MX * MZP + p;     // u or w
+            const float* pv = PLN + MX * MZP + p;
 #pragma unroll
             for (int k2 = 0; k2 < X2; ++k2) {
                 const int o0 = (tx + X1 * k2) * MZP, o1 = o0 + HP;
-                s_uv += (double)pu[o0] * (double)pv[o0] + (double)pu[o1] * (double)pv[o1];
-                s_wv += (double)pw[o0] * (double)pv[o0] + (double)pw[o1] * (double)pv[o1];
+                if (i == 0) {
+                    ff_add_prod(uv_hi, uv_lo, pa[o0], pv[o0]);
+                    ff_add_prod(uv_hi, uv_lo, pa[o1], pv[o1]);
+                } else {
+                    ff_add_prod(wv_hi, wv_lo, pa[o0], pv[o0]);
+                    ff_add_prod(wv_hi, wv_lo, pa[o1], pv[o1]);
+                }
             }
         }
         // forward x transform from the registers: x = tx + X1 k2, K = K1 + X2 K2
@@ -344,22 +383,14 @@ k_plane_lines(GroupView g, const double* __restrict__ Ucur, const double* __rest
         }
         __syncwarp();
     }
-    // plane means: warp sums, then a fixed-order sum over warps
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        s_uv += __shfl_xor_sync(0xffffffffu, s_uv, o);
-        s_wv += __shfl_xor_sync(0xffffffffu, s_wv, o);
-    }
-    if (lane == 0) {
-        red[2 + 2 * warp] = s_uv;
-        red[3 + 2 * warp] = s_wv;
-    }
-    __syncthreads();
-    if (tid == 0) {
-        double a = 0.0, b = 0.0;
-        for (int w = 0; w < K::NW; ++w) { a += red[2 + 2 * w]; b += red[3 + 2 * w]; }
-        g.uv[(size_t)e * My + y + 1] = a / (double)K::PLANE;
-        g.wv[(size_t)e * My + y + 1] = b / (double)K::PLANE;
+    // plane means <uv>, <wv>
+    {
+        double suv = 0.0, swv = 0.0;
+        ff_block_sum2(uv_hi, uv_lo, wv_hi, wv_lo, (float*)red, &suv, &swv);
+        if (tid == 0) {
+            g.uv[(size_t)e * My + y + 1] = suv / (double)K::PLANE;
+            g.wv[(size_t)e * My + y + 1] = swv / (double)K::PLANE;
+        }
     }
 
     // ---- phase 3: forward z transforms of the kept columns, truncation

@@ -100,3 +100,39 @@ def test_library_operators_equal_oracle_operators(dns, flow, mx, my, mz, lx, lz,
                         assert np.array_equal(a, b[ch.Kz + am, n])
     finally:
         dns.dns_destroy(h)
+
+
+def test_integer_pipe_conversions_round_like_ieee(dns):
+    """The mixed-precision kernels convert their FP64 state with integer
+    operations (binary64 -> binary32 round to nearest even; binary32 ->
+    binary64 exact); the host run of the same code must agree with IEEE
+    conversions on random values over the whole normal range, on exact ties in
+    both directions, and on signed zeros, infinities and NaN; magnitudes below
+    2^-126 flush to signed zero."""
+    import numpy as np
+    rng = np.random.default_rng(7)
+    n = 200000
+    mant = rng.uniform(1.0, 2.0, n)
+    expo = rng.integers(-125, 127, n)
+    d = np.ldexp(mant, expo) * rng.choice([-1.0, 1.0], n)
+    # exact ties: a binary32 value plus half an ulp, with even and odd last bits
+    base = np.float32(rng.uniform(1.0, 2.0, 5000)).astype(np.float64)
+    ulp = np.spacing(np.float32(base)).astype(np.float64)
+    ties = np.concatenate([base + 0.5 * ulp, -(base + 0.5 * ulp), base + 0.5 * ulp * (1 + 2 ** -20)])
+    special = np.array([0.0, -0.0, np.inf, -np.inf, 3.4e38, -3.4e38, 1.1754943508222875e-38,
+                        np.finfo(np.float32).max.astype(np.float64), 1e-300, -1e-300, 2.0 ** -127])
+    d = np.concatenate([d, ties, special])
+    f = np.float32(rng.standard_normal(d.size)) * np.float32(10.0) ** rng.integers(-30, 30, d.size).astype(np.float32)
+    f[:4] = [0.0, -0.0, np.inf, -np.inf]
+    f_out, d_out = dns.convert_selftest(d, f)
+    with np.errstate(over="ignore"):
+        ref = d.astype(np.float32)
+    tiny = np.abs(d) < 2.0 ** -126
+    ref[tiny] = np.copysign(np.float32(0.0), d[tiny]).astype(np.float32)
+    assert np.array_equal(f_out.view(np.uint32), ref.view(np.uint32))
+    ref_d = f.astype(np.float64)
+    sub = (np.abs(f) < np.finfo(np.float32).tiny) & (f != 0)
+    ref_d[sub] = np.copysign(0.0, f[sub])
+    assert np.array_equal(d_out.view(np.uint64), ref_d.view(np.uint64))
+    fn, _ = dns.convert_selftest(np.array([np.nan]), np.array([np.nan], dtype=np.float32))
+    assert np.isnan(fn[0])

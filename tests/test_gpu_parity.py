@@ -223,23 +223,29 @@ def test_tensor_core_y_derivatives_match_fp64(mx, my, mz, E):
 
 
 def test_autotuner_picks_a_variant_caches_it_and_matches_that_variant(tmp_path):
+    """Both autotuned choices of a 32x32 mixed group (plane-stage kernel and
+    y-contraction) are timed once, written to the cache, read back without new
+    timing, and the step is bit-identical to requesting those variants."""
     g = group("poiseuille", 32, 33, 32, 2 * np.pi, np.pi, 1650.0, 0.005, 8)
     st = _state(g, 5, 5e-2)
     cache = str(tmp_path / "tune.txt")
     ens = dns.Ensemble([g], precision="mixed", autotune_cache=cache)
     choice = dns.dns_kernel_choice(ens.h, 0)
-    assert choice in ("simt", "tc")
+    plane = dns.dns_kernel_choice(ens.h, 0, "plane")
+    assert choice in ("simt", "tc") and plane in ("cta", "lines")
     ens.set_state(0, st["v"], st["eta"], st["U"], st["W"])
     ens.step(3)
     got = ens.get_state(0)
     ens.close()
-    lines = [ln for ln in open(cache) if ln.strip()]
-    assert len(lines) == 1 and lines[0].startswith("ygemm 32 33 32 8 ")
+    lines = sorted(ln for ln in open(cache) if ln.strip())
+    assert len(lines) == 2
+    assert lines[0].startswith("plane 32 33 32 8 ") and lines[1].startswith("ygemm 32 33 32 8 ")
     ens2 = dns.Ensemble([g], precision="mixed", autotune_cache=cache)   # read back, no new timing
     assert dns.dns_kernel_choice(ens2.h, 0) == choice
+    assert dns.dns_kernel_choice(ens2.h, 0, "plane") == plane
     ens2.close()
-    assert len([ln for ln in open(cache) if ln.strip()]) == 1
-    ref = _run(g, st, 3, "mixed", ygemm=choice)
+    assert len([ln for ln in open(cache) if ln.strip()]) == 2
+    ref = _run(g, st, 3, "mixed", ygemm=choice, plane=plane)
     for a, b in zip(got, ref):
         assert np.array_equal(a, b)
 
