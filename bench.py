@@ -185,14 +185,17 @@ def kernel_work(cls, g, precision):
     return "alu", E * 4.0 * (g["my"]) ** 2, "flop"
 
 
-def profiled_traffic(kernel):
-    """DRAM bytes per launch of `kernel` from the committed ncu record, or None
-    when the kernel's sources changed since the counters were taken."""
+def profiled_traffic(kernel, variant):
+    """DRAM bytes per launch of kernel class `kernel` (variant `variant`) from
+    the committed ncu record, or None when the record is of another variant or
+    the kernel's sources changed since the counters were taken."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "traffic_poiseuille64x65x64_E8_mixed.json")
     try:
         rec = json.load(open(path))["kernels"][kernel]
     except (OSError, KeyError, ValueError):
+        return None
+    if rec.get("variant") != variant:
         return None
     h = hashlib.sha256()
     for f in rec["source_files"]:
@@ -353,7 +356,9 @@ def gpu_arm(args, rank, world, dist):
     sm_mhz = clocks["sm_mhz"] or 2070.0
     peak = alu_peak(kprec, sm_mhz)
     achieved = work / (kt[dom][0] / 1e3) / 1e12
-    traffic = profiled_traffic(dom) if (precision == "mixed" and args.workload == "poiseuille64") else None
+    variant = {"plane": choices[0]["plane"], "yderiv": choices[0]["ygemm"]}.get(dom, "simt")
+    traffic = (profiled_traffic(dom, variant)
+               if (precision == "mixed" and args.workload == "poiseuille64") else None)
     roofline = {"kernel": dom, "bound": bound, "precision": kprec, "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
                 "traffic_unit": "DRAM bytes per launch (ncu, profiles/)",
@@ -427,8 +432,8 @@ def gpu_arm(args, rank, world, dist):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
     ap.add_argument("--no-cpu-baseline", action="store_true")
