@@ -307,7 +307,8 @@ def gpu_arm(args, rank, world, dist):
             ens.set_state(gi, st["v"], st["eta"], st["U"], st["W"])
 
     def timed_run(prec, nsteps, nwarm, flush):
-        ens = dns.Ensemble(groups, precision=prec, use_graph=True, device=dev, ygemm=args.ygemm, plane=args.plane)
+        ens = dns.Ensemble(groups, precision=prec, use_graph=True, device=dev, ygemm=args.ygemm, plane=args.plane,
+                           helm=args.helm)
         load(ens)
         stream = ens.stream
         ens.step(nwarm)
@@ -336,8 +337,8 @@ def gpu_arm(args, rank, world, dist):
 
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
     ens, total_ms, launches, clocks = timed_run(precision, args.steps, args.warmup, flush)
-    choices = [dict(ygemm=dns.dns_kernel_choice(ens.h, gi, "ygemm"), plane=dns.dns_kernel_choice(ens.h, gi, "plane"))
-               for gi in range(len(groups))]
+    choices = [dict(ygemm=dns.dns_kernel_choice(ens.h, gi, "ygemm"), plane=dns.dns_kernel_choice(ens.h, gi, "plane"),
+                    helm=dns.dns_kernel_choice(ens.h, gi, "helm")) for gi in range(len(groups))]
     total_ms = reduce_max(total_ms, dist, dev)
     ms_step = total_ms / args.steps
     value = aggregate(members * args.steps, total_ms / 1e3, world)
@@ -356,7 +357,7 @@ def gpu_arm(args, rank, world, dist):
     sm_mhz = clocks["sm_mhz"] or 2070.0
     peak = alu_peak(kprec, sm_mhz)
     achieved = work / (kt[dom][0] / 1e3) / 1e12
-    variant = {"plane": choices[0]["plane"], "yderiv": choices[0]["ygemm"]}.get(dom, "simt")
+    variant = {"plane": choices[0]["plane"], "yderiv": choices[0]["ygemm"], "helm": choices[0]["helm"]}.get(dom, "simt")
     traffic = (profiled_traffic(dom, variant)
                if (precision == "mixed" and args.workload == "poiseuille64") else None)
     roofline = {"kernel": dom, "bound": bound, "precision": kprec, "achieved": achieved, "peak": peak,
@@ -399,6 +400,7 @@ def gpu_arm(args, rank, world, dist):
         "data": "synthetic (seeded, dns_synth)",
         "config": {"workload": wl["name"], "precision": precision, "graph": True,
                    "kernels": choices, "ygemm_request": args.ygemm, "plane_request": args.plane,
+                   "helm_request": args.helm,
                    "l2": "flushed (256 MiB write) before every timed step", "parallelism": "replicas x%d" % world},
         "grid_pts_steps_per_s": aggregate(pts * args.steps, total_ms / 1e3, world),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
@@ -440,6 +442,8 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparator run")
     ap.add_argument("--plane", choices=["default", "cta", "cluster", "lines"], default="default",
                     help="plane-stage kernel (default: autotuned among those the grid supports)")
+    ap.add_argument("--helm", choices=["default", "simt", "tc"], default="default",
+                    help="implicit-apply variant of the mixed path (default: autotuned)")
     ap.add_argument("--ygemm", choices=["default", "simt", "tc"], default="default",
                     help="y-contraction variant of the mixed path")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="poiseuille64",

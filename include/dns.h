@@ -86,7 +86,8 @@ typedef struct {
     int persistent;                /* reserved, must be 0 */
     unsigned long long barrier_timeout_ns;  /* reserved, 0 */
     const char* autotune_cache;    /* optional text file: autotuner decisions are read from it
-                                      and appended to it ("ygemm Mx My Mz E choice"); NULL = none */
+                                      and appended to it ("ygemm|plane|helm Mx My Mz E choice");
+                                      NULL = none */
     int ygemm;                     /* mixed path y-derivatives: 0 autotuned at dns_bind_workspace
                                       (both variants timed on the bound workspace, the faster
                                       kept), 1 register-tiled FP32, 2 tcgen05 tensor cores with
@@ -99,6 +100,10 @@ typedef struct {
                                       per plane with each 1-D transform owned by one group of
                                       threads (mixed precision, sizes <= 64); a request for a
                                       variant the group's size lacks is ignored */
+    int helm;                      /* mixed path implicit apply: 0 autotuned at
+                                      dns_bind_workspace, 1 register-tiled FP32, 2 tcgen05 tensor
+                                      cores with split-BF16 operands (groups with My <= 66 and
+                                      <= 64 members; others always use 1) */
 } dns_config;
 
 /* One-point statistics of one member (paper Sec. 4), computed from the current
@@ -178,9 +183,9 @@ const char* dns_last_error(const dns_handle* h);
 /* Kernel variants `group` uses, after the autotuner ran (i.e. after
  * dns_bind_workspace): ygemm 1 register-tiled FP32 / 2 tcgen05 y-contraction;
  * plane 1 one CTA per plane / 2 a thread-block cluster per plane / 3 line-owned
- * single CTA per plane.  Either
- * output may be NULL. */
-int dns_kernel_choice(const dns_handle* h, int group, int* ygemm, int* plane);
+ * single CTA per plane; helm 1 register-tiled FP32 / 2 tcgen05 implicit apply.
+ * Any output may be NULL. */
+int dns_kernel_choice(const dns_handle* h, int group, int* ygemm, int* plane, int* helm);
 
 /* Number of kernel launches enqueued by the last dns_step call (all steps). */
 int dns_last_launch_count(const dns_handle* h);

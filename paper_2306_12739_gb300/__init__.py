@@ -50,7 +50,7 @@ class dns_config(ctypes.Structure):
     _fields_ = [("n_groups", ctypes.c_int), ("groups", ctypes.POINTER(dns_group_desc)),
                 ("precision", ctypes.c_int), ("use_graph", ctypes.c_int), ("persistent", ctypes.c_int),
                 ("barrier_timeout_ns", ctypes.c_ulonglong), ("autotune_cache", ctypes.c_char_p),
-                ("ygemm", ctypes.c_int), ("plane", ctypes.c_int)]
+                ("ygemm", ctypes.c_int), ("plane", ctypes.c_int), ("helm", ctypes.c_int)]
 
 
 class dns_stats_t(ctypes.Structure):
@@ -79,7 +79,8 @@ _lib.dns_step_timed.argtypes = [_H, ctypes.c_int, _dp, ctypes.POINTER(ctypes.c_i
 _lib.dns_stats_noalloc.argtypes = [_H, ctypes.c_int, _vp]
 _lib.dns_selftest_timeout.argtypes = [_H]
 _lib.dns_convert_selftest.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_longlong]
-_lib.dns_kernel_choice.argtypes = [_H, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+_lib.dns_kernel_choice.argtypes = [_H, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                   ctypes.POINTER(ctypes.c_int)]
 _lib.dns_export_grid.argtypes = [_H, ctypes.c_int, _dp, _dp, _dp, _dp, _dp]
 _lib.dns_export_operators.argtypes = [_H, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp]
 
@@ -185,11 +186,14 @@ def convert_selftest(d_in, f_in):
 
 
 def dns_kernel_choice(h, group, which="ygemm"):
-    """'ygemm' -> 'simt' | 'tc'; 'plane' -> 'cta' | 'cluster' | 'lines'."""
-    c, p = ctypes.c_int(), ctypes.c_int()
-    _ck(h, _lib.dns_kernel_choice(h, group, ctypes.byref(c), ctypes.byref(p)))
+    """'ygemm' -> 'simt' | 'tc'; 'plane' -> 'cta' | 'cluster' | 'lines';
+    'helm' -> 'simt' | 'tc'."""
+    c, p, m = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _ck(h, _lib.dns_kernel_choice(h, group, ctypes.byref(c), ctypes.byref(p), ctypes.byref(m)))
     if which == "plane":
         return {1: "cta", 2: "cluster", 3: "lines"}.get(p.value, p.value)
+    if which == "helm":
+        return {1: "simt", 2: "tc"}.get(m.value, m.value)
     return {1: "simt", 2: "tc"}.get(c.value, c.value)
 
 
@@ -231,7 +235,8 @@ _YGEMM = {"default": 0, "auto": 0, "simt": 1, "tc": 2}
 _PLANE = {"default": 0, "auto": 0, "cta": 1, "cluster": 2, "lines": 3}
 
 
-def make_config(groups, precision="fp64", use_graph=False, ygemm="default", autotune_cache=None, plane="default"):
+def make_config(groups, precision="fp64", use_graph=False, ygemm="default", autotune_cache=None, plane="default",
+                helm="default"):
     """groups: list of dicts with flow, mx, my, mz, lx, lz, re, dt, members,
     optional u_wall (1.0) and bulk_flux (4/3)."""
     arr = (dns_group_desc * len(groups))()
@@ -240,7 +245,7 @@ def make_config(groups, precision="fp64", use_graph=False, ygemm="default", auto
                                 g["dt"], g.get("u_wall", 1.0), g.get("bulk_flux", 4.0 / 3.0), g["members"])
     cache = autotune_cache.encode() if autotune_cache else None
     cfg = dns_config(len(groups), arr, _PRECS[precision], 1 if use_graph else 0, 0, 0, cache, _YGEMM[ygemm],
-                     _PLANE[plane])
+                     _PLANE[plane], _YGEMM[helm])
     cfg._keep = (arr, cache)
     return cfg
 
@@ -249,14 +254,14 @@ class Ensemble:
     """Owns a handle, its torch workspace and the stream it runs on."""
 
     def __init__(self, groups, precision="fp64", use_graph=False, device="cuda:0", stream=None, ygemm="default",
-                 autotune_cache=None, plane="default"):
+                 autotune_cache=None, plane="default", helm="default"):
         import torch
         self.torch = torch
         self.device = torch.device(device)
         self.groups = [dict(g) for g in groups]
         # a stream of its own: graph capture is not allowed on the legacy default stream
         self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
-        self.cfg = make_config(groups, precision, use_graph, ygemm, autotune_cache, plane)
+        self.cfg = make_config(groups, precision, use_graph, ygemm, autotune_cache, plane, helm)
         self.h = dns_create(self.cfg, self.stream.cuda_stream)
         nbytes = dns_workspace_size(self.h)
         self.ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)

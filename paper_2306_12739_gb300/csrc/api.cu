@@ -25,7 +25,7 @@ struct HostGroup {
     dnsb::CnOps ops[2];
     std::vector<double> kxt, kzt, k2t, k2inv, twx, twz, opsdev[2], mopsdev[2], D1i, D2i;
     std::vector<float> kxtf, kztf, k2invf, twxf, twzf, opsf[2], opsfT[2], D1T, D2T;
-    std::vector<uint16_t> Atc;
+    std::vector<uint16_t> Atc, Htc[2];
     // byte offsets inside the workspace
     struct Off { size_t off, bytes; };
     std::vector<std::pair<void**, Off>> slots;
@@ -117,6 +117,7 @@ size_t layout_group(dns_handle* h, HostGroup& G, size_t cur) {
         add((void**)&v.ops[hi], sizeof(double) * (size_t)v.npairs * 4 * nn);
         if (precision_mixed(h)) {
             add((void**)&v.opsfT[hi], sizeof(float) * (size_t)v.npairs * 4 * v.ny * v.rp);
+            if (v.helm != 1) add((void**)&v.Htc[hi], (size_t)v.npairs * 2 * 3 * 64 * 2 * v.kp * sizeof(uint16_t));
         }
         add((void**)&v.mops[hi], sizeof(double) * (2 * nn + 3 * (size_t)v.ny + (size_t)v.ny * v.my));
     }
@@ -202,8 +203,12 @@ void enqueue_group(dns_handle* h, HostGroup& G, cudaStream_t st, Timer* tm) {
         mark(DNS_K_FORCING);
         // per-wavenumber implicit apply; the same launch carries the mean-flow
         // update as E extra CTAs (independent work that overlaps with it)
-        if (precision_mixed(h)) dnsk::launch_helm_t(g, s, st);
-        else dnsk::launch_helm(g, s, st);
+        if (precision_mixed(h)) {
+            if (g.helm == 2) dnsk::launch_helm_tc(g, s, st);
+            else dnsk::launch_helm_t(g, s, st);
+        } else {
+            dnsk::launch_helm(g, s, st);
+        }
         mark(DNS_K_HELM);
         h->launches += 4;
     }
@@ -254,6 +259,12 @@ bool plane_variant_ok(bool mixed, const GroupView& v, int c) {
     return false;
 }
 
+std::string tune_helm_key(const GroupView& v) {
+    char b[128];
+    snprintf(b, sizeof b, "helm %d %d %d %d", v.mx, v.my, v.mz, v.E);
+    return b;
+}
+
 std::string tune_plane_key(const GroupView& v) {
     char b[128];
     snprintf(b, sizeof b, "plane %d %d %d %d", v.mx, v.my, v.mz, v.E);
@@ -295,6 +306,7 @@ void cache_store(const char* path, const std::string& key, int choice, const flo
 
 namespace dnsk {
 std::vector<uint16_t> yderiv_tc_a_image(const std::vector<double>& D1i, const std::vector<double>& D2i, int ny, int kp);
+std::vector<uint16_t> helm_tc_a_images(const std::vector<double>& ops, int npairs, int ny, int kp);
 void launch_wait_selftest(int* status, cudaStream_t st);
 cudaError_t noalloc_scratch(double** out);
 size_t noalloc_max_partials();
@@ -355,6 +367,12 @@ int dns_create(const dns_config* cfg, void* cuda_stream, dns_handle** out) {
             if (cfg->ygemm == 2) v.ygemm = 2;
             else if (cfg->ygemm == 0) v.ygemm = 0;
         }
+        // implicit-apply variant: 1 register-tiled FP32, 2 tcgen05; 0 = autotuned
+        v.helm = 1;
+        if (precision_mixed(h) && dnsk::helm_tc_supported(v)) {
+            if (cfg->helm == 2) v.helm = 2;
+            else if (cfg->helm == 0) v.helm = 0;
+        }
         v.flow = d.flow == DNS_POISEUILLE ? 1 : 0;
         v.re = d.re; v.dt = d.dt; v.u_wall = d.u_wall; v.bulk_flux = d.bulk_flux;
         if (!make_plan(d.mx, &v.px) || !make_plan(d.mz, &v.pz))
@@ -372,6 +390,7 @@ int dns_create(const dns_config* cfg, void* cuda_stream, dns_handle** out) {
         if (navail > 1 && cfg->plane >= 1 && cfg->plane <= 3 && ok[cfg->plane]) v.plane = cfg->plane;
         if (precision_mixed(h)) {
             size_t m1 = dnsk::helm_t_smem_bytes(v), m2 = dnsk::yderiv_t_smem_bytes(v), m3 = dnsk::forcing_t_smem_bytes(v);
+            if (v.helm != 1 && dnsk::helm_tc_smem_bytes(v) > m1) m1 = dnsk::helm_tc_smem_bytes(v);
             size_t mm = m1 > m2 ? m1 : m2;
             mm = mm > m3 ? mm : m3;
             if (mm > 227 * 1024)
@@ -456,6 +475,8 @@ int dns_create(const dns_config* cfg, void* cuda_stream, dns_handle** out) {
                 G.D2T[(size_t)k * v.rp + r] = (float)G.D2i[(size_t)r * v.ny + k];
             }
         if (v.ygemm != 1) G.Atc = dnsk::yderiv_tc_a_image(G.D1i, G.D2i, v.ny, v.kp);
+        if (precision_mixed(h) && v.helm != 1)
+            for (int hi = 0; hi < 2; ++hi) G.Htc[hi] = dnsk::helm_tc_a_images(G.opsdev[hi], v.npairs, v.ny, v.kp);
         G.twx = dnsb::twiddles(d.mx);
         G.twz = dnsb::twiddles(d.mz);
         G.twxf.assign(G.twx.begin(), G.twx.end());
@@ -502,6 +523,7 @@ int dns_bind_workspace(dns_handle* h, void* dev_ptr, size_t bytes) {
     dnsk::set_attributes_yderiv_tc();
     dnsk::set_attributes_plane_cl();
     dnsk::set_attributes_plane_lines();
+    dnsk::set_attributes_helm_tc();
     {
         int rc0 = check(h, cudaGetLastError(), "kernel attributes");
         if (rc0) return rc0;
@@ -536,6 +558,8 @@ int dns_bind_workspace(dns_handle* h, void* dev_ptr, size_t bytes) {
             {v.opsfT[1], G.opsfT[1].data(), G.opsfT[1].size() * 4},
             {v.D1T, G.D1T.data(), G.D1T.size() * 4},
             {v.Atc, G.Atc.data(), G.Atc.size() * 2},
+            {v.Htc[0], G.Htc[0].data(), G.Htc[0].size() * 2},
+            {v.Htc[1], G.Htc[1].data(), G.Htc[1].size() * 2},
             {v.D2T, G.D2T.data(), G.D2T.size() * 4},
             {v.mops[0], G.mopsdev[0].data(), G.mopsdev[0].size() * 8},
             {v.mops[1], G.mopsdev[1].data(), G.mopsdev[1].size() * 8},
@@ -616,6 +640,41 @@ int dns_bind_workspace(dns_handle* h, void* dev_ptr, size_t bytes) {
             cache_store(h->cfg.autotune_cache, key, choice, best, 2);
         }
         v.ygemm = choice;
+    }
+    for (auto& G : h->groups) {
+        GroupView& v = G.v;
+        if (v.helm != 0) continue;
+        const std::string key = tune_helm_key(v);
+        int choice = cache_lookup(h->cfg.autotune_cache, key);
+        if (!choice) {
+            // the implicit apply is timed on sub-step 2 (both accumulators); it
+            // writes only the sub-step state, which set_state overwrites later
+            float best[3] = {0.f, 0.f, 0.f};
+            cudaEvent_t e0, e1;
+            cudaEventCreate(&e0);
+            cudaEventCreate(&e1);
+            for (int cand = 1; cand <= 2; ++cand) {
+                auto run = [&]() {
+                    if (cand == 2) dnsk::launch_helm_tc(v, 1, st);
+                    else dnsk::launch_helm_t(v, 1, st);
+                };
+                for (int w = 0; w < 2; ++w) run();
+                cudaEventRecord(e0, st);
+                for (int r = 0; r < 5; ++r) run();
+                cudaEventRecord(e1, st);
+                rc = check(h, cudaEventSynchronize(e1), "autotune helm");
+                if (rc) break;
+                cudaEventElapsedTime(&best[cand], e0, e1);
+                best[cand] /= 5.f;
+            }
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            if (rc) return rc;
+            if ((rc = device_status(h))) return rc;
+            choice = best[2] < best[1] ? 2 : 1;
+            cache_store(h->cfg.autotune_cache, key, choice, best, 2);
+        }
+        v.helm = choice;
     }
     h->bound = true;
     return DNS_OK;
@@ -838,10 +897,11 @@ int dns_destroy(dns_handle* h) {
 
 const char* dns_last_error(const dns_handle* h) { return h ? h->err.c_str() : "NULL handle"; }
 
-int dns_kernel_choice(const dns_handle* h, int group, int* ygemm, int* plane) {
+int dns_kernel_choice(const dns_handle* h, int group, int* ygemm, int* plane, int* helm) {
     if (!h || group < 0 || group >= (int)h->groups.size()) return DNS_ERR_INVALID;
     if (ygemm) *ygemm = h->groups[group].v.ygemm;
     if (plane) *plane = h->groups[group].v.plane;
+    if (helm) *helm = h->groups[group].v.helm;
     return DNS_OK;
 }
 

@@ -23,6 +23,8 @@ struct GroupView {
     int plane;            // plane stage: 1 single-CTA kernel, 2 cluster kernel, 3 line-owned
                           // single-CTA kernel (mixed path); 0 = autotune
     const void* Atc;      // tensor-core A image: [D1_int; D2_int] in 3 BF16 pieces
+    int helm;             // mixed path implicit apply: 1 register-tiled FP32, 2 tcgen05 (0 = autotune)
+    const void* Htc[2];   // per h index: [npairs][2 fields] images of [M - I | P] in 3 BF16 pieces
     int* status;          // device error word (1: a bounded wait gave up)
     int flow;             // 0 Couette, 1 Poiseuille
     double re, dt, u_wall, bulk_flux;
@@ -89,6 +91,10 @@ bool yderiv_tc_supported(const GroupView& g);
 size_t yderiv_tc_smem_bytes(const GroupView& g);
 void launch_yderiv_tc(const GroupView& g, const double2* v, const double2* e, cudaStream_t st);
 void set_attributes_yderiv_tc();
+bool helm_tc_supported(const GroupView& g);
+size_t helm_tc_smem_bytes(const GroupView& g);
+void launch_helm_tc(const GroupView& g, int s, cudaStream_t st);
+void set_attributes_helm_tc();
 bool launch_plane_cl(const GroupView& g, bool fp64, const double* U, const double* W, cudaStream_t st);
 size_t plane_cl_smem_bytes(int mx, int mz, bool fp64);
 void set_attributes_plane_cl();

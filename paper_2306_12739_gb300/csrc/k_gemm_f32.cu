@@ -181,6 +181,20 @@ __global__ void __launch_bounds__(THREADS) k_forcing_t(GroupView g, int s) {
         const int q = q0 + qq, e = e0 + el;
         if (q >= NM || e >= E) continue;
         const float rx[4] = {ax.x, ax.y, ax.z, ax.w}, ry[4] = {ay.x, ay.y, ay.z, ay.w};
+        // RK accumulators of the four rows loaded before any store
+        float2* Av = (float2*)g.Av;
+        float2* Ae = (float2*)g.Ae;
+        float2 pav[4], pae[4];
+        if (s != 0) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int y = r0 + i;
+                if (y >= Ny) break;
+                const size_t h = ((size_t)q * Ny + y) * E + e;
+                pav[i] = Av[h];
+                pae[i] = Ae[h];
+            }
+        }
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const int y = r0 + i;
@@ -194,20 +208,18 @@ __global__ void __launch_bounds__(THREADS) k_forcing_t(GroupView g, int s) {
             float2 G = gg;
             if (q == q_mean) { F = make_float2(0.f, 0.f); G = F; }
             const size_t h = ((size_t)q * Ny + y) * E + e;
-            float2* Av = (float2*)g.Av;
-            float2* Ae = (float2*)g.Ae;
             float2 Ft, Gt;
             if (s == 0) {
                 Ft = F; Gt = G;
                 Av[h] = F; Ae[h] = G;
             } else if (s == 1) {
-                const float2 a = Av[h], b = Ae[h];
+                const float2 a = pav[i], b = pae[i];
                 Ft = make_float2(2.f * F.x - a.x, 2.f * F.y - a.y);
                 Gt = make_float2(2.f * G.x - b.x, 2.f * G.y - b.y);
                 Av[h] = make_float2((1.f / 6.f) * a.x + (4.f / 6.f) * F.x, (1.f / 6.f) * a.y + (4.f / 6.f) * F.y);
                 Ae[h] = make_float2((1.f / 6.f) * b.x + (4.f / 6.f) * G.x, (1.f / 6.f) * b.y + (4.f / 6.f) * G.y);
             } else {
-                const float2 a = Av[h], b = Ae[h];
+                const float2 a = pav[i], b = pae[i];
                 Ft = make_float2(a.x + (1.f / 6.f) * F.x, a.y + (1.f / 6.f) * F.y);
                 Gt = make_float2(b.x + (1.f / 6.f) * G.x, b.y + (1.f / 6.f) * G.y);
             }
@@ -319,22 +331,33 @@ __global__ void __launch_bounds__(THREADS) k_helm_t(GroupView g, int s) {
         const double* xg = (const double*)(X + (size_t)q * Ny * E);
         float* m1 = (float*)(M1 + (size_t)q * Ny * E);
         double* og = (double*)(O + (size_t)q * Ny * E);
+        // all loads of the four rows first, then the stores (the output may be
+        // x_t itself, which would otherwise serialise the loads)
+        double x0[4], x1[4];
+        float d0[4], d1[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const int y = r0 + i;
             if (y >= Ny) break;
             const int o = y * 2 * E + cl;
-            float d0, d1;
+            x0[i] = xg[o];
+            x1[i] = xg[o + 1];
             if (needM) {
-                d0 = rm[0][i];
-                d1 = rm[1][i];
-                if (s == 1) { m1[o] = d0; m1[o + 1] = d1; }
+                d0[i] = rm[0][i];
+                d1[i] = rm[1][i];
             } else {
-                d0 = m1[o];
-                d1 = m1[o + 1];
+                d0[i] = m1[o];
+                d1[i] = m1[o + 1];
             }
-            og[o] = xg[o] + f2d(d0 + rp[0][i]);
-            og[o + 1] = xg[o + 1] + f2d(d1 + rp[1][i]);
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int y = r0 + i;
+            if (y >= Ny) break;
+            const int o = y * 2 * E + cl;
+            if (s == 1) { m1[o] = d0[i]; m1[o + 1] = d1[i]; }
+            og[o] = x0[i] + f2d(d0[i] + rp[0][i]);
+            og[o + 1] = x1[i] + f2d(d1[i] + rp[1][i]);
         }
     }
 }

@@ -78,15 +78,20 @@ __device__ __forceinline__ void ld16(unsigned taddr, float* v) {
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// Split x into three BF16 pieces x ~ h + m + l (each the rounding of what is
-// left).  The state is rounded to float once; three 8-bit pieces then hold its
-// 24-bit significand exactly, and the remainders are exact in float.
+// Split x into three BF16 pieces, x = h + m + l exactly: each piece keeps the
+// leading 8 significand bits of what is left (truncation, by masking the low
+// 16 bits), and each remainder is exact in float.  Integer masks and FP32
+// subtractions only: the float -> BF16 conversion instructions would issue to
+// the slow conversion pipe.
 __device__ __forceinline__ void split3(float x, __nv_bfloat16& h, __nv_bfloat16& m, __nv_bfloat16& l) {
-    h = __float2bfloat16_rn(x);
-    const float r1 = x - __bfloat162float(h);
-    m = __float2bfloat16_rn(r1);
-    const float r2 = r1 - __bfloat162float(m);
-    l = __float2bfloat16_rn(r2);
+    const unsigned ux = __float_as_uint(x) & 0xFFFF0000u;
+    const float r1 = x - __uint_as_float(ux);
+    const unsigned u1 = __float_as_uint(r1) & 0xFFFF0000u;
+    const float r2 = r1 - __uint_as_float(u1);
+    const unsigned u2 = __float_as_uint(r2) & 0xFFFF0000u;
+    h = __ushort_as_bfloat16((unsigned short)(ux >> 16));
+    m = __ushort_as_bfloat16((unsigned short)(u1 >> 16));
+    l = __ushort_as_bfloat16((unsigned short)(u2 >> 16));
 }
 
 struct Tile {
@@ -144,26 +149,42 @@ __global__ void __launch_bounds__(THREADS, 2) k_yderiv_tc(GroupView g, const dou
                      ::"r"(su32(A)), "l"(g.Atc), "r"(bytes), "r"(bar_a) : "memory");
     }
     // B: column n = f*(NCOL/2) + 2 j + c, j = qq*EBT + el (H order), rows k (interior y)
+    // each thread's tasks (8 consecutive k of one column): all global loads
+    // first, then the splits and the shared stores
     const int KC = KP / 8;
-    for (int i = threadIdx.x; i < NCOL * KC; i += THREADS) {
-        const int n = i % NCOL, kc = i / NCOL;
-        const int f = n / (NCOL / 2), r = n % (NCOL / 2), j = r >> 1, c = r & 1;
-        const int qq = j / T.EBT, el = j - qq * T.EBT;
-        const int q = q0 + qq, e = e0 + el;
-        const bool ok = (qq < T.QT) && (q < NM) && (e < E);
-        const double* src = (const double*)(f == 0 ? V : H);
-        __nv_bfloat16 hv[8], mv[8], lv[8];
+    constexpr int TPT = 4;
+    for (int i0 = threadIdx.x; i0 < NCOL * KC; i0 += THREADS * TPT) {
+        float xs[TPT][8];
 #pragma unroll
-        for (int t = 0; t < 8; ++t) {
-            const int k = kc * 8 + t;
-            float x = 0.f;
-            if (ok && k < Ny) x = (float)src[(((size_t)q * Ny + k) * E + e) * 2 + c];
-            split3(x, hv[t], mv[t], lv[t]);
+        for (int u = 0; u < TPT; ++u) {
+            const int i = i0 + u * THREADS;
+            const int n = i % NCOL, kc = i / NCOL;
+            const int f = n / (NCOL / 2), r = n % (NCOL / 2), j = r >> 1, c = r & 1;
+            const int qq = j / T.EBT, el = j - qq * T.EBT;
+            const int q = q0 + qq, e = e0 + el;
+            const bool ok = i < NCOL * KC && (qq < T.QT) && (q < NM) && (e < E);
+            const double* src = (const double*)(f == 0 ? V : H);
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+                const int k = kc * 8 + t;
+                float x = 0.f;
+                if (ok && k < Ny) x = (float)src[(((size_t)q * Ny + k) * E + e) * 2 + c];
+                xs[u][t] = x;
+            }
         }
-        const size_t off = (size_t)(n >> 3) * SBO + (size_t)kc * LBO + (size_t)(n & 7) * 16;
-        *(uint4*)(B + off) = *(const uint4*)hv;
-        *(uint4*)(B + pieceB + off) = *(const uint4*)mv;
-        *(uint4*)(B + 2 * pieceB + off) = *(const uint4*)lv;
+#pragma unroll
+        for (int u = 0; u < TPT; ++u) {
+            const int i = i0 + u * THREADS;
+            if (i >= NCOL * KC) break;
+            const int n = i % NCOL, kc = i / NCOL;
+            __nv_bfloat16 hv[8], mv[8], lv[8];
+#pragma unroll
+            for (int t = 0; t < 8; ++t) split3(xs[u][t], hv[t], mv[t], lv[t]);
+            const size_t off = (size_t)(n >> 3) * SBO + (size_t)kc * LBO + (size_t)(n & 7) * 16;
+            *(uint4*)(B + off) = *(const uint4*)hv;
+            *(uint4*)(B + pieceB + off) = *(const uint4*)mv;
+            *(uint4*)(B + 2 * pieceB + off) = *(const uint4*)lv;
+        }
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -240,16 +261,32 @@ __global__ void __launch_bounds__(THREADS, 2) k_yderiv_tc(GroupView g, const dou
         const int dst_field = fld == 0 ? 1 : (fld == 1 ? 2 : 4);
         P[dst_field * fs + ((size_t)y * E + e) * NM + q] = stage[((size_t)fld * 64 + y) * SROW + qq * T.EBT + el];
     }
-    // the fields themselves (rounded to float) in the same layout
-    for (int i = threadIdx.x; i < Ny * per; i += THREADS) {
-        const int y = i / per, r2 = i - y * per, el = r2 / T.QT, qq = r2 - el * T.QT;
-        const int q = q0 + qq, e = e0 + el;
-        if (q >= NM || e >= E) continue;
-        const size_t h = ((size_t)q * Ny + y) * E + e;
-        const double2 a = V[h], b = H[h];
-        const size_t o = ((size_t)y * E + e) * NM + q;
-        P[o] = make_float2((float)a.x, (float)a.y);
-        P[3 * fs + o] = make_float2((float)b.x, (float)b.y);
+    // the fields themselves (rounded to float) in the same layout; each thread
+    // loads its UNR elements before storing any
+    constexpr int UNR = 4;
+    for (int i0 = threadIdx.x; i0 < Ny * per; i0 += THREADS * UNR) {
+        double2 a[UNR], b[UNR];
+        size_t o[UNR];
+        bool in[UNR];
+#pragma unroll
+        for (int u = 0; u < UNR; ++u) {
+            const int i = i0 + u * THREADS;
+            const int y = i / per, r2 = i - y * per, el = r2 / T.QT, qq = r2 - el * T.QT;
+            const int q = q0 + qq, e = e0 + el;
+            in[u] = i < Ny * per && q < NM && e < E;
+            o[u] = ((size_t)y * E + e) * NM + q;
+            if (in[u]) {
+                const size_t h = ((size_t)q * Ny + y) * E + e;
+                a[u] = V[h];
+                b[u] = H[h];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < UNR; ++u)
+            if (in[u]) {
+                P[o[u]] = make_float2((float)a[u].x, (float)a[u].y);
+                P[3 * fs + o[u]] = make_float2((float)b[u].x, (float)b[u].y);
+            }
     }
 }
 

@@ -37,8 +37,8 @@ def _oracle(g):
     return oracle.Channel(g["mx"], g["my"], g["mz"], g["lx"], g["lz"], g["re"], g["dt"], g["flow"])
 
 
-def _run(g, st, nsteps, precision="fp64", use_graph=False, ygemm="default", plane="default"):
-    ens = dns.Ensemble([g], precision=precision, use_graph=use_graph, ygemm=ygemm, plane=plane)
+def _run(g, st, nsteps, precision="fp64", use_graph=False, ygemm="default", plane="default", helm="default"):
+    ens = dns.Ensemble([g], precision=precision, use_graph=use_graph, ygemm=ygemm, plane=plane, helm=helm)
     ens.set_state(0, st["v"], st["eta"], st["U"], st["W"])
     ens.step(nsteps)
     out = ens.get_state(0)
@@ -90,12 +90,13 @@ def mixed_errors(mixed, ref):
     return np.array(out)
 
 
-@pytest.mark.parametrize("ygemm,plane", [("simt", "cta"), ("tc", "cta"), ("tc", "lines")])
-def test_mixed_matches_fp64_over_50_steps(ygemm, plane):
+@pytest.mark.parametrize("ygemm,plane,helm", [("simt", "cta", "simt"), ("tc", "cta", "simt"), ("tc", "lines", "simt"),
+                                              ("tc", "lines", "tc")])
+def test_mixed_matches_fp64_over_50_steps(ygemm, plane, helm):
     g = group("couette", 32, 49, 32, 1.75 * np.pi, 1.2 * np.pi, 500.0, 0.01, 8)
     st = _state(g, 3000, 5e-2, n_max=4, m_max=4)
     a = _run(g, st, 50, "fp64")
-    b = _run(g, st, 50, "mixed", ygemm=ygemm, plane=plane)
+    b = _run(g, st, 50, "mixed", ygemm=ygemm, plane=plane, helm=helm)
     err = mixed_errors(b, a)
     assert np.all(err[:, :3] < 1e-6), err
     assert np.all(err[:, 3] < 1e-5), err
@@ -104,20 +105,24 @@ def test_mixed_matches_fp64_over_50_steps(ygemm, plane):
 def test_graph_replay_is_bitwise_equal_to_eager():
     g = group("poiseuille", 32, 33, 32, 2 * np.pi, np.pi, 1650.0, 0.005, 4)
     st = _state(g, 77, 5e-2)
+    pin = dict(ygemm="tc", plane="lines", helm="tc")      # separate handles: no autotuner choice in between
     for prec in ("fp64", "mixed"):
-        a = _run(g, st, 4, prec, use_graph=False)
-        b = _run(g, st, 4, prec, use_graph=True)
+        a = _run(g, st, 4, prec, use_graph=False, **pin)
+        b = _run(g, st, 4, prec, use_graph=True, **pin)
         for x, y in zip(a, b):
             assert np.array_equal(x, y)
 
 
-def test_member_alone_equals_member_in_batch():
+@pytest.mark.parametrize("precision,pin", [("fp64", {}),
+                                           ("mixed", dict(ygemm="tc", plane="lines", helm="tc")),
+                                           ("mixed", dict(ygemm="simt", plane="cta", helm="simt"))])
+def test_member_alone_equals_member_in_batch(precision, pin):
     g = group("couette", 32, 33, 32, 1.75 * np.pi, 1.2 * np.pi, 400.0, 0.01, 6)
     st = _state(g, 500, 5e-2)
-    full = _run(g, st, 3)
+    full = _run(g, st, 3, precision, **pin)
     g1 = dict(g, members=1)
     one = {k: st[k][4:5] for k in FIELDS}
-    alone = _run(g1, one, 3)
+    alone = _run(g1, one, 3, precision, **pin)
     for a, b in zip(full, alone):
         assert np.array_equal(a[4:5], b)
 
@@ -197,14 +202,15 @@ def test_mixed_matches_fp64_for_every_plane_shape(mx, mz, plane):
 def test_bounded_device_wait_reports_timeout_and_context_survives():
     g = group("couette", 16, 33, 16, 1.75 * np.pi, 1.2 * np.pi, 400.0, 0.01, 1)
     st = _state(g, 1000, 1e-2, n_max=2, m_max=2)
-    ens = dns.Ensemble([g], precision="mixed")
+    pin = dict(ygemm="tc", plane="lines", helm="tc")      # two handles: no autotuner choice in between
+    ens = dns.Ensemble([g], precision="mixed", **pin)
     ens.set_state(0, st["v"], st["eta"], st["U"], st["W"])
     assert dns.dns_selftest_timeout(ens.h) == dns.DNS_ERR_TIMEOUT
     assert "gave up" in dns.dns_last_error(ens.h)
     ens.step(2)                      # the context is still usable
     got = ens.get_state(0)
     ens.close()
-    ref = _run(g, st, 2, "mixed")
+    ref = _run(g, st, 2, "mixed", **pin)
     for a, b in zip(got, ref):
         assert np.array_equal(a, b)
 
@@ -223,8 +229,8 @@ def test_tensor_core_y_derivatives_match_fp64(mx, my, mz, E):
 
 
 def test_autotuner_picks_a_variant_caches_it_and_matches_that_variant(tmp_path):
-    """Both autotuned choices of a 32x32 mixed group (plane-stage kernel and
-    y-contraction) are timed once, written to the cache, read back without new
+    """The autotuned choices of a 32x32 mixed group (plane-stage kernel,
+    y-contraction, implicit apply) are timed once, written to the cache, read back without new
     timing, and the step is bit-identical to requesting those variants."""
     g = group("poiseuille", 32, 33, 32, 2 * np.pi, np.pi, 1650.0, 0.005, 8)
     st = _state(g, 5, 5e-2)
@@ -232,22 +238,42 @@ def test_autotuner_picks_a_variant_caches_it_and_matches_that_variant(tmp_path):
     ens = dns.Ensemble([g], precision="mixed", autotune_cache=cache)
     choice = dns.dns_kernel_choice(ens.h, 0)
     plane = dns.dns_kernel_choice(ens.h, 0, "plane")
-    assert choice in ("simt", "tc") and plane in ("cta", "lines")
+    helm = dns.dns_kernel_choice(ens.h, 0, "helm")
+    assert choice in ("simt", "tc") and plane in ("cta", "lines") and helm in ("simt", "tc")
     ens.set_state(0, st["v"], st["eta"], st["U"], st["W"])
     ens.step(3)
     got = ens.get_state(0)
     ens.close()
     lines = sorted(ln for ln in open(cache) if ln.strip())
-    assert len(lines) == 2
-    assert lines[0].startswith("plane 32 33 32 8 ") and lines[1].startswith("ygemm 32 33 32 8 ")
+    assert len(lines) == 3
+    assert lines[0].startswith("helm 32 33 32 8 ") and lines[1].startswith("plane 32 33 32 8 ")
+    assert lines[2].startswith("ygemm 32 33 32 8 ")
     ens2 = dns.Ensemble([g], precision="mixed", autotune_cache=cache)   # read back, no new timing
     assert dns.dns_kernel_choice(ens2.h, 0) == choice
     assert dns.dns_kernel_choice(ens2.h, 0, "plane") == plane
+    assert dns.dns_kernel_choice(ens2.h, 0, "helm") == helm
     ens2.close()
-    assert len([ln for ln in open(cache) if ln.strip()]) == 2
-    ref = _run(g, st, 3, "mixed", ygemm=choice, plane=plane)
+    assert len([ln for ln in open(cache) if ln.strip()]) == 3
+    ref = _run(g, st, 3, "mixed", ygemm=choice, plane=plane, helm=helm)
     for a, b in zip(got, ref):
         assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("mx,my,mz,E", [(32, 49, 32, 8), (16, 33, 16, 3), (32, 33, 32, 64), (48, 65, 48, 5),
+                                        (64, 65, 64, 2), (16, 21, 32, 33)])
+def test_tensor_core_implicit_apply_matches_fp64(mx, my, mz, E):
+    """tcgen05 implicit apply (split-BF16 operators and right-hand sides, FP32
+    accumulation, one FP64 add): odd and large member counts (column padding,
+    two column passes), the single-mode kx column pairs (m = 0), short and full
+    operator heights."""
+    g = group("poiseuille", mx, my, mz, 2 * np.pi, np.pi, 1650.0, 0.005, E)
+    st = _state(g, 71, 5e-2)
+    ref = _run(g, st, 10, "fp64")
+    ens = dns.Ensemble([g], precision="mixed", helm="tc")
+    assert dns.dns_kernel_choice(ens.h, 0, "helm") == "tc"
+    ens.close()
+    err = mixed_errors(_run(g, st, 10, "mixed", helm="tc"), ref)
+    assert np.all(err[:, :3] < 1e-6), err
 
 
 @pytest.mark.parametrize("mx,mz", [(128, 128), (128, 64), (64, 128)])
@@ -288,13 +314,13 @@ def test_uneven_batch_groups_match_each_group_run_alone(precision, use_graph):
           group("couette", 48, 49, 48, 1.75 * np.pi, 1.2 * np.pi, 800.0, 0.005, 2),
           group("poiseuille", 64, 65, 64, 2 * np.pi, np.pi, 1650.0, 0.005, 2)]
     sts = [_state(g, 4000 + 100 * i, np.linspace(1e-2, 5e-2, g["members"])) for i, g in enumerate(gs)]
-    ens = dns.Ensemble(gs, precision=precision, use_graph=use_graph, ygemm="simt", plane="cta")
+    ens = dns.Ensemble(gs, precision=precision, use_graph=use_graph, ygemm="simt", plane="cta", helm="tc")
     for i, st in enumerate(sts):
         ens.set_state(i, st["v"], st["eta"], st["U"], st["W"])
     ens.step(3)
     together = [ens.get_state(i) for i in range(len(gs))]
     ens.close()
     for g, st, tog in zip(gs, sts, together):
-        alone = _run(g, st, 3, precision, use_graph=True, ygemm="simt", plane="cta")
+        alone = _run(g, st, 3, precision, use_graph=True, ygemm="simt", plane="cta", helm="tc")
         for a, b in zip(tog, alone):
             assert np.array_equal(a, b)
