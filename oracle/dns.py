@@ -135,7 +135,15 @@ class Channel:
     """One group of ensemble members that share a grid, Re and dt."""
 
     def __init__(self, mx, my, mz, lx, lz, re, dt, flow="couette",
-                 u_wall=1.0, bulk_flux=4.0 / 3.0):
+                 u_wall=1.0, bulk_flux=4.0 / 3.0, shared_mean=False):
+        """shared_mean: the S3T-type ensemble of Sec. 5 (ensemble simulations of
+        statistical state dynamics): the members share their streamwise-mean
+        (kx = 0) flow, which every sub-step is driven by the kx = 0 part of the
+        nonlinear term and by the plane means <uv>, <wv> averaged over the
+        members (the perturbation Reynolds stresses averaged over the ensemble).
+        The caller gives every member the same kx = 0 part; it then stays
+        identical because every member receives the same kx = 0 forcing."""
+        self.shared_mean = shared_mean
         self.mx, self.my, self.mz = mx, my, mz
         self.lx, self.lz, self.re, self.dt = lx, lz, re, dt
         self.flow, self.u_wall, self.bulk_flux = flow, u_wall, bulk_flux
@@ -235,7 +243,14 @@ class Channel:
         uv = np.zeros((E, self.my)); wv = np.zeros((E, self.my))
         uv[:, 1:-1] = np.mean(p["u"] * p["v"], axis=(-2, -1))
         wv[:, 1:-1] = np.mean(p["w"] * p["v"], axis=(-2, -1))
-        return self.to_spectral(Nu), self.to_spectral(Nv), self.to_spectral(Nw), uv, wv
+        N = [self.to_spectral(Nu), self.to_spectral(Nv), self.to_spectral(Nw)]
+        if self.shared_mean:
+            # kx = 0 column and plane means: the average over the members
+            for a in N:
+                a[:, :, :, 0] = np.mean(a[:, :, :, 0], axis=0)[None]
+            uv = np.broadcast_to(np.mean(uv, axis=0), uv.shape).copy()
+            wv = np.broadcast_to(np.mean(wv, axis=0), wv.shape).copy()
+        return N[0], N[1], N[2], uv, wv
 
     def forcing(self, state):
         """F, G of Eqs. (Dv_F), (eta) and the mean forcings d/dy<uv>, d/dy<wv>

@@ -394,3 +394,81 @@ def test_energy_budget_residual_is_second_order_in_dt():
         res.append(abs(dEdt - rhs))
         assert abs(dEdt - rhs) < 1e-4 * abs(s0["dissipation"][0])
     assert res[0] / res[1] > 3.5 and res[1] / res[2] > 3.5
+
+
+# ------------------------------------------- shared-mean (S3T-type) ensemble
+
+def _with_shared_kx0(x):
+    """Every member gets the member average of the kx = 0 part (n = 0 column of
+    v, eta and the mean profiles U00, W00); the kx != 0 parts stay per member."""
+    v, eta, U, W = (np.array(a) for a in x)
+    for a in (v, eta):
+        a[:, :, :, 0] = a[:, :, :, 0].mean(axis=0)[None]
+    U[:] = U.mean(axis=0)[None]
+    W[:] = W.mean(axis=0)[None]
+    return (v, eta, U, W)
+
+
+@pytest.fixture(scope="module")
+def s3t_small():
+    args = (16, 33, 16, 2 * np.pi, 1.2 * np.pi, 1000.0, 0.01, "couette")
+    plain = oracle.Channel(*args)
+    shared = oracle.Channel(*args, shared_mean=True)
+    st = dns_synth.make_state(16, 33, 16, 2 * np.pi, 1.2 * np.pi, "couette", 3, 300, 5e-2)
+    return plain, shared, _with_shared_kx0(_state(st))
+
+
+def test_shared_mean_with_one_member_is_the_plain_step(s3t_small):
+    plain, shared, x = s3t_small
+    one = tuple(a[1:2] for a in x)
+    for a, b in zip(shared.step(one, 3), plain.step(one, 3)):
+        assert np.array_equal(a, b)
+
+
+def test_shared_mean_ensemble_of_copies_is_independent_members(s3t_small):
+    plain, shared, x = s3t_small
+    copies = tuple(np.repeat(a[1:2], 3, axis=0) for a in x)
+    for a, b in zip(shared.step(copies, 3), plain.step(copies, 3)):
+        assert np.abs(a - b).max() <= 1e-13 * max(np.abs(b).max(), 1e-300)
+
+
+def test_shared_mean_kx0_flow_stays_shared_and_moves(s3t_small):
+    """The kx = 0 flow of all members stays identical (bit for bit: every member
+    receives the same averaged forcing), it is driven away from its start, and
+    the kx != 0 parts remain different per member."""
+    plain, shared, x = s3t_small
+    y = shared.step(x, 4)
+    for a in (y[0], y[1]):
+        assert np.array_equal(a[0, :, :, 0], a[1, :, :, 0]) and np.array_equal(a[0, :, :, 0], a[2, :, :, 0])
+        assert np.abs(a[0, :, :, 1:] - a[1, :, :, 1:]).max() > 1e-6
+    assert np.array_equal(y[2][0], y[2][1]) and np.array_equal(y[2][0], y[2][2])
+    assert np.abs(y[0][0, :, :, 0] - x[0][0, :, :, 0]).max() > 1e-8
+    assert np.abs(y[2][0] - x[2][0]).max() > 1e-8
+
+
+def test_shared_mean_forcing_and_update_average_the_plain_ones(s3t_small):
+    """First sub-step: the shared-mean forcing of the kx = 0 modes (F, G and the
+    mean forcings) equals the member average of the plain forcing (the step is
+    linear in the nonlinear term), the kx != 0 forcing is the plain one, and by
+    linearity of the CN update the shared kx = 0 state after the sub-step is the
+    member average of the plain sub-step states."""
+    plain, shared, x = s3t_small
+    Fp = plain.forcing(x)
+    Fs = shared.forcing(x)
+    for p, s in zip(Fp[:2], Fs[:2]):
+        avg = p[:, :, :, 0].mean(axis=0)
+        scale = np.abs(avg).max()
+        assert scale > 0
+        for e in range(3):
+            assert np.abs(s[e, :, :, 0] - avg).max() <= 1e-13 * scale
+        assert np.array_equal(s[:, :, :, 1:], p[:, :, :, 1:])
+    for p, s in zip(Fp[2:], Fs[2:]):
+        avg = p.mean(axis=0)
+        assert np.abs(s - avg[None]).max() <= 1e-13 * max(np.abs(avg).max(), 1e-300)
+    up = plain.update(x, Fp, 0.5)
+    us = shared.update(x, Fs, 0.5)
+    for p, s in zip(up[:2], us[:2]):
+        avg = p[:, :, :, 0].mean(axis=0)
+        assert np.abs(s[:, :, :, 0] - avg[None]).max() <= 1e-13 * np.abs(avg).max()
+    for p, s in zip(up[2:], us[2:]):
+        assert np.abs(s - p.mean(axis=0)[None]).max() <= 1e-13 * max(np.abs(p).max(), 1e-300)
