@@ -52,6 +52,11 @@ WORKLOADS = {
              "32 x Poiseuille 64x65x64 Re=1650, dt=0.005",
         noise=[dict(seed0=4000, amp=(1e-2, 5e-2), n_max=4, m_max=4), dict(seed0=4100, amp=(1e-2, 5e-2), n_max=4, m_max=4),
                dict(seed0=4200, amp=(1e-2, 5e-2), n_max=4, m_max=4)]),
+    "s3t": dict(
+        groups=[dict(flow="couette", mx=64, my=63, mz=64, lx=2 * np.pi, lz=1.2 * np.pi, re=1000.0, dt=0.01,
+                     members=5, shared_mean=True)],
+        name="shared-mean (S3T-type) Couette ensemble Re=1000, 2pi x 2 x 1.2pi, 64x63x64, 5 members, dt=0.01",
+        noise=[dict(seed0=6000, amp=2.5e-2, n_max=4, m_max=4)]),
     "channel128": dict(
         groups=[dict(flow="poiseuille", mx=128, my=97, mz=128, lx=4 * np.pi, lz=4 * np.pi / 3, re=3250.0, dt=0.002,
                      members=16)],
@@ -73,9 +78,16 @@ def initial_state(g, rank=0, noise=None):
     amp = nz.get("amp", 5e-2)
     if isinstance(amp, tuple):     # amplitude ramp across members
         amp = np.linspace(amp[0], amp[1], g["members"])
-    return dns_synth.make_state(g["mx"], g["my"], g["mz"], g["lx"], g["lz"], g["flow"], g["members"],
-                                nz["seed0"] + 1000 * rank, amp, n_max=nz.get("n_max"), m_max=nz.get("m_max"),
-                                spectrum=nz.get("spectrum", "flat"))
+    st = dns_synth.make_state(g["mx"], g["my"], g["mz"], g["lx"], g["lz"], g["flow"], g["members"],
+                              nz["seed0"] + 1000 * rank, amp, n_max=nz.get("n_max"), m_max=nz.get("m_max"),
+                              spectrum=nz.get("spectrum", "flat"))
+    if g.get("shared_mean"):
+        # members of a shared-mean ensemble start from one kx = 0 flow
+        for k in ("v", "eta"):
+            st[k][:, :, :, 0] = st[k][:, :, :, 0].mean(axis=0)[None]
+        for k in ("U", "W"):
+            st[k][:] = st[k].mean(axis=0)[None]
+    return st
 
 
 # ----------------------------------------------------------- distributed
@@ -228,7 +240,8 @@ import numpy as np
 import oracle, dns_synth
 g = {g!r}
 E = {members}
-ch = oracle.Channel(g['mx'], g['my'], g['mz'], g['lx'], g['lz'], g['re'], g['dt'], g['flow'])
+ch = oracle.Channel(g['mx'], g['my'], g['mz'], g['lx'], g['lz'], g['re'], g['dt'], g['flow'],
+                    shared_mean=g.get('shared_mean', False))
 st = dns_synth.make_state(g['mx'], g['my'], g['mz'], g['lx'], g['lz'], g['flow'], E, {seed0}, {amp},
                           n_max={n_max}, m_max={m_max})
 x = tuple(st[k] for k in ('v', 'eta', 'U', 'W'))

@@ -76,6 +76,14 @@ typedef struct {
     double u_wall;         /* Couette wall speed: U00(+-1) = +-u_wall (ignored for Poiseuille) */
     double bulk_flux;      /* Poiseuille: prescribed int_{-1}^{1} U00 dy (4/3 for U = 1 - y^2) */
     int members;           /* ensemble size of this group, >= 1 */
+    int shared_mean;       /* 0: independent members.  1: the members share their
+                              streamwise-mean (kx = 0) flow, an S3T-type ensemble (Sec. 5):
+                              every sub-step the kx = 0 part of the nonlinear term and the
+                              plane means <uv>, <wv> are replaced by their average over the
+                              members, so the shared flow is driven by the ensemble-averaged
+                              perturbation Reynolds stresses.  The caller sets the same kx = 0
+                              part (n = 0 column of v, eta and U00, W00) for every member; it
+                              then stays identical. */
 } dns_group_desc;
 
 typedef struct {

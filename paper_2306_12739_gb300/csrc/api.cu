@@ -191,6 +191,7 @@ void enqueue_group(dns_handle* h, HostGroup& G, cudaStream_t st, Timer* tm) {
             else if (g.plane == 3) dnsk::launch_plane_lines(g, cU, cW, st);
             else dnsk::launch_plane_f32(g, cU, cW, st);
             mark(DNS_K_PLANE);
+            if (g.shared_mean && g.E > 1) { dnsk::launch_shared_mean(g, false, st); h->launches += 1; }
             dnsk::launch_forcing_t(g, s, st);
         } else {
             dnsk::launch_yderiv<double>(g, cv, ce, g.P5, st);
@@ -198,6 +199,7 @@ void enqueue_group(dns_handle* h, HostGroup& G, cudaStream_t st, Timer* tm) {
             if (g.plane == 2) dnsk::launch_plane_cl(g, true, cU, cW, st);
             else dnsk::launch_plane_state<double>(g, cU, cW, st);
             mark(DNS_K_PLANE);
+            if (g.shared_mean && g.E > 1) { dnsk::launch_shared_mean(g, true, st); h->launches += 1; }
             dnsk::launch_forcing<double>(g, s, st);
         }
         mark(DNS_K_FORCING);
@@ -374,6 +376,9 @@ int dns_create(const dns_config* cfg, void* cuda_stream, dns_handle** out) {
             else if (cfg->helm == 0) v.helm = 0;
         }
         v.flow = d.flow == DNS_POISEUILLE ? 1 : 0;
+        if (d.shared_mean != 0 && d.shared_mean != 1)
+            return fail(h, DNS_ERR_INVALID, "group %d: shared_mean must be 0 or 1", gi);
+        v.shared_mean = d.shared_mean;
         v.re = d.re; v.dt = d.dt; v.u_wall = d.u_wall; v.bulk_flux = d.bulk_flux;
         if (!make_plan(d.mx, &v.px) || !make_plan(d.mz, &v.pz))
             return fail(h, DNS_ERR_UNSUPPORTED, "group %d: no radix plan", gi);

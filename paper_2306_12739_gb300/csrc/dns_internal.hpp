@@ -27,6 +27,7 @@ struct GroupView {
     const void* Htc[2];   // per h index: [npairs][2 fields] images of [M - I | P] in 3 BF16 pieces
     int* status;          // device error word (1: a bounded wait gave up)
     int flow;             // 0 Couette, 1 Poiseuille
+    int shared_mean;      // 1: the members share the kx = 0 flow (forcing averaged over members)
     double re, dt, u_wall, bulk_flux;
     FftPlan px, pz;
     // constants
@@ -99,6 +100,7 @@ bool launch_plane_cl(const GroupView& g, bool fp64, const double* U, const doubl
 size_t plane_cl_smem_bytes(int mx, int mz, bool fp64);
 void set_attributes_plane_cl();
 void launch_stats(const GroupView& g, cudaStream_t st);
+void launch_shared_mean(const GroupView& g, bool fp64, cudaStream_t st);
 void launch_pack(const GroupView& g, int member0, int count, cudaStream_t st);
 void launch_unpack(const GroupView& g, int member0, int count, cudaStream_t st);
 size_t plane_smem_bytes(const GroupView& g, int elem_bytes);

@@ -359,6 +359,43 @@ __global__ void k_stats_final(GroupView g) {
     }
 }
 
+// Shared-mean (S3T-type) ensemble, Sec. 5: the kx = 0 column of the three
+// nonlinear terms (P layout, n = 0 of every m and interior plane) and the plane
+// means <uv>, <wv> are replaced by their average over the members, summed in
+// member order.  One thread per averaged quantity.
+template <typename C>
+__global__ void k_shared_mean(GroupView g) {
+    const int E = g.E, Ny = g.ny, NM = g.nmodes, NKX = g.nkx, My = g.my;
+    const int nN = 3 * Ny * g.nkz;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < nN) {
+        const int mi = t % g.nkz, r = t / g.nkz, y = r % Ny, f = r / Ny;
+        C* p = (C*)g.N3 + (size_t)f * Ny * E * NM + (size_t)y * E * NM + (size_t)mi * NKX;
+        C acc = p[0];
+        for (int e = 1; e < E; ++e) {
+            acc.x += p[(size_t)e * NM].x;
+            acc.y += p[(size_t)e * NM].y;
+        }
+        acc.x /= E;
+        acc.y /= E;
+        for (int e = 0; e < E; ++e) p[(size_t)e * NM] = acc;
+    } else if (t < nN + 2 * Ny) {
+        const int j = t - nN, y = 1 + j % Ny;
+        double* m = (j < Ny) ? g.uv : g.wv;
+        double acc = m[y];
+        for (int e = 1; e < E; ++e) acc += m[(size_t)e * My + y];
+        acc /= E;
+        for (int e = 0; e < E; ++e) m[(size_t)e * My + y] = acc;
+    }
+}
+
+void launch_shared_mean(const GroupView& g, bool fp64, cudaStream_t st) {
+    const int n = 3 * g.ny * g.nkz + 2 * g.ny;
+    const int th = 256, bl = (n + th - 1) / th;
+    if (fp64) k_shared_mean<double2><<<bl, th, 0, st>>>(g);
+    else k_shared_mean<float2><<<bl, th, 0, st>>>(g);
+}
+
 void launch_stats(const GroupView& g, cudaStream_t st) {
     launch_yderiv<double>(g, g.v_t, g.e_t, g.P5d, st);
     k_stats_plane<<<dim3(g.ny, g.E), 256, 0, st>>>(g);

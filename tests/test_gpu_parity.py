@@ -324,3 +324,59 @@ def test_uneven_batch_groups_match_each_group_run_alone(precision, use_graph):
         alone = _run(g, st, 3, precision, use_graph=True, ygemm="simt", plane="cta", helm="tc")
         for a, b in zip(tog, alone):
             assert np.array_equal(a, b)
+
+
+def _shared_kx0(st):
+    out = {k: np.array(st[k]) for k in FIELDS}
+    for k in ("v", "eta"):
+        out[k][:, :, :, 0] = out[k][:, :, :, 0].mean(axis=0)[None]
+    for k in ("U", "W"):
+        out[k][:] = out[k].mean(axis=0)[None]
+    return out
+
+
+@pytest.mark.parametrize("mx,my,mz,E", [(16, 33, 16, 3), (32, 49, 32, 5)])
+def test_shared_mean_ensemble_fp64_matches_oracle(mx, my, mz, E):
+    """S3T-type ensemble (members share the kx = 0 flow, driven by the
+    member-averaged kx = 0 nonlinear terms and plane means): FP64 GPU vs the
+    oracle's shared-mean mode, and the kx = 0 flow stays bit-identical across
+    members on the GPU."""
+    g = dict(group("couette", mx, my, mz, 2 * np.pi, 1.2 * np.pi, 1000.0, 0.01, E), shared_mean=True)
+    st = _shared_kx0(_state(g, 600, 5e-2))
+    ch = oracle.Channel(mx, my, mz, g["lx"], g["lz"], g["re"], g["dt"], "couette", shared_mean=True)
+    ref = ch.step(tuple(st[k] for k in FIELDS), 4)
+    got = _run(g, st, 4)
+    for a, b, name in zip(got, ref, FIELDS):
+        assert rel(a, b) < 1e-12, (name, rel(a, b))
+    for a in got[:2]:
+        for e in range(1, E):
+            assert np.array_equal(a[e, :, :, 0], a[0, :, :, 0])
+    for a in got[2:]:
+        for e in range(1, E):
+            assert np.array_equal(a[e], a[0])
+    plain = _run(dict(g, shared_mean=False), st, 4)
+    assert rel(got[0], plain[0]) > 1e-9           # the coupling changes the trajectory
+
+
+def test_shared_mean_ensemble_mixed_matches_fp64():
+    g = dict(group("couette", 32, 49, 32, 2 * np.pi, 1.2 * np.pi, 1000.0, 0.01, 5), shared_mean=True)
+    st = _shared_kx0(_state(g, 610, 5e-2))
+    ref = _run(g, st, 20, "fp64")
+    pin = dict(ygemm="tc", plane="lines", helm="simt")
+    got = _run(g, st, 20, "mixed", **pin)
+    err = mixed_errors(got, ref)
+    assert np.all(err[:, :3] < 1e-6), err
+    for a in got[:2]:
+        for e in range(1, 5):
+            assert np.array_equal(a[e, :, :, 0], a[0, :, :, 0])
+
+
+def test_shared_mean_with_one_member_is_the_plain_step():
+    g = group("couette", 16, 33, 16, 2 * np.pi, 1.2 * np.pi, 1000.0, 0.01, 1)
+    st = _state(g, 620, 5e-2)
+    for prec in ("fp64", "mixed"):
+        pin = {} if prec == "fp64" else dict(ygemm="tc", plane="lines", helm="tc")
+        a = _run(dict(g, shared_mean=True), st, 3, prec, **pin)
+        b = _run(g, st, 3, prec, **pin)
+        for x, y in zip(a, b):
+            assert np.array_equal(x, y)
