@@ -86,6 +86,10 @@ typedef struct {
                               then stays identical. */
 } dns_group_desc;
 
+/* Groups of 32 or more independent members (shared_mean = 0) run internally as
+ * member blocks of about 16 members, each an independent branch of the step
+ * (concurrent on the GPU); results and the group / member numbering of every
+ * call are the same as for one block. */
 typedef struct {
     int n_groups;                  /* >= 1 */
     const dns_group_desc* groups;  /* n_groups entries, copied by dns_create */
@@ -261,7 +265,9 @@ int dns_export_operators(const dns_handle* h, int group, int h_index, int pair,
  * calls that overlap on the GPU (other streams, other handles) race; each call
  * writes every partial it reads, so nothing needs clearing between calls.
  * Errors: DNS_ERR_INVALID (unbound workspace, NULL output, or a group with
- * more than 2^20 / 6 member-planes -- members * (My - 2) > 174762),
+ * more than 2^20 / 6 member-planes -- members * (My - 2) > 174762; the
+ * limit applies per member block, see dns_config, so in practice only a
+ * shared-mean group can reach it),
  * DNS_ERR_CUDA (address lookup or launch failed). */
 int dns_stats_noalloc(dns_handle* h, int group, double* out_dev);
 

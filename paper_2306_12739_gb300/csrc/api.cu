@@ -37,7 +37,10 @@ struct dns_handle {
     dns_config cfg;
     std::vector<dns_group_desc> descs;
     std::string cache_path;
-    std::vector<HostGroup> groups;
+    std::vector<HostGroup> groups;     // internal groups (member blocks)
+    // user group -> its member blocks: internal group index, first member, count
+    struct Part { int ig, m0, E; };
+    std::vector<std::vector<Part>> parts;
     cudaStream_t stream = nullptr;
     char* ws = nullptr;
     size_t ws_bytes = 0;
@@ -304,6 +307,51 @@ void cache_store(const char* path, const std::string& key, int choice, const flo
 }
 
 
+// Kernel variants of one (internal) group from its sizes and the request in the
+// config; 0 entries are decided by the autotuner at dns_bind_workspace.
+int choose_variants(dns_handle* h, const dns_config* cfg, GroupView& v, int gi) {
+    const dns_group_desc& d = h->descs[gi];
+    // y-contraction variant: 1 register-tiled FP32, 2 tcgen05; 0 = decided by the
+    // autotuner when the workspace is bound
+    v.ygemm = 1;
+    if (precision_mixed(h) && dnsk::yderiv_tc_supported(v)) {
+        if (cfg->ygemm == 2) v.ygemm = 2;
+        else if (cfg->ygemm == 0) v.ygemm = 0;
+    }
+    // implicit-apply variant: 1 register-tiled FP32, 2 tcgen05; 0 = autotuned
+    v.helm = 1;
+    if (precision_mixed(h) && dnsk::helm_tc_supported(v)) {
+        if (cfg->helm == 2) v.helm = 2;
+        else if (cfg->helm == 0) v.helm = 0;
+    }
+    // plane-stage kernel: single CTA per plane where it fits, a thread-block
+    // cluster (distributed shared memory) where it does not; where both exist
+    // the autotuner decides at bind time
+    const bool mixed = precision_mixed(h);
+    const bool ok[4] = {false, plane_variant_ok(mixed, v, 1), plane_variant_ok(mixed, v, 2),
+                        plane_variant_ok(mixed, v, 3)};
+    const int navail = ok[1] + ok[2] + ok[3];
+    if (navail == 0)
+        return fail(h, DNS_ERR_UNSUPPORTED, "group %d: no plane-stage kernel for %dx%d", gi, d.mx, d.mz);
+    v.plane = navail == 1 ? (ok[1] ? 1 : ok[2] ? 2 : 3) : (mixed ? 0 : 1);
+    if (navail > 1 && cfg->plane >= 1 && cfg->plane <= 3 && ok[cfg->plane]) v.plane = cfg->plane;
+    if (precision_mixed(h)) {
+        size_t m1 = dnsk::helm_t_smem_bytes(v), m2 = dnsk::yderiv_t_smem_bytes(v), m3 = dnsk::forcing_t_smem_bytes(v);
+        if (v.helm != 1 && dnsk::helm_tc_smem_bytes(v) > m1) m1 = dnsk::helm_tc_smem_bytes(v);
+        size_t mm = m1 > m2 ? m1 : m2;
+        mm = mm > m3 ? mm : m3;
+        if (mm > 227 * 1024)
+            return fail(h, DNS_ERR_UNSUPPORTED, "group %d: spectral stage needs %zu B of shared memory", gi, mm);
+    }
+    return DNS_OK;
+}
+
+// number of member blocks a group runs as
+int member_blocks(const dns_group_desc& d) {
+    if (d.shared_mean || d.members < 32) return 1;
+    return d.members / 16;
+}
+
 }  // namespace
 
 namespace dnsk {
@@ -336,13 +384,42 @@ int dns_create(const dns_config* cfg, void* cuda_stream, dns_handle** out) {
     if (cfg->precision != DNS_PREC_FP64 && cfg->precision != DNS_PREC_MIXED)
         return fail(h, DNS_ERR_INVALID, "unknown precision %d", (int)cfg->precision);
     if (cfg->persistent != 0) return fail(h, DNS_ERR_UNSUPPORTED, "persistent launch not available");
-    h->groups.resize(cfg->n_groups);
+    // Groups of 32 or more independent members run as member blocks of about 16
+    // (internal groups, concurrent branches of the step graph); the API keeps
+    // the caller's group and member numbering.
+    h->parts.resize(cfg->n_groups);
+    int nint = 0;
+    for (int gi = 0; gi < cfg->n_groups; ++gi) nint += member_blocks(h->descs[gi]);
+    h->groups.resize(nint);
     int nthreads = (int)std::thread::hardware_concurrency();
     if (nthreads < 1) nthreads = 1;
     size_t cur = 0;
+    int ig = 0;
     for (int gi = 0; gi < cfg->n_groups; ++gi) {
-        const dns_group_desc& d = h->descs[gi];
-        HostGroup& G = h->groups[gi];
+        const int nb = member_blocks(h->descs[gi]);
+        const int E = h->descs[gi].members, base = nb > 0 ? E / nb : 0, rem = nb > 0 ? E % nb : 0;
+        const int ig0 = ig;
+        int m0 = 0;
+        for (int b = 0; b < nb; ++b, ++ig) {
+        dns_group_desc d = h->descs[gi];
+        d.members = base + (b < rem ? 1 : 0);
+        h->parts[gi].push_back({ig, m0, d.members});
+        m0 += d.members;
+        HostGroup& G = h->groups[ig];
+        if (b > 0) {
+            // a further block of the same group: same grid and operators
+            G = h->groups[ig0];
+            G.d = d;
+            G.v.E = d.members;
+            int rcv = choose_variants(h, cfg, G.v, gi);
+            if (rcv) return rcv;
+            if (G.v.ygemm != 1 && G.Atc.empty()) G.Atc = dnsk::yderiv_tc_a_image(G.D1i, G.D2i, G.v.ny, G.v.kp);
+            if (precision_mixed(h) && G.v.helm != 1 && G.Htc[0].empty())
+                for (int hi = 0; hi < 2; ++hi)
+                    G.Htc[hi] = dnsk::helm_tc_a_images(G.opsdev[hi], G.v.npairs, G.v.ny, G.v.kp);
+            cur = layout_group(h, G, cur);
+            continue;
+        }
         G.d = d;
         if (d.flow != DNS_COUETTE && d.flow != DNS_POISEUILLE)
             return fail(h, DNS_ERR_INVALID, "group %d: unknown flow", gi);
@@ -362,19 +439,6 @@ int dns_create(const dns_config* cfg, void* cuda_stream, dns_handle** out) {
         v.npairs = v.nkx * (v.kz + 1);
         v.rp = (v.ny + 3) / 4 * 4;
         v.kp = (v.ny + 15) / 16 * 16;
-        // y-contraction variant: 1 register-tiled FP32, 2 tcgen05; 0 = decided by the
-        // autotuner when the workspace is bound
-        v.ygemm = 1;
-        if (precision_mixed(h) && dnsk::yderiv_tc_supported(v)) {
-            if (cfg->ygemm == 2) v.ygemm = 2;
-            else if (cfg->ygemm == 0) v.ygemm = 0;
-        }
-        // implicit-apply variant: 1 register-tiled FP32, 2 tcgen05; 0 = autotuned
-        v.helm = 1;
-        if (precision_mixed(h) && dnsk::helm_tc_supported(v)) {
-            if (cfg->helm == 2) v.helm = 2;
-            else if (cfg->helm == 0) v.helm = 0;
-        }
         v.flow = d.flow == DNS_POISEUILLE ? 1 : 0;
         if (d.shared_mean != 0 && d.shared_mean != 1)
             return fail(h, DNS_ERR_INVALID, "group %d: shared_mean must be 0 or 1", gi);
@@ -382,24 +446,9 @@ int dns_create(const dns_config* cfg, void* cuda_stream, dns_handle** out) {
         v.re = d.re; v.dt = d.dt; v.u_wall = d.u_wall; v.bulk_flux = d.bulk_flux;
         if (!make_plan(d.mx, &v.px) || !make_plan(d.mz, &v.pz))
             return fail(h, DNS_ERR_UNSUPPORTED, "group %d: no radix plan", gi);
-        // plane-stage kernel: single CTA per plane where it fits, a thread-block
-        // cluster (distributed shared memory) where it does not; where both exist
-        // the autotuner decides at bind time
-        const bool mixed = precision_mixed(h);
-        const bool ok[4] = {false, plane_variant_ok(mixed, v, 1), plane_variant_ok(mixed, v, 2),
-                            plane_variant_ok(mixed, v, 3)};
-        const int navail = ok[1] + ok[2] + ok[3];
-        if (navail == 0)
-            return fail(h, DNS_ERR_UNSUPPORTED, "group %d: no plane-stage kernel for %dx%d", gi, d.mx, d.mz);
-        v.plane = navail == 1 ? (ok[1] ? 1 : ok[2] ? 2 : 3) : (mixed ? 0 : 1);
-        if (navail > 1 && cfg->plane >= 1 && cfg->plane <= 3 && ok[cfg->plane]) v.plane = cfg->plane;
-        if (precision_mixed(h)) {
-            size_t m1 = dnsk::helm_t_smem_bytes(v), m2 = dnsk::yderiv_t_smem_bytes(v), m3 = dnsk::forcing_t_smem_bytes(v);
-            if (v.helm != 1 && dnsk::helm_tc_smem_bytes(v) > m1) m1 = dnsk::helm_tc_smem_bytes(v);
-            size_t mm = m1 > m2 ? m1 : m2;
-            mm = mm > m3 ? mm : m3;
-            if (mm > 227 * 1024)
-                return fail(h, DNS_ERR_UNSUPPORTED, "group %d: spectral stage needs %zu B of shared memory", gi, mm);
+        {
+            int rcv = choose_variants(h, cfg, v, gi);
+            if (rcv) return rcv;
         }
         // operators
         G.grid = dnsb::build_grid(d.my);
@@ -490,6 +539,7 @@ int dns_create(const dns_config* cfg, void* cuda_stream, dns_handle** out) {
         G.kztf.assign(G.kzt.begin(), G.kzt.end());
         G.k2invf.assign(G.k2inv.begin(), G.k2inv.end());
         cur = layout_group(h, G, cur);
+        }
     }
     h->need = align256(cur);
     return DNS_OK;
@@ -686,8 +736,8 @@ int dns_bind_workspace(dns_handle* h, void* dev_ptr, size_t bytes) {
 }
 
 int dns_state_shape(const dns_handle* h, int group, int* n_kx, int* n_kz, int* ny_int, int* my) {
-    if (!h || group < 0 || group >= (int)h->groups.size()) return DNS_ERR_INVALID;
-    const GroupView& v = h->groups[group].v;
+    if (!h || group < 0 || group >= (int)h->parts.size()) return DNS_ERR_INVALID;
+    const GroupView& v = h->groups[h->parts[group][0].ig].v;
     if (n_kx) *n_kx = v.nkx;
     if (n_kz) *n_kz = v.nkz;
     if (ny_int) *ny_int = v.ny;
@@ -695,11 +745,8 @@ int dns_state_shape(const dns_handle* h, int group, int* n_kx, int* n_kz, int* n
     return DNS_OK;
 }
 
-int dns_set_state(dns_handle* h, int group, int member0, int count, const double* v_hat,
+static int set_state_block(dns_handle* h, int group, int member0, int count, const double* v_hat,
                   const double* eta_hat, const double* U00, const double* W00, int ptr_kind) {
-    if (!h) return DNS_ERR_INVALID;
-    if (!h->bound) return fail(h, DNS_ERR_INVALID, "workspace not bound");
-    if (group < 0 || group >= (int)h->groups.size()) return fail(h, DNS_ERR_INVALID, "bad group");
     GroupView& v = h->groups[group].v;
     if (member0 < 0 || count < 1 || member0 + count > v.E) return fail(h, DNS_ERR_INVALID, "member range");
     if (!v_hat || !eta_hat || !U00 || !W00) return fail(h, DNS_ERR_INVALID, "NULL state pointer");
@@ -721,12 +768,31 @@ int dns_set_state(dns_handle* h, int group, int member0, int count, const double
     return DNS_OK;
 }
 
-int dns_get_state(const dns_handle* hc, int group, int member0, int count, double* v_hat,
-                  double* eta_hat, double* U00, double* W00, int ptr_kind) {
-    dns_handle* h = const_cast<dns_handle*>(hc);
+int dns_set_state(dns_handle* h, int group, int member0, int count, const double* v_hat,
+                  const double* eta_hat, const double* U00, const double* W00, int ptr_kind) {
     if (!h) return DNS_ERR_INVALID;
     if (!h->bound) return fail(h, DNS_ERR_INVALID, "workspace not bound");
-    if (group < 0 || group >= (int)h->groups.size()) return fail(h, DNS_ERR_INVALID, "bad group");
+    if (group < 0 || group >= (int)h->parts.size()) return fail(h, DNS_ERR_INVALID, "bad group");
+    const int E = h->descs[group].members;
+    if (member0 < 0 || count < 1 || member0 + count > E) return fail(h, DNS_ERR_INVALID, "member range");
+    if (!v_hat || !eta_hat || !U00 || !W00) return fail(h, DNS_ERR_INVALID, "NULL state pointer");
+    const GroupView& v0 = h->groups[h->parts[group][0].ig].v;
+    const size_t pm = (size_t)v0.ny * v0.nmodes * 2, pu = (size_t)v0.my;   // doubles per member
+    for (const auto& P : h->parts[group]) {
+        const int lo = member0 > P.m0 ? member0 : P.m0;
+        const int hi = (member0 + count) < (P.m0 + P.E) ? (member0 + count) : (P.m0 + P.E);
+        if (lo >= hi) continue;
+        const size_t o = (size_t)(lo - member0);
+        int rc = set_state_block(h, P.ig, lo - P.m0, hi - lo, v_hat + o * pm, eta_hat + o * pm, U00 + o * pu,
+                                 W00 + o * pu, ptr_kind);
+        if (rc) return rc;
+    }
+    return DNS_OK;
+}
+
+static int get_state_block(const dns_handle* hc, int group, int member0, int count, double* v_hat,
+                  double* eta_hat, double* U00, double* W00, int ptr_kind) {
+    dns_handle* h = const_cast<dns_handle*>(hc);
     GroupView& v = h->groups[group].v;
     if (member0 < 0 || count < 1 || member0 + count > v.E) return fail(h, DNS_ERR_INVALID, "member range");
     if (ptr_kind != 0 && ptr_kind != 1) return fail(h, DNS_ERR_INVALID, "ptr_kind must be 0 or 1");
@@ -747,6 +813,29 @@ int dns_get_state(const dns_handle* hc, int group, int member0, int count, doubl
         return rc;
     if ((rc = check(h, cudaStreamSynchronize(st), "get state"))) return rc;
     return device_status(h);
+}
+
+int dns_get_state(const dns_handle* hc, int group, int member0, int count, double* v_hat,
+                  double* eta_hat, double* U00, double* W00, int ptr_kind) {
+    dns_handle* h = const_cast<dns_handle*>(hc);
+    if (!h) return DNS_ERR_INVALID;
+    if (!h->bound) return fail(h, DNS_ERR_INVALID, "workspace not bound");
+    if (group < 0 || group >= (int)h->parts.size()) return fail(h, DNS_ERR_INVALID, "bad group");
+    const int E = h->descs[group].members;
+    if (member0 < 0 || count < 1 || member0 + count > E) return fail(h, DNS_ERR_INVALID, "member range");
+    const GroupView& v0 = h->groups[h->parts[group][0].ig].v;
+    const size_t pm = (size_t)v0.ny * v0.nmodes * 2, pu = (size_t)v0.my;
+    for (const auto& P : h->parts[group]) {
+        const int lo = member0 > P.m0 ? member0 : P.m0;
+        const int hi = (member0 + count) < (P.m0 + P.E) ? (member0 + count) : (P.m0 + P.E);
+        if (lo >= hi) continue;
+        const size_t o = (size_t)(lo - member0);
+        int rc = get_state_block(h, P.ig, lo - P.m0, hi - lo, v_hat ? v_hat + o * pm : nullptr,
+                                 eta_hat ? eta_hat + o * pm : nullptr, U00 ? U00 + o * pu : nullptr,
+                                 W00 ? W00 + o * pu : nullptr, ptr_kind);
+        if (rc) return rc;
+    }
+    return DNS_OK;
 }
 
 int dns_step(dns_handle* h, int nsteps) {
@@ -804,11 +893,8 @@ int dns_step_timed(dns_handle* h, int nsteps, double* ms, int* launches) {
     return check(h, cudaGetLastError(), "timed step launch");
 }
 
-int dns_stats(dns_handle* h, int group, dns_stats_t* per_member, dns_stats_t* ensemble_mean, double* profiles) {
-    if (!h) return DNS_ERR_INVALID;
-    if (!h->bound) return fail(h, DNS_ERR_INVALID, "workspace not bound");
-    if (group < 0 || group >= (int)h->groups.size()) return fail(h, DNS_ERR_INVALID, "bad group");
-    if (!per_member) return fail(h, DNS_ERR_INVALID, "per_member is NULL");
+// per-member statistics of one member block into per_member[0 .. E)
+static int stats_block(dns_handle* h, int group, dns_stats_t* per_member, double* profiles) {
     GroupView& v = h->groups[group].v;
     cudaStream_t st = h->stream;
     dnsk::launch_stats(v, st);
@@ -823,9 +909,6 @@ int dns_stats(dns_handle* h, int group, dns_stats_t* per_member, dns_stats_t* en
         return rc;
     if ((rc = check(h, cudaStreamSynchronize(st), "stats"))) return rc;
     if ((rc = device_status(h))) return rc;
-    bool any_nf = false;
-    dns_stats_t mean;
-    memset(&mean, 0, sizeof mean);
     for (int e = 0; e < v.E; ++e) {
         dns_stats_t& s = per_member[e];
         const double* o = &out[(size_t)e * 8];
@@ -833,10 +916,30 @@ int dns_stats(dns_handle* h, int group, dns_stats_t* per_member, dns_stats_t* en
         s.bulk_flux = o[4]; s.gamma = o[5]; s.max_div = o[6];
         s.nonfinite = o[7] != 0.0 ? 1 : 0;
         s.reserved = 0;
+    }
+    return DNS_OK;
+}
+
+int dns_stats(dns_handle* h, int group, dns_stats_t* per_member, dns_stats_t* ensemble_mean, double* profiles) {
+    if (!h) return DNS_ERR_INVALID;
+    if (!h->bound) return fail(h, DNS_ERR_INVALID, "workspace not bound");
+    if (group < 0 || group >= (int)h->parts.size()) return fail(h, DNS_ERR_INVALID, "bad group");
+    if (!per_member) return fail(h, DNS_ERR_INVALID, "per_member is NULL");
+    const int E = h->descs[group].members;
+    const int my = h->groups[h->parts[group][0].ig].v.my;
+    for (const auto& P : h->parts[group]) {
+        int rc = stats_block(h, P.ig, per_member + P.m0, profiles ? profiles + (size_t)P.m0 * 6 * my : nullptr);
+        if (rc) return rc;
+    }
+    bool any_nf = false;
+    dns_stats_t mean;
+    memset(&mean, 0, sizeof mean);
+    for (int e = 0; e < E; ++e) {
+        const dns_stats_t& s = per_member[e];
         any_nf = any_nf || s.nonfinite;
-        mean.e_total += s.e_total / v.E; mean.e_pert += s.e_pert / v.E;
-        mean.tau_bottom += s.tau_bottom / v.E; mean.tau_top += s.tau_top / v.E;
-        mean.bulk_flux += s.bulk_flux / v.E; mean.gamma += s.gamma / v.E;
+        mean.e_total += s.e_total / E; mean.e_pert += s.e_pert / E;
+        mean.tau_bottom += s.tau_bottom / E; mean.tau_top += s.tau_top / E;
+        mean.bulk_flux += s.bulk_flux / E; mean.gamma += s.gamma / E;
         mean.max_div = mean.max_div > s.max_div ? mean.max_div : s.max_div;
         mean.nonfinite |= s.nonfinite;
     }
@@ -847,19 +950,25 @@ int dns_stats(dns_handle* h, int group, dns_stats_t* per_member, dns_stats_t* en
 int dns_stats_noalloc(dns_handle* h, int group, double* out_dev) {
     if (!h) return DNS_ERR_INVALID;
     if (!h->bound) return fail(h, DNS_ERR_INVALID, "workspace not bound");
-    if (group < 0 || group >= (int)h->groups.size()) return fail(h, DNS_ERR_INVALID, "bad group");
+    if (group < 0 || group >= (int)h->parts.size()) return fail(h, DNS_ERR_INVALID, "bad group");
     if (!out_dev) return fail(h, DNS_ERR_INVALID, "out_dev is NULL");
-    const GroupView& v = h->groups[group].v;
-    const size_t need = (size_t)v.E * v.ny * 6;
-    if (need > dnsk::noalloc_max_partials())
-        return fail(h, DNS_ERR_INVALID,
-                    "dns_stats_noalloc: group %d needs %zu partial sums (members x (My-2) x 6), the fixed array holds %zu",
-                    group, need, dnsk::noalloc_max_partials());
+    for (const auto& P : h->parts[group]) {
+        const GroupView& v = h->groups[P.ig].v;
+        const size_t need = (size_t)v.E * v.ny * 6;
+        if (need > dnsk::noalloc_max_partials())
+            return fail(h, DNS_ERR_INVALID,
+                        "dns_stats_noalloc: group %d needs %zu partial sums (members x (My-2) x 6), the fixed array holds %zu",
+                        group, need, dnsk::noalloc_max_partials());
+    }
     double* scratch = nullptr;
     int rc = check(h, dnsk::noalloc_scratch(&scratch), "dns_stats_noalloc: scratch address");
     if (rc) return rc;
-    dnsk::launch_stats_noalloc(v, scratch, out_dev, h->stream);
-    return check(h, cudaGetLastError(), "dns_stats_noalloc launch");
+    // member blocks one after another on the handle's stream (they share the array)
+    for (const auto& P : h->parts[group]) {
+        dnsk::launch_stats_noalloc(h->groups[P.ig].v, scratch, out_dev + (size_t)P.m0 * 8, h->stream);
+        if ((rc = check(h, cudaGetLastError(), "dns_stats_noalloc launch"))) return rc;
+    }
+    return DNS_OK;
 }
 
 int dns_selftest_timeout(dns_handle* h) {
@@ -903,18 +1012,19 @@ int dns_destroy(dns_handle* h) {
 const char* dns_last_error(const dns_handle* h) { return h ? h->err.c_str() : "NULL handle"; }
 
 int dns_kernel_choice(const dns_handle* h, int group, int* ygemm, int* plane, int* helm) {
-    if (!h || group < 0 || group >= (int)h->groups.size()) return DNS_ERR_INVALID;
-    if (ygemm) *ygemm = h->groups[group].v.ygemm;
-    if (plane) *plane = h->groups[group].v.plane;
-    if (helm) *helm = h->groups[group].v.helm;
+    if (!h || group < 0 || group >= (int)h->parts.size()) return DNS_ERR_INVALID;
+    const GroupView& v = h->groups[h->parts[group][0].ig].v;
+    if (ygemm) *ygemm = v.ygemm;
+    if (plane) *plane = v.plane;
+    if (helm) *helm = v.helm;
     return DNS_OK;
 }
 
 int dns_last_launch_count(const dns_handle* h) { return h ? h->launches : 0; }
 
 int dns_export_grid(const dns_handle* h, int group, double* y, double* D1, double* D2, double* D4c, double* ccw) {
-    if (!h || group < 0 || group >= (int)h->groups.size()) return DNS_ERR_INVALID;
-    const dnsb::GridOps& g = h->groups[group].grid;
+    if (!h || group < 0 || group >= (int)h->parts.size()) return DNS_ERR_INVALID;
+    const dnsb::GridOps& g = h->groups[h->parts[group][0].ig].grid;
     if (y) memcpy(y, g.y.data(), g.y.size() * 8);
     if (D1) memcpy(D1, g.D1.data(), g.D1.size() * 8);
     if (D2) memcpy(D2, g.D2.data(), g.D2.size() * 8);
@@ -925,8 +1035,8 @@ int dns_export_grid(const dns_handle* h, int group, double* y, double* D1, doubl
 
 int dns_export_operators(const dns_handle* h, int group, int h_index, int pair, double* Mv, double* Pv,
                          double* Me, double* Pe) {
-    if (!h || group < 0 || group >= (int)h->groups.size() || h_index < 0 || h_index > 1) return DNS_ERR_INVALID;
-    const HostGroup& G = h->groups[group];
+    if (!h || group < 0 || group >= (int)h->parts.size() || h_index < 0 || h_index > 1) return DNS_ERR_INVALID;
+    const HostGroup& G = h->groups[h->parts[group][0].ig];
     if (pair < 0 || pair >= G.v.npairs) return DNS_ERR_INVALID;
     const size_t nn = (size_t)G.v.ny * G.v.ny;
     const dnsb::CnOps& o = G.ops[h_index];

@@ -380,3 +380,37 @@ def test_shared_mean_with_one_member_is_the_plain_step():
         b = _run(g, st, 3, prec, **pin)
         for x, y in zip(a, b):
             assert np.array_equal(x, y)
+
+
+def test_member_blocks_are_invisible_to_the_caller():
+    """A group of 40 members runs internally as two member blocks (20 + 20,
+    concurrent graph branches).  Members straddling the block boundary evolve
+    bit for bit as in a small group, partial set/get across the boundary
+    round-trips, and the statistics match a small group's member by member."""
+    g = group("couette", 16, 33, 16, 1.75 * np.pi, 1.2 * np.pi, 400.0, 0.01, 40)
+    st = _state(g, 900, 5e-2)
+    sub = {k: st[k][16:24] for k in FIELDS}
+    g8 = dict(g, members=8)
+    for prec, pin in (("fp64", {}), ("mixed", dict(ygemm="tc", plane="lines", helm="simt"))):
+        full = _run(g, st, 2, prec, use_graph=True, **pin)
+        ref = _run(g8, sub, 2, prec, use_graph=True, **pin)
+        for a, b in zip(full, ref):
+            assert np.array_equal(a[16:24], b)
+    ens = dns.Ensemble([g], precision="fp64")
+    ens.set_state(0, st["v"], st["eta"], st["U"], st["W"])
+    ens.set_state(0, *(sub[k][::-1].copy() for k in FIELDS), member0=16)      # overwrite across the boundary
+    got = ens.get_state(0, member0=14, count=12)
+    assert np.array_equal(got[0][2:10], sub["v"][::-1]) and np.array_equal(got[0][:2], st["v"][14:16])
+    assert np.array_equal(got[2][10:], st["U"][24:26])
+    ens.set_state(0, st["v"], st["eta"], st["U"], st["W"])
+    ens.step(1)
+    s40 = ens.stats(0)
+    ens.close()
+    e8 = dns.Ensemble([g8], precision="fp64")
+    e8.set_state(0, *(sub[k] for k in FIELDS))
+    e8.step(1)
+    s8 = e8.stats(0)
+    e8.close()
+    for k in ("e_total", "e_pert", "tau_bottom", "max_div"):
+        assert np.array_equal(s40[k][16:24], s8[k]), k
+    assert np.array_equal(s40["uu"][16:24], s8["uu"])

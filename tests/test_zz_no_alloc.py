@@ -44,8 +44,10 @@ def test_stats_noalloc_matches_dns_stats_on_two_calls_in_a_row(precision):
 
 
 def test_stats_noalloc_rejects_a_group_larger_than_its_array():
-    # 64 x 129 x 64 grid: 127 interior planes; 1400 members need 1066800 > 2^20 partials
-    g = dict(flow="couette", mx=16, my=129, mz=16, lx=2 * np.pi, lz=np.pi, re=400.0, dt=0.01, members=1400)
+    # 127 interior planes; 1400 members need 1066800 > 2^20 partials.  A shared-mean
+    # group is one block (independent members would run in blocks of about 16)
+    g = dict(flow="couette", mx=16, my=129, mz=16, lx=2 * np.pi, lz=np.pi, re=400.0, dt=0.01, members=1400,
+             shared_mean=True)
     cfg = dns.make_config([g])
     h = dns.dns_create(cfg, 0)
     try:
