@@ -135,14 +135,20 @@ class Channel:
     """One group of ensemble members that share a grid, Re and dt."""
 
     def __init__(self, mx, my, mz, lx, lz, re, dt, flow="couette",
-                 u_wall=1.0, bulk_flux=4.0 / 3.0, shared_mean=False):
+                 u_wall=1.0, bulk_flux=4.0 / 3.0, shared_mean=False, form="advective"):
         """shared_mean: the S3T-type ensemble of Sec. 5 (ensemble simulations of
         statistical state dynamics): the members share their streamwise-mean
         (kx = 0) flow, which every sub-step is driven by the kx = 0 part of the
         nonlinear term and by the plane means <uv>, <wv> averaged over the
         members (the perturbation Reynolds stresses averaged over the ensemble).
         The caller gives every member the same kx = 0 part; it then stays
-        identical because every member receives the same kx = 0 forcing."""
+        identical because every member receives the same kx = 0 forcing.
+        form: "advective" N = u . grad u (Sec. 3.1), or "rotational" N = omega x u
+        (the two differ by grad |u|^2/2, whose curl vanishes: the v, eta forcings
+        agree up to the y-aliasing of the collocation derivative; the mean flow is
+        forced by d/dy <uv>, <wv> in both)."""
+        assert form in ("advective", "rotational")
+        self.form = form
         self.shared_mean = shared_mean
         self.mx, self.my, self.mz = mx, my, mz
         self.lx, self.lz, self.re, self.dt = lx, lz, re, dt
@@ -236,9 +242,18 @@ class Channel:
         <uv>(y), <wv>(y) on all nodes (zero at the walls)."""
         f = self.velocity(v, eta, U, W)
         p = {k: self.to_physical(a[:, 1:-1]) for k, a in f.items()}
-        Nu = p["u"] * p["ux"] + p["v"] * p["uy"] + p["w"] * p["uz"]
-        Nv = p["u"] * p["vx"] + p["v"] * p["vy"] + p["w"] * p["vz"]
-        Nw = p["u"] * p["wx"] + p["v"] * p["wy"] + p["w"] * p["wz"]
+        if self.form == "rotational":
+            # omega = curl u from the spectral gradients, then N = omega x u
+            ox = p["wy"] - p["vz"]
+            oy = p["uz"] - p["wx"]
+            oz = p["vx"] - p["uy"]
+            Nu = oy * p["w"] - oz * p["v"]
+            Nv = oz * p["u"] - ox * p["w"]
+            Nw = ox * p["v"] - oy * p["u"]
+        else:
+            Nu = p["u"] * p["ux"] + p["v"] * p["uy"] + p["w"] * p["uz"]
+            Nv = p["u"] * p["vx"] + p["v"] * p["vy"] + p["w"] * p["vz"]
+            Nw = p["u"] * p["wx"] + p["v"] * p["wy"] + p["w"] * p["wz"]
         E = v.shape[0]
         uv = np.zeros((E, self.my)); wv = np.zeros((E, self.my))
         uv[:, 1:-1] = np.mean(p["u"] * p["v"], axis=(-2, -1))

@@ -472,3 +472,48 @@ def test_shared_mean_forcing_and_update_average_the_plain_ones(s3t_small):
         assert np.abs(s[:, :, :, 0] - avg[None]).max() <= 1e-13 * np.abs(avg).max()
     for p, s in zip(up[2:], us[2:]):
         assert np.abs(s - p.mean(axis=0)[None]).max() <= 1e-13 * max(np.abs(p).max(), 1e-300)
+
+
+# ------------------------------------------------ rotational nonlinear form
+
+def test_rotational_form_forcing_equals_advective_where_products_are_resolved():
+    """The two forms differ by grad(|u|^2 / 2).  Its curl vanishes: G (x and z
+    derivatives only, spectral) agrees to round-off for any state; F also uses
+    the Chebyshev collocation derivative in y, which differentiates |u|^2 / 2
+    exactly when it is a polynomial of degree <= My - 1 -- true for these
+    states (v of degree 8, eta of degree 6 in y, laminar mean: |u|^2 of degree
+    16) at My = 33 and 17 but not at My = 13, where F differs at the level of
+    the y aliasing."""
+    def forcings(form, my):
+        ch = oracle.Channel(16, my, 16, 2 * np.pi, np.pi, 800.0, 0.01, "couette", form=form)
+        x = _state(dns_synth.make_state(16, my, 16, 2 * np.pi, np.pi, "couette", 2, 4321, 5e-2,
+                                        n_max=3, m_max=3))
+        return ch.forcing(x)
+    adv, rot = forcings("advective", 33), forcings("rotational", 33)
+    for a, b in zip(adv, rot):
+        scale = max(np.abs(a).max(), 1e-300)
+        assert np.abs(a - b).max() <= 1e-12 * scale
+    adv, rot = forcings("advective", 17), forcings("rotational", 17)
+    for a, b in zip(adv, rot):
+        assert np.abs(a - b).max() <= 1e-12 * max(np.abs(a).max(), 1e-300)
+    adv, rot = forcings("advective", 13), forcings("rotational", 13)
+    G_scale = np.abs(adv[1]).max()
+    assert np.abs(adv[1] - rot[1]).max() <= 1e-12 * G_scale             # G: exact for any My
+    dF = np.abs(adv[0] - rot[0]).max() / np.abs(adv[0]).max()
+    assert 1e-4 < dF < 1e-1                                              # F: y aliasing only
+    for a, b in zip(adv[2:], rot[2:]):                                   # mean forcing: same in both
+        assert np.array_equal(a, b)
+
+
+def test_rotational_form_step_stays_divergence_free_and_close_to_advective():
+    ch_a = oracle.Channel(16, 33, 16, 1.75 * np.pi, 1.2 * np.pi, 400.0, 0.01, "couette")
+    ch_r = oracle.Channel(16, 33, 16, 1.75 * np.pi, 1.2 * np.pi, 400.0, 0.01, "couette", form="rotational")
+    x = _state(dns_synth.make_state(16, 33, 16, 1.75 * np.pi, 1.2 * np.pi, "couette", 2, 77, 5e-2))
+    ya, yr = ch_a.step(x, 5), ch_r.step(x, 5)
+    assert np.all(ch_r.stats(yr)["max_div"] < 1e-14)
+    # the states grow in y-degree, so the forms separate slowly (y aliasing)
+    for a, b in zip(ya[:2], yr[:2]):
+        d = np.abs(a - b).max() / np.abs(a).max()
+        assert 1e-12 < d < 1e-5
+    for a, b in zip(ya[2:], yr[2:]):      # mean flow (U, W) as one field
+        assert np.abs(a - b).max() < 1e-8 * np.abs(ya[2]).max()
