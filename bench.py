@@ -52,6 +52,11 @@ WORKLOADS = {
              "32 x Poiseuille 64x65x64 Re=1650, dt=0.005",
         noise=[dict(seed0=4000, amp=(1e-2, 5e-2), n_max=4, m_max=4), dict(seed0=4100, amp=(1e-2, 5e-2), n_max=4, m_max=4),
                dict(seed0=4200, amp=(1e-2, 5e-2), n_max=4, m_max=4)]),
+    "rotational": dict(
+        groups=[dict(flow="poiseuille", mx=64, my=65, mz=64, lx=2 * np.pi, lz=np.pi, re=1650.0, dt=0.005, members=8,
+                     form="rotational")],
+        name="Poiseuille constant-flux Re=1650, 2pi x 2 x pi, 64x65x64, 8 members, dt=0.005, rotational nonlinear form",
+        noise=[dict(seed0=2000, amp=5e-2, n_max=4, m_max=4)]),
     "s3t": dict(
         groups=[dict(flow="couette", mx=64, my=63, mz=64, lx=2 * np.pi, lz=1.2 * np.pi, re=1000.0, dt=0.01,
                      members=5, shared_mean=True)],
@@ -185,7 +190,12 @@ def kernel_work(cls, g, precision):
     S = nmodes * ny * E                      # complex values of one spectral field
     MM = g["mx"] * g["mz"]
     if cls == "plane":
-        per_plane = 15 * 2.5 * MM * np.log2(MM) + 9 * 2 * MM + 2 * 2 * MM
+        if g.get("form", "advective") == "rotational":
+            # 6 inverse + 3 forward transforms, 6 products, the means
+            per_plane = 9 * 2.5 * MM * np.log2(MM) + 6 * 2 * MM + 2 * 2 * MM
+        else:
+            # 12 inverse + 3 forward transforms, 9 products, the means
+            per_plane = 15 * 2.5 * MM * np.log2(MM) + 9 * 2 * MM + 2 * 2 * MM
         return "alu", E * ny * per_plane, "flop"
     if cls == "yderiv":
         return "alu", S * 3 * 2 * 2 * ny, "flop"
@@ -241,7 +251,7 @@ import oracle, dns_synth
 g = {g!r}
 E = {members}
 ch = oracle.Channel(g['mx'], g['my'], g['mz'], g['lx'], g['lz'], g['re'], g['dt'], g['flow'],
-                    shared_mean=g.get('shared_mean', False))
+                    shared_mean=g.get('shared_mean', False), form=g.get('form', 'advective'))
 st = dns_synth.make_state(g['mx'], g['my'], g['mz'], g['lx'], g['lz'], g['flow'], E, {seed0}, {amp},
                           n_max={n_max}, m_max={m_max})
 x = tuple(st[k] for k in ('v', 'eta', 'U', 'W'))

@@ -84,6 +84,13 @@ typedef struct {
                               perturbation Reynolds stresses.  The caller sets the same kx = 0
                               part (n = 0 column of v, eta and U00, W00) for every member; it
                               then stays identical. */
+    int nonlinear_form;    /* 0: advective N = u . grad u (Sec. 3.1).  1: rotational
+                              N = omega x u; the v, eta forcings differ from the advective
+                              ones only through the aliasing of the y collocation derivative
+                              (the curl of grad |u|^2/2 vanishes), the mean flow is forced by
+                              d/dy <uv>, <wv> in both.  Rotational needs fewer transforms
+                              (6 inverse + 3 forward per plane); it is available for
+                              Mx, Mz <= 64 (DNS_ERR_UNSUPPORTED otherwise). */
 } dns_group_desc;
 
 /* Groups of 32 or more independent members (shared_mean = 0) run internally as

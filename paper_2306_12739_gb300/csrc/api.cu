@@ -249,6 +249,9 @@ std::string tune_key(const GroupView& v) {
 // plane, 3 line-owned single CTA (single precision only)
 bool plane_variant_ok(bool mixed, const GroupView& v, int c) {
     const size_t lim = 227 * 1024;
+    // the rotational form exists in the line-owned kernel (single precision) and
+    // the single-CTA FP64 kernel
+    if (v.rot && !((mixed && c == 3) || (!mixed && c == 1))) return false;
     if (c == 1) {
         const size_t b = mixed ? dnsk::plane_f32_smem_bytes(v.mx, v.mz) : dnsk::plane_smem_bytes(v, 8);
         return (mixed ? b > 0 : (v.mx <= 64 && v.mz <= 64)) && b <= lim;
@@ -443,6 +446,9 @@ int dns_create(const dns_config* cfg, void* cuda_stream, dns_handle** out) {
         if (d.shared_mean != 0 && d.shared_mean != 1)
             return fail(h, DNS_ERR_INVALID, "group %d: shared_mean must be 0 or 1", gi);
         v.shared_mean = d.shared_mean;
+        if (d.nonlinear_form != 0 && d.nonlinear_form != 1)
+            return fail(h, DNS_ERR_INVALID, "group %d: nonlinear_form must be 0 or 1", gi);
+        v.rot = d.nonlinear_form;
         v.re = d.re; v.dt = d.dt; v.u_wall = d.u_wall; v.bulk_flux = d.bulk_flux;
         if (!make_plan(d.mx, &v.px) || !make_plan(d.mz, &v.pz))
             return fail(h, DNS_ERR_UNSUPPORTED, "group %d: no radix plan", gi);

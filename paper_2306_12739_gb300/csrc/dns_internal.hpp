@@ -28,6 +28,7 @@ struct GroupView {
     int* status;          // device error word (1: a bounded wait gave up)
     int flow;             // 0 Couette, 1 Poiseuille
     int shared_mean;      // 1: the members share the kx = 0 flow (forcing averaged over members)
+    int rot;              // nonlinear term: 0 advective u . grad u, 1 rotational omega x u
     double re, dt, u_wall, bulk_flux;
     FftPlan px, pz;
     // constants

@@ -80,8 +80,10 @@ __global__ void __launch_bounds__(PLANE_THREADS) k_plane(GroupView g, const doub
     __syncthreads();
 
     // spectral value of field `which` at mode q:
-    //   0 u, 1 v, 2 w, 3 + 3 i + j: d u_i / d x_j (i: u v w, j: x y z)
-    auto gen = [&](int which, int q) -> C {
+    //   0 u, 1 v, 2 w, 3 + 3 i + j: d u_i / d x_j (i: u v w, j: x y z),
+    //   12, 13, 14: vorticity omega_x = dw/dy - dv/dz, omega_y = eta,
+    //   omega_z = dv/dx - du/dy
+    auto gen0 = [&](int which, int q) -> C {
         const int mi = q / NKX, n = q - mi * NKX;
         const T kx = kxt[n], kz = kzt[mi], ki = k2i[q];
         const bool mean = (q == q_mean);
@@ -115,17 +117,24 @@ __global__ void __launch_bounds__(PLANE_THREADS) k_plane(GroupView g, const doub
         r.x = -k * base.y; r.y = k * base.x;
         return r;
     };
+    auto genw = [&](int which, int q) -> C {
+        if (which < 12) return gen0(which, q);
+        if (which == 13) return Pe[q];
+        C a = gen0(which == 12 ? 10 : 6, q), b = gen0(which == 12 ? 8 : 4, q);   // (wy - vz) or (vx - uy)
+        a.x -= b.x; a.y -= b.y;
+        return a;
+    };
 
     // inverse transform of field `which`; acc = false: dst = field,
-    // acc = true: dst += vel * field
-    auto inverse2d = [&](int which, bool acc, T* dst, const T* vel) {
+    // acc = true: dst += sgn vel * field
+    auto inverse2d = [&](int which, bool acc, T* dst, const T* vel, T sgn) {
         for (int c0 = 0; c0 < NKX; c0 += CHUNK) {
             int nl = min(CHUNK, NKX - c0);
             for (int idx = tid; idx < nl * Mz; idx += nthr) {
                 int l = idx / Mz, z = idx - l * Mz;
                 int m = (z <= Kz) ? z : (z >= Mz - Kz ? z - Mz : INT_MIN);
                 C val = czero<C>();
-                if (m != INT_MIN) val = gen(which, (m + Kz) * NKX + c0 + l);
+                if (m != INT_MIN) val = genw(which, (m + Kz) * NKX + c0 + l);
                 W0[idx] = val;
             }
             __syncthreads();
@@ -161,8 +170,8 @@ __global__ void __launch_bounds__(PLANE_THREADS) k_plane(GroupView g, const doub
                     dst[z * Mx + x] = val.x;
                     dst[z2 * Mx + x] = val.y;
                 } else {
-                    dst[z * Mx + x] += vel[z * Mx + x] * val.x;
-                    dst[z2 * Mx + x] += vel[z2 * Mx + x] * val.y;
+                    dst[z * Mx + x] += sgn * vel[z * Mx + x] * val.x;
+                    dst[z2 * Mx + x] += sgn * vel[z2 * Mx + x] * val.y;
                 }
             }
             __syncthreads();
@@ -215,9 +224,9 @@ __global__ void __launch_bounds__(PLANE_THREADS) k_plane(GroupView g, const doub
     };
 
     __syncthreads();
-    inverse2d(0, false, PU, nullptr);
-    inverse2d(1, false, PV, nullptr);
-    inverse2d(2, false, PW, nullptr);
+    inverse2d(0, false, PU, nullptr, (T)1);
+    inverse2d(1, false, PV, nullptr, (T)1);
+    inverse2d(2, false, PW, nullptr, (T)1);
 
     // plane means <uv>, <wv> (the (0,0) Fourier coefficients of the products)
     {
@@ -239,7 +248,15 @@ __global__ void __launch_bounds__(PLANE_THREADS) k_plane(GroupView g, const doub
     for (int i = 0; i < 3; ++i) {
         for (int k = tid; k < plane; k += nthr) ACC[k] = (T)0;
         __syncthreads();
-        for (int j = 0; j < 3; ++j) inverse2d(3 + 3 * i + j, true, ACC, vel[j]);
+        if (g.rot) {
+            // rotational form N = omega x u: N_i = u_a omega_b - u_b omega_a,
+            // (a, b) = (z, y) for i = x, (x, z) for y, (y, x) for z
+            const int a = (i + 2) % 3, b = (i + 1) % 3;
+            inverse2d(12 + b, true, ACC, vel[a], (T)1);
+            inverse2d(12 + a, true, ACC, vel[b], (T)-1);
+        } else {
+            for (int j = 0; j < 3; ++j) inverse2d(3 + 3 * i + j, true, ACC, vel[j], (T)1);
+        }
         forward2d(ACC, N3 + (size_t)i * fs + off0);
     }
 }

@@ -21,6 +21,9 @@
 //   3  forward z transforms of the kept columns, truncation, output.
 // Row strides, slot strides and a row permutation inside blocks of eight z
 // rows are chosen so that a warp's shared accesses fall in distinct banks.
+// Rotational form (ROT): N = omega x u instead of u . grad u; phase 1 then
+// transforms u, v, w and the three vorticity components (6 fields), and each
+// phase-2b group inverts the two vorticity lines its component needs.
 #include "dns_internal.hpp"
 #include "dft.cuh"
 #include "ff.cuh"
@@ -81,7 +84,7 @@ constexpr int pln_stride(int mx, int mz) {
          : (mx == 16 ? 72 : 68);
 }
 
-template <int MX, int MZ>
+template <int MX, int MZ, bool ROT = false>
 struct LCfg {
     static constexpr int KX = (MX - 1) / 3, KZ = (MZ - 1) / 3;
     static constexpr int NKX = KX + 1, NKZ = 2 * KZ + 1, NM = NKX * NKZ;
@@ -90,7 +93,8 @@ struct LCfg {
     static constexpr int GX = cmax(X1, X2), GZ = cmax(Z1, Z2);   // threads per line
     static constexpr int UX = 32 / GX, UZ = 32 / GZ;              // lines per warp
     static constexpr int HP = MZ / 2;                             // line pairs
-    static constexpr int NU1 = 9 * NKX, NU2 = 3 * HP, NU3 = 3 * NKX;
+    static constexpr int NF1 = ROT ? 6 : 9;                       // fields with a z stage
+    static constexpr int NU1 = NF1 * NKX, NU2 = 3 * HP, NU3 = 3 * NKX;
     static constexpr int NT0 = cmax(NU2 * GX, (NU1 + 1) / 2 * GZ);
     static constexpr int NT = rup(NT0, 32) > 1024 ? 1024 : rup(NT0, 32);
     static constexpr int NW = NT / 32;
@@ -105,7 +109,7 @@ struct LCfg {
     static constexpr int RSX = pad_to(cmax(cmax(X1 * XR, X2 * XRF), MX), 16, UX == 4 ? 12 : 6);
     static constexpr int PLANE = MX * MZ;
     static constexpr size_t B_COL = 0;
-    static constexpr size_t B_PLN = al16(B_COL + sizeof(C) * 9 * CFS);
+    static constexpr size_t B_PLN = al16(B_COL + sizeof(C) * NF1 * CFS);
     static constexpr size_t PLN_BYTES = smax(sizeof(float) * 3 * MX * MZP, sizeof(C) * 5 * NKZ * NKXB);
     static constexpr size_t B_X = al16(B_PLN + PLN_BYTES);
     static constexpr size_t B_TW = al16(B_X + sizeof(C) * smax((size_t)NSX * RSX, (size_t)NSZ * RSZ));
@@ -124,10 +128,10 @@ __device__ __forceinline__ int zrow(int z) {
     return (z & ~7) | ((2 * b) & 7) | (b >> 2);
 }
 
-template <int MX, int MZ>
-__global__ void __launch_bounds__(LCfg<MX, MZ>::NT, LCfg<MX, MZ>::MINB)
+template <int MX, int MZ, bool ROT>
+__global__ void __launch_bounds__(LCfg<MX, MZ, ROT>::NT, LCfg<MX, MZ, ROT>::MINB)
 k_plane_lines(GroupView g, const double* __restrict__ Ucur, const double* __restrict__ Wcur) {
-    typedef LCfg<MX, MZ> K;
+    typedef LCfg<MX, MZ, ROT> K;
     constexpr int KX = K::KX, KZ = K::KZ, NKX = K::NKX, NKZ = K::NKZ, NM = K::NM;
     constexpr int X1 = K::X1, X2 = K::X2, Z1 = K::Z1, Z2 = K::Z2, HP = K::HP;
     constexpr int GX = K::GX, UX = K::UX, UZ = K::UZ, NT = K::NT;
@@ -210,6 +214,18 @@ k_plane_lines(GroupView g, const double* __restrict__ Ucur, const double* __rest
             const bool act = u < K::NU1;
             const int f = act ? u / NKX : 0, n = act ? u - f * NKX : 0;
             const int kind = f / 3, comp = f - 3 * kind;
+            // rotational form: f = 3 + c is omega_c (x: dw/dy - dv/dz, y: eta, z: dv/dx - du/dy)
+            auto field = [&](int mi) -> C {
+                if (!ROT || f < 3) return gen(kind, comp, mi, n);
+                if (comp == 1) return BASE[3 * FSB + mi * NKXB + n];
+                if (comp == 0) {
+                    const C a = gen(1, 2, mi, n), b = gen(2, 1, mi, n);
+                    return f2(a.x - b.x, a.y - b.y);
+                }
+                const C vv = BASE[mi * NKXB + n], b = gen(1, 0, mi, n);
+                const float kx = kxs[n];
+                return f2(-kx * vv.y - b.x, kx * vv.x - b.y);
+            };
             if (act && t < Z2) {
                 C v[Z1];
                 // slot n1 holds z = Z2 n1 + t: blocks of slots wholly inside the
@@ -224,7 +240,7 @@ k_plane_lines(GroupView g, const double* __restrict__ Ucur, const double* __rest
                         const bool in_lo = lo || (!hi && z <= KZ);
                         const bool keep = lo || hi || z <= KZ || z >= MZ - KZ;
                         const int mi = keep ? (in_lo ? z + KZ : z - MZ + KZ) : KZ;
-                        const C r = gen(kind, comp, mi, n);
+                        const C r = field(mi);
                         v[n1] = keep ? r : f2(0.f, 0.f);
                     }
                 };
@@ -323,17 +339,32 @@ k_plane_lines(GroupView g, const double* __restrict__ Ucur, const double* __rest
         C acc[X2];
 #pragma unroll
         for (int k2 = 0; k2 < X2; ++k2) acc[k2] = f2(0.f, 0.f);
+        // advective: N_i = sum_j u_j d_j u_i (d_x from the columns of u_i times
+        // i kx); rotational: N_i = u_a omega_b - u_b omega_a with
+        // (a, b) = (i + 2, i + 1) mod 3
+        constexpr int NTERM = ROT ? 2 : 3;
 #pragma unroll 1
-        for (int j = 0; j < 3; ++j) {
+        for (int j = 0; j < NTERM; ++j) {
             C o[X2];
-            xinv(COL + (j == 0 ? i : 3 * j + i) * CFS, p, j == 0, tx, act, XX, o);
+            int src, vel;
+            float sgn = 1.f;
+            if (ROT) {
+                const int a = (i + 2) % 3, b = (i + 1) % 3;
+                src = 3 + (j == 0 ? b : a);
+                vel = j == 0 ? a : b;
+                sgn = j == 0 ? 1.f : -1.f;
+            } else {
+                src = j == 0 ? i : 3 * j + i;
+                vel = j;
+            }
+            xinv(COL + src * CFS, p, !ROT && j == 0, tx, act, XX, o);
             if (act && tx < X1) {
-                const float* pj = PLN + j * MX * MZP + p;
+                const float* pj = PLN + vel * MX * MZP + p;
 #pragma unroll
                 for (int k2 = 0; k2 < X2; ++k2) {
                     const int x = tx + X1 * k2;
-                    acc[k2].x += pj[x * MZP] * o[k2].x;
-                    acc[k2].y += pj[x * MZP + HP] * o[k2].y;
+                    acc[k2].x += (sgn * pj[x * MZP]) * o[k2].x;
+                    acc[k2].y += (sgn * pj[x * MZP + HP]) * o[k2].y;
                 }
             }
         }
@@ -431,17 +462,20 @@ k_plane_lines(GroupView g, const double* __restrict__ Ucur, const double* __rest
     }
 }
 
-template <int MX, int MZ>
+template <int MX, int MZ, bool ROT>
 void launch_t(const GroupView& g, const double* U, const double* W, cudaStream_t st) {
-    typedef LCfg<MX, MZ> K;
-    k_plane_lines<MX, MZ><<<dim3(g.ny, g.E), K::NT, K::BYTES, st>>>(g, U, W);
+    typedef LCfg<MX, MZ, ROT> K;
+    k_plane_lines<MX, MZ, ROT><<<dim3(g.ny, g.E), K::NT, K::BYTES, st>>>(g, U, W);
 }
 
 template <int MX, int MZ>
 void set_attr_t() {
-    typedef LCfg<MX, MZ> K;
-    static_assert(K::BYTES <= 227 * 1024, "plane stage does not fit in shared memory");
-    cudaFuncSetAttribute(k_plane_lines<MX, MZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)K::BYTES);
+    static_assert(LCfg<MX, MZ, false>::BYTES <= 227 * 1024, "plane stage does not fit in shared memory");
+    static_assert(LCfg<MX, MZ, true>::BYTES <= 227 * 1024, "plane stage does not fit in shared memory");
+    cudaFuncSetAttribute(k_plane_lines<MX, MZ, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)LCfg<MX, MZ, false>::BYTES);
+    cudaFuncSetAttribute(k_plane_lines<MX, MZ, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)LCfg<MX, MZ, true>::BYTES);
 }
 
 }  // namespace pln
@@ -450,14 +484,19 @@ void set_attr_t() {
     X(48, 16) X(48, 32) X(48, 48) X(48, 64) X(64, 16) X(64, 32) X(64, 48) X(64, 64)
 
 bool launch_plane_lines(const GroupView& g, const double* U, const double* W, cudaStream_t st) {
-#define DNS_CASE(a, b) if (g.mx == a && g.mz == b) { pln::launch_t<a, b>(g, U, W, st); return true; }
+#define DNS_CASE(a, b)                                                   \
+    if (g.mx == a && g.mz == b) {                                        \
+        if (g.rot) pln::launch_t<a, b, true>(g, U, W, st);               \
+        else pln::launch_t<a, b, false>(g, U, W, st);                    \
+        return true;                                                     \
+    }
     DNS_LINES_SIZES(DNS_CASE)
 #undef DNS_CASE
     return false;
 }
 
 size_t plane_lines_smem_bytes(int mx, int mz) {
-#define DNS_CASE(a, b) if (mx == a && mz == b) return pln::LCfg<a, b>::BYTES;
+#define DNS_CASE(a, b) if (mx == a && mz == b) return pln::LCfg<a, b, false>::BYTES;
     DNS_LINES_SIZES(DNS_CASE)
 #undef DNS_CASE
     return 0;

@@ -136,3 +136,18 @@ def test_integer_pipe_conversions_round_like_ieee(dns):
     assert np.array_equal(d_out.view(np.uint64), ref_d.view(np.uint64))
     fn, _ = dns.convert_selftest(np.array([np.nan]), np.array([np.nan], dtype=np.float32))
     assert np.isnan(fn[0])
+
+
+def test_rotational_form_is_refused_where_no_kernel_has_it(dns):
+    g = dict(flow="couette", mx=128, my=33, mz=128, lx=2 * np.pi, lz=np.pi, re=400.0, dt=0.01, members=1,
+             form="rotational")
+    for prec in ("fp64", "mixed"):
+        with pytest.raises(dns.DnsError) as ei:
+            dns.dns_create(dns.make_config([g], precision=prec), 0)
+        assert ei.value.code == dns.DNS_ERR_UNSUPPORTED
+    bad = dict(g, mx=32, mz=32)
+    cfg = dns.make_config([bad])
+    cfg.groups[0].nonlinear_form = 5
+    with pytest.raises(dns.DnsError) as ei:
+        dns.dns_create(cfg, 0)
+    assert ei.value.code == dns.DNS_ERR_INVALID

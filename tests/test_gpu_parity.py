@@ -414,3 +414,28 @@ def test_member_blocks_are_invisible_to_the_caller():
     for k in ("e_total", "e_pert", "tau_bottom", "max_div"):
         assert np.array_equal(s40[k][16:24], s8[k]), k
     assert np.array_equal(s40["uu"][16:24], s8["uu"])
+
+
+@pytest.mark.parametrize("mx,my,mz,E", [(16, 33, 16, 2), (32, 49, 32, 3), (64, 33, 48, 2)])
+def test_rotational_form_fp64_matches_oracle(mx, my, mz, E):
+    g = dict(group("poiseuille", mx, my, mz, 2 * np.pi, np.pi, 1650.0, 0.005, E), form="rotational")
+    st = _state(g, 700, 5e-2)
+    ch = oracle.Channel(mx, my, mz, g["lx"], g["lz"], g["re"], g["dt"], "poiseuille", form="rotational")
+    ref = ch.step(tuple(st[k] for k in FIELDS), 4)
+    got = _run(g, st, 4)
+    for a, b, name in zip(got, ref, FIELDS):
+        assert rel(a, b) < 1e-12, (name, rel(a, b))
+    adv = _run(dict(g, form="advective"), st, 4)
+    assert rel(got[0], adv[0]) > 1e-14         # a different discretisation of N
+
+
+@pytest.mark.parametrize("mx,mz", [(16, 16), (32, 48), (48, 32), (64, 64), (64, 16)])
+def test_rotational_form_mixed_matches_fp64(mx, mz):
+    g = dict(group("poiseuille", mx, 33, mz, 2 * np.pi, np.pi, 1650.0, 0.005, 3), form="rotational")
+    st = _state(g, 710, 5e-2)
+    ref = _run(g, st, 10, "fp64")
+    ens = dns.Ensemble([g], precision="mixed")
+    assert dns.dns_kernel_choice(ens.h, 0, "plane") == "lines"
+    ens.close()
+    err = mixed_errors(_run(g, st, 10, "mixed"), ref)
+    assert np.all(err[:, :3] < 1e-6), err
