@@ -26,6 +26,7 @@ struct HostGroup {
     std::vector<double> kxt, kzt, k2t, k2inv, twx, twz, opsdev[2], mopsdev[2], D1i, D2i;
     std::vector<float> kxtf, kztf, k2invf, twxf, twzf, opsf[2], opsfT[2], D1T, D2T;
     std::vector<uint16_t> Atc, Htc[2];
+
     // byte offsets inside the workspace
     struct Off { size_t off, bytes; };
     std::vector<std::pair<void**, Off>> slots;
@@ -206,8 +207,7 @@ void enqueue_group(dns_handle* h, HostGroup& G, cudaStream_t st, Timer* tm) {
             dnsk::launch_forcing<double>(g, s, st);
         }
         mark(DNS_K_FORCING);
-        // per-wavenumber implicit apply; the same launch carries the mean-flow
-        // update as E extra CTAs (independent work that overlaps with it)
+        // per-wavenumber implicit apply (and the rows of the mean-flow update)
         if (precision_mixed(h)) {
             if (g.helm == 2) dnsk::launch_helm_tc(g, s, st);
             else dnsk::launch_helm_t(g, s, st);
@@ -215,7 +215,11 @@ void enqueue_group(dns_handle* h, HostGroup& G, cudaStream_t st, Timer* tm) {
             dnsk::launch_helm(g, s, st);
         }
         mark(DNS_K_HELM);
-        h->launches += 4;
+        // the mean-flow rows ran as leading CTAs of the implicit apply; gamma and
+        // the profiles
+        dnsk::launch_mean_finish(g, s, st);
+        mark(DNS_K_MEAN);
+        h->launches += 5;
     }
 }
 
@@ -1009,6 +1013,7 @@ int dns_destroy(dns_handle* h) {
     if (h->gexec) cudaGraphExecDestroy(h->gexec);
     if (h->graph) cudaGraphDestroy(h->graph);
     for (auto s2 : h->gstreams) cudaStreamDestroy(s2);
+
     for (auto e2 : h->gevents) cudaEventDestroy(e2);
     if (h->fork_ev) cudaEventDestroy(h->fork_ev);
     delete h;

@@ -158,6 +158,18 @@ __device__ __forceinline__ void mean_dy_row(const double* __restrict__ D1, const
     if (threadIdx.x == 0) { out[0] = a; out[1] = b; }
 }
 
+// Division by a divisor fixed for the whole kernel (Granlund and Montgomery,
+// division by invariant integers): q = floor(n / d) = high 32 bits of n * M with
+// M = floor((2^32 - 1) / d) + 1, exact whenever n * d < 2^32 (the error n * (M
+// - 2^32 / d) / 2^32 then stays below 1/d).  One division per thread to set up,
+// a multiply-high per use instead of the general integer division sequence.
+struct FastDiv {
+    unsigned d, M;
+    __device__ __forceinline__ explicit FastDiv(unsigned dd) : d(dd), M(dd > 1 ? 0xFFFFFFFFu / dd + 1u : 0u) {}
+    __device__ __forceinline__ unsigned div(unsigned n) const { return d > 1 ? __umulhi(n, M) : n; }
+    __device__ __forceinline__ unsigned mod(unsigned n) const { return n - div(n) * d; }
+};
+
 // Allow a kernel the largest dynamic shared memory the SM offers next to its
 // static shared memory (227 KB per block on sm_103).
 template <typename F>

@@ -59,7 +59,7 @@ struct GroupView {
     double2 *Fv, *Fe, *Av, *Ae;   // combined forcing of this sub-step; RK accumulators
     double *U_t, *W_t, *U_s, *W_s;   // [E][My]
     double *AU, *AW;                 // RK accumulators of <uv>, <wv> [E][My]
-    double *dU, *dW;                 // [E][My] (unused by the step)
+    double *dU, *dW;                 // [E][My] scratch: pre-gamma mean profiles of the sub-step
     double *uv, *wv;                 // [E][My] plane means <uv>, <wv>
     double* gamma;                   // [E]
     // P layout work arrays (element type by precision)
@@ -81,6 +81,9 @@ void launch_plane_state(const GroupView& g, const double* U, const double* W, cu
 template <typename T>
 void launch_forcing(const GroupView& g, int s, cudaStream_t st);
 void launch_helm(const GroupView& g, int s, cudaStream_t st);
+void launch_mean_finish(const GroupView& g, int s, cudaStream_t st);
+// CTAs of the mean-flow rows carried by the implicit-apply launches (8 rows each)
+__host__ __device__ inline int mean_row_ctas(const GroupView& g) { return g.E * ((g.ny + 7) / 8); }
 inline size_t mean_smem_bytes(const GroupView& g) { return (8 * (size_t)g.my + 32) * sizeof(double); }
 size_t helm_t_smem_bytes(const GroupView& g);
 size_t yderiv_t_smem_bytes(const GroupView& g);

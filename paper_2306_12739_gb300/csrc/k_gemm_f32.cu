@@ -64,8 +64,10 @@ __global__ void __launch_bounds__(THREADS) k_yderiv_t(GroupView g, const double2
         }
         // state tile, read in H order [q][y][e], written [y][(el QT + qq)]
         const int per_q = Ny * T.EBT;
+        const FastDiv dPQ((unsigned)per_q), dEB((unsigned)T.EBT);
         for (int i = threadIdx.x; i < T.QT * per_q; i += THREADS) {
-            const int qq = i / per_q, r = i - qq * per_q, k = r / T.EBT, el = r - k * T.EBT;
+            const int qq = (int)dPQ.div((unsigned)i), r = i - qq * per_q;
+            const int k = (int)dEB.div((unsigned)r), el = r - k * T.EBT;
             const int q = q0 + qq, e = e0 + el;
             double2 a = make_double2(0.0, 0.0), b = a;
             if (q < NM && e < E) {
@@ -82,8 +84,9 @@ __global__ void __launch_bounds__(THREADS) k_yderiv_t(GroupView g, const double2
     const size_t fs = (size_t)Ny * E * NM;
     float2* P = (float2*)g.P5;
     const int RB = RP / 4;
+    const FastDiv dNC((unsigned)T.NC), dQT((unsigned)T.QT);
     for (int m = threadIdx.x; m < RB * T.NC; m += THREADS) {
-        const int j = m % T.NC, rb = m / T.NC;       // consecutive threads: consecutive q
+        const int rb = (int)dNC.div((unsigned)m), j = m - rb * T.NC;   // consecutive threads: consecutive q
         const int r0 = 4 * rb;
         float4 av[2] = {make_float4(0, 0, 0, 0), make_float4(0, 0, 0, 0)};   // D1 v: re, im
         float4 bv[2] = {make_float4(0, 0, 0, 0), make_float4(0, 0, 0, 0)};   // D2 v
@@ -101,7 +104,7 @@ __global__ void __launch_bounds__(THREADS) k_yderiv_t(GroupView g, const double2
             ae[0].x += d1.x * h.x; ae[0].y += d1.y * h.x; ae[0].z += d1.z * h.x; ae[0].w += d1.w * h.x;
             ae[1].x += d1.x * h.y; ae[1].y += d1.y * h.y; ae[1].z += d1.z * h.y; ae[1].w += d1.w * h.y;
         }
-        const int el = j / T.QT, qq = j - el * T.QT;
+        const int el = (int)dQT.div((unsigned)j), qq = j - el * T.QT;
         const int q = q0 + qq, e = e0 + el;
         if (q >= NM || e >= E) continue;
         const float r_av[2][4] = {{av[0].x, av[0].y, av[0].z, av[0].w}, {av[1].x, av[1].y, av[1].z, av[1].w}};
@@ -127,6 +130,7 @@ __global__ void __launch_bounds__(THREADS) k_forcing_t(GroupView g, int s) {
     extern __shared__ __align__(16) unsigned char sm[];
     const int Ny = g.ny, RP = g.rp, E = g.E, NM = g.nmodes, NKX = g.nkx;
     const Tile T = tile_of(E, Ny, NM);
+    const FastDiv dNKX((unsigned)NKX);
     const int q0 = blockIdx.x * T.QT, e0 = blockIdx.y * T.EBT;
     const int NCR = 2 * T.NC;
     float* D1 = (float*)sm;              // [Ny][RP]
@@ -140,14 +144,16 @@ __global__ void __launch_bounds__(THREADS) k_forcing_t(GroupView g, int s) {
         for (int i = threadIdx.x; i < Ny * RP / 4; i += THREADS) ((float4*)D1)[i] = s1[i];
         // P layout [y][e][q]: consecutive threads read consecutive q
         const int per_y = T.EBT * T.QT;
+        const FastDiv dPY((unsigned)per_y), dQT((unsigned)T.QT);
         for (int i = threadIdx.x; i < Ny * per_y; i += THREADS) {
-            const int k = i / per_y, r = i - k * per_y, el = r / T.QT, qq = r - el * T.QT;
+            const int k = (int)dPY.div((unsigned)i), r = i - k * per_y;
+            const int el = (int)dQT.div((unsigned)r), qq = r - el * T.QT;
             const int q = q0 + qq, e = e0 + el;
             float2 ph = make_float2(0.f, 0.f), gg = ph, kv = ph;
             if (q < NM && e < E) {
                 const size_t o = ((size_t)k * E + e) * NM + q;
                 const float2 nu = N3[o], nv = N3[fs + o], nw = N3[2 * fs + o];
-                const int mi = q / NKX, n = q - mi * NKX;
+                const int mi = (int)dNKX.div((unsigned)q), n = q - mi * NKX;
                 const float kx = g.kxtf[n], kz = g.kztf[mi];
                 const float k2 = kx * kx + kz * kz;
                 const float ax = kx * nu.x + kz * nw.x, ay = kx * nu.y + kz * nw.y;   // i kx Nu + i kz Nw
@@ -164,10 +170,12 @@ __global__ void __launch_bounds__(THREADS) k_forcing_t(GroupView g, int s) {
     }
     __syncthreads();
     const int RB = RP / 4;
+    const FastDiv dEB2((unsigned)T.EBT), dQT2((unsigned)T.QT);
     const int q_mean = g.kz * NKX;
     for (int m = threadIdx.x; m < RB * T.NC; m += THREADS) {
         // consecutive threads: consecutive members (the H layout's fastest index)
-        const int el = m % T.EBT, r = m / T.EBT, qq = r % T.QT, rb = r / T.QT;
+        const int r = (int)dEB2.div((unsigned)m), el = m - r * T.EBT;
+        const int rb = (int)dQT2.div((unsigned)r), qq = r - rb * T.QT;
         const int j = el * T.QT + qq;
         const int r0 = 4 * rb;
         float4 ax = make_float4(0, 0, 0, 0), ay = ax;
@@ -250,8 +258,14 @@ __device__ __forceinline__ bool mbar_wait0(unsigned bar) {
 __global__ void __launch_bounds__(THREADS) k_helm_t(GroupView g, int s) {
     extern __shared__ __align__(16) unsigned char sm[];
     const int Ny = g.ny, RP = g.rp, E = g.E, NKX = g.nkx;
-    if ((int)blockIdx.x < E) { mean_cta(g, s, blockIdx.x, sm); return; }
-    const int b = blockIdx.x - E;
+    // leading CTAs: rows of the mean-flow update (independent work that fills
+    // SMs beside the wavenumber pairs), finished by launch_mean_finish
+    const int nrow = mean_row_ctas(g);
+    if ((int)blockIdx.x < nrow) {
+        mean_rows(g, s, blockIdx.x % E, (blockIdx.x / E) * (THREADS / 32), sm);
+        return;
+    }
+    const int b = blockIdx.x - nrow;
     const int p = b % g.npairs, f = b / g.npairs;
     const int n = p % NKX, am = p / NKX;
     if (n == 0 && am == 0) return;
@@ -285,9 +299,10 @@ __global__ void __launch_bounds__(THREADS) k_helm_t(GroupView g, int s) {
     const double2* X = f == 0 ? g.v_t : g.e_t;
     const float* F = (const float*)(f == 0 ? g.Fv : g.Fe);     // single-precision F~ (mixed path)
     const int per = Ny * 2 * E;
+    const FastDiv dPER((unsigned)per), d2E((unsigned)(2 * E));
     for (int i = threadIdx.x; i < nq * per; i += THREADS) {
-        const int which = i / per, r = i - which * per;
-        const int k = r / (2 * E), c = r - k * (2 * E);
+        const int which = (int)dPER.div((unsigned)i), r = i - which * per;
+        const int k = (int)d2E.div((unsigned)r), c = r - k * (2 * E);
         const int q = which == 0 ? q1 : q2;
         const size_t o = (size_t)q * per + r;
         if (needM) Xs[k * NC + which * 2 * E + c] = d2f(((const double*)X)[o]);
@@ -304,8 +319,9 @@ __global__ void __launch_bounds__(THREADS) k_helm_t(GroupView g, int s) {
     double2* M1 = f == 0 ? g.mx1_v : g.mx1_e;
     double2* O = (s == 2) ? (f == 0 ? g.v_t : g.e_t) : (f == 0 ? g.v_s : g.e_s);
     const int RB = RP / 4, CB = NC / 2;
+    const FastDiv dCB((unsigned)CB);
     for (int m = threadIdx.x; m < RB * CB; m += THREADS) {
-        const int cb = m % CB, rb = m / CB;
+        const int rb = (int)dCB.div((unsigned)m), cb = m - rb * CB;
         const int r0 = 4 * rb, c0 = 2 * cb;
         float4 pa = make_float4(0, 0, 0, 0), pb = pa, ma = pa, mb = pa;   // columns c0, c0+1
 #pragma unroll 4
@@ -321,7 +337,7 @@ __global__ void __launch_bounds__(THREADS) k_helm_t(GroupView g, int s) {
                 mb.x += mk.x * xk.y; mb.y += mk.y * xk.y; mb.z += mk.z * xk.y; mb.w += mk.w * xk.y;
             }
         }
-        const int which = c0 / (2 * E), cl = c0 - which * 2 * E;
+        const int which = (int)d2E.div((unsigned)c0), cl = c0 - which * 2 * E;
         const int q = which == 0 ? q1 : q2;
         const float rp[2][4] = {{pa.x, pa.y, pa.z, pa.w}, {pb.x, pb.y, pb.z, pb.w}};
         const float rm[2][4] = {{ma.x, ma.y, ma.z, ma.w}, {mb.x, mb.y, mb.z, mb.w}};
@@ -409,7 +425,7 @@ void launch_forcing_t(const GroupView& g, int s, cudaStream_t st) {
 }
 
 void launch_helm_t(const GroupView& g, int s, cudaStream_t st) {
-    gt::k_helm_t<<<g.E + 2 * g.npairs, gt::THREADS, helm_t_smem_bytes(g), st>>>(g, s);
+    gt::k_helm_t<<<mean_row_ctas(g) + 2 * g.npairs, gt::THREADS, helm_t_smem_bytes(g), st>>>(g, s);
 }
 
 void set_attributes_gemm_t() {

@@ -15,8 +15,7 @@
 // The MMA runs with M = 128: rows 0..63 are the operator rows (Ny <= 64), rows
 // 64..127 read whatever follows in shared memory and their results are never
 // read.  The pair's operator image (3 pieces, 64 rows) arrives by one TMA bulk
-// copy; columns beyond 128 are done in passes.  The E leading CTAs of the
-// launch run the mean-flow update instead (as in the SIMT kernel).  Every
+// copy; columns beyond 128 are done in passes.  Every
 // mbarrier wait is bounded; on a timeout the CTA latches the status word,
 // waits once more for what it issued, releases its TMEM and leaves.
 #include "dns_internal.hpp"
@@ -129,9 +128,14 @@ __host__ __device__ inline size_t smem_total(int KP, int NP) { return bytes_a(KP
 __global__ void __launch_bounds__(THREADS, 1) k_helm_tc(GroupView g, int s) {
     extern __shared__ __align__(1024) unsigned char sm[];
     const int E = g.E;
-    if ((int)blockIdx.x < E) { mean_cta(g, s, blockIdx.x, sm); return; }
     const int Ny = g.ny, KP = g.kp, NKX = g.nkx;
-    const int b = blockIdx.x - E;
+    // leading CTAs: rows of the mean-flow update (see the SIMT kernel)
+    const int nrow = mean_row_ctas(g);
+    if ((int)blockIdx.x < nrow) {
+        mean_rows(g, s, blockIdx.x % E, (blockIdx.x / E) * (THREADS / 32), sm);
+        return;
+    }
+    const int b = blockIdx.x - nrow;
     const int p = b % g.npairs, f = b / g.npairs;
     const int n = p % NKX, am = p / NKX;
     if (n == 0 && am == 0) return;
@@ -357,7 +361,7 @@ size_t helm_tc_smem_bytes(const GroupView& g) {
 }
 
 void launch_helm_tc(const GroupView& g, int s, cudaStream_t st) {
-    htc::k_helm_tc<<<g.E + 2 * g.npairs, htc::THREADS, helm_tc_smem_bytes(g), st>>>(g, s);
+    htc::k_helm_tc<<<mean_row_ctas(g) + 2 * g.npairs, htc::THREADS, helm_tc_smem_bytes(g), st>>>(g, s);
 }
 
 void set_attributes_helm_tc() { allow_max_dynamic_smem(htc::k_helm_tc); }

@@ -209,13 +209,34 @@ template void launch_forcing<double>(const GroupView&, int, cudaStream_t);
 
 // --------------------------------------------------------------------- mean
 
+// Mean-flow update of every member (Eqs. CN3, CN4), one CTA per member.  It
+// depends only on the plane means and the mean profiles, so it runs beside the
+// forcing and implicit-apply kernels (own stream, joined before the next plane
+// stage).
+// The rows of every member run as leading CTAs of the implicit-apply launch
+// (mean_rows, E x ceil(Ny / 8) CTAs, one warp per row); this kernel adds the
+// constant-flux correction and writes the profiles, one CTA per member.
+__global__ void __launch_bounds__(128) k_mean_finish(GroupView g, int s) {
+    __shared__ double red[32];
+    mean_finish(g, s, blockIdx.x, (unsigned char*)red);
+}
+
+void launch_mean_finish(const GroupView& g, int s, cudaStream_t st) {
+    k_mean_finish<<<g.E, 128, 0, st>>>(g, s);
+}
+
 // --------------------------------------------------------------------- helm
 
 __global__ void __launch_bounds__(256) k_helm(GroupView g, int s) {
     extern __shared__ __align__(16) unsigned char sm[];
     const int Ny = g.ny, E = g.E, NKX = g.nkx;
-    if ((int)blockIdx.x < E) { mean_cta(g, s, blockIdx.x, sm); return; }
-    const int b = blockIdx.x - E;
+    // leading CTAs: rows of the mean-flow update
+    const int nrow = mean_row_ctas(g);
+    if ((int)blockIdx.x < nrow) {
+        mean_rows(g, s, blockIdx.x % E, (blockIdx.x / E) * (blockDim.x >> 5), sm);
+        return;
+    }
+    const int b = blockIdx.x - nrow;
     const int p = b % g.npairs, f = b / g.npairs;
     const int n = p % NKX, am = p / NKX;
     if (n == 0 && am == 0) return;
@@ -268,7 +289,7 @@ __global__ void __launch_bounds__(256) k_helm(GroupView g, int s) {
 void launch_helm(const GroupView& g, int s, cudaStream_t st) {
     size_t smem = 2 * (size_t)g.ny * g.ny * sizeof(double);
     if (smem < mean_smem_bytes(g)) smem = mean_smem_bytes(g);
-    k_helm<<<g.E + 2 * g.npairs, 256, smem, st>>>(g, s);
+    k_helm<<<mean_row_ctas(g) + 2 * g.npairs, 256, smem, st>>>(g, s);
 }
 
 

@@ -153,6 +153,7 @@ __global__ void __launch_bounds__(THREADS, 2) k_yderiv_tc(GroupView g, const dou
     // first, then the splits and the shared stores
     const int KC = KP / 8;
     constexpr int TPT = 4;
+    const FastDiv dEBT((unsigned)T.EBT), dQT((unsigned)T.QT);
     for (int i0 = threadIdx.x; i0 < NCOL * KC; i0 += THREADS * TPT) {
         float xs[TPT][8];
 #pragma unroll
@@ -160,7 +161,7 @@ __global__ void __launch_bounds__(THREADS, 2) k_yderiv_tc(GroupView g, const dou
             const int i = i0 + u * THREADS;
             const int n = i % NCOL, kc = i / NCOL;
             const int f = n / (NCOL / 2), r = n % (NCOL / 2), j = r >> 1, c = r & 1;
-            const int qq = j / T.EBT, el = j - qq * T.EBT;
+            const int qq = (int)dEBT.div((unsigned)j), el = j - qq * T.EBT;
             const int q = q0 + qq, e = e0 + el;
             const bool ok = i < NCOL * KC && (qq < T.QT) && (q < NM) && (e < E);
             const double* src = (const double*)(f == 0 ? V : H);
@@ -253,9 +254,11 @@ __global__ void __launch_bounds__(THREADS, 2) k_yderiv_tc(GroupView g, const dou
     float2* P = (float2*)g.P5;
     const size_t fs = (size_t)Ny * E * NM;
     const int per = T.EBT * T.QT;
+    const FastDiv dNP((unsigned)(Ny * per)), dPER((unsigned)per);
     for (int i = threadIdx.x; i < 3 * Ny * per; i += THREADS) {
-        const int fld = i / (Ny * per), r = i - fld * (Ny * per);
-        const int y = r / per, r2 = r - y * per, el = r2 / T.QT, qq = r2 - el * T.QT;
+        const int fld = (int)dNP.div((unsigned)i), r = i - fld * (Ny * per);
+        const int y = (int)dPER.div((unsigned)r), r2 = r - y * per;
+        const int el = (int)dQT.div((unsigned)r2), qq = r2 - el * T.QT;
         const int q = q0 + qq, e = e0 + el;
         if (q >= NM || e >= E) continue;
         const int dst_field = fld == 0 ? 1 : (fld == 1 ? 2 : 4);
@@ -271,7 +274,8 @@ __global__ void __launch_bounds__(THREADS, 2) k_yderiv_tc(GroupView g, const dou
 #pragma unroll
         for (int u = 0; u < UNR; ++u) {
             const int i = i0 + u * THREADS;
-            const int y = i / per, r2 = i - y * per, el = r2 / T.QT, qq = r2 - el * T.QT;
+            const int y = (int)dPER.div((unsigned)i), r2 = i - y * per;
+            const int el = (int)dQT.div((unsigned)r2), qq = r2 - el * T.QT;
             const int q = q0 + qq, e = e0 + el;
             in[u] = i < Ny * per && q < NM && e < E;
             o[u] = ((size_t)y * E + e) * NM + q;
