@@ -91,12 +91,18 @@ typedef struct {
                               d/dy <uv>, <wv> in both.  Rotational needs fewer transforms
                               (6 inverse + 3 forward per plane); it is available for
                               Mx, Mz <= 64 (DNS_ERR_UNSUPPORTED otherwise). */
+    int member_block;      /* independent members (shared_mean = 0) run internally as member
+                              blocks of about this many members, each an independent branch
+                              of the step that runs concurrently with the others on the GPU,
+                              so that one block's last partial wave of CTAs overlaps another
+                              block's work.  0: automatic, E/4 clamped to [4, 16] (one block
+                              below 8 members).  Values >= members give one block; < 0 is
+                              DNS_ERR_INVALID.  Shared-mean groups are always one block. */
 } dns_group_desc;
 
-/* Groups of 32 or more independent members (shared_mean = 0) run internally as
- * member blocks of about 16 members, each an independent branch of the step
- * (concurrent on the GPU); results and the group / member numbering of every
- * call are the same as for one block. */
+/* Member blocks are invisible to the caller: results (bit for bit, for a given
+ * kernel choice) and the group / member numbering of every call are the same
+ * as for one block. */
 typedef struct {
     int n_groups;                  /* >= 1 */
     const dns_group_desc* groups;  /* n_groups entries, copied by dns_create */

@@ -43,7 +43,8 @@ class dns_group_desc(ctypes.Structure):
     _fields_ = [("flow", ctypes.c_int), ("mx", ctypes.c_int), ("my", ctypes.c_int), ("mz", ctypes.c_int),
                 ("lx", ctypes.c_double), ("lz", ctypes.c_double), ("re", ctypes.c_double),
                 ("dt", ctypes.c_double), ("u_wall", ctypes.c_double), ("bulk_flux", ctypes.c_double),
-                ("members", ctypes.c_int), ("shared_mean", ctypes.c_int), ("nonlinear_form", ctypes.c_int)]
+                ("members", ctypes.c_int), ("shared_mean", ctypes.c_int), ("nonlinear_form", ctypes.c_int),
+                ("member_block", ctypes.c_int)]
 
 
 class dns_config(ctypes.Structure):
@@ -239,14 +240,16 @@ def make_config(groups, precision="fp64", use_graph=False, ygemm="default", auto
                 helm="default"):
     """groups: list of dicts with flow, mx, my, mz, lx, lz, re, dt, members,
     optional u_wall (1.0), bulk_flux (4/3), shared_mean (False; True: the
-    members share their kx = 0 flow, S3T-type ensemble) and form ("advective"
-    or "rotational" nonlinear term)."""
+    members share their kx = 0 flow, S3T-type ensemble), form ("advective"
+    or "rotational" nonlinear term) and member_block (0: automatic size of the
+    concurrently run member blocks)."""
     arr = (dns_group_desc * len(groups))()
     for i, g in enumerate(groups):
         arr[i] = dns_group_desc(_FLOWS[g["flow"]], g["mx"], g["my"], g["mz"], g["lx"], g["lz"], g["re"],
                                 g["dt"], g.get("u_wall", 1.0), g.get("bulk_flux", 4.0 / 3.0), g["members"],
                                 1 if g.get("shared_mean", False) else 0,
-                                {"advective": 0, "rotational": 1}[g.get("form", "advective")])
+                                {"advective": 0, "rotational": 1}[g.get("form", "advective")],
+                                int(g.get("member_block", 0)))
     cache = autotune_cache.encode() if autotune_cache else None
     cfg = dns_config(len(groups), arr, _PRECS[precision], 1 if use_graph else 0, 0, 0, cache, _YGEMM[ygemm],
                      _PLANE[plane], _YGEMM[helm])

@@ -7,6 +7,7 @@
 #include "dns_internal.hpp"
 #include "cvt.cuh"
 
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 #include <cstdarg>
@@ -354,9 +355,15 @@ int choose_variants(dns_handle* h, const dns_config* cfg, GroupView& v, int gi) 
 }
 
 // number of member blocks a group runs as
+// Number of member blocks of a group.  Several blocks run as concurrent graph
+// branches: the dominant plane kernel launches planes x members CTAs, and at
+// one or a few CTAs per SM its last wave is partly empty; a concurrent block
+// fills it.  Blocks of E/4 members (4 to 16) measured best from 8 to 64 members.
 int member_blocks(const dns_group_desc& d) {
-    if (d.shared_mean || d.members < 32) return 1;
-    return d.members / 16;
+    if (d.shared_mean) return 1;
+    int b = d.member_block;
+    if (b <= 0) b = std::min(16, std::max(4, d.members / 4));
+    return std::max(1, d.members / b);
 }
 
 }  // namespace
@@ -452,6 +459,7 @@ int dns_create(const dns_config* cfg, void* cuda_stream, dns_handle** out) {
         v.shared_mean = d.shared_mean;
         if (d.nonlinear_form != 0 && d.nonlinear_form != 1)
             return fail(h, DNS_ERR_INVALID, "group %d: nonlinear_form must be 0 or 1", gi);
+        if (d.member_block < 0) return fail(h, DNS_ERR_INVALID, "group %d: member_block must be >= 0", gi);
         v.rot = d.nonlinear_form;
         v.re = d.re; v.dt = d.dt; v.u_wall = d.u_wall; v.bulk_flux = d.bulk_flux;
         if (!make_plan(d.mx, &v.px) || !make_plan(d.mz, &v.pz))

@@ -53,6 +53,7 @@ def _g(**kw):
 @pytest.mark.parametrize("bad,code", [
     (dict(mx=40), -6), (dict(mz=128), -6), (dict(my=3), -6), (dict(my=200), -6),
     (dict(re=0.0), -1), (dict(dt=-1.0), -1), (dict(members=0), -1), (dict(lx=0.0), -1),
+    (dict(member_block=-1), -1),
 ])
 def test_invalid_configurations_are_rejected(dns, bad, code):
     with pytest.raises(dns.DnsError) as ei:

@@ -246,8 +246,9 @@ def test_autotuner_picks_a_variant_caches_it_and_matches_that_variant(tmp_path):
     ens.close()
     lines = sorted(ln for ln in open(cache) if ln.strip())
     assert len(lines) == 3
-    assert lines[0].startswith("helm 32 33 32 8 ") and lines[1].startswith("plane 32 33 32 8 ")
-    assert lines[2].startswith("ygemm 32 33 32 8 ")
+    # keyed by the member block's size: 8 members run as 2 blocks of 4, tuned once
+    assert lines[0].startswith("helm 32 33 32 4 ") and lines[1].startswith("plane 32 33 32 4 ")
+    assert lines[2].startswith("ygemm 32 33 32 4 ")
     ens2 = dns.Ensemble([g], precision="mixed", autotune_cache=cache)   # read back, no new timing
     assert dns.dns_kernel_choice(ens2.h, 0) == choice
     assert dns.dns_kernel_choice(ens2.h, 0, "plane") == plane
@@ -382,15 +383,17 @@ def test_shared_mean_with_one_member_is_the_plain_step():
             assert np.array_equal(x, y)
 
 
-def test_member_blocks_are_invisible_to_the_caller():
-    """A group of 40 members runs internally as two member blocks (20 + 20,
-    concurrent graph branches).  Members straddling the block boundary evolve
-    bit for bit as in a small group, partial set/get across the boundary
-    round-trips, and the statistics match a small group's member by member."""
-    g = group("couette", 16, 33, 16, 1.75 * np.pi, 1.2 * np.pi, 400.0, 0.01, 40)
+@pytest.mark.parametrize("block", [0, 20, 3])
+def test_member_blocks_are_invisible_to_the_caller(block):
+    """A group of 40 members runs internally as concurrent member blocks
+    (automatic: 4 x 10; 2 x 20; 13 blocks of 3 or 4).  Members straddling a
+    block boundary evolve bit for bit as in a single-block group of 8, partial
+    set/get across the boundary round-trips, and the statistics match the small
+    group's member by member."""
+    g = dict(group("couette", 16, 33, 16, 1.75 * np.pi, 1.2 * np.pi, 400.0, 0.01, 40), member_block=block)
     st = _state(g, 900, 5e-2)
     sub = {k: st[k][16:24] for k in FIELDS}
-    g8 = dict(g, members=8)
+    g8 = dict(g, members=8, member_block=8)
     for prec, pin in (("fp64", {}), ("mixed", dict(ygemm="tc", plane="lines", helm="simt"))):
         full = _run(g, st, 2, prec, use_graph=True, **pin)
         ref = _run(g8, sub, 2, prec, use_graph=True, **pin)
