@@ -133,3 +133,63 @@ def make_state(mx, my, mz, lx, lz, flow, members, seed0, amplitude,
         raise ValueError(flow)
     W = np.zeros((members, my))
     return {"v": v, "eta": eta, "U": U, "W": W}
+
+
+def make_disturbances(my, mz, lz, members, seed0, amplitude=1.0, m_max=None):
+    """Seeded disturbance vectors of one streamwise wavenumber: member e uses
+    seed `seed0 + e`; for every kz index |m| <= m_max (default all kept)
+      v_hat(y) = (1 - y^2)^2 sum_{p<=4} a_p T_p(y),  eta_hat(y) = (1 - y^2) sum_{p<=4} b_p T_p(y)
+    with complex standard normals a_p, b_p (no Hermitian constraint: a single
+    kx != 0 column), rescaled like make_state.  Returns complex128
+    [members][My-2][2 Kz + 1] arrays v, eta."""
+    Kz = truncation(mz)
+    m_max = Kz if m_max is None else min(m_max, Kz)
+    nyi = my - 2
+    yi = nodes(my)[1:-1]
+    amp = np.broadcast_to(np.asarray(amplitude, dtype=np.float64), (members,))
+    T = np.cos(np.arange(5)[:, None] * np.arccos(np.clip(yi, -1.0, 1.0))[None, :])
+    v = np.zeros((members, nyi, 2 * Kz + 1), dtype=np.complex128)
+    eta = np.zeros_like(v)
+    mask = (np.abs(np.arange(-Kz, Kz + 1)) <= m_max).astype(np.float64)
+    for e in range(members):
+        cnt = np.arange((2 * Kz + 1) * 20, dtype=np.uint64)
+        z = normal(seed0 + e, cnt).reshape(2 * Kz + 1, 4, 5)
+        a = (z[:, 0, :] + 1j * z[:, 1, :]) * mask[:, None]
+        b = (z[:, 2, :] + 1j * z[:, 3, :]) * mask[:, None]
+        ve = np.einsum("mp,pj->jm", a, T) * ((1.0 - yi ** 2) ** 2)[:, None]
+        ee = np.einsum("mp,pj->jm", b, T) * (1.0 - yi ** 2)[:, None]
+        ms = np.sum(np.abs(ve) ** 2 + np.abs(ee) ** 2) / nyi
+        s = amp[e] / np.sqrt(ms) if ms > 0 else 0.0
+        v[e] = ve * s
+        eta[e] = ee * s
+    return {"v": v, "eta": eta}
+
+
+def make_base_flow(my, mz, lz, flow, seed, streak=0.2, roll=0.02, harmonics=3, u_wall=1.0):
+    """Seeded streamwise-mean base flow (U, V, W) on the (My, Mz) grid, walls
+    included, y ascending, z_k = k Lz / Mz:
+      U = laminar + streak * (1 - y^2) sum_{m=1..H} (c_m cos m b z + s_m sin m b z)
+      psi = roll * (1 - y^2)^2 (1 + 0.3 y) sum_{m=1..H} (p_m cos m b z + q_m sin m b z)
+      V = d psi / dz,  W = -d psi / dy       (b = 2 pi / Lz)
+    so (V, W) is divergence-free and every component vanishes at the walls
+    except the laminar U.  Coefficients are standard normals of stream `seed`;
+    the y-factors are polynomials (degrees 2, 5 and 4)."""
+    y = nodes(my)
+    zk = np.arange(mz) * (lz / mz)
+    b = 2.0 * np.pi / lz
+    z = normal(seed, np.arange(4 * harmonics, dtype=np.uint64)).reshape(4, harmonics)
+    c, s, p, q = z
+    m = np.arange(1, harmonics + 1)[:, None]
+    cz = np.cos(m * b * zk[None, :])
+    sz = np.sin(m * b * zk[None, :])
+    S_u = (c[:, None] * cz + s[:, None] * sz).sum(0)
+    S_psi = (p[:, None] * cz + q[:, None] * sz).sum(0)
+    dS_psi = (m * b * (-p[:, None] * sz + q[:, None] * cz)).sum(0)
+    lam = u_wall * y if flow == "couette" else 1.0 - y ** 2
+    U = lam[:, None] + streak * (1.0 - y ** 2)[:, None] * S_u[None, :]
+    g = 1.0 - y ** 2                        # exactly 0 at the walls
+    fpsi = g * g * (1.0 + 0.3 * y)
+    dfpsi = -4.0 * y * g * (1.0 + 0.3 * y) + 0.3 * g * g
+    V = roll * fpsi[:, None] * dS_psi[None, :]
+    W = -roll * dfpsi[:, None] * S_psi[None, :]
+    return {"U": U, "V": V, "W": W}

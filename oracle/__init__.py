@@ -7,3 +7,4 @@ code with the GPU library and never calls it.
 """
 from .dns import (Channel, RK3_SUBSTEPS, cn_rk3, grid, cc_weights, cn_operators,  # noqa: F401
                   mean_operators, quad_solve, fundamental)
+from .linear import Linear  # noqa: F401
