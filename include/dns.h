@@ -98,6 +98,21 @@ typedef struct {
                               block's work.  0: automatic, E/4 clamped to [4, 16] (one block
                               below 8 members).  Values >= members give one block; < 0 is
                               DNS_ERR_INVALID.  Shared-mean groups are always one block. */
+    int linear;            /* 0: a DNS group.  1: a linearised disturbance ensemble (paper,
+                              "Diagnostic utilities that benefit from vectorization" and
+                              "Growth functional and linearized adjoint equations"): every
+                              member is one disturbance of the single streamwise wavenumber
+                              kx = kx_index 2 pi / lx with every kept kz, advanced by the
+                              forward equations d/dt u' = -[(B . grad) u' + (u' . grad) B]
+                              - grad p' + lap u' / Re, or by the adjoint equations in reversed
+                              time (dns_set_direction), about the group's frozen
+                              streamwise-mean base flow B (dns_set_base_flow; zero until set),
+                              with the DNS's CN/RK3 scheme and step dt.  The state has one kx
+                              column (dns_state_shape reports n_kx = 1) and no mean profiles:
+                              U00, W00 are ignored by dns_set_state (may be NULL) and read as
+                              zero.  mx, flow, u_wall, bulk_flux and member_block are ignored
+                              (always one block); shared_mean and nonlinear_form must be 0. */
+    int kx_index;          /* linear groups: n >= 1 (DNS_ERR_INVALID otherwise) */
 } dns_group_desc;
 
 /* Member blocks are invisible to the caller: results (bit for bit, for a given
@@ -168,14 +183,16 @@ int dns_workspace_size(const dns_handle* h, size_t* bytes);
  * small), DNS_ERR_INVALID (misaligned / NULL), DNS_ERR_CUDA. */
 int dns_bind_workspace(dns_handle* h, void* dev_ptr, size_t bytes);
 
-/* Sizes of group `group`: n_kx = Kx + 1, n_kz = 2 Kz + 1, ny_int = My - 2, my = My. */
+/* Sizes of group `group`: n_kx = Kx + 1 (1 for a linear group), n_kz = 2 Kz + 1,
+ * ny_int = My - 2, my = My. */
 int dns_state_shape(const dns_handle* h, int group, int* n_kx, int* n_kz, int* ny_int, int* my);
 
 /* Copy `count` members starting at `member0` of group `group` into the library
  * (layout in the header comment).  ptr_kind: 0 = host pointers (pageable or
  * pinned), 1 = device pointers.  The n = 0 column is replaced by its Hermitian
  * part in m, x(0,m) := (x(0,m) + conj x(0,-m))/2 (the only part a real field
- * carries), and the (0,0) entries are zeroed.  Host pointers are read before
+ * carries), and the (0,0) entries are zeroed (DNS groups; a linear group's
+ * single column is stored as given).  Host pointers are read before
  * the call returns.  Errors: DNS_ERR_INVALID (range, NULL), DNS_ERR_CUDA. */
 int dns_set_state(dns_handle* h, int group, int member0, int count,
                   const double* v_hat, const double* eta_hat,
@@ -283,6 +300,50 @@ int dns_export_operators(const dns_handle* h, int group, int h_index, int pair,
  * shared-mean group can reach it),
  * DNS_ERR_CUDA (address lookup or launch failed). */
 int dns_stats_noalloc(dns_handle* h, int group, double* out_dev);
+
+/* ---- Linearised disturbance groups (dns_group_desc.linear = 1).
+ * dns_stats of a linear group reports in e_pert (and e_total) the energy of
+ * each disturbance, E = (1/4) sum_kz sum_j w_j (|u|^2 + |v|^2 + |w|^2) over the
+ * interior Chebyshev nodes (w_j Clenshaw-Curtis weights): the volume average of
+ * |u|^2 / 2 of the complex single-harmonic field. */
+
+/* Frozen base flow of linear group `group`: U, V, W, each [My][Mz] row-major
+ * on the Chebyshev nodes y_j (ascending, walls included) times the uniform
+ * z_k = k lz / Mz.  Each field is truncated to the kept kz (|m| <= Kz) before
+ * use, so that its products with the disturbances are free of aliasing; d/dy
+ * is taken by the collocation derivative, d/dz spectrally.  (V, W) should be
+ * divergence-free and every field but U zero at the walls; the library does not
+ * check.  ptr_kind: 0 host, 1 device.  Synchronises the stream.
+ * Errors: DNS_ERR_INVALID (not a linear group, NULL, non-finite values, unbound
+ * workspace), DNS_ERR_CUDA. */
+int dns_set_base_flow(dns_handle* h, int group, const double* U, const double* V, const double* W, int ptr_kind);
+
+/* Equations the following dns_step calls advance linear group `group` with
+ * (group = -1: every linear group): adjoint = 0 the forward linearised
+ * equations, otherwise the adjoint equations (in reversed time).  Enqueued on
+ * the stream (a captured step graph serves both directions).
+ * Errors: DNS_ERR_INVALID (not a linear group, unbound workspace). */
+int dns_set_direction(dns_handle* h, int group, int adjoint);
+
+/* Modified Gram-Schmidt of the members of linear group `group`, in member
+ * order, in the energy inner product (the one dns_stats reports): member k is
+ * normalised after the projections on members 0..k-1 are removed.  norms
+ * (optional host array [members]) receives each member's energy norm sqrt(E)
+ * just before its normalisation; with norms the call synchronises, without it
+ * it is only enqueued.  Errors: DNS_ERR_INVALID, DNS_ERR_CUDA. */
+int dns_orthonormalize(dns_handle* h, int group, double* norms);
+
+/* One iteration of the forward-adjoint optimal-growth method (Luchini 2000, as
+ * the paper's optimal-disturbance ensembles use it) on a handle whose groups
+ * are all linear: nsteps forward steps, nsteps adjoint steps starting from the
+ * forward result, Gram-Schmidt (dns_orthonormalize) of every group; the
+ * members are left orthonormal, ready for the next iteration, and the
+ * direction forward.  gains (optional host array, the members of group 0, then
+ * group 1, ...) receives the norms, which converge to the energy gains G_k =
+ * E(T) / E(0) of the leading optimal disturbances (T = nsteps dt) once the
+ * members have unit energy.  With gains the call synchronises.
+ * Errors: DNS_ERR_INVALID (a non-linear group, nsteps < 1), DNS_ERR_CUDA. */
+int dns_optimal_sweep(dns_handle* h, int nsteps, double* gains);
 
 #ifdef __cplusplus
 }

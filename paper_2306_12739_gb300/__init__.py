@@ -35,7 +35,8 @@ EXPORTED = ["dns_create", "dns_workspace_size", "dns_bind_workspace", "dns_state
             "dns_set_state", "dns_get_state", "dns_step", "dns_stats", "dns_destroy",
             "dns_last_error", "dns_last_launch_count", "dns_export_grid", "dns_export_operators",
             "dns_step_timed", "dns_stats_noalloc", "dns_selftest_timeout", "dns_kernel_choice",
-            "dns_convert_selftest"]
+            "dns_convert_selftest", "dns_set_base_flow", "dns_set_direction", "dns_orthonormalize",
+            "dns_optimal_sweep"]
 KERNEL_CLASSES = ["mean_deriv", "yderiv", "plane", "forcing", "helm", "mean"]
 
 
@@ -44,7 +45,7 @@ class dns_group_desc(ctypes.Structure):
                 ("lx", ctypes.c_double), ("lz", ctypes.c_double), ("re", ctypes.c_double),
                 ("dt", ctypes.c_double), ("u_wall", ctypes.c_double), ("bulk_flux", ctypes.c_double),
                 ("members", ctypes.c_int), ("shared_mean", ctypes.c_int), ("nonlinear_form", ctypes.c_int),
-                ("member_block", ctypes.c_int)]
+                ("member_block", ctypes.c_int), ("linear", ctypes.c_int), ("kx_index", ctypes.c_int)]
 
 
 class dns_config(ctypes.Structure):
@@ -84,6 +85,10 @@ _lib.dns_kernel_choice.argtypes = [_H, ctypes.c_int, ctypes.POINTER(ctypes.c_int
                                    ctypes.POINTER(ctypes.c_int)]
 _lib.dns_export_grid.argtypes = [_H, ctypes.c_int, _dp, _dp, _dp, _dp, _dp]
 _lib.dns_export_operators.argtypes = [_H, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp]
+_lib.dns_set_base_flow.argtypes = [_H, ctypes.c_int, _vp, _vp, _vp, ctypes.c_int]
+_lib.dns_set_direction.argtypes = [_H, ctypes.c_int, ctypes.c_int]
+_lib.dns_orthonormalize.argtypes = [_H, ctypes.c_int, _vp]
+_lib.dns_optimal_sweep.argtypes = [_H, ctypes.c_int, _vp]
 
 
 class DnsError(RuntimeError):
@@ -192,10 +197,26 @@ def dns_kernel_choice(h, group, which="ygemm"):
     c, p, m = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
     _ck(h, _lib.dns_kernel_choice(h, group, ctypes.byref(c), ctypes.byref(p), ctypes.byref(m)))
     if which == "plane":
-        return {1: "cta", 2: "cluster", 3: "lines"}.get(p.value, p.value)
+        return {1: "cta", 2: "cluster", 3: "lines", 4: "linear"}.get(p.value, p.value)
     if which == "helm":
         return {1: "simt", 2: "tc"}.get(m.value, m.value)
     return {1: "simt", 2: "tc"}.get(c.value, c.value)
+
+
+def dns_set_base_flow(h, group, U, V, W, ptr_kind):
+    return _ck(h, _lib.dns_set_base_flow(h, group, _vp(U), _vp(V), _vp(W), ptr_kind))
+
+
+def dns_set_direction(h, group, adjoint):
+    return _ck(h, _lib.dns_set_direction(h, group, 1 if adjoint else 0))
+
+
+def dns_orthonormalize(h, group, norms_ptr=None):
+    return _ck(h, _lib.dns_orthonormalize(h, group, _vp(norms_ptr) if norms_ptr else None))
+
+
+def dns_optimal_sweep(h, nsteps, gains_ptr=None):
+    return _ck(h, _lib.dns_optimal_sweep(h, nsteps, _vp(gains_ptr) if gains_ptr else None))
 
 
 def dns_destroy(h):
@@ -241,15 +262,17 @@ def make_config(groups, precision="fp64", use_graph=False, ygemm="default", auto
     """groups: list of dicts with flow, mx, my, mz, lx, lz, re, dt, members,
     optional u_wall (1.0), bulk_flux (4/3), shared_mean (False; True: the
     members share their kx = 0 flow, S3T-type ensemble), form ("advective"
-    or "rotational" nonlinear term) and member_block (0: automatic size of the
-    concurrently run member blocks)."""
+    or "rotational" nonlinear term), member_block (0: automatic size of the
+    concurrently run member blocks), linear (True: a linearised disturbance
+    ensemble of one streamwise wavenumber) and kx_index (its n >= 1)."""
     arr = (dns_group_desc * len(groups))()
     for i, g in enumerate(groups):
         arr[i] = dns_group_desc(_FLOWS[g["flow"]], g["mx"], g["my"], g["mz"], g["lx"], g["lz"], g["re"],
                                 g["dt"], g.get("u_wall", 1.0), g.get("bulk_flux", 4.0 / 3.0), g["members"],
                                 1 if g.get("shared_mean", False) else 0,
                                 {"advective": 0, "rotational": 1}[g.get("form", "advective")],
-                                int(g.get("member_block", 0)))
+                                int(g.get("member_block", 0)), 1 if g.get("linear", False) else 0,
+                                int(g.get("kx_index", 0)))
     cache = autotune_cache.encode() if autotune_cache else None
     cfg = dns_config(len(groups), arr, _PRECS[precision], 1 if use_graph else 0, 0, 0, cache, _YGEMM[ygemm],
                      _PLANE[plane], _YGEMM[helm])
@@ -288,10 +311,17 @@ class Ensemble:
         except Exception:
             pass
 
-    def set_state(self, group, v, eta, U, W, member0=0):
-        """v, eta complex128 [count][Ny][NKZ][NKX]; U, W float64 [count][My].
+    def set_state(self, group, v, eta, U=None, W=None, member0=0):
+        """v, eta complex128 [count][Ny][NKZ][NKX]; U, W float64 [count][My]
+        (None for a linear group, whose NKX is 1 and which has no mean profiles).
         numpy arrays (host) or torch CUDA tensors (device, complex128/float64)."""
         torch = self.torch
+        if U is None or W is None:
+            nkx, nkz, ny, _ = self.shapes[group]
+            arrs = [np.ascontiguousarray(np.reshape(a, (-1, ny, nkz, nkx)), dtype=np.complex128) for a in (v, eta)]
+            dns_set_state(self.h, group, member0, arrs[0].shape[0], arrs[0].ctypes.data, arrs[1].ctypes.data,
+                          None, None, 0)
+            return
         if isinstance(v, torch.Tensor):
             ts = [t.contiguous() for t in (v, eta, U, W)]
             count = ts[0].shape[0]
@@ -316,6 +346,30 @@ class Ensemble:
 
     def step(self, nsteps=1):
         dns_step(self.h, nsteps)
+
+    # ---- linearised disturbance groups
+    def set_base_flow(self, group, U, V, W):
+        """U, V, W float64 [My][Mz] on the Chebyshev nodes x uniform z (host)."""
+        a = [np.ascontiguousarray(x, dtype=np.float64) for x in (U, V, W)]
+        dns_set_base_flow(self.h, group, a[0].ctypes.data, a[1].ctypes.data, a[2].ctypes.data, 0)
+
+    def set_direction(self, adjoint, group=-1):
+        dns_set_direction(self.h, group, adjoint)
+
+    def orthonormalize(self, group):
+        """Energy-norm modified Gram-Schmidt of the group's members; returns the
+        norms before normalisation."""
+        r = np.zeros(self.groups[group]["members"])
+        dns_orthonormalize(self.h, group, r.ctypes.data)
+        return r
+
+    def optimal_sweep(self, nsteps):
+        """One forward-adjoint iteration of every (linear) group; returns the
+        gains per group."""
+        sizes = [g["members"] for g in self.groups]
+        out = np.zeros(sum(sizes))
+        dns_optimal_sweep(self.h, nsteps, out.ctypes.data)
+        return np.split(out, np.cumsum(sizes)[:-1])
 
     def step_timed(self, nsteps=1):
         return dns_step_timed(self.h, nsteps)

@@ -8,6 +8,7 @@
 #include "cvt.cuh"
 
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <cstdarg>
@@ -133,6 +134,12 @@ size_t layout_group(dns_handle* h, HostGroup& G, size_t cur) {
     add((void**)&v.AU, sizeof(double) * (size_t)v.E * v.my);
     add((void**)&v.AW, sizeof(double) * (size_t)v.E * v.my);
     add((void**)&v.gamma, sizeof(double) * v.E);
+    if (v.lin) {
+        add((void**)&v.dir, 256);
+        add((void**)&v.gsr, sizeof(double) * v.E);
+        add((void**)&v.base, sizeof(double) * 9 * (size_t)v.ny * v.mz);
+        if (precision_mixed(h)) add((void**)&v.basef, sizeof(float) * 9 * (size_t)v.ny * v.mz);
+    }
     const size_t elem = precision_mixed(h) ? sizeof(float2) : sizeof(double2);
     add(&v.P5, elem * 5 * S);
     add(&v.N3, elem * 3 * S);
@@ -192,7 +199,8 @@ void enqueue_group(dns_handle* h, HostGroup& G, cudaStream_t st, Timer* tm) {
             if (g.ygemm == 2) dnsk::launch_yderiv_tc(g, cv, ce, st);
             else dnsk::launch_yderiv_t(g, cv, ce, st);
             mark(DNS_K_YDERIV);
-            if (g.plane == 2) dnsk::launch_plane_cl(g, false, cU, cW, st);
+            if (g.lin) dnsk::launch_lin_plane(g, false, st);
+            else if (g.plane == 2) dnsk::launch_plane_cl(g, false, cU, cW, st);
             else if (g.plane == 3) dnsk::launch_plane_lines(g, cU, cW, st);
             else dnsk::launch_plane_f32(g, cU, cW, st);
             mark(DNS_K_PLANE);
@@ -201,7 +209,8 @@ void enqueue_group(dns_handle* h, HostGroup& G, cudaStream_t st, Timer* tm) {
         } else {
             dnsk::launch_yderiv<double>(g, cv, ce, g.P5, st);
             mark(DNS_K_YDERIV);
-            if (g.plane == 2) dnsk::launch_plane_cl(g, true, cU, cW, st);
+            if (g.lin) dnsk::launch_lin_plane(g, true, st);
+            else if (g.plane == 2) dnsk::launch_plane_cl(g, true, cU, cW, st);
             else dnsk::launch_plane_state<double>(g, cU, cW, st);
             mark(DNS_K_PLANE);
             if (g.shared_mean && g.E > 1) { dnsk::launch_shared_mean(g, true, st); h->launches += 1; }
@@ -216,6 +225,10 @@ void enqueue_group(dns_handle* h, HostGroup& G, cudaStream_t st, Timer* tm) {
             dnsk::launch_helm(g, s, st);
         }
         mark(DNS_K_HELM);
+        if (g.lin) {   // no mean flow
+            h->launches += 4;
+            continue;
+        }
         // the mean-flow rows ran as leading CTAs of the implicit apply; gamma and
         // the profiles
         dnsk::launch_mean_finish(g, s, st);
@@ -336,13 +349,17 @@ int choose_variants(dns_handle* h, const dns_config* cfg, GroupView& v, int gi) 
     // cluster (distributed shared memory) where it does not; where both exist
     // the autotuner decides at bind time
     const bool mixed = precision_mixed(h);
-    const bool ok[4] = {false, plane_variant_ok(mixed, v, 1), plane_variant_ok(mixed, v, 2),
-                        plane_variant_ok(mixed, v, 3)};
-    const int navail = ok[1] + ok[2] + ok[3];
-    if (navail == 0)
-        return fail(h, DNS_ERR_UNSUPPORTED, "group %d: no plane-stage kernel for %dx%d", gi, d.mx, d.mz);
-    v.plane = navail == 1 ? (ok[1] ? 1 : ok[2] ? 2 : 3) : (mixed ? 0 : 1);
-    if (navail > 1 && cfg->plane >= 1 && cfg->plane <= 3 && ok[cfg->plane]) v.plane = cfg->plane;
+    if (v.lin) {
+        v.plane = 4;   // the z-only linearised plane stage, the only one a linear group has
+    } else {
+        const bool ok[4] = {false, plane_variant_ok(mixed, v, 1), plane_variant_ok(mixed, v, 2),
+                            plane_variant_ok(mixed, v, 3)};
+        const int navail = ok[1] + ok[2] + ok[3];
+        if (navail == 0)
+            return fail(h, DNS_ERR_UNSUPPORTED, "group %d: no plane-stage kernel for %dx%d", gi, d.mx, d.mz);
+        v.plane = navail == 1 ? (ok[1] ? 1 : ok[2] ? 2 : 3) : (mixed ? 0 : 1);
+        if (navail > 1 && cfg->plane >= 1 && cfg->plane <= 3 && ok[cfg->plane]) v.plane = cfg->plane;
+    }
     if (precision_mixed(h)) {
         size_t m1 = dnsk::helm_t_smem_bytes(v), m2 = dnsk::yderiv_t_smem_bytes(v), m3 = dnsk::forcing_t_smem_bytes(v);
         if (v.helm != 1 && dnsk::helm_tc_smem_bytes(v) > m1) m1 = dnsk::helm_tc_smem_bytes(v);
@@ -360,7 +377,7 @@ int choose_variants(dns_handle* h, const dns_config* cfg, GroupView& v, int gi) 
 // one or a few CTAs per SM its last wave is partly empty; a concurrent block
 // fills it.  Blocks of E/4 members (4 to 16) measured best from 8 to 64 members.
 int member_blocks(const dns_group_desc& d) {
-    if (d.shared_mean) return 1;
+    if (d.shared_mean || d.linear) return 1;
     int b = d.member_block;
     if (b <= 0) b = std::min(16, std::max(4, d.members / 4));
     return std::max(1, d.members / b);
@@ -435,17 +452,24 @@ int dns_create(const dns_config* cfg, void* cuda_stream, dns_handle** out) {
             continue;
         }
         G.d = d;
-        if (d.flow != DNS_COUETTE && d.flow != DNS_POISEUILLE)
+        if (d.linear != 0 && d.linear != 1) return fail(h, DNS_ERR_INVALID, "group %d: linear must be 0 or 1", gi);
+        const bool lin = d.linear == 1;
+        if (!lin && d.flow != DNS_COUETTE && d.flow != DNS_POISEUILLE)
             return fail(h, DNS_ERR_INVALID, "group %d: unknown flow", gi);
         if (!(d.re > 0) || !(d.dt > 0) || !(d.lx > 0) || !(d.lz > 0) || d.members < 1)
             return fail(h, DNS_ERR_INVALID, "group %d: re, dt, lx, lz must be > 0 and members >= 1", gi);
+        if (lin && d.kx_index < 1) return fail(h, DNS_ERR_INVALID, "group %d: kx_index must be >= 1", gi);
+        if (lin && (d.shared_mean != 0 || d.nonlinear_form != 0))
+            return fail(h, DNS_ERR_INVALID, "group %d: a linear group has no shared mean or nonlinear form", gi);
         if (d.my < 5 || d.my > 129) return fail(h, DNS_ERR_UNSUPPORTED, "group %d: My=%d outside 5..129", gi, d.my);
-        if (!supported_m(d.mx) || !supported_m(d.mz))
-            return fail(h, DNS_ERR_UNSUPPORTED, "group %d: Mx, Mz must be 16, 32, 48 or 64", gi);
+        if ((!lin && !supported_m(d.mx)) || !supported_m(d.mz))
+            return fail(h, DNS_ERR_UNSUPPORTED, "group %d: Mx, Mz must be 16, 32, 48, 64 or 128", gi);
         GroupView& v = G.v;
         memset(&v, 0, sizeof v);
-        v.mx = d.mx; v.my = d.my; v.mz = d.mz;
-        v.kx = (d.mx - 1) / 3; v.kz = (d.mz - 1) / 3;
+        // a linear group has no x grid: one kx column, kxt[0] = kx_index * 2 pi / lx
+        v.lin = lin ? 1 : 0;
+        v.mx = lin ? 0 : d.mx; v.my = d.my; v.mz = d.mz;
+        v.kx = lin ? 0 : (d.mx - 1) / 3; v.kz = (d.mz - 1) / 3;
         v.nkx = v.kx + 1; v.nkz = 2 * v.kz + 1;
         v.nmodes = v.nkx * v.nkz;
         v.ny = d.my - 2;
@@ -462,7 +486,7 @@ int dns_create(const dns_config* cfg, void* cuda_stream, dns_handle** out) {
         if (d.member_block < 0) return fail(h, DNS_ERR_INVALID, "group %d: member_block must be >= 0", gi);
         v.rot = d.nonlinear_form;
         v.re = d.re; v.dt = d.dt; v.u_wall = d.u_wall; v.bulk_flux = d.bulk_flux;
-        if (!make_plan(d.mx, &v.px) || !make_plan(d.mz, &v.pz))
+        if ((!lin && !make_plan(d.mx, &v.px)) || !make_plan(d.mz, &v.pz))
             return fail(h, DNS_ERR_UNSUPPORTED, "group %d: no radix plan", gi);
         {
             int rcv = choose_variants(h, cfg, v, gi);
@@ -472,7 +496,7 @@ int dns_create(const dns_config* cfg, void* cuda_stream, dns_handle** out) {
         G.grid = dnsb::build_grid(d.my);
         double a1 = dnsb::fundamental(d.lx), a3 = dnsb::fundamental(d.lz);
         G.kxt.resize(v.nkx); G.kzt.resize(v.nkz);
-        for (int n = 0; n < v.nkx; ++n) G.kxt[n] = n * a1;
+        for (int n = 0; n < v.nkx; ++n) G.kxt[n] = (lin ? d.kx_index : n) * a1;
         for (int mi = 0; mi < v.nkz; ++mi) G.kzt[mi] = (mi - v.kz) * a3;
         G.k2t.resize(v.nmodes); G.k2inv.resize(v.nmodes);
         for (int mi = 0; mi < v.nkz; ++mi)
@@ -486,7 +510,7 @@ int dns_create(const dns_config* cfg, void* cuda_stream, dns_handle** out) {
         std::vector<double> pk2(v.npairs);
         for (int am = 0; am <= v.kz; ++am)
             for (int n = 0; n < v.nkx; ++n) {
-                double kx = n * a1, kz = am * a3;
+                double kx = G.kxt[n], kz = am * a3;
                 pk2[am * v.nkx + n] = kx * kx + kz * kz;
             }
         const double hs[2] = {0.5, 1.0};
@@ -549,7 +573,7 @@ int dns_create(const dns_config* cfg, void* cuda_stream, dns_handle** out) {
         if (v.ygemm != 1) G.Atc = dnsk::yderiv_tc_a_image(G.D1i, G.D2i, v.ny, v.kp);
         if (precision_mixed(h) && v.helm != 1)
             for (int hi = 0; hi < 2; ++hi) G.Htc[hi] = dnsk::helm_tc_a_images(G.opsdev[hi], v.npairs, v.ny, v.kp);
-        G.twx = dnsb::twiddles(d.mx);
+        if (!lin) G.twx = dnsb::twiddles(d.mx);
         G.twz = dnsb::twiddles(d.mz);
         G.twxf.assign(G.twx.begin(), G.twx.end());
         G.twzf.assign(G.twz.begin(), G.twz.end());
@@ -597,6 +621,7 @@ int dns_bind_workspace(dns_handle* h, void* dev_ptr, size_t bytes) {
     dnsk::set_attributes_plane_cl();
     dnsk::set_attributes_plane_lines();
     dnsk::set_attributes_helm_tc();
+    dnsk::set_attributes_linear();
     {
         int rc0 = check(h, cudaGetLastError(), "kernel attributes");
         if (rc0) return rc0;
@@ -767,7 +792,7 @@ static int set_state_block(dns_handle* h, int group, int member0, int count, con
                   const double* eta_hat, const double* U00, const double* W00, int ptr_kind) {
     GroupView& v = h->groups[group].v;
     if (member0 < 0 || count < 1 || member0 + count > v.E) return fail(h, DNS_ERR_INVALID, "member range");
-    if (!v_hat || !eta_hat || !U00 || !W00) return fail(h, DNS_ERR_INVALID, "NULL state pointer");
+    if (!v_hat || !eta_hat || (!v.lin && (!U00 || !W00))) return fail(h, DNS_ERR_INVALID, "NULL state pointer");
     if (ptr_kind != 0 && ptr_kind != 1) return fail(h, DNS_ERR_INVALID, "ptr_kind must be 0 or 1");
     cudaMemcpyKind k = ptr_kind ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     const size_t per = (size_t)count * v.ny * v.nmodes;
@@ -775,10 +800,14 @@ static int set_state_block(dns_handle* h, int group, int member0, int count, con
     int rc;
     if ((rc = check(h, cudaMemcpyAsync(v.stage, v_hat, per * sizeof(double2), k, st), "set v"))) return rc;
     if ((rc = check(h, cudaMemcpyAsync(v.stage + per, eta_hat, per * sizeof(double2), k, st), "set eta"))) return rc;
-    if ((rc = check(h, cudaMemcpyAsync(v.U_t + (size_t)member0 * v.my, U00, sizeof(double) * count * v.my, k, st), "set U")))
-        return rc;
-    if ((rc = check(h, cudaMemcpyAsync(v.W_t + (size_t)member0 * v.my, W00, sizeof(double) * count * v.my, k, st), "set W")))
-        return rc;
+    if (!v.lin) {   // a linear group has no mean profiles (they stay zero)
+        if ((rc = check(h, cudaMemcpyAsync(v.U_t + (size_t)member0 * v.my, U00, sizeof(double) * count * v.my, k, st),
+                        "set U")))
+            return rc;
+        if ((rc = check(h, cudaMemcpyAsync(v.W_t + (size_t)member0 * v.my, W00, sizeof(double) * count * v.my, k, st),
+                        "set W")))
+            return rc;
+    }
     dnsk::launch_pack(v, member0, count, st);
     if ((rc = check(h, cudaGetLastError(), "pack state"))) return rc;
     // host buffers may be pageable and reused by the caller right away
@@ -793,16 +822,16 @@ int dns_set_state(dns_handle* h, int group, int member0, int count, const double
     if (group < 0 || group >= (int)h->parts.size()) return fail(h, DNS_ERR_INVALID, "bad group");
     const int E = h->descs[group].members;
     if (member0 < 0 || count < 1 || member0 + count > E) return fail(h, DNS_ERR_INVALID, "member range");
-    if (!v_hat || !eta_hat || !U00 || !W00) return fail(h, DNS_ERR_INVALID, "NULL state pointer");
     const GroupView& v0 = h->groups[h->parts[group][0].ig].v;
+    if (!v_hat || !eta_hat || (!v0.lin && (!U00 || !W00))) return fail(h, DNS_ERR_INVALID, "NULL state pointer");
     const size_t pm = (size_t)v0.ny * v0.nmodes * 2, pu = (size_t)v0.my;   // doubles per member
     for (const auto& P : h->parts[group]) {
         const int lo = member0 > P.m0 ? member0 : P.m0;
         const int hi = (member0 + count) < (P.m0 + P.E) ? (member0 + count) : (P.m0 + P.E);
         if (lo >= hi) continue;
         const size_t o = (size_t)(lo - member0);
-        int rc = set_state_block(h, P.ig, lo - P.m0, hi - lo, v_hat + o * pm, eta_hat + o * pm, U00 + o * pu,
-                                 W00 + o * pu, ptr_kind);
+        int rc = set_state_block(h, P.ig, lo - P.m0, hi - lo, v_hat + o * pm, eta_hat + o * pm,
+                                 U00 ? U00 + o * pu : nullptr, W00 ? W00 + o * pu : nullptr, ptr_kind);
         if (rc) return rc;
     }
     return DNS_OK;
@@ -987,6 +1016,173 @@ int dns_stats_noalloc(dns_handle* h, int group, double* out_dev) {
         if ((rc = check(h, cudaGetLastError(), "dns_stats_noalloc launch"))) return rc;
     }
     return DNS_OK;
+}
+
+// ---- linearised disturbance groups
+
+// Base flow on the (My, Mz) grid -> the nine fields the linear plane stage
+// reads, on the interior planes: B, d_y B, d_z B for B = U, V, W.  Each field
+// is truncated to |m| <= Kz first (its products with the disturbances are then
+// free of aliasing on the 3/2 grid); d_y is the collocation derivative D1 on
+// all My nodes, d_z spectral.  Plain host DFTs with the library's twiddles.
+static void base_fields(const HostGroup& G, const std::vector<double>* f, std::vector<double>& out) {
+    const GroupView& v = G.v;
+    const int My = v.my, Mz = v.mz, Kz = v.kz, Ny = v.ny, NM = v.nkz;
+    const std::vector<double> tw = dnsb::twiddles(Mz);   // exp(-2 pi i t / Mz)
+    out.assign((size_t)9 * Ny * Mz, 0.0);
+    std::vector<double> val((size_t)My * Mz), dz((size_t)My * Mz), cr(NM), ci(NM);
+    for (int c = 0; c < 3; ++c) {
+        const std::vector<double>& F = f[c];
+        for (int y = 0; y < My; ++y) {
+            for (int mi = 0; mi < NM; ++mi) {
+                const int m = mi - Kz;
+                double ar = 0.0, ai = 0.0;
+                for (int z = 0; z < Mz; ++z) {
+                    const int t = (int)((((long long)m * z) % Mz + Mz) % Mz);
+                    ar += F[(size_t)y * Mz + z] * tw[2 * t];
+                    ai += F[(size_t)y * Mz + z] * tw[2 * t + 1];
+                }
+                cr[mi] = ar / Mz;
+                ci[mi] = ai / Mz;
+            }
+            for (int z = 0; z < Mz; ++z) {
+                double sv = 0.0, sd = 0.0;
+                for (int mi = 0; mi < NM; ++mi) {
+                    const int m = mi - Kz;
+                    const int t = (int)((((long long)m * z) % Mz + Mz) % Mz);
+                    // exp(+2 pi i m z / Mz) = conj of the forward twiddle
+                    const double er = tw[2 * t], ei = -tw[2 * t + 1];
+                    sv += cr[mi] * er - ci[mi] * ei;
+                    // i kz c exp(...): real part -kz (c_r e_i + c_i e_r)
+                    sd += -G.kzt[mi] * (cr[mi] * ei + ci[mi] * er);
+                }
+                val[(size_t)y * Mz + z] = sv;
+                dz[(size_t)y * Mz + z] = sd;
+            }
+        }
+        for (int y = 1; y < My - 1; ++y)
+            for (int z = 0; z < Mz; ++z) {
+                double dy = 0.0;
+                for (int k = 0; k < My; ++k) dy += G.grid.D1[(size_t)y * My + k] * val[(size_t)k * Mz + z];
+                const size_t o = (size_t)(y - 1) * Mz + z;
+                out[(size_t)c * Ny * Mz + o] = val[(size_t)y * Mz + z];
+                out[(size_t)(3 + c) * Ny * Mz + o] = dy;
+                out[(size_t)(6 + c) * Ny * Mz + o] = dz[(size_t)y * Mz + z];
+            }
+    }
+}
+
+static int linear_group(dns_handle* h, int group, HostGroup** G) {
+    if (!h->bound) return fail(h, DNS_ERR_INVALID, "workspace not bound");
+    if (group < 0 || group >= (int)h->parts.size()) return fail(h, DNS_ERR_INVALID, "bad group");
+    HostGroup& g = h->groups[h->parts[group][0].ig];
+    if (!g.v.lin) return fail(h, DNS_ERR_INVALID, "group %d is not a linear group", group);
+    *G = &g;
+    return DNS_OK;
+}
+
+int dns_set_base_flow(dns_handle* h, int group, const double* U, const double* V, const double* W, int ptr_kind) {
+    if (!h) return DNS_ERR_INVALID;
+    HostGroup* G = nullptr;
+    int rc = linear_group(h, group, &G);
+    if (rc) return rc;
+    if (!U || !V || !W) return fail(h, DNS_ERR_INVALID, "NULL base-flow pointer");
+    if (ptr_kind != 0 && ptr_kind != 1) return fail(h, DNS_ERR_INVALID, "ptr_kind must be 0 or 1");
+    GroupView& v = G->v;
+    const size_t n = (size_t)v.my * v.mz;
+    std::vector<double> f[3];
+    const double* src[3] = {U, V, W};
+    for (int c = 0; c < 3; ++c) {
+        f[c].resize(n);
+        if (ptr_kind == 1) {
+            if ((rc = check(h, cudaMemcpyAsync(f[c].data(), src[c], n * 8, cudaMemcpyDeviceToHost, h->stream),
+                            "read base flow")))
+                return rc;
+        } else {
+            memcpy(f[c].data(), src[c], n * 8);
+        }
+    }
+    if (ptr_kind == 1 && (rc = check(h, cudaStreamSynchronize(h->stream), "read base flow"))) return rc;
+    for (int c = 0; c < 3; ++c)
+        for (double x : f[c])
+            if (!std::isfinite(x)) return fail(h, DNS_ERR_INVALID, "base flow holds a non-finite value");
+    std::vector<double> b;
+    base_fields(*G, f, b);
+    if ((rc = check(h, cudaMemcpyAsync((void*)v.base, b.data(), b.size() * 8, cudaMemcpyHostToDevice, h->stream),
+                    "upload base flow")))
+        return rc;
+    std::vector<float> bf;
+    if (precision_mixed(h)) {
+        bf.assign(b.begin(), b.end());
+        if ((rc = check(h, cudaMemcpyAsync((void*)v.basef, bf.data(), bf.size() * 4, cudaMemcpyHostToDevice, h->stream),
+                        "upload base flow")))
+            return rc;
+    }
+    return check(h, cudaStreamSynchronize(h->stream), "set base flow");
+}
+
+int dns_set_direction(dns_handle* h, int group, int adjoint) {
+    if (!h) return DNS_ERR_INVALID;
+    if (group == -1) {
+        if (!h->bound) return fail(h, DNS_ERR_INVALID, "workspace not bound");
+        for (auto& G : h->groups)
+            if (G.v.lin) {
+                int rc = check(h, cudaMemsetAsync(G.v.dir, adjoint ? 1 : 0, sizeof(int), h->stream), "set direction");
+                if (rc) return rc;
+            }
+        return DNS_OK;
+    }
+    HostGroup* G = nullptr;
+    int rc = linear_group(h, group, &G);
+    if (rc) return rc;
+    return check(h, cudaMemsetAsync(G->v.dir, adjoint ? 1 : 0, sizeof(int), h->stream), "set direction");
+}
+
+int dns_orthonormalize(dns_handle* h, int group, double* norms) {
+    if (!h) return DNS_ERR_INVALID;
+    HostGroup* G = nullptr;
+    int rc = linear_group(h, group, &G);
+    if (rc) return rc;
+    dnsk::launch_lin_orthonormalize(G->v, h->stream);
+    if ((rc = check(h, cudaGetLastError(), "orthonormalize launch"))) return rc;
+    if (!norms) return DNS_OK;
+    if ((rc = check(h, cudaMemcpyAsync(norms, G->v.gsr, sizeof(double) * G->v.E, cudaMemcpyDeviceToHost, h->stream),
+                    "read norms")))
+        return rc;
+    if ((rc = check(h, cudaStreamSynchronize(h->stream), "orthonormalize"))) return rc;
+    return device_status(h);
+}
+
+int dns_optimal_sweep(dns_handle* h, int nsteps, double* gains) {
+    if (!h) return DNS_ERR_INVALID;
+    if (!h->bound) return fail(h, DNS_ERR_INVALID, "workspace not bound");
+    if (nsteps < 1) return fail(h, DNS_ERR_INVALID, "nsteps < 1");
+    for (auto& G : h->groups)
+        if (!G.v.lin) return fail(h, DNS_ERR_INVALID, "dns_optimal_sweep needs every group to be linear");
+    int rc;
+    if ((rc = dns_set_direction(h, -1, 0))) return rc;
+    if ((rc = dns_step(h, nsteps))) return rc;
+    int launches = h->launches;
+    if ((rc = dns_set_direction(h, -1, 1))) return rc;
+    if ((rc = dns_step(h, nsteps))) return rc;
+    launches += h->launches;
+    if ((rc = dns_set_direction(h, -1, 0))) return rc;
+    for (auto& G : h->groups) {
+        launches += dnsk::launch_lin_orthonormalize(G.v, h->stream);
+        if ((rc = check(h, cudaGetLastError(), "orthonormalize launch"))) return rc;
+    }
+    h->launches = launches;
+    if (!gains) return DNS_OK;
+    size_t off = 0;
+    for (auto& G : h->groups) {
+        if ((rc = check(h, cudaMemcpyAsync(gains + off, G.v.gsr, sizeof(double) * G.v.E, cudaMemcpyDeviceToHost,
+                                           h->stream),
+                        "read gains")))
+            return rc;
+        off += G.v.E;
+    }
+    if ((rc = check(h, cudaStreamSynchronize(h->stream), "optimal sweep"))) return rc;
+    return device_status(h);
 }
 
 int dns_selftest_timeout(dns_handle* h) {

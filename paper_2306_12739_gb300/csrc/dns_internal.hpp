@@ -29,6 +29,13 @@ struct GroupView {
     int flow;             // 0 Couette, 1 Poiseuille
     int shared_mean;      // 1: the members share the kx = 0 flow (forcing averaged over members)
     int rot;              // nonlinear term: 0 advective u . grad u, 1 rotational omega x u
+    int lin;              // 1: linearised disturbance group: one kx != 0 column (nkx = 1, kxt[0]),
+                          //    no mean mode, members are disturbance vectors
+    int* dir;             // linear groups: device word, 0 forward equations, nonzero adjoint
+    const double* base;   // linear groups: [9][Ny][Mz] U, V, W, d_y(U, V, W), d_z(U, V, W) of the
+                          //    base flow on the interior planes
+    const float* basef;   // single-precision copy (mixed path)
+    double* gsr;          // linear groups: [E] energy norms recorded by the last Gram-Schmidt
     double re, dt, u_wall, bulk_flux;
     FftPlan px, pz;
     // constants
@@ -83,7 +90,12 @@ void launch_forcing(const GroupView& g, int s, cudaStream_t st);
 void launch_helm(const GroupView& g, int s, cudaStream_t st);
 void launch_mean_finish(const GroupView& g, int s, cudaStream_t st);
 // CTAs of the mean-flow rows carried by the implicit-apply launches (8 rows each)
-__host__ __device__ inline int mean_row_ctas(const GroupView& g) { return g.E * ((g.ny + 7) / 8); }
+__host__ __device__ inline int mean_row_ctas(const GroupView& g) { return g.lin ? 0 : g.E * ((g.ny + 7) / 8); }
+// index of the (0, 0) mode, or -1 in a linear group (which has none)
+__host__ __device__ inline int mean_mode(const GroupView& g) { return g.lin ? -1 : g.kz * g.nkx; }
+void launch_lin_plane(const GroupView& g, bool fp64, cudaStream_t st);
+int launch_lin_orthonormalize(const GroupView& g, cudaStream_t st);   // returns the launch count
+void set_attributes_linear();
 inline size_t mean_smem_bytes(const GroupView& g) { return (8 * (size_t)g.my + 32) * sizeof(double); }
 size_t helm_t_smem_bytes(const GroupView& g);
 size_t yderiv_t_smem_bytes(const GroupView& g);

@@ -171,7 +171,7 @@ __global__ void __launch_bounds__(THREADS) k_forcing_t(GroupView g, int s) {
     __syncthreads();
     const int RB = RP / 4;
     const FastDiv dEB2((unsigned)T.EBT), dQT2((unsigned)T.QT);
-    const int q_mean = g.kz * NKX;
+    const int q_mean = mean_mode(g);
     for (int m = threadIdx.x; m < RB * T.NC; m += THREADS) {
         // consecutive threads: consecutive members (the H layout's fastest index)
         const int r = (int)dEB2.div((unsigned)m), el = m - r * T.EBT;
@@ -268,7 +268,7 @@ __global__ void __launch_bounds__(THREADS) k_helm_t(GroupView g, int s) {
     const int b = blockIdx.x - nrow;
     const int p = b % g.npairs, f = b / g.npairs;
     const int n = p % NKX, am = p / NKX;
-    if (n == 0 && am == 0) return;
+    if (!g.lin && n == 0 && am == 0) return;   // the mean mode (DNS groups)
     const int hi = (s == 0) ? 0 : 1;
     const bool needM = (s != 2);
     const int nq = am > 0 ? 2 : 1;

@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_helm_tc(GroupView g, int s) {
     const int b = blockIdx.x - nrow;
     const int p = b % g.npairs, f = b / g.npairs;
     const int n = p % NKX, am = p / NKX;
-    if (n == 0 && am == 0) return;
+    if (!g.lin && n == 0 && am == 0) return;   // the mean mode (DNS groups)
     const int hi = (s == 0) ? 0 : 1;
     const int nq = am > 0 ? 2 : 1;
     const int q1 = (g.kz + am) * NKX + n, q2 = (g.kz - am) * NKX + n;

@@ -36,7 +36,7 @@ __global__ void __launch_bounds__(256) k_na_plane(GroupView g, double* __restric
     const size_t fs = (size_t)Ny * E * nmodes;
     const double2* P = g.P5d + ((size_t)y * E + e) * nmodes;
     double uu = 0, vv = 0, ww = 0, uv = 0, dmax = 0, nf = 0;
-    const int q_mean = g.kz * NKX;
+    const int q_mean = mean_mode(g);
     for (int q = threadIdx.x; q < nmodes; q += blockDim.x) {
         const double2 v = P[q], dv = P[fs + q], et = P[3 * fs + q];
         if (!isfinite(v.x) || !isfinite(v.y) || !isfinite(et.x) || !isfinite(et.y)) nf = 1.0;
@@ -46,7 +46,7 @@ __global__ void __launch_bounds__(256) k_na_plane(GroupView g, double* __restric
         const double ax = (kx * dv.x - kz * et.x) * ki, ay = (kx * dv.y - kz * et.y) * ki;
         const double bx = (kz * dv.x + kx * et.x) * ki, by = (kz * dv.y + kx * et.y) * ki;
         const double2 u = make_double2(-ay, ax), w = make_double2(-by, bx);
-        const double c = (n == 0) ? 1.0 : 2.0;
+        const double c = (n == 0 || g.lin) ? 1.0 : 2.0;   // real fields carry -kx too
         uu += c * (u.x * u.x + u.y * u.y);
         vv += c * (v.x * v.x + v.y * v.y);
         ww += c * (w.x * w.x + w.y * w.y);

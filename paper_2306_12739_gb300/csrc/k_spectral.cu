@@ -151,7 +151,7 @@ __global__ void __launch_bounds__(256) k_forcing(GroupView g, int s) {
         phi[(qq * Ny + y) * EB + ee] = p;
     }
     __syncthreads();
-    const int q_mean = g.kz * NKX;
+    const int q_mean = mean_mode(g);
     for (int idx = threadIdx.x; idx < tile; idx += blockDim.x) {
         int ee = idx % EB;
         int y = (idx / EB) % Ny;
@@ -239,7 +239,7 @@ __global__ void __launch_bounds__(256) k_helm(GroupView g, int s) {
     const int b = blockIdx.x - nrow;
     const int p = b % g.npairs, f = b / g.npairs;
     const int n = p % NKX, am = p / NKX;
-    if (n == 0 && am == 0) return;
+    if (!g.lin && n == 0 && am == 0) return;   // the mean mode (DNS groups)
     const int hi = (s == 0) ? 0 : 1;
     const size_t nn = (size_t)Ny * Ny;
     const double* Mg = g.ops[hi] + ((size_t)p * 4 + (f == 0 ? 0 : 2)) * nn;
@@ -304,7 +304,7 @@ __global__ void __launch_bounds__(256) k_stats_plane(GroupView g) {
     const size_t fs = (size_t)Ny * E * nmodes;
     const double2* P = g.P5d + ((size_t)y * E + e) * nmodes;
     double uu = 0, vv = 0, ww = 0, uv = 0, dmax = 0, nf = 0;
-    const int q_mean = g.kz * NKX;
+    const int q_mean = mean_mode(g);
     for (int q = threadIdx.x; q < nmodes; q += blockDim.x) {
         double2 v = P[q], dv = P[fs + q], et = P[3 * fs + q];
         if (!isfinite(v.x) || !isfinite(v.y) || !isfinite(et.x) || !isfinite(et.y)) nf = 1.0;
@@ -315,7 +315,7 @@ __global__ void __launch_bounds__(256) k_stats_plane(GroupView g) {
         double ax = (kx * dv.x - kz * et.x) * ki, ay = (kx * dv.y - kz * et.y) * ki;
         double bx = (kz * dv.x + kx * et.x) * ki, by = (kz * dv.y + kx * et.y) * ki;
         double2 u = make_double2(-ay, ax), w = make_double2(-by, bx);
-        double c = (n == 0) ? 1.0 : 2.0;
+        double c = (n == 0 || g.lin) ? 1.0 : 2.0;   // real fields carry -kx too
         uu += c * (u.x * u.x + u.y * u.y);
         vv += c * (v.x * v.x + v.y * v.y);
         ww += c * (w.x * w.x + w.y * w.y);
@@ -429,14 +429,14 @@ void launch_stats(const GroupView& g, cudaStream_t st) {
 __global__ void k_pack(GroupView g, int member0, int count) {
     const int Ny = g.ny, E = g.E, nmodes = g.nmodes, NKX = g.nkx, NKZ = g.nkz;
     const size_t per = (size_t)count * Ny * nmodes;
-    const int q_mean = g.kz * NKX;
+    const int q_mean = mean_mode(g);
     for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < per; idx += (size_t)gridDim.x * blockDim.x) {
         int q = (int)(idx % nmodes);
         int y = (int)((idx / nmodes) % Ny);
         int el = (int)(idx / ((size_t)nmodes * Ny));
         int mi = q / NKX, n = q - mi * NKX;
         double2 a = g.stage[idx], b = g.stage[per + idx];
-        if (n == 0) {
+        if (n == 0 && !g.lin) {
             // Hermitian part of the n = 0 column: (x(m) + conj x(-m)) / 2
             int qp = (NKZ - 1 - mi) * NKX;
             size_t ip = ((size_t)el * Ny + y) * nmodes + qp;

@@ -152,3 +152,38 @@ def test_rotational_form_is_refused_where_no_kernel_has_it(dns):
     with pytest.raises(dns.DnsError) as ei:
         dns.dns_create(cfg, 0)
     assert ei.value.code == dns.DNS_ERR_INVALID
+
+
+def _lin_group(**kw):
+    g = dict(flow="couette", mx=0, my=33, mz=32, lx=2 * np.pi, lz=np.pi, re=1000.0, dt=0.04, members=3,
+             linear=True, kx_index=2)
+    g.update(kw)
+    return g
+
+
+def test_linear_groups_validate_and_build_the_single_kx_operators(dns):
+    for bad in (dict(kx_index=0), dict(shared_mean=True), dict(form="rotational")):
+        with pytest.raises(dns.DnsError) as ei:
+            dns.dns_create(dns.make_config([_lin_group(**bad)]), 0)
+        assert ei.value.code == dns.DNS_ERR_INVALID
+    with pytest.raises(dns.DnsError) as ei:
+        dns.dns_create(dns.make_config([_lin_group(mz=40)]), 0)
+    assert ei.value.code == dns.DNS_ERR_UNSUPPORTED
+    g = _lin_group(members=40)                     # one block whatever the size
+    h = dns.dns_create(dns.make_config([g]), 0)
+    try:
+        assert dns.dns_state_shape(h, 0) == (1, 21, 31, 33)
+        from oracle.linear import Linear
+        z = np.zeros((33, 32))
+        lin = Linear(33, 32, g["lx"], g["lz"], g["re"], g["dt"], 2, z, z, z)
+        for hi, hv in enumerate((0.5, 1.0)):
+            for am in range(lin.Kz + 1):
+                got = dns.dns_export_operators(h, 0, hi, am, 31)
+                for a, b in zip(got, lin.ops[hv]):
+                    assert np.array_equal(a, b[lin.Kz + am])
+        for fn in (lambda: dns.dns_set_direction(h, 0, 1), lambda: dns.dns_orthonormalize(h, 0)):
+            with pytest.raises(dns.DnsError) as ei:
+                fn()
+            assert "not bound" in str(ei.value)
+    finally:
+        dns.dns_destroy(h)
