@@ -67,6 +67,13 @@ WORKLOADS = {
                      members=16)],
         name="Poiseuille constant-flux Re=3250 (Re_tau~180), 4pi x 2 x 4pi/3, 128x97x128, 16 members, dt=0.002",
         noise=[dict(seed0=5000, amp=1e-1, spectrum="kolmogorov")]),
+    "optimal": dict(
+        groups=[dict(flow="couette", mx=0, my=63, mz=64, lx=2 * np.pi, lz=np.pi, re=3000.0, dt=0.04, members=45,
+                     linear=True, kx_index=n) for n in (1, 2, 3)],
+        name="optimal disturbances: forward/adjoint linearised ensembles about a streak+roll Couette mean flow, "
+             "Re=3000, 2pi x 2 x pi, My=63, Mz=64, kx = 1, 2, 3 x 45 vectors, dt = 5 x 0.008, T_opt = 15",
+        noise=[dict(seed0=7000 + 100 * n) for n in (1, 2, 3)],
+        base=dict(seed=77, streak=0.3, roll=0.03), t_opt=15.0),
 }
 WORKLOAD = WORKLOADS["poiseuille64"]["groups"][0]
 WORKLOAD_NAME = WORKLOADS["poiseuille64"]["name"]
@@ -80,6 +87,9 @@ N_SM = 152
 def initial_state(g, rank=0, noise=None):
     import dns_synth
     nz = dict(NOISE if noise is None else noise)
+    if g.get("linear"):
+        # disturbance vectors of one kx (no mean profiles)
+        return dns_synth.make_disturbances(g["my"], g["mz"], g["lz"], g["members"], nz["seed0"] + 1000 * rank)
     amp = nz.get("amp", 5e-2)
     if isinstance(amp, tuple):     # amplitude ramp across members
         amp = np.linspace(amp[0], amp[1], g["members"])
@@ -185,10 +195,16 @@ def kernel_work(cls, g, precision):
     """Algorithmic work of ONE launch of kernel class `cls` for group g:
     (bound, amount, unit).  Counts per unit are in the design notes."""
     ny, E = g["my"] - 2, g["members"]
-    nkx, nkz = (g["mx"] - 1) // 3 + 1, 2 * ((g["mz"] - 1) // 3) + 1
+    nkx = 1 if g.get("linear") else (g["mx"] - 1) // 3 + 1
+    nkz = 2 * ((g["mz"] - 1) // 3) + 1
     nmodes = nkx * nkz
     S = nmodes * ny * E                      # complex values of one spectral field
     MM = g["mx"] * g["mz"]
+    if cls == "plane" and g.get("linear"):
+        # 9 inverse + 3 forward complex transforms of length Mz (5 N log2 N each),
+        # the base-flow products (about 60 flops per z point)
+        Mz = g["mz"]
+        return "alu", E * ny * (12 * 5 * Mz * np.log2(Mz) + 60 * Mz), "flop"
     if cls == "plane":
         if g.get("form", "advective") == "rotational":
             # 6 inverse + 3 forward transforms, 6 products, the means
@@ -265,12 +281,38 @@ print(json.dumps(dict(seconds=dt, steps={steps}, members=E)))
 """
 
 
-def run_oracle(g, members, steps, warm=0):
+CPU_SNIPPET_LIN = r"""
+import json, sys, time
+sys.path.insert(0, {root!r})
+import dns_synth
+from oracle.linear import Linear
+g = {g!r}
+E = {members}
+b = dns_synth.make_base_flow(g['my'], g['mz'], g['lz'], g['flow'], {bseed}, streak={streak}, roll={roll})
+lin = Linear(g['my'], g['mz'], g['lx'], g['lz'], g['re'], g['dt'], g['kx_index'], b['U'], b['V'], b['W'])
+d = dns_synth.make_disturbances(g['my'], g['mz'], g['lz'], E, {seed0})
+x = (d['v'], d['eta'])
+for _ in range({warm}):
+    x = lin.step(x, 1)
+t = time.perf_counter()
+for _ in range({steps}):
+    x = lin.step(x, 1)
+dt = time.perf_counter() - t
+print(json.dumps(dict(seconds=dt, steps={steps}, members=E)))
+"""
+
+
+def run_oracle(g, members, steps, warm=0, wl=None):
     env = dict(os.environ)
     for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS_STEP", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
         env[k] = "1"
-    code = CPU_SNIPPET.format(root=ROOT, g=g, members=members, seed0=NOISE["seed0"], amp=NOISE["amp"],
-                              n_max=NOISE["n_max"], m_max=NOISE["m_max"], steps=steps, warm=warm)
+    if g.get("linear"):
+        bw = wl["base"]
+        code = CPU_SNIPPET_LIN.format(root=ROOT, g=g, members=members, bseed=bw["seed"], streak=bw["streak"],
+                                      roll=bw["roll"], seed0=wl["noise"][0]["seed0"], steps=steps, warm=warm)
+    else:
+        code = CPU_SNIPPET.format(root=ROOT, g=g, members=members, seed0=NOISE["seed0"], amp=NOISE["amp"],
+                                  n_max=NOISE["n_max"], m_max=NOISE["m_max"], steps=steps, warm=warm)
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
     if r.returncode != 0:
         raise RuntimeError("oracle run failed: " + r.stderr[-2000:])
@@ -322,12 +364,23 @@ def gpu_arm(args, rank, world, dist):
     groups = [dict(g) for g in wl["groups"]]
     states = [initial_state(g, rank, nz) for g, nz in zip(groups, wl["noise"])]
     members = sum(g["members"] for g in groups)
-    pts = sum(g["members"] * g["mx"] * g["my"] * g["mz"] for g in groups)   # member grid points
+    # member grid points (a linear group's disturbance lives on the (y, z) plane of one harmonic)
+    pts = sum(g["members"] * max(g["mx"], 1) * g["my"] * g["mz"] for g in groups)
     precision = args.precision
+    linear = any(g.get("linear") for g in groups)
+    if linear:
+        import dns_synth
+        bw = wl["base"]
+        bases = [dns_synth.make_base_flow(g["my"], g["mz"], g["lz"], g["flow"], bw["seed"], streak=bw["streak"],
+                                          roll=bw["roll"]) for g in groups]
 
     def load(ens):
         for gi, st in enumerate(states):
-            ens.set_state(gi, st["v"], st["eta"], st["U"], st["W"])
+            if groups[gi].get("linear"):
+                ens.set_base_flow(gi, bases[gi]["U"], bases[gi]["V"], bases[gi]["W"])
+                ens.set_state(gi, st["v"][..., None], st["eta"][..., None])
+            else:
+                ens.set_state(gi, st["v"], st["eta"], st["U"], st["W"])
 
     def timed_run(prec, nsteps, nwarm, flush):
         ens = dns.Ensemble(groups, precision=prec, use_graph=True, device=dev, ygemm=args.ygemm, plane=args.plane,
@@ -368,12 +421,14 @@ def gpu_arm(args, rank, world, dist):
 
     # per-kernel device times (events around every launch), for the roofline
     load(ens)
-    kt = ens.step_timed(max(1, min(args.steps, 5)))
+    n_timed = max(1, min(args.steps, 5))
+    kt = ens.step_timed(n_timed)
     tot = sum(v[0] for v in kt.values())
     shares = {k: (v[0] / tot if tot > 0 else 0.0) for k, v in kt.items()}
     dom = max(kt, key=lambda k: kt[k][0])
-    per_group_launches = kt[dom][1] / len(groups)
-    work = sum(kernel_work(dom, g, precision)[1] for g in groups) * per_group_launches
+    # every member of every group passes through the kernel once per sub-step
+    # (member blocks split a group over several launches; the work is per member)
+    work = sum(kernel_work(dom, g, precision)[1] for g in groups) * 3 * n_timed
     bound = kernel_work(dom, groups[0], precision)[0]
     avg_ms = kt[dom][0] / max(1, kt[dom][1])
     kprec = kernel_precision(dom, precision)
@@ -394,12 +449,14 @@ def gpu_arm(args, rank, world, dist):
     # end to end through the C ABI with host buffers: upload state, step, download state
     pins, outs = [], []
     for st in states:
-        pin = [torch.from_numpy(np.ascontiguousarray(st[k]).view(np.float64)).pin_memory()
-               for k in ("v", "eta", "U", "W")]
+        keys = ("v", "eta") if "U" not in st else ("v", "eta", "U", "W")
+        pin = [torch.from_numpy(np.ascontiguousarray(st[k]).view(np.float64)).pin_memory() for k in keys]
+        pin += [None] * (4 - len(pin))
         pins.append(pin)
-        outs.append([torch.empty_like(p).pin_memory() for p in pin])
-    h2d = sum(p.numel() * 8 for pin in pins for p in pin)
-    d2h = sum(o.numel() * 8 for out in outs for o in out)
+        outs.append([torch.empty_like(p).pin_memory() if p is not None else None for p in pin])
+    h2d = sum(p.numel() * 8 for pin in pins for p in pin if p is not None)
+    d2h = sum(o.numel() * 8 for out in outs for o in out if o is not None)
+    ptr = lambda t: t.data_ptr() if t is not None else None
     e2e_steps = max(1, min(args.steps, 10))
     torch.cuda.synchronize()
     if dist is not None:
@@ -407,13 +464,30 @@ def gpu_arm(args, rank, world, dist):
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         for gi, g in enumerate(groups):
-            dns.dns_set_state(ens.h, gi, 0, g["members"], *[p.data_ptr() for p in pins[gi]], 0)
+            dns.dns_set_state(ens.h, gi, 0, g["members"], *[ptr(p) for p in pins[gi]], 0)
         dns.dns_step(ens.h, 1)
         for gi, g in enumerate(groups):
-            dns.dns_get_state(ens.h, gi, 0, g["members"], *[o.data_ptr() for o in outs[gi]], 0)
+            dns.dns_get_state(ens.h, gi, 0, g["members"], *[ptr(o) for o in outs[gi]], 0)
     e2e_s = time.perf_counter() - t0
     e2e_s = reduce_max(e2e_s, dist, dev)
     e2e_value = aggregate(members * e2e_steps, e2e_s, world)
+    optimal = None
+    if "t_opt" in wl:
+        # one whole optimal-growth iteration of every group: T_opt forward, T_opt
+        # adjoint, Gram-Schmidt (device time, L2 not flushed inside it)
+        nopt = int(round(wl["t_opt"] / groups[0]["dt"]))
+        load(ens)
+        ens.optimal_sweep(nopt)                       # warm (graph already captured)
+        load(ens)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(ens.stream)
+        gains = ens.optimal_sweep(nopt)
+        e1.record(ens.stream)
+        torch.cuda.synchronize()
+        optimal = {"iteration_s": e0.elapsed_time(e1) / 1e3, "steps_each_way": nopt,
+                   "vectors": members, "launches": ens.launches(),
+                   "leading_gain_estimates": [float(np.max(gn)) for gn in gains]}
     ens.close()
 
     line = {
@@ -432,6 +506,8 @@ def gpu_arm(args, rank, world, dist):
         "clocks": clocks,
         "roofline": roofline,
     }
+    if optimal is not None:
+        line["optimal_iteration"] = optimal
 
     if precision == "mixed" and not args.no_fp64:
         n64 = max(1, min(args.steps, 5))
@@ -444,7 +520,10 @@ def gpu_arm(args, rank, world, dist):
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         g0 = groups[0]
-        out = run_oracle(g0, min(g0["members"], 4), 2)
+        if g0.get("linear"):
+            out = run_oracle(g0, g0["members"], 10, wl=wl)     # about 7 s of single-core numpy
+        else:
+            out = run_oracle(g0, min(g0["members"], 4), 2, wl=wl)
         model, ncpu = cpu_info()
         line["cpu_baseline"] = {"value": out["members"] * out["steps"] / out["seconds"], "unit": UNIT, "cores": 1,
                                 "kind": "oracle",

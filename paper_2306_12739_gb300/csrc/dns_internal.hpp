@@ -91,6 +91,21 @@ void launch_helm(const GroupView& g, int s, cudaStream_t st);
 void launch_mean_finish(const GroupView& g, int s, cudaStream_t st);
 // CTAs of the mean-flow rows carried by the implicit-apply launches (8 rows each)
 __host__ __device__ inline int mean_row_ctas(const GroupView& g) { return g.lin ? 0 : g.E * ((g.ny + 7) / 8); }
+// Members per CTA of the implicit-apply kernels (k_helm, k_helm_t).  A DNS
+// group has hundreds of wavenumber pairs and keeps all its members in one CTA
+// (operator reuse); a linear group has only Kz + 1 pairs, so its members are
+// split into chunks until one group alone gives about one CTA per SM.
+__host__ __device__ inline int helm_member_chunk(const GroupView& g) {
+    if (!g.lin) return g.E;
+    int want = (152 + 2 * g.npairs - 1) / (2 * g.npairs);
+    if (want < 1) want = 1;
+    if (want > g.E) want = g.E;
+    return (g.E + want - 1) / want;
+}
+__host__ __device__ inline int helm_member_chunks(const GroupView& g) {
+    const int ec = helm_member_chunk(g);
+    return (g.E + ec - 1) / ec;
+}
 // index of the (0, 0) mode, or -1 in a linear group (which has none)
 __host__ __device__ inline int mean_mode(const GroupView& g) { return g.lin ? -1 : g.kz * g.nkx; }
 void launch_lin_plane(const GroupView& g, bool fp64, cudaStream_t st);

@@ -266,14 +266,16 @@ __global__ void __launch_bounds__(THREADS) k_helm_t(GroupView g, int s) {
         return;
     }
     const int b = blockIdx.x - nrow;
-    const int p = b % g.npairs, f = b / g.npairs;
+    const int p = b % g.npairs, f = (b / g.npairs) & 1, ch = b / (2 * g.npairs);
     const int n = p % NKX, am = p / NKX;
     if (!g.lin && n == 0 && am == 0) return;   // the mean mode (DNS groups)
+    // members e0 .. e0 + ec - 1 (all of them unless the group is split into chunks)
+    const int EC = helm_member_chunk(g), e0 = ch * EC, ec = min(EC, E - e0);
     const int hi = (s == 0) ? 0 : 1;
     const bool needM = (s != 2);
     const int nq = am > 0 ? 2 : 1;
     const int q1 = (g.kz + am) * NKX + n, q2 = (g.kz - am) * NKX + n;
-    const int NC = nq * 2 * E;                    // real columns
+    const int NC = nq * 2 * ec;                   // real columns
     const size_t mat = (size_t)Ny * RP;           // floats per transposed operator
     float* MT = (float*)sm;                       // [Ny][RP]  (M - I)^T
     float* PT = MT + mat;                         // [Ny][RP]  P^T
@@ -298,15 +300,15 @@ __global__ void __launch_bounds__(THREADS) k_helm_t(GroupView g, int s) {
     }
     const double2* X = f == 0 ? g.v_t : g.e_t;
     const float* F = (const float*)(f == 0 ? g.Fv : g.Fe);     // single-precision F~ (mixed path)
-    const int per = Ny * 2 * E;
-    const FastDiv dPER((unsigned)per), d2E((unsigned)(2 * E));
+    const int per = Ny * 2 * ec;
+    const FastDiv dPER((unsigned)per), d2E((unsigned)(2 * ec));
     for (int i = threadIdx.x; i < nq * per; i += THREADS) {
         const int which = (int)dPER.div((unsigned)i), r = i - which * per;
-        const int k = (int)d2E.div((unsigned)r), c = r - k * (2 * E);
+        const int k = (int)d2E.div((unsigned)r), c = r - k * (2 * ec);
         const int q = which == 0 ? q1 : q2;
-        const size_t o = (size_t)q * per + r;
-        if (needM) Xs[k * NC + which * 2 * E + c] = d2f(((const double*)X)[o]);
-        Fs[k * NC + which * 2 * E + c] = F[o];
+        const size_t o = ((size_t)q * Ny + k) * 2 * E + 2 * e0 + c;
+        if (needM) Xs[k * NC + which * 2 * ec + c] = d2f(((const double*)X)[o]);
+        Fs[k * NC + which * 2 * ec + c] = F[o];
     }
     __syncthreads();
     if (!mbar_wait0(bar_a)) {
@@ -337,7 +339,7 @@ __global__ void __launch_bounds__(THREADS) k_helm_t(GroupView g, int s) {
                 mb.x += mk.x * xk.y; mb.y += mk.y * xk.y; mb.z += mk.z * xk.y; mb.w += mk.w * xk.y;
             }
         }
-        const int which = (int)d2E.div((unsigned)c0), cl = c0 - which * 2 * E;
+        const int which = (int)d2E.div((unsigned)c0), cl = 2 * e0 + c0 - which * 2 * ec;
         const int q = which == 0 ? q1 : q2;
         const float rp[2][4] = {{pa.x, pa.y, pa.z, pa.w}, {pb.x, pb.y, pb.z, pb.w}};
         const float rm[2][4] = {{ma.x, ma.y, ma.z, ma.w}, {mb.x, mb.y, mb.z, mb.w}};
@@ -396,7 +398,7 @@ __global__ void k_wait_selftest(int* status) {
 void launch_wait_selftest(int* status, cudaStream_t st) { gt::k_wait_selftest<<<1, 32, 0, st>>>(status); }
 
 size_t helm_t_smem_bytes(const GroupView& g) {
-    const int nc = 2 * 2 * g.E;
+    const int nc = 2 * 2 * helm_member_chunk(g);
     size_t b = (2 * (size_t)g.ny * g.rp + 2 * (size_t)g.ny * nc + 2) * sizeof(float) + 16;
     size_t m = mean_smem_bytes(g);
     return b > m ? b : m;
@@ -425,7 +427,8 @@ void launch_forcing_t(const GroupView& g, int s, cudaStream_t st) {
 }
 
 void launch_helm_t(const GroupView& g, int s, cudaStream_t st) {
-    gt::k_helm_t<<<mean_row_ctas(g) + 2 * g.npairs, gt::THREADS, helm_t_smem_bytes(g), st>>>(g, s);
+    gt::k_helm_t<<<mean_row_ctas(g) + 2 * g.npairs * helm_member_chunks(g), gt::THREADS, helm_t_smem_bytes(g), st>>>(
+        g, s);
 }
 
 void set_attributes_gemm_t() {

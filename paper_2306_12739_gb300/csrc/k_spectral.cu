@@ -237,9 +237,11 @@ __global__ void __launch_bounds__(256) k_helm(GroupView g, int s) {
         return;
     }
     const int b = blockIdx.x - nrow;
-    const int p = b % g.npairs, f = b / g.npairs;
+    const int p = b % g.npairs, f = (b / g.npairs) & 1, ch = b / (2 * g.npairs);
     const int n = p % NKX, am = p / NKX;
     if (!g.lin && n == 0 && am == 0) return;   // the mean mode (DNS groups)
+    // members e0 .. e0 + ec - 1 (all of them unless the group is split into chunks)
+    const int EC = helm_member_chunk(g), e0 = ch * EC, ec = min(EC, E - e0);
     const int hi = (s == 0) ? 0 : 1;
     const size_t nn = (size_t)Ny * Ny;
     const double* Mg = g.ops[hi] + ((size_t)p * 4 + (f == 0 ? 0 : 2)) * nn;
@@ -258,12 +260,12 @@ __global__ void __launch_bounds__(256) k_helm(GroupView g, int s) {
     const double2* F = f == 0 ? g.Fv : g.Fe;
     double2* M1 = f == 0 ? g.mx1_v : g.mx1_e;
     double2* O = (s == 2) ? (f == 0 ? g.v_t : g.e_t) : (f == 0 ? g.v_s : g.e_s);
-    const int ncol = 2 * E;
-    const int per = Ny * ncol;
+    const int ncol = 2 * E;                // real columns of a row in global memory
+    const int per = Ny * 2 * ec;
     for (int idx = threadIdx.x; idx < nq * per; idx += blockDim.x) {
         int which = idx / per;
         int r = idx - which * per;
-        int y = r / ncol, c = r - y * ncol;
+        int y = r / (2 * ec), c = 2 * e0 + r - y * (2 * ec);
         int q = which == 0 ? q1 : q2;
         const double* xc = (const double*)(X + (size_t)q * Ny * E);
         const double* fc = (const double*)(F + (size_t)q * Ny * E);
@@ -289,7 +291,7 @@ __global__ void __launch_bounds__(256) k_helm(GroupView g, int s) {
 void launch_helm(const GroupView& g, int s, cudaStream_t st) {
     size_t smem = 2 * (size_t)g.ny * g.ny * sizeof(double);
     if (smem < mean_smem_bytes(g)) smem = mean_smem_bytes(g);
-    k_helm<<<mean_row_ctas(g) + 2 * g.npairs, 256, smem, st>>>(g, s);
+    k_helm<<<mean_row_ctas(g) + 2 * g.npairs * helm_member_chunks(g), 256, smem, st>>>(g, s);
 }
 
 
