@@ -11,6 +11,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <cstdarg>
 #include <string>
 #include <thread>
@@ -670,11 +671,14 @@ int dns_bind_workspace(dns_handle* h, void* dev_ptr, size_t bytes) {
     }
     rc = check(h, cudaStreamSynchronize(st), "bind workspace");
     if (rc) return rc;
+    // decisions of this call by key: the member blocks of a group (and equal
+    // groups) are tuned once and share the choice
+    std::map<std::string, int> decided;
     for (auto& G : h->groups) {
         GroupView& v = G.v;
         if (v.plane != 0) continue;
         const std::string key = tune_plane_key(v);
-        int choice = cache_lookup(h->cfg.autotune_cache, key);
+        int choice = decided.count(key) ? decided[key] : cache_lookup(h->cfg.autotune_cache, key);
         if (!choice) {
             float best[4] = {0.f, 0.f, 0.f, 0.f};
             cudaEvent_t e0, e1;
@@ -704,13 +708,14 @@ int dns_bind_workspace(dns_handle* h, void* dev_ptr, size_t bytes) {
                 if (best[cand] > 0.f && (choice == 0 || best[cand] < best[choice])) choice = cand;
             cache_store(h->cfg.autotune_cache, key, choice, best, 3);
         }
+        decided[key] = choice;
         v.plane = choice;
     }
     for (auto& G : h->groups) {
         GroupView& v = G.v;
         if (v.ygemm != 0) continue;
         const std::string key = tune_key(v);
-        int choice = cache_lookup(h->cfg.autotune_cache, key);
+        int choice = decided.count(key) ? decided[key] : cache_lookup(h->cfg.autotune_cache, key);
         if (!choice) {
             float best[3] = {0.f, 0.f, 0.f};
             cudaEvent_t e0, e1;
@@ -737,13 +742,14 @@ int dns_bind_workspace(dns_handle* h, void* dev_ptr, size_t bytes) {
             choice = best[2] < best[1] ? 2 : 1;
             cache_store(h->cfg.autotune_cache, key, choice, best, 2);
         }
+        decided[key] = choice;
         v.ygemm = choice;
     }
     for (auto& G : h->groups) {
         GroupView& v = G.v;
         if (v.helm != 0) continue;
         const std::string key = tune_helm_key(v);
-        int choice = cache_lookup(h->cfg.autotune_cache, key);
+        int choice = decided.count(key) ? decided[key] : cache_lookup(h->cfg.autotune_cache, key);
         if (!choice) {
             // the implicit apply is timed on sub-step 2 (both accumulators); it
             // writes only the sub-step state, which set_state overwrites later
@@ -772,6 +778,7 @@ int dns_bind_workspace(dns_handle* h, void* dev_ptr, size_t bytes) {
             choice = best[2] < best[1] ? 2 : 1;
             cache_store(h->cfg.autotune_cache, key, choice, best, 2);
         }
+        decided[key] = choice;
         v.helm = choice;
     }
     h->bound = true;

@@ -105,6 +105,56 @@ __device__ C* fft_lines(C* b0, C* b1, int nl, const FftPlan& p, const C* tw) {
     return src;
 }
 
+// Compile-time radix plan of length N, in the order make_plan builds it (a
+// factor 3 first, then 4s, then a final 2): radix of stage s, number of stages.
+__host__ __device__ constexpr int ct_radix(int N, int s) {
+    int n = N, st = 0;
+    if (n % 3 == 0) { if (st == s) return 3; ++st; n /= 3; }
+    while (n % 4 == 0) { if (st == s) return 4; ++st; n /= 4; }
+    if (n % 2 == 0) { if (st == s) return 2; ++st; n /= 2; }
+    return 1;
+}
+__host__ __device__ constexpr int ct_stages(int N) {
+    int s = 0;
+    while (ct_radix(N, s) > 1) ++s;
+    return s;
+}
+
+// fft_lines with the length, the line count and the plan known at compile
+// time: the same stages and the same arithmetic in the same order (bitwise the
+// same results), with the index divisions by constants.
+template <typename C, int SIGN, int N, int NL, int S = 0, int NS = 1>
+__device__ __forceinline__ C* fft_lines_ct(C* src, C* dst, const C* tw) {
+    if constexpr (S == ct_stages(N)) {
+        return src;
+    } else {
+        constexpr int R = ct_radix(N, S), NB = N / R, TSTEP = N / (NS * R);
+        for (int idx = threadIdx.x; idx < NL * NB; idx += blockDim.x) {
+            const int line = idx / NB, j = idx - line * NB;
+            const C* in = src + line * N;
+            C* out = dst + line * N;
+            const int k = j % NS;
+            C v[4];
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[r] = in[j + r * NB];
+            if (NS > 1) {
+#pragma unroll
+                for (int r = 1; r < R; ++r) {
+                    C w = tw[k * r * TSTEP];
+                    if (SIGN > 0) w.y = -w.y;
+                    v[r] = cmul(v[r], w);
+                }
+            }
+            butterfly<C, SIGN>(v, R);
+            const int base = (j / NS) * NS * R + k;
+#pragma unroll
+            for (int r = 0; r < R; ++r) out[base + r * NS] = v[r];
+        }
+        __syncthreads();
+        return fft_lines_ct<C, SIGN, N, NL, S + 1, NS * R>(dst, src, tw);
+    }
+}
+
 // Block-wide sum of a double (blockDim.x multiple of 32, <= 1024); result valid in
 // every thread.  red must hold 32 doubles.
 __device__ __forceinline__ double block_sum(double v, double* red) {

@@ -28,8 +28,17 @@
 
 namespace dnsk {
 
-constexpr int LIN_THREADS = 128;
 constexpr int GS_THREADS = 256;
+
+// threads of the plane stage for transforms of length MZ: one per butterfly of
+// the widest stage over the nine lines (at most 320)
+__host__ __device__ constexpr int lin_threads(int MZ) {
+    int nb = 0;
+    for (int s = 0; s < ct_stages(MZ); ++s) nb = MZ / ct_radix(MZ, s) > nb ? MZ / ct_radix(MZ, s) : nb;
+    int t = 9 * nb;
+    t = t > 320 ? 320 : t;
+    return (t + 31) / 32 * 32;
+}
 
 template <typename T> struct LinTab;
 template <> struct LinTab<double> {
@@ -46,8 +55,8 @@ template <> struct LinTab<float> {
 };
 
 template <typename T>
-size_t lin_plane_smem_bytes(const GroupView& g) {
-    return 2 * 9 * (size_t)g.mz * sizeof(typename C2<T>::type);
+size_t lin_plane_smem_bytes(int mz) {
+    return 2 * 9 * (size_t)mz * sizeof(typename C2<T>::type);
 }
 
 // i * (a x + b y) for complex x, y and real a, b
@@ -67,12 +76,13 @@ __device__ __forceinline__ C axpy3(T a, C x, T b, C y, T c, C z) {
     return r;
 }
 
-template <typename T>
-__global__ void __launch_bounds__(LIN_THREADS) k_lin_plane(GroupView g) {
+template <typename T, int MZ>
+__global__ void __launch_bounds__(lin_threads(MZ)) k_lin_plane(GroupView g) {
     typedef typename C2<T>::type C;
     extern __shared__ __align__(16) unsigned char sm[];
     const int y = blockIdx.x, e = blockIdx.y;
-    const int Ny = g.ny, E = g.E, NM = g.nmodes, Mz = g.mz, Kz = g.kz;
+    constexpr int Mz = MZ;
+    const int Ny = g.ny, E = g.E, NM = g.nmodes, Kz = g.kz;
     C* b0 = (C*)sm;
     C* b1 = b0 + 9 * Mz;
     const bool adjoint = *g.dir != 0;
@@ -104,7 +114,7 @@ __global__ void __launch_bounds__(LIN_THREADS) k_lin_plane(GroupView g) {
         b0[8 * Mz + pos] = cscale(cmuli(w), kz);
     }
     __syncthreads();
-    C* ph = fft_lines<C, +1>(b0, b1, 9, g.pz, LinTab<T>::tw(g));
+    C* ph = fft_lines_ct<C, +1, MZ, 9>(b0, b1, LinTab<T>::tw(g));
     // products at every z (one thread reads the nine values at z and writes the
     // three results there)
     const T* B = LinTab<T>::base(g) + (size_t)y * Mz;
@@ -140,7 +150,7 @@ __global__ void __launch_bounds__(LIN_THREADS) k_lin_plane(GroupView g) {
         for (int i = 0; i < 3; ++i) ph[i * Mz + z] = N[i];
     }
     __syncthreads();
-    C* out = fft_lines<C, -1>(ph, ph == b0 ? b1 : b0, 3, g.pz, LinTab<T>::tw(g));
+    C* out = fft_lines_ct<C, -1, MZ, 3>(ph, ph == b0 ? b1 : b0, LinTab<T>::tw(g));
     // keep |m| <= Kz; the forward transform carries 1/Mz
     const T sc = (T)(1.0 / (double)Mz);
     C* N3 = (C*)g.N3 + ((size_t)y * E + e) * NM;
@@ -150,11 +160,25 @@ __global__ void __launch_bounds__(LIN_THREADS) k_lin_plane(GroupView g) {
     }
 }
 
+template <typename T, int MZ>
+void launch_lin_plane_t(const GroupView& g, cudaStream_t st) {
+    k_lin_plane<T, MZ><<<dim3(g.ny, g.E), lin_threads(MZ), lin_plane_smem_bytes<T>(MZ), st>>>(g);
+}
+
+template <typename T>
+void launch_lin_plane_p(const GroupView& g, cudaStream_t st) {
+    switch (g.mz) {   // the spanwise sizes a group accepts
+        case 16: launch_lin_plane_t<T, 16>(g, st); break;
+        case 32: launch_lin_plane_t<T, 32>(g, st); break;
+        case 48: launch_lin_plane_t<T, 48>(g, st); break;
+        case 64: launch_lin_plane_t<T, 64>(g, st); break;
+        default: launch_lin_plane_t<T, 128>(g, st); break;
+    }
+}
+
 void launch_lin_plane(const GroupView& g, bool fp64, cudaStream_t st) {
-    if (fp64)
-        k_lin_plane<double><<<dim3(g.ny, g.E), LIN_THREADS, lin_plane_smem_bytes<double>(g), st>>>(g);
-    else
-        k_lin_plane<float><<<dim3(g.ny, g.E), LIN_THREADS, lin_plane_smem_bytes<float>(g), st>>>(g);
+    if (fp64) launch_lin_plane_p<double>(g, st);
+    else launch_lin_plane_p<float>(g, st);
 }
 
 // ------------------------------------------------------------ Gram-Schmidt
@@ -259,8 +283,7 @@ int launch_lin_orthonormalize(const GroupView& g, cudaStream_t st) {
 
 void set_attributes_linear() {
     allow_max_dynamic_smem(k_lin_dv);
-    allow_max_dynamic_smem(k_lin_plane<double>);
-    allow_max_dynamic_smem(k_lin_plane<float>);
+    // the plane stage needs at most 2 x 9 x 128 x 16 B = 36 KB, below the default limit
 }
 
 }  // namespace dnsk
