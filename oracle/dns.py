@@ -149,6 +149,11 @@ class Channel:
         forced by d/dy <uv>, <wv> in both)."""
         assert form in ("advective", "rotational")
         self.form = form
+        # optional stochastic forcing (oracle.forcing.StochasticForcing), its
+        # step counter and the current step's terms
+        self.stochastic = None
+        self.fstep = 0
+        self._noise = None
         self.shared_mean = shared_mean
         self.mx, self.my, self.mz = mx, my, mz
         self.lx, self.lz, self.re, self.dt = lx, lz, re, dt
@@ -279,6 +284,11 @@ class Channel:
         G = ikz * Nu - ikx * Nw
         F[:, :, self.Kz, 0] = 0.0
         G[:, :, self.Kz, 0] = 0.0
+        if self._noise is not None:
+            # stochastic forcing of this step, the same in all three sub-steps
+            Fn, Gn = self._noise
+            F[:, :, :, self.stochastic.n] += Fn
+            G[:, :, :, self.stochastic.n] += Gn
         fU = (uv @ self.D1.T)[:, 1:-1]
         fW = (wv @ self.D1.T)[:, 1:-1]
         return (F, G, fU, fW)
@@ -318,7 +328,11 @@ class Channel:
         """Advance (v, eta, U, W) by nsteps full CN/RK3 steps."""
         x = tuple(np.array(a) for a in state)
         for _ in range(nsteps):
+            if self.stochastic is not None:
+                self._noise = self.stochastic.terms(self.fstep, x[0].shape[0])
+                self.fstep += 1
             x = cn_rk3(x, self.forcing, self.update)
+        self._noise = None
         return x
 
     # --------------------------------------------------------- statistics
