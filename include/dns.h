@@ -345,6 +345,34 @@ int dns_orthonormalize(dns_handle* h, int group, double* norms);
  * Errors: DNS_ERR_INVALID (a non-linear group, nsteps < 1), DNS_ERR_CUDA. */
 int dns_optimal_sweep(dns_handle* h, int nsteps, double* gains);
 
+/* ---- Stochastic forcing of a DNS group (the paper's S3T ensemble run:
+ * realisations mixed from eigenvectors of the diffusion operator acting on a
+ * (Delta v, eta) state, scaled to equal diffusion rate, at one streamwise
+ * wavenumber).  Structures: for kx = kx_index 2 pi / lx and every kept kz, the
+ * n_eig least-damped eigenfunctions of d/dt Delta v = Delta Delta v / Re
+ * (v = Dv = 0 at the walls: the even and odd Stokes modes) and n_eig of
+ * d/dt eta = Delta eta / Re (eta = 0: sine modes), sampled at the Chebyshev
+ * nodes and scaled to unit energy (the dns_stats inner product of one complex
+ * kx column), so each injects energy at the same rate.  Every step, every
+ * member receives sum_j xi_j f_j eps / sqrt(dt) with independent complex
+ * unit-variance normals xi_j, held over the step's three sub-steps; eps is set
+ * so that the mean injection rate of e_pert (dns_stats, which counts the +-kx
+ * pair of the real field) is `rate` per member.  Random numbers: SplitMix64 on
+ * counters (Steele, Lea & Flood 2014), 53-bit uniforms, Box-Muller; stream
+ * `seed`, counter from (step, member, kz, block, structure), the step counted
+ * from this call (a member's noise does not depend on member blocks).
+ * rate = 0 switches the forcing off.  Invalidates a captured step graph (the
+ * next dns_step captures again).  Synchronises the stream.
+ * Errors: DNS_ERR_INVALID (linear group, kx_index outside 1..Kx, n_eig outside
+ * 1..min(16, (My - 2) / 2), rate < 0 or not finite, unbound workspace). */
+int dns_set_stochastic_forcing(dns_handle* h, int group, int kx_index, int n_eig, double rate,
+                               unsigned long long seed);
+
+/* Host copy of the forcing structures of kz index m_index (0 .. 2 Kz):
+ * structures [2][n_eig][My - 2] (v block, then eta block), decay [2][n_eig]
+ * their eigenvalues (negative, least damped first).  Either may be NULL. */
+int dns_export_forcing(const dns_handle* h, int group, int m_index, double* structures, double* decay);
+
 #ifdef __cplusplus
 }
 #endif

@@ -36,7 +36,7 @@ EXPORTED = ["dns_create", "dns_workspace_size", "dns_bind_workspace", "dns_state
             "dns_last_error", "dns_last_launch_count", "dns_export_grid", "dns_export_operators",
             "dns_step_timed", "dns_stats_noalloc", "dns_selftest_timeout", "dns_kernel_choice",
             "dns_convert_selftest", "dns_set_base_flow", "dns_set_direction", "dns_orthonormalize",
-            "dns_optimal_sweep"]
+            "dns_optimal_sweep", "dns_set_stochastic_forcing", "dns_export_forcing"]
 KERNEL_CLASSES = ["mean_deriv", "yderiv", "plane", "forcing", "helm", "mean"]
 
 
@@ -89,6 +89,9 @@ _lib.dns_set_base_flow.argtypes = [_H, ctypes.c_int, _vp, _vp, _vp, ctypes.c_int
 _lib.dns_set_direction.argtypes = [_H, ctypes.c_int, ctypes.c_int]
 _lib.dns_orthonormalize.argtypes = [_H, ctypes.c_int, _vp]
 _lib.dns_optimal_sweep.argtypes = [_H, ctypes.c_int, _vp]
+_lib.dns_set_stochastic_forcing.argtypes = [_H, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                            ctypes.c_ulonglong]
+_lib.dns_export_forcing.argtypes = [_H, ctypes.c_int, ctypes.c_int, _vp, _vp]
 
 
 class DnsError(RuntimeError):
@@ -219,6 +222,17 @@ def dns_optimal_sweep(h, nsteps, gains_ptr=None):
     return _ck(h, _lib.dns_optimal_sweep(h, nsteps, _vp(gains_ptr) if gains_ptr else None))
 
 
+def dns_set_stochastic_forcing(h, group, kx_index, n_eig, rate, seed):
+    return _ck(h, _lib.dns_set_stochastic_forcing(h, group, kx_index, n_eig, float(rate), int(seed)))
+
+
+def dns_export_forcing(h, group, m_index, n_eig, ny):
+    f = np.zeros((2, n_eig, ny))
+    lam = np.zeros((2, n_eig))
+    _ck(h, _lib.dns_export_forcing(h, group, m_index, f.ctypes.data, lam.ctypes.data))
+    return f, lam
+
+
 def dns_destroy(h):
     return _lib.dns_destroy(h)
 
@@ -346,6 +360,9 @@ class Ensemble:
 
     def step(self, nsteps=1):
         dns_step(self.h, nsteps)
+
+    def set_stochastic_forcing(self, group, kx_index, n_eig, rate, seed):
+        dns_set_stochastic_forcing(self.h, group, kx_index, n_eig, rate, seed)
 
     # ---- linearised disturbance groups
     def set_base_flow(self, group, U, V, W):

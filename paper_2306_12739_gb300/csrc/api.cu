@@ -11,6 +11,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <cstdarg>
 #include <string>
@@ -29,6 +30,7 @@ struct HostGroup {
     std::vector<double> kxt, kzt, k2t, k2inv, twx, twz, opsdev[2], mopsdev[2], D1i, D2i;
     std::vector<float> kxtf, kztf, k2invf, twxf, twzf, opsf[2], opsfT[2], D1T, D2T;
     std::vector<uint16_t> Atc, Htc[2];
+    std::vector<double> fstruct, flam;   // stochastic forcing: structures [NKZ][2][n][Ny], decay rates
 
     // byte offsets inside the workspace
     struct Off { size_t off, bytes; };
@@ -135,6 +137,11 @@ size_t layout_group(dns_handle* h, HostGroup& G, size_t cur) {
     add((void**)&v.AU, sizeof(double) * (size_t)v.E * v.my);
     add((void**)&v.AW, sizeof(double) * (size_t)v.E * v.my);
     add((void**)&v.gamma, sizeof(double) * v.E);
+    if (!v.lin) {   // stochastic forcing (structures, one step's terms, the step counter)
+        add((void**)&v.fbasis, sizeof(double) * (size_t)v.nkz * 2 * dnsk::STOCH_NEIG_MAX * v.ny);
+        add((void**)&v.noise, sizeof(double2) * 2 * (size_t)v.nkz * v.ny * v.E);
+        add((void**)&v.fstep, 256);
+    }
     if (v.lin) {
         add((void**)&v.dir, 256);
         add((void**)&v.gsr, sizeof(double) * v.E);
@@ -206,6 +213,7 @@ void enqueue_group(dns_handle* h, HostGroup& G, cudaStream_t st, Timer* tm) {
             else dnsk::launch_plane_f32(g, cU, cW, st);
             mark(DNS_K_PLANE);
             if (g.shared_mean && g.E > 1) { dnsk::launch_shared_mean(g, false, st); h->launches += 1; }
+            if (s == 0 && g.fn > 0) { dnsk::launch_stoch_noise(g, st); h->launches += 1; }
             dnsk::launch_forcing_t(g, s, st);
         } else {
             dnsk::launch_yderiv<double>(g, cv, ce, g.P5, st);
@@ -215,6 +223,7 @@ void enqueue_group(dns_handle* h, HostGroup& G, cudaStream_t st, Timer* tm) {
             else dnsk::launch_plane_state<double>(g, cU, cW, st);
             mark(DNS_K_PLANE);
             if (g.shared_mean && g.E > 1) { dnsk::launch_shared_mean(g, true, st); h->launches += 1; }
+            if (s == 0 && g.fn > 0) { dnsk::launch_stoch_noise(g, st); h->launches += 1; }
             dnsk::launch_forcing<double>(g, s, st);
         }
         mark(DNS_K_FORCING);
@@ -1190,6 +1199,152 @@ int dns_optimal_sweep(dns_handle* h, int nsteps, double* gains) {
     }
     if ((rc = check(h, cudaStreamSynchronize(h->stream), "optimal sweep"))) return rc;
     return device_status(h);
+}
+
+// ---- stochastic forcing
+
+// Root of f on (lo, hi), where f changes sign, by bisection to the last bit.
+static double bisect(const std::function<double(double)>& f, double lo, double hi) {
+    double flo = f(lo);
+    for (int it = 0; it < 400; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        const double fm = f(mid);
+        if (fm == 0.0) return mid;
+        if ((fm < 0.0) == (flo < 0.0)) { lo = mid; flo = fm; } else { hi = mid; }
+    }
+    return 0.5 * (lo + hi);
+}
+
+// Forcing structures of a group at kx index n, per kz: the J least-damped
+// eigenfunctions of each block of the diffusion operator on (Delta v, eta),
+// sampled at the interior nodes and scaled to unit energy (the statistics'
+// inner product of one complex kx column), k^2 = kx^2 + kz^2:
+//   v (d/dt Delta v = Delta Delta v / Re, v = Dv = 0): Stokes modes by increasing mu,
+//     even cos(mu y)/cos(mu) - cosh(k y)/cosh(k), mu tan(mu) = -k tanh(k), mu in ((m - 1/2) pi, m pi),
+//     odd  sin(mu y)/sin(mu) - sinh(k y)/sinh(k), mu cot(mu) = k coth(k),  mu in (m pi, (m + 1/2) pi),
+//     decay rate (mu^2 + k^2) / Re;
+//   eta (d/dt eta = Delta eta / Re, eta = 0): sin(j pi (y + 1) / 2), rate ((j pi / 2)^2 + k^2) / Re.
+// f: [NKZ][2][J][Ny] structures, rhs: their right-hand-side terms (-Delta f_v
+// for F, -f_eta for G), lam: [NKZ][2][J] eigenvalues.
+static void forcing_structures(const HostGroup& G, int n, int J, std::vector<double>& f, std::vector<double>& rhs,
+                               std::vector<double>& lam) {
+    const GroupView& v = G.v;
+    const int Ny = v.ny, NKZ = v.nkz;
+    const double pi = 3.141592653589793;
+    f.assign((size_t)NKZ * 2 * J * Ny, 0.0);
+    rhs.assign(f.size(), 0.0);
+    lam.assign((size_t)NKZ * 2 * J, 0.0);
+    const double* w = G.grid.ccw.data() + 1;
+    const double* yy = G.grid.y.data() + 1;
+    std::vector<double> phi(Ny), dphi(Ny);
+    const double kx = G.kxt[n];
+    auto finish = [&](int mi, int b, int j, double k2, double l, bool vblock) {
+        double e = 0.0;
+        if (vblock) {
+            for (int r = 0; r < Ny; ++r) {
+                double d = 0.0;
+                for (int c = 0; c < Ny; ++c) d += G.D1i[(size_t)r * Ny + c] * phi[c];
+                dphi[r] = d;
+            }
+            double e0 = 0.0, e1 = 0.0;
+            for (int r = 0; r < Ny; ++r) { e0 += w[r] * phi[r] * phi[r]; e1 += w[r] * dphi[r] * dphi[r]; }
+            e = 0.25 * (e0 + e1 / k2);
+        } else {
+            for (int r = 0; r < Ny; ++r) e += w[r] * phi[r] * phi[r];
+            e = 0.25 * e / k2;
+        }
+        const double sc = std::sqrt(e);
+        const size_t o = (((size_t)mi * 2 + b) * J + j) * Ny;
+        for (int r = 0; r < Ny; ++r) f[o + r] = phi[r] / sc;
+        for (int r = 0; r < Ny; ++r) {
+            if (vblock) {
+                double d = 0.0;
+                for (int c = 0; c < Ny; ++c) d += G.D2i[(size_t)r * Ny + c] * f[o + c];
+                rhs[o + r] = -(d - k2 * f[o + r]);
+            } else {
+                rhs[o + r] = -f[o + r];
+            }
+        }
+        lam[((size_t)mi * 2 + b) * J + j] = l;
+    };
+    for (int mi = 0; mi < NKZ; ++mi) {
+        const double kz = G.kzt[mi], k2 = kx * kx + kz * kz, k = std::sqrt(k2);
+        const double th = std::tanh(k), cth = k / std::tanh(k);
+        int j = 0;
+        for (int m = 1; j < J; ++m)
+            for (int odd = 0; odd < 2 && j < J; ++odd, ++j) {
+                double mu;
+                if (odd) {
+                    mu = bisect([&](double x) { return x * std::cos(x) - cth * std::sin(x); }, m * pi + 1e-12,
+                                (m + 0.5) * pi - 1e-12);
+                    for (int r = 0; r < Ny; ++r) phi[r] = std::sin(mu * yy[r]) / std::sin(mu) - std::sinh(k * yy[r]) / std::sinh(k);
+                } else {
+                    mu = bisect([&](double x) { return x * std::sin(x) + k * th * std::cos(x); }, (m - 0.5) * pi + 1e-12,
+                                m * pi - 1e-12);
+                    for (int r = 0; r < Ny; ++r) phi[r] = std::cos(mu * yy[r]) / std::cos(mu) - std::cosh(k * yy[r]) / std::cosh(k);
+                }
+                finish(mi, 0, j, k2, -(mu * mu + k2) / v.re, true);
+            }
+        for (j = 0; j < J; ++j) {
+            const double a = 0.5 * (j + 1) * pi;
+            for (int r = 0; r < Ny; ++r) phi[r] = std::sin(a * (yy[r] + 1.0));
+            finish(mi, 1, j, k2, -(a * a + k2) / v.re, false);
+        }
+    }
+}
+
+int dns_set_stochastic_forcing(dns_handle* h, int group, int kx_index, int n_eig, double rate, unsigned long long seed) {
+    if (!h) return DNS_ERR_INVALID;
+    if (!h->bound) return fail(h, DNS_ERR_INVALID, "workspace not bound");
+    if (group < 0 || group >= (int)h->parts.size()) return fail(h, DNS_ERR_INVALID, "bad group");
+    const HostGroup& G0 = h->groups[h->parts[group][0].ig];
+    if (G0.v.lin) return fail(h, DNS_ERR_INVALID, "group %d is linear: no stochastic forcing", group);
+    if (!(rate >= 0.0) || !std::isfinite(rate)) return fail(h, DNS_ERR_INVALID, "rate must be finite and >= 0");
+    const bool on = rate > 0.0;
+    if (on && (kx_index < 1 || kx_index > G0.v.kx))
+        return fail(h, DNS_ERR_INVALID, "kx_index must be in 1..Kx = %d", G0.v.kx);
+    if (on && (n_eig < 1 || n_eig > dnsk::STOCH_NEIG_MAX || n_eig > G0.v.ny / 2))
+        return fail(h, DNS_ERR_INVALID, "n_eig must be in 1..%d", std::min(dnsk::STOCH_NEIG_MAX, G0.v.ny / 2));
+    std::vector<double> f, rhs, lam;
+    if (on) forcing_structures(G0, kx_index, n_eig, f, rhs, lam);
+    const double eps = on ? std::sqrt(rate / (2.0 * G0.v.nkz * 2 * n_eig)) : 0.0;
+    int rc;
+    for (const auto& P : h->parts[group]) {
+        HostGroup& G = h->groups[P.ig];
+        GroupView& v = G.v;
+        v.fn = on ? kx_index : 0;
+        v.fneig = on ? n_eig : 0;
+        v.fscale = eps / std::sqrt(v.dt);
+        v.fseed = seed;
+        v.m0 = P.m0;
+        v.Eu = h->descs[group].members;
+        G.fstruct = f;
+        G.flam = lam;
+        if (!on) continue;
+        if ((rc = check(h, cudaMemcpyAsync((void*)v.fbasis, rhs.data(), rhs.size() * 8, cudaMemcpyHostToDevice, h->stream),
+                        "upload forcing structures")))
+            return rc;
+        if ((rc = check(h, cudaMemsetAsync(v.fstep, 0, sizeof(unsigned long long), h->stream), "reset noise step")))
+            return rc;
+    }
+    // a captured step graph holds the previous group views
+    if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
+    if (h->graph) { cudaGraphDestroy(h->graph); h->graph = nullptr; }
+    return check(h, cudaStreamSynchronize(h->stream), "set stochastic forcing");
+}
+
+int dns_export_forcing(const dns_handle* hc, int group, int m_index, double* structures, double* decay) {
+    dns_handle* h = const_cast<dns_handle*>(hc);
+    if (!h) return DNS_ERR_INVALID;
+    if (group < 0 || group >= (int)h->parts.size()) return fail(h, DNS_ERR_INVALID, "bad group");
+    const HostGroup& G = h->groups[h->parts[group][0].ig];
+    if (G.v.fn <= 0) return fail(h, DNS_ERR_INVALID, "group %d has no stochastic forcing", group);
+    if (m_index < 0 || m_index >= G.v.nkz) return fail(h, DNS_ERR_INVALID, "m_index out of range");
+    const int J = G.v.fneig, Ny = G.v.ny;
+    if (structures) memcpy(structures, &G.fstruct[(size_t)m_index * 2 * J * Ny], sizeof(double) * 2 * J * Ny);
+    if (decay) memcpy(decay, &G.flam[(size_t)m_index * 2 * J], sizeof(double) * 2 * J);
+    return DNS_OK;
 }
 
 int dns_selftest_timeout(dns_handle* h) {

@@ -36,6 +36,15 @@ struct GroupView {
                           //    base flow on the interior planes
     const float* basef;   // single-precision copy (mixed path)
     double* gsr;          // linear groups: [E] energy norms recorded by the last Gram-Schmidt
+    // stochastic forcing (DNS groups; fn = 0: off)
+    int fn;               // forced streamwise index
+    int fneig;            // structures per block (v, eta) and kz
+    int m0, Eu;           // first member of this block in its group, members of the group
+    double fscale;        // eps / sqrt(dt)
+    unsigned long long fseed;
+    const double* fbasis; // [NKZ][2][fneig][Ny] right-hand-side terms -Delta f_v, -f_eta
+    double2* noise;       // [2][NKZ][Ny][E] this step's F and G terms of the forced column
+    unsigned long long* fstep;   // device step counter of the noise
     double re, dt, u_wall, bulk_flux;
     FftPlan px, pz;
     // constants
@@ -111,6 +120,8 @@ __host__ __device__ inline int mean_mode(const GroupView& g) { return g.lin ? -1
 void launch_lin_plane(const GroupView& g, bool fp64, cudaStream_t st);
 int launch_lin_orthonormalize(const GroupView& g, cudaStream_t st);   // returns the launch count
 void set_attributes_linear();
+constexpr int STOCH_NEIG_MAX = 16;   // forcing structures per block and kz
+void launch_stoch_noise(const GroupView& g, cudaStream_t st);
 inline size_t mean_smem_bytes(const GroupView& g) { return (8 * (size_t)g.my + 32) * sizeof(double); }
 size_t helm_t_smem_bytes(const GroupView& g);
 size_t yderiv_t_smem_bytes(const GroupView& g);

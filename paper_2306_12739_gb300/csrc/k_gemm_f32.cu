@@ -189,6 +189,9 @@ __global__ void __launch_bounds__(THREADS) k_forcing_t(GroupView g, int s) {
         const int q = q0 + qq, e = e0 + el;
         if (q >= NM || e >= E) continue;
         const float rx[4] = {ax.x, ax.y, ax.z, ax.w}, ry[4] = {ay.x, ay.y, ay.z, ay.w};
+        // stochastic forcing of the step in this mode's column
+        const int fmi = g.fn > 0 ? q / g.nkx : 0;
+        const bool forced = g.fn > 0 && q - fmi * g.nkx == g.fn;
         // RK accumulators of the four rows loaded before any store
         float2* Av = (float2*)g.Av;
         float2* Ae = (float2*)g.Ae;
@@ -215,6 +218,11 @@ __global__ void __launch_bounds__(THREADS) k_forcing_t(GroupView g, int s) {
             float2 F = make_float2(kv.x - rx[i], kv.y - ry[i]);
             float2 G = gg;
             if (q == q_mean) { F = make_float2(0.f, 0.f); G = F; }
+            if (forced) {
+                const size_t o = ((size_t)fmi * Ny + y) * E + e, half = (size_t)g.nkz * Ny * E;
+                F.x += (float)g.noise[o].x; F.y += (float)g.noise[o].y;
+                G.x += (float)g.noise[half + o].x; G.y += (float)g.noise[half + o].y;
+            }
             const size_t h = ((size_t)q * Ny + y) * E + e;
             float2 Ft, Gt;
             if (s == 0) {

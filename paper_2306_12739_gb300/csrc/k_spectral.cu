@@ -178,6 +178,11 @@ __global__ void __launch_bounds__(256) k_forcing(GroupView g, int s) {
         double by = kz * (double)nu.y - kx * (double)nw.y;
         G = make_double2(-by, bx);
         if (q == q_mean) { F = make_double2(0.0, 0.0); G = F; }
+        if (g.fn > 0 && n == g.fn) {   // stochastic forcing of the step
+            const size_t o = ((size_t)mi * Ny + y) * E + e, half = (size_t)g.nkz * Ny * E;
+            F.x += g.noise[o].x; F.y += g.noise[o].y;
+            G.x += g.noise[half + o].x; G.y += g.noise[half + o].y;
+        }
         size_t h = ((size_t)q * Ny + y) * E + e;
         double2 Ft, Gt;
         if (s == 0) {
@@ -219,6 +224,8 @@ template void launch_forcing<double>(const GroupView&, int, cudaStream_t);
 __global__ void __launch_bounds__(128) k_mean_finish(GroupView g, int s) {
     __shared__ double red[32];
     mean_finish(g, s, blockIdx.x, (unsigned char*)red);
+    // the step's noise has been used by all three forcing assemblies: next step's
+    if (s == 2 && g.fn > 0 && blockIdx.x == 0 && threadIdx.x == 0) *g.fstep += 1ULL;
 }
 
 void launch_mean_finish(const GroupView& g, int s, cudaStream_t st) {

@@ -187,3 +187,19 @@ def test_linear_groups_validate_and_build_the_single_kx_operators(dns):
             assert "not bound" in str(ei.value)
     finally:
         dns.dns_destroy(h)
+
+
+def test_forcing_calls_before_binding_fail_cleanly(dns):
+    """Calls before binding fail cleanly; the structures themselves are
+    compared with the oracle's in the GPU tests (the call needs a bound
+    workspace, which needs device memory)."""
+    g = _g(my=33)
+    h = dns.dns_create(dns.make_config([g]), 0)
+    try:
+        with pytest.raises(dns.DnsError) as ei:
+            dns.dns_set_stochastic_forcing(h, 0, 1, 4, 1e-3, 7)
+        assert "not bound" in str(ei.value)
+        with pytest.raises(dns.DnsError):
+            dns.dns_export_forcing(h, 0, 0, 4, 31)
+    finally:
+        dns.dns_destroy(h)
