@@ -60,8 +60,10 @@ WORKLOADS = {
     "s3t": dict(
         groups=[dict(flow="couette", mx=64, my=63, mz=64, lx=2 * np.pi, lz=1.2 * np.pi, re=1000.0, dt=0.01,
                      members=5, shared_mean=True)],
-        name="shared-mean (S3T-type) Couette ensemble Re=1000, 2pi x 2 x 1.2pi, 64x63x64, 5 members, dt=0.01",
-        noise=[dict(seed0=6000, amp=2.5e-2, n_max=4, m_max=4)]),
+        name="shared-mean (S3T-type) Couette ensemble Re=1000, 2pi x 2 x 1.2pi, 64x63x64, 5 members, dt=0.01, "
+             "stochastic forcing at kx/a = 1 (4 + 4 diffusion eigenfunctions per kz, e_pert injection 1e-5)",
+        noise=[dict(seed0=6000, amp=2.5e-2, n_max=4, m_max=4)],
+        forcing=[(1, 4, 1e-5, 6060)]),
     "channel128": dict(
         groups=[dict(flow="poiseuille", mx=128, my=97, mz=128, lx=4 * np.pi, lz=4 * np.pi / 3, re=3250.0, dt=0.002,
                      members=16)],
@@ -268,6 +270,9 @@ g = {g!r}
 E = {members}
 ch = oracle.Channel(g['mx'], g['my'], g['mz'], g['lx'], g['lz'], g['re'], g['dt'], g['flow'],
                     shared_mean=g.get('shared_mean', False), form=g.get('form', 'advective'))
+if {forcing!r} is not None:
+    from oracle.forcing import StochasticForcing
+    ch.stochastic = StochasticForcing(ch, *{forcing!r})
 st = dns_synth.make_state(g['mx'], g['my'], g['mz'], g['lx'], g['lz'], g['flow'], E, {seed0}, {amp},
                           n_max={n_max}, m_max={m_max})
 x = tuple(st[k] for k in ('v', 'eta', 'U', 'W'))
@@ -311,8 +316,9 @@ def run_oracle(g, members, steps, warm=0, wl=None):
         code = CPU_SNIPPET_LIN.format(root=ROOT, g=g, members=members, bseed=bw["seed"], streak=bw["streak"],
                                       roll=bw["roll"], seed0=wl["noise"][0]["seed0"], steps=steps, warm=warm)
     else:
+        fc = (wl or {}).get("forcing", [None])[0]
         code = CPU_SNIPPET.format(root=ROOT, g=g, members=members, seed0=NOISE["seed0"], amp=NOISE["amp"],
-                                  n_max=NOISE["n_max"], m_max=NOISE["m_max"], steps=steps, warm=warm)
+                                  n_max=NOISE["n_max"], m_max=NOISE["m_max"], steps=steps, warm=warm, forcing=fc)
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
     if r.returncode != 0:
         raise RuntimeError("oracle run failed: " + r.stderr[-2000:])
@@ -375,6 +381,9 @@ def gpu_arm(args, rank, world, dist):
                                           roll=bw["roll"]) for g in groups]
 
     def load(ens):
+        for gi, f in enumerate(wl.get("forcing", [])):
+            if f is not None:
+                ens.set_stochastic_forcing(gi, *f)
         for gi, st in enumerate(states):
             if groups[gi].get("linear"):
                 ens.set_base_flow(gi, bases[gi]["U"], bases[gi]["V"], bases[gi]["W"])
