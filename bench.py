@@ -553,7 +553,7 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparator run")
     ap.add_argument("--plane", choices=["default", "cta", "cluster", "lines"], default="default",
                     help="plane-stage kernel (default: autotuned among those the grid supports)")
-    ap.add_argument("--helm", choices=["default", "simt", "tc"], default="default",
+    ap.add_argument("--helm", choices=["default", "simt", "tc", "persist"], default="default",
                     help="implicit-apply variant of the mixed path (default: autotuned)")
     ap.add_argument("--ygemm", choices=["default", "simt", "tc"], default="default",
                     help="y-contraction variant of the mixed path")

@@ -141,9 +141,11 @@ typedef struct {
                                       threads (mixed precision, sizes <= 64); a request for a
                                       variant the group's size lacks is ignored */
     int helm;                      /* mixed path implicit apply: 0 autotuned at
-                                      dns_bind_workspace, 1 register-tiled FP32, 2 tcgen05 tensor
-                                      cores with split-BF16 operands (groups with My <= 66 and
-                                      <= 64 members; others always use 1) */
+                                      dns_bind_workspace, 1 register-tiled FP32 (one CTA per
+                                      wavenumber pair and field), 2 tcgen05 tensor cores with
+                                      split-BF16 operands (groups with My <= 66 and <= 64 members;
+                                      others use 1), 3 register-tiled FP32 in persistent CTAs that
+                                      copy the next pair's operators while computing the current */
 } dns_config;
 
 /* One-point statistics of one member (paper Sec. 4), computed from the current

@@ -195,14 +195,14 @@ def convert_selftest(d_in, f_in):
 
 
 def dns_kernel_choice(h, group, which="ygemm"):
-    """'ygemm' -> 'simt' | 'tc'; 'plane' -> 'cta' | 'cluster' | 'lines';
-    'helm' -> 'simt' | 'tc'."""
+    """'ygemm' -> 'simt' | 'tc'; 'plane' -> 'cta' | 'cluster' | 'lines' | 'linear';
+    'helm' -> 'simt' | 'tc' | 'persist'."""
     c, p, m = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
     _ck(h, _lib.dns_kernel_choice(h, group, ctypes.byref(c), ctypes.byref(p), ctypes.byref(m)))
     if which == "plane":
         return {1: "cta", 2: "cluster", 3: "lines", 4: "linear"}.get(p.value, p.value)
     if which == "helm":
-        return {1: "simt", 2: "tc"}.get(m.value, m.value)
+        return {1: "simt", 2: "tc", 3: "persist"}.get(m.value, m.value)
     return {1: "simt", 2: "tc"}.get(c.value, c.value)
 
 
@@ -271,6 +271,9 @@ _YGEMM = {"default": 0, "auto": 0, "simt": 1, "tc": 2}
 _PLANE = {"default": 0, "auto": 0, "cta": 1, "cluster": 2, "lines": 3}
 
 
+_HELM = {"default": 0, "auto": 0, "simt": 1, "tc": 2, "persist": 3}
+
+
 def make_config(groups, precision="fp64", use_graph=False, ygemm="default", autotune_cache=None, plane="default",
                 helm="default"):
     """groups: list of dicts with flow, mx, my, mz, lx, lz, re, dt, members,
@@ -289,7 +292,7 @@ def make_config(groups, precision="fp64", use_graph=False, ygemm="default", auto
                                 int(g.get("kx_index", 0)))
     cache = autotune_cache.encode() if autotune_cache else None
     cfg = dns_config(len(groups), arr, _PRECS[precision], 1 if use_graph else 0, 0, 0, cache, _YGEMM[ygemm],
-                     _PLANE[plane], _YGEMM[helm])
+                     _PLANE[plane], _HELM[helm])
     cfg._keep = (arr, cache)
     return cfg
 

@@ -92,6 +92,9 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 bool precision_mixed(const dns_handle* h) { return h->cfg.precision == DNS_PREC_MIXED; }
 
+// the tcgen05 implicit apply may run: its operator images are needed
+bool helm_tc_candidate(const GroupView& v) { return v.helm == 2 || (v.helm == 0 && dnsk::helm_tc_supported(v)); }
+
 // Assign workspace offsets for every device array of group g (base = 0).
 size_t layout_group(dns_handle* h, HostGroup& G, size_t cur) {
     GroupView& v = G.v;
@@ -126,7 +129,7 @@ size_t layout_group(dns_handle* h, HostGroup& G, size_t cur) {
         add((void**)&v.ops[hi], sizeof(double) * (size_t)v.npairs * 4 * nn);
         if (precision_mixed(h)) {
             add((void**)&v.opsfT[hi], sizeof(float) * (size_t)v.npairs * 4 * v.ny * v.rp);
-            if (v.helm != 1) add((void**)&v.Htc[hi], (size_t)v.npairs * 2 * 3 * 64 * 2 * v.kp * sizeof(uint16_t));
+            if (helm_tc_candidate(v)) add((void**)&v.Htc[hi], (size_t)v.npairs * 2 * 3 * 64 * 2 * v.kp * sizeof(uint16_t));
         }
         add((void**)&v.mops[hi], sizeof(double) * (2 * nn + 3 * (size_t)v.ny + (size_t)v.ny * v.my));
     }
@@ -230,6 +233,7 @@ void enqueue_group(dns_handle* h, HostGroup& G, cudaStream_t st, Timer* tm) {
         // per-wavenumber implicit apply (and the rows of the mean-flow update)
         if (precision_mixed(h)) {
             if (g.helm == 2) dnsk::launch_helm_tc(g, s, st);
+            else if (g.helm == 3) dnsk::launch_helm_tp(g, s, st);
             else dnsk::launch_helm_t(g, s, st);
         } else {
             dnsk::launch_helm(g, s, st);
@@ -349,11 +353,13 @@ int choose_variants(dns_handle* h, const dns_config* cfg, GroupView& v, int gi) 
         if (cfg->ygemm == 2) v.ygemm = 2;
         else if (cfg->ygemm == 0) v.ygemm = 0;
     }
-    // implicit-apply variant: 1 register-tiled FP32, 2 tcgen05; 0 = autotuned
+    // implicit-apply variant: 1 register-tiled FP32, 2 tcgen05, 3 persistent
+    // register-tiled FP32 with double-buffered operator copies; 0 = autotuned
     v.helm = 1;
-    if (precision_mixed(h) && dnsk::helm_tc_supported(v)) {
-        if (cfg->helm == 2) v.helm = 2;
-        else if (cfg->helm == 0) v.helm = 0;
+    if (precision_mixed(h)) {
+        if (cfg->helm == 0) v.helm = 0;
+        else if (cfg->helm == 2 && dnsk::helm_tc_supported(v)) v.helm = 2;
+        else if (cfg->helm == 3) v.helm = 3;
     }
     // plane-stage kernel: single CTA per plane where it fits, a thread-block
     // cluster (distributed shared memory) where it does not; where both exist
@@ -372,7 +378,8 @@ int choose_variants(dns_handle* h, const dns_config* cfg, GroupView& v, int gi) 
     }
     if (precision_mixed(h)) {
         size_t m1 = dnsk::helm_t_smem_bytes(v), m2 = dnsk::yderiv_t_smem_bytes(v), m3 = dnsk::forcing_t_smem_bytes(v);
-        if (v.helm != 1 && dnsk::helm_tc_smem_bytes(v) > m1) m1 = dnsk::helm_tc_smem_bytes(v);
+        if (helm_tc_candidate(v) && dnsk::helm_tc_smem_bytes(v) > m1) m1 = dnsk::helm_tc_smem_bytes(v);
+        if ((v.helm == 0 || v.helm == 3) && dnsk::helm_tp_smem_bytes(v) > m1) m1 = dnsk::helm_tp_smem_bytes(v);
         size_t mm = m1 > m2 ? m1 : m2;
         mm = mm > m3 ? mm : m3;
         if (mm > 227 * 1024)
@@ -455,7 +462,7 @@ int dns_create(const dns_config* cfg, void* cuda_stream, dns_handle** out) {
             int rcv = choose_variants(h, cfg, G.v, gi);
             if (rcv) return rcv;
             if (G.v.ygemm != 1 && G.Atc.empty()) G.Atc = dnsk::yderiv_tc_a_image(G.D1i, G.D2i, G.v.ny, G.v.kp);
-            if (precision_mixed(h) && G.v.helm != 1 && G.Htc[0].empty())
+            if (precision_mixed(h) && helm_tc_candidate(G.v) && G.Htc[0].empty())
                 for (int hi = 0; hi < 2; ++hi)
                     G.Htc[hi] = dnsk::helm_tc_a_images(G.opsdev[hi], G.v.npairs, G.v.ny, G.v.kp);
             cur = layout_group(h, G, cur);
@@ -581,7 +588,7 @@ int dns_create(const dns_config* cfg, void* cuda_stream, dns_handle** out) {
                 G.D2T[(size_t)k * v.rp + r] = (float)G.D2i[(size_t)r * v.ny + k];
             }
         if (v.ygemm != 1) G.Atc = dnsk::yderiv_tc_a_image(G.D1i, G.D2i, v.ny, v.kp);
-        if (precision_mixed(h) && v.helm != 1)
+        if (precision_mixed(h) && helm_tc_candidate(v))
             for (int hi = 0; hi < 2; ++hi) G.Htc[hi] = dnsk::helm_tc_a_images(G.opsdev[hi], v.npairs, v.ny, v.kp);
         if (!lin) G.twx = dnsb::twiddles(d.mx);
         G.twz = dnsb::twiddles(d.mz);
@@ -762,13 +769,15 @@ int dns_bind_workspace(dns_handle* h, void* dev_ptr, size_t bytes) {
         if (!choice) {
             // the implicit apply is timed on sub-step 2 (both accumulators); it
             // writes only the sub-step state, which set_state overwrites later
-            float best[3] = {0.f, 0.f, 0.f};
+            float best[4] = {0.f, 0.f, 0.f, 0.f};
             cudaEvent_t e0, e1;
             cudaEventCreate(&e0);
             cudaEventCreate(&e1);
-            for (int cand = 1; cand <= 2; ++cand) {
+            for (int cand = 1; cand <= 3; ++cand) {
+                if (cand == 2 && !dnsk::helm_tc_supported(v)) continue;
                 auto run = [&]() {
                     if (cand == 2) dnsk::launch_helm_tc(v, 1, st);
+                    else if (cand == 3) dnsk::launch_helm_tp(v, 1, st);
                     else dnsk::launch_helm_t(v, 1, st);
                 };
                 for (int w = 0; w < 2; ++w) run();
@@ -784,8 +793,10 @@ int dns_bind_workspace(dns_handle* h, void* dev_ptr, size_t bytes) {
             cudaEventDestroy(e1);
             if (rc) return rc;
             if ((rc = device_status(h))) return rc;
-            choice = best[2] < best[1] ? 2 : 1;
-            cache_store(h->cfg.autotune_cache, key, choice, best, 2);
+            choice = 0;
+            for (int cand = 1; cand <= 3; ++cand)
+                if (best[cand] > 0.f && (choice == 0 || best[cand] < best[choice])) choice = cand;
+            cache_store(h->cfg.autotune_cache, key, choice, best, 3);
         }
         decided[key] = choice;
         v.helm = choice;

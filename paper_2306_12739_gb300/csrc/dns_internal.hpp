@@ -23,7 +23,8 @@ struct GroupView {
     int plane;            // plane stage: 1 single-CTA kernel, 2 cluster kernel, 3 line-owned
                           // single-CTA kernel (mixed path); 0 = autotune
     const void* Atc;      // tensor-core A image: [D1_int; D2_int] in 3 BF16 pieces
-    int helm;             // mixed path implicit apply: 1 register-tiled FP32, 2 tcgen05 (0 = autotune)
+    int helm;             // mixed path implicit apply: 1 register-tiled FP32, 2 tcgen05, 3 persistent
+                          // register-tiled FP32 with double-buffered operator copies (0 = autotune)
     const void* Htc[2];   // per h index: [npairs][2 fields] images of [M - I | P] in 3 BF16 pieces
     int* status;          // device error word (1: a bounded wait gave up)
     int flow;             // 0 Couette, 1 Poiseuille
@@ -129,6 +130,8 @@ size_t forcing_t_smem_bytes(const GroupView& g);
 void launch_yderiv_t(const GroupView& g, const double2* v, const double2* e, cudaStream_t st);
 void launch_forcing_t(const GroupView& g, int s, cudaStream_t st);
 void launch_helm_t(const GroupView& g, int s, cudaStream_t st);
+size_t helm_tp_smem_bytes(const GroupView& g);
+void launch_helm_tp(const GroupView& g, int s, cudaStream_t st);
 void set_attributes_gemm_t();
 bool yderiv_tc_supported(const GroupView& g);
 size_t yderiv_tc_smem_bytes(const GroupView& g);

@@ -252,84 +252,68 @@ __device__ __forceinline__ unsigned smem_u32(const void* p) {
 }
 
 // Bounded wait on phase 0 of an mbarrier; false if it did not complete.
-__device__ __forceinline__ bool mbar_wait0(unsigned bar) {
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
     for (int it = 0; it < (1 << 22); ++it) {
         unsigned done;
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(done) : "r"(bar), "r"(0) : "memory");
+            : "=r"(done) : "r"(bar), "r"(parity) : "memory");
         if (done) return true;
     }
     return false;
 }
+__device__ __forceinline__ bool mbar_wait0(unsigned bar) { return mbar_wait(bar, 0); }
 
-__global__ void __launch_bounds__(THREADS) k_helm_t(GroupView g, int s) {
-    extern __shared__ __align__(16) unsigned char sm[];
-    const int Ny = g.ny, RP = g.rp, E = g.E, NKX = g.nkx;
-    // leading CTAs: rows of the mean-flow update (independent work that fills
-    // SMs beside the wavenumber pairs), finished by launch_mean_finish
-    const int nrow = mean_row_ctas(g);
-    if ((int)blockIdx.x < nrow) {
-        mean_rows(g, s, blockIdx.x % E, (blockIdx.x / E) * (THREADS / 32), sm);
-        return;
-    }
-    const int b = blockIdx.x - nrow;
-    const int p = b % g.npairs, f = (b / g.npairs) & 1, ch = b / (2 * g.npairs);
-    const int n = p % NKX, am = p / NKX;
-    if (!g.lin && n == 0 && am == 0) return;   // the mean mode (DNS groups)
-    // members e0 .. e0 + ec - 1 (all of them unless the group is split into chunks)
-    const int EC = helm_member_chunk(g), e0 = ch * EC, ec = min(EC, E - e0);
-    const int hi = (s == 0) ? 0 : 1;
-    const bool needM = (s != 2);
-    const int nq = am > 0 ? 2 : 1;
-    const int q1 = (g.kz + am) * NKX + n, q2 = (g.kz - am) * NKX + n;
-    const int NC = nq * 2 * ec;                   // real columns
-    const size_t mat = (size_t)Ny * RP;           // floats per transposed operator
-    float* MT = (float*)sm;                       // [Ny][RP]  (M - I)^T
-    float* PT = MT + mat;                         // [Ny][RP]  P^T
-    float* Xs = PT + mat;                         // [Ny][NC]
-    float* Fs = Xs + (size_t)Ny * NC;             // [Ny][NC]
-    unsigned long long* bar = (unsigned long long*)(Fs + (size_t)Ny * NC + 2);
-    const float* src = g.opsfT[hi] + ((size_t)p * 4 + 2 * f) * mat;   // M^T then P^T, contiguous
-    const unsigned bar_a = smem_u32(bar);
-    if (threadIdx.x == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_a) : "memory");
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        // TMA bulk copy of the operators of this pair and field
-        const unsigned bytes = (unsigned)((needM ? 2 : 1) * mat * sizeof(float));
-        const float* from = needM ? src : src + mat;
-        float* to = needM ? MT : PT;
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_a), "r"(bytes) : "memory");
-        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                     ::"r"(smem_u32(to)), "l"(from), "r"(bytes), "r"(bar_a) : "memory");
-    }
-    const double2* X = f == 0 ? g.v_t : g.e_t;
-    const float* F = (const float*)(f == 0 ? g.Fv : g.Fe);     // single-precision F~ (mixed path)
+// One work item of the implicit apply: wavenumber pair p, field f (0 v, 1 eta),
+// member chunk ch.
+struct HelmItem {
+    int p, f, e0, ec, nq, q1, q2, NC;
+};
+
+__device__ __forceinline__ HelmItem helm_item(const GroupView& g, int p, int f, int ch) {
+    HelmItem it;
+    const int NKX = g.nkx, n = p % NKX, am = p / NKX;
+    const int EC = helm_member_chunk(g);
+    it.p = p;
+    it.f = f;
+    it.e0 = ch * EC;
+    it.ec = min(EC, g.E - it.e0);
+    it.nq = am > 0 ? 2 : 1;
+    it.q1 = (g.kz + am) * NKX + n;
+    it.q2 = (g.kz - am) * NKX + n;
+    it.NC = it.nq * 2 * it.ec;
+    return it;
+}
+
+// x_t (single precision, needM only) and F~ of the item's modes and members
+// into shared memory, [Ny][NC]
+__device__ __forceinline__ void helm_stage(const GroupView& g, const HelmItem& it, bool needM, float* Xs, float* Fs) {
+    const int Ny = g.ny, E = g.E, ec = it.ec, NC = it.NC;
+    const double2* X = it.f == 0 ? g.v_t : g.e_t;
+    const float* F = (const float*)(it.f == 0 ? g.Fv : g.Fe);   // single-precision F~ (mixed path)
     const int per = Ny * 2 * ec;
     const FastDiv dPER((unsigned)per), d2E((unsigned)(2 * ec));
-    for (int i = threadIdx.x; i < nq * per; i += THREADS) {
+    for (int i = threadIdx.x; i < it.nq * per; i += THREADS) {
         const int which = (int)dPER.div((unsigned)i), r = i - which * per;
         const int k = (int)d2E.div((unsigned)r), c = r - k * (2 * ec);
-        const int q = which == 0 ? q1 : q2;
-        const size_t o = ((size_t)q * Ny + k) * 2 * E + 2 * e0 + c;
+        const int q = which == 0 ? it.q1 : it.q2;
+        const size_t o = ((size_t)q * Ny + k) * 2 * E + 2 * it.e0 + c;
         if (needM) Xs[k * NC + which * 2 * ec + c] = d2f(((const double*)X)[o]);
         Fs[k * NC + which * 2 * ec + c] = F[o];
     }
-    __syncthreads();
-    if (!mbar_wait0(bar_a)) {
-        // the operator copy did not land: flag it, give the copy one more bounded
-        // wait so no write into this CTA's shared memory is left in flight, leave
-        if (threadIdx.x == 0) atomicExch(g.status, 1);
-        mbar_wait0(bar_a);
-        return;
-    }
-    double2* M1 = f == 0 ? g.mx1_v : g.mx1_e;
-    double2* O = (s == 2) ? (f == 0 ? g.v_t : g.e_t) : (f == 0 ? g.v_s : g.e_s);
+}
+
+// products with the transposed operators MT = (M - I)^T, PT = P^T and the
+// update x+ = x_t + ((M - I) x_t + P F~) of the item's columns
+__device__ __forceinline__ void helm_compute(const GroupView& g, int s, const HelmItem& it, const float* MT,
+                                             const float* PT, const float* Xs, const float* Fs) {
+    const int Ny = g.ny, RP = g.rp, E = g.E, NC = it.NC, ec = it.ec;
+    const bool needM = (s != 2);
+    const double2* X = it.f == 0 ? g.v_t : g.e_t;
+    double2* M1 = it.f == 0 ? g.mx1_v : g.mx1_e;
+    double2* O = (s == 2) ? (it.f == 0 ? g.v_t : g.e_t) : (it.f == 0 ? g.v_s : g.e_s);
     const int RB = RP / 4, CB = NC / 2;
-    const FastDiv dCB((unsigned)CB);
+    const FastDiv dCB((unsigned)CB), d2E((unsigned)(2 * ec));
     for (int m = threadIdx.x; m < RB * CB; m += THREADS) {
         const int rb = (int)dCB.div((unsigned)m), cb = m - rb * CB;
         const int r0 = 4 * rb, c0 = 2 * cb;
@@ -347,8 +331,8 @@ __global__ void __launch_bounds__(THREADS) k_helm_t(GroupView g, int s) {
                 mb.x += mk.x * xk.y; mb.y += mk.y * xk.y; mb.z += mk.z * xk.y; mb.w += mk.w * xk.y;
             }
         }
-        const int which = (int)d2E.div((unsigned)c0), cl = 2 * e0 + c0 - which * 2 * ec;
-        const int q = which == 0 ? q1 : q2;
+        const int which = (int)d2E.div((unsigned)c0), cl = 2 * it.e0 + c0 - which * 2 * ec;
+        const int q = which == 0 ? it.q1 : it.q2;
         const float rp[2][4] = {{pa.x, pa.y, pa.z, pa.w}, {pb.x, pb.y, pb.z, pb.w}};
         const float rm[2][4] = {{ma.x, ma.y, ma.z, ma.w}, {mb.x, mb.y, mb.z, mb.w}};
         // x+ = x_t + ((M - I) x_t + P F~): the increment in single precision, one
@@ -385,6 +369,122 @@ __global__ void __launch_bounds__(THREADS) k_helm_t(GroupView g, int s) {
             og[o] = x0[i] + f2d(d0[i] + rp[0][i]);
             og[o + 1] = x1[i] + f2d(d1[i] + rp[1][i]);
         }
+    }
+}
+
+// TMA bulk copy of the item's operators ((M - I)^T then P^T, contiguous; only
+// P^T when M is not needed) into dst, completing on mbarrier bar
+__device__ __forceinline__ void helm_issue(const GroupView& g, int s, const HelmItem& it, float* dst, unsigned bar) {
+    const size_t mat = (size_t)g.ny * g.rp;
+    const bool needM = (s != 2);
+    const float* src = g.opsfT[s == 0 ? 0 : 1] + ((size_t)it.p * 4 + 2 * it.f) * mat;
+    const unsigned bytes = (unsigned)((needM ? 2 : 1) * mat * sizeof(float));
+    const float* from = needM ? src : src + mat;
+    float* to = needM ? dst : dst + mat;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_u32(to)), "l"(from), "r"(bytes), "r"(bar) : "memory");
+}
+
+// one CTA per (pair, field, member chunk)
+__global__ void __launch_bounds__(THREADS) k_helm_t(GroupView g, int s) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    const int Ny = g.ny, RP = g.rp, E = g.E, NKX = g.nkx;
+    // leading CTAs: rows of the mean-flow update (independent work that fills
+    // SMs beside the wavenumber pairs), finished by launch_mean_finish
+    const int nrow = mean_row_ctas(g);
+    if ((int)blockIdx.x < nrow) {
+        mean_rows(g, s, blockIdx.x % E, (blockIdx.x / E) * (THREADS / 32), sm);
+        return;
+    }
+    const int b = blockIdx.x - nrow;
+    const int p = b % g.npairs, f = (b / g.npairs) & 1, ch = b / (2 * g.npairs);
+    if (!g.lin && p % NKX == 0 && p / NKX == 0) return;   // the mean mode (DNS groups)
+    const HelmItem it = helm_item(g, p, f, ch);
+    const size_t mat = (size_t)Ny * RP;           // floats per transposed operator
+    float* MT = (float*)sm;                       // [Ny][RP]  (M - I)^T
+    float* PT = MT + mat;                         // [Ny][RP]  P^T
+    float* Xs = PT + mat;                         // [Ny][NC]
+    float* Fs = Xs + (size_t)Ny * it.NC;          // [Ny][NC]
+    unsigned long long* bar = (unsigned long long*)(Fs + (size_t)Ny * it.NC + 2);
+    const unsigned bar_a = smem_u32(bar);
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_a) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) helm_issue(g, s, it, MT, bar_a);
+    helm_stage(g, it, s != 2, Xs, Fs);
+    __syncthreads();
+    if (!mbar_wait(bar_a, 0)) {
+        // the operator copy did not land: flag it, give the copy one more bounded
+        // wait so no write into this CTA's shared memory is left in flight, leave
+        if (threadIdx.x == 0) atomicExch(g.status, 1);
+        mbar_wait(bar_a, 0);
+        return;
+    }
+    helm_compute(g, s, it, MT, PT, Xs, Fs);
+}
+
+// Persistent variant: after the mean-row CTAs, every CTA loops over work items
+// (the valid (pair, field, chunk) triples, the DNS mean mode left out) with the
+// grid stride, and while it computes one item the TMA copy of its next item's
+// operators lands in the other of two buffers.  Every thread takes part in
+// every bounded wait and the CTA decides together (__syncthreads_and), so a
+// wait that gives up ends the whole CTA, after one more bounded wait for each
+// copy still in flight.
+__global__ void __launch_bounds__(THREADS) k_helm_tp(GroupView g, int s) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    const int Ny = g.ny, RP = g.rp, E = g.E;
+    const int nrow = mean_row_ctas(g);
+    if ((int)blockIdx.x < nrow) {
+        mean_rows(g, s, blockIdx.x % E, (blockIdx.x / E) * (THREADS / 32), sm);
+        return;
+    }
+    const int npv = g.lin ? g.npairs : g.npairs - 1, p0 = g.lin ? 0 : 1;
+    const int nitems = 2 * npv * helm_member_chunks(g);
+    const int stride = gridDim.x - nrow;
+    const size_t mat = (size_t)Ny * RP;
+    float* OP0 = (float*)sm;                      // [2][Ny][RP] (M - I)^T, P^T
+    float* OP1 = OP0 + 2 * mat;
+    float* Xs = OP1 + 2 * mat;
+    float* Fs = Xs + (size_t)Ny * 4 * helm_member_chunk(g);
+    unsigned long long* bars = (unsigned long long*)(Fs + (size_t)Ny * 4 * helm_member_chunk(g) + 2);
+    const unsigned bar0 = smem_u32(bars), bar1 = smem_u32(bars + 1);
+    auto decode = [&](int t) {
+        const int p = p0 + t % npv, f = (t / npv) & 1, ch = t / (2 * npv);
+        return helm_item(g, p, f, ch);
+    };
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar1) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    int t = blockIdx.x - nrow;
+    if (t < nitems && threadIdx.x == 0) helm_issue(g, s, decode(t), OP0, bar0);
+    unsigned ph0 = 0, ph1 = 0;
+    for (int buf = 0; t < nitems; t += stride, buf ^= 1) {
+        const HelmItem it = decode(t);
+        helm_stage(g, it, s != 2, Xs, Fs);
+        // staging done, and every thread finished the previous item (whose
+        // operator buffer the next copy reuses)
+        __syncthreads();
+        const int tn = t + stride;
+        if (tn < nitems && threadIdx.x == 0) helm_issue(g, s, decode(tn), buf ? OP0 : OP1, buf ? bar0 : bar1);
+        const bool ok = mbar_wait(buf ? bar1 : bar0, buf ? ph1 : ph0);
+        if (!__syncthreads_and(ok)) {
+            if (threadIdx.x == 0) {
+                atomicExch(g.status, 1);
+                mbar_wait(buf ? bar1 : bar0, buf ? ph1 : ph0);
+                if (tn < nitems) mbar_wait(buf ? bar0 : bar1, buf ? ph0 : ph1);
+            }
+            return;
+        }
+        if (buf) ph1 ^= 1u; else ph0 ^= 1u;
+        const float* OP = buf ? OP1 : OP0;
+        helm_compute(g, s, it, OP, OP + mat, Xs, Fs);
+        __syncthreads();   // Xs, Fs are restaged for the next item
     }
 }
 
@@ -439,10 +539,41 @@ void launch_helm_t(const GroupView& g, int s, cudaStream_t st) {
         g, s);
 }
 
+size_t helm_tp_smem_bytes(const GroupView& g) {
+    const int nc = 2 * 2 * helm_member_chunk(g);
+    size_t b = (4 * (size_t)g.ny * g.rp + 2 * (size_t)g.ny * nc + 2) * sizeof(float) + 2 * 8 + 16;
+    size_t m = mean_smem_bytes(g);
+    return b > m ? b : m;
+}
+
+// persistent CTAs: as many as fit on the GPU at once (never more than items)
+void launch_helm_tp(const GroupView& g, int s, cudaStream_t st) {
+    static int n_sm = 0, occ = 0;
+    static size_t occ_smem = 0;
+    const size_t smem = helm_tp_smem_bytes(g);
+    if (n_sm == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    }
+    if (occ_smem != smem) {
+        occ = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, gt::k_helm_tp, gt::THREADS, smem);
+        if (occ < 1) occ = 1;
+        occ_smem = smem;
+    }
+    const int nitems = 2 * (g.lin ? g.npairs : g.npairs - 1) * helm_member_chunks(g);
+    int np = occ * (n_sm > 0 ? n_sm : 1);
+    if (np > nitems) np = nitems;
+    if (np < 1) np = 1;
+    gt::k_helm_tp<<<mean_row_ctas(g) + np, gt::THREADS, smem, st>>>(g, s);
+}
+
 void set_attributes_gemm_t() {
     allow_max_dynamic_smem(gt::k_yderiv_t);
     allow_max_dynamic_smem(gt::k_forcing_t);
     allow_max_dynamic_smem(gt::k_helm_t);
+    allow_max_dynamic_smem(gt::k_helm_tp);
 }
 
 }  // namespace dnsk

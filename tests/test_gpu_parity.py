@@ -239,7 +239,7 @@ def test_autotuner_picks_a_variant_caches_it_and_matches_that_variant(tmp_path):
     choice = dns.dns_kernel_choice(ens.h, 0)
     plane = dns.dns_kernel_choice(ens.h, 0, "plane")
     helm = dns.dns_kernel_choice(ens.h, 0, "helm")
-    assert choice in ("simt", "tc") and plane in ("cta", "lines") and helm in ("simt", "tc")
+    assert choice in ("simt", "tc") and plane in ("cta", "lines") and helm in ("simt", "tc", "persist")
     ens.set_state(0, st["v"], st["eta"], st["U"], st["W"])
     ens.step(3)
     got = ens.get_state(0)
@@ -275,6 +275,24 @@ def test_tensor_core_implicit_apply_matches_fp64(mx, my, mz, E):
     ens.close()
     err = mixed_errors(_run(g, st, 10, "mixed", helm="tc"), ref)
     assert np.all(err[:, :3] < 1e-6), err
+
+
+@pytest.mark.parametrize("mx,my,mz,E", [(32, 49, 32, 8), (16, 33, 16, 3), (32, 33, 32, 64), (64, 65, 64, 2),
+                                        (16, 21, 32, 33), (128, 33, 128, 2)])
+def test_persistent_implicit_apply_is_bitwise_the_one_shot_kernel(mx, my, mz, E):
+    """The persistent, double-buffered implicit apply runs the same per-pair
+    arithmetic as the one-CTA-per-pair kernel: identical results, bit for bit
+    (member blocks, 128-point grids, odd member counts)."""
+    g = group("poiseuille", mx, my, mz, 2 * np.pi, np.pi, 1650.0, 0.005, E)
+    st = _state(g, 72, 5e-2)
+    pin = dict(ygemm="simt", plane="default")
+    ens = dns.Ensemble([g], precision="mixed", helm="persist", **pin)
+    assert dns.dns_kernel_choice(ens.h, 0, "helm") == "persist"
+    ens.close()
+    a = _run(g, st, 4, "mixed", helm="persist", **pin)
+    b = _run(g, st, 4, "mixed", helm="simt", **pin)
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
 
 
 @pytest.mark.parametrize("mx,mz", [(128, 128), (128, 64), (64, 128)])
