@@ -145,7 +145,10 @@ typedef struct {
                                       wavenumber pair and field), 2 tcgen05 tensor cores with
                                       split-BF16 operands (groups with My <= 66 and <= 64 members;
                                       others use 1), 3 register-tiled FP32 in persistent CTAs that
-                                      copy the next pair's operators while computing the current */
+                                      copy the next pair's operators while computing the current
+                                      (only on request: its grid fills the GPU, which in a step
+                                      starves concurrent member blocks; the autotuner chooses
+                                      between 1 and 2) */
 } dns_config;
 
 /* One-point statistics of one member (paper Sec. 4), computed from the current

@@ -379,7 +379,7 @@ int choose_variants(dns_handle* h, const dns_config* cfg, GroupView& v, int gi) 
     if (precision_mixed(h)) {
         size_t m1 = dnsk::helm_t_smem_bytes(v), m2 = dnsk::yderiv_t_smem_bytes(v), m3 = dnsk::forcing_t_smem_bytes(v);
         if (helm_tc_candidate(v) && dnsk::helm_tc_smem_bytes(v) > m1) m1 = dnsk::helm_tc_smem_bytes(v);
-        if ((v.helm == 0 || v.helm == 3) && dnsk::helm_tp_smem_bytes(v) > m1) m1 = dnsk::helm_tp_smem_bytes(v);
+        if (v.helm == 3 && dnsk::helm_tp_smem_bytes(v) > m1) m1 = dnsk::helm_tp_smem_bytes(v);
         size_t mm = m1 > m2 ? m1 : m2;
         mm = mm > m3 ? mm : m3;
         if (mm > 227 * 1024)
@@ -773,7 +773,10 @@ int dns_bind_workspace(dns_handle* h, void* dev_ptr, size_t bytes) {
             cudaEvent_t e0, e1;
             cudaEventCreate(&e0);
             cudaEventCreate(&e1);
-            for (int cand = 1; cand <= 3; ++cand) {
+            // the persistent variant (3) fills the whole GPU, which timed alone
+            // wins but inside the step starves the concurrent member blocks and
+            // groups: only on request, never autotuned
+            for (int cand = 1; cand <= 2; ++cand) {
                 if (cand == 2 && !dnsk::helm_tc_supported(v)) continue;
                 auto run = [&]() {
                     if (cand == 2) dnsk::launch_helm_tc(v, 1, st);

@@ -291,15 +291,34 @@ __device__ __forceinline__ void helm_stage(const GroupView& g, const HelmItem& i
     const int Ny = g.ny, E = g.E, ec = it.ec, NC = it.NC;
     const double2* X = it.f == 0 ? g.v_t : g.e_t;
     const float* F = (const float*)(it.f == 0 ? g.Fv : g.Fe);   // single-precision F~ (mixed path)
-    const int per = Ny * 2 * ec;
+    const int per = Ny * 2 * ec, total = it.nq * per;
     const FastDiv dPER((unsigned)per), d2E((unsigned)(2 * ec));
-    for (int i = threadIdx.x; i < it.nq * per; i += THREADS) {
-        const int which = (int)dPER.div((unsigned)i), r = i - which * per;
-        const int k = (int)d2E.div((unsigned)r), c = r - k * (2 * ec);
-        const int q = which == 0 ? it.q1 : it.q2;
-        const size_t o = ((size_t)q * Ny + k) * 2 * E + 2 * it.e0 + c;
-        if (needM) Xs[k * NC + which * 2 * ec + c] = d2f(((const double*)X)[o]);
-        Fs[k * NC + which * 2 * ec + c] = F[o];
+    // a thread's elements in batches of four: all global loads first, then the
+    // conversions and the shared stores
+    constexpr int B = 4;
+    for (int i0 = threadIdx.x; i0 < total; i0 += B * THREADS) {
+        double xv[B];
+        float fv[B];
+        int so[B];
+#pragma unroll
+        for (int u = 0; u < B; ++u) {
+            const int i = i0 + u * THREADS;
+            so[u] = -1;
+            if (i >= total) continue;
+            const int which = (int)dPER.div((unsigned)i), r = i - which * per;
+            const int k = (int)d2E.div((unsigned)r), c = r - k * (2 * ec);
+            const int q = which == 0 ? it.q1 : it.q2;
+            const size_t o = ((size_t)q * Ny + k) * 2 * E + 2 * it.e0 + c;
+            so[u] = k * NC + which * 2 * ec + c;
+            xv[u] = needM ? ((const double*)X)[o] : 0.0;
+            fv[u] = F[o];
+        }
+#pragma unroll
+        for (int u = 0; u < B; ++u) {
+            if (so[u] < 0) continue;
+            if (needM) Xs[so[u]] = d2f(xv[u]);
+            Fs[so[u]] = fv[u];
+        }
     }
 }
 
@@ -387,7 +406,7 @@ __device__ __forceinline__ void helm_issue(const GroupView& g, int s, const Helm
 }
 
 // one CTA per (pair, field, member chunk)
-__global__ void __launch_bounds__(THREADS) k_helm_t(GroupView g, int s) {
+__global__ void __launch_bounds__(THREADS, 3) k_helm_t(GroupView g, int s) {
     extern __shared__ __align__(16) unsigned char sm[];
     const int Ny = g.ny, RP = g.rp, E = g.E, NKX = g.nkx;
     // leading CTAs: rows of the mean-flow update (independent work that fills
@@ -433,7 +452,7 @@ __global__ void __launch_bounds__(THREADS) k_helm_t(GroupView g, int s) {
 // every bounded wait and the CTA decides together (__syncthreads_and), so a
 // wait that gives up ends the whole CTA, after one more bounded wait for each
 // copy still in flight.
-__global__ void __launch_bounds__(THREADS) k_helm_tp(GroupView g, int s) {
+__global__ void __launch_bounds__(THREADS, 3) k_helm_tp(GroupView g, int s) {
     extern __shared__ __align__(16) unsigned char sm[];
     const int Ny = g.ny, RP = g.rp, E = g.E;
     const int nrow = mean_row_ctas(g);
