@@ -433,6 +433,7 @@ def gpu_arm(args, rank, world, dist):
     n_timed = max(1, min(args.steps, 5))
     kt = ens.step_timed(n_timed)
     tot = sum(v[0] for v in kt.values())
+    kt = {k: v for k, v in kt.items() if v[1] > 0}          # classes that launched
     shares = {k: (v[0] / tot if tot > 0 else 0.0) for k, v in kt.items()}
     dom = max(kt, key=lambda k: kt[k][0])
     # every member of every group passes through the kernel once per sub-step

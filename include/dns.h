@@ -239,7 +239,7 @@ int dns_last_launch_count(const dns_handle* h);
 
 /* Kernel classes reported by dns_step_timed, in launch order within a sub-step. */
 enum {
-    DNS_K_MEAN_DERIV = 0,  /* dU00/dy, dW00/dy of the sub-step state */
+    DNS_K_MEAN_DERIV = 0,  /* reserved (no kernel of this class any more; always 0) */
     DNS_K_YDERIV = 1,      /* Dv, D2v, D eta (shared Chebyshev operators) */
     DNS_K_PLANE = 2,       /* transforms + advective products + plane means */
     DNS_K_FORCING = 3,     /* F, G and the RK3 combination */

@@ -90,7 +90,6 @@ struct GroupView {
     double2* stage;  // host-layout staging [E][Ny][nmodes] x 2 fields
 };
 
-void launch_mean_deriv(const GroupView& g, const double* U, const double* W, cudaStream_t st);
 template <typename T>
 void launch_yderiv(const GroupView& g, const double2* v, const double2* e, void* P5, cudaStream_t st);
 template <typename T>

@@ -1,45 +1,19 @@
 // Spectral-space kernels of one CN/RK3 sub-step (paper Sec. 3):
-//   k_mean_deriv  dU00/dy, dW00/dy of the sub-step state
 //   k_yderiv      Dv, D2v, D eta on the interior nodes (y-contraction with the
 //                 shared Chebyshev operators, Sec. 3.1) and the H -> P relayout
 //   k_forcing     F = -k^2 Nv - D(i kx Nu + i kz Nw), G = i kz Nu - i kx Nw
 //                 (Eqs. Dv, eta) and the RK3 combination of Sec. 3.1
 //   k_helm        x_s = M_h x_t + P_h F~ per wavenumber pair (Eqs. CN1, CN2),
 //                 with M_1 x_t computed once and reused by sub-steps 2 and 3
-//   k_mean        U00, W00 update (Eqs. CN3, CN4) with the wall columns on the
-//                 right-hand side and the Poiseuille constant-flux gamma
+//   k_mean_finish U00, W00 update (Eqs. CN3, CN4): the Poiseuille constant-flux
+//                 gamma and the profiles, after the rows (mean.cuh) that run as
+//                 extra CTAs of the implicit apply
 //   k_stats_*     one-point statistics (Sec. 4)
 //   k_pack/unpack host layout <-> H layout, Hermitian projection of n = 0
 #include "dns_internal.hpp"
 #include "mean.cuh"
 
 namespace dnsk {
-
-// ----------------------------------------------------------------- mean derivs
-
-__global__ void k_mean_deriv(const double* __restrict__ D1, const double* __restrict__ U,
-                             const double* __restrict__ W, double* __restrict__ dU,
-                             double* __restrict__ dW, int My) {
-    const int e = blockIdx.x;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    for (int i = warp; i < My; i += nw) {
-        double su = 0.0, sw = 0.0;
-        for (int j = lane; j < My; j += 32) {
-            double d = D1[(size_t)i * My + j];
-            su += d * U[(size_t)e * My + j];
-            sw += d * W[(size_t)e * My + j];
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-            su += __shfl_xor_sync(0xffffffffu, su, o);
-            sw += __shfl_xor_sync(0xffffffffu, sw, o);
-        }
-        if (lane == 0) { dU[(size_t)e * My + i] = su; dW[(size_t)e * My + i] = sw; }
-    }
-}
-
-void launch_mean_deriv(const GroupView& g, const double* U, const double* W, cudaStream_t st) {
-    k_mean_deriv<<<g.E, 256, 0, st>>>(g.D1, U, W, g.dU, g.dW, g.my);
-}
 
 // ------------------------------------------------------------------ y-derivs
 

@@ -4,90 +4,19 @@
 
 namespace dnsk {
 
-// Mean-flow update of member e (Eqs. CN3, CN4), run by one 256-thread CTA of
-// the implicit-apply launch.  The forcing d/dy <uv> is folded into the solve
-// (PD = PU D1), so the RK3 combination acts on the plane means themselves:
+// Mean-flow update of every member (Eqs. CN3, CN4).  The forcing d/dy <uv> is
+// folded into the solve (PD = PU D1), so the RK3 combination acts on the plane
+// means themselves:
 //   U_int = MU U_int + PD <uv>~ + bU [U(-1), U(+1)] (+ gamma Ug, Poiseuille),
-// each row one warp with a lane-strided sum and a fixed shuffle tree.
+// each row one warp with a lane-strided sum and a fixed shuffle tree.  The rows
+// are spread over many SMs (the FP64 pipe of one SM is slow):
 __device__ __forceinline__ double warp_sum(double v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
 }
 
-__device__ __forceinline__ void mean_cta(const GroupView& g, int s, int e, unsigned char* sm) {
-    const int Ny = g.ny, My = g.my;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    double* red = (double*)sm;     // [32]
-    double* uvs = red + 32;        // [My] each below
-    double* wvs = uvs + My;
-    double* Ut = wvs + My;
-    double* Wt = Ut + My;
-    double* cu = Wt + My;
-    double* cw = cu + My;
-    double* Un = cw + My;
-    double* Wn = Un + My;
-    const int hi = (s == 0) ? 0 : 1;
-    const double* MU = g.mops[hi];
-    const double* PU = MU + (size_t)Ny * Ny;
-    const double* bU = PU + (size_t)Ny * Ny;
-    const double* Ug = bU + 2 * (size_t)Ny;
-    const double* PD = Ug + Ny;
-    for (int j = threadIdx.x; j < My; j += blockDim.x) {
-        const size_t o = (size_t)e * My + j;
-        const double a = g.uv[o], b = g.wv[o];
-        Ut[j] = g.U_t[o];
-        Wt[j] = g.W_t[o];
-        double ca, cb;
-        if (s == 0) {
-            ca = a; cb = b; g.AU[o] = a; g.AW[o] = b;
-        } else if (s == 1) {
-            const double pa = g.AU[o], pb = g.AW[o];
-            ca = 2.0 * a - pa; cb = 2.0 * b - pb;
-            g.AU[o] = (1.0 / 6.0) * pa + (4.0 / 6.0) * a;
-            g.AW[o] = (1.0 / 6.0) * pb + (4.0 / 6.0) * b;
-        } else {
-            ca = g.AU[o] + (1.0 / 6.0) * a;
-            cb = g.AW[o] + (1.0 / 6.0) * b;
-        }
-        cu[j] = ca;
-        cw[j] = cb;
-    }
-    __syncthreads();
-    for (int i = warp; i < Ny; i += nw) {
-        const double* mr = MU + (size_t)i * Ny;
-        const double* pr = PD + (size_t)i * My;
-        double a = 0.0, c = 0.0;
-        for (int j = lane; j < Ny; j += 32) { a += mr[j] * Ut[j + 1]; c += mr[j] * Wt[j + 1]; }
-        for (int j = lane; j < My; j += 32) { a += pr[j] * cu[j]; c += pr[j] * cw[j]; }
-        a = warp_sum(a);
-        c = warp_sum(c);
-        if (lane == 0) {
-            Un[i + 1] = a + (bU[2 * i] * Ut[0] + bU[2 * i + 1] * Ut[My - 1]);
-            Wn[i + 1] = c + (bU[2 * i] * Wt[0] + bU[2 * i + 1] * Wt[My - 1]);
-        }
-    }
-    if (threadIdx.x == 0) { Un[0] = Ut[0]; Un[My - 1] = Ut[My - 1]; Wn[0] = Wt[0]; Wn[My - 1] = Wt[My - 1]; }
-    __syncthreads();
-    double gam = 0.0;
-    if (g.flow == 1) {
-        double fl = 0.0, fg = 0.0;
-        for (int j = threadIdx.x; j < My; j += blockDim.x) fl += g.ccw[j] * Un[j];
-        for (int i = threadIdx.x; i < Ny; i += blockDim.x) fg += g.ccw[i + 1] * Ug[i];
-        fl = block_sum(fl, red);
-        fg = block_sum(fg, red);
-        gam = (g.bulk_flux - fl) / fg;
-    }
-    double* Uo = (s == 2) ? (g.U_t + (size_t)e * My) : (g.U_s + (size_t)e * My);
-    double* Wo = (s == 2) ? (g.W_t + (size_t)e * My) : (g.W_s + (size_t)e * My);
-    for (int j = threadIdx.x; j < My; j += blockDim.x) {
-        Uo[j] = (j > 0 && j < My - 1) ? Un[j] + gam * Ug[j - 1] : Un[j];
-        Wo[j] = Wn[j];
-    }
-    if (threadIdx.x == 0) g.gamma[e] = gam;
-}
-
-// The same update spread over more SMs (the FP64 pipe of one SM is slow):
-// mean_rows, grid (E, ceil(Ny / warps)), one warp per interior row i, writes
+// mean_rows, E x ceil(Ny / 8) extra CTAs of the implicit-apply launch, one warp
+// per interior row i, writes
 // the pre-gamma profiles Un, Wn (interior rows) to the scratch rows dU, dW.
 // mean_finish, one CTA per member, adds gamma Ug (Poiseuille), writes the
 // profiles and advances the RK accumulators of <uv>, <wv> (after every row CTA
