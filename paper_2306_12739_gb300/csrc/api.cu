@@ -31,6 +31,10 @@ struct HostGroup {
     std::vector<float> kxtf, kztf, k2invf, twxf, twzf, opsf[2], opsfT[2], D1T, D2T;
     std::vector<uint16_t> Atc, Htc[2];
     std::vector<double> fstruct, flam;   // stochastic forcing: structures [NKZ][2][n][Ny], decay rates
+    // stochastic forcing: a side stream for the noise kernel, forked at the start
+    // of every step and joined before the first forcing assembly
+    cudaStream_t nstream = nullptr;
+    cudaEvent_t nfork = nullptr, njoin = nullptr;
 
     // byte offsets inside the workspace
     struct Off { size_t off, bytes; };
@@ -200,6 +204,16 @@ void enqueue_group(dns_handle* h, HostGroup& G, cudaStream_t st, Timer* tm) {
         tm->cls.push_back(c);
     };
     const GroupView& g = G.v;
+    // the step's noise depends only on the step counter: it is drawn beside the
+    // y-derivatives and the plane stage (per-launch timing keeps it in line)
+    const bool side_noise = g.fn > 0 && !tm && G.nstream;
+    if (side_noise) {
+        cudaEventRecord(G.nfork, st);
+        cudaStreamWaitEvent(G.nstream, G.nfork, 0);
+        dnsk::launch_stoch_noise(g, G.nstream);
+        cudaEventRecord(G.njoin, G.nstream);
+        h->launches += 1;
+    }
     for (int s = 0; s < 3; ++s) {
         const double2* cv = s == 0 ? g.v_t : g.v_s;
         const double2* ce = s == 0 ? g.e_t : g.e_s;
@@ -216,7 +230,8 @@ void enqueue_group(dns_handle* h, HostGroup& G, cudaStream_t st, Timer* tm) {
             else dnsk::launch_plane_f32(g, cU, cW, st);
             mark(DNS_K_PLANE);
             if (g.shared_mean && g.E > 1) { dnsk::launch_shared_mean(g, false, st); h->launches += 1; }
-            if (s == 0 && g.fn > 0) { dnsk::launch_stoch_noise(g, st); h->launches += 1; }
+            if (s == 0 && g.fn > 0 && !side_noise) { dnsk::launch_stoch_noise(g, st); h->launches += 1; }
+            if (s == 0 && side_noise) cudaStreamWaitEvent(st, G.njoin, 0);
             dnsk::launch_forcing_t(g, s, st);
         } else {
             dnsk::launch_yderiv<double>(g, cv, ce, g.P5, st);
@@ -226,7 +241,8 @@ void enqueue_group(dns_handle* h, HostGroup& G, cudaStream_t st, Timer* tm) {
             else dnsk::launch_plane_state<double>(g, cU, cW, st);
             mark(DNS_K_PLANE);
             if (g.shared_mean && g.E > 1) { dnsk::launch_shared_mean(g, true, st); h->launches += 1; }
-            if (s == 0 && g.fn > 0) { dnsk::launch_stoch_noise(g, st); h->launches += 1; }
+            if (s == 0 && g.fn > 0 && !side_noise) { dnsk::launch_stoch_noise(g, st); h->launches += 1; }
+            if (s == 0 && side_noise) cudaStreamWaitEvent(st, G.njoin, 0);
             dnsk::launch_forcing<double>(g, s, st);
         }
         mark(DNS_K_FORCING);
@@ -1336,6 +1352,11 @@ int dns_set_stochastic_forcing(dns_handle* h, int group, int kx_index, int n_eig
         G.fstruct = f;
         G.flam = lam;
         if (!on) continue;
+        if (!G.nstream) {
+            if ((rc = check(h, cudaStreamCreateWithFlags(&G.nstream, cudaStreamNonBlocking), "noise stream"))) return rc;
+            if ((rc = check(h, cudaEventCreateWithFlags(&G.nfork, cudaEventDisableTiming), "noise event"))) return rc;
+            if ((rc = check(h, cudaEventCreateWithFlags(&G.njoin, cudaEventDisableTiming), "noise event"))) return rc;
+        }
         if ((rc = check(h, cudaMemcpyAsync((void*)v.fbasis, rhs.data(), rhs.size() * 8, cudaMemcpyHostToDevice, h->stream),
                         "upload forcing structures")))
             return rc;
@@ -1393,6 +1414,11 @@ int dns_destroy(dns_handle* h) {
     if (h->gexec) cudaGraphExecDestroy(h->gexec);
     if (h->graph) cudaGraphDestroy(h->graph);
     for (auto s2 : h->gstreams) cudaStreamDestroy(s2);
+    for (auto& G : h->groups) {
+        if (G.nstream) cudaStreamDestroy(G.nstream);
+        if (G.nfork) cudaEventDestroy(G.nfork);
+        if (G.njoin) cudaEventDestroy(G.njoin);
+    }
 
     for (auto e2 : h->gevents) cudaEventDestroy(e2);
     if (h->fork_ev) cudaEventDestroy(h->fork_ev);
