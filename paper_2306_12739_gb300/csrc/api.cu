@@ -219,10 +219,11 @@ void enqueue_group(dns_handle* h, HostGroup& G, cudaStream_t st, Timer* tm) {
         const double2* ce = s == 0 ? g.e_t : g.e_s;
         const double* cU = s == 0 ? g.U_t : g.U_s;
         const double* cW = s == 0 ? g.W_t : g.W_s;
+        const int sprev = (s > 0 && !g.lin) ? s - 1 : -1;   // mean-flow finish carried by the y-derivatives
         mark(-1);
         if (precision_mixed(h)) {
-            if (g.ygemm == 2) dnsk::launch_yderiv_tc(g, cv, ce, st);
-            else dnsk::launch_yderiv_t(g, cv, ce, st);
+            if (g.ygemm == 2) dnsk::launch_yderiv_tc(g, cv, ce, st, sprev);
+            else dnsk::launch_yderiv_t(g, cv, ce, st, sprev);
             mark(DNS_K_YDERIV);
             if (g.lin) dnsk::launch_lin_plane(g, false, st);
             else if (g.plane == 2) dnsk::launch_plane_cl(g, false, cU, cW, st);
@@ -234,7 +235,7 @@ void enqueue_group(dns_handle* h, HostGroup& G, cudaStream_t st, Timer* tm) {
             if (s == 0 && side_noise) cudaStreamWaitEvent(st, G.njoin, 0);
             dnsk::launch_forcing_t(g, s, st);
         } else {
-            dnsk::launch_yderiv<double>(g, cv, ce, g.P5, st);
+            dnsk::launch_yderiv<double>(g, cv, ce, g.P5, st, sprev);
             mark(DNS_K_YDERIV);
             if (g.lin) dnsk::launch_lin_plane(g, true, st);
             else if (g.plane == 2) dnsk::launch_plane_cl(g, true, cU, cW, st);
@@ -260,10 +261,14 @@ void enqueue_group(dns_handle* h, HostGroup& G, cudaStream_t st, Timer* tm) {
             continue;
         }
         // the mean-flow rows ran as leading CTAs of the implicit apply; gamma and
-        // the profiles
-        dnsk::launch_mean_finish(g, s, st);
-        mark(DNS_K_MEAN);
-        h->launches += 5;
+        // the profiles: the next sub-step's y-derivative launch carries them, the
+        // last sub-step's (which completes the step's state) runs here
+        if (s == 2) {
+            dnsk::launch_mean_finish(g, s, st);
+            mark(DNS_K_MEAN);
+            h->launches += 1;
+        }
+        h->launches += 4;
     }
 }
 

@@ -90,8 +90,9 @@ struct GroupView {
     double2* stage;  // host-layout staging [E][Ny][nmodes] x 2 fields
 };
 
+// sprev >= 0: the launch also carries the mean-flow finish of sub-step sprev
 template <typename T>
-void launch_yderiv(const GroupView& g, const double2* v, const double2* e, void* P5, cudaStream_t st);
+void launch_yderiv(const GroupView& g, const double2* v, const double2* e, void* P5, cudaStream_t st, int sprev = -1);
 template <typename T>
 void launch_plane_state(const GroupView& g, const double* U, const double* W, cudaStream_t st);
 template <typename T>
@@ -126,7 +127,7 @@ inline size_t mean_smem_bytes(const GroupView& g) { return (8 * (size_t)g.my + 3
 size_t helm_t_smem_bytes(const GroupView& g);
 size_t yderiv_t_smem_bytes(const GroupView& g);
 size_t forcing_t_smem_bytes(const GroupView& g);
-void launch_yderiv_t(const GroupView& g, const double2* v, const double2* e, cudaStream_t st);
+void launch_yderiv_t(const GroupView& g, const double2* v, const double2* e, cudaStream_t st, int sprev = -1);
 void launch_forcing_t(const GroupView& g, int s, cudaStream_t st);
 void launch_helm_t(const GroupView& g, int s, cudaStream_t st);
 size_t helm_tp_smem_bytes(const GroupView& g);
@@ -134,7 +135,7 @@ void launch_helm_tp(const GroupView& g, int s, cudaStream_t st);
 void set_attributes_gemm_t();
 bool yderiv_tc_supported(const GroupView& g);
 size_t yderiv_tc_smem_bytes(const GroupView& g);
-void launch_yderiv_tc(const GroupView& g, const double2* v, const double2* e, cudaStream_t st);
+void launch_yderiv_tc(const GroupView& g, const double2* v, const double2* e, cudaStream_t st, int sprev = -1);
 void set_attributes_yderiv_tc();
 bool helm_tc_supported(const GroupView& g);
 size_t helm_tc_smem_bytes(const GroupView& g);

@@ -45,10 +45,11 @@ __host__ __device__ inline Tile tile_of(int E, int ny, int nm) {
 // --------------------------------------------------------------- y-derivs
 
 __global__ void __launch_bounds__(THREADS) k_yderiv_t(GroupView g, const double2* __restrict__ V,
-                                                     const double2* __restrict__ H) {
+                                                     const double2* __restrict__ H, int sprev) {
     extern __shared__ __align__(16) unsigned char sm[];
     const int Ny = g.ny, RP = g.rp, E = g.E, NM = g.nmodes;
     const Tile T = tile_of(E, Ny, NM);
+    if (mean_finish_rows(g, sprev, (E + T.EBT - 1) / T.EBT, sm)) return;
     const int q0 = blockIdx.x * T.QT, e0 = blockIdx.y * T.EBT;
     const int NCR = 2 * T.NC;                       // real columns
     float* D1 = (float*)sm;                         // [Ny][RP]
@@ -541,10 +542,11 @@ size_t forcing_t_smem_bytes(const GroupView& g) {
     return ((size_t)g.ny * g.rp + 3 * (size_t)g.ny * 2 * t.NC) * sizeof(float);
 }
 
-void launch_yderiv_t(const GroupView& g, const double2* v, const double2* e, cudaStream_t st) {
+void launch_yderiv_t(const GroupView& g, const double2* v, const double2* e, cudaStream_t st, int sprev) {
     gt::Tile t = gt::tile_of(g.E, g.ny, g.nmodes);
     dim3 grid((g.nmodes + t.QT - 1) / t.QT, (g.E + t.EBT - 1) / t.EBT);
-    gt::k_yderiv_t<<<grid, gt::THREADS, yderiv_t_smem_bytes(g), st>>>(g, v, e);
+    grid.y += mean_finish_extra_rows(g, grid.x, sprev);
+    gt::k_yderiv_t<<<grid, gt::THREADS, yderiv_t_smem_bytes(g), st>>>(g, v, e, sprev);
 }
 
 void launch_forcing_t(const GroupView& g, int s, cudaStream_t st) {

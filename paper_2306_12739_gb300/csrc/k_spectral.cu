@@ -25,9 +25,11 @@ constexpr int EB = 4;   // members per tile
 template <typename T>
 __global__ void __launch_bounds__(256) k_yderiv(const double2* __restrict__ v, const double2* __restrict__ et,
                                                 const T* __restrict__ D1i, const T* __restrict__ D2i,
-                                                typename C2<T>::type* __restrict__ P5, int Ny, int E, int nmodes) {
+                                                typename C2<T>::type* __restrict__ P5, int Ny, int E, int nmodes,
+                                                GroupView g, int sprev) {
     typedef typename C2<T>::type C;
     extern __shared__ __align__(16) unsigned char sm[];
+    if (mean_finish_rows(g, sprev, (E + EB - 1) / EB, sm)) return;
     C* xv = (C*)sm;                 // [QB][Ny][EB]
     C* xe = xv + QB * Ny * EB;
     const int q0 = blockIdx.x * QB, e0 = blockIdx.y * EB;
@@ -85,13 +87,14 @@ template <typename T> __host__ __device__ const T* d2i_of(const GroupView& g);
 template <> __host__ __device__ const double* d2i_of<double>(const GroupView& g) { return g.D2i; }
 
 template <typename T>
-void launch_yderiv(const GroupView& g, const double2* v, const double2* e, void* P5, cudaStream_t st) {
+void launch_yderiv(const GroupView& g, const double2* v, const double2* e, void* P5, cudaStream_t st, int sprev) {
     dim3 grid((g.nmodes + QB - 1) / QB, (g.E + EB - 1) / EB);
+    grid.y += mean_finish_extra_rows(g, grid.x, sprev);
     size_t smem = 2 * (size_t)QB * g.ny * EB * sizeof(typename C2<T>::type);
     k_yderiv<T><<<grid, 256, smem, st>>>(v, e, d1i_of<T>(g), d2i_of<T>(g), (typename C2<T>::type*)P5, g.ny, g.E,
-                                         g.nmodes);
+                                         g.nmodes, g, sprev);
 }
-template void launch_yderiv<double>(const GroupView&, const double2*, const double2*, void*, cudaStream_t);
+template void launch_yderiv<double>(const GroupView&, const double2*, const double2*, void*, cudaStream_t, int);
 
 // ------------------------------------------------------------------- forcing
 

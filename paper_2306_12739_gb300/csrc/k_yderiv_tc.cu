@@ -16,6 +16,7 @@
 // a timeout the kernel latches the status word, still releases its TMEM, and
 // leaves.
 #include "dns_internal.hpp"
+#include "mean.cuh"
 #include <cuda_bf16.h>
 #include <cstring>
 #include <vector>
@@ -117,10 +118,11 @@ __host__ __device__ inline size_t smem_b(int KP) {
 __host__ __device__ inline size_t smem_total(int KP) { return smem_a(KP) + smem_b(KP) + 64; }
 
 __global__ void __launch_bounds__(THREADS, 2) k_yderiv_tc(GroupView g, const double2* __restrict__ V,
-                                                          const double2* __restrict__ H) {
+                                                          const double2* __restrict__ H, int sprev) {
     extern __shared__ __align__(1024) unsigned char sm[];
     const int Ny = g.ny, KP = g.kp, E = g.E, NM = g.nmodes;
     const Tile T = tile_of(E);
+    if (mean_finish_rows(g, sprev, (E + T.EBT - 1) / T.EBT, sm)) return;
     const int q0 = blockIdx.x * T.QT, e0 = blockIdx.y * T.EBT;
     unsigned char* A = sm;
     unsigned char* B = sm + smem_a(KP);
@@ -300,10 +302,11 @@ bool yderiv_tc_supported(const GroupView& g) { return g.ny <= 64 && g.E <= 64; }
 
 size_t yderiv_tc_smem_bytes(const GroupView& g) { return tc::smem_total(g.kp); }
 
-void launch_yderiv_tc(const GroupView& g, const double2* v, const double2* e, cudaStream_t st) {
+void launch_yderiv_tc(const GroupView& g, const double2* v, const double2* e, cudaStream_t st, int sprev) {
     tc::Tile t = tc::tile_of(g.E);
     dim3 grid((g.nmodes + t.QT - 1) / t.QT, (g.E + t.EBT - 1) / t.EBT);
-    tc::k_yderiv_tc<<<grid, tc::THREADS, tc::smem_total(g.kp), st>>>(g, v, e);
+    grid.y += mean_finish_extra_rows(g, grid.x, sprev);
+    tc::k_yderiv_tc<<<grid, tc::THREADS, tc::smem_total(g.kp), st>>>(g, v, e, sprev);
 }
 
 void set_attributes_yderiv_tc() {

@@ -110,4 +110,20 @@ __device__ __forceinline__ void mean_finish(const GroupView& g, int s, int e, un
     if (threadIdx.x == 0) g.gamma[e] = gam;
 }
 
+// The finish of sub-steps 1 and 2 rides on the next sub-step's y-derivative
+// launch (it is independent of it and done before the plane stage reads the
+// profiles): grid rows gy0 and beyond of that 2-D launch hold one CTA per
+// member, row-major over the grid's x extent.  True for those CTAs (which then
+// return without touching the y-derivative work).
+__device__ __forceinline__ bool mean_finish_rows(const GroupView& g, int sprev, int gy0, unsigned char* sm) {
+    if (sprev < 0 || (int)blockIdx.y < gy0) return false;
+    const int e = ((int)blockIdx.y - gy0) * (int)gridDim.x + (int)blockIdx.x;
+    if (e < g.E) mean_finish(g, sprev, e, sm);
+    return true;
+}
+
+inline int mean_finish_extra_rows(const GroupView& g, int gx, int sprev) {
+    return sprev < 0 ? 0 : (g.E + gx - 1) / gx;
+}
+
 }  // namespace dnsk
