@@ -860,10 +860,7 @@ static int set_state_block(dns_handle* h, int group, int member0, int count, con
             return rc;
     }
     dnsk::launch_pack(v, member0, count, st);
-    if ((rc = check(h, cudaGetLastError(), "pack state"))) return rc;
-    // host buffers may be pageable and reused by the caller right away
-    if (ptr_kind == 0) return check(h, cudaStreamSynchronize(st), "set state");
-    return DNS_OK;
+    return check(h, cudaGetLastError(), "pack state");
 }
 
 int dns_set_state(dns_handle* h, int group, int member0, int count, const double* v_hat,
@@ -885,6 +882,9 @@ int dns_set_state(dns_handle* h, int group, int member0, int count, const double
                                  U00 ? U00 + o * pu : nullptr, W00 ? W00 + o * pu : nullptr, ptr_kind);
         if (rc) return rc;
     }
+    // host buffers may be pageable and reused by the caller right away: one
+    // synchronisation after every block's copies
+    if (ptr_kind == 0) return check(h, cudaStreamSynchronize(h->stream), "set state");
     return DNS_OK;
 }
 
@@ -909,8 +909,7 @@ static int get_state_block(const dns_handle* hc, int group, int member0, int cou
     if (W00 && (rc = check(h, cudaMemcpyAsync(W00, v.W_t + (size_t)member0 * v.my, sizeof(double) * count * v.my, k, st),
                            "get W")))
         return rc;
-    if ((rc = check(h, cudaStreamSynchronize(st), "get state"))) return rc;
-    return device_status(h);
+    return DNS_OK;
 }
 
 int dns_get_state(const dns_handle* hc, int group, int member0, int count, double* v_hat,
@@ -933,7 +932,10 @@ int dns_get_state(const dns_handle* hc, int group, int member0, int count, doubl
                                  W00 ? W00 + o * pu : nullptr, ptr_kind);
         if (rc) return rc;
     }
-    return DNS_OK;
+    // one synchronisation after every block's unpack and copies
+    int rc = check(h, cudaStreamSynchronize(h->stream), "get state");
+    if (rc) return rc;
+    return device_status(h);
 }
 
 int dns_step(dns_handle* h, int nsteps) {
