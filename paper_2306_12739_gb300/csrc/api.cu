@@ -476,7 +476,7 @@ int dns_create(const dns_config* cfg, void* cuda_stream, dns_handle** out) {
         m0 += d.members;
         HostGroup& G = h->groups[ig];
         if (b > 0) {
-            // a further block of the same group: same grid and operators
+            // a further block of the same group: same grid and operators (and nblk)
             G = h->groups[ig0];
             G.d = d;
             G.v.E = d.members;
@@ -512,6 +512,7 @@ int dns_create(const dns_config* cfg, void* cuda_stream, dns_handle** out) {
         v.nmodes = v.nkx * v.nkz;
         v.ny = d.my - 2;
         v.E = d.members;
+        v.nblk = nb;
         v.npairs = v.nkx * (v.kz + 1);
         v.rp = (v.ny + 3) / 4 * 4;
         v.kp = (v.ny + 15) / 16 * 16;

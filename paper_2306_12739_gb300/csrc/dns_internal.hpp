@@ -41,6 +41,7 @@ struct GroupView {
     int fn;               // forced streamwise index
     int fneig;            // structures per block (v, eta) and kz
     int m0, Eu;           // first member of this block in its group, members of the group
+    int nblk;             // member blocks the group runs as (concurrent graph branches)
     double fscale;        // eps / sqrt(dt)
     unsigned long long fseed;
     const double* fbasis; // [NKZ][2][fneig][Ny] right-hand-side terms -Delta f_v, -f_eta

@@ -26,8 +26,9 @@ namespace dnsk {
 namespace tc {
 
 constexpr int THREADS = 256;          // 8 warps; warp w reads TMEM lanes 32 (w % 4) in the epilogue
-constexpr int NCOL = 128;             // tile width (real columns) = TMEM columns: 64 of v, 64 of eta
-constexpr int JT = NCOL / 4;          // complex columns per field in a tile
+// Tile width NCOL (template parameter, 128 or 64): real columns = TMEM columns,
+// half of v, half of eta; NCOL / 4 complex columns per field.  The narrow tile
+// doubles the CTAs where the wide one would leave most SMs idle.
 constexpr int MROWS = 128;
 
 __device__ __forceinline__ unsigned su32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -99,7 +100,9 @@ struct Tile {
     int QT, EBT;
 };
 
+template <int NCOL>
 __host__ __device__ inline Tile tile_of(int E) {
+    constexpr int JT = NCOL / 4;
     Tile t;
     t.EBT = E < JT ? E : JT;
     t.QT = JT / t.EBT;
@@ -108,26 +111,30 @@ __host__ __device__ inline Tile tile_of(int E) {
 
 // Shared memory: A pieces [3][128 x KP] bf16 | B pieces [3][NCOL x KP] bf16 (reused
 // as the output staging [3][64][JT+1] float2) | tmem slot | 2 mbarriers.
-constexpr int SROW = JT + 1;          // staging row stride (odd: conflict-free column writes)
+// staging row stride JT + 1 (odd: conflict-free column writes)
 __host__ __device__ inline size_t smem_a(int KP) { return (size_t)3 * MROWS * KP * 2; }
+template <int NCOL>
 __host__ __device__ inline size_t smem_b(int KP) {
     size_t b = (size_t)3 * NCOL * KP * 2;
-    size_t st = (size_t)3 * 64 * SROW * 8;
+    size_t st = (size_t)3 * 64 * (NCOL / 4 + 1) * 8;
     return b > st ? b : st;
 }
-__host__ __device__ inline size_t smem_total(int KP) { return smem_a(KP) + smem_b(KP) + 64; }
+template <int NCOL>
+__host__ __device__ inline size_t smem_total(int KP) { return smem_a(KP) + smem_b<NCOL>(KP) + 64; }
 
+template <int NCOL>
 __global__ void __launch_bounds__(THREADS, 2) k_yderiv_tc(GroupView g, const double2* __restrict__ V,
                                                           const double2* __restrict__ H, int sprev) {
     extern __shared__ __align__(1024) unsigned char sm[];
+    constexpr int SROW = NCOL / 4 + 1;
     const int Ny = g.ny, KP = g.kp, E = g.E, NM = g.nmodes;
-    const Tile T = tile_of(E);
+    const Tile T = tile_of<NCOL>(E);
     if (mean_finish_rows(g, sprev, (E + T.EBT - 1) / T.EBT, sm)) return;
     const int q0 = blockIdx.x * T.QT, e0 = blockIdx.y * T.EBT;
     unsigned char* A = sm;
     unsigned char* B = sm + smem_a(KP);
-    unsigned* tslot = (unsigned*)(B + smem_b(KP));
-    unsigned long long* bars = (unsigned long long*)(B + smem_b(KP) + 16);
+    unsigned* tslot = (unsigned*)(B + smem_b<NCOL>(KP));
+    unsigned long long* bars = (unsigned long long*)(B + smem_b<NCOL>(KP) + 16);
     const unsigned bar_a = su32(&bars[0]), bar_m = su32(&bars[1]);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned LBO = 128, SBO = 16 * KP;            // bytes
@@ -300,17 +307,35 @@ __global__ void __launch_bounds__(THREADS, 2) k_yderiv_tc(GroupView g, const dou
 
 bool yderiv_tc_supported(const GroupView& g) { return g.ny <= 64 && g.E <= 64; }
 
-size_t yderiv_tc_smem_bytes(const GroupView& g) { return tc::smem_total(g.kp); }
+// the narrow tile where the wide one, with the group's concurrent member
+// blocks, gives fewer than two CTAs per SM (with enough concurrent blocks the
+// finer grid only adds per-CTA overhead)
+static int yderiv_tc_width(const GroupView& g) {
+    const tc::Tile t = tc::tile_of<128>(g.E);
+    const long ctas = (long)((g.nmodes + t.QT - 1) / t.QT) * ((g.E + t.EBT - 1) / t.EBT);
+    return ctas * (g.nblk > 0 ? g.nblk : 1) < 2 * 152 ? 64 : 128;
+}
 
-void launch_yderiv_tc(const GroupView& g, const double2* v, const double2* e, cudaStream_t st, int sprev) {
-    tc::Tile t = tc::tile_of(g.E);
+size_t yderiv_tc_smem_bytes(const GroupView& g) {
+    return yderiv_tc_width(g) == 64 ? tc::smem_total<64>(g.kp) : tc::smem_total<128>(g.kp);
+}
+
+template <int NCOL>
+static void launch_yderiv_tc_w(const GroupView& g, const double2* v, const double2* e, cudaStream_t st, int sprev) {
+    const tc::Tile t = tc::tile_of<NCOL>(g.E);
     dim3 grid((g.nmodes + t.QT - 1) / t.QT, (g.E + t.EBT - 1) / t.EBT);
     grid.y += mean_finish_extra_rows(g, grid.x, sprev);
-    tc::k_yderiv_tc<<<grid, tc::THREADS, tc::smem_total(g.kp), st>>>(g, v, e, sprev);
+    tc::k_yderiv_tc<NCOL><<<grid, tc::THREADS, tc::smem_total<NCOL>(g.kp), st>>>(g, v, e, sprev);
+}
+
+void launch_yderiv_tc(const GroupView& g, const double2* v, const double2* e, cudaStream_t st, int sprev) {
+    if (yderiv_tc_width(g) == 64) launch_yderiv_tc_w<64>(g, v, e, st, sprev);
+    else launch_yderiv_tc_w<128>(g, v, e, st, sprev);
 }
 
 void set_attributes_yderiv_tc() {
-    allow_max_dynamic_smem(tc::k_yderiv_tc);
+    allow_max_dynamic_smem(tc::k_yderiv_tc<64>);
+    allow_max_dynamic_smem(tc::k_yderiv_tc<128>);
 }
 
 // Host image of A = [D1_int ; D2_int] split into three BF16 pieces, in the
