@@ -225,6 +225,50 @@ def kernel_work(cls, g, precision):
     return "alu", E * 4.0 * (g["my"]) ** 2, "flop"
 
 
+def member_blocks(g):
+    """Member blocks a group runs as (the library's rule: E/4 clamped to [4, 16],
+    one block below 8 members, shared-mean and linear groups one block)."""
+    if g.get("shared_mean") or g.get("linear"):
+        return 1
+    b = g.get("member_block", 0) or min(16, max(4, g["members"] // 4))
+    return max(1, g["members"] // b)
+
+
+def kernel_bytes(cls, g, precision):
+    """Algorithmic DRAM bytes of kernel class `cls` over one sub-step of group g
+    (every member): the arrays the kernel must read and write once, averaged
+    over the three sub-steps where that differs.  Complex values: 8 B (FP32)
+    or 16 B (FP64) in the P-layout and forcing arrays, 16 B in the FP64 state."""
+    ny, E = g["my"] - 2, g["members"]
+    nkx = 1 if g.get("linear") else (g["mx"] - 1) // 3 + 1
+    nkz = 2 * ((g["mz"] - 1) // 3) + 1
+    S = nkx * nkz * ny * E
+    c = 8 if precision == "mixed" else 16
+    if cls == "yderiv":
+        return 2 * 16 * S + 5 * c * S                    # state in, 5 P-layout fields out
+    if cls == "plane":
+        return 5 * c * S + 3 * c * S                     # 5 fields in, 3 nonlinear terms out
+    if cls == "forcing":
+        return 3 * c * S + 2 * c * S + 2 * c * S * (4.0 / 3.0)   # N in, F G out, RK accumulators
+    if cls == "helm":
+        rp = (ny + 3) // 4 * 4
+        npairs = nkx * (nkz // 2 + 1)
+        opb = 4 if precision == "mixed" else 8
+        mats = (2 + 2 + 1) / 3.0                         # M and P, M reused in the third sub-step
+        ops = member_blocks(g) * npairs * 2 * mats * ny * (rp if precision == "mixed" else ny) * opb
+        m1 = (c if precision == "mixed" else 16) * (2.0 / 3.0)
+        return ops + 2 * S * (16 * (2.0 / 3.0) + c + 16 + m1)   # x_t, F~ in, x+ out, M1 x_t
+    return 0.0
+
+
+def hbm_peak():
+    try:
+        d = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return float(d["hbm_gbs"]), "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback 6.8 TB/s (no MEASURED_PEAKS.json)"
+
+
 def profiled_traffic(kernel, variant):
     """DRAM bytes per launch of kernel class `kernel` (variant `variant`) from
     the committed ncu record, or None when the record is of another variant or
@@ -448,13 +492,25 @@ def gpu_arm(args, rank, world, dist):
     variant = {"plane": choices[0]["plane"], "yderiv": choices[0]["ygemm"], "helm": choices[0]["helm"]}.get(dom, "simt")
     traffic = (profiled_traffic(dom, variant)
                if (precision == "mixed" and args.workload == "poiseuille64") else None)
+    # every class against the HBM roofline of its own algorithmic bytes (the
+    # event pass runs the kernels one at a time)
+    hpk, hsrc = hbm_peak()
+    per_class = {}
+    for cls, (ms, nl) in kt.items():
+        b = sum(kernel_bytes(cls, g, precision) for g in groups) * 3 * n_timed
+        if b <= 0 or ms <= 0:
+            continue
+        gbs = b / (ms / 1e3) / 1e9
+        per_class[cls] = {"ms_per_launch": ms / max(1, nl), "algorithmic_bytes_per_launch": b / max(1, nl),
+                          "achieved_gbs": gbs, "frac_of_hbm": gbs / hpk}
     roofline = {"kernel": dom, "bound": bound, "precision": kprec, "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
                 "traffic_unit": "DRAM bytes per launch (ncu, profiles/)",
                 "peak_source": ("nominal GB300 FP64" if kprec == "f64" else
                                 "152 SM x 128 FP32 lanes x 2 x median sampled SM clock %.0f MHz" % sm_mhz),
                 "kernel_ms_per_launch": avg_ms,
-                "shares": {k: round(v, 4) for k, v in shares.items()}}
+                "shares": {k: round(v, 4) for k, v in shares.items()},
+                "hbm_view": {"peak_gbs": hpk, "peak_source": hsrc, "classes": per_class}}
 
     # end to end through the C ABI with host buffers: upload state, step, download state
     pins, outs = [], []
