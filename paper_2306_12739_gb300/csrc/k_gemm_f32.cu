@@ -25,8 +25,9 @@ struct Tile {
 };
 
 // Up to 64 complex columns per tile (32 for tall operators), halved down to 16
-// while the grid would hold fewer than three CTAs per SM (152 SMs) and a tile
-// still spans several modes (member runs are not split).
+// while the grid would hold fewer than three CTAs per SM (152 SMs): first fewer
+// modes per tile, then, for large member counts with few modes (linear groups),
+// shorter member runs (never below 16 members: 128-byte runs of the H layout).
 __host__ __device__ inline Tile tile_of(int E, int ny, int nm) {
     int cap = ny <= 96 ? 64 : 32;
     Tile t;
@@ -36,7 +37,7 @@ __host__ __device__ inline Tile tile_of(int E, int ny, int nm) {
         if (t.QT < 1) t.QT = 1;
         t.NC = t.QT * t.EBT;
         const long long ctas = (long long)((nm + t.QT - 1) / t.QT) * ((E + t.EBT - 1) / t.EBT);
-        if (cap <= 16 || ctas >= 3 * 152 || t.QT < 2) break;
+        if (cap <= 16 || ctas >= 3 * 152) break;
         cap /= 2;
     }
     return t;
