@@ -353,7 +353,9 @@ print(json.dumps(dict(seconds=dt, steps={steps}, members=E)))
 
 def run_oracle(g, members, steps, warm=0, wl=None):
     env = dict(os.environ)
-    for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS_STEP", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
+    # the timed steps run on one core (BLAS pinned to one thread, numpy's FFT is
+    # single-threaded); only the untimed quad-precision operator build uses OpenMP
+    for k in ("OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
         env[k] = "1"
     if g.get("linear"):
         bw = wl["base"]
@@ -389,7 +391,12 @@ def reference_arm(args, rank, world):
     if rank != 0:
         return
     g = WORKLOAD
-    out = run_oracle(g, g["members"], args.steps, warm=args.warmup)
+    # each step a bounded sample of the workload: one member (the oracle advances
+    # members independently, so member-steps/s does not depend on how many it
+    # holds), at most 200 timed steps after at most 3 warm-up steps -- about a
+    # minute of single-core numpy at 64x65x64, whatever --steps says
+    n_steps, n_warm = max(1, min(args.steps, 200)), min(args.warmup, 3)
+    out = run_oracle(g, 1, n_steps, warm=n_warm)
     value = out["members"] * out["steps"] / out["seconds"]
     model, ncpu = cpu_info()
     line = {
@@ -399,8 +406,9 @@ def reference_arm(args, rank, world):
         "data": "synthetic (seeded, dns_synth)",
         "config": {"workload": WORKLOAD_NAME, "precision": "fp64", "l2": "n/a (CPU)"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": "%d steps x %d members of the workload (after %d warm-up steps), cpu %s, %d cores on host"
-                                   % (out["steps"], out["members"], args.warmup, model, ncpu)},
+                         "sample": "%d steps x %d member of the workload (after %d warm-up steps; the run's --steps %d "
+                                   "capped at 200), cpu %s, %d cores on host"
+                                   % (out["steps"], out["members"], n_warm, args.steps, model, ncpu)},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
