@@ -73,6 +73,25 @@ def test_config2_fp64_matches_oracle_few_steps():
         assert rel(a, b) < 1e-12, (name, rel(a, b))
 
 
+def test_config2_fp64_sampled_member_matches_oracle_over_100_steps():
+    """Full-size 64x65x64 Poiseuille ensemble (8 members) advanced 100 steps by
+    the FP64 path in the benchmark's launch configuration (CUDA graph, member
+    blocks); the oracle follows one sampled member (members are independent: the
+    GPU ran it inside the whole ensemble)."""
+    st = _state(CFG2, 2000, 5e-2, n_max=4, m_max=4)
+    ens = dns.Ensemble([CFG2], precision="fp64", use_graph=True)
+    try:
+        ens.set_state(0, st["v"], st["eta"], st["U"], st["W"])
+        ens.step(100)
+        got = ens.get_state(0)
+    finally:
+        ens.close()
+    e = 5
+    ref = _oracle(CFG2).step(tuple(st[k][e:e + 1] for k in FIELDS), 100)
+    for a, b, name in zip(got, ref, FIELDS):
+        assert rel(a[e:e + 1], b) < 1e-11, (name, rel(a[e:e + 1], b))
+
+
 def mixed_errors(mixed, ref):
     """Relative errors of the mixed step against the FP64 step, per member:
     v and eta each against their own maximum; the mean flow (U00, W00) as one
