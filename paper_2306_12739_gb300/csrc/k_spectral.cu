@@ -211,7 +211,10 @@ void launch_mean_finish(const GroupView& g, int s, cudaStream_t st) {
 
 // --------------------------------------------------------------------- helm
 
-__global__ void __launch_bounds__(256) k_helm(GroupView g, int s) {
+// stage: the pair's two operators are copied to shared memory (they fit up to
+// Ny = 120); above that every CTA reads them from global memory, where the
+// 2 npairs x 2 operators stay L2-resident across the CTAs of the launch.
+__global__ void __launch_bounds__(256) k_helm(GroupView g, int s, bool stage) {
     extern __shared__ __align__(16) unsigned char sm[];
     const int Ny = g.ny, E = g.E, NKX = g.nkx;
     // leading CTAs: rows of the mean-flow update
@@ -230,14 +233,20 @@ __global__ void __launch_bounds__(256) k_helm(GroupView g, int s) {
     const size_t nn = (size_t)Ny * Ny;
     const double* Mg = g.ops[hi] + ((size_t)p * 4 + (f == 0 ? 0 : 2)) * nn;
     const double* Pg = Mg + nn;
-    double* Ms = (double*)sm;
-    double* Ps = Ms + nn;
     const bool needM = (s != 2);
-    for (size_t i = threadIdx.x; i < nn; i += blockDim.x) {
-        if (needM) Ms[i] = Mg[i];
-        Ps[i] = Pg[i];
+    const double* Ms = Mg;
+    const double* Ps = Pg;
+    if (stage) {
+        double* ms = (double*)sm;
+        double* ps = ms + nn;
+        for (size_t i = threadIdx.x; i < nn; i += blockDim.x) {
+            if (needM) ms[i] = Mg[i];
+            ps[i] = Pg[i];
+        }
+        __syncthreads();
+        Ms = ms;
+        Ps = ps;
     }
-    __syncthreads();
     const int nq = am > 0 ? 2 : 1;
     const int q1 = (g.kz + am) * NKX + n, q2 = (g.kz - am) * NKX + n;
     const double2* X = f == 0 ? g.v_t : g.e_t;
@@ -274,8 +283,10 @@ __global__ void __launch_bounds__(256) k_helm(GroupView g, int s) {
 
 void launch_helm(const GroupView& g, int s, cudaStream_t st) {
     size_t smem = 2 * (size_t)g.ny * g.ny * sizeof(double);
+    const bool stage = smem <= 227 * 1024;
+    if (!stage) smem = 0;
     if (smem < mean_smem_bytes(g)) smem = mean_smem_bytes(g);
-    k_helm<<<mean_row_ctas(g) + 2 * g.npairs * helm_member_chunks(g), 256, smem, st>>>(g, s);
+    k_helm<<<mean_row_ctas(g) + 2 * g.npairs * helm_member_chunks(g), 256, smem, st>>>(g, s, stage);
 }
 
 

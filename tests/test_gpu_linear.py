@@ -49,7 +49,7 @@ def _case(my, mz, lz, n, E, seed, flow="couette"):
 
 @pytest.mark.parametrize("my,mz,n,E,flow", [(33, 32, 1, 3, "couette"), (25, 16, 2, 2, "poiseuille"),
                                             (49, 48, 3, 4, "couette"), (65, 64, 1, 3, "poiseuille"),
-                                            (21, 128, 2, 2, "couette")])
+                                            (21, 128, 2, 2, "couette"), (129, 16, 1, 2, "couette")])
 def test_linear_fp64_forward_and_adjoint_steps_match_the_oracle(my, mz, n, E, flow):
     lz, re, dt = np.pi, 1000.0, 0.02
     b, d = _case(my, mz, lz, n, E, 7, flow)

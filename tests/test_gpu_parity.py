@@ -92,6 +92,21 @@ def test_config2_fp64_sampled_member_matches_oracle_over_100_steps():
         assert rel(a[e:e + 1], b) < 1e-11, (name, rel(a[e:e + 1], b))
 
 
+@pytest.mark.parametrize("flow,mx,mz", [("couette", 16, 16), ("poiseuille", 32, 16)])
+def test_maximum_wall_normal_resolution_matches_oracle(flow, mx, mz):
+    """My = 129, the largest Chebyshev grid a group accepts (operators 127 x 127;
+    the tensor-core kernels stop at 66, so the mixed path runs the register-
+    tiled ones): FP64 vs the oracle, mixed vs FP64."""
+    g = group(flow, mx, 129, mz, 2 * np.pi, np.pi, 1000.0, 0.002, 2)
+    st = _state(g, 77, 2e-2)
+    ref = _oracle(g).step(tuple(st[k] for k in FIELDS), 2)
+    got = _run(g, st, 2)
+    for a, b, name in zip(got, ref, FIELDS):
+        assert rel(a, b) < 1e-11, (name, rel(a, b))
+    err = mixed_errors(_run(g, st, 2, "mixed"), got)
+    assert np.all(err[:, :3] < 1e-6), err
+
+
 def mixed_errors(mixed, ref):
     """Relative errors of the mixed step against the FP64 step, per member:
     v and eta each against their own maximum; the mean flow (U00, W00) as one
