@@ -107,6 +107,23 @@ def test_maximum_wall_normal_resolution_matches_oracle(flow, mx, mz):
     assert np.all(err[:, :3] < 1e-6), err
 
 
+@pytest.mark.parametrize("flow,my", [("couette", 5), ("poiseuille", 5), ("poiseuille", 7)])
+def test_minimum_wall_normal_resolution_matches_oracle(flow, my):
+    """My = 5 (three interior nodes, the smallest grid a group accepts) and 7:
+    FP64 vs the oracle, then every y-contraction / implicit-apply pair of the
+    mixed path (tensor-core tiles padded far beyond Ny) vs FP64."""
+    g = group(flow, 32, my, 16, 2 * np.pi, np.pi, 500.0, 0.01, 3)
+    st = _state(g, 91, 2e-2)
+    ref = _oracle(g).step(tuple(st[k] for k in FIELDS), 3)
+    got = _run(g, st, 3)
+    for a, b, name in zip(got, ref, FIELDS):
+        assert rel(a, b) < 1e-11, (name, rel(a, b))
+    for ygemm in ("simt", "tc"):
+        for helm in ("simt", "tc"):
+            err = mixed_errors(_run(g, st, 3, "mixed", ygemm=ygemm, helm=helm), got)
+            assert np.all(err[:, :3] < 1e-6), (ygemm, helm, err)
+
+
 def mixed_errors(mixed, ref):
     """Relative errors of the mixed step against the FP64 step, per member:
     v and eta each against their own maximum; the mean flow (U00, W00) as one
