@@ -531,17 +531,19 @@ def gpu_arm(args, rank, world, dist):
     h2d = sum(p.numel() * 8 for pin in pins for p in pin if p is not None)
     d2h = sum(o.numel() * 8 for out in outs for o in out if o is not None)
     ptr = lambda t: t.data_ptr() if t is not None else None
-    e2e_steps = max(1, min(args.steps, 10))
+    e2e_steps = max(1, min(args.steps, 50))
+    ins_p = [tuple(ptr(p) for p in pin) for pin in pins]
+    outs_p = [tuple(ptr(o) for o in out) for out in outs]
+    for _ in range(max(3, args.warmup)):   # the first call captures the member blocks' step graphs
+        dns.dns_advance(ens.h, 1, ins_p, outs_p, 0)
     torch.cuda.synchronize()
     if dist is not None:
         dist.barrier()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        for gi, g in enumerate(groups):
-            dns.dns_set_state(ens.h, gi, 0, g["members"], *[ptr(p) for p in pins[gi]], 0)
-        dns.dns_step(ens.h, 1)
-        for gi, g in enumerate(groups):
-            dns.dns_get_state(ens.h, gi, 0, g["members"], *[ptr(o) for o in outs[gi]], 0)
+        # one call per step: upload every group from page-locked memory, one
+        # step, download (member blocks overlap transfers with computation)
+        dns.dns_advance(ens.h, 1, ins_p, outs_p, 0)
     e2e_s = time.perf_counter() - t0
     e2e_s = reduce_max(e2e_s, dist, dev)
     e2e_value = aggregate(members * e2e_steps, e2e_s, world)

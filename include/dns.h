@@ -198,14 +198,57 @@ int dns_state_shape(const dns_handle* h, int group, int* n_kx, int* n_kz, int* n
  * part in m, x(0,m) := (x(0,m) + conj x(0,-m))/2 (the only part a real field
  * carries), and the (0,0) entries are zeroed (DNS groups; a linear group's
  * single column is stored as given).  Host pointers are read before
- * the call returns.  Errors: DNS_ERR_INVALID (range, NULL), DNS_ERR_CUDA. */
+ * the call returns.
+ * Transfer path: device buffers, and page-locked host buffers mapped into the
+ * device's address space (cudaHostAlloc / pinned tensors; both ends of each
+ * buffer are checked with cudaPointerGetAttributes), are read by the packing
+ * kernel itself when v_hat, eta_hat are 16-byte and U00, W00 8-byte aligned:
+ * one pass over the CPU-GPU link, no staging copy.  Pageable or less aligned
+ * buffers are first copied into a device staging buffer.  Device buffers must
+ * hold the whole range (count members), as for a copy.
+ * Errors: DNS_ERR_INVALID (range, NULL, ptr_kind), DNS_ERR_CUDA. */
 int dns_set_state(dns_handle* h, int group, int member0, int count,
                   const double* v_hat, const double* eta_hat,
                   const double* U00, const double* W00, int ptr_kind);
 
-/* Copy members out (same layout).  Synchronises the stream. */
+/* Copy members out (same layout; the same transfer paths, the unpacking
+ * kernel writing device or mapped page-locked host buffers itself).  Any of
+ * the four destinations may be NULL (not wanted).  Synchronises the stream. */
 int dns_get_state(const dns_handle* h, int group, int member0, int count,
                   double* v_hat, double* eta_hat, double* U00, double* W00, int ptr_kind);
+
+/* One group's whole state (all members), layouts as for dns_set_state /
+ * dns_get_state.  In dns_state_out any pointer may be NULL (not wanted); U00
+ * and W00 are not read for a linear group. */
+typedef struct {
+    const double* v_hat;
+    const double* eta_hat;
+    const double* U00;
+    const double* W00;
+} dns_state_in;
+typedef struct {
+    double* v_hat;
+    double* eta_hat;
+    double* U00;
+    double* W00;
+} dns_state_out;
+
+/* Upload, advance and download in one call: every group's state is replaced by
+ * in[group] (in == NULL: keep the current state), nsteps CN/RK3 steps run, and
+ * the result is written to out[group] (out == NULL: nothing is read back).
+ * Same results, bit for bit, as dns_set_state for every group, dns_step and
+ * dns_get_state for every group; the difference is scheduling.  When every
+ * buffer takes the direct path (device memory, mapped page-locked host memory;
+ * see dns_set_state) each member block uploads, steps and downloads on its own
+ * stream, the uploads one after another, so the link transfers of one block
+ * overlap the computation of the others; with use_graph and nsteps <= 16 the
+ * whole call is one CUDA graph, kept for the next call with the same buffers
+ * and nsteps.  Otherwise (staged buffers, longer runs) it runs the uploads, the
+ * steps and the downloads in sequence.  ptr_kind as for dns_set_state.
+ * Synchronises the stream; host buffers may be reused when it returns.
+ * Errors: DNS_ERR_INVALID (not bound, nsteps < 0, NULL inputs, ptr_kind),
+ * DNS_ERR_CUDA, and the device status codes of dns_get_state. */
+int dns_advance(dns_handle* h, int nsteps, const dns_state_in* in, const dns_state_out* out, int ptr_kind);
 
 /* Enqueue nsteps full CN/RK3 steps of every group on the handle's stream. */
 int dns_step(dns_handle* h, int nsteps);

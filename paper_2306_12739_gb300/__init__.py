@@ -36,7 +36,7 @@ EXPORTED = ["dns_create", "dns_workspace_size", "dns_bind_workspace", "dns_state
             "dns_last_error", "dns_last_launch_count", "dns_export_grid", "dns_export_operators",
             "dns_step_timed", "dns_stats_noalloc", "dns_selftest_timeout", "dns_kernel_choice",
             "dns_convert_selftest", "dns_set_base_flow", "dns_set_direction", "dns_orthonormalize",
-            "dns_optimal_sweep", "dns_set_stochastic_forcing", "dns_export_forcing"]
+            "dns_optimal_sweep", "dns_set_stochastic_forcing", "dns_export_forcing", "dns_advance"]
 KERNEL_CLASSES = ["mean_deriv", "yderiv", "plane", "forcing", "helm", "mean"]
 
 
@@ -61,6 +61,16 @@ class dns_stats_t(ctypes.Structure):
                 ("max_div", ctypes.c_double), ("nonfinite", ctypes.c_int), ("reserved", ctypes.c_int)]
 
 
+class dns_state_in(ctypes.Structure):
+    _fields_ = [("v_hat", ctypes.c_void_p), ("eta_hat", ctypes.c_void_p), ("U00", ctypes.c_void_p),
+                ("W00", ctypes.c_void_p)]
+
+
+class dns_state_out(ctypes.Structure):
+    _fields_ = [("v_hat", ctypes.c_void_p), ("eta_hat", ctypes.c_void_p), ("U00", ctypes.c_void_p),
+                ("W00", ctypes.c_void_p)]
+
+
 _H = ctypes.c_void_p
 _dp = ctypes.POINTER(ctypes.c_double)
 _vp = ctypes.c_void_p
@@ -72,6 +82,8 @@ _lib.dns_state_shape.argtypes = [_H, ctypes.c_int] + [ctypes.POINTER(ctypes.c_in
 _lib.dns_set_state.argtypes = [_H, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp, ctypes.c_int]
 _lib.dns_get_state.argtypes = [_H, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp, ctypes.c_int]
 _lib.dns_step.argtypes = [_H, ctypes.c_int]
+_lib.dns_advance.argtypes = [_H, ctypes.c_int, ctypes.POINTER(dns_state_in), ctypes.POINTER(dns_state_out),
+                             ctypes.c_int]
 _lib.dns_stats.argtypes = [_H, ctypes.c_int, ctypes.POINTER(dns_stats_t), ctypes.POINTER(dns_stats_t), _dp]
 _lib.dns_destroy.argtypes = [_H]
 _lib.dns_last_error.argtypes = [_H]
@@ -146,6 +158,14 @@ def dns_get_state(h, group, member0, count, v, eta, U, W, ptr_kind):
 
 def dns_step(h, nsteps):
     return _ck(h, _lib.dns_step(h, nsteps))
+
+
+def dns_advance(h, nsteps, ins, outs, ptr_kind):
+    """ins, outs: one (v, eta, U, W) tuple of raw addresses (or None) per group,
+    or None for the whole argument (no upload / no download)."""
+    pin = (dns_state_in * len(ins))(*[dns_state_in(*a) for a in ins]) if ins is not None else None
+    pout = (dns_state_out * len(outs))(*[dns_state_out(*a) for a in outs]) if outs is not None else None
+    return _ck(h, _lib.dns_advance(h, nsteps, pin, pout, ptr_kind))
 
 
 def dns_step_timed(h, nsteps):
@@ -363,6 +383,27 @@ class Ensemble:
 
     def step(self, nsteps=1):
         dns_step(self.h, nsteps)
+
+    def advance(self, nsteps, states):
+        """Replace every group's state by states[group] = (v, eta, U, W) (host
+        numpy arrays, U and W None for a linear group), advance nsteps steps and
+        return the new states, in one dns_advance call."""
+        ins, outs, res = [], [], []
+        for gi, st in enumerate(states):
+            nkx, nkz, ny, my = self.shapes[gi]
+            E = self.groups[gi]["members"]
+            v = np.ascontiguousarray(np.reshape(st[0], (E, ny, nkz, nkx)), dtype=np.complex128)
+            e = np.ascontiguousarray(np.reshape(st[1], (E, ny, nkz, nkx)), dtype=np.complex128)
+            U = None if st[2] is None else np.ascontiguousarray(st[2], dtype=np.float64)
+            W = None if st[3] is None else np.ascontiguousarray(st[3], dtype=np.float64)
+            o = (np.zeros_like(v), np.zeros_like(e), np.zeros((E, my)), np.zeros((E, my)))
+            ins.append((v, e, U, W))
+            res.append(o)
+            outs.append(o)
+        addr = lambda a: a.ctypes.data if a is not None else None
+        dns_advance(self.h, nsteps, [tuple(addr(a) for a in t) for t in ins],
+                    [tuple(addr(a) for a in t) for t in outs], 0)
+        return res
 
     def set_stochastic_forcing(self, group, kx_index, n_eig, rate, seed):
         dns_set_stochastic_forcing(self.h, group, kx_index, n_eig, rate, seed)

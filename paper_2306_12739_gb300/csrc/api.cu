@@ -9,6 +9,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <functional>
@@ -35,6 +36,7 @@ struct HostGroup {
     // of every step and joined before the first forcing assembly
     cudaStream_t nstream = nullptr;
     cudaEvent_t nfork = nullptr, njoin = nullptr;
+    cudaEvent_t uploaded = nullptr;   // this block's input is on the device (dns_advance)
 
     // byte offsets inside the workspace
     struct Off { size_t off, bytes; };
@@ -66,7 +68,16 @@ struct dns_handle {
     std::vector<cudaStream_t> gstreams;
     std::vector<cudaEvent_t> gevents;
     cudaEvent_t fork_ev = nullptr;
+    // dns_advance as one graph, for the buffers and step count in akey
+    cudaGraph_t agraph = nullptr;
+    cudaGraphExec_t aexec = nullptr;
+    std::vector<uintptr_t> akey;
+    int alaunches = 0;
+    int* hstatus = nullptr;   // page-locked copies of the groups' status words
 };
+
+// dns_advance calls of at most this many steps are captured whole
+constexpr int ADVANCE_GRAPH_STEPS = 16;
 
 namespace {
 
@@ -183,6 +194,30 @@ int device_status(dns_handle* h) {
         if (st != 0) {
             cudaMemset(G.v.status, 0, sizeof(int));
             return fail(h, DNS_ERR_TIMEOUT, "a bounded device wait gave up (status %d)", st);
+        }
+    }
+    return DNS_OK;
+}
+
+// The same check folded into a call's own synchronisation: the status words
+// are copied into page-locked memory on stream st before it synchronises
+// (one host round trip instead of one per member block), checked after.
+int sync_with_status(dns_handle* h, cudaStream_t st, const char* what) {
+    int rc;
+    if (!h->hstatus &&
+        (rc = check(h, cudaHostAlloc((void**)&h->hstatus, sizeof(int) * h->groups.size(), cudaHostAllocDefault),
+                    "status buffer")))
+        return rc;
+    for (size_t ig = 0; ig < h->groups.size(); ++ig)
+        if ((rc = check(h, cudaMemcpyAsync(h->hstatus + ig, h->groups[ig].v.status, sizeof(int), cudaMemcpyDeviceToHost,
+                                           st), "read status")))
+            return rc;
+    if ((rc = check(h, cudaStreamSynchronize(st), what))) return rc;
+    for (size_t ig = 0; ig < h->groups.size(); ++ig) {
+        const int sv = h->hstatus[ig];
+        if (sv != 0) {
+            cudaMemset(h->groups[ig].v.status, 0, sizeof(int));
+            return fail(h, DNS_ERR_TIMEOUT, "a bounded device wait gave up (status %d)", sv);
         }
     }
     return DNS_OK;
@@ -632,14 +667,23 @@ int dns_workspace_size(const dns_handle* h, size_t* bytes) {
     return DNS_OK;
 }
 
+// Captured graphs hold the group views (workspace pointers, forcing set-up):
+// every change of those drops them, and the next step captures anew.
+static void drop_graphs(dns_handle* h) {
+    if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
+    if (h->graph) { cudaGraphDestroy(h->graph); h->graph = nullptr; }
+    if (h->aexec) { cudaGraphExecDestroy(h->aexec); h->aexec = nullptr; }
+    if (h->agraph) { cudaGraphDestroy(h->agraph); h->agraph = nullptr; }
+    h->akey.clear();
+}
+
 int dns_bind_workspace(dns_handle* h, void* dev_ptr, size_t bytes) {
     if (!h) return DNS_ERR_INVALID;
     if (!dev_ptr || ((uintptr_t)dev_ptr & 255)) return fail(h, DNS_ERR_INVALID, "workspace NULL or not 256-byte aligned");
     if (bytes < h->need) return fail(h, DNS_ERR_NOMEM, "workspace has %zu bytes, needs %zu", bytes, h->need);
     h->ws = (char*)dev_ptr;
     h->ws_bytes = bytes;
-    if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
-    if (h->graph) { cudaGraphDestroy(h->graph); h->graph = nullptr; }
+    drop_graphs(h);
     if (h->groups.size() > 1 && h->gstreams.empty()) {
         int rc0 = check(h, cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming), "fork event");
         if (rc0) return rc0;
@@ -840,16 +884,47 @@ int dns_state_shape(const dns_handle* h, int group, int* n_kx, int* n_kz, int* n
     return DNS_OK;
 }
 
+// True when the whole host range [p, p + bytes) is page-locked memory mapped
+// into the device's address space at the same address (unified addressing), so
+// that a kernel may read or write it directly.  Both ends of the range are
+// checked; anything else (pageable memory, a mapping at another address) takes
+// the staged path.
+static bool host_mapped(const void* p, size_t bytes) {
+    if (!p || bytes == 0) return false;
+    const char* c = (const char*)p;
+    const char* ends[2] = {c, c + bytes - 1};
+    for (const char* q : ends) {
+        cudaPointerAttributes a;
+        if (cudaPointerGetAttributes(&a, q) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        if (a.type != cudaMemoryTypeHost || a.devicePointer != (const void*)q) return false;
+    }
+    return true;
+}
+
+// The pack and unpack kernels move v, eta as 16-byte complex values and U, W as
+// doubles: a caller's buffer is accessed by them only when so aligned.
+static bool aligned_for_kernels(const void* v, const void* e, const void* U, const void* W) {
+    return ((uintptr_t)v % 16) == 0 && ((uintptr_t)e % 16) == 0 && ((uintptr_t)U % 8) == 0 && ((uintptr_t)W % 8) == 0;
+}
+
+// direct: the sources are device memory or mapped host memory and the pack
+// kernel reads them itself; otherwise they are copied (kind k) into the staging
+// buffer (v, eta) and the profile rows (U, W) first.
 static int set_state_block(dns_handle* h, int group, int member0, int count, const double* v_hat,
-                  const double* eta_hat, const double* U00, const double* W00, int ptr_kind) {
+                           const double* eta_hat, const double* U00, const double* W00, bool direct,
+                           cudaMemcpyKind k, cudaStream_t st) {
     GroupView& v = h->groups[group].v;
     if (member0 < 0 || count < 1 || member0 + count > v.E) return fail(h, DNS_ERR_INVALID, "member range");
-    if (!v_hat || !eta_hat || (!v.lin && (!U00 || !W00))) return fail(h, DNS_ERR_INVALID, "NULL state pointer");
-    if (ptr_kind != 0 && ptr_kind != 1) return fail(h, DNS_ERR_INVALID, "ptr_kind must be 0 or 1");
-    cudaMemcpyKind k = ptr_kind ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    const size_t per = (size_t)count * v.ny * v.nmodes;
-    cudaStream_t st = h->stream;
     int rc;
+    if (direct) {
+        dnsk::launch_pack(v, member0, count, (const double2*)v_hat, (const double2*)eta_hat, v.lin ? nullptr : U00,
+                          v.lin ? nullptr : W00, st);
+        return check(h, cudaGetLastError(), "pack state");
+    }
+    const size_t per = (size_t)count * v.ny * v.nmodes;
     if ((rc = check(h, cudaMemcpyAsync(v.stage, v_hat, per * sizeof(double2), k, st), "set v"))) return rc;
     if ((rc = check(h, cudaMemcpyAsync(v.stage + per, eta_hat, per * sizeof(double2), k, st), "set eta"))) return rc;
     if (!v.lin) {   // a linear group has no mean profiles (they stay zero)
@@ -860,7 +935,7 @@ static int set_state_block(dns_handle* h, int group, int member0, int count, con
                         "set W")))
             return rc;
     }
-    dnsk::launch_pack(v, member0, count, st);
+    dnsk::launch_pack(v, member0, count, v.stage, v.stage + per, nullptr, nullptr, st);
     return check(h, cudaGetLastError(), "pack state");
 }
 
@@ -869,36 +944,42 @@ int dns_set_state(dns_handle* h, int group, int member0, int count, const double
     if (!h) return DNS_ERR_INVALID;
     if (!h->bound) return fail(h, DNS_ERR_INVALID, "workspace not bound");
     if (group < 0 || group >= (int)h->parts.size()) return fail(h, DNS_ERR_INVALID, "bad group");
+    if (ptr_kind != 0 && ptr_kind != 1) return fail(h, DNS_ERR_INVALID, "ptr_kind must be 0 or 1");
     const int E = h->descs[group].members;
     if (member0 < 0 || count < 1 || member0 + count > E) return fail(h, DNS_ERR_INVALID, "member range");
     const GroupView& v0 = h->groups[h->parts[group][0].ig].v;
     if (!v_hat || !eta_hat || (!v0.lin && (!U00 || !W00))) return fail(h, DNS_ERR_INVALID, "NULL state pointer");
     const size_t pm = (size_t)v0.ny * v0.nmodes * 2, pu = (size_t)v0.my;   // doubles per member
+    const size_t bv = sizeof(double) * pm * count, bu = sizeof(double) * pu * count;
+    const bool direct = aligned_for_kernels(v_hat, eta_hat, U00, W00) &&
+                        (ptr_kind == 1 || (host_mapped(v_hat, bv) && host_mapped(eta_hat, bv) &&
+                                           (v0.lin || (host_mapped(U00, bu) && host_mapped(W00, bu)))));
+    const cudaMemcpyKind k = ptr_kind ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     for (const auto& P : h->parts[group]) {
         const int lo = member0 > P.m0 ? member0 : P.m0;
         const int hi = (member0 + count) < (P.m0 + P.E) ? (member0 + count) : (P.m0 + P.E);
         if (lo >= hi) continue;
         const size_t o = (size_t)(lo - member0);
         int rc = set_state_block(h, P.ig, lo - P.m0, hi - lo, v_hat + o * pm, eta_hat + o * pm,
-                                 U00 ? U00 + o * pu : nullptr, W00 ? W00 + o * pu : nullptr, ptr_kind);
+                                 U00 ? U00 + o * pu : nullptr, W00 ? W00 + o * pu : nullptr, direct, k, h->stream);
         if (rc) return rc;
     }
-    // host buffers may be pageable and reused by the caller right away: one
-    // synchronisation after every block's copies
+    // host buffers may be reused by the caller as soon as the call returns: one
+    // synchronisation after every block's copies (or direct reads)
     if (ptr_kind == 0) return check(h, cudaStreamSynchronize(h->stream), "set state");
     return DNS_OK;
 }
 
-static int get_state_block(const dns_handle* hc, int group, int member0, int count, double* v_hat,
-                  double* eta_hat, double* U00, double* W00, int ptr_kind) {
-    dns_handle* h = const_cast<dns_handle*>(hc);
+static int get_state_block(dns_handle* h, int group, int member0, int count, double* v_hat, double* eta_hat,
+                           double* U00, double* W00, bool direct, cudaMemcpyKind k, cudaStream_t st) {
     GroupView& v = h->groups[group].v;
     if (member0 < 0 || count < 1 || member0 + count > v.E) return fail(h, DNS_ERR_INVALID, "member range");
-    if (ptr_kind != 0 && ptr_kind != 1) return fail(h, DNS_ERR_INVALID, "ptr_kind must be 0 or 1");
-    cudaMemcpyKind k = ptr_kind ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (direct) {
+        dnsk::launch_unpack(v, member0, count, (double2*)v_hat, (double2*)eta_hat, U00, W00, st);
+        return check(h, cudaGetLastError(), "unpack state");
+    }
     const size_t per = (size_t)count * v.ny * v.nmodes;
-    cudaStream_t st = h->stream;
-    dnsk::launch_unpack(v, member0, count, st);
+    dnsk::launch_unpack(v, member0, count, v.stage, v.stage + per, nullptr, nullptr, st);
     int rc;
     if ((rc = check(h, cudaGetLastError(), "unpack state"))) return rc;
     if (v_hat && (rc = check(h, cudaMemcpyAsync(v_hat, v.stage, per * sizeof(double2), k, st), "get v"))) return rc;
@@ -919,10 +1000,16 @@ int dns_get_state(const dns_handle* hc, int group, int member0, int count, doubl
     if (!h) return DNS_ERR_INVALID;
     if (!h->bound) return fail(h, DNS_ERR_INVALID, "workspace not bound");
     if (group < 0 || group >= (int)h->parts.size()) return fail(h, DNS_ERR_INVALID, "bad group");
+    if (ptr_kind != 0 && ptr_kind != 1) return fail(h, DNS_ERR_INVALID, "ptr_kind must be 0 or 1");
     const int E = h->descs[group].members;
     if (member0 < 0 || count < 1 || member0 + count > E) return fail(h, DNS_ERR_INVALID, "member range");
     const GroupView& v0 = h->groups[h->parts[group][0].ig].v;
     const size_t pm = (size_t)v0.ny * v0.nmodes * 2, pu = (size_t)v0.my;
+    const size_t bv = sizeof(double) * pm * count, bu = sizeof(double) * pu * count;
+    const bool direct = aligned_for_kernels(v_hat, eta_hat, U00, W00) &&
+                        (ptr_kind == 1 || ((!v_hat || host_mapped(v_hat, bv)) && (!eta_hat || host_mapped(eta_hat, bv)) &&
+                                           (!U00 || host_mapped(U00, bu)) && (!W00 || host_mapped(W00, bu))));
+    const cudaMemcpyKind k = ptr_kind ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     for (const auto& P : h->parts[group]) {
         const int lo = member0 > P.m0 ? member0 : P.m0;
         const int hi = (member0 + count) < (P.m0 + P.E) ? (member0 + count) : (P.m0 + P.E);
@@ -930,20 +1017,17 @@ int dns_get_state(const dns_handle* hc, int group, int member0, int count, doubl
         const size_t o = (size_t)(lo - member0);
         int rc = get_state_block(h, P.ig, lo - P.m0, hi - lo, v_hat ? v_hat + o * pm : nullptr,
                                  eta_hat ? eta_hat + o * pm : nullptr, U00 ? U00 + o * pu : nullptr,
-                                 W00 ? W00 + o * pu : nullptr, ptr_kind);
+                                 W00 ? W00 + o * pu : nullptr, direct, k, h->stream);
         if (rc) return rc;
     }
     // one synchronisation after every block's unpack and copies
-    int rc = check(h, cudaStreamSynchronize(h->stream), "get state");
-    if (rc) return rc;
-    return device_status(h);
+    return sync_with_status(h, h->stream, "get state");
 }
 
-int dns_step(dns_handle* h, int nsteps) {
-    if (!h) return DNS_ERR_INVALID;
-    if (!h->bound) return fail(h, DNS_ERR_INVALID, "workspace not bound");
-    if (nsteps < 0) return fail(h, DNS_ERR_INVALID, "nsteps < 0");
-    h->launches = 0;
+// nsteps steps of every group on the handle's stream: the captured step graph
+// (captured on first use) or the kernels enqueued directly; adds the launches
+// to h->launches.
+static int run_steps(dns_handle* h, int nsteps) {
     int rc;
     if (h->cfg.use_graph) {
         if (h->stream == nullptr)
@@ -958,7 +1042,7 @@ int dns_step(dns_handle* h, int nsteps) {
             h->graph = gr;
             if ((rc = check(h, cudaGraphInstantiate(&h->gexec, gr, 0), "instantiate graph"))) return rc;
             h->graph_launches = h->launches - before;
-            h->launches = 0;
+            h->launches = before;
         }
         for (int i = 0; i < nsteps; ++i) {
             if ((rc = check(h, cudaGraphLaunch(h->gexec, h->stream), "graph launch"))) return rc;
@@ -968,6 +1052,177 @@ int dns_step(dns_handle* h, int nsteps) {
         for (int i = 0; i < nsteps; ++i) enqueue_step(h);
     }
     return check(h, cudaGetLastError(), "step launch");
+}
+
+int dns_step(dns_handle* h, int nsteps) {
+    if (!h) return DNS_ERR_INVALID;
+    if (!h->bound) return fail(h, DNS_ERR_INVALID, "workspace not bound");
+    if (nsteps < 0) return fail(h, DNS_ERR_INVALID, "nsteps < 0");
+    h->launches = 0;
+    return run_steps(h, nsteps);
+}
+
+// Upload, nsteps steps and download.  With direct transfers (device or mapped
+// page-locked buffers) every member block runs on its own stream (pack, its
+// sub-step kernels, unpack), the uploads one after another so that the first
+// block computes while the next one's input is still crossing the link, and a
+// block's download overlaps the blocks still computing; in graph mode the
+// whole call is one captured graph, kept for the next call with the same
+// buffers and step count.  Staged transfers (pageable memory, which a graph
+// cannot hold) and long runs take the plain sequence: uploads, the step graph,
+// downloads.  Per block the kernels and their order are those of
+// dns_set_state + dns_step + dns_get_state, so the results are bitwise the same.
+int dns_advance(dns_handle* h, int nsteps, const dns_state_in* in, const dns_state_out* out, int ptr_kind) {
+    if (!h) return DNS_ERR_INVALID;
+    if (!h->bound) return fail(h, DNS_ERR_INVALID, "workspace not bound");
+    if (nsteps < 0) return fail(h, DNS_ERR_INVALID, "nsteps < 0");
+    if (ptr_kind != 0 && ptr_kind != 1) return fail(h, DNS_ERR_INVALID, "ptr_kind must be 0 or 1");
+    const bool graph = h->cfg.use_graph != 0;
+    if (graph && h->stream == nullptr)
+        return fail(h, DNS_ERR_INVALID, "graph capture needs a non-default stream (got the legacy NULL stream)");
+    const int ng = (int)h->parts.size();
+    std::vector<char> din(ng, 0), dout(ng, 0);   // transfer path per group: direct or staged
+    for (int gi = 0; gi < ng; ++gi) {
+        const GroupView& v0 = h->groups[h->parts[gi][0].ig].v;
+        const size_t E = (size_t)h->descs[gi].members;
+        const size_t bv = sizeof(double) * 2 * (size_t)v0.ny * v0.nmodes * E, bu = sizeof(double) * v0.my * E;
+        if (in) {
+            const dns_state_in& I = in[gi];
+            if (!I.v_hat || !I.eta_hat || (!v0.lin && (!I.U00 || !I.W00)))
+                return fail(h, DNS_ERR_INVALID, "group %d: NULL input pointer", gi);
+            const double* U = v0.lin ? nullptr : I.U00;
+            const double* W = v0.lin ? nullptr : I.W00;
+            din[gi] = aligned_for_kernels(I.v_hat, I.eta_hat, U, W) &&
+                      (ptr_kind == 1 || (host_mapped(I.v_hat, bv) && host_mapped(I.eta_hat, bv) &&
+                                         (v0.lin || (host_mapped(U, bu) && host_mapped(W, bu)))));
+        }
+        if (out) {
+            const dns_state_out& O = out[gi];
+            dout[gi] = aligned_for_kernels(O.v_hat, O.eta_hat, O.U00, O.W00) &&
+                       (ptr_kind == 1 || ((!O.v_hat || host_mapped(O.v_hat, bv)) &&
+                                          (!O.eta_hat || host_mapped(O.eta_hat, bv)) &&
+                                          (!O.U00 || host_mapped(O.U00, bu)) && (!O.W00 || host_mapped(O.W00, bu))));
+        }
+    }
+    const bool multi = h->groups.size() > 1 && !h->gstreams.empty();
+    auto bstream = [&](int ig) { return multi ? h->gstreams[ig] : h->stream; };
+    int rc;
+    for (auto& G : h->groups)
+        if (!G.uploaded &&
+            (rc = check(h, cudaEventCreateWithFlags(&G.uploaded, cudaEventDisableTiming), "upload event")))
+            return rc;
+    const cudaMemcpyKind kin = ptr_kind ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    const cudaMemcpyKind kout = ptr_kind ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    // Fork, per block: upload (after the previous block's), nsteps steps,
+    // download; join.
+    auto enqueue_advance = [&]() -> int {
+        int r;
+        if (multi) cudaEventRecord(h->fork_ev, h->stream);
+        cudaEvent_t prev_upload = nullptr;
+        for (int gi = 0; gi < ng; ++gi) {
+            const GroupView& v0 = h->groups[h->parts[gi][0].ig].v;
+            const size_t pm = (size_t)v0.ny * v0.nmodes * 2, pu = (size_t)v0.my;
+            for (const auto& P : h->parts[gi]) {
+                HostGroup& G = h->groups[P.ig];
+                cudaStream_t sb = bstream(P.ig);
+                const size_t o = (size_t)P.m0;
+                if (multi) cudaStreamWaitEvent(sb, h->fork_ev, 0);
+                if (in) {
+                    const dns_state_in& I = in[gi];
+                    if (prev_upload) cudaStreamWaitEvent(sb, prev_upload, 0);   // one upload at a time
+                    if ((r = set_state_block(h, P.ig, 0, P.E, I.v_hat + o * pm, I.eta_hat + o * pm,
+                                             I.U00 ? I.U00 + o * pu : nullptr, I.W00 ? I.W00 + o * pu : nullptr,
+                                             din[gi] != 0, kin, sb)))
+                        return r;
+                    cudaEventRecord(G.uploaded, sb);
+                    prev_upload = G.uploaded;
+                    h->launches += 1;
+                }
+                for (int i = 0; i < nsteps; ++i) enqueue_group(h, G, sb, nullptr);
+                if (out) {
+                    const dns_state_out& O = out[gi];
+                    if ((r = get_state_block(h, P.ig, 0, P.E, O.v_hat ? O.v_hat + o * pm : nullptr,
+                                             O.eta_hat ? O.eta_hat + o * pm : nullptr,
+                                             O.U00 ? O.U00 + o * pu : nullptr, O.W00 ? O.W00 + o * pu : nullptr,
+                                             dout[gi] != 0, kout, sb)))
+                        return r;
+                    h->launches += 1;
+                }
+                if (multi) cudaEventRecord(h->gevents[P.ig], sb);
+            }
+        }
+        if (multi)
+            for (size_t ig = 0; ig < h->groups.size(); ++ig) cudaStreamWaitEvent(h->stream, h->gevents[ig], 0);
+        return DNS_OK;
+    };
+    bool all_direct = true;
+    for (int gi = 0; gi < ng; ++gi) all_direct = all_direct && (!in || din[gi]) && (!out || dout[gi]);
+    if (graph && all_direct && nsteps <= ADVANCE_GRAPH_STEPS) {
+        // the whole call as one graph (one submission: every block starts at
+        // once), kept for the next call with the same buffers and step count
+        std::vector<uintptr_t> key = {(uintptr_t)nsteps, (uintptr_t)ptr_kind, (uintptr_t)(in != nullptr),
+                                      (uintptr_t)(out != nullptr)};
+        for (int gi = 0; gi < ng; ++gi) {
+            if (in) for (const void* q : {in[gi].v_hat, in[gi].eta_hat, in[gi].U00, in[gi].W00}) key.push_back((uintptr_t)q);
+            if (out) for (const void* q : {out[gi].v_hat, out[gi].eta_hat, out[gi].U00, out[gi].W00}) key.push_back((uintptr_t)q);
+        }
+        if (!h->aexec || key != h->akey) {
+            if (h->aexec) { cudaGraphExecDestroy(h->aexec); h->aexec = nullptr; }
+            if (h->agraph) { cudaGraphDestroy(h->agraph); h->agraph = nullptr; }
+            h->launches = 0;
+            if ((rc = check(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal), "begin capture")))
+                return rc;
+            int rc_enq = enqueue_advance();
+            cudaGraph_t gr = nullptr;
+            rc = check(h, cudaStreamEndCapture(h->stream, &gr), "end capture");
+            if (rc_enq) { if (gr) cudaGraphDestroy(gr); return rc_enq; }
+            if (rc) return rc;
+            h->agraph = gr;
+            if ((rc = check(h, cudaGraphInstantiate(&h->aexec, gr, 0), "instantiate advance graph"))) return rc;
+            h->akey = key;
+            h->alaunches = h->launches;
+        }
+        if ((rc = check(h, cudaGraphLaunch(h->aexec, h->stream), "advance graph launch"))) return rc;
+        h->launches = h->alaunches;
+    } else if (!graph) {
+        h->launches = 0;
+        if ((rc = enqueue_advance())) return rc;
+    } else {
+        // staged transfers (pageable memory cannot be captured) or many steps:
+        // uploads, the step graph, downloads, one after another on the stream
+        h->launches = 0;
+        for (int gi = 0; gi < ng; ++gi) {
+            const GroupView& v0 = h->groups[h->parts[gi][0].ig].v;
+            const size_t pm = (size_t)v0.ny * v0.nmodes * 2, pu = (size_t)v0.my;
+            for (const auto& P : h->parts[gi]) {
+                if (!in) break;
+                const dns_state_in& I = in[gi];
+                const size_t o = (size_t)P.m0;
+                if ((rc = set_state_block(h, P.ig, 0, P.E, I.v_hat + o * pm, I.eta_hat + o * pm,
+                                          I.U00 ? I.U00 + o * pu : nullptr, I.W00 ? I.W00 + o * pu : nullptr,
+                                          din[gi] != 0, kin, h->stream)))
+                    return rc;
+                h->launches += 1;
+            }
+        }
+        if ((rc = run_steps(h, nsteps))) return rc;
+        for (int gi = 0; gi < ng; ++gi) {
+            const GroupView& v0 = h->groups[h->parts[gi][0].ig].v;
+            const size_t pm = (size_t)v0.ny * v0.nmodes * 2, pu = (size_t)v0.my;
+            for (const auto& P : h->parts[gi]) {
+                if (!out) break;
+                const dns_state_out& O = out[gi];
+                const size_t o = (size_t)P.m0;
+                if ((rc = get_state_block(h, P.ig, 0, P.E, O.v_hat ? O.v_hat + o * pm : nullptr,
+                                          O.eta_hat ? O.eta_hat + o * pm : nullptr, O.U00 ? O.U00 + o * pu : nullptr,
+                                          O.W00 ? O.W00 + o * pu : nullptr, dout[gi] != 0, kout, h->stream)))
+                    return rc;
+                h->launches += 1;
+            }
+        }
+    }
+    if ((rc = check(h, cudaGetLastError(), "advance launch"))) return rc;
+    return sync_with_status(h, h->stream, "advance");
 }
 
 int dns_step_timed(dns_handle* h, int nsteps, double* ms, int* launches) {
@@ -1008,8 +1263,7 @@ static int stats_block(dns_handle* h, int group, dns_stats_t* per_member, double
         (rc = check(h, cudaMemcpyAsync(profiles, v.prof, sizeof(double) * (size_t)v.E * 6 * v.my, cudaMemcpyDeviceToHost, st),
                     "profile copy")))
         return rc;
-    if ((rc = check(h, cudaStreamSynchronize(st), "stats"))) return rc;
-    if ((rc = device_status(h))) return rc;
+    if ((rc = sync_with_status(h, st, "stats"))) return rc;
     for (int e = 0; e < v.E; ++e) {
         dns_stats_t& s = per_member[e];
         const double* o = &out[(size_t)e * 8];
@@ -1203,8 +1457,7 @@ int dns_orthonormalize(dns_handle* h, int group, double* norms) {
     if ((rc = check(h, cudaMemcpyAsync(norms, G->v.gsr, sizeof(double) * G->v.E, cudaMemcpyDeviceToHost, h->stream),
                     "read norms")))
         return rc;
-    if ((rc = check(h, cudaStreamSynchronize(h->stream), "orthonormalize"))) return rc;
-    return device_status(h);
+    return sync_with_status(h, h->stream, "orthonormalize");
 }
 
 int dns_optimal_sweep(dns_handle* h, int nsteps, double* gains) {
@@ -1235,8 +1488,7 @@ int dns_optimal_sweep(dns_handle* h, int nsteps, double* gains) {
             return rc;
         off += G.v.E;
     }
-    if ((rc = check(h, cudaStreamSynchronize(h->stream), "optimal sweep"))) return rc;
-    return device_status(h);
+    return sync_with_status(h, h->stream, "optimal sweep");
 }
 
 // ---- stochastic forcing
@@ -1372,8 +1624,7 @@ int dns_set_stochastic_forcing(dns_handle* h, int group, int kx_index, int n_eig
             return rc;
     }
     // a captured step graph holds the previous group views
-    if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
-    if (h->graph) { cudaGraphDestroy(h->graph); h->graph = nullptr; }
+    drop_graphs(h);
     return check(h, cudaStreamSynchronize(h->stream), "set stochastic forcing");
 }
 
@@ -1396,8 +1647,7 @@ int dns_selftest_timeout(dns_handle* h) {
     dnsk::launch_wait_selftest(h->groups[0].v.status, h->stream);
     int rc = check(h, cudaGetLastError(), "selftest launch");
     if (rc) return rc;
-    if ((rc = check(h, cudaStreamSynchronize(h->stream), "selftest"))) return rc;
-    return device_status(h);
+    return sync_with_status(h, h->stream, "selftest");
 }
 
 int dns_convert_selftest(const double* d_in, float* f_out, const float* f_in, double* d_out, long long n) {
@@ -1419,10 +1669,10 @@ int dns_convert_selftest(const double* d_in, float* f_out, const float* f_in, do
 int dns_destroy(dns_handle* h) {
     if (!h) return DNS_ERR_INVALID;
     if (h->bound) cudaStreamSynchronize(h->stream);
-    if (h->gexec) cudaGraphExecDestroy(h->gexec);
-    if (h->graph) cudaGraphDestroy(h->graph);
+    drop_graphs(h);
     for (auto s2 : h->gstreams) cudaStreamDestroy(s2);
     for (auto& G : h->groups) {
+        if (G.uploaded) cudaEventDestroy(G.uploaded);
         if (G.nstream) cudaStreamDestroy(G.nstream);
         if (G.nfork) cudaEventDestroy(G.nfork);
         if (G.njoin) cudaEventDestroy(G.njoin);
@@ -1430,6 +1680,7 @@ int dns_destroy(dns_handle* h) {
 
     for (auto e2 : h->gevents) cudaEventDestroy(e2);
     if (h->fork_ev) cudaEventDestroy(h->fork_ev);
+    if (h->hstatus) cudaFreeHost(h->hstatus);
     delete h;
     return DNS_OK;
 }

@@ -147,8 +147,10 @@ size_t plane_cl_smem_bytes(int mx, int mz, bool fp64);
 void set_attributes_plane_cl();
 void launch_stats(const GroupView& g, cudaStream_t st);
 void launch_shared_mean(const GroupView& g, bool fp64, cudaStream_t st);
-void launch_pack(const GroupView& g, int member0, int count, cudaStream_t st);
-void launch_unpack(const GroupView& g, int member0, int count, cudaStream_t st);
+void launch_pack(const GroupView& g, int member0, int count, const double2* sv, const double2* se, const double* sU,
+                 const double* sW, cudaStream_t st);
+void launch_unpack(const GroupView& g, int member0, int count, double2* dv, double2* de, double* dU, double* dW,
+                   cudaStream_t st);
 size_t plane_smem_bytes(const GroupView& g, int elem_bytes);
 bool launch_plane_f32(const GroupView& g, const double* U, const double* W, cudaStream_t st);
 size_t plane_f32_smem_bytes(int mx, int mz);

@@ -422,22 +422,31 @@ void launch_stats(const GroupView& g, cudaStream_t st) {
 
 // --------------------------------------------------------------- pack/unpack
 
-// stage: v then eta, each [count][Ny][NKZ][NKX] complex (host layout)
-__global__ void k_pack(GroupView g, int member0, int count) {
+// Host layout -> H layout.  sv, se: v and eta, each [count][Ny][NKZ][NKX]
+// complex; sU, sW: [count][My] (nullptr: the profiles were copied separately).
+// The sources are device memory, the host-layout staging buffer, or page-locked
+// host memory mapped into the device's address space (read over the CPU-GPU
+// link; no intermediate copy).
+constexpr int TRANSFER_BOUND = 64;   // threads per CTA of the transfer kernels (at most)
+__global__ void __launch_bounds__(TRANSFER_BOUND) k_pack(GroupView g, int member0, int count,
+                                                         const double2* __restrict__ sv,
+                                                         const double2* __restrict__ se, const double* __restrict__ sU,
+                                                         const double* __restrict__ sW) {
     const int Ny = g.ny, E = g.E, nmodes = g.nmodes, NKX = g.nkx, NKZ = g.nkz;
     const size_t per = (size_t)count * Ny * nmodes;
     const int q_mean = mean_mode(g);
-    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < per; idx += (size_t)gridDim.x * blockDim.x) {
+    const size_t t0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x, nt = (size_t)gridDim.x * blockDim.x;
+    for (size_t idx = t0; idx < per; idx += nt) {
         int q = (int)(idx % nmodes);
         int y = (int)((idx / nmodes) % Ny);
         int el = (int)(idx / ((size_t)nmodes * Ny));
         int mi = q / NKX, n = q - mi * NKX;
-        double2 a = g.stage[idx], b = g.stage[per + idx];
+        double2 a = sv[idx], b = se[idx];
         if (n == 0 && !g.lin) {
             // Hermitian part of the n = 0 column: (x(m) + conj x(-m)) / 2
             int qp = (NKZ - 1 - mi) * NKX;
             size_t ip = ((size_t)el * Ny + y) * nmodes + qp;
-            double2 ap = g.stage[ip], bp = g.stage[per + ip];
+            double2 ap = sv[ip], bp = se[ip];
             a = make_double2(0.5 * (a.x + ap.x), 0.5 * (a.y - ap.y));
             b = make_double2(0.5 * (b.x + bp.x), 0.5 * (b.y - bp.y));
         }
@@ -446,26 +455,63 @@ __global__ void k_pack(GroupView g, int member0, int count) {
         g.v_t[h] = a;
         g.e_t[h] = b;
     }
+    if (sU) {
+        const size_t nu = (size_t)count * g.my, o = (size_t)member0 * g.my;
+        for (size_t i = t0; i < nu; i += nt) {
+            g.U_t[o + i] = sU[i];
+            g.W_t[o + i] = sW[i];
+        }
+    }
 }
 
-__global__ void k_unpack(GroupView g, int member0, int count) {
+// H layout -> host layout, into device memory, the staging buffer or mapped
+// page-locked host memory (written over the CPU-GPU link).  Any destination may
+// be nullptr (not wanted).
+__global__ void __launch_bounds__(TRANSFER_BOUND) k_unpack(GroupView g, int member0, int count,
+                                                           double2* __restrict__ dv, double2* __restrict__ de,
+                         double* __restrict__ dU, double* __restrict__ dW) {
     const int Ny = g.ny, E = g.E, nmodes = g.nmodes;
     const size_t per = (size_t)count * Ny * nmodes;
-    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < per; idx += (size_t)gridDim.x * blockDim.x) {
+    const size_t t0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x, nt = (size_t)gridDim.x * blockDim.x;
+    for (size_t idx = t0; idx < per; idx += nt) {
         int q = (int)(idx % nmodes);
         int y = (int)((idx / nmodes) % Ny);
         int el = (int)(idx / ((size_t)nmodes * Ny));
         size_t h = ((size_t)q * Ny + y) * E + member0 + el;
-        g.stage[idx] = g.v_t[h];
-        g.stage[per + idx] = g.e_t[h];
+        if (dv) dv[idx] = g.v_t[h];
+        if (de) de[idx] = g.e_t[h];
+    }
+    const size_t nu = (size_t)count * g.my, o = (size_t)member0 * g.my;
+    for (size_t i = t0; i < nu; i += nt) {
+        if (dU) dU[i] = g.U_t[o + i];
+        if (dW) dW[i] = g.W_t[o + i];
     }
 }
 
-void launch_pack(const GroupView& g, int member0, int count, cudaStream_t st) {
-    k_pack<<<1024, 256, 0, st>>>(g, member0, count);
+// Small CTAs, three per SM: about 0.9 MB of reads in flight keeps the CPU-GPU
+// link busy (a larger grid moves the data no faster), and CTAs of 64 threads x
+// 32 registers still fit beside the step kernels of the member blocks that
+// compute meanwhile (a line-owned plane CTA leaves 7936 of the SM's 65536
+// registers: room for three; three implicit-apply CTAs leave 4096: two).
+constexpr int TRANSFER_THREADS = TRANSFER_BOUND;
+static int transfer_ctas() {
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        n = 3 * (sms > 0 ? sms : 1);
+    }
+    return n;
 }
-void launch_unpack(const GroupView& g, int member0, int count, cudaStream_t st) {
-    k_unpack<<<1024, 256, 0, st>>>(g, member0, count);
+
+void launch_pack(const GroupView& g, int member0, int count, const double2* sv, const double2* se, const double* sU,
+                 const double* sW, cudaStream_t st) {
+    k_pack<<<transfer_ctas(), TRANSFER_THREADS, 0, st>>>(g, member0, count, sv, se, sU, sW);
+}
+void launch_unpack(const GroupView& g, int member0, int count, double2* dv, double2* de, double* dU, double* dW,
+                   cudaStream_t st) {
+    k_unpack<<<transfer_ctas(), TRANSFER_THREADS, 0, st>>>(g, member0, count, dv, de, dU, dW);
 }
 
 void set_attributes_spectral() {
