@@ -577,7 +577,8 @@ def gpu_arm(args, rank, world, dist):
                    "l2": "flushed (256 MiB write) before every timed step", "parallelism": "replicas x%d" % world},
         "grid_pts_steps_per_s": aggregate(pts * args.steps, total_ms / 1e3, world),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "steps": e2e_steps},
+                "steps": e2e_steps,
+                "call": "dns_advance per step: upload from page-locked host memory, one step, download"},
         "gpu_launches": launches,
         "clocks": clocks,
         "roofline": roofline,
