@@ -338,6 +338,42 @@ def test_divergence_free_and_hermitian(couette_small):
         assert np.abs(col - np.conj(col[:, :, ::-1])).max() < 1e-15 * np.abs(col).max() + 1e-300
 
 
+@pytest.mark.parametrize("flow,mx,my,mz", [("couette", 16, 33, 16), ("poiseuille", 12, 17, 20)])
+def test_statistics_equal_physical_space_averages(flow, mx, my, mz):
+    """The one-point statistics (Sec. 4) are spectral sums (Parseval, each
+    kx > 0 column counted twice for its conjugate); here the same quantities
+    are formed the plain way, from the velocity on the physical grid (a library
+    inverse FFT): <u'u'>, <v'v'>, <w'w'>, <u'v'> as x-z averages of products of
+    the fluctuations about the x-z mean, and the kinetic energies as the
+    Clenshaw-Curtis average over y of 1/2 |u|^2 (the wall nodes carry only the
+    mean flow)."""
+    lx, lz = 2 * np.pi, np.pi
+    ch = oracle.Channel(mx, my, mz, lx, lz, 500.0, 0.01, flow)
+    x = ch.step(_state(dns_synth.make_state(mx, my, mz, lx, lz, flow, 2, 321, 1e-1)), 2)
+    s = ch.stats(x)
+    f = ch.velocity(*x)
+    phys = {k: ch.to_physical(f[k]) for k in ("u", "v", "w")}        # [e, y, z, x]
+    mean = {k: p.mean(axis=(-2, -1)) for k, p in phys.items()}
+    assert np.abs(mean["u"] - x[2]).max() < 1e-15 and np.abs(mean["w"] - x[3]).max() < 1e-15
+    assert np.abs(mean["v"]).max() < 1e-17
+    fl = {k: p - mean[k][..., None, None] for k, p in phys.items()}
+    scale = max(np.abs(fl[k]).max() for k in fl) ** 2
+    for key, (a, b) in {"uu": ("u", "u"), "vv": ("v", "v"), "ww": ("w", "w"), "uv": ("u", "v")}.items():
+        direct = (fl[a] * fl[b]).mean(axis=(-2, -1))
+        direct[:, 0] = 0.0
+        direct[:, -1] = 0.0
+        assert np.abs(s[key] - direct).max() < 1e-13 * scale, key
+        assert np.abs(direct).max() > 1e-3 * scale, key    # the check is not vacuous
+    w = oracle.cc_weights(my)
+    q = sum(fl[k] ** 2 for k in fl).mean(axis=(-2, -1))
+    q[:, 0] = 0.0
+    q[:, -1] = 0.0
+    e_pert = 0.25 * (q @ w)
+    e_mean = 0.25 * ((mean["u"] ** 2 + mean["w"] ** 2) @ w)
+    assert np.allclose(s["e_pert"], e_pert, rtol=1e-12, atol=0)
+    assert np.allclose(s["e_total"], e_pert + e_mean, rtol=1e-13, atol=0)
+
+
 def test_poiseuille_flux_constant_under_perturbation():
     ch = oracle.Channel(16, 33, 16, 2 * np.pi, np.pi, 1650.0, 0.005, "poiseuille")
     x = _state(dns_synth.make_state(16, 33, 16, 2 * np.pi, np.pi, "poiseuille", 2, 2000, 5e-2,
