@@ -24,7 +24,11 @@ Readings of the paper where it is silent or garbled (each also in the design not
     phi = i kx Nu + i kz Nw needs them;
   * the Poiseuille pressure gradient gamma is chosen at every sub-step so that
     the Clenshaw-Curtis integral of U00 equals the prescribed bulk flux;
-  * transform convention: forward = sum / (Mx Mz), inverse unnormalised.
+  * transform convention: forward = sum / (Mx Mz), inverse unnormalised;
+  * CFL number (the paper steps at fixed dt and defines none): dt times the
+    maximum over the interior collocation points (the Mx x Mz grid of every
+    interior plane) of |u|/dx + |v|/dy_j + |w|/dz, mean flow included, with
+    dx = Lx/Mx, dz = Lz/Mz and dy_j the smaller of the node's two gaps.
 """
 import ctypes
 import numpy as np
@@ -339,7 +343,8 @@ class Channel:
     def stats(self, state):
         """One-point statistics per member (Sec. 4): volume-averaged kinetic
         energy (total and without the mean mode), wall shear dU/dy at both walls,
-        bulk flux, max |div u| and profiles U, W, <u'u'>, <v'v'>, <w'w'>, <u'v'>."""
+        bulk flux, max |div u|, the CFL number and profiles U, W, <u'u'>,
+        <v'v'>, <w'w'>, <u'v'>."""
         v, eta, U, W = state
         f = self.velocity(v, eta, U, W)
         cn = np.where(np.arange(self.Kx + 1) == 0, 1.0, 2.0)[None, None, None, :]
@@ -369,6 +374,14 @@ class Channel:
         # work done by the moving walls (Couette) per unit volume:
         # (1/(2 Re)) [U dU/dy]_{y=-1}^{y=+1}
         wall_work = (U[:, -1] * dU[:, -1] - U[:, 0] * dU[:, 0]) / (2.0 * self.re)
+        # CFL number (reading in the module header): velocity on the interior
+        # collocation points by the library inverse transform
+        yn = self.y
+        dy = np.minimum(yn[1:-1] - yn[:-2], yn[2:] - yn[1:-1])
+        up, vp, wp = (self.to_physical(f[k][:, 1:-1]) for k in ("u", "v", "w"))   # [e, y, z, x]
+        rate = (np.abs(up) * (self.mx / self.lx) + np.abs(vp) / dy[None, :, None, None]
+                + np.abs(wp) * (self.mz / self.lz))
+        cfl = self.dt * rate.max(axis=(1, 2, 3))
         div = 1j * self.kx[None, None, None, :] * f["u"] + f["vy"] + 1j * self.kz[None, None, :, None] * f["w"]
         div[:, :, self.Kz, 0] = 0.0
         return {
@@ -376,6 +389,6 @@ class Channel:
             "tau_bottom": dU[:, 0], "tau_top": dU[:, -1],
             "bulk_flux": U @ self.w,
             "max_div": np.max(np.abs(div[:, 1:-1]), axis=(1, 2, 3)),
-            "dissipation": dissipation, "wall_work": wall_work,
+            "dissipation": dissipation, "wall_work": wall_work, "cfl": cfl,
             "U": U, "W": W, "uu": uu, "vv": vv, "ww": ww, "uv": uv,
         }

@@ -374,6 +374,55 @@ def test_statistics_equal_physical_space_averages(flow, mx, my, mz):
     assert np.allclose(s["e_total"], e_pert + e_mean, rtol=1e-13, atol=0)
 
 
+def test_cfl_of_laminar_profiles_is_the_closed_form():
+    """Laminar flows carry only U(y): the CFL number (reading: dt max of
+    |u|/dx + |v|/dy + |w|/dz over the interior collocation points) is
+    dt max_j |U(y_j)| Mx / Lx over the interior nodes."""
+    for flow, prof in (("couette", lambda y: y), ("poiseuille", lambda y: 1.0 - y ** 2)):
+        for my in (17, 32):
+            mx, mz, lx, lz, dt = 16, 12, 1.75 * np.pi, 1.2 * np.pi, 0.01
+            ch = oracle.Channel(mx, my, mz, lx, lz, 400.0, dt, flow)
+            x = _state(dns_synth.make_state(mx, my, mz, lx, lz, flow, 1, 0, 0.0))
+            y = oracle.grid(my)[0]
+            want = dt * np.abs(prof(y[1:-1])).max() * mx / lx
+            assert abs(ch.stats(x)["cfl"][0] - want) < 1e-14 * want, (flow, my)
+
+
+def test_cfl_equals_brute_force_fourier_sums():
+    """CFL number of a random state against the velocity summed mode by mode in
+    real form, f(x, z) = sum_m Re c(0, m) e^(i kz z) + 2 sum_(n >= 1) sum_m
+    Re c(n, m) e^(i (kx x + kz z)), at every interior collocation point."""
+    mx, my, mz, lx, lz, dt = 10, 9, 13, 2 * np.pi, np.pi, 0.02
+    ch = oracle.Channel(mx, my, mz, lx, lz, 300.0, dt, "poiseuille")
+    x = ch.step(_state(dns_synth.make_state(mx, my, mz, lx, lz, "poiseuille", 2, 77, 2e-1)), 1)
+    f = ch.velocity(*x)
+    Kx, Kz = (mx - 1) // 3, (mz - 1) // 3
+    xs = np.arange(mx) * lx / mx
+    zs = np.arange(mz) * lz / mz
+    y = oracle.grid(my)[0]
+    dy = [min(y[j] - y[j - 1], y[j + 1] - y[j]) for j in range(1, my - 1)]
+    want = np.zeros(2)
+    for e in range(2):
+        for j in range(1, my - 1):
+            for iz, z in enumerate(zs):
+                for ix, xx in enumerate(xs):
+                    vals = []
+                    for k in ("u", "v", "w"):
+                        tot = 0.0
+                        for mi in range(2 * Kz + 1):
+                            for n in range(Kx + 1):
+                                c = f[k][e, j, mi, n]
+                                ph = 2 * np.pi * (n * xx / lx + (mi - Kz) * z / lz)
+                                term = c.real * np.cos(ph) - c.imag * np.sin(ph)
+                                tot += term if n == 0 else 2.0 * term
+                        vals.append(abs(tot))
+                    r = vals[0] * mx / lx + vals[1] / dy[j - 1] + vals[2] * mz / lz
+                    want[e] = max(want[e], dt * r)
+    got = ch.stats(x)["cfl"]
+    assert np.allclose(got, want, rtol=1e-12, atol=0)
+    assert np.all(want > 2 * dt * mx / lx)   # the perturbation dominates the laminar dt Mx / Lx
+
+
 def test_poiseuille_flux_constant_under_perturbation():
     ch = oracle.Channel(16, 33, 16, 2 * np.pi, np.pi, 1650.0, 0.005, "poiseuille")
     x = _state(dns_synth.make_state(16, 33, 16, 2 * np.pi, np.pi, "poiseuille", 2, 2000, 5e-2,
