@@ -159,11 +159,19 @@ typedef struct {
  *   bulk_flux  int_{-1}^{1} U00 dy (Clenshaw-Curtis)
  *   gamma      Poiseuille pressure gradient of the last sub-step (0 for Couette)
  *   max_div    max over interior nodes and modes of |i kx u + dv/dy + i kz w|
- *   nonfinite  1 if any value of this member's state is NaN or Inf       */
+ *   nonfinite  1 if any value of this member's state is NaN or Inf
+ *   cfl        CFL number: dt times the maximum over the interior collocation
+ *              points (the Mx x Mz grid of every interior plane) of
+ *              |u|/dx + |v|/dy_j + |w|/dz, mean flow included, dx = Lx/Mx,
+ *              dz = Lz/Mz, dy_j the smaller gap from node j to a neighbour
+ *              (the velocity synthesised in single precision: about 1e-6
+ *              relative); 0 for a linear group (disturbances of arbitrary
+ *              amplitude)                                                    */
 typedef struct {
     double e_total, e_pert, tau_bottom, tau_top, bulk_flux, gamma, max_div;
     int nonfinite;
     int reserved;
+    double cfl;
 } dns_stats_t;
 
 typedef struct dns_handle dns_handle;
@@ -255,7 +263,8 @@ int dns_step(dns_handle* h, int nsteps);
 
 /* Statistics of every member of `group` at the current time (synchronises).
  * per_member: [members] (required); ensemble_mean: arithmetic mean over the
- * group's members (optional); profiles: optional host array
+ * group's members, except max_div and cfl (the largest over the members) and
+ * nonfinite (any member) (optional); profiles: optional host array
  * [members][6][My] holding U00, W00, <u'u'>, <v'v'>, <w'w'>, <u'v'> (plane
  * averages; the perturbation parts vanish on the walls).
  * Returns DNS_ERR_NONFINITE (after filling the outputs) when any member of the

@@ -58,7 +58,8 @@ class dns_config(ctypes.Structure):
 class dns_stats_t(ctypes.Structure):
     _fields_ = [("e_total", ctypes.c_double), ("e_pert", ctypes.c_double), ("tau_bottom", ctypes.c_double),
                 ("tau_top", ctypes.c_double), ("bulk_flux", ctypes.c_double), ("gamma", ctypes.c_double),
-                ("max_div", ctypes.c_double), ("nonfinite", ctypes.c_int), ("reserved", ctypes.c_int)]
+                ("max_div", ctypes.c_double), ("nonfinite", ctypes.c_int), ("reserved", ctypes.c_int),
+                ("cfl", ctypes.c_double)]
 
 
 class dns_state_in(ctypes.Structure):

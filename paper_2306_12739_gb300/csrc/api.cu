@@ -171,7 +171,8 @@ size_t layout_group(dns_handle* h, HostGroup& G, size_t cur) {
     add(&v.N3, elem * 3 * S);
     if (precision_mixed(h)) add((void**)&v.P5d, sizeof(double2) * 5 * S);
     add((void**)&v.st_y, sizeof(double) * (size_t)v.E * v.ny * 6);
-    add((void**)&v.st_out, sizeof(double) * (size_t)v.E * 8);
+    add((void**)&v.st_out, sizeof(double) * (size_t)v.E * 9);
+    add((void**)&v.cfl_y, sizeof(double) * (size_t)v.E * v.ny);
     add((void**)&v.prof, sizeof(double) * (size_t)v.E * 6 * v.my);
     add((void**)&v.stage, sizeof(double2) * 2 * S);
     return cur;
@@ -560,6 +561,7 @@ int dns_create(const dns_config* cfg, void* cuda_stream, dns_handle** out) {
         if (d.member_block < 0) return fail(h, DNS_ERR_INVALID, "group %d: member_block must be >= 0", gi);
         v.rot = d.nonlinear_form;
         v.re = d.re; v.dt = d.dt; v.u_wall = d.u_wall; v.bulk_flux = d.bulk_flux;
+        v.lx = d.lx; v.lz = d.lz;
         if ((!lin && !make_plan(d.mx, &v.px)) || !make_plan(d.mz, &v.pz))
             return fail(h, DNS_ERR_UNSUPPORTED, "group %d: no radix plan", gi);
         {
@@ -1256,7 +1258,7 @@ static int stats_block(dns_handle* h, int group, dns_stats_t* per_member, double
     dnsk::launch_stats(v, st);
     int rc;
     if ((rc = check(h, cudaGetLastError(), "stats launch"))) return rc;
-    std::vector<double> out((size_t)v.E * 8);
+    std::vector<double> out((size_t)v.E * 9);
     if ((rc = check(h, cudaMemcpyAsync(out.data(), v.st_out, out.size() * 8, cudaMemcpyDeviceToHost, st), "stats copy")))
         return rc;
     if (profiles &&
@@ -1266,10 +1268,11 @@ static int stats_block(dns_handle* h, int group, dns_stats_t* per_member, double
     if ((rc = sync_with_status(h, st, "stats"))) return rc;
     for (int e = 0; e < v.E; ++e) {
         dns_stats_t& s = per_member[e];
-        const double* o = &out[(size_t)e * 8];
+        const double* o = &out[(size_t)e * 9];
         s.e_total = o[0]; s.e_pert = o[1]; s.tau_bottom = o[2]; s.tau_top = o[3];
         s.bulk_flux = o[4]; s.gamma = o[5]; s.max_div = o[6];
         s.nonfinite = o[7] != 0.0 ? 1 : 0;
+        s.cfl = o[8];
         s.reserved = 0;
     }
     return DNS_OK;
@@ -1296,6 +1299,7 @@ int dns_stats(dns_handle* h, int group, dns_stats_t* per_member, dns_stats_t* en
         mean.tau_bottom += s.tau_bottom / E; mean.tau_top += s.tau_top / E;
         mean.bulk_flux += s.bulk_flux / E; mean.gamma += s.gamma / E;
         mean.max_div = mean.max_div > s.max_div ? mean.max_div : s.max_div;
+        mean.cfl = mean.cfl > s.cfl ? mean.cfl : s.cfl;
         mean.nonfinite |= s.nonfinite;
     }
     if (ensemble_mean) *ensemble_mean = mean;

@@ -47,7 +47,7 @@ struct GroupView {
     const double* fbasis; // [NKZ][2][fneig][Ny] right-hand-side terms -Delta f_v, -f_eta
     double2* noise;       // [2][NKZ][Ny][E] this step's F and G terms of the forced column
     unsigned long long* fstep;   // device step counter of the noise
-    double re, dt, u_wall, bulk_flux;
+    double re, dt, u_wall, bulk_flux, lx, lz;
     FftPlan px, pz;
     // constants
     const double* D1;     // [My][My]
@@ -86,7 +86,8 @@ struct GroupView {
     double2* P5d;  // FP64 copy for statistics (== P5 in FP64 mode)
     // statistics
     double* st_y;    // [E][Ny][6]: uu, vv, ww, uv, maxdiv, nonfinite
-    double* st_out;  // [E][8] packed dns_stats_t doubles (+nonfinite as double)
+    double* st_out;  // [E][9] packed dns_stats_t doubles (+nonfinite as double, then the CFL number)
+    double* cfl_y;   // [E][Ny] CFL rate (without dt) of every interior plane
     double* prof;    // [E][6][My]
     double2* stage;  // host-layout staging [E][Ny][nmodes] x 2 fields
 };

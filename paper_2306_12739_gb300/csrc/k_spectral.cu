@@ -330,13 +330,108 @@ __global__ void __launch_bounds__(256) k_stats_plane(GroupView g) {
     }
 }
 
+// CFL rate of one interior plane (y, e), without the factor dt: the maximum over
+// the plane's Mx x Mz collocation points of |u|/dx + |v|/dy + |w|/dz, mean flow
+// included, dy the smaller gap from the node to a neighbour.  u, v, w come from
+// the FP64 spectra of the statistics pass (v, Dv, eta of P5d; u, w by the
+// explicit solutions, Sec. 3.2) and are synthesised on the grid in single
+// precision by direct sums, along z for every kept kx, then along x (the kx = 0
+// column entering by its real part, every other column twice).
+__global__ void __launch_bounds__(256) k_stats_cfl(GroupView g) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    __shared__ float red[32];
+    const int y = blockIdx.x, e = blockIdx.y;
+    const int Ny = g.ny, E = g.E, nmodes = g.nmodes, NKX = g.nkx, NKZ = g.nkz, Kz = g.kz;
+    const int Mx = g.mx, Mz = g.mz, My = g.my, jn = y + 1;
+    float2* c = (float2*)sm;                   // [NKZ][NKX] coefficients of one field
+    float2* s = c + nmodes;                    // [NKX][Mz] after the z sums
+    float2* tz = s + (size_t)NKX * Mz;         // exp(2 pi i k / Mz)
+    float2* tx = tz + Mz;                      // exp(2 pi i k / Mx)
+    float* acc = (float*)(tx + Mx);            // [Mz][Mx] rate of every point
+    for (int k = threadIdx.x; k < Mz; k += blockDim.x) {
+        double sn, cs;
+        sincospi(2.0 * k / Mz, &sn, &cs);
+        tz[k] = make_float2((float)cs, (float)sn);
+    }
+    for (int k = threadIdx.x; k < Mx; k += blockDim.x) {
+        double sn, cs;
+        sincospi(2.0 * k / Mx, &sn, &cs);
+        tx[k] = make_float2((float)cs, (float)sn);
+    }
+    const double yj = -cospi((double)jn / (My - 1));
+    const double dy = fmin(yj + cospi((double)(jn - 1) / (My - 1)), -cospi((double)(jn + 1) / (My - 1)) - yj);
+    const size_t fs = (size_t)Ny * E * nmodes;
+    const double2* P = g.P5d + ((size_t)y * E + e) * nmodes;
+    const int q_mean = mean_mode(g);
+    for (int f = 0; f < 3; ++f) {   // u, v, w
+        const float inv = (float)(f == 0 ? Mx / g.lx : f == 1 ? 1.0 / dy : Mz / g.lz);
+        __syncthreads();   // the previous field's sums are done with c and s
+        for (int q = threadIdx.x; q < nmodes; q += blockDim.x) {
+            double2 val;
+            if (q == q_mean) {
+                val = make_double2(f == 0 ? g.U_t[(size_t)e * My + jn] : f == 2 ? g.W_t[(size_t)e * My + jn] : 0.0,
+                                   0.0);
+            } else if (f == 1) {
+                val = P[q];
+            } else {
+                // u = i (kx Dv - kz eta) / k^2, w = i (kz Dv + kx eta) / k^2
+                const int mi = q / NKX, n = q - mi * NKX;
+                const double kx = g.kxt[n], kz = g.kzt[mi], ki = g.k2inv[q];
+                const double a = f == 0 ? kx : kz, b = f == 0 ? -kz : kx;
+                const double2 dv = P[fs + q], et = P[3 * fs + q];
+                val = make_double2(-(a * dv.y + b * et.y) * ki, (a * dv.x + b * et.x) * ki);
+            }
+            c[q] = make_float2((float)val.x, (float)val.y);
+        }
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < NKX * Mz; idx += blockDim.x) {
+            const int n = idx / Mz, k = idx - n * Mz;
+            float sr = 0.f, si = 0.f;
+            for (int mi = 0; mi < NKZ; ++mi) {
+                int r = ((mi - Kz) * k) % Mz;
+                if (r < 0) r += Mz;
+                const float2 a = c[mi * NKX + n], t = tz[r];
+                sr += a.x * t.x - a.y * t.y;
+                si += a.x * t.y + a.y * t.x;
+            }
+            s[idx] = make_float2(sr, si);
+        }
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < Mz * Mx; idx += blockDim.x) {
+            const int k = idx / Mx, i = idx - k * Mx;
+            float sum = 0.f;
+            for (int n = 1; n < NKX; ++n) {
+                const float2 a = s[n * Mz + k], t = tx[(n * i) % Mx];
+                sum += a.x * t.x - a.y * t.y;
+            }
+            const float r = fabsf(s[k].x + 2.f * sum) * inv;
+            acc[idx] = f == 0 ? r : acc[idx] + r;   // the same thread owns idx for every field
+        }
+    }
+    float mx = 0.f;
+    for (int idx = threadIdx.x; idx < Mz * Mx; idx += blockDim.x) mx = fmaxf(mx, acc[idx]);
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        float v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.f;
+        for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+        if (threadIdx.x == 0) g.cfl_y[(size_t)e * Ny + y] = (double)v;
+    }
+}
+
+size_t stats_cfl_smem_bytes(const GroupView& g) {
+    return sizeof(float2) * ((size_t)g.nmodes + (size_t)g.nkx * g.mz + g.mz + g.mx) +
+           sizeof(float) * (size_t)g.mz * g.mx;
+}
+
 __global__ void k_stats_final(GroupView g) {
     __shared__ double red[32];
     const int e = blockIdx.x, Ny = g.ny, My = g.my;
     const double* U = g.U_t + (size_t)e * My;
     const double* W = g.W_t + (size_t)e * My;
     double* prof = g.prof + (size_t)e * 6 * My;
-    double ep = 0, em = 0, fl = 0, dm = 0, nf = 0;
+    double ep = 0, em = 0, fl = 0, dm = 0, nf = 0, cf = 0;
     for (int j = threadIdx.x; j < My; j += blockDim.x) {
         double uu = 0, vv = 0, ww = 0, uv = 0;
         if (j > 0 && j < My - 1) {
@@ -344,6 +439,7 @@ __global__ void k_stats_final(GroupView g) {
             uu = s[0]; vv = s[1]; ww = s[2]; uv = s[3];
             dm = fmax(dm, s[4]);
             nf = fmax(nf, s[5]);
+            if (!g.lin) cf = fmax(cf, g.cfl_y[(size_t)e * Ny + (j - 1)]);
         }
         if (!isfinite(U[j]) || !isfinite(W[j])) nf = 1.0;
         prof[0 * My + j] = U[j];
@@ -358,14 +454,14 @@ __global__ void k_stats_final(GroupView g) {
         fl += w * U[j];
     }
     ep = block_sum(ep, red); em = block_sum(em, red); fl = block_sum(fl, red);
-    dm = block_max(dm, red); nf = block_max(nf, red);
+    dm = block_max(dm, red); nf = block_max(nf, red); cf = block_max(cf, red);
     if (threadIdx.x == 0) {
         double t0 = 0, t1 = 0;
         for (int j = 0; j < My; ++j) {
             t0 += g.D1[j] * U[j];
             t1 += g.D1[(size_t)(My - 1) * My + j] * U[j];
         }
-        double* o = g.st_out + (size_t)e * 8;
+        double* o = g.st_out + (size_t)e * 9;
         o[0] = 0.25 * (ep + em);
         o[1] = 0.25 * ep;
         o[2] = t0;
@@ -374,6 +470,7 @@ __global__ void k_stats_final(GroupView g) {
         o[5] = g.gamma[e];
         o[6] = dm;
         o[7] = nf;
+        o[8] = cf * g.dt;
     }
 }
 
@@ -417,6 +514,7 @@ void launch_shared_mean(const GroupView& g, bool fp64, cudaStream_t st) {
 void launch_stats(const GroupView& g, cudaStream_t st) {
     launch_yderiv<double>(g, g.v_t, g.e_t, g.P5d, st);
     k_stats_plane<<<dim3(g.ny, g.E), 256, 0, st>>>(g);
+    if (!g.lin) k_stats_cfl<<<dim3(g.ny, g.E), 256, stats_cfl_smem_bytes(g), st>>>(g);
     k_stats_final<<<g.E, 128, 0, st>>>(g);
 }
 
@@ -515,6 +613,7 @@ void launch_unpack(const GroupView& g, int member0, int count, double2* dv, doub
 }
 
 void set_attributes_spectral() {
+    allow_max_dynamic_smem(k_stats_cfl);
     allow_max_dynamic_smem(k_yderiv<double>);
     allow_max_dynamic_smem(k_forcing<double>);
     allow_max_dynamic_smem(k_helm);

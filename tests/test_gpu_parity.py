@@ -209,6 +209,31 @@ def test_stats_match_oracle():
     for k in ("uu", "vv", "ww", "uv"):
         assert rel(s[k], ref[k]) < 1e-12, k
     assert np.all(s["nonfinite"] == 0)
+    # the CFL number's velocity is synthesised in single precision
+    assert np.allclose(s["cfl"], ref["cfl"], rtol=1e-5, atol=0), (s["cfl"], ref["cfl"])
+
+
+@pytest.mark.parametrize("flow,mx,my,mz,precision,E", [("couette", 16, 33, 16, "fp64", 3),
+                                                       ("poiseuille", 48, 21, 16, "mixed", 3),
+                                                       ("poiseuille", 128, 33, 128, "mixed", 3),
+                                                       ("couette", 64, 65, 64, "mixed", 8)])
+def test_cfl_matches_oracle(flow, mx, my, mz, precision, E):
+    """CFL number of every member (dt max of |u|/dx + |v|/dy + |w|/dz over the
+    interior collocation points) against the oracle on ragged and 128-point
+    grids and across two member blocks; the ensemble entry is the largest
+    member's."""
+    g = group(flow, mx, my, mz, 2 * np.pi, np.pi, 1000.0, 0.004, E)
+    st = _state(g, 17, 1e-1)
+    ens = dns.Ensemble([g], precision=precision)
+    try:
+        ens.set_state(0, st["v"], st["eta"], st["U"], st["W"])
+        s = ens.stats(0)
+        rc, per, mean = dns.dns_stats(ens.h, 0, E, 0)
+    finally:
+        ens.close()
+    ref = _oracle(g).stats(tuple(st[k] for k in FIELDS))["cfl"]
+    assert np.allclose(s["cfl"], ref, rtol=1e-5, atol=0), (s["cfl"], ref)
+    assert mean.cfl == max(s["cfl"])
 
 
 def test_nonfinite_member_is_flagged_without_touching_others():
