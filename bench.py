@@ -2,7 +2,7 @@
 """Throughput of the ensemble channel-DNS step on one node.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp64]
-                  [--impl gpu|reference] [--no-cpu-baseline]
+                  [--impl gpu|reference] [--no-cpu-baseline] [--no-cpu-all-cores]
 
 One step = one full CN/RK3 step (three sub-steps: y-derivatives, transforms and
 advective products, forcing + RK combination, per-wavenumber implicit apply,
@@ -351,6 +351,73 @@ print(json.dumps(dict(seconds=dt, steps={steps}, members=E)))
 """
 
 
+# All host cores: the oracle is built once (its operators in OpenMP), then one
+# single-threaded worker per core is forked -- this process never touched CUDA
+# -- and each advances its own member (members are independent); every worker
+# warms up, waits at a barrier, and the rate is all members' steps over the
+# time from the barrier to the last worker's end.
+CPU_SNIPPET_PAR = r"""
+import json, multiprocessing as mp, os, sys, time
+sys.path.insert(0, {root!r})
+import numpy as np
+import dns_synth
+g = {g!r}
+n = {nproc}
+if g.get('linear'):
+    from oracle.linear import Linear
+    b = dns_synth.make_base_flow(g['my'], g['mz'], g['lz'], g['flow'], {bseed}, streak={streak}, roll={roll})
+    ch = Linear(g['my'], g['mz'], g['lx'], g['lz'], g['re'], g['dt'], g['kx_index'], b['U'], b['V'], b['W'])
+    def first(i):
+        d = dns_synth.make_disturbances(g['my'], g['mz'], g['lz'], 1, {seed0} + i)
+        return (d['v'], d['eta'])
+else:
+    import oracle
+    ch = oracle.Channel(g['mx'], g['my'], g['mz'], g['lx'], g['lz'], g['re'], g['dt'], g['flow'],
+                        shared_mean=g.get('shared_mean', False), form=g.get('form', 'advective'))
+    if {forcing!r} is not None:
+        from oracle.forcing import StochasticForcing
+        ch.stochastic = StochasticForcing(ch, *{forcing!r})
+    def first(i):
+        st = dns_synth.make_state(g['mx'], g['my'], g['mz'], g['lx'], g['lz'], g['flow'], 1, {seed0} + i, {amp},
+                                  n_max={n_max}, m_max={m_max})
+        return tuple(st[k] for k in ('v', 'eta', 'U', 'W'))
+ctx = mp.get_context('fork')
+bar = ctx.Barrier(n + 1)
+q = ctx.Queue()
+def work(i):
+    x = ch.step(first(i), 1)
+    bar.wait()
+    for _ in range({steps}):
+        x = ch.step(x, 1)
+    q.put(time.time())
+ps = [ctx.Process(target=work, args=(i,)) for i in range(n)]
+for p in ps:
+    p.start()
+bar.wait()
+t0 = time.time()
+ends = [q.get() for _ in range(n)]
+for p in ps:
+    p.join()
+print(json.dumps(dict(seconds=max(ends) - t0, steps={steps}, members=n, workers=n)))
+"""
+
+
+def run_oracle_all_cores(g, nproc, steps, wl=None):
+    env = dict(os.environ)
+    for k in ("OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
+        env[k] = "1"
+    bw = (wl or {}).get("base", {"seed": 0, "streak": 0.0, "roll": 0.0})
+    fc = None if g.get("linear") else (wl or {}).get("forcing", [None])[0]
+    seed0 = wl["noise"][0]["seed0"] if g.get("linear") else NOISE["seed0"]
+    code = CPU_SNIPPET_PAR.format(root=ROOT, g=g, nproc=nproc, bseed=bw["seed"], streak=bw["streak"],
+                                  roll=bw["roll"], seed0=seed0, amp=NOISE["amp"], n_max=NOISE["n_max"],
+                                  m_max=NOISE["m_max"], steps=steps, forcing=fc)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
+    if r.returncode != 0:
+        raise RuntimeError("oracle run failed: " + r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
 def run_oracle(g, members, steps, warm=0, wl=None):
     env = dict(os.environ)
     # the timed steps run on one core (BLAS pinned to one thread, numpy's FFT is
@@ -372,16 +439,32 @@ def run_oracle(g, members, steps, warm=0, wl=None):
     return out
 
 
+ARM_PARTS = {0xd4f: "Neoverse-V2", 0xd40: "Neoverse-V1", 0xd0c: "Neoverse-N1", 0xd49: "Neoverse-N2",
+             0xd84: "Neoverse-V3"}
+
+
 def cpu_info():
-    model = "unknown"
+    """(model, logical cores).  Arm kernels list no model name: the implementer
+    and part codes of /proc/cpuinfo name the core instead."""
+    model, impl, part = "unknown", None, None
     try:
         with open("/proc/cpuinfo") as f:
             for ln in f:
-                if ln.lower().startswith(("model name", "cpu model")):
+                key = ln.split(":", 1)[0].strip().lower()
+                if key in ("model name", "cpu model") and model == "unknown":
                     model = ln.split(":", 1)[1].strip()
-                    break
+                elif key == "cpu implementer" and impl is None:
+                    impl = ln.split(":", 1)[1].strip()
+                elif key == "cpu part" and part is None:
+                    part = ln.split(":", 1)[1].strip()
     except OSError:
         pass
+    if model == "unknown" and part is not None:
+        try:
+            name = ARM_PARTS.get(int(part, 16))
+        except ValueError:
+            name = None
+        model = "Arm %s (implementer %s, part %s)" % (name or "core", impl, part)
     return model, os.cpu_count()
 
 
@@ -606,6 +689,22 @@ def gpu_arm(args, rank, world, dist):
                                 "kind": "oracle",
                                 "sample": "%d steps x %d members of the workload's first group, single-threaded numpy, "
                                           "cpu %s (%d cores on host)" % (out["steps"], out["members"], model, ncpu)}
+        if not args.no_cpu_all_cores:
+            try:
+                avail = len(os.sched_getaffinity(0))
+            except AttributeError:
+                avail = ncpu
+            try:
+                par = run_oracle_all_cores(g0, avail, 20 if g0.get("linear") else 2, wl=wl)
+                line["cpu_baseline_all_cores"] = {
+                    "value": par["members"] * par["steps"] / par["seconds"], "unit": UNIT, "cores": par["workers"],
+                    "kind": "oracle",
+                    "sample": "%d single-threaded oracle workers (forked after one operator build), one member of "
+                              "the workload's first group each, %d steps after a barrier, cpu %s"
+                              % (par["workers"], par["steps"], model)}
+            except (RuntimeError, OSError, ValueError) as exc:   # a secondary figure: never lose the line for it
+                line["cpu_baseline_all_cores"] = {"unavailable": str(exc).splitlines()[-1][:200] if str(exc) else
+                                                  type(exc).__name__}
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -618,6 +717,8 @@ def main():
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-cpu-all-cores", action="store_true",
+                    help="skip the oracle timing over all host cores (one forked worker per core)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparator run")
     ap.add_argument("--plane", choices=["default", "cta", "cluster", "lines"], default="default",
                     help="plane-stage kernel (default: autotuned among those the grid supports)")
