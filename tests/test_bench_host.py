@@ -1,0 +1,47 @@
+"""Host logic of bench.py, on the CPU: the member-block rule it uses for its byte
+model (the library's: E/4 clamped to [4, 16] members per block, the quotient
+rounded down), the whole-job aggregate, the CPU name on Arm hosts, and the
+oracle timing over all host cores (one forked single-threaded worker per
+member)."""
+import builtins
+import io
+
+import numpy as np
+import pytest
+
+import bench
+
+G = dict(flow="couette", mx=16, my=17, mz=16, lx=1.75 * np.pi, lz=1.2 * np.pi, re=400.0, dt=0.01, members=2)
+
+
+@pytest.mark.parametrize("members,block,blocks", [(1, 0, 1), (5, 0, 1), (7, 0, 1), (8, 0, 2), (12, 0, 3),
+                                                  (16, 0, 4), (64, 0, 4), (128, 0, 8), (200, 0, 12),
+                                                  (5, 2, 2), (6, 3, 2), (8, 4, 2), (3, 4, 1)])
+def test_member_blocks_follow_the_library_rule(members, block, blocks):
+    assert bench.member_blocks(dict(members=members, member_block=block)) == blocks
+
+
+def test_shared_mean_and_linear_groups_are_one_block():
+    assert bench.member_blocks(dict(members=64, shared_mean=True)) == 1
+    assert bench.member_blocks(dict(members=45, linear=True)) == 1
+
+
+def test_aggregate_counts_every_rank_against_the_slowest():
+    assert bench.aggregate(800, 2.0, 1) == 400.0
+    assert bench.aggregate(800, 2.0, 4) == 1600.0
+
+
+def test_cpu_info_names_arm_cores(monkeypatch):
+    text = ("processor\t: 0\nBogoMIPS\t: 2000.00\nFeatures\t: fp asimd\nCPU implementer\t: 0x41\n"
+            "CPU architecture: 8\nCPU variant\t: 0x0\nCPU part\t: 0xd4f\nCPU revision\t: 0\n")
+    real_open = builtins.open
+    monkeypatch.setattr(builtins, "open",
+                        lambda p, *a, **k: io.StringIO(text) if p == "/proc/cpuinfo" else real_open(p, *a, **k))
+    model, n = bench.cpu_info()
+    assert model == "Arm Neoverse-V2 (implementer 0x41, part 0xd4f)" and n >= 1
+
+
+def test_oracle_on_all_cores_times_one_member_per_worker():
+    out = bench.run_oracle_all_cores(G, 2, 2, wl=bench.WORKLOADS["poiseuille64"])
+    assert out["workers"] == 2 and out["members"] == 2 and out["steps"] == 2
+    assert 0.0 < out["seconds"] < 120.0

@@ -169,7 +169,7 @@ def _reference(groups, sts, nsteps, **kw):
 @pytest.mark.parametrize("nsteps", [0, 1, 3, 17])   # 17: above the whole-call graph's limit
 def test_advance_equals_set_step_get(use_graph, nsteps):
     """dns_advance over an uneven batch (a group of two member blocks of 4 and a
-    group of three blocks of 2, 2, 1) = dns_set_state + dns_step + dns_get_state,
+    group of 5 members in blocks of 3 and 2) = dns_set_state + dns_step + dns_get_state,
     bitwise, with pageable buffers and with page-locked ones."""
     groups = [G, G2]
     sts = _states(groups, 7)
