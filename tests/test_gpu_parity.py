@@ -1,4 +1,6 @@
 """GPU path vs the CPU oracle, through the C ABI (needs a GPU)."""
+import os
+
 import numpy as np
 import pytest
 
@@ -90,6 +92,50 @@ def test_config2_fp64_sampled_member_matches_oracle_over_100_steps():
     ref = _oracle(CFG2).step(tuple(st[k][e:e + 1] for k in FIELDS), 100)
     for a, b, name in zip(got, ref, FIELDS):
         assert rel(a[e:e + 1], b) < 1e-11, (name, rel(a[e:e + 1], b))
+
+
+def _golden_channel128():
+    path = os.path.join(os.path.dirname(__file__), "golden", "channel128_member5_2steps.txt")
+    samples, prof, scale = {"v": [], "eta": []}, {"U": {}, "W": {}}, None
+    with open(path) as f:
+        for line in f:
+            t = line.split()
+            if not t or t[0].startswith("#"):
+                continue
+            if t[0] == "scale":
+                scale = {"v": float(t[1]), "eta": float(t[2])}
+            elif t[0] in samples:
+                samples[t[0]].append((int(t[1]), int(t[2]), int(t[3]), complex(float(t[4]), float(t[5]))))
+            else:
+                prof[t[0]][int(t[1])] = float(t[2])
+    return samples, prof, scale
+
+
+def test_config5_fp64_sampled_member_matches_stored_oracle_values():
+    """Full-size 128x97x128 constant-flux Poiseuille ensemble (Re_tau ~ 180, 16
+    members, k^-5/3 noise at 10 %) advanced two steps by the FP64 path in the
+    benchmark's launch configuration (CUDA graph, four member blocks, the
+    cluster plane kernel); member 5 against 400 sampled v and eta values and
+    the whole U, W profiles that the oracle wrote for it
+    (tests/golden/make_channel128_samples.py, which calls only the oracle)."""
+    lx, lz = 4 * np.pi, 4 * np.pi / 3
+    g = group("poiseuille", 128, 97, 128, lx, lz, 3250.0, 0.002, 16)
+    st = dns_synth.make_state(128, 97, 128, lx, lz, "poiseuille", 16, 5000, 1e-1, spectrum="kolmogorov")
+    ens = dns.Ensemble([g], precision="fp64", use_graph=True)
+    try:
+        ens.set_state(0, st["v"], st["eta"], st["U"], st["W"])
+        ens.step(2)
+        v, eta, U, W = ens.get_state(0, member0=5, count=1)
+    finally:
+        ens.close()
+    samples, prof, scale = _golden_channel128()
+    for name, a in (("v", v), ("eta", eta)):
+        assert len(samples[name]) == 400
+        err = max(abs(a[0, y, m, n] - c) for y, m, n, c in samples[name])
+        assert err < 1e-11 * scale[name], (name, err / scale[name])
+    for name, a in (("U", U), ("W", W)):
+        ref = np.array([prof[name][j] for j in range(97)])
+        assert np.abs(a[0] - ref).max() < 1e-11 * np.abs(ref).max(), name
 
 
 @pytest.mark.parametrize("flow,mx,mz", [("couette", 16, 16), ("poiseuille", 32, 16)])
