@@ -493,6 +493,31 @@ def test_uneven_batch_groups_match_each_group_run_alone(precision, use_graph):
             assert np.array_equal(a, b)
 
 
+def test_uneven_batch_at_full_size_sampled_members_match_oracle():
+    """The 128-member uneven batch at full size in the benchmark's configuration
+    (64 x Couette 32x33x32 Re 400, 32 x Couette 48x49x48 Re 800, 32 x Poiseuille
+    64x65x64 Re 1650; amplitudes ramped 1e-2 to 5e-2; mixed precision, one CUDA
+    graph, autotuned kernels, member blocks), 5 steps: one sampled member of each
+    group against the oracle within the mixed path's 1e-6."""
+    import bench
+    wl = bench.WORKLOADS["uneven"]
+    gs = [dict(g) for g in wl["groups"]]
+    sts = [bench.initial_state(g, 0, nz) for g, nz in zip(gs, wl["noise"])]
+    ens = dns.Ensemble(gs, precision="mixed", use_graph=True)
+    picks = (37, 11, 29)
+    try:
+        for gi, st in enumerate(sts):
+            ens.set_state(gi, st["v"], st["eta"], st["U"], st["W"])
+        ens.step(5)
+        got = [ens.get_state(gi, member0=e, count=1) for gi, e in enumerate(picks)]
+    finally:
+        ens.close()
+    for gi, (g, st, e) in enumerate(zip(gs, sts, picks)):
+        ref = _oracle(g).step(tuple(st[k][e:e + 1] for k in FIELDS), 5)
+        err = mixed_errors(got[gi], ref)
+        assert np.all(err[:, :3] < 1e-6), (gi, err)
+
+
 def _shared_kx0(st):
     out = {k: np.array(st[k]) for k in FIELDS}
     for k in ("v", "eta"):
