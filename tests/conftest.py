@@ -13,6 +13,6 @@ def pytest_configure(config):
 
 def pytest_sessionstart(session):
     # compile the library (and the oracle helper) once per session, so a fresh
-    # checkout or a fresh GPU machine can run the suite directly
+    # checkout or a freshly provisioned machine can run the suite directly
     import __graft_entry__
     __graft_entry__.build()
