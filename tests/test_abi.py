@@ -203,3 +203,64 @@ def test_forcing_calls_before_binding_fail_cleanly(dns):
             dns.dns_export_forcing(h, 0, 0, 4, 31)
     finally:
         dns.dns_destroy(h)
+
+
+def test_state_transfer_and_advance_calls_before_binding_fail_cleanly(dns):
+    h = dns.dns_create(dns.make_config([_g(members=2)]), 0)
+    try:
+        for call in (lambda: dns.dns_advance(h, 1, None, None, 0),
+                     lambda: dns.dns_set_state(h, 0, 0, 1, 8, 8, 8, 8, 0),
+                     lambda: dns.dns_get_state(h, 0, 0, 1, 8, 8, 8, 8, 0)):
+            with pytest.raises(dns.DnsError) as ei:
+                call()
+            assert ei.value.code == dns.DNS_ERR_INVALID
+            assert "not bound" in dns.dns_last_error(h)
+    finally:
+        dns.dns_destroy(h)
+
+
+_LAYOUT_C = r"""
+#include <stddef.h>
+#include <stdio.h>
+#include "dns.h"
+#define F(T, f) printf(#T " " #f " %zu\n", offsetof(T, f));
+int main(void) {
+    printf("dns_stats_t size %zu\n", sizeof(dns_stats_t));
+    F(dns_stats_t, e_total) F(dns_stats_t, e_pert) F(dns_stats_t, tau_bottom) F(dns_stats_t, tau_top)
+    F(dns_stats_t, bulk_flux) F(dns_stats_t, gamma) F(dns_stats_t, max_div) F(dns_stats_t, nonfinite)
+    F(dns_stats_t, reserved) F(dns_stats_t, cfl)
+    printf("dns_state_in size %zu\n", sizeof(dns_state_in));
+    F(dns_state_in, v_hat) F(dns_state_in, eta_hat) F(dns_state_in, U00) F(dns_state_in, W00)
+    printf("dns_state_out size %zu\n", sizeof(dns_state_out));
+    F(dns_state_out, v_hat) F(dns_state_out, eta_hat) F(dns_state_out, U00) F(dns_state_out, W00)
+    printf("dns_group_desc size %zu\n", sizeof(dns_group_desc));
+    F(dns_group_desc, flow) F(dns_group_desc, mx) F(dns_group_desc, my) F(dns_group_desc, mz)
+    F(dns_group_desc, lx) F(dns_group_desc, lz) F(dns_group_desc, re) F(dns_group_desc, dt)
+    F(dns_group_desc, u_wall) F(dns_group_desc, bulk_flux) F(dns_group_desc, members)
+    F(dns_group_desc, shared_mean) F(dns_group_desc, nonlinear_form) F(dns_group_desc, member_block)
+    F(dns_group_desc, linear) F(dns_group_desc, kx_index)
+    printf("dns_config size %zu\n", sizeof(dns_config));
+    F(dns_config, n_groups) F(dns_config, groups) F(dns_config, precision) F(dns_config, use_graph)
+    F(dns_config, persistent) F(dns_config, barrier_timeout_ns) F(dns_config, autotune_cache)
+    F(dns_config, ygemm) F(dns_config, plane) F(dns_config, helm)
+    return 0;
+}
+"""
+
+
+def test_python_struct_mirrors_match_the_c_header(dns, tmp_path):
+    """Every struct the binding passes across the ABI has the header's size and
+    field offsets (compiled with the host C compiler against include/dns.h)."""
+    src = tmp_path / "layout.c"
+    src.write_text(_LAYOUT_C)
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    c = {}
+    for line in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines():
+        t, f, v = line.split()
+        c[(t, f)] = int(v)
+    for name in ("dns_stats_t", "dns_state_in", "dns_state_out", "dns_group_desc", "dns_config"):
+        cls = getattr(dns, name)
+        assert ctypes.sizeof(cls) == c[(name, "size")], name
+        for field, _ in cls._fields_:
+            assert getattr(cls, field).offset == c[(name, field)], (name, field)
