@@ -20,6 +20,9 @@ import paper_2306_12739_gb300 as dns  # noqa: E402
 
 G = dict(flow="poiseuille", mx=32, my=33, mz=32, lx=2 * np.pi, lz=np.pi, re=1650.0, dt=0.005, members=8,
          member_block=4)
+# every handle in these comparisons runs the same kernel variants (the autotuner
+# decides per handle, and near-equal timings may resolve differently)
+PIN = dict(ygemm="tc", plane="lines", helm="simt")
 
 
 def _pinned(a, offset=0):
@@ -57,9 +60,9 @@ def _state():
 @pytest.mark.parametrize("offset", [0, 2, 5])   # doubles: 5 leaves v, eta 8-byte aligned only (staged copies)
 def test_pinned_and_device_buffers_move_the_same_state_as_pageable_ones(offset):
     st = _state()
-    a = dns.Ensemble([G], precision="mixed")
-    b = dns.Ensemble([G], precision="mixed")
-    c = dns.Ensemble([G], precision="mixed")
+    a = dns.Ensemble([G], precision="mixed", **PIN)
+    b = dns.Ensemble([G], precision="mixed", **PIN)
+    c = dns.Ensemble([G], precision="mixed", **PIN)
     try:
         a.set_state(0, st["v"], st["eta"], st["U"], st["W"])               # pageable numpy: staged copies
         keep = [_pinned(st[k], offset) for k in ("v", "eta", "U", "W")]   # page-locked: direct reads
@@ -89,8 +92,8 @@ def test_pinned_and_device_buffers_move_the_same_state_as_pageable_ones(offset):
 
 def test_partial_member_ranges_across_blocks_and_missing_destinations():
     st = _state()
-    a = dns.Ensemble([G], precision="mixed")
-    b = dns.Ensemble([G], precision="mixed")
+    a = dns.Ensemble([G], precision="mixed", **PIN)
+    b = dns.Ensemble([G], precision="mixed", **PIN)
     try:
         a.set_state(0, st["v"], st["eta"], st["U"], st["W"])
         b.set_state(0, st["v"], st["eta"], st["U"], st["W"])
@@ -155,7 +158,7 @@ def _states(groups, seed):
 
 
 def _reference(groups, sts, nsteps, **kw):
-    ens = dns.Ensemble(groups, precision="mixed", **kw)
+    ens = dns.Ensemble(groups, precision="mixed", **PIN, **kw)
     try:
         for gi, st in enumerate(sts):
             ens.set_state(gi, st["v"], st["eta"], st["U"], st["W"])
@@ -174,7 +177,7 @@ def test_advance_equals_set_step_get(use_graph, nsteps):
     groups = [G, G2]
     sts = _states(groups, 7)
     ref = _reference(groups, sts, nsteps, use_graph=use_graph)
-    ens = dns.Ensemble(groups, precision="mixed", use_graph=use_graph)
+    ens = dns.Ensemble(groups, precision="mixed", use_graph=use_graph, **PIN)
     try:
         got = ens.advance(nsteps, [(s["v"], s["eta"], s["U"], s["W"]) for s in sts])   # pageable
         for a, b in zip(got, ref):
@@ -197,7 +200,7 @@ def test_advance_without_upload_or_download_continues_the_current_state():
     groups = [G, G2]
     sts = _states(groups, 11)
     ref = _reference(groups, sts, 4, use_graph=True)
-    ens = dns.Ensemble(groups, precision="mixed", use_graph=True)
+    ens = dns.Ensemble(groups, precision="mixed", use_graph=True, **PIN)
     try:
         ens.advance(1, [(s["v"], s["eta"], s["U"], s["W"]) for s in sts])
         dns.dns_advance(ens.h, 2, None, None, 0)                         # keep the state, read nothing
@@ -224,7 +227,7 @@ def test_advance_with_stochastic_forcing_and_a_linear_group():
     st = _states([gf], 3)[0]
     out = []
     for mode in ("separate", "advance"):
-        ens = dns.Ensemble([gf, gl], precision="mixed", use_graph=True)
+        ens = dns.Ensemble([gf, gl], precision="mixed", use_graph=True, **PIN)
         try:
             ens.set_stochastic_forcing(0, 1, 4, 1e-3, 99)
             ens.set_base_flow(1, b["U"], b["V"], b["W"])
