@@ -407,7 +407,9 @@ def test_persistent_implicit_apply_is_bitwise_the_one_shot_kernel(mx, my, mz, E)
     (member blocks, 128-point grids, odd member counts)."""
     g = group("poiseuille", mx, my, mz, 2 * np.pi, np.pi, 1650.0, 0.005, E)
     st = _state(g, 72, 5e-2)
-    pin = dict(ygemm="simt", plane="default")
+    # separate handles: pin every autotuned variant (the cluster plane kernel is
+    # the only one at 128 points)
+    pin = dict(ygemm="simt", plane="cluster" if max(mx, mz) == 128 else "lines")
     ens = dns.Ensemble([g], precision="mixed", helm="persist", **pin)
     assert dns.dns_kernel_choice(ens.h, 0, "helm") == "persist"
     ens.close()
