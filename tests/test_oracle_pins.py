@@ -259,6 +259,37 @@ def test_laminar_poiseuille_is_steady_with_gamma_two_over_re():
     assert abs(ch.stats(y)["bulk_flux"][0] - 4.0 / 3.0) < 1e-14
 
 
+@pytest.mark.parametrize("u_wall", [0.5, -2.0])
+def test_laminar_couette_at_other_wall_speeds_is_steady(u_wall):
+    """U = U_w y with walls at +-U_w is a steady solution; its wall shear is U_w."""
+    ch = oracle.Channel(16, 25, 16, 1.75 * np.pi, 1.2 * np.pi, 400.0, 0.01, "couette", u_wall=u_wall)
+    y = oracle.grid(25)[0]
+    sh = (1, 23, 11, 6)
+    x = (np.zeros(sh, complex), np.zeros(sh, complex), (u_wall * y)[None].copy(), np.zeros((1, 25)))
+    z = ch.step(x, 10)
+    assert np.abs(z[2] - x[2]).max() < 1e-14 * abs(u_wall)
+    s = ch.stats(z)
+    assert abs(s["tau_bottom"][0] - u_wall) < 1e-13 * abs(u_wall)
+    assert abs(s["tau_top"][0] - u_wall) < 1e-13 * abs(u_wall)
+
+
+@pytest.mark.parametrize("q", [2.0, 0.25])
+def test_laminar_poiseuille_at_other_fluxes_is_steady(q):
+    """At bulk flux Q the laminar profile is U = (3Q/4)(1 - y^2), held by the
+    pressure gradient gamma = 3Q/(2 Re) (0 = gamma + U''/Re)."""
+    re = 1000.0
+    ch = oracle.Channel(16, 25, 16, 2 * np.pi, np.pi, re, 0.005, "poiseuille", bulk_flux=q)
+    y = oracle.grid(25)[0]
+    sh = (1, 23, 11, 6)
+    x = (np.zeros(sh, complex), np.zeros(sh, complex), (0.75 * q * (1 - y ** 2))[None].copy(), np.zeros((1, 25)))
+    z = ch.step(x, 10)
+    assert np.abs(z[2] - x[2]).max() < 1e-14 * q
+    # gamma = (Q - flux0) / flux1 cancels in Q - flux0: relative rounding about
+    # eps Q / (flux1 gamma) ~ eps Re / (2 dt) = 2e-11 here
+    assert abs(ch.last_gamma[0] - 1.5 * q / re) < 1e-10 * (1.5 * q / re)
+    assert abs(ch.stats(z)["bulk_flux"][0] - q) < 1e-14 * max(q, 1.0)
+
+
 @pytest.mark.parametrize("m", [1, 2])
 def test_viscous_streak_decays_by_closed_form_factor(m):
     """A streamwise-uniform streak on laminar Couette has no nonlinear term
