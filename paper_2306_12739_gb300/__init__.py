@@ -295,6 +295,13 @@ _PLANE = {"default": 0, "auto": 0, "cta": 1, "cluster": 2, "lines": 3}
 _HELM = {"default": 0, "auto": 0, "simt": 1, "tc": 2, "persist": 3}
 
 
+def _pick(table, name, what):
+    try:
+        return table[name]
+    except KeyError:
+        raise ValueError("unknown %s %r (choices: %s)" % (what, name, ", ".join(sorted(table)))) from None
+
+
 def make_config(groups, precision="fp64", use_graph=False, ygemm="default", autotune_cache=None, plane="default",
                 helm="default"):
     """groups: list of dicts with flow, mx, my, mz, lx, lz, re, dt, members,
@@ -305,15 +312,16 @@ def make_config(groups, precision="fp64", use_graph=False, ygemm="default", auto
     ensemble of one streamwise wavenumber) and kx_index (its n >= 1)."""
     arr = (dns_group_desc * len(groups))()
     for i, g in enumerate(groups):
-        arr[i] = dns_group_desc(_FLOWS[g["flow"]], g["mx"], g["my"], g["mz"], g["lx"], g["lz"], g["re"],
+        arr[i] = dns_group_desc(_pick(_FLOWS, g["flow"], "flow"), g["mx"], g["my"], g["mz"], g["lx"], g["lz"], g["re"],
                                 g["dt"], g.get("u_wall", 1.0), g.get("bulk_flux", 4.0 / 3.0), g["members"],
                                 1 if g.get("shared_mean", False) else 0,
-                                {"advective": 0, "rotational": 1}[g.get("form", "advective")],
+                                _pick({"advective": 0, "rotational": 1}, g.get("form", "advective"), "form"),
                                 int(g.get("member_block", 0)), 1 if g.get("linear", False) else 0,
                                 int(g.get("kx_index", 0)))
     cache = autotune_cache.encode() if autotune_cache else None
-    cfg = dns_config(len(groups), arr, _PRECS[precision], 1 if use_graph else 0, 0, 0, cache, _YGEMM[ygemm],
-                     _PLANE[plane], _HELM[helm])
+    cfg = dns_config(len(groups), arr, _pick(_PRECS, precision, "precision"), 1 if use_graph else 0, 0, 0, cache,
+                     _pick(_YGEMM, ygemm, "ygemm variant"), _pick(_PLANE, plane, "plane variant"),
+                     _pick(_HELM, helm, "helm variant"))
     cfg._keep = (arr, cache)
     return cfg
 

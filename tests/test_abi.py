@@ -264,3 +264,13 @@ def test_python_struct_mirrors_match_the_c_header(dns, tmp_path):
         assert ctypes.sizeof(cls) == c[(name, "size")], name
         for field, _ in cls._fields_:
             assert getattr(cls, field).offset == c[(name, field)], (name, field)
+
+
+@pytest.mark.parametrize("kw,word", [(dict(ygemm="bogus"), "ygemm"), (dict(plane="fast"), "plane"),
+                                     (dict(helm="x"), "helm"), (dict(precision="fp16"), "precision")])
+def test_unknown_names_are_rejected_with_the_choices(dns, kw, word):
+    with pytest.raises(ValueError) as ei:
+        dns.make_config([_g()], **kw)
+    assert word in str(ei.value) and "choices" in str(ei.value)
+    with pytest.raises(ValueError):
+        dns.make_config([_g(flow="channel")])
