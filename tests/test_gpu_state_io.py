@@ -183,7 +183,7 @@ def test_advance_equals_set_step_get(use_graph, nsteps):
         for a, b in zip(got, ref):
             for x, y in zip(a, b):
                 assert np.array_equal(x, y)
-        # page-locked buffers, twice in a row (the second call replays the block graphs)
+        # page-locked buffers, twice in a row (the second call replays the captured advance graph)
         keep_in = [[_pinned(s[k]) for k in ("v", "eta", "U", "W")] for s in sts]
         keep_out = [[_pinned(np.zeros_like(x)) for x in r] for r in ref]
         for _ in range(2):
