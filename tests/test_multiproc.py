@@ -81,3 +81,69 @@ def test_two_gloo_ranks_run_replicas_and_report_whole_job_throughput():
     alone = [_replica(r) for r in range(2)]
     for r in range(2):
         assert np.allclose(results[0][4][r], alone[r], rtol=1e-13, atol=0)
+
+
+E4 = dict(G, members=4)
+
+
+def _shard_stats(lo, hi):
+    """Oracle statistics of members lo..hi-1 of one seeded 4-member ensemble
+    after two steps (members are independent: a shard is the same computation)."""
+    import dns_synth
+    import oracle
+    st = dns_synth.make_state(E4["mx"], E4["my"], E4["mz"], E4["lx"], E4["lz"], E4["flow"], E4["members"], 500, 5e-2)
+    ch = oracle.Channel(E4["mx"], E4["my"], E4["mz"], E4["lx"], E4["lz"], E4["re"], E4["dt"], E4["flow"])
+    x = ch.step(tuple(st[k][lo:hi] for k in ("v", "eta", "U", "W")), 2)
+    return ch.stats(x)
+
+
+def _shard_worker(rank, world, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world), LOCAL_RANK=str(rank))
+    try:
+        import bench
+        r, w, dist = bench.dist_setup()
+        per = E4["members"] // w
+        s = _shard_stats(r * per, (r + 1) * per)
+        # host-side sums over the ranks' member ranges: the ensemble means
+        sums = torch.tensor([s["e_total"].sum(), s["e_pert"].sum(), s["tau_bottom"].sum()] + list(s["uu"].sum(0)),
+                            dtype=torch.float64)
+        dist.all_reduce(sums)
+        dist.barrier()
+        dist.destroy_process_group()
+        q.put((rank, "ok", (sums / E4["members"]).numpy(), s["e_total"]))
+    except Exception as exc:  # pragma: no cover - reported to the parent
+        q.put((rank, "error", repr(exc)))
+
+
+def test_member_range_sharding_with_host_summed_statistics_equals_one_ensemble():
+    """One ensemble split by member range over two gloo ranks, each advancing
+    its own members, statistics summed on the host: the ensemble means and
+    every member's values equal those of the whole ensemble in one process."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_shard_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    results = {}
+    try:
+        for _ in range(2):
+            item = q.get(timeout=240)
+            assert item[1] != "error", item
+            results[item[0]] = item
+    except queue.Empty:  # pragma: no cover
+        pytest.fail("a rank did not report")
+    finally:
+        for p in procs:
+            p.join(timeout=60)
+            if p.is_alive():
+                p.terminate()
+    whole = _shard_stats(0, E4["members"])
+    want = np.array([whole["e_total"].mean(), whole["e_pert"].mean(), whole["tau_bottom"].mean()]
+                    + list(whole["uu"].mean(0)))
+    for r in range(2):
+        assert np.allclose(results[r][2], want, rtol=1e-12, atol=1e-18)
+    per_member = np.concatenate([results[0][3], results[1][3]])
+    assert np.allclose(per_member, whole["e_total"], rtol=1e-13, atol=0)
