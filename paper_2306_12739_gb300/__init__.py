@@ -309,7 +309,9 @@ def make_config(groups, precision="fp64", use_graph=False, ygemm="default", auto
     members share their kx = 0 flow, S3T-type ensemble), form ("advective"
     or "rotational" nonlinear term), member_block (0: automatic size of the
     concurrently run member blocks), linear (True: a linearised disturbance
-    ensemble of one streamwise wavenumber) and kx_index (its n >= 1)."""
+    ensemble of one streamwise wavenumber) and kx_index (its n >= 1).
+    autotune_cache: file of kernel-variant decisions read and appended at bind
+    time (None: the DNS_AUTOTUNE_CACHE environment variable, if set)."""
     arr = (dns_group_desc * len(groups))()
     for i, g in enumerate(groups):
         arr[i] = dns_group_desc(_pick(_FLOWS, g["flow"], "flow"), g["mx"], g["my"], g["mz"], g["lx"], g["lz"], g["re"],
@@ -318,6 +320,8 @@ def make_config(groups, precision="fp64", use_graph=False, ygemm="default", auto
                                 _pick({"advective": 0, "rotational": 1}, g.get("form", "advective"), "form"),
                                 int(g.get("member_block", 0)), 1 if g.get("linear", False) else 0,
                                 int(g.get("kx_index", 0)))
+    if autotune_cache is None:      # the environment may name a cache shared by every handle
+        autotune_cache = os.environ.get("DNS_AUTOTUNE_CACHE") or None
     cache = autotune_cache.encode() if autotune_cache else None
     cfg = dns_config(len(groups), arr, _pick(_PRECS, precision, "precision"), 1 if use_graph else 0, 0, 0, cache,
                      _pick(_YGEMM, ygemm, "ygemm variant"), _pick(_PLANE, plane, "plane variant"),

@@ -7,6 +7,8 @@
 #include "dns_internal.hpp"
 #include "cvt.cuh"
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -22,6 +24,15 @@
 using dnsk::GroupView;
 
 namespace {
+
+// NVTX range over one library call (a named span on a profiler's host
+// timeline; a no-op unless a profiler is attached)
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 struct HostGroup {
     dns_group_desc d;
@@ -680,6 +691,7 @@ static void drop_graphs(dns_handle* h) {
 }
 
 int dns_bind_workspace(dns_handle* h, void* dev_ptr, size_t bytes) {
+    NvtxRange range_("dns_bind_workspace");
     if (!h) return DNS_ERR_INVALID;
     if (!dev_ptr || ((uintptr_t)dev_ptr & 255)) return fail(h, DNS_ERR_INVALID, "workspace NULL or not 256-byte aligned");
     if (bytes < h->need) return fail(h, DNS_ERR_NOMEM, "workspace has %zu bytes, needs %zu", bytes, h->need);
@@ -943,6 +955,7 @@ static int set_state_block(dns_handle* h, int group, int member0, int count, con
 
 int dns_set_state(dns_handle* h, int group, int member0, int count, const double* v_hat,
                   const double* eta_hat, const double* U00, const double* W00, int ptr_kind) {
+    NvtxRange range_("dns_set_state");
     if (!h) return DNS_ERR_INVALID;
     if (!h->bound) return fail(h, DNS_ERR_INVALID, "workspace not bound");
     if (group < 0 || group >= (int)h->parts.size()) return fail(h, DNS_ERR_INVALID, "bad group");
@@ -998,6 +1011,7 @@ static int get_state_block(dns_handle* h, int group, int member0, int count, dou
 
 int dns_get_state(const dns_handle* hc, int group, int member0, int count, double* v_hat,
                   double* eta_hat, double* U00, double* W00, int ptr_kind) {
+    NvtxRange range_("dns_get_state");
     dns_handle* h = const_cast<dns_handle*>(hc);
     if (!h) return DNS_ERR_INVALID;
     if (!h->bound) return fail(h, DNS_ERR_INVALID, "workspace not bound");
@@ -1057,6 +1071,7 @@ static int run_steps(dns_handle* h, int nsteps) {
 }
 
 int dns_step(dns_handle* h, int nsteps) {
+    NvtxRange range_("dns_step");
     if (!h) return DNS_ERR_INVALID;
     if (!h->bound) return fail(h, DNS_ERR_INVALID, "workspace not bound");
     if (nsteps < 0) return fail(h, DNS_ERR_INVALID, "nsteps < 0");
@@ -1075,6 +1090,7 @@ int dns_step(dns_handle* h, int nsteps) {
 // downloads.  Per block the kernels and their order are those of
 // dns_set_state + dns_step + dns_get_state, so the results are bitwise the same.
 int dns_advance(dns_handle* h, int nsteps, const dns_state_in* in, const dns_state_out* out, int ptr_kind) {
+    NvtxRange range_("dns_advance");
     if (!h) return DNS_ERR_INVALID;
     if (!h->bound) return fail(h, DNS_ERR_INVALID, "workspace not bound");
     if (nsteps < 0) return fail(h, DNS_ERR_INVALID, "nsteps < 0");
@@ -1279,6 +1295,7 @@ static int stats_block(dns_handle* h, int group, dns_stats_t* per_member, double
 }
 
 int dns_stats(dns_handle* h, int group, dns_stats_t* per_member, dns_stats_t* ensemble_mean, double* profiles) {
+    NvtxRange range_("dns_stats");
     if (!h) return DNS_ERR_INVALID;
     if (!h->bound) return fail(h, DNS_ERR_INVALID, "workspace not bound");
     if (group < 0 || group >= (int)h->parts.size()) return fail(h, DNS_ERR_INVALID, "bad group");
@@ -1451,6 +1468,7 @@ int dns_set_direction(dns_handle* h, int group, int adjoint) {
 }
 
 int dns_orthonormalize(dns_handle* h, int group, double* norms) {
+    NvtxRange range_("dns_orthonormalize");
     if (!h) return DNS_ERR_INVALID;
     HostGroup* G = nullptr;
     int rc = linear_group(h, group, &G);
@@ -1465,6 +1483,7 @@ int dns_orthonormalize(dns_handle* h, int group, double* norms) {
 }
 
 int dns_optimal_sweep(dns_handle* h, int nsteps, double* gains) {
+    NvtxRange range_("dns_optimal_sweep");
     if (!h) return DNS_ERR_INVALID;
     if (!h->bound) return fail(h, DNS_ERR_INVALID, "workspace not bound");
     if (nsteps < 1) return fail(h, DNS_ERR_INVALID, "nsteps < 1");

@@ -274,3 +274,12 @@ def test_unknown_names_are_rejected_with_the_choices(dns, kw, word):
     assert word in str(ei.value) and "choices" in str(ei.value)
     with pytest.raises(ValueError):
         dns.make_config([_g(flow="channel")])
+
+
+def test_autotune_cache_path_may_come_from_the_environment(dns, monkeypatch, tmp_path):
+    path = str(tmp_path / "tune.txt")
+    monkeypatch.setenv("DNS_AUTOTUNE_CACHE", path)
+    assert dns.make_config([_g()]).autotune_cache == path.encode()
+    assert dns.make_config([_g()], autotune_cache="other").autotune_cache == b"other"
+    monkeypatch.delenv("DNS_AUTOTUNE_CACHE")
+    assert dns.make_config([_g()]).autotune_cache is None
