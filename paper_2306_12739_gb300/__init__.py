@@ -9,6 +9,7 @@ raises ImportError if ``libdns.so`` has not been built (run
 ``python -c "import __graft_entry__ as g; g.build()"``); there is no fallback.
 """
 import ctypes
+import json
 import os
 
 import numpy as np
@@ -330,6 +331,38 @@ def make_config(groups, precision="fp64", use_graph=False, ygemm="default", auto
     return cfg
 
 
+# ------------------------------------------------------------- checkpoints
+
+_STATE_KEYS = ("v", "eta", "U", "W")
+
+
+def save_states(path, groups, states):
+    """Checkpoint file (.npz): the group descriptions (as JSON) and every
+    group's state (v, eta, U, W in the host layout; U, W None for a linear
+    group), written exactly (no conversion)."""
+    arrs = {"groups": np.array(json.dumps(groups))}
+    for i, st in enumerate(states):
+        for k, a in zip(_STATE_KEYS, st):
+            if a is not None:
+                arrs["g%d_%s" % (i, k)] = np.asarray(a)
+    np.savez(path, **arrs)
+
+
+def load_states(path):
+    """(groups, states) of a checkpoint written by save_states."""
+    with np.load(path, allow_pickle=False) as z:
+        groups = json.loads(str(z["groups"]))
+        states = [tuple(z["g%d_%s" % (i, k)] if "g%d_%s" % (i, k) in z.files else None for k in _STATE_KEYS)
+                  for i in range(len(groups))]
+    return groups, states
+
+
+def same_groups(a, b):
+    """True when two lists of group descriptions describe the same groups (as a
+    checkpoint stores them)."""
+    return json.loads(json.dumps(a)) == json.loads(json.dumps(b))
+
+
 class Ensemble:
     """Owns a handle, its torch workspace and the stream it runs on."""
 
@@ -396,6 +429,21 @@ class Ensemble:
 
     def step(self, nsteps=1):
         dns_step(self.h, nsteps)
+
+    def checkpoint(self, path):
+        """Write every group's current state to a checkpoint file (save_states)."""
+        save_states(path, self.groups, [self.get_state(i) for i in range(len(self.groups))])
+
+    def restore(self, path):
+        """Set every group's state from a checkpoint of the same groups."""
+        groups, states = load_states(path)
+        if not same_groups(groups, self.groups):
+            raise ValueError("the checkpoint holds other groups")
+        for i, st in enumerate(states):
+            if self.groups[i].get("linear"):
+                self.set_state(i, st[0], st[1])
+            else:
+                self.set_state(i, *st)
 
     def advance(self, nsteps, states):
         """Replace every group's state by states[group] = (v, eta, U, W) (host

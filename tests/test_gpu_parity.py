@@ -224,12 +224,18 @@ def test_member_alone_equals_member_in_batch(precision, pin):
         assert np.array_equal(a[4:5], b)
 
 
-def test_resume_is_bitwise():
+def test_resume_is_bitwise(tmp_path):
+    """Three steps, a checkpoint file (save_states / load_states), three more
+    steps from it in a new handle: bitwise the six uninterrupted steps."""
     g = group("poiseuille", 16, 33, 16, 2 * np.pi, np.pi, 1650.0, 0.005, 2)
     st = _state(g, 9, 5e-2)
     direct = _run(g, st, 6)
     mid = _run(g, st, 3)
-    st2 = dict(zip(FIELDS, mid))
+    path = str(tmp_path / "mid.npz")
+    dns.save_states(path, [g], [mid])
+    groups, states = dns.load_states(path)
+    assert dns.same_groups(groups, [g])
+    st2 = dict(zip(FIELDS, states[0]))
     resumed = _run(g, st2, 3)
     for a, b in zip(direct, resumed):
         assert np.array_equal(a, b)
