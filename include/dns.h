@@ -77,7 +77,7 @@ typedef struct {
     double bulk_flux;      /* Poiseuille: prescribed int_{-1}^{1} U00 dy (4/3 for U = 1 - y^2) */
     int members;           /* ensemble size of this group, >= 1 */
     int shared_mean;       /* 0: independent members.  1: the members share their
-                              streamwise-mean (kx = 0) flow, an S3T-type ensemble (Sec. 5):
+                              streamwise-mean (kx = 0) flow, an S3T-type ensemble (Sec. 4.1):
                               every sub-step the kx = 0 part of the nonlinear term and the
                               plane means <uv>, <wv> are replaced by their average over the
                               members, so the shared flow is driven by the ensemble-averaged

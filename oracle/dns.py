@@ -64,7 +64,9 @@ def _p(a):
 
 
 def grid(My):
-    """Nodes, D1, D2 = D1 D1 on all My nodes and the clamped D4c (interior)."""
+    """Nodes, D1, D2 = D1 D1 on all My nodes and the clamped D4c (interior):
+    the Chebyshev collocation of Sec. 3.2 (the Laplacians of Listing 1 are
+    built from them; D4c enters the v operator of Eq. CN1)."""
     y = np.zeros(My); D1 = np.zeros((My, My)); D2 = np.zeros((My, My))
     D4c = np.zeros((My - 2, My - 2))
     rc = _ops().orc_grid(My, _p(y), _p(D1), _p(D2), _p(D4c))
@@ -73,6 +75,8 @@ def grid(My):
 
 
 def cc_weights(My):
+    """Clenshaw-Curtis weights of the nodes: the y-integrals of the bulk flux
+    (the constant-flux condition of Sec. 3.2) and of the statistics (Sec. 4)."""
     w = np.zeros(My)
     assert _ops().orc_cc_weights(My, _p(w)) == 0
     return w
@@ -89,6 +93,8 @@ def cn_operators(My, k2, dt, re, h):
 
 
 def mean_operators(My, dt, re, h):
+    """MU, PU, bU (wall terms) and the unit pressure-gradient response Ug of
+    the mean-flow update (Eqs. CN3, CN4, Sec. 3.2), built in binary128."""
     n = My - 2
     MU = np.zeros((n, n)); PU = np.zeros((n, n)); bU = np.zeros((n, 2)); Ug = np.zeros(n)
     assert _ops().orc_mean_ops(My, dt, re, h, _p(MU), _p(PU), _p(bU), _p(Ug)) == 0
@@ -96,6 +102,8 @@ def mean_operators(My, dt, re, h):
 
 
 def quad_solve(A, B):
+    """A^-1 B solved in binary128 and rounded once (the precalculated inverses
+    of Sec. 3.2, Listing 3)."""
     A = np.ascontiguousarray(A, dtype=np.float64)
     B = np.ascontiguousarray(B, dtype=np.float64)
     B2 = B.reshape(B.shape[0], -1)
@@ -105,7 +113,7 @@ def quad_solve(A, B):
 
 
 def fundamental(L):
-    """2 pi / L, rounded once to double."""
+    """2 pi / L, rounded once to double (kx = n 2 pi / Lx, kz = m 2 pi / Lz, Sec. 2)."""
     return _ops().orc_fundamental(float(L))
 
 
@@ -136,11 +144,12 @@ def _combine(wts, Fs):
 
 
 class Channel:
-    """One group of ensemble members that share a grid, Re and dt."""
+    """One group of ensemble members that share a grid, Re and dt (Secs. 2-3;
+    the members are the ensemble of Sec. 4.1)."""
 
     def __init__(self, mx, my, mz, lx, lz, re, dt, flow="couette",
                  u_wall=1.0, bulk_flux=4.0 / 3.0, shared_mean=False, form="advective"):
-        """shared_mean: the S3T-type ensemble of Sec. 5 (ensemble simulations of
+        """shared_mean: the S3T-type ensemble of Sec. 4.1 (ensemble simulations of
         statistical state dynamics): the members share their streamwise-mean
         (kx = 0) flow, which every sub-step is driven by the kx = 0 part of the
         nonlinear term and by the plane means <uv>, <wv> averaged over the
@@ -193,7 +202,7 @@ class Channel:
     def to_physical(self, c):
         """Kept coefficients [..., 2Kz+1, Kx+1] -> real field [..., Mz, Mx]
         (zero-padded inverse transform; the n = 0 column contributes its
-        Hermitian part)."""
+        Hermitian part) (Sec. 3.2)."""
         Kx, Kz = self.Kx, self.Kz
         Z = np.zeros(c.shape[:-2] + (self.mz, self.mx // 2 + 1), dtype=np.complex128)
         Z[..., 0:Kz + 1, 0:Kx + 1] = c[..., Kz:, :]
@@ -202,7 +211,8 @@ class Channel:
         return np.fft.irfft2(Z, s=(self.mz, self.mx), norm="forward")
 
     def to_spectral(self, f):
-        """Real field [..., Mz, Mx] -> coefficients of the kept modes."""
+        """Real field [..., Mz, Mx] -> coefficients of the kept modes (forward
+        transform and 2/3-rule truncation, Sec. 3.2)."""
         Kx, Kz = self.Kx, self.Kz
         F = np.fft.rfft2(f, norm="forward")
         out = np.zeros(f.shape[:-2] + (2 * Kz + 1, Kx + 1), dtype=np.complex128)
@@ -329,7 +339,7 @@ class Channel:
         return (vn, en, Un, Wn)
 
     def step(self, state, nsteps=1):
-        """Advance (v, eta, U, W) by nsteps full CN/RK3 steps."""
+        """Advance (v, eta, U, W) by nsteps full CN/RK3 steps (Sec. 3.1)."""
         x = tuple(np.array(a) for a in state)
         for _ in range(nsteps):
             if self.stochastic is not None:

@@ -70,7 +70,8 @@ def _uniform(seed, k):
 
 
 def normals(seed, counters):
-    """Standard normals N(c): Box-Muller (cosine branch) of draws 2c, 2c + 1."""
+    """Standard normals N(c): Box-Muller (Box and Muller 1958; cosine branch)
+    of draws 2c, 2c + 1."""
     c = np.asarray(counters, dtype=np.uint64)
     u1 = _uniform(seed, np.uint64(2) * c)
     u2 = _uniform(seed, np.uint64(2) * c + np.uint64(1))
@@ -84,7 +85,9 @@ def _root(f, lo, hi):
 
 
 def stokes_mu(k, count):
-    """The first `count` Stokes-mode wavenumbers mu (increasing), with parity."""
+    """The first `count` Stokes-mode wavenumbers mu (increasing), with parity:
+    eigenfunctions of the diffusion operator that the S3T run of Sec. 4.1
+    draws its forcing from."""
     out = []
     n = 1
     while len(out) < count:
@@ -98,7 +101,7 @@ def stokes_mu(k, count):
 
 class StochasticForcing:
     """Forcing structures of one DNS group (oracle.Channel) and the per-step
-    noise they are mixed with."""
+    noise they are mixed with (Sec. 4.1, the S3T run)."""
 
     def __init__(self, ch, kx_index, n_eig, rate, seed):
         assert 1 <= kx_index <= ch.Kx and 1 <= n_eig <= ch.nyi
@@ -138,7 +141,7 @@ class StochasticForcing:
         self.eps = np.sqrt(rate / (2.0 * (nm * 2 * n_eig)))
 
     def xi(self, step, E):
-        """Complex unit-variance noise [E, 2Kz+1, 2, n_eig] of one step."""
+        """Complex unit-variance noise [E, 2Kz+1, 2, n_eig] of one step (Sec. 4.1)."""
         nm = 2 * self.ch.Kz + 1
         idx = np.arange(E * nm * 2 * self.n_eig, dtype=np.uint64) + np.uint64(step * E * nm * 2 * self.n_eig)
         c = np.uint64(2) * idx
@@ -147,7 +150,7 @@ class StochasticForcing:
 
     def terms(self, step, E):
         """(F_noise, G_noise) [E, Ny, 2Kz+1] at column kx_index for one step:
-        the forcing constant over the step, eps / sqrt(dt) sum_j xi_j (rhs_j)."""
+        the forcing constant over the step, eps / sqrt(dt) sum_j xi_j (rhs_j) (Sec. 4.1)."""
         x = self.xi(step, E)
         s = self.eps / np.sqrt(self.ch.dt)
         Fn = s * np.einsum("emj,mjy->eym", x[:, :, 0], self.rhs[:, 0])

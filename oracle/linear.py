@@ -52,7 +52,9 @@ from .dns import grid, cc_weights, cn_operators, fundamental, cn_rk3
 
 
 class Linear:
-    """A group of disturbance vectors of one kx about one frozen base flow."""
+    """A group of disturbance vectors of one kx about one frozen base flow
+    (Sec. 4.1.1, "Diagnostic utilities that benefit from vectorization";
+    Appendix B)."""
 
     def __init__(self, my, mz, lx, lz, re, dt, kx_index, U, V, W):
         assert kx_index >= 1
@@ -99,7 +101,7 @@ class Linear:
 
     def set_base(self, U, V, W):
         """Base flow on the (My, Mz) grid -> nine real fields on the interior
-        planes: B_i, d_y B_i, d_z B_i for B = (U, V, W)."""
+        planes: B_i, d_y B_i, d_z B_i for B = (U, V, W) (Sec. 4.1.1)."""
         self.base = {}
         ikz = 1j * self.kz
         for name, f in (("U", U), ("V", V), ("W", W)):
@@ -114,7 +116,8 @@ class Linear:
     # ------------------------------------------------------- velocity field
     def velocity(self, v, eta):
         """u, v, w and their y- and z-derivatives on all My nodes, spectral
-        [e, My, 2Kz+1] (x-derivatives are i kx times the field)."""
+        [e, My, 2Kz+1] (x-derivatives are i kx times the field; u, w recovered as
+        in Sec. 3.2)."""
         E = v.shape[0]
         sh = (E, self.my, 2 * self.Kz + 1)
         vf = np.zeros(sh, dtype=np.complex128); vf[:, 1:-1] = v
@@ -135,7 +138,7 @@ class Linear:
     # --------------------------------------------------------- linear terms
     def term(self, v, eta, adjoint=None):
         """N_fwd or N_adj (module docstring) on the interior planes, transformed
-        and truncated: three spectral arrays [e, Ny_i, 2Kz+1]."""
+        and truncated: three spectral arrays [e, Ny_i, 2Kz+1] (Appendix B)."""
         if adjoint is None:
             adjoint = self.adjoint
         f = self.velocity(v, eta)
@@ -167,7 +170,8 @@ class Linear:
         return (F, G)
 
     def update(self, state_t, Ft, h, s=None):
-        """CN sub-step from the state at t with the single-kx operators."""
+        """CN sub-step from the state at t with the single-kx operators
+        (Eqs. CN1, CN2, valid for the adjoint equations too, Sec. 4.1.1)."""
         v, eta = state_t
         F, G = Ft
         Mv, Pv, Me, Pe = self.ops[h]
@@ -177,7 +181,7 @@ class Linear:
 
     def step(self, state, nsteps=1, adjoint=False):
         """Advance (v, eta) by nsteps CN/RK3 steps of the forward (or adjoint)
-        equations."""
+        equations (the scheme of Sec. 3.1, as Sec. 4.1.1 applies it)."""
         self.adjoint = adjoint
         x = tuple(np.array(a) for a in state)
         for _ in range(nsteps):
@@ -186,7 +190,7 @@ class Linear:
 
     # ------------------------------------------------------------ energy
     def inner(self, a, b):
-        """Energy inner products <a_i, b_j> (module docstring): [Ea, Eb]."""
+        """Energy inner products <a_i, b_j> (module docstring): [Ea, Eb] (Appendix B)."""
         va, ea = a
         vb, eb = b
         Dva = np.einsum("ij,ejm->eim", self.D1i, va)
@@ -199,12 +203,13 @@ class Linear:
         return 0.25 * g
 
     def energy(self, state):
+        """Energy of every vector: the diagonal of inner (Appendix B)."""
         return np.real(np.diagonal(self.inner(state, state))).copy()
 
     def orthonormalize(self, state):
-        """Modified Gram-Schmidt in the energy inner product, in member order.
-        Returns the orthonormal set and each vector's norm before its
-        normalisation."""
+        """Modified Gram-Schmidt in the energy inner product, in member order
+        (Sec. 4.1.1: the orthonormalisation step).  Returns the orthonormal set
+        and each vector's norm before its normalisation."""
         v = np.array(state[0]); eta = np.array(state[1])
         E = v.shape[0]
         r = np.zeros(E)
@@ -221,7 +226,7 @@ class Linear:
 
     def sweep(self, state, nsteps):
         """One forward-adjoint iteration over nsteps steps each way, followed by
-        Gram-Schmidt.  Returns the next initial conditions and the growth
+        Gram-Schmidt (Sec. 4.1.1: the forward-adjoint iteration loop).  Returns the next initial conditions and the growth
         estimates (the norms before normalisation)."""
         fwd = self.step(state, nsteps, adjoint=False)
         adj = self.step(fwd, nsteps, adjoint=True)

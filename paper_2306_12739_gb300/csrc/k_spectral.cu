@@ -474,7 +474,7 @@ __global__ void k_stats_final(GroupView g) {
     }
 }
 
-// Shared-mean (S3T-type) ensemble, Sec. 5: the kx = 0 column of the three
+// Shared-mean (S3T-type) ensemble, Sec. 4.1: the kx = 0 column of the three
 // nonlinear terms (P layout, n = 0 of every m and interior plane) and the plane
 // means <uv>, <wv> are replaced by their average over the members, summed in
 // member order.  One thread per averaged quantity.
