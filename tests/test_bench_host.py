@@ -45,3 +45,20 @@ def test_oracle_on_all_cores_times_one_member_per_worker():
     out = bench.run_oracle_all_cores(G, 2, 2, wl=bench.WORKLOADS["poiseuille64"])
     assert out["workers"] == 2 and out["members"] == 2 and out["steps"] == 2
     assert 0.0 < out["seconds"] < 120.0
+
+
+def test_byte_and_work_models_are_the_documented_counts():
+    """The algorithmic bytes and flops that the roofline figures divide by, for
+    one launch of the headline case (64x65x64, one member block of 4): S =
+    modes x Ny x E complex values; y-derivatives 2*16 S in + 5*8 S out, plane
+    stage 5*8 S in + 3*8 S out, forcing 3*8 S + 2*8 S + the RK accumulators
+    (2*8 S, read in two sub-steps of three and written in all); the plane stage
+    15 * 2.5 MxMz log2(MxMz) + 22 MxMz flop per plane and member."""
+    g = dict(bench.WORKLOADS["poiseuille64"]["groups"][0], members=4)
+    S = 22 * 43 * 63 * 4
+    assert bench.kernel_bytes("yderiv", g, "mixed") == 72 * S == 17164224
+    assert bench.kernel_bytes("plane", g, "mixed") == 64 * S == 15257088
+    assert bench.kernel_bytes("forcing", g, "mixed") == pytest.approx((40 + 16 * 4 / 3) * S) == 14621376
+    bound, flops, unit = bench.kernel_work("plane", g, "mixed")
+    per = 15 * 2.5 * 4096 * 12 + 22 * 4096
+    assert (bound, unit) == ("alu", "flop") and flops == pytest.approx(4 * 63 * per)
