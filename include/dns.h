@@ -242,8 +242,9 @@ typedef struct {
 } dns_state_out;
 
 /* Upload, advance and download in one call (host-transfer scheduling, no
- * counterpart in the paper; the steps are those of dns_step, Sec. 3.1): every group's state is replaced by
- * in[group] (in == NULL: keep the current state), nsteps CN/RK3 steps run, and
+ * counterpart in the paper; the steps are those of dns_step, Sec. 3.1): every
+ * group's state is replaced by in[group] (in == NULL: keep the current state),
+ * nsteps CN/RK3 steps run, and
  * the result is written to out[group] (out == NULL: nothing is read back).
  * Same results, bit for bit, as dns_set_state for every group, dns_step and
  * dns_get_state for every group; the difference is scheduling.  When every
