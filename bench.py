@@ -32,6 +32,12 @@ UNIT = "member-steps/s"
 
 # The default workload (the headline) and the other ensemble configurations.
 WORKLOADS = {
+    "couette16": dict(
+        groups=[dict(flow="couette", mx=16, my=33, mz=16, lx=1.75 * np.pi, lz=1.2 * np.pi, re=400.0, dt=0.01,
+                     members=1)],
+        name="Couette Re=400, 1.75pi x 2 x 1.2pi, 16x33x16, 1 member, dt=0.01 (laminar u = y + 1e-2 noise in "
+             "|n|, |m| <= 2)",
+        noise=[dict(seed0=1000, amp=1e-2, n_max=2, m_max=2)]),
     "poiseuille64": dict(
         groups=[dict(flow="poiseuille", mx=64, my=65, mz=64, lx=2 * np.pi, lz=np.pi, re=1650.0, dt=0.005, members=8)],
         name="Poiseuille constant-flux Re=1650 (Re_tau~100), 2pi x 2 x pi, 64x65x64, 8 members, dt=0.005",
@@ -83,7 +89,7 @@ NOISE = WORKLOADS["poiseuille64"]["noise"][0]
 
 FP32_PEAK_PER_SM_CLK = 128 * 2          # FP32 lanes x 2 flops (FMA) per SM per clock
 FP64_NOMINAL_TFLOPS = 1.25              # GB300 FP64 (nominal)
-N_SM = 152
+ERR_HORIZON = 50                        # steps of the mixed-vs-FP64 error stated on the line
 
 
 def initial_state(g, rank=0, noise=None):
@@ -292,10 +298,36 @@ def profiled_traffic(kernel, variant):
     return rec["dram_bytes_per_launch"]
 
 
-def alu_peak(precision_of_kernel, sm_mhz):
+def alu_peak(precision_of_kernel, sm_mhz, n_sm):
+    """FP32 peak of n_sm SMs at the sampled clock (TFLOP/s), or the nominal FP64
+    rate."""
     if precision_of_kernel == "f64":
         return FP64_NOMINAL_TFLOPS
-    return N_SM * FP32_PEAK_PER_SM_CLK * sm_mhz * 1e6 / 1e12
+    return n_sm * FP32_PEAK_PER_SM_CLK * sm_mhz * 1e6 / 1e12
+
+
+def rel_errors(got, ref):
+    """Mixed-vs-FP64 relative errors of one group's states (v, eta, U, W as
+    returned by get_state, U and W None for a linear group).  Per field and
+    member: max |x - x_ref| / max |x_ref| over modes and y; the mean flow
+    (U00, W00) is one velocity field normalised by max(|U00|, |W00|) of the
+    reference, and W00 alone is reported on its own scale as well.  Returns the
+    maxima over members and the per-member values."""
+    E = ref[0].shape[0]
+    out = {"v": [], "eta": [], "mean_flow": [], "w00_alone": []}
+    for e in range(E):
+        for k, i in (("v", 0), ("eta", 1)):
+            a, b = np.asarray(got[i][e]), np.asarray(ref[i][e])
+            out[k].append(float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300)))
+        if ref[2] is not None:
+            du = np.abs(np.asarray(got[2][e]) - np.asarray(ref[2][e]))
+            dw = np.abs(np.asarray(got[3][e]) - np.asarray(ref[3][e]))
+            scale = max(np.max(np.abs(ref[2][e])), np.max(np.abs(ref[3][e])), 1e-300)
+            out["mean_flow"].append(float(max(np.max(du), np.max(dw)) / scale))
+            out["w00_alone"].append(float(np.max(dw) / max(np.max(np.abs(ref[3][e])), 1e-300)))
+    res = {k: max(v) for k, v in out.items() if v}
+    res["per_member"] = {k: v for k, v in out.items() if v}
+    return res
 
 
 def kernel_precision(cls, precision):
@@ -578,7 +610,8 @@ def gpu_arm(args, rank, world, dist):
     avg_ms = kt[dom][0] / max(1, kt[dom][1])
     kprec = kernel_precision(dom, precision)
     sm_mhz = clocks["sm_mhz"] or 2070.0
-    peak = alu_peak(kprec, sm_mhz)
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = alu_peak(kprec, sm_mhz, n_sm)
     achieved = work / (kt[dom][0] / 1e3) / 1e12
     variant = {"plane": choices[0]["plane"], "yderiv": choices[0]["ygemm"], "helm": choices[0]["helm"]}.get(dom, "simt")
     traffic = (profiled_traffic(dom, variant)
@@ -598,10 +631,20 @@ def gpu_arm(args, rank, world, dist):
                 "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
                 "traffic_unit": "DRAM bytes per launch (ncu, profiles/)",
                 "peak_source": ("nominal GB300 FP64" if kprec == "f64" else
-                                "152 SM x 128 FP32 lanes x 2 x median sampled SM clock %.0f MHz" % sm_mhz),
+                                "%d SM (device attribute) x 128 FP32 lanes x 2 x median sampled SM clock %.0f MHz"
+                                % (n_sm, sm_mhz)),
                 "kernel_ms_per_launch": avg_ms,
                 "shares": {k: round(v, 4) for k, v in shares.items()},
                 "hbm_view": {"peak_gbs": hpk, "peak_source": hsrc, "classes": per_class}}
+
+    # the mixed states after ERR_HORIZON steps of this very launch configuration
+    # (same handle, kernel variants, member blocks and graph), for the error
+    # against FP64 stated on the line
+    mixed_states = None
+    if precision == "mixed" and not args.no_fp64:
+        load(ens)
+        ens.step(ERR_HORIZON)
+        mixed_states = [ens.get_state(gi) for gi in range(len(groups))]
 
     # end to end through the C ABI with host buffers: upload state, step, download state
     pins, outs = [], []
@@ -670,13 +713,32 @@ def gpu_arm(args, rank, world, dist):
         line["optimal_iteration"] = optimal
 
     if precision == "mixed" and not args.no_fp64:
-        n64 = max(1, min(args.steps, 5))
+        n64 = max(20, min(args.steps, 50))
         ens64, t64, _, _ = timed_run("fp64", n64, min(args.warmup, 3), flush)
+        load(ens64)
+        ens64.step(ERR_HORIZON)
+        errs = []
+        for gi in range(len(groups)):
+            st64 = ens64.get_state(gi)
+            got = mixed_states[gi]
+            if groups[gi].get("linear"):
+                st64, got = (st64[0], st64[1], None, None), (got[0], got[1], None, None)
+            errs.append(rel_errors(got, st64))
         ens64.close()
         t64 = reduce_max(t64, dist, dev)
         v64 = aggregate(members * n64, t64 / 1e3, world)
         line["fp64"] = {"value": v64, "unit": UNIT, "ms_per_step": t64 / n64, "steps": n64}
         line["mixed_over_fp64"] = value / v64
+        fields = [k for k in ("v", "eta", "mean_flow", "w00_alone") if k in errs[0]]
+        line["err_vs_fp64"] = {
+            "horizon_steps": ERR_HORIZON,
+            "metric": "max over members of max|mixed - fp64| / max|fp64| per field, after the same seeded steps "
+                      "(mean flow: U00 and W00 as one field; w00_alone on its own scale)",
+            "max": {k: max(e[k] for e in errs if k in e) for k in fields},
+            "tolerance": {"v": 1e-6, "eta": 1e-6, "mean_flow": 1e-6, "w00_alone": 1e-5},
+            "per_group": [{k: e[k] for k in fields if k in e} for e in errs],
+            "per_member_first_group": errs[0]["per_member"],
+        }
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         g0 = groups[0]

@@ -349,8 +349,12 @@ int dns_export_operators(const dns_handle* h, int group, int h_index, int pair,
  *            e_total, e_pert, tau_bottom, tau_top, bulk_flux, gamma, max_div,
  *            nonfinite (1.0 or 0.0).  Caller-owned.
  * Enqueued on the handle's stream; returns without synchronising.
- * The first call on a device looks up the array's device address; make that
- * first call before any stream capture.  Every call shares the one array, so
+ * dns_bind_workspace does this call's set-up, on the device that is current
+ * there: it looks up the array's device address and loads the module that holds
+ * the array and the statistics kernels.  With lazy module loading (the CUDA
+ * default since 12.2) those loads are what takes device memory for the array
+ * and the code, so they happen at bind time, never inside this call.  Every
+ * call shares the one array, so
  * calls that overlap on the GPU (other streams, other handles) race; each call
  * writes every partial it reads, so nothing needs clearing between calls.
  * Errors: DNS_ERR_INVALID (unbound workspace, NULL output, or a group with

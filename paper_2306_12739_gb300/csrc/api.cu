@@ -476,6 +476,7 @@ std::vector<uint16_t> helm_tc_a_images(const std::vector<double>& ops, int npair
 void launch_wait_selftest(int* status, cudaStream_t st);
 cudaError_t noalloc_scratch(double** out);
 size_t noalloc_max_partials();
+cudaError_t noalloc_prepare();
 void launch_stats_noalloc(const GroupView& g, double* scratch, double* out, cudaStream_t st);
 void set_attributes_spectral();
 void set_attributes_plane();
@@ -722,6 +723,8 @@ int dns_bind_workspace(dns_handle* h, void* dev_ptr, size_t bytes) {
     {
         int rc0 = check(h, cudaGetLastError(), "kernel attributes");
         if (rc0) return rc0;
+        // the fixed array of dns_stats_noalloc and its kernels, resolved and loaded now
+        if ((rc0 = check(h, dnsk::noalloc_prepare(), "dns_stats_noalloc set-up"))) return rc0;
     }
     cudaStream_t st = h->stream;
     int rc = check(h, cudaMemsetAsync(dev_ptr, 0, h->need, st), "clear workspace");

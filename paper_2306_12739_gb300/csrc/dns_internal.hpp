@@ -147,6 +147,10 @@ bool launch_plane_cl(const GroupView& g, bool fp64, const double* U, const doubl
 size_t plane_cl_smem_bytes(int mx, int mz, bool fp64);
 void set_attributes_plane_cl();
 void launch_stats(const GroupView& g, cudaStream_t st);
+// the statistics without profiles and CFL: per-plane sums into part [E][Ny][6],
+// packed values into out [E][8]
+void launch_stats_packed(const GroupView& g, double* part, double* out, cudaStream_t st);
+cudaError_t load_stats_kernels();   // loads the kernels launch_stats_packed uses
 void launch_shared_mean(const GroupView& g, bool fp64, cudaStream_t st);
 void launch_pack(const GroupView& g, int member0, int count, const double2* sv, const double2* se, const double* sU,
                  const double* sW, cudaStream_t st);

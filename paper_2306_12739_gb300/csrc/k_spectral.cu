@@ -294,7 +294,9 @@ void launch_helm(const GroupView& g, int s, cudaStream_t st) {
 
 // -------------------------------------------------------------------- stats
 
-__global__ void __launch_bounds__(256) k_stats_plane(GroupView g) {
+// Per-plane Parseval sums of one (interior plane y, member e) into part[e][y][6]:
+// uu, vv, ww, uv (perturbation, Sec. 4), max |div u|, non-finite flag.
+__global__ void __launch_bounds__(256) k_stats_plane(GroupView g, double* __restrict__ part) {
     __shared__ double red[32];
     const int y = blockIdx.x, e = blockIdx.y;
     const int Ny = g.ny, E = g.E, nmodes = g.nmodes, NKX = g.nkx;
@@ -325,7 +327,7 @@ __global__ void __launch_bounds__(256) k_stats_plane(GroupView g) {
     uu = block_sum(uu, red); vv = block_sum(vv, red); ww = block_sum(ww, red);
     uv = block_sum(uv, red); dmax = block_max(dmax, red); nf = block_max(nf, red);
     if (threadIdx.x == 0) {
-        double* o = g.st_y + ((size_t)e * Ny + y) * 6;
+        double* o = part + ((size_t)e * Ny + y) * 6;
         o[0] = uu; o[1] = vv; o[2] = ww; o[3] = uv; o[4] = dmax; o[5] = nf;
     }
 }
@@ -425,29 +427,37 @@ size_t stats_cfl_smem_bytes(const GroupView& g) {
            sizeof(float) * (size_t)g.mz * g.mx;
 }
 
-__global__ void k_stats_final(GroupView g) {
+// Per-member reduction over y (Clenshaw-Curtis weights) of the plane sums in
+// part, packed into out[e][ostride]: e_total, e_pert, tau_bottom, tau_top,
+// bulk_flux, gamma, max_div, nonfinite and, with full, the CFL number (then
+// ostride >= 9), the profiles going to g.prof.  Without full only the first
+// eight values are written and neither the profiles nor the CFL rates are read.
+__global__ void k_stats_final(GroupView g, const double* __restrict__ part, double* __restrict__ out, int ostride,
+                              int full) {
     __shared__ double red[32];
     const int e = blockIdx.x, Ny = g.ny, My = g.my;
     const double* U = g.U_t + (size_t)e * My;
     const double* W = g.W_t + (size_t)e * My;
-    double* prof = g.prof + (size_t)e * 6 * My;
+    double* prof = full ? g.prof + (size_t)e * 6 * My : nullptr;
     double ep = 0, em = 0, fl = 0, dm = 0, nf = 0, cf = 0;
     for (int j = threadIdx.x; j < My; j += blockDim.x) {
         double uu = 0, vv = 0, ww = 0, uv = 0;
         if (j > 0 && j < My - 1) {
-            const double* s = g.st_y + ((size_t)e * Ny + (j - 1)) * 6;
+            const double* s = part + ((size_t)e * Ny + (j - 1)) * 6;
             uu = s[0]; vv = s[1]; ww = s[2]; uv = s[3];
             dm = fmax(dm, s[4]);
             nf = fmax(nf, s[5]);
-            if (!g.lin) cf = fmax(cf, g.cfl_y[(size_t)e * Ny + (j - 1)]);
+            if (full && !g.lin) cf = fmax(cf, g.cfl_y[(size_t)e * Ny + (j - 1)]);
         }
         if (!isfinite(U[j]) || !isfinite(W[j])) nf = 1.0;
-        prof[0 * My + j] = U[j];
-        prof[1 * My + j] = W[j];
-        prof[2 * My + j] = uu;
-        prof[3 * My + j] = vv;
-        prof[4 * My + j] = ww;
-        prof[5 * My + j] = uv;
+        if (prof) {
+            prof[0 * My + j] = U[j];
+            prof[1 * My + j] = W[j];
+            prof[2 * My + j] = uu;
+            prof[3 * My + j] = vv;
+            prof[4 * My + j] = ww;
+            prof[5 * My + j] = uv;
+        }
         double w = g.ccw[j];
         ep += w * (uu + vv + ww);
         em += w * (U[j] * U[j] + W[j] * W[j]);
@@ -461,7 +471,7 @@ __global__ void k_stats_final(GroupView g) {
             t0 += g.D1[j] * U[j];
             t1 += g.D1[(size_t)(My - 1) * My + j] * U[j];
         }
-        double* o = g.st_out + (size_t)e * 9;
+        double* o = out + (size_t)e * ostride;
         o[0] = 0.25 * (ep + em);
         o[1] = 0.25 * ep;
         o[2] = t0;
@@ -470,7 +480,7 @@ __global__ void k_stats_final(GroupView g) {
         o[5] = g.gamma[e];
         o[6] = dm;
         o[7] = nf;
-        o[8] = cf * g.dt;
+        if (full) o[8] = cf * g.dt;
     }
 }
 
@@ -513,9 +523,15 @@ void launch_shared_mean(const GroupView& g, bool fp64, cudaStream_t st) {
 
 void launch_stats(const GroupView& g, cudaStream_t st) {
     launch_yderiv<double>(g, g.v_t, g.e_t, g.P5d, st);
-    k_stats_plane<<<dim3(g.ny, g.E), 256, 0, st>>>(g);
+    k_stats_plane<<<dim3(g.ny, g.E), 256, 0, st>>>(g, g.st_y);
     if (!g.lin) k_stats_cfl<<<dim3(g.ny, g.E), 256, stats_cfl_smem_bytes(g), st>>>(g);
-    k_stats_final<<<g.E, 128, 0, st>>>(g);
+    k_stats_final<<<g.E, 128, 0, st>>>(g, g.st_y, g.st_out, 9, 1);
+}
+
+void launch_stats_packed(const GroupView& g, double* part, double* out, cudaStream_t st) {
+    launch_yderiv<double>(g, g.v_t, g.e_t, g.P5d, st);
+    k_stats_plane<<<dim3(g.ny, g.E), 256, 0, st>>>(g, part);
+    k_stats_final<<<g.E, 128, 0, st>>>(g, part, out, 8, 0);
 }
 
 // --------------------------------------------------------------- pack/unpack
@@ -610,6 +626,14 @@ void launch_pack(const GroupView& g, int member0, int count, const double2* sv, 
 void launch_unpack(const GroupView& g, int member0, int count, double2* dv, double2* de, double* dU, double* dW,
                    cudaStream_t st) {
     k_unpack<<<transfer_ctas(), TRANSFER_THREADS, 0, st>>>(g, member0, count, dv, de, dU, dW);
+}
+
+cudaError_t load_stats_kernels() {
+    cudaFuncAttributes a;
+    cudaError_t e = cudaFuncGetAttributes(&a, (const void*)k_stats_plane);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, (const void*)k_stats_final);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, (const void*)k_yderiv<double>);
+    return e;
 }
 
 void set_attributes_spectral() {

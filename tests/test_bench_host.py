@@ -62,3 +62,38 @@ def test_byte_and_work_models_are_the_documented_counts():
     bound, flops, unit = bench.kernel_work("plane", g, "mixed")
     per = 15 * 2.5 * 4096 * 12 + 22 * 4096
     assert (bound, unit) == ("alu", "flop") and flops == pytest.approx(4 * 63 * per)
+
+
+def test_alu_peak_scales_with_the_sm_count_and_clock():
+    assert bench.alu_peak("f32", 2070.0, 152) == pytest.approx(152 * 256 * 2.07e9 / 1e12)
+    assert bench.alu_peak("f32", 1000.0, 100) == pytest.approx(100 * 256 * 1e9 / 1e12)
+    assert bench.alu_peak("f64", 2070.0, 152) == bench.FP64_NOMINAL_TFLOPS
+
+
+def test_rel_errors_per_field_and_member():
+    rng = np.random.default_rng(3)
+    E, ny, nkz, nkx, my = 3, 5, 7, 4, 7
+    v = rng.standard_normal((E, ny, nkz, nkx)) + 1j * rng.standard_normal((E, ny, nkz, nkx))
+    eta = 2.0 * v[::-1].copy()
+    U = rng.standard_normal((E, my))
+    W = 1e-3 * rng.standard_normal((E, my))
+    ref = (v, eta, U, W)
+    got = (v.copy(), eta.copy(), U.copy(), W.copy())
+    got[0][1, 2, 3, 1] += 1e-7                        # member 1, v
+    got[3][2, 4] += 1e-9                              # member 2, W00
+    r = bench.rel_errors(got, ref)
+    assert r["v"] == pytest.approx(1e-7 / np.max(np.abs(v[1])), rel=1e-6)
+    assert r["per_member"]["v"][0] == 0.0 and r["per_member"]["v"][2] == 0.0
+    assert r["eta"] == 0.0
+    scale2 = max(np.max(np.abs(U[2])), np.max(np.abs(W[2])))
+    assert r["mean_flow"] == pytest.approx(1e-9 / scale2, rel=1e-6)
+    assert r["w00_alone"] == pytest.approx(1e-9 / np.max(np.abs(W[2])), rel=1e-6)
+    lin = bench.rel_errors((got[0], got[1], None, None), (v, eta, None, None))
+    assert set(lin) == {"v", "eta", "per_member"}
+
+
+def test_config1_workload_is_the_16x33x16_couette_case():
+    wl = bench.WORKLOADS["couette16"]
+    g = wl["groups"][0]
+    assert (g["mx"], g["my"], g["mz"], g["members"], g["re"], g["dt"]) == (16, 33, 16, 1, 400.0, 0.01)
+    assert wl["noise"][0]["amp"] == 1e-2 and wl["noise"][0]["n_max"] == 2 and wl["noise"][0]["m_max"] == 2

@@ -444,13 +444,31 @@ def test_every_64x64_plane_kernel_matches_fp64(plane):
     assert np.all(err[:, :3] < 1e-6), err
 
 
-def test_channel_128x97x128_mixed_matches_fp64():
-    """Re_tau ~ 180 Poiseuille ensemble at full size (16 members, k^-5/3 noise)."""
+def test_channel_128x97x128_mixed_matches_fp64_over_50_steps():
+    """Re_tau ~ 180 Poiseuille ensemble at full size (16 members, k^-5/3 noise,
+    four member blocks), in the benchmark's launch configuration (CUDA graph,
+    autotuned kernels), mixed against FP64 over the 50-step horizon."""
     g = group("poiseuille", 128, 97, 128, 4 * np.pi, 4 * np.pi / 3, 3250.0, 0.002, 16)
     st = dns_synth.make_state(128, 97, 128, g["lx"], g["lz"], "poiseuille", 16, 5000, 1e-1, spectrum="kolmogorov")
-    ref = _run(g, st, 10, "fp64")
-    err = mixed_errors(_run(g, st, 10, "mixed"), ref)
+    ref = _run(g, st, 50, "fp64", use_graph=True)
+    err = mixed_errors(_run(g, st, 50, "mixed", use_graph=True), ref)
     assert np.all(err[:, :3] < 1e-6), err
+    assert np.all(err[:, 3] < 1e-5), err
+
+
+@pytest.mark.parametrize("pin", [{}, dict(ygemm="tc", plane="lines", helm="simt"),
+                                 dict(ygemm="tc", plane="lines", helm="tc")])
+def test_headline_64x65x64_mixed_matches_fp64_over_50_steps_in_the_benchmark_launch(pin):
+    """The benchmarked configuration itself: Poiseuille 64x65x64, 8 members (two
+    member blocks of 4, concurrent graph branches), Re = 1650, dt = 0.005, 5 %
+    noise, CUDA-graph replay, with the autotuned kernels ({}) and with the
+    variants pinned; mixed against FP64 after 50 steps, per field and member."""
+    st = _state(CFG2, 2000, 5e-2, n_max=4, m_max=4)
+    ref = _run(CFG2, st, 50, "fp64", use_graph=True)
+    err = mixed_errors(_run(CFG2, st, 50, "mixed", use_graph=True, **pin), ref)
+    assert err.shape[0] == 8
+    assert np.all(err[:, :3] < 1e-6), err
+    assert np.all(err[:, 3] < 1e-5), err
 
 
 def test_config3_long_run_ensemble_statistics_mixed_match_fp64():
