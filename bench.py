@@ -228,6 +228,16 @@ def kernel_work(cls, g, precision):
     if cls == "helm":
         npairs = nkx * (nkz // 2 + 1)
         return "alu", 2 * npairs * 2 * 2 * ny * ny * 4 * E, "flop"
+    if cls == "d2v":
+        # D2 v of the new state: 2 ny flops per real output value
+        return "alu", S * 2 * 2 * ny, "flop"
+    if cls == "spec":
+        # the fused stage: forcing (D1 phi), the implicit apply (M - I and P of
+        # both fields; the third sub-step reuses (M_1 - I) x_t), the three
+        # y-derivatives of the new state; 2 ny flops per output value of each
+        npairs = nkx * (nkz // 2 + 1)
+        apply = 2 * npairs * 2 * 2 * ny * ny * 4 * E * (5.0 / 6.0)
+        return "alu", S * 2 * 2 * ny * 4 + apply, "flop"
     return "alu", E * 4.0 * (g["my"]) ** 2, "flop"
 
 
@@ -256,6 +266,18 @@ def kernel_bytes(cls, g, precision):
         return 5 * c * S + 3 * c * S                     # 5 fields in, 3 nonlinear terms out
     if cls == "forcing":
         return 3 * c * S + 2 * c * S + 2 * c * S * (4.0 / 3.0)   # N in, F G out, RK accumulators
+    if cls == "d2v":
+        return 16 * S + 8 * S                            # v (FP64) in, D2 v (P layout) out
+    if cls == "spec":
+        # N in (P layout), the state x_t in (first two sub-steps) and x+ out
+        # (FP64), (M_1 - I) x_t out / in, the RK accumulators of F and G, the
+        # operators (all four, two in the third sub-step), five P-layout fields out
+        rp = (ny + 3) // 4 * 4
+        npairs = nkx * (nkz // 2 + 1)
+        ops = member_blocks(g) * npairs * ((4 + 4 + 2) / 3.0) * ny * rp * 4
+        state = 2 * S * (16 * (2.0 / 3.0) + 16 + 8 * (2.0 / 3.0))
+        acc = 2 * 8 * S * (4.0 / 3.0)
+        return ops + 3 * 8 * S + state + acc + 5 * 8 * S
     if cls == "helm":
         rp = (ny + 3) // 4 * 4
         npairs = nkx * (nkz // 2 + 1)
@@ -613,7 +635,8 @@ def gpu_arm(args, rank, world, dist):
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     peak = alu_peak(kprec, sm_mhz, n_sm)
     achieved = work / (kt[dom][0] / 1e3) / 1e12
-    variant = {"plane": choices[0]["plane"], "yderiv": choices[0]["ygemm"], "helm": choices[0]["helm"]}.get(dom, "simt")
+    variant = {"plane": choices[0]["plane"], "yderiv": choices[0]["ygemm"], "helm": choices[0]["helm"],
+               "spec": "fused"}.get(dom, "simt")
     traffic = (profiled_traffic(dom, variant)
                if (precision == "mixed" and args.workload == "poiseuille64") else None)
     # every class against the HBM roofline of its own algorithmic bytes (the
@@ -784,8 +807,9 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparator run")
     ap.add_argument("--plane", choices=["default", "cta", "cluster", "lines"], default="default",
                     help="plane-stage kernel (default: autotuned among those the grid supports)")
-    ap.add_argument("--helm", choices=["default", "simt", "tc", "persist"], default="default",
-                    help="implicit-apply variant of the mixed path (default: autotuned)")
+    ap.add_argument("--helm", choices=["default", "simt", "tc", "persist", "fused"], default="default",
+                    help="per-wavenumber stage of the mixed path (default: the fused stage where the group "
+                         "supports it, else the autotuned implicit apply)")
     ap.add_argument("--ygemm", choices=["default", "simt", "tc"], default="default",
                     help="y-contraction variant of the mixed path")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="poiseuille64",

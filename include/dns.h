@@ -128,11 +128,15 @@ typedef struct {
     const char* autotune_cache;    /* optional text file: autotuner decisions are read from it
                                       and appended to it ("ygemm|plane|helm Mx My Mz E choice");
                                       NULL = none */
-    int ygemm;                     /* mixed path y-derivatives: 0 autotuned at dns_bind_workspace
-                                      (both variants timed on the bound workspace, the faster
-                                      kept), 1 register-tiled FP32, 2 tcgen05 tensor cores with
-                                      split-BF16 operands (groups with My <= 66 and <= 64
-                                      members; others always use 1) */
+    int ygemm;                     /* mixed path y-derivatives of the step-by-step stage
+                                      (helm 1-3): 0 chosen at dns_bind_workspace, 1
+                                      register-tiled FP32 with D2 v summed in float-float (the
+                                      automatic choice of every DNS group: the 1e-6 budget needs
+                                      it), 2 tcgen05 tensor cores with split-BF16 operands and
+                                      FP32 accumulation (groups with My <= 66 and <= 64
+                                      members; chosen automatically, by timing, for linear
+                                      groups only; about 1e-5 of |D2 v| is lost to the
+                                      cancellation in D2's rows) */
     int plane;                     /* plane stage: 0 autotuned where several kernels exist (else
                                       the only one; FP64 defaults to 1), 1 one CTA per plane
                                       (sizes <= 64), 2 a thread-block cluster per plane (64x64
@@ -140,15 +144,19 @@ typedef struct {
                                       per plane with each 1-D transform owned by one group of
                                       threads (mixed precision, sizes <= 64); a request for a
                                       variant the group's size lacks is ignored */
-    int helm;                      /* mixed path implicit apply: 0 autotuned at
-                                      dns_bind_workspace, 1 register-tiled FP32 (one CTA per
+    int helm;                      /* mixed path per-wavenumber stage: 0 automatic (4 where the
+                                      group supports it, else the autotuner's choice of 1 or 2),
+                                      1 register-tiled FP32 implicit apply (one CTA per
                                       wavenumber pair and field), 2 tcgen05 tensor cores with
                                       split-BF16 operands (groups with My <= 66 and <= 64 members;
                                       others use 1), 3 register-tiled FP32 in persistent CTAs that
                                       copy the next pair's operators while computing the current
                                       (only on request: its grid fills the GPU, which in a step
-                                      starves concurrent member blocks; the autotuner chooses
-                                      between 1 and 2) */
+                                      starves concurrent member blocks), 4 the fused stage: one
+                                      launch per sub-step does the forcing, RK3 combination,
+                                      implicit apply, the y-derivatives of the new state and the
+                                      mean flow (DNS groups whose operators fit in shared memory:
+                                      My <= 99; linear groups use 1 or 2) */
 } dns_config;
 
 /* One-point statistics of one member (paper Sec. 4), computed from the current
@@ -284,7 +292,8 @@ const char* dns_last_error(const dns_handle* h);
 /* Kernel variants `group` uses, after the autotuner ran (i.e. after
  * dns_bind_workspace): ygemm 1 register-tiled FP32 / 2 tcgen05 y-contraction;
  * plane 1 one CTA per plane / 2 a thread-block cluster per plane / 3 line-owned
- * single CTA per plane; helm 1 register-tiled FP32 / 2 tcgen05 implicit apply.
+ * single CTA per plane; helm 1 register-tiled FP32 / 2 tcgen05 implicit apply /
+ * 3 persistent register-tiled FP32 / 4 the fused per-wavenumber stage.
  * Any output may be NULL. */
 int dns_kernel_choice(const dns_handle* h, int group, int* ygemm, int* plane, int* helm);
 
@@ -299,7 +308,10 @@ enum {
     DNS_K_FORCING = 3,     /* F, G and the RK3 combination */
     DNS_K_HELM = 4,        /* per-wavenumber implicit apply */
     DNS_K_MEAN = 5,        /* mean flow + constant-flux gamma */
-    DNS_K_NCLASS = 6
+    DNS_K_SPEC = 6,        /* fused per-wavenumber stage (helm = 4): forcing, RK3 combination,
+                              implicit apply, y-derivatives of the new state, mean flow */
+    DNS_K_D2V = 7,         /* D2 v of the new state on tensor cores (with the fused stage, My <= 66) */
+    DNS_K_NCLASS = 8
 };
 
 /* Like dns_step (never through a graph), with a CUDA event pair recorded on

@@ -38,7 +38,7 @@ EXPORTED = ["dns_create", "dns_workspace_size", "dns_bind_workspace", "dns_state
             "dns_step_timed", "dns_stats_noalloc", "dns_selftest_timeout", "dns_kernel_choice",
             "dns_convert_selftest", "dns_set_base_flow", "dns_set_direction", "dns_orthonormalize",
             "dns_optimal_sweep", "dns_set_stochastic_forcing", "dns_export_forcing", "dns_advance"]
-KERNEL_CLASSES = ["mean_deriv", "yderiv", "plane", "forcing", "helm", "mean"]
+KERNEL_CLASSES = ["mean_deriv", "yderiv", "plane", "forcing", "helm", "mean", "spec", "d2v"]
 
 
 class dns_group_desc(ctypes.Structure):
@@ -218,13 +218,13 @@ def convert_selftest(d_in, f_in):
 
 def dns_kernel_choice(h, group, which="ygemm"):
     """'ygemm' -> 'simt' | 'tc'; 'plane' -> 'cta' | 'cluster' | 'lines' | 'linear';
-    'helm' -> 'simt' | 'tc' | 'persist'."""
+    'helm' -> 'simt' | 'tc' | 'persist' | 'fused'."""
     c, p, m = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
     _ck(h, _lib.dns_kernel_choice(h, group, ctypes.byref(c), ctypes.byref(p), ctypes.byref(m)))
     if which == "plane":
         return {1: "cta", 2: "cluster", 3: "lines", 4: "linear"}.get(p.value, p.value)
     if which == "helm":
-        return {1: "simt", 2: "tc", 3: "persist"}.get(m.value, m.value)
+        return {1: "simt", 2: "tc", 3: "persist", 4: "fused"}.get(m.value, m.value)
     return {1: "simt", 2: "tc"}.get(c.value, c.value)
 
 
@@ -293,7 +293,7 @@ _YGEMM = {"default": 0, "auto": 0, "simt": 1, "tc": 2}
 _PLANE = {"default": 0, "auto": 0, "cta": 1, "cluster": 2, "lines": 3}
 
 
-_HELM = {"default": 0, "auto": 0, "simt": 1, "tc": 2, "persist": 3}
+_HELM = {"default": 0, "auto": 0, "simt": 1, "tc": 2, "persist": 3, "fused": 4}
 
 
 def _pick(table, name, what):

@@ -40,8 +40,9 @@ struct HostGroup {
     dnsb::GridOps grid;
     dnsb::CnOps ops[2];
     std::vector<double> kxt, kzt, k2t, k2inv, twx, twz, opsdev[2], mopsdev[2], D1i, D2i;
-    std::vector<float> kxtf, kztf, k2invf, twxf, twzf, opsf[2], opsfT[2], D1T, D2T;
-    std::vector<uint16_t> Atc, Htc[2];
+    std::vector<float> kxtf, kztf, k2invf, twxf, twzf, opsf[2], opsfT[2], D1T, D2T, D2Tl;
+    std::vector<uint16_t> Atc, Htc[2], D2oz;
+    std::vector<int> D2ozexp;
     std::vector<double> fstruct, flam;   // stochastic forcing: structures [NKZ][2][n][Ny], decay rates
     // stochastic forcing: a side stream for the noise kernel, forked at the start
     // of every step and joined before the first forcing assembly
@@ -137,8 +138,13 @@ size_t layout_group(dns_handle* h, HostGroup& G, size_t cur) {
     add((void**)&v.D2i, sizeof(double) * nn);
     add((void**)&v.D1T, sizeof(float) * (size_t)v.ny * v.rp);
     add((void**)&v.D2T, sizeof(float) * (size_t)v.ny * v.rp);
+    add((void**)&v.D2Tl, sizeof(float) * (size_t)v.ny * v.rp);
     add((void**)&v.status, 256);
     if (v.ygemm != 1) add((void**)&v.Atc, 3 * 128 * (size_t)v.kp * sizeof(uint16_t));
+    if (v.d2tc) {
+        add((void**)&v.D2oz, 7 * 64 * (size_t)v.kp * sizeof(uint16_t));
+        add((void**)&v.D2ozexp, 64 * sizeof(int));
+    }
     add((void**)&v.ccw, sizeof(double) * v.my);
     add((void**)&v.kxt, sizeof(double) * v.nkx);
     add((void**)&v.kzt, sizeof(double) * v.nkz);
@@ -166,6 +172,7 @@ size_t layout_group(dns_handle* h, HostGroup& G, size_t cur) {
     add((void**)&v.AU, sizeof(double) * (size_t)v.E * v.my);
     add((void**)&v.AW, sizeof(double) * (size_t)v.E * v.my);
     add((void**)&v.gamma, sizeof(double) * v.E);
+    add((void**)&v.mcnt, sizeof(int) * (size_t)v.E);
     if (!v.lin) {   // stochastic forcing (structures, one step's terms, the step counter)
         add((void**)&v.fbasis, sizeof(double) * (size_t)v.nkz * 2 * dnsk::STOCH_NEIG_MAX * v.ny);
         add((void**)&v.noise, sizeof(double2) * 2 * (size_t)v.nkz * v.ny * v.E);
@@ -268,6 +275,26 @@ void enqueue_group(dns_handle* h, HostGroup& G, cudaStream_t st, Timer* tm) {
         const double* cW = s == 0 ? g.W_t : g.W_s;
         const int sprev = (s > 0 && !g.lin) ? s - 1 : -1;   // mean-flow finish carried by the y-derivatives
         mark(-1);
+        if (precision_mixed(h) && g.helm == 4) {
+            // the derivatives of this sub-step's state came with the previous
+            // fused launch (or with the setting of the state)
+            if (g.plane == 2) dnsk::launch_plane_cl(g, false, cU, cW, st);
+            else if (g.plane == 3) dnsk::launch_plane_lines(g, cU, cW, st);
+            else dnsk::launch_plane_f32(g, cU, cW, st);
+            mark(DNS_K_PLANE);
+            if (g.shared_mean && g.E > 1) { dnsk::launch_shared_mean(g, false, st); h->launches += 1; }
+            if (s == 0 && g.fn > 0 && !side_noise) { dnsk::launch_stoch_noise(g, st); h->launches += 1; }
+            if (s == 0 && side_noise) cudaStreamWaitEvent(st, G.njoin, 0);
+            dnsk::launch_spec(g, s, st);
+            mark(DNS_K_SPEC);
+            h->launches += 2;
+            if (g.d2tc) {
+                dnsk::launch_d2v_tc(g, s == 2 ? g.v_t : g.v_s, st);
+                mark(DNS_K_D2V);
+                h->launches += 1;
+            }
+            continue;
+        }
         if (precision_mixed(h)) {
             if (g.ygemm == 2) dnsk::launch_yderiv_tc(g, cv, ce, st, sprev);
             else dnsk::launch_yderiv_t(g, cv, ce, st, sprev);
@@ -416,19 +443,25 @@ int choose_variants(dns_handle* h, const dns_config* cfg, GroupView& v, int gi) 
     const dns_group_desc& d = h->descs[gi];
     // y-contraction variant: 1 register-tiled FP32, 2 tcgen05; 0 = decided by the
     // autotuner when the workspace is bound
+    // (DNS groups: the register-tiled kernel, whose float-float D2 v keeps the
+    // 1e-6 budget; the tensor-core one only on request.  Linear groups: timed.)
     v.ygemm = 1;
     if (precision_mixed(h) && dnsk::yderiv_tc_supported(v)) {
         if (cfg->ygemm == 2) v.ygemm = 2;
-        else if (cfg->ygemm == 0) v.ygemm = 0;
+        else if (cfg->ygemm == 0 && v.lin) v.ygemm = 0;
     }
-    // implicit-apply variant: 1 register-tiled FP32, 2 tcgen05, 3 persistent
-    // register-tiled FP32 with double-buffered operator copies; 0 = autotuned
+    // per-wavenumber stage: 1 register-tiled FP32 apply, 2 tcgen05, 3 persistent
+    // register-tiled FP32 with double-buffered operator copies, 4 the fused
+    // stage; 0 = 4 where supported, else autotuned between 1 and 2
     v.helm = 1;
     if (precision_mixed(h)) {
-        if (cfg->helm == 0) v.helm = 0;
+        if (cfg->helm == 0 || cfg->helm == 4) v.helm = dnsk::spec_supported(v) ? 4 : 0;
         else if (cfg->helm == 2 && dnsk::helm_tc_supported(v)) v.helm = 2;
         else if (cfg->helm == 3) v.helm = 3;
     }
+    if (v.helm == 4) v.ygemm = 1;   // only the derivatives of a newly set state run separately
+    // with the fused stage, D2 v of each new state on tensor cores where the rows fit
+    v.d2tc = (v.helm == 4 && dnsk::d2v_tc_supported(v)) ? 1 : 0;
     // plane-stage kernel: single CTA per plane where it fits, a thread-block
     // cluster (distributed shared memory) where it does not; where both exist
     // the autotuner decides at bind time
@@ -448,6 +481,8 @@ int choose_variants(dns_handle* h, const dns_config* cfg, GroupView& v, int gi) 
         size_t m1 = dnsk::helm_t_smem_bytes(v), m2 = dnsk::yderiv_t_smem_bytes(v), m3 = dnsk::forcing_t_smem_bytes(v);
         if (helm_tc_candidate(v) && dnsk::helm_tc_smem_bytes(v) > m1) m1 = dnsk::helm_tc_smem_bytes(v);
         if (v.helm == 3 && dnsk::helm_tp_smem_bytes(v) > m1) m1 = dnsk::helm_tp_smem_bytes(v);
+        if (v.helm == 4 && dnsk::spec_smem_bytes(v) > m1) m1 = dnsk::spec_smem_bytes(v);
+        if (v.d2tc && dnsk::d2v_tc_smem_bytes(v) > m1) m1 = dnsk::d2v_tc_smem_bytes(v);
         size_t mm = m1 > m2 ? m1 : m2;
         mm = mm > m3 ? mm : m3;
         if (mm > 227 * 1024)
@@ -474,6 +509,7 @@ namespace dnsk {
 std::vector<uint16_t> yderiv_tc_a_image(const std::vector<double>& D1i, const std::vector<double>& D2i, int ny, int kp);
 std::vector<uint16_t> helm_tc_a_images(const std::vector<double>& ops, int npairs, int ny, int kp);
 void launch_wait_selftest(int* status, cudaStream_t st);
+void d2v_tc_image(const std::vector<double>& D2i, int ny, int kp, std::vector<uint16_t>& img, std::vector<int>& rexp);
 cudaError_t noalloc_scratch(double** out);
 size_t noalloc_max_partials();
 cudaError_t noalloc_prepare();
@@ -531,6 +567,7 @@ int dns_create(const dns_config* cfg, void* cuda_stream, dns_handle** out) {
             int rcv = choose_variants(h, cfg, G.v, gi);
             if (rcv) return rcv;
             if (G.v.ygemm != 1 && G.Atc.empty()) G.Atc = dnsk::yderiv_tc_a_image(G.D1i, G.D2i, G.v.ny, G.v.kp);
+            if (G.v.d2tc && G.D2oz.empty()) dnsk::d2v_tc_image(G.D2i, G.v.ny, G.v.kp, G.D2oz, G.D2ozexp);
             if (precision_mixed(h) && helm_tc_candidate(G.v) && G.Htc[0].empty())
                 for (int hi = 0; hi < 2; ++hi)
                     G.Htc[hi] = dnsk::helm_tc_a_images(G.opsdev[hi], G.v.npairs, G.v.ny, G.v.kp);
@@ -653,12 +690,16 @@ int dns_create(const dns_config* cfg, void* cuda_stream, dns_handle** out) {
             }
         G.D1T.assign((size_t)v.ny * v.rp, 0.f);
         G.D2T.assign((size_t)v.ny * v.rp, 0.f);
+        G.D2Tl.assign((size_t)v.ny * v.rp, 0.f);
         for (int r = 0; r < v.ny; ++r)
             for (int k = 0; k < v.ny; ++k) {
+                const double d2 = G.D2i[(size_t)r * v.ny + k];
                 G.D1T[(size_t)k * v.rp + r] = (float)G.D1i[(size_t)r * v.ny + k];
-                G.D2T[(size_t)k * v.rp + r] = (float)G.D2i[(size_t)r * v.ny + k];
+                G.D2T[(size_t)k * v.rp + r] = (float)d2;
+                G.D2Tl[(size_t)k * v.rp + r] = (float)(d2 - (double)(float)d2);
             }
         if (v.ygemm != 1) G.Atc = dnsk::yderiv_tc_a_image(G.D1i, G.D2i, v.ny, v.kp);
+        if (v.d2tc) dnsk::d2v_tc_image(G.D2i, v.ny, v.kp, G.D2oz, G.D2ozexp);
         if (precision_mixed(h) && helm_tc_candidate(v))
             for (int hi = 0; hi < 2; ++hi) G.Htc[hi] = dnsk::helm_tc_a_images(G.opsdev[hi], v.npairs, v.ny, v.kp);
         if (!lin) G.twx = dnsb::twiddles(d.mx);
@@ -720,6 +761,8 @@ int dns_bind_workspace(dns_handle* h, void* dev_ptr, size_t bytes) {
     dnsk::set_attributes_plane_lines();
     dnsk::set_attributes_helm_tc();
     dnsk::set_attributes_linear();
+    dnsk::set_attributes_spec();
+    dnsk::set_attributes_d2v_tc();
     {
         int rc0 = check(h, cudaGetLastError(), "kernel attributes");
         if (rc0) return rc0;
@@ -759,6 +802,9 @@ int dns_bind_workspace(dns_handle* h, void* dev_ptr, size_t bytes) {
             {v.Htc[0], G.Htc[0].data(), G.Htc[0].size() * 2},
             {v.Htc[1], G.Htc[1].data(), G.Htc[1].size() * 2},
             {v.D2T, G.D2T.data(), G.D2T.size() * 4},
+            {v.D2Tl, G.D2Tl.data(), G.D2Tl.size() * 4},
+            {v.D2oz, G.D2oz.data(), G.D2oz.size() * 2},
+            {v.D2ozexp, G.D2ozexp.data(), G.D2ozexp.size() * 4},
             {v.mops[0], G.mopsdev[0].data(), G.mopsdev[0].size() * 8},
             {v.mops[1], G.mopsdev[1].data(), G.mopsdev[1].size() * 8},
         };
@@ -927,6 +973,17 @@ static bool aligned_for_kernels(const void* v, const void* e, const void* U, con
     return ((uintptr_t)v % 16) == 0 && ((uintptr_t)e % 16) == 0 && ((uintptr_t)U % 8) == 0 && ((uintptr_t)W % 8) == 0;
 }
 
+// After the pack kernel: a group on the fused stage keeps the y-derivatives of
+// its state at time t in the per-plane arrays (every fused launch writes those
+// of the state it produces), so a newly set state gets them here.
+static int new_state_derivatives(dns_handle* h, const GroupView& v, cudaStream_t st) {
+    int rc = check(h, cudaGetLastError(), "pack state");
+    if (rc || !precision_mixed(h) || v.helm != 4) return rc;
+    dnsk::launch_yderiv_t(v, v.v_t, v.e_t, st);
+    h->launches += 1;
+    return check(h, cudaGetLastError(), "derivatives of the new state");
+}
+
 // direct: the sources are device memory or mapped host memory and the pack
 // kernel reads them itself; otherwise they are copied (kind k) into the staging
 // buffer (v, eta) and the profile rows (U, W) first.
@@ -939,7 +996,7 @@ static int set_state_block(dns_handle* h, int group, int member0, int count, con
     if (direct) {
         dnsk::launch_pack(v, member0, count, (const double2*)v_hat, (const double2*)eta_hat, v.lin ? nullptr : U00,
                           v.lin ? nullptr : W00, st);
-        return check(h, cudaGetLastError(), "pack state");
+        return new_state_derivatives(h, v, st);
     }
     const size_t per = (size_t)count * v.ny * v.nmodes;
     if ((rc = check(h, cudaMemcpyAsync(v.stage, v_hat, per * sizeof(double2), k, st), "set v"))) return rc;
@@ -953,7 +1010,7 @@ static int set_state_block(dns_handle* h, int group, int member0, int count, con
             return rc;
     }
     dnsk::launch_pack(v, member0, count, v.stage, v.stage + per, nullptr, nullptr, st);
-    return check(h, cudaGetLastError(), "pack state");
+    return new_state_derivatives(h, v, st);
 }
 
 int dns_set_state(dns_handle* h, int group, int member0, int count, const double* v_hat,

@@ -24,7 +24,8 @@ struct GroupView {
                           // single-CTA kernel (mixed path); 0 = autotune
     const void* Atc;      // tensor-core A image: [D1_int; D2_int] in 3 BF16 pieces
     int helm;             // mixed path implicit apply: 1 register-tiled FP32, 2 tcgen05, 3 persistent
-                          // register-tiled FP32 with double-buffered operator copies (0 = autotune)
+                          // register-tiled FP32 with double-buffered operator copies, 4 the fused
+                          // per-wavenumber stage (forcing, apply, y-derivatives, mean flow; 0 = autotune)
     const void* Htc[2];   // per h index: [npairs][2 fields] images of [M - I | P] in 3 BF16 pieces
     int* status;          // device error word (1: a bounded wait gave up)
     int flow;             // 0 Couette, 1 Poiseuille
@@ -55,6 +56,10 @@ struct GroupView {
     const double* D2i;    // [Ny][Ny]
     const float* D1T;     // mixed path, transposed and row-padded: D1T[k][r] = D1i[r][k], [Ny][rp]
     const float* D2T;
+    const float* D2Tl;    // D2T's residual: D2i - (double) D2T in single precision (compensated D2 v)
+    int d2tc;             // fused stage: 1 = D2 v of the new state by the tensor-core digit kernel
+    const void* D2oz;     // its image of D2: 7 slices of 7-bit digits [64 rows][kp] (BF16)
+    const int* D2ozexp;   // [64] row exponents of that image
     const double* ccw;    // [My]
     const double* kxt;    // [NKX]
     const double* kzt;    // [NKZ]
@@ -80,6 +85,7 @@ struct GroupView {
     double *dU, *dW;                 // [E][My] scratch: pre-gamma mean profiles of the sub-step
     double *uv, *wv;                 // [E][My] plane means <uv>, <wv>
     double* gamma;                   // [E]
+    int* mcnt;                       // [E] mean-flow row CTAs done in the current launch (fused stage)
     // P layout work arrays (element type by precision)
     void* P5;    // 5 fields: v, Dv, D2v, eta, Deta
     void* N3;    // 3 fields: Nu, Nv, Nw
@@ -146,6 +152,16 @@ void set_attributes_helm_tc();
 bool launch_plane_cl(const GroupView& g, bool fp64, const double* U, const double* W, cudaStream_t st);
 size_t plane_cl_smem_bytes(int mx, int mz, bool fp64);
 void set_attributes_plane_cl();
+// D2 v on tensor cores with exact digit accumulation (k_d2v_tc.cu), Ny <= 64
+bool d2v_tc_supported(const GroupView& g);
+size_t d2v_tc_smem_bytes(const GroupView& g);
+void launch_d2v_tc(const GroupView& g, const double2* v, cudaStream_t st);
+void set_attributes_d2v_tc();
+// fused per-wavenumber stage of the mixed path (k_spec.cu)
+bool spec_supported(const GroupView& g);
+size_t spec_smem_bytes(const GroupView& g);
+void launch_spec(const GroupView& g, int s, cudaStream_t st);
+void set_attributes_spec();
 void launch_stats(const GroupView& g, cudaStream_t st);
 // the statistics without profiles and CFL: per-plane sums into part [E][Ny][6],
 // packed values into out [E][8]

@@ -26,6 +26,16 @@ __device__ __forceinline__ void ff_add_prod(float& hi, float& lo, float a, float
     ff_add(hi, lo, p, pe);
 }
 
+// (hi, lo) += (a + al) * (b + bl) for operands held as single-precision
+// pairs (|al| <= ulp(a) / 2, |bl| <= ulp(b) / 2): the leading product exactly
+// as above, the two cross terms into lo (their own rounding is far below
+// single precision of the sum); al * bl is dropped
+__device__ __forceinline__ void ff_add_prod2(float& hi, float& lo, float a, float b, float al, float bl) {
+    ff_add_prod(hi, lo, a, b);
+    lo = __fmaf_rn(a, bl, lo);
+    lo = __fmaf_rn(al, b, lo);
+}
+
 // butterfly over the warp; lane 0's result is used (a fixed order)
 __device__ __forceinline__ void ff_warp_sum(float& hi, float& lo) {
 #pragma unroll

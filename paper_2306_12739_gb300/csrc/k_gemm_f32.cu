@@ -11,6 +11,7 @@
 //               by one TMA bulk copy (cp.async.bulk + mbarrier) per CTA.
 #include "dns_internal.hpp"
 #include "cvt.cuh"
+#include "ff.cuh"
 #include "mean.cuh"
 
 namespace dnsk {
@@ -45,24 +46,47 @@ __host__ __device__ inline Tile tile_of(int E, int ny, int nm) {
 
 // --------------------------------------------------------------- y-derivs
 
+// Tile of the y-derivative kernel: tile_of's, with fewer columns while the
+// shared memory would pass YD_SMEM_MAX; the residual of D2 is staged in shared
+// memory when it fits beside the tile, else read from global memory (L1).
+constexpr size_t YD_SMEM_MAX = 200 * 1024;
+__host__ __device__ inline size_t yd_bytes(int ny, int rp, int nc, bool stage_d2l) {
+    return ((size_t)(stage_d2l ? 3 : 2) * ny * rp + 3 * (size_t)ny * 2 * nc) * sizeof(float);
+}
+__host__ __device__ inline Tile yd_tile(int E, int ny, int rp, int nm) {
+    Tile t = tile_of(E, ny, nm);
+    while (yd_bytes(ny, rp, t.NC, false) > YD_SMEM_MAX && t.NC > 4) {
+        if (t.QT > 1) t.QT /= 2;
+        else t.EBT = (t.EBT + 1) / 2;
+        t.NC = t.QT * t.EBT;
+    }
+    return t;
+}
+__host__ __device__ inline bool yd_stage_d2l(int ny, int rp, int nc) { return yd_bytes(ny, rp, nc, true) <= YD_SMEM_MAX; }
+
 __global__ void __launch_bounds__(THREADS) k_yderiv_t(GroupView g, const double2* __restrict__ V,
                                                      const double2* __restrict__ H, int sprev) {
     extern __shared__ __align__(16) unsigned char sm[];
     const int Ny = g.ny, RP = g.rp, E = g.E, NM = g.nmodes;
-    const Tile T = tile_of(E, Ny, NM);
+    const Tile T = yd_tile(E, Ny, RP, NM);
+    const bool stage_d2l = yd_stage_d2l(Ny, RP, T.NC);
     if (mean_finish_rows(g, sprev, (E + T.EBT - 1) / T.EBT, sm)) return;
     const int q0 = blockIdx.x * T.QT, e0 = blockIdx.y * T.EBT;
     const int NCR = 2 * T.NC;                       // real columns
     float* D1 = (float*)sm;                         // [Ny][RP]
     float* D2 = D1 + Ny * RP;
-    float* Xv = D2 + Ny * RP;                       // [Ny][NCR], column = 2 (el QT + qq) + c
-    float* Xe = Xv + Ny * NCR;
+    float* D2ls = D2 + Ny * RP;                     // residual of D2 (compensated D2 v)
+    float* Xv = D2ls + (stage_d2l ? Ny * RP : 0);   // [Ny][NCR], column = 2 (el QT + qq) + c
+    float* Xvl = Xv + Ny * NCR;                     // residual of v: v - (double) Xv
+    float* Xe = Xvl + Ny * NCR;
     {
         const float4* s1 = (const float4*)g.D1T;
         const float4* s2 = (const float4*)g.D2T;
+        const float4* s3 = (const float4*)g.D2Tl;
         for (int i = threadIdx.x; i < Ny * RP / 4; i += THREADS) {
             ((float4*)D1)[i] = s1[i];
             ((float4*)D2)[i] = s2[i];
+            if (stage_d2l) ((float4*)D2ls)[i] = s3[i];
         }
         // state tile, read in H order [q][y][e], written [y][(el QT + qq)]
         const int per_q = Ny * T.EBT;
@@ -78,7 +102,9 @@ __global__ void __launch_bounds__(THREADS) k_yderiv_t(GroupView g, const double2
                 b = H[o];
             }
             const int c = 2 * (el * T.QT + qq);
-            *(float2*)&Xv[k * NCR + c] = make_float2((float)a.x, (float)a.y);
+            const float2 ah = make_float2((float)a.x, (float)a.y);
+            *(float2*)&Xv[k * NCR + c] = ah;
+            *(float2*)&Xvl[k * NCR + c] = make_float2((float)(a.x - (double)ah.x), (float)(a.y - (double)ah.y));
             *(float2*)&Xe[k * NCR + c] = make_float2((float)b.x, (float)b.y);
         }
     }
@@ -86,23 +112,34 @@ __global__ void __launch_bounds__(THREADS) k_yderiv_t(GroupView g, const double2
     const size_t fs = (size_t)Ny * E * NM;
     float2* P = (float2*)g.P5;
     const int RB = RP / 4;
+    const float* D2l = stage_d2l ? D2ls : g.D2Tl;
     const FastDiv dNC((unsigned)T.NC), dQT((unsigned)T.QT);
     for (int m = threadIdx.x; m < RB * T.NC; m += THREADS) {
         const int rb = (int)dNC.div((unsigned)m), j = m - rb * T.NC;   // consecutive threads: consecutive q
         const int r0 = 4 * rb;
         float4 av[2] = {make_float4(0, 0, 0, 0), make_float4(0, 0, 0, 0)};   // D1 v: re, im
-        float4 bv[2] = {make_float4(0, 0, 0, 0), make_float4(0, 0, 0, 0)};   // D2 v
+        float bh[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};         // D2 v, float-float
+        float bl[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
         float4 ae[2] = {make_float4(0, 0, 0, 0), make_float4(0, 0, 0, 0)};   // D1 eta
-#pragma unroll 4
+#pragma unroll 2
         for (int k = 0; k < Ny; ++k) {
             const float4 d1 = *(const float4*)&D1[k * RP + r0];
             const float4 d2 = *(const float4*)&D2[k * RP + r0];
+            const float4 d2r = *(const float4*)&D2l[k * RP + r0];
             const float2 x = *(const float2*)&Xv[k * NCR + 2 * j];
+            const float2 xl = *(const float2*)&Xvl[k * NCR + 2 * j];
             const float2 h = *(const float2*)&Xe[k * NCR + 2 * j];
             av[0].x += d1.x * x.x; av[0].y += d1.y * x.x; av[0].z += d1.z * x.x; av[0].w += d1.w * x.x;
             av[1].x += d1.x * x.y; av[1].y += d1.y * x.y; av[1].z += d1.z * x.y; av[1].w += d1.w * x.y;
-            bv[0].x += d2.x * x.x; bv[0].y += d2.y * x.x; bv[0].z += d2.z * x.x; bv[0].w += d2.w * x.x;
-            bv[1].x += d2.x * x.y; bv[1].y += d2.y * x.y; bv[1].z += d2.z * x.y; bv[1].w += d2.w * x.y;
+            // D2 v: the collocation D2 has entries up to ~N^4 / 10 that cancel in every
+            // row, so a single-precision sum would lose ~1e-5 of |D2 v|: D2 and v
+            // are held as single-precision pairs and the sum is compensated
+            const float dh[4] = {d2.x, d2.y, d2.z, d2.w}, dl[4] = {d2r.x, d2r.y, d2r.z, d2r.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                ff_add_prod2(bh[0][i], bl[0][i], dh[i], x.x, dl[i], xl.x);
+                ff_add_prod2(bh[1][i], bl[1][i], dh[i], x.y, dl[i], xl.y);
+            }
             ae[0].x += d1.x * h.x; ae[0].y += d1.y * h.x; ae[0].z += d1.z * h.x; ae[0].w += d1.w * h.x;
             ae[1].x += d1.x * h.y; ae[1].y += d1.y * h.y; ae[1].z += d1.z * h.y; ae[1].w += d1.w * h.y;
         }
@@ -110,7 +147,12 @@ __global__ void __launch_bounds__(THREADS) k_yderiv_t(GroupView g, const double2
         const int q = q0 + qq, e = e0 + el;
         if (q >= NM || e >= E) continue;
         const float r_av[2][4] = {{av[0].x, av[0].y, av[0].z, av[0].w}, {av[1].x, av[1].y, av[1].z, av[1].w}};
-        const float r_bv[2][4] = {{bv[0].x, bv[0].y, bv[0].z, bv[0].w}, {bv[1].x, bv[1].y, bv[1].z, bv[1].w}};
+        float r_bv[2][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            r_bv[0][i] = __fadd_rn(bh[0][i], bl[0][i]);
+            r_bv[1][i] = __fadd_rn(bh[1][i], bl[1][i]);
+        }
         const float r_ae[2][4] = {{ae[0].x, ae[0].y, ae[0].z, ae[0].w}, {ae[1].x, ae[1].y, ae[1].z, ae[1].w}};
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
@@ -534,8 +576,8 @@ size_t helm_t_smem_bytes(const GroupView& g) {
 }
 
 size_t yderiv_t_smem_bytes(const GroupView& g) {
-    gt::Tile t = gt::tile_of(g.E, g.ny, g.nmodes);
-    return (2 * (size_t)g.ny * g.rp + 2 * (size_t)g.ny * 2 * t.NC) * sizeof(float);
+    gt::Tile t = gt::yd_tile(g.E, g.ny, g.rp, g.nmodes);
+    return gt::yd_bytes(g.ny, g.rp, t.NC, gt::yd_stage_d2l(g.ny, g.rp, t.NC));
 }
 
 size_t forcing_t_smem_bytes(const GroupView& g) {
@@ -544,7 +586,7 @@ size_t forcing_t_smem_bytes(const GroupView& g) {
 }
 
 void launch_yderiv_t(const GroupView& g, const double2* v, const double2* e, cudaStream_t st, int sprev) {
-    gt::Tile t = gt::tile_of(g.E, g.ny, g.nmodes);
+    gt::Tile t = gt::yd_tile(g.E, g.ny, g.rp, g.nmodes);
     dim3 grid((g.nmodes + t.QT - 1) / t.QT, (g.E + t.EBT - 1) / t.EBT);
     grid.y += mean_finish_extra_rows(g, grid.x, sprev);
     gt::k_yderiv_t<<<grid, gt::THREADS, yderiv_t_smem_bytes(g), st>>>(g, v, e, sprev);

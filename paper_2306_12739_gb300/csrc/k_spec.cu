@@ -1,0 +1,508 @@
+// Fused per-wavenumber stage of the mixed path: everything of one sub-step
+// that follows the physical-space stage, in one launch (paper Sec. 3.1-3.2):
+//   forcing     F = -k^2 Nv - D1 (i kx Nu + i kz Nw),  G = i kz Nu - i kx Nw
+//               (Eqs. Dv, eta) and the RK3 combination F~, G~ of the sub-step;
+//   implicit    x+ = x_t + ((M_h - I) x_t + P_h F~)  per wavenumber pair
+//   apply       (increment form of Eqs. CN1, CN2; the increment in single
+//               precision, one double add);
+//   derivatives Dv, D2v, D eta of the new state, written in the per-plane
+//               layout the next physical-space stage reads (so the next
+//               sub-step, or the next step, starts with the transforms);
+//   mean flow   the rows of the mean-flow update (Eqs. CN3, CN4) in leading
+//               CTAs, the last of a member's row CTAs finishing it (constant-
+//               flux gamma, profiles, RK accumulators of <uv>, <wv>).
+// One CTA per (wavenumber pair (n, |m|), member chunk): both modes +-m and
+// both fields.  The pair's four operators and D1 arrive by TMA bulk copies (the
+// third sub-step needs only the P matrices); D2 and its residual are copied
+// over the eta operators once those are used.  The CTA's 256 threads run the
+// stages in four phases separated by barriers; in the two middle phases the
+// two halves of the CTA work on v and eta side by side.
+//
+// D2 v needs more than single precision: the collocation D2 has entries up to
+// ~N^4/10 that cancel in every row, so a single-precision sum (or any FP32-
+// accumulated split tensor-core product) loses ~1e-5 of |D2 v|.  Where Ny <= 64
+// the tensor-core digit kernel (k_d2v_tc.cu, exact accumulation) computes it
+// from the new FP64 state after this launch; otherwise this kernel sums it in
+// float-float: D2 and v are held as pairs of single-precision numbers and every
+// product enters a compensated sum (TwoSum, the FMA product residual, the cross
+// terms into the low part).
+#include "dns_internal.hpp"
+#include "cvt.cuh"
+#include "ff.cuh"
+#include "mean.cuh"
+
+namespace dnsk {
+
+namespace spc {
+
+constexpr int THREADS = 256;
+constexpr int HALF = THREADS / 2;
+constexpr int NCR_MAX = 32;   // real columns per CTA (modes x members x re/im)
+
+// Member chunk: at most NCR_MAX real columns per CTA (two modes, re and im).
+__host__ __device__ inline int chunk_members(const GroupView& g) {
+    const int ec = NCR_MAX / 4;
+    return g.E < ec ? g.E : ec;
+}
+__host__ __device__ inline int chunks(const GroupView& g) {
+    const int ec = chunk_members(g);
+    return (g.E + ec - 1) / ec;
+}
+// row stride (floats) of the shared-memory vectors: the chunk's real columns
+__host__ __device__ inline int vec_stride(const GroupView& g) { return 4 * chunk_members(g); }
+__host__ __device__ inline size_t vec_floats(const GroupView& g) { return (size_t)g.ny * vec_stride(g); }
+// shared memory: operators [4][Ny][RP] (the eta pair reused for D2 and its
+// residual after phase 2) | D1 [Ny][RP] | 7 vectors [Ny][vec_stride] | 2 mbarriers
+__host__ __device__ inline size_t smem_bytes(const GroupView& g) {
+    return (5 * (size_t)g.ny * g.rp + 7 * vec_floats(g)) * sizeof(float) + 32;
+}
+
+__device__ __forceinline__ unsigned su32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ bool waitp(unsigned bar, unsigned parity) {
+    for (int it = 0; it < (1 << 22); ++it) {
+        unsigned done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done) : "r"(bar), "r"(parity) : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void bulk(void* dst, const void* src, unsigned bytes, unsigned bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(su32(dst)), "l"(src), "r"(bytes), "r"(bar) : "memory");
+}
+
+// Finish of a member's mean-flow update after its last row CTA (see
+// mean_finish): gamma, the profiles, the RK accumulators of <uv>, <wv>.  The
+// pre-gamma rows dU, dW were written by other CTAs of this launch: they are
+// read through L2.
+__device__ void finish_member(const GroupView& g, int s, int e, unsigned char* sm) {
+    const int Ny = g.ny, My = g.my;
+    double* red = (double*)sm;
+    const int hi = (s == 0) ? 0 : 1;
+    const double* Ug = g.mops[hi] + 2 * (size_t)Ny * Ny + 2 * (size_t)Ny;
+    const double* Un = g.dU + (size_t)e * My;
+    const double* Wn = g.dW + (size_t)e * My;
+    const double* Ut = g.U_t + (size_t)e * My;
+    const double* Wt = g.W_t + (size_t)e * My;
+    double gam = 0.0;
+    if (g.flow == 1) {
+        double fl = 0.0, fg = 0.0;
+        for (int j = threadIdx.x; j < My; j += blockDim.x)
+            fl += g.ccw[j] * ((j > 0 && j < My - 1) ? __ldcg(Un + j) : Ut[j]);
+        for (int i = threadIdx.x; i < Ny; i += blockDim.x) fg += g.ccw[i + 1] * Ug[i];
+        fl = block_sum(fl, red);
+        fg = block_sum(fg, red);
+        gam = (g.bulk_flux - fl) / fg;
+    }
+    double* Uo = (s == 2) ? (g.U_t + (size_t)e * My) : (g.U_s + (size_t)e * My);
+    double* Wo = (s == 2) ? (g.W_t + (size_t)e * My) : (g.W_s + (size_t)e * My);
+    const double u0 = Ut[0], u1 = Ut[My - 1], w0 = Wt[0], w1 = Wt[My - 1];
+    __syncthreads();
+    for (int j = threadIdx.x; j < My; j += blockDim.x) {
+        const bool wall = (j == 0 || j == My - 1);
+        Uo[j] = wall ? (j == 0 ? u0 : u1) : __ldcg(Un + j) + gam * Ug[j - 1];
+        Wo[j] = wall ? (j == 0 ? w0 : w1) : __ldcg(Wn + j);
+        const size_t o = (size_t)e * My + j;
+        if (s == 0) {
+            g.AU[o] = g.uv[o];
+            g.AW[o] = g.wv[o];
+        } else if (s == 1) {
+            g.AU[o] = (1.0 / 6.0) * g.AU[o] + (4.0 / 6.0) * g.uv[o];
+            g.AW[o] = (1.0 / 6.0) * g.AW[o] + (4.0 / 6.0) * g.wv[o];
+        }
+    }
+    if (threadIdx.x == 0) g.gamma[e] = gam;
+}
+
+// Rows of the mean-flow update (one warp per interior row), then the member's
+// finish by whichever of its row CTAs completes last (a counter per member,
+// reset by that CTA for the next launch).
+__device__ void mean_cta(const GroupView& g, int s, int b, unsigned char* sm) {
+    const int E = g.E, per = (g.ny + 7) / 8;
+    const int e = b % E, r = b / E;
+    mean_rows(g, s, e, r * (THREADS / 32), sm);
+    __shared__ int last;
+    __threadfence();        // this CTA's rows are visible device-wide before it counts itself
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(&g.mcnt[e], 1) == per - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    finish_member(g, s, e, sm);
+    if (threadIdx.x == 0) g.mcnt[e] = 0;
+}
+
+// Columns of a CTA: j = which * ec + el (which 0: mode +m, 1: mode -m; el the
+// member in the chunk), real column 2 j + c.
+struct Cols {
+    int p, n, am, nq, q1, q2, e0, ec, C;
+};
+
+__device__ __forceinline__ int col_q(const Cols& c, int j) { return j < c.ec ? c.q1 : c.q2; }
+__device__ __forceinline__ int col_e(const Cols& c, int j) { return c.e0 + (j < c.ec ? j : j - c.ec); }
+
+// 4-row x 1-complex-column products of two transposed operators with two
+// right-hand sides: a = A x, b = B y (rows r0..r0+3, shared memory operands)
+__device__ __forceinline__ void mm2(const float* A, const float* B, const float* X, const float* Y, int Ny, int RP,
+                                    int VS, int r0, int c2, bool needA, float (&a)[2][4], float (&b)[2][4]) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) { a[0][i] = a[1][i] = b[0][i] = b[1][i] = 0.f; }
+#pragma unroll 4
+    for (int k = 0; k < Ny; ++k) {
+        const float4 bk = *(const float4*)&B[k * RP + r0];
+        const float2 yk = *(const float2*)&Y[k * VS + c2];
+        b[0][0] += bk.x * yk.x; b[0][1] += bk.y * yk.x; b[0][2] += bk.z * yk.x; b[0][3] += bk.w * yk.x;
+        b[1][0] += bk.x * yk.y; b[1][1] += bk.y * yk.y; b[1][2] += bk.z * yk.y; b[1][3] += bk.w * yk.y;
+        if (needA) {
+            const float4 ak = *(const float4*)&A[k * RP + r0];
+            const float2 xk = *(const float2*)&X[k * VS + c2];
+            a[0][0] += ak.x * xk.x; a[0][1] += ak.y * xk.x; a[0][2] += ak.z * xk.x; a[0][3] += ak.w * xk.x;
+            a[1][0] += ak.x * xk.y; a[1][1] += ak.y * xk.y; a[1][2] += ak.z * xk.y; a[1][3] += ak.w * xk.y;
+        }
+    }
+}
+
+// 4-row x 1-complex-column product of D1 (transposed [k][RP]) with a
+// right-hand side, both in shared memory
+__device__ __forceinline__ void d1mm(const float* D1T, const float* X, int Ny, int RP, int VS, int r0, int c2,
+                                     float (&a)[2][4]) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) a[0][i] = a[1][i] = 0.f;
+#pragma unroll 4
+    for (int k = 0; k < Ny; ++k) {
+        const float4 d = *(const float4*)&D1T[k * RP + r0];
+        const float2 x = *(const float2*)&X[k * VS + c2];
+        a[0][0] += d.x * x.x; a[0][1] += d.y * x.x; a[0][2] += d.z * x.x; a[0][3] += d.w * x.x;
+        a[1][0] += d.x * x.y; a[1][1] += d.y * x.y; a[1][2] += d.z * x.y; a[1][3] += d.w * x.y;
+    }
+}
+
+// The implicit apply of one field for a 4-row x 1-complex-column task: reads
+// x_t (FP64) and, in the third sub-step, the stored (M_1 - I) x_t; writes x+
+// (FP64; over x_t in the third sub-step), (M_1 - I) x_t in the second, and the
+// single-precision x+ (hi, and lo when lo_out) into shared memory.
+__device__ __forceinline__ void apply_epilogue(const GroupView& g, int s, int f, const Cols& c, int r0, int j,
+                                               const float (&ma)[2][4], const float (&pa)[2][4], float* hi_out,
+                                               float* lo_out) {
+    const int Ny = g.ny, E = g.E, VS = vec_stride(g);
+    const int q = col_q(c, j), e = col_e(c, j);
+    const double2* X = f == 0 ? g.v_t : g.e_t;
+    float2* M1 = (float2*)(f == 0 ? g.mx1_v : g.mx1_e);
+    double2* O = (s == 2) ? (f == 0 ? g.v_t : g.e_t) : (f == 0 ? g.v_s : g.e_s);
+    double2 x[4];
+    float2 m1[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int y = r0 + i;
+        if (y >= Ny) break;
+        const size_t o = ((size_t)q * Ny + y) * E + e;
+        x[i] = X[o];
+        m1[i] = (s == 2) ? M1[o] : make_float2(ma[0][i], ma[1][i]);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int y = r0 + i;
+        if (y >= Ny) break;
+        const size_t o = ((size_t)q * Ny + y) * E + e;
+        if (s == 1) M1[o] = m1[i];
+        const double2 xn = make_double2(x[i].x + f2d(m1[i].x + pa[0][i]), x[i].y + f2d(m1[i].y + pa[1][i]));
+        O[o] = xn;
+        const float hx = d2f(xn.x), hy = d2f(xn.y);
+        *(float2*)&hi_out[y * VS + 2 * j] = make_float2(hx, hy);
+        if (lo_out)
+            *(float2*)&lo_out[y * VS + 2 * j] = make_float2(d2f(xn.x - f2d(hx)), d2f(xn.y - f2d(hy)));
+    }
+}
+
+__global__ void __launch_bounds__(THREADS, 2) k_spec(GroupView g, int s) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    const int nrow = mean_row_ctas(g);
+    if ((int)blockIdx.x < nrow) {
+        mean_cta(g, s, blockIdx.x, sm);
+        return;
+    }
+    const int Ny = g.ny, RP = g.rp, E = g.E, NM = g.nmodes, NKX = g.nkx, VS = vec_stride(g);
+    const int b = blockIdx.x - nrow;
+    const int np1 = g.npairs - 1;                 // pair 0 is the mean mode: no CTA
+    Cols c;
+    c.p = 1 + b % np1;
+    const int ch = b / np1;
+    c.n = c.p % NKX;
+    c.am = c.p / NKX;
+    c.nq = c.am > 0 ? 2 : 1;
+    c.q1 = (g.kz + c.am) * NKX + c.n;
+    c.q2 = (g.kz - c.am) * NKX + c.n;
+    const int EC = chunk_members(g);
+    c.e0 = ch * EC;
+    c.ec = min(EC, E - c.e0);
+    c.C = c.nq * c.ec;
+    const size_t mat = (size_t)Ny * RP;
+    float* OPS = (float*)sm;                      // [4][Ny][RP]: (Mv-I)^T, Pv^T, (Me-I)^T, Pe^T;
+                                                  // after phase 2: D2^T, its residual in the last two
+    float* D1S = OPS + 4 * mat;                   // D1^T [Ny][RP]
+    float* PH = D1S + mat;                        // phi, then v+ (hi)
+    float* KV = PH + vec_floats(g);               // -k^2 Nv (+ noise), then v+ (lo)
+    float* GT = KV + vec_floats(g);               // G~
+    float* XV = GT + vec_floats(g);               // x_t of v (single precision)
+    float* XE = XV + vec_floats(g);               // x_t of eta
+    float* FT = XE + vec_floats(g);               // F~
+    float* EN = FT + vec_floats(g);               // eta+ (single precision)
+    unsigned long long* bar = (unsigned long long*)(EN + vec_floats(g));
+    const unsigned bar_a = su32(bar), bar_d = su32(bar + 1);
+    const int tid = threadIdx.x;
+    const bool needM = (s != 2);
+    const int hidx = (s == 0) ? 0 : 1;
+
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_a) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_d) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (tid == 0) {
+        const float* src = g.opsfT[hidx] + (size_t)c.p * 4 * mat;
+        const unsigned mb = (unsigned)(mat * sizeof(float));
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_a),
+                     "r"(needM ? 5 * mb : 3 * mb) : "memory");
+        bulk(D1S, g.D1T, mb, bar_a);
+        if (needM) {
+            bulk(OPS, src, 4 * mb, bar_a);
+        } else {
+            bulk(OPS + mat, src + mat, mb, bar_a);
+            bulk(OPS + 3 * mat, src + 3 * mat, mb, bar_a);
+        }
+    }
+
+    // ---- phase 1: nonlinear terms of the pair's modes (per-plane layout) ->
+    // phi, -k^2 Nv, G~ (with its RK accumulator); x_t in single precision
+    {
+        const size_t fs = (size_t)Ny * E * NM;
+        const float2* N3 = (const float2*)g.N3;
+        float2* Ae = (float2*)g.Ae;
+        const int total = Ny * c.C;
+        const float kx = g.kxtf[c.n];
+        const bool forced = g.fn > 0 && c.n == g.fn;
+        for (int i = tid; i < total; i += THREADS) {
+            const int y = i / c.C, j = i - y * c.C;
+            const int q = col_q(c, j), e = col_e(c, j);
+            const float kz = g.kztf[q / NKX];
+            const size_t op = ((size_t)y * E + e) * NM + q;
+            const size_t oh = ((size_t)q * Ny + y) * E + e;
+            const float2 nu = N3[op], nv = N3[fs + op], nw = N3[2 * fs + op];
+            float2 ae = make_float2(0.f, 0.f);
+            if (s != 0) ae = Ae[oh];
+            double2 xv = make_double2(0.0, 0.0), xe = xv;
+            if (needM) {
+                xv = g.v_t[oh];
+                xe = g.e_t[oh];
+            }
+            const float k2 = kx * kx + kz * kz;
+            const float ax = kx * nu.x + kz * nw.x, ay = kx * nu.y + kz * nw.y;   // i kx Nu + i kz Nw
+            const float bx = kz * nu.x - kx * nw.x, by = kz * nu.y - kx * nw.y;   // i kz Nu - i kx Nw
+            float2 kv = make_float2(-k2 * nv.x, -k2 * nv.y);
+            float2 G = make_float2(-by, bx);
+            if (forced) {
+                const size_t o = ((size_t)(q / NKX) * Ny + y) * E + e, half = (size_t)g.nkz * Ny * E;
+                kv.x += (float)g.noise[o].x; kv.y += (float)g.noise[o].y;
+                G.x += (float)g.noise[half + o].x; G.y += (float)g.noise[half + o].y;
+            }
+            float2 Gt;
+            if (s == 0) {
+                Gt = G;
+                Ae[oh] = G;
+            } else if (s == 1) {
+                Gt = make_float2(2.f * G.x - ae.x, 2.f * G.y - ae.y);
+                Ae[oh] = make_float2((1.f / 6.f) * ae.x + (4.f / 6.f) * G.x, (1.f / 6.f) * ae.y + (4.f / 6.f) * G.y);
+            } else {
+                Gt = make_float2(ae.x + (1.f / 6.f) * G.x, ae.y + (1.f / 6.f) * G.y);
+            }
+            const int so = y * VS + 2 * j;
+            *(float2*)&PH[so] = make_float2(-ay, ax);
+            *(float2*)&KV[so] = kv;
+            *(float2*)&GT[so] = Gt;
+            if (needM) {
+                *(float2*)&XV[so] = make_float2(d2f(xv.x), d2f(xv.y));
+                *(float2*)&XE[so] = make_float2(d2f(xe.x), d2f(xe.y));
+            }
+        }
+    }
+    __syncthreads();
+    // every thread waits for the operators (bounded); on a timeout the CTA
+    // latches the status word, waits once more for the copy and leaves
+    if (!__syncthreads_and(waitp(bar_a, 0))) {
+        if (tid == 0) {
+            atomicExch(g.status, 1);
+            waitp(bar_a, 0);
+        }
+        return;
+    }
+    const int RB = (Ny + 3) / 4, ntask = RB * c.C;
+    const size_t fs5 = (size_t)Ny * E * NM;
+    float2* P5 = (float2*)g.P5;
+
+    // ---- phase 2: F~ (threads 0..127) | eta+ (threads 128..255)
+    if (tid < HALF) {
+        float2* Av = (float2*)g.Av;
+        for (int t = tid; t < ntask; t += HALF) {
+            const int rb = t / c.C, j = t - rb * c.C, r0 = 4 * rb;
+            float a[2][4];
+            d1mm(D1S, PH, Ny, RP, VS, r0, 2 * j, a);
+            const int q = col_q(c, j), e = col_e(c, j);
+            float2 pav[4];
+            if (s != 0) {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int y = r0 + i;
+                    if (y >= Ny) break;
+                    pav[i] = Av[((size_t)q * Ny + y) * E + e];
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int y = r0 + i;
+                if (y >= Ny) break;
+                const float2 kv = *(const float2*)&KV[y * VS + 2 * j];
+                const float2 F = make_float2(kv.x - a[0][i], kv.y - a[1][i]);
+                const size_t oh = ((size_t)q * Ny + y) * E + e;
+                float2 Ft;
+                if (s == 0) {
+                    Ft = F;
+                    Av[oh] = F;
+                } else if (s == 1) {
+                    const float2 pa = pav[i];
+                    Ft = make_float2(2.f * F.x - pa.x, 2.f * F.y - pa.y);
+                    Av[oh] = make_float2((1.f / 6.f) * pa.x + (4.f / 6.f) * F.x, (1.f / 6.f) * pa.y + (4.f / 6.f) * F.y);
+                } else {
+                    const float2 pa = pav[i];
+                    Ft = make_float2(pa.x + (1.f / 6.f) * F.x, pa.y + (1.f / 6.f) * F.y);
+                }
+                *(float2*)&FT[y * VS + 2 * j] = Ft;
+            }
+        }
+    } else {
+        for (int t = tid - HALF; t < ntask; t += HALF) {
+            const int rb = t / c.C, j = t - rb * c.C, r0 = 4 * rb;
+            float ma[2][4], pa[2][4];
+            mm2(OPS + 2 * mat, OPS + 3 * mat, XE, GT, Ny, RP, VS, r0, 2 * j, needM, ma, pa);
+            apply_epilogue(g, s, 1, c, r0, j, ma, pa, EN, nullptr);
+        }
+    }
+    __syncthreads();
+    // the eta operators are no longer read: D2^T and its residual go there
+    // (the generic-proxy reads of phase 2 ordered before the async-proxy writes)
+    const bool d2here = !g.d2tc;     // else D2 v comes from the tensor-core digit kernel
+    if (tid == 0 && d2here) {
+        const unsigned mb = (unsigned)(mat * sizeof(float));
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_d), "r"(2 * mb) : "memory");
+        bulk(OPS + 2 * mat, g.D2T, mb, bar_d);
+        bulk(OPS + 3 * mat, g.D2Tl, mb, bar_d);
+    }
+
+    // ---- phase 3: v+ (threads 0..127) | D eta and the eta planes (threads 128..255)
+    if (tid < HALF) {
+        for (int t = tid; t < ntask; t += HALF) {
+            const int rb = t / c.C, j = t - rb * c.C, r0 = 4 * rb;
+            float ma[2][4], pa[2][4];
+            mm2(OPS, OPS + mat, XV, FT, Ny, RP, VS, r0, 2 * j, needM, ma, pa);
+            // v+ hi, lo over phi and -k^2 Nv (read by phase 2 only)
+            apply_epilogue(g, s, 0, c, r0, j, ma, pa, PH, d2here ? KV : nullptr);
+        }
+    } else {
+        for (int t = tid - HALF; t < ntask; t += HALF) {
+            const int rb = t / c.C, j = t - rb * c.C, r0 = 4 * rb;
+            float a[2][4];
+            d1mm(D1S, EN, Ny, RP, VS, r0, 2 * j, a);
+            const int q = col_q(c, j), e = col_e(c, j);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int y = r0 + i;
+                if (y >= Ny) break;
+                const size_t o = ((size_t)y * E + e) * NM + q;
+                P5[3 * fs5 + o] = *(const float2*)&EN[y * VS + 2 * j];
+                P5[4 * fs5 + o] = make_float2(a[0][i], a[1][i]);
+            }
+        }
+    }
+    __syncthreads();
+
+    if (!__syncthreads_and(!d2here || waitp(bar_d, 0))) {
+        if (tid == 0) {
+            atomicExch(g.status, 1);
+            waitp(bar_d, 0);
+        }
+        return;
+    }
+
+    // ---- phase 4: Dv and the compensated D2 v, 2-row x 1-complex-column tasks
+    // on every thread; the v planes
+    {
+        const float* VH = PH;
+        const float* VL = KV;
+        const float* D2S = OPS + 2 * mat;
+        const float* D2LS = OPS + 3 * mat;
+        const int RB2 = (Ny + 1) / 2, ntask2 = RB2 * c.C;
+        for (int t = tid; t < ntask2; t += THREADS) {
+            const int rb = t / c.C, j = t - rb * c.C, r0 = 2 * rb;
+            float d1[2][2] = {{0.f, 0.f}, {0.f, 0.f}};    // [row][re/im]
+            float sh[2][2] = {{0.f, 0.f}, {0.f, 0.f}}, sl[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
+            if (!d2here) {
+#pragma unroll 4
+                for (int k = 0; k < Ny; ++k) {
+                    const float2 a1 = *(const float2*)&D1S[k * RP + r0];
+                    const float2 xh = *(const float2*)&VH[k * VS + 2 * j];
+                    d1[0][0] += a1.x * xh.x; d1[0][1] += a1.x * xh.y;
+                    d1[1][0] += a1.y * xh.x; d1[1][1] += a1.y * xh.y;
+                }
+            } else
+#pragma unroll 2
+            for (int k = 0; k < Ny; ++k) {
+                const float2 a1 = *(const float2*)&D1S[k * RP + r0];
+                const float2 a2 = *(const float2*)&D2S[k * RP + r0];
+                const float2 a2l = *(const float2*)&D2LS[k * RP + r0];
+                const float2 xh = *(const float2*)&VH[k * VS + 2 * j];
+                const float2 xl = *(const float2*)&VL[k * VS + 2 * j];
+                d1[0][0] += a1.x * xh.x; d1[0][1] += a1.x * xh.y;
+                d1[1][0] += a1.y * xh.x; d1[1][1] += a1.y * xh.y;
+                ff_add_prod2(sh[0][0], sl[0][0], a2.x, xh.x, a2l.x, xl.x);
+                ff_add_prod2(sh[0][1], sl[0][1], a2.x, xh.y, a2l.x, xl.y);
+                ff_add_prod2(sh[1][0], sl[1][0], a2.y, xh.x, a2l.y, xl.x);
+                ff_add_prod2(sh[1][1], sl[1][1], a2.y, xh.y, a2l.y, xl.y);
+            }
+            const int q = col_q(c, j), e = col_e(c, j);
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                const int y = r0 + i;
+                if (y >= Ny) break;
+                const size_t o = ((size_t)y * E + e) * NM + q;
+                P5[o] = *(const float2*)&VH[y * VS + 2 * j];
+                P5[fs5 + o] = make_float2(d1[i][0], d1[i][1]);
+                if (d2here) P5[2 * fs5 + o] = make_float2(__fadd_rn(sh[i][0], sl[i][0]), __fadd_rn(sh[i][1], sl[i][1]));
+            }
+        }
+    }
+}
+
+}  // namespace spc
+
+bool spec_supported(const GroupView& g) {
+    return !g.lin && g.npairs > 1 && spc::smem_bytes(g) + 1024 <= 227 * 1024;
+}
+
+size_t spec_smem_bytes(const GroupView& g) {
+    const size_t b = spc::smem_bytes(g), m = mean_smem_bytes(g);
+    return b > m ? b : m;
+}
+
+void launch_spec(const GroupView& g, int s, cudaStream_t st) {
+    const int ctas = mean_row_ctas(g) + (g.npairs - 1) * spc::chunks(g);
+    spc::k_spec<<<ctas, spc::THREADS, spec_smem_bytes(g), st>>>(g, s);
+}
+
+void set_attributes_spec() { allow_max_dynamic_smem(spc::k_spec); }
+
+}  // namespace dnsk
