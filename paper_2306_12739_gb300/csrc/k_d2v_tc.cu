@@ -17,7 +17,7 @@
 // the row and column scales), combined in float-float and scaled back:
 //   D2 v = 2^(e_r + f_c) sum_L 2^(-7(L+2)) acc_L.
 // One CTA per 16 complex columns (32 real columns, 7 accumulators of 32 TMEM
-// columns each); M = 128 with the 64 used rows (Ny <= 64), rows 64..127 reading
+// columns each; two CTAs per SM; four warps read the accumulators back); M = 128 with the 64 used rows (Ny <= 64), rows 64..127 reading
 // the shared memory that follows and never read back.  The digit image of D2
 // arrives by one TMA bulk copy; v is read from the FP64 state and split by the
 // CTA.  Every mbarrier wait is bounded; on a timeout the CTA latches the status
@@ -32,7 +32,7 @@ namespace dnsk {
 
 namespace oz {
 
-constexpr int THREADS = 128;
+constexpr int THREADS = 256;
 constexpr int NDIG = 7;            // digits per value (7 bits each)
 constexpr int NLEV = 7;            // levels s + t kept
 constexpr int CC = 16;             // complex columns per CTA
@@ -110,9 +110,10 @@ __device__ __forceinline__ void digits(double x, int f, unsigned short (&d)[NDIG
         if (X >= (1ull << 49)) X = (1ull << 49) - 1;
     }
     const unsigned short sg = (bits >> 63) ? 0x8000u : 0u;
+    const unsigned hi = (unsigned)(X >> 21), lo = (unsigned)X & 0x1FFFFFu;   // digits 0..3 | 4..6
 #pragma unroll
     for (int s = 0; s < NDIG; ++s) {
-        const unsigned u = (unsigned)(X >> (7 * (NDIG - 1 - s))) & 127u;
+        const unsigned u = (s < 4 ? hi >> (7 * (3 - s)) : lo >> (7 * (6 - s))) & 127u;
         // the BF16 of a small integer u: the float u (exact), its top 16 bits
         const float fu = __int_as_float(0x4B000000 | (int)u) - 8388608.0f;
         d[s] = u ? (unsigned short)((unsigned)__float_as_int(fu) >> 16) | sg : (unsigned short)0;
@@ -163,11 +164,11 @@ __global__ void __launch_bounds__(THREADS, 2) k_d2v_tc(GroupView g, const double
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const unsigned tmem = *tslot;
 
-    // ---- B: tasks (complex column j, 8 consecutive k); pass 1 the column
+    // ---- B: tasks (complex column j, 4 consecutive k); pass 1 the column
     // exponents, pass 2 the digits (each thread keeps its values in registers)
-    const int KC = KP / 8, ntask = CC * KC;
-    constexpr int TPT = 2;                        // tasks per thread: CC * KC <= 128 * TPT (KP <= 64)
-    double2 xv[TPT][8];
+    const int KC = KP / 4, ntask = CC * KC;
+    constexpr int TPT = 1;                        // tasks per thread: CC * KC <= THREADS (KP <= 64)
+    double2 xv[TPT][4];
 #pragma unroll
     for (int u = 0; u < TPT; ++u) {
         const int t = tid + u * THREADS;
@@ -177,8 +178,8 @@ __global__ void __launch_bounds__(THREADS, 2) k_d2v_tc(GroupView g, const double
         const int q = col ? cc / E : 0, e = col ? cc - q * E : 0;
         int mr = 0, mi = 0;
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const int k = kc * 8 + i;
+        for (int i = 0; i < 4; ++i) {
+            const int k = kc * 4 + i;
             double2 x = make_double2(0.0, 0.0);
             if (col && k < Ny) x = V[((size_t)q * Ny + k) * E + e];
             xv[u][i] = x;
@@ -200,18 +201,17 @@ __global__ void __launch_bounds__(THREADS, 2) k_d2v_tc(GroupView g, const double
         for (int part = 0; part < 2; ++part) {
             const int c = 2 * j + part;
             const int f = cexp[c] - 1022;         // |x| < 2^f for every x of the column
-            unsigned short dg[8][NDIG];
+            unsigned short dg[4][NDIG];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) digits(part ? xv[u][i].y : xv[u][i].x, f, dg[i]);
-            const size_t off = (size_t)(c >> 3) * SBO + (size_t)kc * LBO + (size_t)(c & 7) * 16;
+            for (int i = 0; i < 4; ++i) digits(part ? xv[u][i].y : xv[u][i].x, f, dg[i]);
+            // k = 4 kc .. 4 kc + 3: half of a core-matrix row (8 k, 16 bytes)
+            const size_t off = (size_t)(c >> 3) * SBO + (size_t)(kc >> 1) * LBO + (size_t)(c & 7) * 16 + (kc & 1) * 8;
 #pragma unroll
             for (int s = 0; s < NDIG; ++s) {
-                uint4 w;
+                uint2 w;
                 w.x = (unsigned)dg[0][s] | ((unsigned)dg[1][s] << 16);
                 w.y = (unsigned)dg[2][s] | ((unsigned)dg[3][s] << 16);
-                w.z = (unsigned)dg[4][s] | ((unsigned)dg[5][s] << 16);
-                w.w = (unsigned)dg[6][s] | ((unsigned)dg[7][s] << 16);
-                *(uint4*)(B + s * sb + off) = w;
+                *(uint2*)(B + s * sb + off) = w;
             }
         }
     }
@@ -251,39 +251,39 @@ __global__ void __launch_bounds__(THREADS, 2) k_d2v_tc(GroupView g, const double
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const bool ok = ok_flag != 0;
 
-    // ---- epilogue: rows 0..63 (warps 0, 1), 16 real columns at a time
-    if (ok && warp < 2) {
-        const int y = 32 * warp + lane;
-        const unsigned trow = tmem + ((unsigned)(32 * warp) << 16);
+    // ---- epilogue: rows 0..63; warp w (0, 1, 4, 5) reads TMEM lanes 32 (w & 3)
+    // (the lanes its sub-partition may access) and real columns 16 (w >> 2) ..
+    if (ok && (warp & 3) < 2) {
+        const int y = 32 * (warp & 3) + lane;
+        const unsigned trow = tmem + ((unsigned)(32 * (warp & 3)) << 16);
         const int er = y < Ny ? g.D2ozexp[y] : 0;
         const size_t fs = (size_t)Ny * E * NM;
         float2* P5 = (float2*)g.P5;
-        for (int c0 = 0; c0 < NCOL; c0 += 16) {
-            float hi[16], lo[16], a[16];
+        const int c0 = 16 * (warp >> 2);
+        float hi[16], lo[16], a[16];
 #pragma unroll
-            for (int i = 0; i < 16; ++i) { hi[i] = 0.f; lo[i] = 0.f; }
-            // Horner over the levels from the smallest: (hi, lo) = acc_L + 2^-7 (hi, lo)
-            for (int L = NLEV - 1; L >= 0; --L) {
-                ld16(trow + (unsigned)(L * NCOL + c0), a);
+        for (int i = 0; i < 16; ++i) { hi[i] = 0.f; lo[i] = 0.f; }
+        // Horner over the levels from the smallest: (hi, lo) = acc_L + 2^-7 (hi, lo)
+        for (int L = NLEV - 1; L >= 0; --L) {
+            ld16(trow + (unsigned)(L * NCOL + c0), a);
 #pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    hi[i] *= 0.0078125f;
-                    lo[i] *= 0.0078125f;
-                    ff_add(hi[i], lo[i], a[i], 0.f);
-                }
+            for (int i = 0; i < 16; ++i) {
+                hi[i] *= 0.0078125f;
+                lo[i] *= 0.0078125f;
+                ff_add(hi[i], lo[i], a[i], 0.f);
             }
-            if (y < Ny) {
+        }
+        if (y < Ny) {
+            const float sr = p2f(er - 14);
 #pragma unroll
-                for (int i = 0; i < 16; i += 2) {
-                    const int c = c0 + i, j = c >> 1, cc = cc0 + j;
-                    if (cc >= ncc) break;
-                    const int q = cc / E, e = cc - q * E;
-                    // 2^(e_r + f_c) 2^-14 in two exact steps (each in the float range)
-                    const float sr = p2f(er - 14);
-                    const float re = __fadd_rn(hi[i], lo[i]) * sr * p2f(cexp[c] - 1022);
-                    const float im = __fadd_rn(hi[i + 1], lo[i + 1]) * sr * p2f(cexp[c + 1] - 1022);
-                    P5[2 * fs + ((size_t)y * E + e) * NM + q] = make_float2(re, im);
-                }
+            for (int i = 0; i < 16; i += 2) {
+                const int c = c0 + i, j = c >> 1, cc = cc0 + j;
+                if (cc >= ncc) break;
+                const int q = cc / E, e = cc - q * E;
+                // 2^(e_r + f_c) 2^-14 in two exact steps (each in the float range)
+                const float re = __fadd_rn(hi[i], lo[i]) * sr * p2f(cexp[c] - 1022);
+                const float im = __fadd_rn(hi[i + 1], lo[i + 1]) * sr * p2f(cexp[c + 1] - 1022);
+                P5[2 * fs + ((size_t)y * E + e) * NM + q] = make_float2(re, im);
             }
         }
     }
