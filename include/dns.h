@@ -129,14 +129,14 @@ typedef struct {
                                       and appended to it ("ygemm|plane|helm Mx My Mz E choice");
                                       NULL = none */
     int ygemm;                     /* mixed path y-derivatives of the step-by-step stage
-                                      (helm 1-3): 0 chosen at dns_bind_workspace, 1
-                                      register-tiled FP32 with D2 v summed in float-float (the
-                                      automatic choice of every DNS group: the 1e-6 budget needs
-                                      it), 2 tcgen05 tensor cores with split-BF16 operands and
-                                      FP32 accumulation (groups with My <= 66 and <= 64
-                                      members; chosen automatically, by timing, for linear
-                                      groups only; about 1e-5 of |D2 v| is lost to the
-                                      cancellation in D2's rows) */
+                                      (helm 1-3): 0 autotuned at dns_bind_workspace, 1
+                                      register-tiled FP32 with D2 v summed in float-float, 2
+                                      tcgen05 tensor cores with split-BF16 operands and FP32
+                                      accumulation (groups with My <= 66 and <= 64 members).
+                                      The FP32 accumulation loses about 1e-5 of |D2 v| to the
+                                      cancellation in D2's rows at My = 65, over the 1e-6 budget
+                                      of the mixed step, so DNS groups time 2 against 1 only up
+                                      to My = 49 (linear groups at every size) */
     int plane;                     /* plane stage: 0 autotuned where several kernels exist (else
                                       the only one; FP64 defaults to 1), 1 one CTA per plane
                                       (sizes <= 64), 2 a thread-block cluster per plane (64x64
@@ -144,8 +144,10 @@ typedef struct {
                                       per plane with each 1-D transform owned by one group of
                                       threads (mixed precision, sizes <= 64); a request for a
                                       variant the group's size lacks is ignored */
-    int helm;                      /* mixed path per-wavenumber stage: 0 automatic (4 where the
-                                      group supports it, else the autotuner's choice of 1 or 2),
+    int helm;                      /* mixed path per-wavenumber stage: 0 autotuned at
+                                      dns_bind_workspace (DNS groups: 1 and 2, each timed with the
+                                      y-derivatives and the forcing, against 4; linear groups: 1
+                                      against 2),
                                       1 register-tiled FP32 implicit apply (one CTA per
                                       wavenumber pair and field), 2 tcgen05 tensor cores with
                                       split-BF16 operands (groups with My <= 66 and <= 64 members;

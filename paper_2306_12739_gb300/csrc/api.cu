@@ -122,6 +122,10 @@ bool precision_mixed(const dns_handle* h) { return h->cfg.precision == DNS_PREC_
 // the tcgen05 implicit apply may run: its operator images are needed
 bool helm_tc_candidate(const GroupView& v) { return v.helm == 2 || (v.helm == 0 && dnsk::helm_tc_supported(v)); }
 
+// Largest My at which DNS groups may take the FP32-accumulated tensor-core
+// y-derivatives (see choose_variants)
+constexpr int FP32_D2_MAX_MY = 49;
+
 // Assign workspace offsets for every device array of group g (base = 0).
 size_t layout_group(dns_handle* h, HostGroup& G, size_t cur) {
     GroupView& v = G.v;
@@ -416,7 +420,7 @@ int cache_lookup(const char* path, const std::string& key) {
         std::string ln(line);
         if (ln.compare(0, key.size(), key) == 0 && ln.size() > key.size() + 1) {
             int c = atoi(ln.c_str() + key.size() + 1);
-            if (c >= 1 && c <= 3) found = c;
+            if (c >= 1 && c <= 4) found = c;
         }
     }
     fclose(f);
@@ -443,25 +447,30 @@ int choose_variants(dns_handle* h, const dns_config* cfg, GroupView& v, int gi) 
     const dns_group_desc& d = h->descs[gi];
     // y-contraction variant: 1 register-tiled FP32, 2 tcgen05; 0 = decided by the
     // autotuner when the workspace is bound
-    // (DNS groups: the register-tiled kernel, whose float-float D2 v keeps the
-    // 1e-6 budget; the tensor-core one only on request.  Linear groups: timed.)
+    // The tensor-core one accumulates D2 v in FP32, which loses about 1e-5 of
+    // |D2 v| to the cancellation in D2's rows at My = 65 (max row sum of |D2_int|
+    // 1.2e6; eta 2.2e-6 after 50 steps, over the 1e-6 budget) but not at My = 49
+    // (3.8e5; 4.2e-7): DNS groups time it against the float-float register-tiled
+    // kernel up to My = 49 and use the latter above; linear groups time both.
     v.ygemm = 1;
     if (precision_mixed(h) && dnsk::yderiv_tc_supported(v)) {
         if (cfg->ygemm == 2) v.ygemm = 2;
-        else if (cfg->ygemm == 0 && v.lin) v.ygemm = 0;
+        else if (cfg->ygemm == 0 && (v.lin || v.my <= FP32_D2_MAX_MY)) v.ygemm = 0;
     }
     // per-wavenumber stage: 1 register-tiled FP32 apply, 2 tcgen05, 3 persistent
     // register-tiled FP32 with double-buffered operator copies, 4 the fused
-    // stage; 0 = 4 where supported, else autotuned between 1 and 2
+    // stage; 0 = autotuned among 1, 2 (each after the y-derivatives and the
+    // forcing) and 4
     v.helm = 1;
     if (precision_mixed(h)) {
-        if (cfg->helm == 0 || cfg->helm == 4) v.helm = dnsk::spec_supported(v) ? 4 : 0;
+        if (cfg->helm == 4) v.helm = dnsk::spec_supported(v) ? 4 : 0;
+        else if (cfg->helm == 0) v.helm = 0;
         else if (cfg->helm == 2 && dnsk::helm_tc_supported(v)) v.helm = 2;
         else if (cfg->helm == 3) v.helm = 3;
     }
     if (v.helm == 4) v.ygemm = 1;   // only the derivatives of a newly set state run separately
     // with the fused stage, D2 v of each new state on tensor cores where the rows fit
-    v.d2tc = (v.helm == 4 && dnsk::d2v_tc_supported(v)) ? 1 : 0;
+    v.d2tc = ((v.helm == 4 || v.helm == 0) && dnsk::spec_supported(v) && dnsk::d2v_tc_supported(v)) ? 1 : 0;
     // plane-stage kernel: single CTA per plane where it fits, a thread-block
     // cluster (distributed shared memory) where it does not; where both exist
     // the autotuner decides at bind time
@@ -824,6 +833,7 @@ int dns_bind_workspace(dns_handle* h, void* dev_ptr, size_t bytes) {
         if (v.plane != 0) continue;
         const std::string key = tune_plane_key(v);
         int choice = decided.count(key) ? decided[key] : cache_lookup(h->cfg.autotune_cache, key);
+        if (choice && !plane_variant_ok(true, v, choice)) choice = 0;   // a cache entry this group cannot run
         if (!choice) {
             float best[4] = {0.f, 0.f, 0.f, 0.f};
             cudaEvent_t e0, e1;
@@ -861,6 +871,7 @@ int dns_bind_workspace(dns_handle* h, void* dev_ptr, size_t bytes) {
         if (v.ygemm != 0) continue;
         const std::string key = tune_key(v);
         int choice = decided.count(key) ? decided[key] : cache_lookup(h->cfg.autotune_cache, key);
+        if (choice > 2) choice = 0;
         if (!choice) {
             float best[3] = {0.f, 0.f, 0.f};
             cudaEvent_t e0, e1;
@@ -895,21 +906,37 @@ int dns_bind_workspace(dns_handle* h, void* dev_ptr, size_t bytes) {
         if (v.helm != 0) continue;
         const std::string key = tune_helm_key(v);
         int choice = decided.count(key) ? decided[key] : cache_lookup(h->cfg.autotune_cache, key);
+        if ((choice == 2 && !dnsk::helm_tc_supported(v)) || (choice == 4 && (v.lin || !dnsk::spec_supported(v))) || choice == 3)
+            choice = 0;
         if (!choice) {
             // the implicit apply is timed on sub-step 2 (both accumulators); it
             // writes only the sub-step state, which set_state overwrites later
-            float best[4] = {0.f, 0.f, 0.f, 0.f};
+            float best[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
             cudaEvent_t e0, e1;
             cudaEventCreate(&e0);
             cudaEventCreate(&e1);
             // the persistent variant (3) fills the whole GPU, which timed alone
             // wins but inside the step starves the concurrent member blocks and
-            // groups: only on request, never autotuned
-            for (int cand = 1; cand <= 2; ++cand) {
+            // groups: only on request, never autotuned.  A DNS group times the
+            // whole per-wavenumber part of a sub-step: the y-derivatives, the
+            // forcing and the apply (1, 2) against the fused stage (4).
+            const bool whole = !v.lin;
+            for (int cand = 1; cand <= 4; ++cand) {
                 if (cand == 2 && !dnsk::helm_tc_supported(v)) continue;
+                if (cand == 3) continue;
+                if (cand == 4 && !(whole && dnsk::spec_supported(v))) continue;
                 auto run = [&]() {
+                    if (cand == 4) {
+                        dnsk::launch_spec(v, 1, st);
+                        if (v.d2tc) dnsk::launch_d2v_tc(v, v.v_s, st);
+                        return;
+                    }
+                    if (whole) {
+                        if (v.ygemm == 2) dnsk::launch_yderiv_tc(v, v.v_t, v.e_t, st);
+                        else dnsk::launch_yderiv_t(v, v.v_t, v.e_t, st);
+                        dnsk::launch_forcing_t(v, 1, st);
+                    }
                     if (cand == 2) dnsk::launch_helm_tc(v, 1, st);
-                    else if (cand == 3) dnsk::launch_helm_tp(v, 1, st);
                     else dnsk::launch_helm_t(v, 1, st);
                 };
                 for (int w = 0; w < 2; ++w) run();
@@ -926,12 +953,13 @@ int dns_bind_workspace(dns_handle* h, void* dev_ptr, size_t bytes) {
             if (rc) return rc;
             if ((rc = device_status(h))) return rc;
             choice = 0;
-            for (int cand = 1; cand <= 3; ++cand)
+            for (int cand = 1; cand <= 4; ++cand)
                 if (best[cand] > 0.f && (choice == 0 || best[cand] < best[choice])) choice = cand;
-            cache_store(h->cfg.autotune_cache, key, choice, best, 3);
+            cache_store(h->cfg.autotune_cache, key, choice, best, 4);
         }
         decided[key] = choice;
         v.helm = choice;
+        if (choice == 4) v.ygemm = 1;
     }
     h->bound = true;
     return DNS_OK;

@@ -116,6 +116,8 @@ __device__ void finish_member(const GroupView& g, int s, int e, unsigned char* s
         }
     }
     if (threadIdx.x == 0) g.gamma[e] = gam;
+    // the step is complete: the next step draws new noise
+    if (s == 2 && g.fn > 0 && e == 0 && threadIdx.x == 0) *g.fstep += 1ULL;
 }
 
 // Rows of the mean-flow update (one warp per interior row), then the member's

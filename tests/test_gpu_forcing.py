@@ -99,7 +99,8 @@ def test_fp64_forced_shared_mean_ensemble_matches_the_oracle():
     assert np.array_equal(got[2][0], got[2][3])                           # the mean stays shared
 
 
-@pytest.mark.parametrize("precision,pin", [("fp64", {}), ("mixed", dict(ygemm="tc", plane="lines", helm="simt"))])
+@pytest.mark.parametrize("precision,pin", [("fp64", {}), ("mixed", dict(ygemm="tc", plane="lines", helm="simt")),
+                                           ("mixed", dict(plane="lines", helm="fused"))])
 def test_forced_graph_replay_and_member_blocks_are_bitwise_invisible(precision, pin):
     g = group("couette", 16, 33, 16, 400.0, 0.01, 40)
     st = _state(g, 60)
@@ -110,12 +111,15 @@ def test_forced_graph_replay_and_member_blocks_are_bitwise_invisible(precision, 
         assert np.array_equal(a, b)
 
 
-def test_mixed_forced_run_matches_fp64_over_50_steps():
+@pytest.mark.parametrize("pin", [dict(ygemm="tc", plane="lines", helm="simt"), dict(helm="fused")])
+def test_mixed_forced_run_matches_fp64_over_50_steps(pin):
+    """Every step draws new noise (the step counter advances once per step in
+    the step-by-step and in the fused stage alike)."""
     g = group("poiseuille", 32, 33, 32, 1650.0, 0.005, 6)
     st = _state(g, 70, amp=5e-2)
     forcing = (1, 4, 1e-3, 123)
     a = _run(g, st, 50, forcing, "fp64")
-    b = _run(g, st, 50, forcing, "mixed", ygemm="tc", plane="lines", helm="simt")
+    b = _run(g, st, 50, forcing, "mixed", **pin)
     scale = max(np.abs(a[2]).max(), np.abs(a[3]).max())
     for x, y, k in zip(b, a, FIELDS):
         err = np.max(np.abs(x - y)) / (scale if k in ("U", "W") else np.max(np.abs(y)))
