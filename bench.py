@@ -557,6 +557,9 @@ def gpu_arm(args, rank, world, dist):
     dev = torch.device("cuda", torch.cuda.current_device())
     wl = WORKLOADS[args.workload]
     groups = [dict(g) for g in wl["groups"]]
+    if args.member_block > 0:
+        for g in groups:
+            g["member_block"] = args.member_block
     states = [initial_state(g, rank, nz) for g, nz in zip(groups, wl["noise"])]
     members = sum(g["members"] for g in groups)
     # member grid points (a linear group's disturbance lives on the (y, z) plane of one harmonic)
@@ -722,7 +725,7 @@ def gpu_arm(args, rank, world, dist):
         "data": "synthetic (seeded, dns_synth)",
         "config": {"workload": wl["name"], "precision": precision, "graph": True,
                    "kernels": choices, "ygemm_request": args.ygemm, "plane_request": args.plane,
-                   "helm_request": args.helm,
+                   "helm_request": args.helm, "member_block_request": args.member_block,
                    "l2": "flushed (256 MiB write) before every timed step", "parallelism": "replicas x%d" % world},
         "grid_pts_steps_per_s": aggregate(pts * args.steps, total_ms / 1e3, world),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
@@ -812,6 +815,8 @@ def main():
                          "supports it, else the autotuned implicit apply)")
     ap.add_argument("--ygemm", choices=["default", "simt", "tc"], default="default",
                     help="y-contraction variant of the mixed path")
+    ap.add_argument("--member-block", type=int, default=0,
+                    help="members per block of every independent-member group (0: the library's rule)")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="poiseuille64",
                     help="ensemble configuration (default: the headline 64x65x64 Poiseuille ensemble)")
     args = ap.parse_args()

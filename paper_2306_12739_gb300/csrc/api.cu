@@ -146,7 +146,7 @@ size_t layout_group(dns_handle* h, HostGroup& G, size_t cur) {
     add((void**)&v.status, 256);
     if (v.ygemm != 1) add((void**)&v.Atc, 3 * 128 * (size_t)v.kp * sizeof(uint16_t));
     if (v.d2tc) {
-        add((void**)&v.D2oz, 7 * 64 * (size_t)v.kp * sizeof(uint16_t));
+        add((void**)&v.D2oz, dnsk::d2v_tc_image_bytes(v));
         add((void**)&v.D2ozexp, 64 * sizeof(int));
     }
     add((void**)&v.ccw, sizeof(double) * v.my);

@@ -58,7 +58,7 @@ struct GroupView {
     const float* D2T;
     const float* D2Tl;    // D2T's residual: D2i - (double) D2T in single precision (compensated D2 v)
     int d2tc;             // fused stage: 1 = D2 v of the new state by the tensor-core digit kernel
-    const void* D2oz;     // its image of D2: 7 slices of 7-bit digits [64 rows][kp] (BF16)
+    const void* D2oz;     // its image of D2: slices of 7-bit digits [64 rows][kp] (BF16)
     const int* D2ozexp;   // [64] row exponents of that image
     const double* ccw;    // [My]
     const double* kxt;    // [NKX]
@@ -155,6 +155,7 @@ void set_attributes_plane_cl();
 // D2 v on tensor cores with exact digit accumulation (k_d2v_tc.cu), Ny <= 64
 bool d2v_tc_supported(const GroupView& g);
 size_t d2v_tc_smem_bytes(const GroupView& g);
+size_t d2v_tc_image_bytes(const GroupView& g);
 void launch_d2v_tc(const GroupView& g, const double2* v, cudaStream_t st);
 void set_attributes_d2v_tc();
 // fused per-wavenumber stage of the mixed path (k_spec.cu)

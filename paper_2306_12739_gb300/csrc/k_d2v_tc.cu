@@ -7,16 +7,17 @@
 // "Error-free transformations of matrix multiplication by using fast routines
 // of matrix multiplication", 2012, with small integers in place of floating
 // slices): every row r of D2 is scaled by a power of two 2^e_r above its
-// largest entry and written as S = 7 signed 7-bit digits, D2_rk = 2^e_r
+// largest entry and written as S = 6 signed 7-bit digits, D2_rk = 2^e_r
 // sum_s a_s 2^(-7(s+1)); every real column c of v (one mode, member, real or
 // imaginary part) likewise with 2^f_c.  Digits are integers of magnitude
 // <= 127, exact in BF16, their products exact, and a level L = s + t sums at
-// most 7 x 64 products of at most 127^2: below 2^24, so the FP32 accumulators
+// most 6 x 64 products of at most 127^2: below 2^24, so the FP32 accumulators
 // of tcgen05 (kind::f16, BF16 operands) hold every level EXACTLY.  The levels
-// L <= 6 are kept (the rest and the digits beyond the seventh weigh < 2^-49 of
-// the row and column scales), combined in float-float and scaled back:
+// L <= 5 are kept (the rest and the digits beyond the sixth weigh < 2^-42 of
+// the row and column scales: about 3e-9 of |D2 v| at My = 65 and 97), combined
+// in float-float and scaled back:
 //   D2 v = 2^(e_r + f_c) sum_L 2^(-7(L+2)) acc_L.
-// One CTA per 16 complex columns (32 real columns, 7 accumulators of 32 TMEM
+// One CTA per 16 complex columns (32 real columns, 6 accumulators of 32 TMEM
 // columns each; two CTAs per SM; four warps read the accumulators back); M = 128 with the 64 used rows (Ny <= 64), rows 64..127 reading
 // the shared memory that follows and never read back.  The digit image of D2
 // arrives by one TMA bulk copy; v is read from the FP64 state and split by the
@@ -33,8 +34,9 @@ namespace dnsk {
 namespace oz {
 
 constexpr int THREADS = 256;
-constexpr int NDIG = 7;            // digits per value (7 bits each)
-constexpr int NLEV = 7;            // levels s + t kept
+constexpr int NDIG = 6;            // digits per value (7 bits each: 42 fraction bits)
+constexpr int NLEV = 6;            // levels s + t kept
+constexpr int FBITS = 7 * NDIG;
 constexpr int CC = 16;             // complex columns per CTA
 constexpr int NCOL = 2 * CC;       // real columns = TMEM columns per level
 constexpr int MROWS = 128;
@@ -97,7 +99,7 @@ __device__ __forceinline__ void ld16(unsigned taddr, float* v) {
 __device__ __forceinline__ int bexp(double x) { return (int)((__double_as_longlong(x) >> 52) & 0x7FF); }
 
 // The NDIG digits of x in units of 2^f (|x| < 2^f), as BF16 bit patterns:
-// the magnitude rounded to 49 fraction bits, 7 bits per digit, the sign on
+// the magnitude rounded to FBITS fraction bits, 7 bits per digit, the sign on
 // every digit.  Integer operations only.
 __device__ __forceinline__ void digits(double x, int f, unsigned short (&d)[NDIG]) {
     const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
@@ -105,15 +107,16 @@ __device__ __forceinline__ void digits(double x, int f, unsigned short (&d)[NDIG
     unsigned long long X = 0;
     if (ex > 0) {
         const unsigned long long m = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-        const int rs = 1026 + f - ex;      // right shift: X = round(m 2^(ex - 1075 + 49 - f))
+        const int rs = 1075 - FBITS + f - ex;   // right shift: X = round(m 2^(ex - 1075 + FBITS - f))
         if (rs < 64) X = rs > 0 ? (m + (1ull << (rs - 1))) >> rs : m;
-        if (X >= (1ull << 49)) X = (1ull << 49) - 1;
+        if (X >= (1ull << FBITS)) X = (1ull << FBITS) - 1;
     }
     const unsigned short sg = (bits >> 63) ? 0x8000u : 0u;
-    const unsigned hi = (unsigned)(X >> 21), lo = (unsigned)X & 0x1FFFFFu;   // digits 0..3 | 4..6
+    const unsigned hi = (unsigned)(X >> 21), lo = (unsigned)X & 0x1FFFFFu;   // digits 0..2 | 3..5
+    static_assert(NDIG == 6, "the split into two 21-bit halves assumes six digits");
 #pragma unroll
     for (int s = 0; s < NDIG; ++s) {
-        const unsigned u = (s < 4 ? hi >> (7 * (3 - s)) : lo >> (7 * (6 - s))) & 127u;
+        const unsigned u = (s < 3 ? hi >> (7 * (2 - s)) : lo >> (7 * (5 - s))) & 127u;
         // the BF16 of a small integer u: the float u (exact), its top 16 bits
         const float fu = __int_as_float(0x4B000000 | (int)u) - 8388608.0f;
         d[s] = u ? (unsigned short)((unsigned)__float_as_int(fu) >> 16) | sg : (unsigned short)0;
@@ -141,7 +144,7 @@ __global__ void __launch_bounds__(THREADS, 2) k_d2v_tc(GroupView g, const double
     const unsigned bar_a = su32(&bars[0]), bar_m = su32(&bars[1]);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const unsigned LBO = 128, SBO = 16 * KP;
-    constexpr unsigned TCOLS = 256;               // NLEV * NCOL = 224, allocated as 256
+    constexpr unsigned TCOLS = 256;               // NLEV * NCOL = 192, allocated as 256
 
     if (tid < NCOL) cexp[tid] = 0;
     if (tid == 0) {
@@ -300,6 +303,8 @@ bool d2v_tc_supported(const GroupView& g) { return g.ny <= 64 && !g.lin; }
 
 size_t d2v_tc_smem_bytes(const GroupView& g) { return oz::smem_total(g.kp); }
 
+size_t d2v_tc_image_bytes(const GroupView& g) { return oz::NDIG * oz::slice_a(g.kp); }
+
 void launch_d2v_tc(const GroupView& g, const double2* v, cudaStream_t st) {
     const int ctas = (g.nmodes * g.E + oz::CC - 1) / oz::CC;
     oz::k_d2v_tc<<<ctas, oz::THREADS, d2v_tc_smem_bytes(g), st>>>(g, v);
@@ -334,8 +339,8 @@ void d2v_tc_image(const std::vector<double>& D2i, int ny, int kp, std::vector<ui
         for (int k = 0; k < ny; ++k) {
             const double x = std::ldexp(D2i[(size_t)r * ny + k], -e);   // |x| < 1, exact
             const double ax = std::fabs(x);
-            uint64_t X = (uint64_t)std::llround(std::ldexp(ax, 49));
-            if (X >= (1ull << 49)) X = (1ull << 49) - 1;
+            uint64_t X = (uint64_t)std::llround(std::ldexp(ax, oz::FBITS));
+            if (X >= (1ull << oz::FBITS)) X = (1ull << oz::FBITS) - 1;
             for (int s = 0; s < oz::NDIG; ++s) {
                 const int u = (int)((X >> (7 * (oz::NDIG - 1 - s))) & 127u);
                 const size_t off = (size_t)(r >> 3) * sbo + (size_t)(k >> 3) * 64 + (size_t)(r & 7) * 8 + (k & 7);
