@@ -320,6 +320,15 @@ def profiled_traffic(kernel, variant):
     return rec["dram_bytes_per_launch"]
 
 
+def roofline_bound(flops, nbytes, alu_tflops, hbm_gbs):
+    """'hbm' when the algorithmic intensity flops / nbytes lies below the ridge
+    point alu peak / HBM peak (the memory roofline is the lower one), else 'alu'."""
+    if nbytes <= 0:
+        return "alu"
+    ridge = alu_tflops * 1e12 / (hbm_gbs * 1e9)
+    return "hbm" if flops / nbytes < ridge else "alu"
+
+
 def alu_peak(precision_of_kernel, sm_mhz, n_sm):
     """FP32 peak of n_sm SMs at the sampled clock (TFLOP/s), or the nominal FP64
     rate."""
@@ -631,20 +640,28 @@ def gpu_arm(args, rank, world, dist):
     # every member of every group passes through the kernel once per sub-step
     # (member blocks split a group over several launches; the work is per member)
     work = sum(kernel_work(dom, g, precision)[1] for g in groups) * 3 * n_timed
-    bound = kernel_work(dom, groups[0], precision)[0]
+    dbytes = sum(kernel_bytes(dom, g, precision) for g in groups) * 3 * n_timed
     avg_ms = kt[dom][0] / max(1, kt[dom][1])
     kprec = kernel_precision(dom, precision)
     sm_mhz = clocks["sm_mhz"] or 2070.0
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
-    peak = alu_peak(kprec, sm_mhz, n_sm)
-    achieved = work / (kt[dom][0] / 1e3) / 1e12
+    hpk, hsrc = hbm_peak()
+    apk = alu_peak(kprec, sm_mhz, n_sm)
+    # the roofline that bounds the kernel at its algorithmic intensity: HBM below
+    # the ridge (peak flops / peak bytes per second), the ALU peak above it
+    bound = roofline_bound(work, dbytes, apk, hpk)
+    if bound == "hbm":
+        peak, unit = hpk, "GB/s"
+        achieved = dbytes / (kt[dom][0] / 1e3) / 1e9
+    else:
+        peak, unit = apk, "TFLOP/s"
+        achieved = work / (kt[dom][0] / 1e3) / 1e12
     variant = {"plane": choices[0]["plane"], "yderiv": choices[0]["ygemm"], "helm": choices[0]["helm"],
-               "spec": "fused"}.get(dom, "simt")
+               "spec": "fused", "d2v": "tc"}.get(dom, "simt")
     traffic = (profiled_traffic(dom, variant)
                if (precision == "mixed" and args.workload == "poiseuille64") else None)
     # every class against the HBM roofline of its own algorithmic bytes (the
     # event pass runs the kernels one at a time)
-    hpk, hsrc = hbm_peak()
     per_class = {}
     for cls, (ms, nl) in kt.items():
         b = sum(kernel_bytes(cls, g, precision) for g in groups) * 3 * n_timed
@@ -654,9 +671,12 @@ def gpu_arm(args, rank, world, dist):
         per_class[cls] = {"ms_per_launch": ms / max(1, nl), "algorithmic_bytes_per_launch": b / max(1, nl),
                           "achieved_gbs": gbs, "frac_of_hbm": gbs / hpk}
     roofline = {"kernel": dom, "bound": bound, "precision": kprec, "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
+                "unit": unit, "frac": achieved / peak, "traffic": traffic,
                 "traffic_unit": "DRAM bytes per launch (ncu, profiles/)",
-                "peak_source": ("nominal GB300 FP64" if kprec == "f64" else
+                "intensity_flop_per_byte": work / dbytes if dbytes > 0 else None,
+                "ridge_flop_per_byte": apk * 1e3 / hpk,
+                "alu_peak_tflops": apk, "hbm_peak_gbs": hpk,
+                "peak_source": (hsrc if bound == "hbm" else "nominal GB300 FP64" if kprec == "f64" else
                                 "%d SM (device attribute) x 128 FP32 lanes x 2 x median sampled SM clock %.0f MHz"
                                 % (n_sm, sm_mhz)),
                 "kernel_ms_per_launch": avg_ms,

@@ -97,3 +97,19 @@ def test_config1_workload_is_the_16x33x16_couette_case():
     g = wl["groups"][0]
     assert (g["mx"], g["my"], g["mz"], g["members"], g["re"], g["dt"]) == (16, 33, 16, 1, 400.0, 0.01)
     assert wl["noise"][0]["amp"] == 1e-2 and wl["noise"][0]["n_max"] == 2 and wl["noise"][0]["m_max"] == 2
+
+
+def test_roofline_bound_follows_the_ridge_point():
+    # ridge at 80 TFLOP/s over 6.8 TB/s: ~11.8 flop per byte
+    assert bench.roofline_bound(7e8, 1e8, 80.0, 6800.0) == "hbm"
+    assert bench.roofline_bound(3e9, 1e8, 80.0, 6800.0) == "alu"
+    assert bench.roofline_bound(1e9, 0, 80.0, 6800.0) == "alu"
+    # the fused stage of the headline (64x65x64, 4 members per launch) is below the ridge
+    g = dict(bench.WORKLOADS["poiseuille64"]["groups"][0], members=4)
+    w = bench.kernel_work("spec", g, "mixed")[1]
+    b = bench.kernel_bytes("spec", g, "mixed")
+    assert bench.roofline_bound(w, b, 80.5, 6799.3) == "hbm"
+    # the plane stage is above it
+    w = bench.kernel_work("plane", g, "mixed")[1]
+    b = bench.kernel_bytes("plane", g, "mixed")
+    assert bench.roofline_bound(w, b, 80.5, 6799.3) == "alu"
