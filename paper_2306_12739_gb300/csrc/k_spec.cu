@@ -168,6 +168,21 @@ __device__ __forceinline__ void mm2(const float* A, const float* B, const float*
     }
 }
 
+// 4-row x 1-complex-column product of one transposed operator (shared memory)
+// with a right-hand side: a = A x
+__device__ __forceinline__ void mm1(const float* A, const float* X, int Ny, int RP, int VS, int r0, int c2,
+                                    float (&a)[2][4]) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) a[0][i] = a[1][i] = 0.f;
+#pragma unroll 4
+    for (int k = 0; k < Ny; ++k) {
+        const float4 ak = *(const float4*)&A[k * RP + r0];
+        const float2 xk = *(const float2*)&X[k * VS + c2];
+        a[0][0] += ak.x * xk.x; a[0][1] += ak.y * xk.x; a[0][2] += ak.z * xk.x; a[0][3] += ak.w * xk.x;
+        a[1][0] += ak.x * xk.y; a[1][1] += ak.y * xk.y; a[1][2] += ak.z * xk.y; a[1][3] += ak.w * xk.y;
+    }
+}
+
 // 4-row x 1-complex-column product of D1 (transposed [k][RP]) with a
 // right-hand side, both in shared memory
 __device__ __forceinline__ void d1mm(const float* D1T, const float* X, int Ny, int RP, int VS, int r0, int c2,
@@ -183,35 +198,47 @@ __device__ __forceinline__ void d1mm(const float* D1T, const float* X, int Ny, i
     }
 }
 
-// The implicit apply of one field for a 4-row x 1-complex-column task: reads
-// x_t (FP64) and, in the third sub-step, the stored (M_1 - I) x_t; writes x+
-// (FP64; over x_t in the third sub-step), (M_1 - I) x_t in the second, and the
+// Loads of an implicit-apply task, issued before its products so that their
+// latency overlaps them: x_t (FP64) and, in the third sub-step, (M_1 - I) x_t.
+__device__ __forceinline__ void apply_prefetch(const GroupView& g, int s, int f, const Cols& c, int r0, int j,
+                                               double2 (&x)[4], float2 (&m1)[4]) {
+    const int Ny = g.ny, E = g.E;
+    const int q = col_q(c, j), e = col_e(c, j);
+    const double2* X = f == 0 ? g.v_t : g.e_t;
+    const float2* M1 = (const float2*)(f == 0 ? g.mx1_v : g.mx1_e);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int y = r0 + i;
+        x[i] = make_double2(0.0, 0.0);
+        m1[i] = make_float2(0.f, 0.f);
+        if (y >= Ny) continue;
+        const size_t o = ((size_t)q * Ny + y) * E + e;
+        x[i] = X[o];
+        if (s == 2) m1[i] = M1[o];
+    }
+}
+
+// The implicit apply of one field for a 4-row x 1-complex-column task, from
+// x_t (FP64) and, in the third sub-step, the stored (M_1 - I) x_t, both
+// loaded by apply_prefetch before the task's products: writes x+ (FP64; over
+// x_t in the third sub-step), (M_1 - I) x_t in the second, and the
 // single-precision x+ (hi, and lo when lo_out) into shared memory.
 __device__ __forceinline__ void apply_epilogue(const GroupView& g, int s, int f, const Cols& c, int r0, int j,
-                                               const float (&ma)[2][4], const float (&pa)[2][4], float* hi_out,
+                                               const float (&ma)[2][4], const float (&pa)[2][4],
+                                               const double2 (&x)[4], const float2 (&m1s)[4], float* hi_out,
                                                float* lo_out) {
     const int Ny = g.ny, E = g.E, VS = vec_stride(g);
     const int q = col_q(c, j), e = col_e(c, j);
-    const double2* X = f == 0 ? g.v_t : g.e_t;
     float2* M1 = (float2*)(f == 0 ? g.mx1_v : g.mx1_e);
     double2* O = (s == 2) ? (f == 0 ? g.v_t : g.e_t) : (f == 0 ? g.v_s : g.e_s);
-    double2 x[4];
-    float2 m1[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         const int y = r0 + i;
         if (y >= Ny) break;
         const size_t o = ((size_t)q * Ny + y) * E + e;
-        x[i] = X[o];
-        m1[i] = (s == 2) ? M1[o] : make_float2(ma[0][i], ma[1][i]);
-    }
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int y = r0 + i;
-        if (y >= Ny) break;
-        const size_t o = ((size_t)q * Ny + y) * E + e;
-        if (s == 1) M1[o] = m1[i];
-        const double2 xn = make_double2(x[i].x + f2d(m1[i].x + pa[0][i]), x[i].y + f2d(m1[i].y + pa[1][i]));
+        const float2 m1 = (s == 2) ? m1s[i] : make_float2(ma[0][i], ma[1][i]);
+        if (s == 1) M1[o] = m1;
+        const double2 xn = make_double2(x[i].x + f2d(m1.x + pa[0][i]), x[i].y + f2d(m1.y + pa[1][i]));
         O[o] = xn;
         const float hx = d2f(xn.x), hy = d2f(xn.y);
         *(float2*)&hi_out[y * VS + 2 * j] = make_float2(hx, hy);
@@ -346,23 +373,21 @@ __global__ void __launch_bounds__(THREADS, 2) k_spec(GroupView g, int s) {
     const size_t fs5 = (size_t)Ny * E * NM;
     float2* P5 = (float2*)g.P5;
 
-    // ---- phase 2: F~ (threads 0..127) | eta+ (threads 128..255)
+    // ---- phase 2: F~ and (M_v - I) v_t (threads 0..127) | eta+ (threads 128..255)
     if (tid < HALF) {
         float2* Av = (float2*)g.Av;
         for (int t = tid; t < ntask; t += HALF) {
             const int rb = t / c.C, j = t - rb * c.C, r0 = 4 * rb;
-            float a[2][4];
-            d1mm(D1S, PH, Ny, RP, VS, r0, 2 * j, a);
             const int q = col_q(c, j), e = col_e(c, j);
             float2 pav[4];
-            if (s != 0) {
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const int y = r0 + i;
-                    if (y >= Ny) break;
-                    pav[i] = Av[((size_t)q * Ny + y) * E + e];
-                }
+            for (int i = 0; i < 4; ++i) {
+                const int y = r0 + i;
+                pav[i] = make_float2(0.f, 0.f);
+                if (s != 0 && y < Ny) pav[i] = Av[((size_t)q * Ny + y) * E + e];
             }
+            float a[2][4];
+            d1mm(D1S, PH, Ny, RP, VS, r0, 2 * j, a);
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 const int y = r0 + i;
@@ -384,13 +409,28 @@ __global__ void __launch_bounds__(THREADS, 2) k_spec(GroupView g, int s) {
                 }
                 *(float2*)&FT[y * VS + 2 * j] = Ft;
             }
+            // (M_v - I) x_t of the same rows and column (it needs no F~), kept in
+            // the -k^2 Nv slots this thread has just read, for phase 3
+            if (needM) {
+                float ma[2][4];
+                mm1(OPS, XV, Ny, RP, VS, r0, 2 * j, ma);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int y = r0 + i;
+                    if (y >= Ny) break;
+                    *(float2*)&KV[y * VS + 2 * j] = make_float2(ma[0][i], ma[1][i]);
+                }
+            }
         }
     } else {
         for (int t = tid - HALF; t < ntask; t += HALF) {
             const int rb = t / c.C, j = t - rb * c.C, r0 = 4 * rb;
+            double2 x[4];
+            float2 m1[4];
+            apply_prefetch(g, s, 1, c, r0, j, x, m1);
             float ma[2][4], pa[2][4];
             mm2(OPS + 2 * mat, OPS + 3 * mat, XE, GT, Ny, RP, VS, r0, 2 * j, needM, ma, pa);
-            apply_epilogue(g, s, 1, c, r0, j, ma, pa, EN, nullptr);
+            apply_epilogue(g, s, 1, c, r0, j, ma, pa, x, m1, EN, nullptr);
         }
     }
     __syncthreads();
@@ -405,14 +445,26 @@ __global__ void __launch_bounds__(THREADS, 2) k_spec(GroupView g, int s) {
         bulk(OPS + 3 * mat, g.D2Tl, mb, bar_d);
     }
 
-    // ---- phase 3: v+ (threads 0..127) | D eta and the eta planes (threads 128..255)
+    // ---- phase 3: v+ (P_v F~, threads 0..127) | D eta and the eta planes (threads 128..255)
     if (tid < HALF) {
         for (int t = tid; t < ntask; t += HALF) {
             const int rb = t / c.C, j = t - rb * c.C, r0 = 4 * rb;
+            double2 x[4];
+            float2 m1[4];
+            apply_prefetch(g, s, 0, c, r0, j, x, m1);
             float ma[2][4], pa[2][4];
-            mm2(OPS, OPS + mat, XV, FT, Ny, RP, VS, r0, 2 * j, needM, ma, pa);
-            // v+ hi, lo over phi and -k^2 Nv (read by phase 2 only)
-            apply_epilogue(g, s, 0, c, r0, j, ma, pa, PH, d2here ? KV : nullptr);
+            mm1(OPS + mat, FT, Ny, RP, VS, r0, 2 * j, pa);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int y = r0 + i;
+                float2 m = make_float2(0.f, 0.f);
+                if (needM && y < Ny) m = *(const float2*)&KV[y * VS + 2 * j];
+                ma[0][i] = m.x;
+                ma[1][i] = m.y;
+            }
+            // v+ hi, lo over phi and the (M_v - I) v_t slots (each read first by
+            // this thread)
+            apply_epilogue(g, s, 0, c, r0, j, ma, pa, x, m1, PH, d2here ? KV : nullptr);
         }
     } else {
         for (int t = tid - HALF; t < ntask; t += HALF) {
