@@ -328,6 +328,18 @@ int dns_step_timed(dns_handle* h, int nsteps, double* ms, int* launches);
  * DNS_ERR_TIMEOUT (the context stays usable).  Synchronises. */
 int dns_selftest_timeout(dns_handle* h);
 
+/* Bounds-checked debug build.  libdns_check.so is the same library compiled with
+ * -DDNS_CHECK: the hot-path kernels check their global (and the fused stage its
+ * shared-memory) indices; the first failing index of a launch and the kernel are
+ * recorded in the group's device status word, the access is skipped (no trap),
+ * and the next synchronising call returns DNS_ERR_CUDA with
+ * "bounds check failed: kernel K, index I (mod 2^24)" in dns_last_error.
+ * dns_checked_build returns 1 in that build, 0 in libdns.so.
+ * dns_selftest_bounds enqueues one check whose condition is false (it touches no
+ * memory) and synchronises: DNS_ERR_CUDA in the checked build, DNS_OK otherwise. */
+int dns_checked_build(void);
+int dns_selftest_bounds(dns_handle* h);
+
 /* Host run of the integer-operation binary64 <-> binary32 conversions the
  * mixed-precision kernels apply to the FP64 state (the same source code the
  * device compiles): f_out[i] = d_in[i] rounded to nearest even (magnitudes

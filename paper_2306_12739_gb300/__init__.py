@@ -15,7 +15,9 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libdns.so")
+# DNS_CHECKED=1 loads the bounds-checked debug build instead (built by
+# paper_2306_12739_gb300/build.py with checked=True)
+LIB_PATH = os.path.join(_HERE, "libdns_check.so" if os.environ.get("DNS_CHECKED") == "1" else "libdns.so")
 
 if not os.path.exists(LIB_PATH):
     raise ImportError("libdns.so is not built at %s; build it with paper_2306_12739_gb300.build" % LIB_PATH)
@@ -37,7 +39,8 @@ EXPORTED = ["dns_create", "dns_workspace_size", "dns_bind_workspace", "dns_state
             "dns_last_error", "dns_last_launch_count", "dns_export_grid", "dns_export_operators",
             "dns_step_timed", "dns_stats_noalloc", "dns_selftest_timeout", "dns_kernel_choice",
             "dns_convert_selftest", "dns_set_base_flow", "dns_set_direction", "dns_orthonormalize",
-            "dns_optimal_sweep", "dns_set_stochastic_forcing", "dns_export_forcing", "dns_advance"]
+            "dns_optimal_sweep", "dns_set_stochastic_forcing", "dns_export_forcing", "dns_advance",
+            "dns_checked_build", "dns_selftest_bounds"]
 KERNEL_CLASSES = ["mean_deriv", "yderiv", "plane", "forcing", "helm", "mean", "spec", "d2v"]
 
 
@@ -94,6 +97,8 @@ _lib.dns_last_launch_count.argtypes = [_H]
 _lib.dns_step_timed.argtypes = [_H, ctypes.c_int, _dp, ctypes.POINTER(ctypes.c_int)]
 _lib.dns_stats_noalloc.argtypes = [_H, ctypes.c_int, _vp]
 _lib.dns_selftest_timeout.argtypes = [_H]
+_lib.dns_selftest_bounds.argtypes = [_H]
+_lib.dns_checked_build.argtypes = []
 _lib.dns_convert_selftest.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_longlong]
 _lib.dns_kernel_choice.argtypes = [_H, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                    ctypes.POINTER(ctypes.c_int)]
@@ -192,6 +197,18 @@ def dns_stats_noalloc(h, group, out_dev_ptr):
     """Allocation-free statistics into a caller-owned DEVICE buffer
     [members][8] (see include/dns.h); asynchronous on the handle's stream."""
     return _ck(h, _lib.dns_stats_noalloc(h, group, _vp(out_dev_ptr)))
+
+
+def dns_checked_build():
+    """1 when the loaded library is the bounds-checked debug build."""
+    return _lib.dns_checked_build()
+
+
+def dns_selftest_bounds(h):
+    """Records one failing bounds check (no memory touched) and synchronises;
+    returns the status code (DNS_ERR_CUDA in the checked build, DNS_OK
+    otherwise) without raising."""
+    return _lib.dns_selftest_bounds(h)
 
 
 def dns_selftest_timeout(h):

@@ -11,6 +11,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdns.so")
+# the bounds-checked debug build (-DDNS_CHECK), loaded when DNS_CHECKED=1
+BUILD_CHECK = os.path.join(HERE, "_build_check")
+LIB_CHECK = os.path.join(HERE, "libdns_check.so")
 ROOT = os.path.dirname(HERE)
 
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
@@ -32,8 +35,8 @@ def _deps():
                          if f.endswith((".hpp", ".cuh", ".h"))] + [os.path.join(ROOT, "include", "dns.h")]
 
 
-def _compile(src, extra=()):
-    obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+def _compile(src, extra=(), build_dir=BUILD):
+    obj = os.path.join(build_dir, os.path.basename(src) + ".o")
     if src.endswith(".cu"):
         cmd = [NVCC] + ARCH + NVFLAGS + list(extra) + ["-c", src, "-o", obj]
     else:
@@ -58,25 +61,28 @@ def _locked(fn):
 
 
 @_locked
-def build(force=False, verbose=False, extra_nvcc=()):
-    if (not force and os.path.exists(LIB)
-            and os.path.getmtime(LIB) >= max(os.path.getmtime(p) for p in _deps())):
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+def build(force=False, verbose=False, extra_nvcc=(), checked=False):
+    """Build libdns.so (or, with checked, the bounds-checked libdns_check.so)."""
+    lib, bdir = (LIB_CHECK, BUILD_CHECK) if checked else (LIB, BUILD)
+    extra = tuple(extra_nvcc) + (("-DDNS_CHECK",) if checked else ())
+    if (not force and os.path.exists(lib)
+            and os.path.getmtime(lib) >= max(os.path.getmtime(p) for p in _deps())):
+        return lib
+    os.makedirs(bdir, exist_ok=True)
     with cf.ThreadPoolExecutor(max_workers=len(_sources())) as ex:
-        results = list(ex.map(lambda s: _compile(s, extra_nvcc), _sources()))
+        results = list(ex.map(lambda s: _compile(s, extra, bdir), _sources()))
     if verbose:
         for _, err in results:
             if err:
                 print(err)
     objs = [o for o, _ in results]
-    tmp = LIB + ".tmp"
+    tmp = lib + ".tmp"
     cmd = [NVCC] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart", "-lpthread", "-ldl"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed: %s\n%s" % (r.stdout, r.stderr))
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

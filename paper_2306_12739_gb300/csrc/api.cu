@@ -207,6 +207,16 @@ int check(dns_handle* h, cudaError_t e, const char* what) {
     return DNS_OK;
 }
 
+// A non-zero device status word as an error: a bounded wait that gave up
+// (small codes), or, in the bounds-checked build, the first out-of-range index
+// of a launch (dnsk::BOUNDS_FLAG | kernel << 24 | index & 0xFFFFFF).
+int status_error(dns_handle* h, int sv) {
+    if (sv & dnsk::BOUNDS_FLAG)
+        return fail(h, DNS_ERR_CUDA, "bounds check failed: kernel %d, index %d (mod 2^24); the access was skipped",
+                    (sv >> 24) & 0x3F, sv & 0xFFFFFF);
+    return fail(h, DNS_ERR_TIMEOUT, "a bounded device wait gave up (status %d)", sv);
+}
+
 // Read and clear the device status words after a synchronising call: a kernel
 // whose bounded wait gave up latches 1 there.
 int device_status(dns_handle* h) {
@@ -216,7 +226,7 @@ int device_status(dns_handle* h) {
         if (rc) return rc;
         if (st != 0) {
             cudaMemset(G.v.status, 0, sizeof(int));
-            return fail(h, DNS_ERR_TIMEOUT, "a bounded device wait gave up (status %d)", st);
+            return status_error(h, st);
         }
     }
     return DNS_OK;
@@ -240,7 +250,7 @@ int sync_with_status(dns_handle* h, cudaStream_t st, const char* what) {
         const int sv = h->hstatus[ig];
         if (sv != 0) {
             cudaMemset(h->groups[ig].v.status, 0, sizeof(int));
-            return fail(h, DNS_ERR_TIMEOUT, "a bounded device wait gave up (status %d)", sv);
+            return status_error(h, sv);
         }
     }
     return DNS_OK;
@@ -518,6 +528,7 @@ namespace dnsk {
 std::vector<uint16_t> yderiv_tc_a_image(const std::vector<double>& D1i, const std::vector<double>& D2i, int ny, int kp);
 std::vector<uint16_t> helm_tc_a_images(const std::vector<double>& ops, int npairs, int ny, int kp);
 void launch_wait_selftest(int* status, cudaStream_t st);
+void launch_bounds_selftest(int* status, cudaStream_t st);
 void d2v_tc_image(const std::vector<double>& D2i, int ny, int kp, std::vector<uint16_t>& img, std::vector<int>& rexp);
 cudaError_t noalloc_scratch(double** out);
 size_t noalloc_max_partials();
@@ -1759,6 +1770,23 @@ int dns_selftest_timeout(dns_handle* h) {
     int rc = check(h, cudaGetLastError(), "selftest launch");
     if (rc) return rc;
     return sync_with_status(h, h->stream, "selftest");
+}
+
+int dns_selftest_bounds(dns_handle* h) {
+    if (!h) return DNS_ERR_INVALID;
+    if (!h->bound) return fail(h, DNS_ERR_INVALID, "workspace not bound");
+    dnsk::launch_bounds_selftest(h->groups[0].v.status, h->stream);
+    int rc = check(h, cudaGetLastError(), "selftest launch");
+    if (rc) return rc;
+    return sync_with_status(h, h->stream, "bounds selftest");
+}
+
+int dns_checked_build(void) {
+#ifdef DNS_CHECK
+    return 1;
+#else
+    return 0;
+#endif
 }
 
 int dns_convert_selftest(const double* d_in, float* f_out, const float* f_in, double* d_out, long long n) {

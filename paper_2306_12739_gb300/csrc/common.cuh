@@ -6,6 +6,27 @@
 
 namespace dnsk {
 
+// Bounds checks of the debug build (compiled with -DDNS_CHECK, libdns_check.so):
+// DNS_CK(status, cond, kernel, index) is true when cond holds; when it does not,
+// the first failure of a launch is recorded in the group's device status word
+// as BOUNDS_FLAG | kernel << 24 | (index & 0xFFFFFF) and the caller skips the
+// access (no trap: the next synchronising call reports it).  Without
+// DNS_CHECK the macro is the constant true and costs nothing.
+constexpr int BOUNDS_FLAG = 0x40000000;
+enum CheckKernel {
+    CK_SELFTEST = 1, CK_SPEC = 2, CK_D2V = 3, CK_PLANE_LINES = 4, CK_YDERIV_T = 5, CK_FORCING_T = 6,
+    CK_HELM_T = 7, CK_PACK = 8, CK_UNPACK = 9, CK_SPEC_SMEM = 10
+};
+__device__ __forceinline__ bool ck_record(int* status, bool ok, int kernel, long long index) {
+    if (!ok) atomicCAS(status, 0, BOUNDS_FLAG | (kernel << 24) | (int)(index & 0xFFFFFF));
+    return ok;
+}
+#ifdef DNS_CHECK
+#define DNS_CK(status, cond, kernel, index) (::dnsk::ck_record((status), (cond), (kernel), (long long)(index)))
+#else
+#define DNS_CK(status, cond, kernel, index) (true)
+#endif
+
 template <typename T> struct C2;
 template <> struct C2<double> { typedef double2 type; };
 template <> struct C2<float> { typedef float2 type; };

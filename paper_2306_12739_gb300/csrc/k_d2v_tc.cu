@@ -184,7 +184,7 @@ __global__ void __launch_bounds__(THREADS, 2) k_d2v_tc(GroupView g, const double
         for (int i = 0; i < 4; ++i) {
             const int k = kc * 4 + i;
             double2 x = make_double2(0.0, 0.0);
-            if (col && k < Ny) x = V[((size_t)q * Ny + k) * E + e];
+            if (col && k < Ny && DNS_CK(g.status, q < NM && e < E, CK_D2V, cc)) x = V[((size_t)q * Ny + k) * E + e];
             xv[u][i] = x;
             mr = max(mr, bexp(x.x));
             mi = max(mi, bexp(x.y));
@@ -283,6 +283,7 @@ __global__ void __launch_bounds__(THREADS, 2) k_d2v_tc(GroupView g, const double
                 const int c = c0 + i, j = c >> 1, cc = cc0 + j;
                 if (cc >= ncc) break;
                 const int q = cc / E, e = cc - q * E;
+                if (!DNS_CK(g.status, q < NM && e < E && y < Ny, CK_D2V, cc)) continue;
                 // 2^(e_r + f_c) 2^-14 in two exact steps (each in the float range)
                 const float re = __fadd_rn(hi[i], lo[i]) * sr * p2f(cexp[c] - 1022);
                 const float im = __fadd_rn(hi[i + 1], lo[i + 1]) * sr * p2f(cexp[c + 1] - 1022);

@@ -96,7 +96,7 @@ __global__ void __launch_bounds__(THREADS) k_yderiv_t(GroupView g, const double2
             const int k = (int)dEB.div((unsigned)r), el = r - k * T.EBT;
             const int q = q0 + qq, e = e0 + el;
             double2 a = make_double2(0.0, 0.0), b = a;
-            if (q < NM && e < E) {
+            if (q < NM && e < E && DNS_CK(g.status, k < Ny, CK_YDERIV_T, i)) {
                 const size_t o = ((size_t)q * Ny + k) * E + e;
                 a = V[o];
                 b = H[o];
@@ -158,6 +158,7 @@ __global__ void __launch_bounds__(THREADS) k_yderiv_t(GroupView g, const double2
         for (int i = 0; i < 4; ++i) {
             const int y = r0 + i;
             if (y >= Ny) break;
+            if (!DNS_CK(g.status, q < NM && e < E && 2 * j + 1 < NCR, CK_YDERIV_T, q)) continue;
             const size_t o = ((size_t)y * E + e) * NM + q;
             P[o] = *(const float2*)&Xv[y * NCR + 2 * j];
             P[fs + o] = make_float2(r_av[0][i], r_av[1][i]);
@@ -194,7 +195,7 @@ __global__ void __launch_bounds__(THREADS) k_forcing_t(GroupView g, int s) {
             const int el = (int)dQT.div((unsigned)r), qq = r - el * T.QT;
             const int q = q0 + qq, e = e0 + el;
             float2 ph = make_float2(0.f, 0.f), gg = ph, kv = ph;
-            if (q < NM && e < E) {
+            if (q < NM && e < E && DNS_CK(g.status, k < Ny, CK_FORCING_T, i)) {
                 const size_t o = ((size_t)k * E + e) * NM + q;
                 const float2 nu = N3[o], nv = N3[fs + o], nw = N3[2 * fs + o];
                 const int mi = (int)dNKX.div((unsigned)q), n = q - mi * NKX;
@@ -352,6 +353,7 @@ __device__ __forceinline__ void helm_stage(const GroupView& g, const HelmItem& i
             const int which = (int)dPER.div((unsigned)i), r = i - which * per;
             const int k = (int)d2E.div((unsigned)r), c = r - k * (2 * ec);
             const int q = which == 0 ? it.q1 : it.q2;
+            if (!DNS_CK(g.status, q < g.nmodes && k < Ny && it.e0 + c / 2 < E, CK_HELM_T, i)) continue;
             const size_t o = ((size_t)q * Ny + k) * 2 * E + 2 * it.e0 + c;
             so[u] = k * NC + which * 2 * ec + c;
             xv[u] = needM ? ((const double*)X)[o] : 0.0;
@@ -567,6 +569,15 @@ __global__ void k_wait_selftest(int* status) {
 }  // namespace gt
 
 void launch_wait_selftest(int* status, cudaStream_t st) { gt::k_wait_selftest<<<1, 32, 0, st>>>(status); }
+
+// Self-test of the bounds-check reporting: one check whose condition is false
+// (index 12345 against a limit of 0), touching no memory; recorded only by the
+// checked build.
+__global__ void k_bounds_selftest(int* status) {
+    const long long idx = 12345 + threadIdx.x;
+    (void)DNS_CK(status, idx < 0, CK_SELFTEST, idx);
+}
+void launch_bounds_selftest(int* status, cudaStream_t st) { k_bounds_selftest<<<1, 1, 0, st>>>(status); }
 
 size_t helm_t_smem_bytes(const GroupView& g) {
     const int nc = 2 * 2 * helm_member_chunk(g);

@@ -154,6 +154,9 @@ k_plane_lines(GroupView g, const double* __restrict__ Ucur, const double* __rest
     const int y = blockIdx.x, e = blockIdx.y, E = g.E, Ny = g.ny, My = g.my;
     const size_t fs = (size_t)Ny * E * NM;
     const size_t off0 = ((size_t)y * E + e) * NM;
+    // the grid covers the interior planes and members exactly; the kept-mode
+    // count is the compile-time one (checked by the debug build)
+    if (!DNS_CK(g.status, y < Ny && e < E && NM == g.nmodes, CK_PLANE_LINES, (long long)y * E + e)) return;
 
     // ---- stage inputs [f][m][n] (padded rows) and tables, all copies in flight at once
     {

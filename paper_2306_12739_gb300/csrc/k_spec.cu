@@ -126,6 +126,7 @@ __device__ void finish_member(const GroupView& g, int s, int e, unsigned char* s
 __device__ void mean_cta(const GroupView& g, int s, int b, unsigned char* sm) {
     const int E = g.E, per = (g.ny + 7) / 8;
     const int e = b % E, r = b / E;
+    if (!DNS_CK(g.status, r < per, CK_SPEC, b)) return;
     mean_rows(g, s, e, r * (THREADS / 32), sm);
     __shared__ int last;
     __threadfence();        // this CTA's rows are visible device-wide before it counts itself
@@ -136,6 +137,13 @@ __device__ void mean_cta(const GroupView& g, int s, int b, unsigned char* sm) {
     __threadfence();
     finish_member(g, s, e, sm);
     if (threadIdx.x == 0) g.mcnt[e] = 0;
+}
+
+// Bounds check of the debug build (a no-op otherwise): the mode, interior
+// plane and member of an access, which fix every index of the H and P layouts
+__device__ __forceinline__ bool in_range(const GroupView& g, int q, int y, int e) {
+    return DNS_CK(g.status, (unsigned)q < (unsigned)g.nmodes && (unsigned)y < (unsigned)g.ny && (unsigned)e < (unsigned)g.E,
+                  CK_SPEC, ((long long)q * g.ny + y) * g.E + e);
 }
 
 // Columns of a CTA: j = which * ec + el (which 0: mode +m, 1: mode -m; el the
@@ -211,7 +219,7 @@ __device__ __forceinline__ void apply_prefetch(const GroupView& g, int s, int f,
         const int y = r0 + i;
         x[i] = make_double2(0.0, 0.0);
         m1[i] = make_float2(0.f, 0.f);
-        if (y >= Ny) continue;
+        if (y >= Ny || !in_range(g, q, y, e)) continue;
         const size_t o = ((size_t)q * Ny + y) * E + e;
         x[i] = X[o];
         if (s == 2) m1[i] = M1[o];
@@ -235,6 +243,7 @@ __device__ __forceinline__ void apply_epilogue(const GroupView& g, int s, int f,
     for (int i = 0; i < 4; ++i) {
         const int y = r0 + i;
         if (y >= Ny) break;
+        if (!in_range(g, q, y, e) || !DNS_CK(g.status, 2 * j + 1 < VS, CK_SPEC_SMEM, y * VS + 2 * j)) continue;
         const size_t o = ((size_t)q * Ny + y) * E + e;
         const float2 m1 = (s == 2) ? m1s[i] : make_float2(ma[0][i], ma[1][i]);
         if (s == 1) M1[o] = m1;
@@ -292,7 +301,7 @@ __global__ void __launch_bounds__(THREADS, 2) k_spec(GroupView g, int s) {
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    if (tid == 0) {
+    if (tid == 0 && DNS_CK(g.status, c.p < g.npairs, CK_SPEC, c.p)) {
         const float* src = g.opsfT[hidx] + (size_t)c.p * 4 * mat;
         const unsigned mb = (unsigned)(mat * sizeof(float));
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_a),
@@ -318,6 +327,7 @@ __global__ void __launch_bounds__(THREADS, 2) k_spec(GroupView g, int s) {
         for (int i = tid; i < total; i += THREADS) {
             const int y = i / c.C, j = i - y * c.C;
             const int q = col_q(c, j), e = col_e(c, j);
+            if (!in_range(g, q, y, e) || !DNS_CK(g.status, 2 * j + 1 < VS, CK_SPEC_SMEM, y * VS + 2 * j)) continue;
             const float kz = g.kztf[q / NKX];
             const size_t op = ((size_t)y * E + e) * NM + q;
             const size_t oh = ((size_t)q * Ny + y) * E + e;
@@ -334,7 +344,7 @@ __global__ void __launch_bounds__(THREADS, 2) k_spec(GroupView g, int s) {
             const float bx = kz * nu.x - kx * nw.x, by = kz * nu.y - kx * nw.y;   // i kz Nu - i kx Nw
             float2 kv = make_float2(-k2 * nv.x, -k2 * nv.y);
             float2 G = make_float2(-by, bx);
-            if (forced) {
+            if (forced && DNS_CK(g.status, q / NKX < g.nkz, CK_SPEC, q)) {
                 const size_t o = ((size_t)(q / NKX) * Ny + y) * E + e, half = (size_t)g.nkz * Ny * E;
                 kv.x += (float)g.noise[o].x; kv.y += (float)g.noise[o].y;
                 G.x += (float)g.noise[half + o].x; G.y += (float)g.noise[half + o].y;
@@ -384,7 +394,7 @@ __global__ void __launch_bounds__(THREADS, 2) k_spec(GroupView g, int s) {
             for (int i = 0; i < 4; ++i) {
                 const int y = r0 + i;
                 pav[i] = make_float2(0.f, 0.f);
-                if (s != 0 && y < Ny) pav[i] = Av[((size_t)q * Ny + y) * E + e];
+                if (s != 0 && y < Ny && in_range(g, q, y, e)) pav[i] = Av[((size_t)q * Ny + y) * E + e];
             }
             float a[2][4];
             d1mm(D1S, PH, Ny, RP, VS, r0, 2 * j, a);
@@ -392,6 +402,7 @@ __global__ void __launch_bounds__(THREADS, 2) k_spec(GroupView g, int s) {
             for (int i = 0; i < 4; ++i) {
                 const int y = r0 + i;
                 if (y >= Ny) break;
+                if (!in_range(g, q, y, e)) continue;
                 const float2 kv = *(const float2*)&KV[y * VS + 2 * j];
                 const float2 F = make_float2(kv.x - a[0][i], kv.y - a[1][i]);
                 const size_t oh = ((size_t)q * Ny + y) * E + e;
@@ -476,6 +487,7 @@ __global__ void __launch_bounds__(THREADS, 2) k_spec(GroupView g, int s) {
             for (int i = 0; i < 4; ++i) {
                 const int y = r0 + i;
                 if (y >= Ny) break;
+                if (!in_range(g, q, y, e)) continue;
                 const size_t o = ((size_t)y * E + e) * NM + q;
                 P5[3 * fs5 + o] = *(const float2*)&EN[y * VS + 2 * j];
                 P5[4 * fs5 + o] = make_float2(a[0][i], a[1][i]);
@@ -532,6 +544,7 @@ __global__ void __launch_bounds__(THREADS, 2) k_spec(GroupView g, int s) {
             for (int i = 0; i < 2; ++i) {
                 const int y = r0 + i;
                 if (y >= Ny) break;
+                if (!in_range(g, q, y, e)) continue;
                 const size_t o = ((size_t)y * E + e) * NM + q;
                 P5[o] = *(const float2*)&VH[y * VS + 2 * j];
                 P5[fs5 + o] = make_float2(d1[i][0], d1[i][1]);

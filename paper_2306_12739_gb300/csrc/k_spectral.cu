@@ -565,6 +565,7 @@ __global__ void __launch_bounds__(TRANSFER_BOUND) k_pack(GroupView g, int member
             b = make_double2(0.5 * (b.x + bp.x), 0.5 * (b.y - bp.y));
         }
         if (q == q_mean) { a = make_double2(0.0, 0.0); b = a; }
+        if (!DNS_CK(g.status, member0 + el < E, CK_PACK, idx)) continue;
         size_t h = ((size_t)q * Ny + y) * E + member0 + el;
         g.v_t[h] = a;
         g.e_t[h] = b;
@@ -572,6 +573,7 @@ __global__ void __launch_bounds__(TRANSFER_BOUND) k_pack(GroupView g, int member
     if (sU) {
         const size_t nu = (size_t)count * g.my, o = (size_t)member0 * g.my;
         for (size_t i = t0; i < nu; i += nt) {
+            if (!DNS_CK(g.status, o + i < (size_t)E * g.my, CK_PACK, i)) continue;
             g.U_t[o + i] = sU[i];
             g.W_t[o + i] = sW[i];
         }
@@ -591,12 +593,14 @@ __global__ void __launch_bounds__(TRANSFER_BOUND) k_unpack(GroupView g, int memb
         int q = (int)(idx % nmodes);
         int y = (int)((idx / nmodes) % Ny);
         int el = (int)(idx / ((size_t)nmodes * Ny));
+        if (!DNS_CK(g.status, member0 + el < E, CK_UNPACK, idx)) continue;
         size_t h = ((size_t)q * Ny + y) * E + member0 + el;
         if (dv) dv[idx] = g.v_t[h];
         if (de) de[idx] = g.e_t[h];
     }
     const size_t nu = (size_t)count * g.my, o = (size_t)member0 * g.my;
     for (size_t i = t0; i < nu; i += nt) {
+        if (!DNS_CK(g.status, o + i < (size_t)E * g.my, CK_UNPACK, i)) continue;
         if (dU) dU[i] = g.U_t[o + i];
         if (dW) dW[i] = g.W_t[o + i];
     }
