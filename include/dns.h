@@ -126,8 +126,11 @@ typedef struct {
     int persistent;                /* reserved, must be 0 */
     unsigned long long barrier_timeout_ns;  /* reserved, 0 */
     const char* autotune_cache;    /* optional text file: autotuner decisions are read from it
-                                      and appended to it ("ygemm|plane|helm Mx My Mz E choice");
-                                      NULL = none */
+                                      and appended to it ("ygemm|plane|helm Mx My Mz E choice" for
+                                      kernel variants, "spec_ec|ytile Mx My Mz E value" for the
+                                      tile shapes: members per CTA of the fused stage, first
+                                      column-tile cap of the register-tiled y-derivatives; the
+                                      shapes never change a result); NULL = none */
     int ygemm;                     /* mixed path y-derivatives of the step-by-step stage
                                       (helm 1-3): 0 autotuned at dns_bind_workspace, 1
                                       register-tiled FP32 with D2 v summed in float-float, 2

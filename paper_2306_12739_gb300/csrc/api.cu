@@ -420,6 +420,33 @@ std::string tune_plane_key(const GroupView& v) {
     return b;
 }
 
+// the integer after key on its last line in the cache (0: none)
+int cache_lookup_value(const char* path, const std::string& key) {
+    if (!path) return 0;
+    FILE* f = fopen(path, "r");
+    if (!f) return 0;
+    char line[256];
+    int found = 0;
+    while (fgets(line, sizeof line, f)) {
+        std::string ln(line);
+        if (ln.compare(0, key.size(), key) == 0 && ln.size() > key.size() + 1) found = atoi(ln.c_str() + key.size() + 1);
+    }
+    fclose(f);
+    return found;
+}
+
+// a tile-shape decision: the chosen value and every candidate's time
+void cache_store_shape(const char* path, const std::string& key, int choice, const std::vector<int>& vals,
+                       const std::vector<float>& ms) {
+    if (!path) return;
+    FILE* f = fopen(path, "a");
+    if (!f) return;
+    fprintf(f, "%s %d   #", key.c_str(), choice);
+    for (size_t i = 0; i < vals.size(); ++i) fprintf(f, " value %d %.4f ms", vals[i], ms[i]);
+    fprintf(f, "\n");
+    fclose(f);
+}
+
 int cache_lookup(const char* path, const std::string& key) {
     if (!path) return 0;
     FILE* f = fopen(path, "r");
@@ -912,6 +939,57 @@ int dns_bind_workspace(dns_handle* h, void* dev_ptr, size_t bytes) {
         decided[key] = choice;
         v.ygemm = choice;
     }
+    // The per-wavenumber stage of a DNS group (step-by-step SIMT or tcgen05
+    // apply, or the fused stage) is chosen by timing whole steps of the handle,
+    // every member block of the group on the candidate: what it costs inside
+    // the step graph, where member blocks and groups run concurrently, is not
+    // what a kernel costs alone (the 64-member 32x49x32 Couette blocks: the
+    // fused stage wins alone, the step-by-step stage by 20 % in the step).
+    // Groups still undecided run the SIMT apply meanwhile.
+    for (size_t gi = 0; gi < h->parts.size(); ++gi) {
+        GroupView& v0 = h->groups[h->parts[gi][0].ig].v;
+        if (v0.lin || v0.helm != 0) continue;
+        const std::string key = tune_helm_key(v0);
+        int choice = decided.count(key) ? decided[key] : cache_lookup(h->cfg.autotune_cache, key);
+        if ((choice == 2 && !dnsk::helm_tc_supported(v0)) || (choice == 4 && !dnsk::spec_supported(v0)) ||
+            choice == 3)
+            choice = 0;
+        if (!choice) {
+            float best[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+            cudaEvent_t e0, e1;
+            cudaEventCreate(&e0);
+            cudaEventCreate(&e1);
+            for (int cand = 1; cand <= 4 && !rc; ++cand) {
+                if (cand == 3 || (cand == 2 && !dnsk::helm_tc_supported(v0)) ||
+                    (cand == 4 && !dnsk::spec_supported(v0)))
+                    continue;
+                for (const auto& P : h->parts[gi]) h->groups[P.ig].v.helm = cand;
+                for (int w = 0; w < 2; ++w) enqueue_step(h);
+                cudaEventRecord(e0, st);
+                for (int r = 0; r < 3; ++r) enqueue_step(h);
+                cudaEventRecord(e1, st);
+                rc = check(h, cudaEventSynchronize(e1), "autotune per-wavenumber stage");
+                if (!rc) cudaEventElapsedTime(&best[cand], e0, e1);
+                best[cand] /= 3.f;
+            }
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            h->launches = 0;
+            if (rc) return rc;
+            if ((rc = device_status(h))) return rc;
+            choice = 0;
+            for (int cand = 1; cand <= 4; ++cand)
+                if (best[cand] > 0.f && (choice == 0 || best[cand] < best[choice])) choice = cand;
+            cache_store(h->cfg.autotune_cache, key, choice, best, 4);
+        }
+        decided[key] = choice;
+        for (const auto& P : h->parts[gi]) {
+            GroupView& v = h->groups[P.ig].v;
+            v.helm = choice;
+            if (choice == 4) v.ygemm = 1;
+        }
+    }
+    // linear groups: the apply kernels alone
     for (auto& G : h->groups) {
         GroupView& v = G.v;
         if (v.helm != 0) continue;
@@ -971,6 +1049,91 @@ int dns_bind_workspace(dns_handle* h, void* dev_ptr, size_t bytes) {
         decided[key] = choice;
         v.helm = choice;
         if (choice == 4) v.ygemm = 1;
+    }
+    // Tile shapes (neither changes a result: every column is computed the same
+    // way whatever tile holds it).  Members per CTA of the fused stage:
+    for (auto& G : h->groups) {
+        GroupView& v = G.v;
+        if (!precision_mixed(h) || v.helm != 4 || v.E < 2) continue;
+        char kb[96];
+        snprintf(kb, sizeof kb, "spec_ec %d %d %d %d", v.mx, v.my, v.mz, v.E);
+        const std::string key = kb;
+        std::vector<int> cands;
+        for (int ec : {std::min(v.E, 8), (std::min(v.E, 8) + 1) / 2, 2}) {
+            v.spec_ec = ec;
+            if (ec >= 1 && dnsk::spec_supported(v) && std::find(cands.begin(), cands.end(), ec) == cands.end())
+                cands.push_back(ec);
+        }
+        int choice = decided.count(key) ? decided[key] : cache_lookup_value(h->cfg.autotune_cache, key);
+        if (std::find(cands.begin(), cands.end(), choice) == cands.end()) choice = 0;
+        if (!choice && cands.size() == 1) choice = cands[0];
+        if (!choice) {
+            std::vector<float> ms(cands.size(), 0.f);
+            cudaEvent_t e0, e1;
+            cudaEventCreate(&e0);
+            cudaEventCreate(&e1);
+            for (size_t ci = 0; ci < cands.size() && !rc; ++ci) {
+                v.spec_ec = cands[ci];
+                for (int w = 0; w < 2; ++w) dnsk::launch_spec(v, 1, st);
+                cudaEventRecord(e0, st);
+                for (int r = 0; r < 5; ++r) dnsk::launch_spec(v, 1, st);
+                cudaEventRecord(e1, st);
+                rc = check(h, cudaEventSynchronize(e1), "autotune fused-stage tile");
+                if (!rc) cudaEventElapsedTime(&ms[ci], e0, e1);
+            }
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            if (rc) return rc;
+            if ((rc = device_status(h))) return rc;
+            size_t best = 0;
+            for (size_t ci = 1; ci < cands.size(); ++ci)
+                if (ms[ci] < ms[best]) best = ci;
+            choice = cands[best];
+            for (auto& m : ms) m /= 5.f;
+            cache_store_shape(h->cfg.autotune_cache, key, choice, cands, ms);
+        }
+        decided[key] = choice;
+        v.spec_ec = choice;
+    }
+    // First column-tile cap of the register-tiled y-derivatives (in the
+    // step-by-step stage every sub-step, with the fused stage for every newly
+    // set state):
+    for (auto& G : h->groups) {
+        GroupView& v = G.v;
+        if (!precision_mixed(h) || v.ygemm != 1) continue;
+        char kb[96];
+        snprintf(kb, sizeof kb, "ytile %d %d %d %d", v.mx, v.my, v.mz, v.E);
+        const std::string key = kb;
+        const std::vector<int> cands = {16, 32, 64};
+        int choice = decided.count(key) ? decided[key] : cache_lookup_value(h->cfg.autotune_cache, key);
+        if (std::find(cands.begin(), cands.end(), choice) == cands.end()) choice = 0;
+        if (!choice) {
+            std::vector<float> ms(cands.size(), 0.f);
+            cudaEvent_t e0, e1;
+            cudaEventCreate(&e0);
+            cudaEventCreate(&e1);
+            for (size_t ci = 0; ci < cands.size() && !rc; ++ci) {
+                v.yd_cap = cands[ci];
+                for (int w = 0; w < 2; ++w) dnsk::launch_yderiv_t(v, v.v_t, v.e_t, st);
+                cudaEventRecord(e0, st);
+                for (int r = 0; r < 5; ++r) dnsk::launch_yderiv_t(v, v.v_t, v.e_t, st);
+                cudaEventRecord(e1, st);
+                rc = check(h, cudaEventSynchronize(e1), "autotune y-derivative tile");
+                if (!rc) cudaEventElapsedTime(&ms[ci], e0, e1);
+            }
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            if (rc) return rc;
+            if ((rc = device_status(h))) return rc;
+            size_t best = 0;
+            for (size_t ci = 1; ci < cands.size(); ++ci)
+                if (ms[ci] < ms[best]) best = ci;
+            choice = cands[best];
+            for (auto& m : ms) m /= 5.f;
+            cache_store_shape(h->cfg.autotune_cache, key, choice, cands, ms);
+        }
+        decided[key] = choice;
+        v.yd_cap = choice;
     }
     h->bound = true;
     return DNS_OK;

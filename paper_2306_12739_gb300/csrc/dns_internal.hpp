@@ -58,6 +58,9 @@ struct GroupView {
     const float* D2T;
     const float* D2Tl;    // D2T's residual: D2i - (double) D2T in single precision (compensated D2 v)
     int d2tc;             // fused stage: 1 = D2 v of the new state by the tensor-core digit kernel
+    int spec_ec;          // fused stage: members per CTA (0 = up to 8), set by the autotuner
+    int yd_cap;           // register-tiled y-derivatives: first column-tile cap (0 = 64, or 32 above
+                          //    Ny = 96), halved while the grid is short of 3 CTAs per SM; autotuned
     const void* D2oz;     // its image of D2: slices of 7-bit digits [64 rows][kp] (BF16)
     const int* D2ozexp;   // [64] row exponents of that image
     const double* ccw;    // [My]

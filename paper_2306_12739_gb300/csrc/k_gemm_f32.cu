@@ -29,8 +29,8 @@ struct Tile {
 // while the grid would hold fewer than three CTAs per SM (152 SMs): first fewer
 // modes per tile, then, for large member counts with few modes (linear groups),
 // shorter member runs (never below 16 members: 128-byte runs of the H layout).
-__host__ __device__ inline Tile tile_of(int E, int ny, int nm) {
-    int cap = ny <= 96 ? 64 : 32;
+__host__ __device__ inline Tile tile_of(int E, int ny, int nm, int cap0 = 0) {
+    int cap = cap0 > 0 ? cap0 : (ny <= 96 ? 64 : 32);
     Tile t;
     for (;;) {
         t.EBT = E < cap ? E : cap;
@@ -53,8 +53,8 @@ constexpr size_t YD_SMEM_MAX = 200 * 1024;
 __host__ __device__ inline size_t yd_bytes(int ny, int rp, int nc, bool stage_d2l) {
     return ((size_t)(stage_d2l ? 3 : 2) * ny * rp + 3 * (size_t)ny * 2 * nc) * sizeof(float);
 }
-__host__ __device__ inline Tile yd_tile(int E, int ny, int rp, int nm) {
-    Tile t = tile_of(E, ny, nm);
+__host__ __device__ inline Tile yd_tile(int E, int ny, int rp, int nm, int cap0) {
+    Tile t = tile_of(E, ny, nm, cap0);
     while (yd_bytes(ny, rp, t.NC, false) > YD_SMEM_MAX && t.NC > 4) {
         if (t.QT > 1) t.QT /= 2;
         else t.EBT = (t.EBT + 1) / 2;
@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(THREADS) k_yderiv_t(GroupView g, const double2
                                                      const double2* __restrict__ H, int sprev) {
     extern __shared__ __align__(16) unsigned char sm[];
     const int Ny = g.ny, RP = g.rp, E = g.E, NM = g.nmodes;
-    const Tile T = yd_tile(E, Ny, RP, NM);
+    const Tile T = yd_tile(E, Ny, RP, NM, g.yd_cap);
     const bool stage_d2l = yd_stage_d2l(Ny, RP, T.NC);
     if (mean_finish_rows(g, sprev, (E + T.EBT - 1) / T.EBT, sm)) return;
     const int q0 = blockIdx.x * T.QT, e0 = blockIdx.y * T.EBT;
@@ -587,7 +587,7 @@ size_t helm_t_smem_bytes(const GroupView& g) {
 }
 
 size_t yderiv_t_smem_bytes(const GroupView& g) {
-    gt::Tile t = gt::yd_tile(g.E, g.ny, g.rp, g.nmodes);
+    gt::Tile t = gt::yd_tile(g.E, g.ny, g.rp, g.nmodes, g.yd_cap);
     return gt::yd_bytes(g.ny, g.rp, t.NC, gt::yd_stage_d2l(g.ny, g.rp, t.NC));
 }
 
@@ -597,7 +597,7 @@ size_t forcing_t_smem_bytes(const GroupView& g) {
 }
 
 void launch_yderiv_t(const GroupView& g, const double2* v, const double2* e, cudaStream_t st, int sprev) {
-    gt::Tile t = gt::yd_tile(g.E, g.ny, g.rp, g.nmodes);
+    gt::Tile t = gt::yd_tile(g.E, g.ny, g.rp, g.nmodes, g.yd_cap);
     dim3 grid((g.nmodes + t.QT - 1) / t.QT, (g.E + t.EBT - 1) / t.EBT);
     grid.y += mean_finish_extra_rows(g, grid.x, sprev);
     gt::k_yderiv_t<<<grid, gt::THREADS, yderiv_t_smem_bytes(g), st>>>(g, v, e, sprev);

@@ -41,7 +41,7 @@ constexpr int NCR_MAX = 32;   // real columns per CTA (modes x members x re/im)
 
 // Member chunk: at most NCR_MAX real columns per CTA (two modes, re and im).
 __host__ __device__ inline int chunk_members(const GroupView& g) {
-    const int ec = NCR_MAX / 4;
+    const int ec = (g.spec_ec > 0 && g.spec_ec <= NCR_MAX / 4) ? g.spec_ec : NCR_MAX / 4;
     return g.E < ec ? g.E : ec;
 }
 __host__ __device__ inline int chunks(const GroupView& g) {

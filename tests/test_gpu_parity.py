@@ -376,16 +376,24 @@ def test_autotuner_picks_a_variant_caches_it_and_matches_that_variant(tmp_path):
     got = ens.get_state(0)
     ens.close()
     lines = sorted(ln for ln in open(cache) if ln.strip())
-    assert len(lines) == 3
-    # keyed by the member block's size: 8 members run as 2 blocks of 4, tuned once
-    assert lines[0].startswith("helm 32 33 32 4 ") and lines[1].startswith("plane 32 33 32 4 ")
-    assert lines[2].startswith("ygemm 32 33 32 4 ")
+    keys = [ln.split()[0] for ln in lines]
+    # keyed by the member block's size: 8 members run as 2 blocks of 4, tuned once;
+    # the tile shapes: the fused stage's members per CTA, the y-derivative tile
+    assert all(ln.split()[1:5] == ["32", "33", "32", "4"] for ln in lines)
+    want = {"helm", "plane", "ygemm"} | ({"ytile"} if choice == "simt" else set()) | \
+        ({"spec_ec"} if helm == "fused" else set())
+    assert sorted(keys) == sorted(want)
     ens2 = dns.Ensemble([g], precision="mixed", autotune_cache=cache)   # read back, no new timing
     assert dns.dns_kernel_choice(ens2.h, 0) == choice
     assert dns.dns_kernel_choice(ens2.h, 0, "plane") == plane
     assert dns.dns_kernel_choice(ens2.h, 0, "helm") == helm
+    ens2.set_state(0, st["v"], st["eta"], st["U"], st["W"])
+    ens2.step(3)
+    again = ens2.get_state(0)                  # the cached choices reproduce the tuned run
     ens2.close()
-    assert len([ln for ln in open(cache) if ln.strip()]) == 3
+    assert len([ln for ln in open(cache) if ln.strip()]) == len(lines)
+    for a, b in zip(got, again):
+        assert np.array_equal(a, b)
     ref = _run(g, st, 3, "mixed", ygemm=choice, plane=plane, helm=helm)
     for a, b in zip(got, ref):
         assert np.array_equal(a, b)
