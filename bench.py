@@ -781,7 +781,10 @@ def gpu_arm(args, rank, world, dist):
             "metric": "max over members of max|mixed - fp64| / max|fp64| per field, after the same seeded steps "
                       "(mean flow: U00 and W00 as one field; w00_alone on its own scale)",
             "max": {k: max(e[k] for e in errs if k in e) for k in fields},
-            "tolerance": {"v": 1e-6, "eta": 1e-6, "mean_flow": 1e-6, "w00_alone": 1e-5},
+            # the parity tests' bounds: DNS fields 1e-6 (W00 on its own scale 3e-5), linearised
+            # disturbance vectors 1e-5 (their growth amplifies the single-precision rounding)
+            "tolerance": ({"v": 1e-5, "eta": 1e-5} if any(g.get("linear") for g in groups) else
+                          {"v": 1e-6, "eta": 1e-6, "mean_flow": 1e-6, "w00_alone": 3e-5}),
             "per_group": [{k: e[k] for k in fields if k in e} for e in errs],
             "per_member_first_group": errs[0]["per_member"],
         }
