@@ -233,12 +233,20 @@ def kernel_work(cls, g, precision):
         return "alu", S * 2 * 2 * ny, "flop"
     if cls == "spec":
         # the fused stage: forcing (D1 phi), the implicit apply (M - I and P of
-        # both fields; the third sub-step reuses (M_1 - I) x_t), the three
-        # y-derivatives of the new state; 2 ny flops per output value of each
+        # both fields; the third sub-step reuses (M_1 - I) x_t), the
+        # y-derivatives of the new state (D2 v too where no separate kernel
+        # computes it); 2 ny flops per output value of each
         npairs = nkx * (nkz // 2 + 1)
         apply = 2 * npairs * 2 * 2 * ny * ny * 4 * E * (5.0 / 6.0)
-        return "alu", S * 2 * 2 * ny * 4 + apply, "flop"
+        return "alu", S * 2 * 2 * ny * (4 if spec_computes_d2v(g) else 3) + apply, "flop"
     return "alu", E * 4.0 * (g["my"]) ** 2, "flop"
+
+
+def spec_computes_d2v(g):
+    """The fused stage writes D2 v itself: with the digit product inside it
+    (per-wavenumber stage "fused_d2v") or, above Ny = 64, in float-float; else
+    the separate tensor-core D2 v kernel does."""
+    return g.get("_stage") == "fused_d2v" or g["my"] - 2 > 64
 
 
 def member_blocks(g):
@@ -271,13 +279,14 @@ def kernel_bytes(cls, g, precision):
     if cls == "spec":
         # N in (P layout), the state x_t in (first two sub-steps) and x+ out
         # (FP64), (M_1 - I) x_t out / in, the RK accumulators of F and G, the
-        # operators (all four, two in the third sub-step), five P-layout fields out
+        # operators (all four, two in the third sub-step), the P-layout fields
+        # out (v, Dv, eta, D eta, and D2 v where this stage computes it)
         rp = (ny + 3) // 4 * 4
-        npairs = nkx * (nkz // 2 + 1)
+        npairs = nkx * (nkz // 2 + 1) - 1              # the mean mode's pair has no CTA
         ops = member_blocks(g) * npairs * ((4 + 4 + 2) / 3.0) * ny * rp * 4
         state = 2 * S * (16 * (2.0 / 3.0) + 16 + 8 * (2.0 / 3.0))
         acc = 2 * 8 * S * (4.0 / 3.0)
-        return ops + 3 * 8 * S + state + acc + 5 * 8 * S
+        return ops + 3 * 8 * S + state + acc + (5 if spec_computes_d2v(g) else 4) * 8 * S
     if cls == "helm":
         rp = (ny + 3) // 4 * 4
         npairs = nkx * (nkz // 2 + 1)
@@ -625,6 +634,8 @@ def gpu_arm(args, rank, world, dist):
     ens, total_ms, launches, clocks = timed_run(precision, args.steps, args.warmup, flush)
     choices = [dict(ygemm=dns.dns_kernel_choice(ens.h, gi, "ygemm"), plane=dns.dns_kernel_choice(ens.h, gi, "plane"),
                     helm=dns.dns_kernel_choice(ens.h, gi, "helm")) for gi in range(len(groups))]
+    for g, ch in zip(groups, choices):
+        g["_stage"] = ch["helm"]            # the byte and flop models of the fused stage depend on it
     total_ms = reduce_max(total_ms, dist, dev)
     ms_step = total_ms / args.steps
     value = aggregate(members * args.steps, total_ms / 1e3, world)
@@ -833,7 +844,7 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparator run")
     ap.add_argument("--plane", choices=["default", "cta", "cluster", "lines"], default="default",
                     help="plane-stage kernel (default: autotuned among those the grid supports)")
-    ap.add_argument("--helm", choices=["default", "simt", "tc", "persist", "fused"], default="default",
+    ap.add_argument("--helm", choices=["default", "simt", "tc", "persist", "fused", "fused_d2v"], default="default",
                     help="per-wavenumber stage of the mixed path (default: the fused stage where the group "
                          "supports it, else the autotuned implicit apply)")
     ap.add_argument("--ygemm", choices=["default", "simt", "tc"], default="default",

@@ -149,8 +149,8 @@ typedef struct {
                                       variant the group's size lacks is ignored */
     int helm;                      /* mixed path per-wavenumber stage: 0 autotuned at
                                       dns_bind_workspace (DNS groups: 1 and 2, each timed with the
-                                      y-derivatives and the forcing, against 4; linear groups: 1
-                                      against 2),
+                                      y-derivatives and the forcing, against 4 and 5; linear
+                                      groups: 1 against 2),
                                       1 register-tiled FP32 implicit apply (one CTA per
                                       wavenumber pair and field), 2 tcgen05 tensor cores with
                                       split-BF16 operands (groups with My <= 66 and <= 64 members;
@@ -161,7 +161,11 @@ typedef struct {
                                       launch per sub-step does the forcing, RK3 combination,
                                       implicit apply, the y-derivatives of the new state and the
                                       mean flow (DNS groups whose operators fit in shared memory:
-                                      My <= 99; linear groups use 1 or 2) */
+                                      My <= 99; linear groups use 1 or 2), 5 the fused stage
+                                      with D2 v of the new state computed inside the same launch
+                                      (the tensor-core digit product of the separate D2 v
+                                      kernel, bit for bit the same result; groups with
+                                      My <= 66, at most 4 members per CTA; others run 4) */
 } dns_config;
 
 /* One-point statistics of one member (paper Sec. 4), computed from the current
@@ -298,8 +302,8 @@ const char* dns_last_error(const dns_handle* h);
  * dns_bind_workspace): ygemm 1 register-tiled FP32 / 2 tcgen05 y-contraction;
  * plane 1 one CTA per plane / 2 a thread-block cluster per plane / 3 line-owned
  * single CTA per plane; helm 1 register-tiled FP32 / 2 tcgen05 implicit apply /
- * 3 persistent register-tiled FP32 / 4 the fused per-wavenumber stage.
- * Any output may be NULL. */
+ * 3 persistent register-tiled FP32 / 4 the fused per-wavenumber stage / 5 the
+ * fused stage with D2 v inside it.  Any output may be NULL. */
 int dns_kernel_choice(const dns_handle* h, int group, int* ygemm, int* plane, int* helm);
 
 /* Number of kernel launches enqueued by the last dns_step call (all steps). */

@@ -121,6 +121,11 @@ bool precision_mixed(const dns_handle* h) { return h->cfg.precision == DNS_PREC_
 
 // the tcgen05 implicit apply may run: its operator images are needed
 bool helm_tc_candidate(const GroupView& v) { return v.helm == 2 || (v.helm == 0 && dnsk::helm_tc_supported(v)); }
+// the fused stage can run with its D2 v inside (helm request 5); v's own flag is untouched
+bool d2fuse_ok(GroupView v) {
+    v.d2fuse = 1;
+    return dnsk::spec_d2fuse_supported(v);
+}
 
 // Largest My at which DNS groups may take the FP32-accumulated tensor-core
 // y-derivatives (see choose_variants)
@@ -302,7 +307,7 @@ void enqueue_group(dns_handle* h, HostGroup& G, cudaStream_t st, Timer* tm) {
             dnsk::launch_spec(g, s, st);
             mark(DNS_K_SPEC);
             h->launches += 2;
-            if (g.d2tc) {
+            if (g.d2tc && !g.d2fuse) {
                 dnsk::launch_d2v_tc(g, s == 2 ? g.v_t : g.v_s, st);
                 mark(DNS_K_D2V);
                 h->launches += 1;
@@ -457,7 +462,7 @@ int cache_lookup(const char* path, const std::string& key) {
         std::string ln(line);
         if (ln.compare(0, key.size(), key) == 0 && ln.size() > key.size() + 1) {
             int c = atoi(ln.c_str() + key.size() + 1);
-            if (c >= 1 && c <= 4) found = c;
+            if (c >= 1 && c <= 5) found = c;
         }
     }
     fclose(f);
@@ -500,7 +505,7 @@ int choose_variants(dns_handle* h, const dns_config* cfg, GroupView& v, int gi) 
     // forcing) and 4
     v.helm = 1;
     if (precision_mixed(h)) {
-        if (cfg->helm == 4) v.helm = dnsk::spec_supported(v) ? 4 : 0;
+        if (cfg->helm == 4 || cfg->helm == 5) v.helm = dnsk::spec_supported(v) ? 4 : 0;
         else if (cfg->helm == 0) v.helm = 0;
         else if (cfg->helm == 2 && dnsk::helm_tc_supported(v)) v.helm = 2;
         else if (cfg->helm == 3) v.helm = 3;
@@ -508,6 +513,8 @@ int choose_variants(dns_handle* h, const dns_config* cfg, GroupView& v, int gi) 
     if (v.helm == 4) v.ygemm = 1;   // only the derivatives of a newly set state run separately
     // with the fused stage, D2 v of each new state on tensor cores where the rows fit
     v.d2tc = ((v.helm == 4 || v.helm == 0) && dnsk::spec_supported(v) && dnsk::d2v_tc_supported(v)) ? 1 : 0;
+    // and, on request (helm 5) or by the autotuner, that digit product inside the fused launch
+    v.d2fuse = (cfg->helm == 5 && v.helm == 4 && d2fuse_ok(v)) ? 1 : 0;
     // plane-stage kernel: single CTA per plane where it fits, a thread-block
     // cluster (distributed shared memory) where it does not; where both exist
     // the autotuner decides at bind time
@@ -951,19 +958,25 @@ int dns_bind_workspace(dns_handle* h, void* dev_ptr, size_t bytes) {
         if (v0.lin || v0.helm != 0) continue;
         const std::string key = tune_helm_key(v0);
         int choice = decided.count(key) ? decided[key] : cache_lookup(h->cfg.autotune_cache, key);
+        // 5: the fused stage with its D2 v inside (every block of the group must allow it)
+        bool fuse_ok = dnsk::spec_supported(v0);
+        for (const auto& P : h->parts[gi]) fuse_ok = fuse_ok && d2fuse_ok(h->groups[P.ig].v);
         if ((choice == 2 && !dnsk::helm_tc_supported(v0)) || (choice == 4 && !dnsk::spec_supported(v0)) ||
-            choice == 3)
+            (choice == 5 && !fuse_ok) || choice == 3)
             choice = 0;
         if (!choice) {
-            float best[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+            float best[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             cudaEvent_t e0, e1;
             cudaEventCreate(&e0);
             cudaEventCreate(&e1);
-            for (int cand = 1; cand <= 4 && !rc; ++cand) {
+            for (int cand = 1; cand <= 5 && !rc; ++cand) {
                 if (cand == 3 || (cand == 2 && !dnsk::helm_tc_supported(v0)) ||
-                    (cand == 4 && !dnsk::spec_supported(v0)))
+                    (cand == 4 && !dnsk::spec_supported(v0)) || (cand == 5 && !fuse_ok))
                     continue;
-                for (const auto& P : h->parts[gi]) h->groups[P.ig].v.helm = cand;
+                for (const auto& P : h->parts[gi]) {
+                    h->groups[P.ig].v.helm = cand == 5 ? 4 : cand;
+                    h->groups[P.ig].v.d2fuse = cand == 5 ? 1 : 0;
+                }
                 for (int w = 0; w < 2; ++w) enqueue_step(h);
                 cudaEventRecord(e0, st);
                 for (int r = 0; r < 3; ++r) enqueue_step(h);
@@ -978,15 +991,16 @@ int dns_bind_workspace(dns_handle* h, void* dev_ptr, size_t bytes) {
             if (rc) return rc;
             if ((rc = device_status(h))) return rc;
             choice = 0;
-            for (int cand = 1; cand <= 4; ++cand)
+            for (int cand = 1; cand <= 5; ++cand)
                 if (best[cand] > 0.f && (choice == 0 || best[cand] < best[choice])) choice = cand;
-            cache_store(h->cfg.autotune_cache, key, choice, best, 4);
+            cache_store(h->cfg.autotune_cache, key, choice, best, 5);
         }
         decided[key] = choice;
         for (const auto& P : h->parts[gi]) {
             GroupView& v = h->groups[P.ig].v;
-            v.helm = choice;
-            if (choice == 4) v.ygemm = 1;
+            v.helm = choice == 5 ? 4 : choice;
+            v.d2fuse = choice == 5 ? 1 : 0;
+            if (v.helm == 4) v.ygemm = 1;
         }
     }
     // linear groups: the apply kernels alone
@@ -1017,7 +1031,7 @@ int dns_bind_workspace(dns_handle* h, void* dev_ptr, size_t bytes) {
                 auto run = [&]() {
                     if (cand == 4) {
                         dnsk::launch_spec(v, 1, st);
-                        if (v.d2tc) dnsk::launch_d2v_tc(v, v.v_s, st);
+                        if (v.d2tc && !v.d2fuse) dnsk::launch_d2v_tc(v, v.v_s, st);
                         return;
                     }
                     if (whole) {
@@ -1059,13 +1073,19 @@ int dns_bind_workspace(dns_handle* h, void* dev_ptr, size_t bytes) {
         snprintf(kb, sizeof kb, "spec_ec %d %d %d %d", v.mx, v.my, v.mz, v.E);
         const std::string key = kb;
         std::vector<int> cands;
+        const int ec_before = v.spec_ec;
         for (int ec : {std::min(v.E, 8), (std::min(v.E, 8) + 1) / 2, 2}) {
             v.spec_ec = ec;
+            if (v.d2fuse && (ec > 4 || !dnsk::spec_d2fuse_supported(v))) continue;   // its N holds 4 members
             if (ec >= 1 && dnsk::spec_supported(v) && std::find(cands.begin(), cands.end(), ec) == cands.end())
                 cands.push_back(ec);
         }
         int choice = decided.count(key) ? decided[key] : cache_lookup_value(h->cfg.autotune_cache, key);
         if (std::find(cands.begin(), cands.end(), choice) == cands.end()) choice = 0;
+        if (cands.empty()) {
+            v.spec_ec = ec_before;
+            continue;
+        }
         if (!choice && cands.size() == 1) choice = cands[0];
         if (!choice) {
             std::vector<float> ms(cands.size(), 0.f);
@@ -1994,7 +2014,7 @@ int dns_kernel_choice(const dns_handle* h, int group, int* ygemm, int* plane, in
     const GroupView& v = h->groups[h->parts[group][0].ig].v;
     if (ygemm) *ygemm = v.ygemm;
     if (plane) *plane = v.plane;
-    if (helm) *helm = v.helm;
+    if (helm) *helm = (v.helm == 4 && v.d2fuse) ? 5 : v.helm;
     return DNS_OK;
 }
 

@@ -58,6 +58,7 @@ struct GroupView {
     const float* D2T;
     const float* D2Tl;    // D2T's residual: D2i - (double) D2T in single precision (compensated D2 v)
     int d2tc;             // fused stage: 1 = D2 v of the new state by the tensor-core digit kernel
+    int d2fuse;           // fused stage: 1 = that digit product inside the fused launch (no D2 v launch)
     int spec_ec;          // fused stage: members per CTA (0 = up to 8), set by the autotuner
     int yd_cap;           // register-tiled y-derivatives: first column-tile cap (0 = 64, or 32 above
                           //    Ny = 96), halved while the grid is short of 3 CTAs per SM; autotuned
@@ -163,6 +164,7 @@ void launch_d2v_tc(const GroupView& g, const double2* v, cudaStream_t st);
 void set_attributes_d2v_tc();
 // fused per-wavenumber stage of the mixed path (k_spec.cu)
 bool spec_supported(const GroupView& g);
+bool spec_d2fuse_supported(const GroupView& g);   // with g.d2fuse set: the fused D2 v can run
 size_t spec_smem_bytes(const GroupView& g);
 void launch_spec(const GroupView& g, int s, cudaStream_t st);
 void set_attributes_spec();

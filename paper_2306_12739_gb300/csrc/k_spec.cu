@@ -26,10 +26,18 @@
 // float-float: D2 and v are held as pairs of single-precision numbers and every
 // product enters a compensated sum (TwoSum, the FMA product residual, the cross
 // terms into the low part).
+//
+// With d2fuse the stage runs that digit product itself (oz.cuh, the same digit
+// arithmetic, so the same bits): the image of D2's digits is copied over the
+// operators phase 2 has finished with while phase 3 runs, the new state's
+// digits go over P_v after phase 3, one thread issues the MMAs while the CTA
+// computes D v, and four warps read the six levels back from TMEM.  A sub-step
+// is then two launches per member block (plane stage, this one).
 #include "dns_internal.hpp"
 #include "cvt.cuh"
 #include "ff.cuh"
 #include "mean.cuh"
+#include "oz.cuh"
 
 namespace dnsk {
 
@@ -39,9 +47,14 @@ constexpr int THREADS = 256;
 constexpr int HALF = THREADS / 2;
 constexpr int NCR_MAX = 32;   // real columns per CTA (modes x members x re/im)
 
-// Member chunk: at most NCR_MAX real columns per CTA (two modes, re and im).
+constexpr int DCOL = 16;      // real columns of the fused D2 v digit product (MMA N)
+constexpr unsigned DTCOLS = 128;   // its TMEM columns: NLEV x DCOL = 96, allocated as 128
+
+// Member chunk: at most NCR_MAX real columns per CTA (two modes, re and im);
+// with the fused D2 v at most DCOL.
 __host__ __device__ inline int chunk_members(const GroupView& g) {
-    const int ec = (g.spec_ec > 0 && g.spec_ec <= NCR_MAX / 4) ? g.spec_ec : NCR_MAX / 4;
+    const int cap = g.d2fuse ? DCOL / 4 : NCR_MAX / 4;
+    const int ec = (g.spec_ec > 0 && g.spec_ec <= cap) ? g.spec_ec : cap;
     return g.E < ec ? g.E : ec;
 }
 __host__ __device__ inline int chunks(const GroupView& g) {
@@ -51,10 +64,30 @@ __host__ __device__ inline int chunks(const GroupView& g) {
 // row stride (floats) of the shared-memory vectors: the chunk's real columns
 __host__ __device__ inline int vec_stride(const GroupView& g) { return 4 * chunk_members(g); }
 __host__ __device__ inline size_t vec_floats(const GroupView& g) { return (size_t)g.ny * vec_stride(g); }
-// shared memory: operators [4][Ny][RP] (the eta pair reused for D2 and its
-// residual after phase 2) | D1 [Ny][RP] | 7 vectors [Ny][vec_stride] | 2 mbarriers
+// Operator slot (floats): one [Ny][RP] matrix; with the fused D2 v at least
+// two digit slices of D2's image (2 x 64 rows x KP BF16 = 64 KP floats).
+__host__ __device__ inline size_t slot_floats(const GroupView& g) {
+    const size_t m = (size_t)g.ny * g.rp, s2 = (size_t)64 * g.kp;
+    return (g.d2fuse && s2 > m) ? s2 : m;
+}
+// shared memory: 4 operator slots (the eta pair reused for D2 and its residual
+// after phase 2; with d2fuse the image of D2's digits in slots 0, 2, 3 from
+// phase 3 and the new state's digits in slot 1 in phase 4) | D1 [Ny][RP] |
+// 7 vectors [Ny][vec_stride] | 4 mbarriers
 __host__ __device__ inline size_t smem_bytes(const GroupView& g) {
-    return (5 * (size_t)g.ny * g.rp + 7 * vec_floats(g)) * sizeof(float) + 32;
+    // (with d2fuse, 128 more bytes after the mbarriers: column exponents, TMEM base, status)
+    const size_t b = (4 * slot_floats(g) + (size_t)g.ny * g.rp + 7 * vec_floats(g)) * sizeof(float) + 32 +
+                     (g.d2fuse ? 128 : 0);
+    // with d2fuse, room for the 64 unused A rows that follow the last digit slice
+    const size_t t = g.d2fuse ? 3 * slot_floats(g) * sizeof(float) + 3 * (size_t)64 * g.kp * 2 : 0;
+    return b > t ? b : t;
+}
+// With d2fuse the MMA's A operand is M = 128 rows of which 64 are D2's: the
+// other 64 read the 128 KP bytes that follow each slice (never read back), so
+// those must lie inside the CTA's shared memory, also after the last slice.
+__host__ __device__ inline bool fused_d2_fits(const GroupView& g) {
+    const size_t slot = slot_floats(g) * sizeof(float), sa = (size_t)64 * g.kp * 2;
+    return 3 * slot + 3 * sa <= smem_bytes(g) && 6 * (size_t)DCOL * g.kp * 2 <= slot;
 }
 
 __device__ __forceinline__ unsigned su32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -256,6 +289,7 @@ __device__ __forceinline__ void apply_epilogue(const GroupView& g, int s, int f,
     }
 }
 
+template <bool FUSE>
 __global__ void __launch_bounds__(THREADS, 2) k_spec(GroupView g, int s) {
     extern __shared__ __align__(16) unsigned char sm[];
     const int nrow = mean_row_ctas(g);
@@ -278,10 +312,11 @@ __global__ void __launch_bounds__(THREADS, 2) k_spec(GroupView g, int s) {
     c.e0 = ch * EC;
     c.ec = min(EC, E - c.e0);
     c.C = c.nq * c.ec;
-    const size_t mat = (size_t)Ny * RP;
-    float* OPS = (float*)sm;                      // [4][Ny][RP]: (Mv-I)^T, Pv^T, (Me-I)^T, Pe^T;
+    const size_t mat = (size_t)Ny * RP, slot = FUSE ? slot_floats(g) : mat;
+    float* OPS = (float*)sm;                      // 4 slots: (Mv-I)^T, Pv^T, (Me-I)^T, Pe^T;
                                                   // after phase 2: D2^T, its residual in the last two
-    float* D1S = OPS + 4 * mat;                   // D1^T [Ny][RP]
+                                                  // (or, with d2fuse, D2's digit image in 0, 2, 3)
+    float* D1S = OPS + 4 * slot;                  // D1^T [Ny][RP]
     float* PH = D1S + mat;                        // phi, then v+ (hi)
     float* KV = PH + vec_floats(g);               // -k^2 Nv (+ noise), then v+ (lo)
     float* GT = KV + vec_floats(g);               // G~
@@ -290,14 +325,20 @@ __global__ void __launch_bounds__(THREADS, 2) k_spec(GroupView g, int s) {
     float* FT = XE + vec_floats(g);               // F~
     float* EN = FT + vec_floats(g);               // eta+ (single precision)
     unsigned long long* bar = (unsigned long long*)(EN + vec_floats(g));
-    const unsigned bar_a = su32(bar), bar_d = su32(bar + 1);
+    const unsigned bar_a = su32(bar), bar_d = su32(bar + 1), bar_m = su32(bar + 2);
+    constexpr bool fuse = FUSE;                   // D2 v by the digit product below
+    int* dcexp = (int*)(bar + 4);                 // fused D2 v: column exponent maxima [DCOL],
+    unsigned* tslot = (unsigned*)(dcexp + DCOL);  // its TMEM base,
+    int* dok = (int*)(tslot + 1);                 // its status
     const int tid = threadIdx.x;
     const bool needM = (s != 2);
     const int hidx = (s == 0) ? 0 : 1;
 
+    if (fuse && tid < DCOL) dcexp[tid] = 0;
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_a) : "memory");
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_d) : "memory");
+        if (fuse) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_m) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
@@ -307,7 +348,9 @@ __global__ void __launch_bounds__(THREADS, 2) k_spec(GroupView g, int s) {
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_a),
                      "r"(needM ? 5 * mb : 3 * mb) : "memory");
         bulk(D1S, g.D1T, mb, bar_a);
-        if (needM) {
+        if (fuse) {
+            for (int k = needM ? 0 : 1; k < 4; k += needM ? 1 : 2) bulk(OPS + k * slot, src + k * mat, mb, bar_a);
+        } else if (needM) {
             bulk(OPS, src, 4 * mb, bar_a);
         } else {
             bulk(OPS + mat, src + mat, mb, bar_a);
@@ -440,7 +483,7 @@ __global__ void __launch_bounds__(THREADS, 2) k_spec(GroupView g, int s) {
             float2 m1[4];
             apply_prefetch(g, s, 1, c, r0, j, x, m1);
             float ma[2][4], pa[2][4];
-            mm2(OPS + 2 * mat, OPS + 3 * mat, XE, GT, Ny, RP, VS, r0, 2 * j, needM, ma, pa);
+            mm2(OPS + 2 * slot, OPS + 3 * slot, XE, GT, Ny, RP, VS, r0, 2 * j, needM, ma, pa);
             apply_epilogue(g, s, 1, c, r0, j, ma, pa, x, m1, EN, nullptr);
         }
     }
@@ -452,8 +495,19 @@ __global__ void __launch_bounds__(THREADS, 2) k_spec(GroupView g, int s) {
         const unsigned mb = (unsigned)(mat * sizeof(float));
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_d), "r"(2 * mb) : "memory");
-        bulk(OPS + 2 * mat, g.D2T, mb, bar_d);
-        bulk(OPS + 3 * mat, g.D2Tl, mb, bar_d);
+        bulk(OPS + 2 * slot, g.D2T, mb, bar_d);
+        bulk(OPS + 3 * slot, g.D2Tl, mb, bar_d);
+    }
+    // fused D2 v: the six digit slices of D2's image, two per slot, over the
+    // operators phase 2 has finished with (slots 0, 2, 3), while phase 3 runs
+    if (tid == 0 && fuse) {
+        const unsigned b2 = (unsigned)(2 * oz::slice_a(g.kp));
+        const unsigned char* img = (const unsigned char*)g.D2oz;
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_d), "r"(3 * b2) : "memory");
+        bulk(OPS, img, b2, bar_d);
+        bulk(OPS + 2 * slot, img + b2, b2, bar_d);
+        bulk(OPS + 3 * slot, img + 2 * b2, b2, bar_d);
     }
 
     // ---- phase 3: v+ (P_v F~, threads 0..127) | D eta and the eta planes (threads 128..255)
@@ -464,7 +518,7 @@ __global__ void __launch_bounds__(THREADS, 2) k_spec(GroupView g, int s) {
             float2 m1[4];
             apply_prefetch(g, s, 0, c, r0, j, x, m1);
             float ma[2][4], pa[2][4];
-            mm1(OPS + mat, FT, Ny, RP, VS, r0, 2 * j, pa);
+            mm1(OPS + slot, FT, Ny, RP, VS, r0, 2 * j, pa);
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 const int y = r0 + i;
@@ -504,13 +558,104 @@ __global__ void __launch_bounds__(THREADS, 2) k_spec(GroupView g, int s) {
         return;
     }
 
+    // ---- fused D2 v (oz.cuh): digits of the new state's columns into slot 1,
+    // the MMAs issued by one thread into TMEM; phase 4 runs under them
+    const int warp = tid >> 5, lane = tid & 31;
+    if (fuse) {
+        if (warp == 0) {
+            asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tslot)),
+                         "r"(DTCOLS) : "memory");
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        }
+        const int KP = g.kp, KC = KP / 4;
+        const unsigned LBO = 128, SBO = 16 * KP;
+        const size_t sb = (size_t)DCOL * KP * 2;          // bytes of one digit slice of v
+        unsigned char* B = (unsigned char*)(OPS + slot);
+        const double2* Vn = (s == 2) ? g.v_t : g.v_s;    // the new state (this CTA's columns written in phase 3)
+        // task (complex column j, 4 consecutive k); the columns j >= C and rows
+        // k >= Ny are zero
+        const int j = tid % (DCOL / 2), kc = tid / (DCOL / 2);
+        const bool task = kc < KC;
+        double2 xv[4];
+        int mr = 0, mi = 0;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int k = 4 * kc + i;
+            xv[i] = make_double2(0.0, 0.0);
+            if (task && j < c.C && k < Ny) {
+                const int q = col_q(c, j), e = col_e(c, j);
+                if (in_range(g, q, k, e)) xv[i] = Vn[((size_t)q * Ny + k) * E + e];
+            }
+            mr = max(mr, oz::bexp(xv[i].x));
+            mi = max(mi, oz::bexp(xv[i].y));
+        }
+        if (task) {
+            atomicMax(&dcexp[2 * j], mr);
+            atomicMax(&dcexp[2 * j + 1], mi);
+        }
+        __syncthreads();
+        // (debug build) every digit of this task lands inside slot 1
+        if (task && DNS_CK(g.status, (oz::NDIG - 1) * sb + (size_t)(DCOL / 8 - 1) * SBO + (size_t)(kc >> 1) * LBO + 8 * 16 <=
+                                         slot * sizeof(float), CK_SPEC_SMEM, kc)) {
+#pragma unroll
+            for (int part = 0; part < 2; ++part) {
+                const int cr = 2 * j + part;
+                const int f = dcexp[cr] - 1022;           // |x| < 2^f for every x of the column
+                unsigned short dg[4][oz::NDIG];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) oz::digits(part ? xv[i].y : xv[i].x, f, dg[i]);
+                const size_t off = (size_t)(cr >> 3) * SBO + (size_t)(kc >> 1) * LBO + (size_t)(cr & 7) * 16 + (kc & 1) * 8;
+#pragma unroll
+                for (int sd = 0; sd < oz::NDIG; ++sd) {
+                    uint2 w;
+                    w.x = (unsigned)dg[0][sd] | ((unsigned)dg[1][sd] << 16);
+                    w.y = (unsigned)dg[2][sd] | ((unsigned)dg[3][sd] << 16);
+                    *(uint2*)(B + sd * sb + off) = w;
+                }
+            }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (tid == 0) {
+            int good = waitp(bar_d, 0) ? 1 : 0;
+            if (!good) waitp(bar_d, 0);                   // one more bounded wait: no copy left in flight
+            if (good) {
+                const unsigned tmem = *tslot;
+                const unsigned idesc = oz::idesc_bf16(oz::MROWS, DCOL);
+                const size_t sa = oz::slice_a(KP);
+                const unsigned char* A0 = (const unsigned char*)OPS;
+                const unsigned char* A2 = (const unsigned char*)(OPS + 2 * slot);
+                const unsigned char* A4 = (const unsigned char*)(OPS + 3 * slot);
+                const int KS = KP / 16;
+                for (int L = 0; L < oz::NLEV; ++L) {
+                    unsigned acc = 0;
+                    for (int sd = 0; sd <= L; ++sd) {
+                        const int t = L - sd;
+                        const unsigned char* As = (sd < 2 ? A0 : sd < 4 ? A2 : A4) + (size_t)(sd & 1) * sa;
+                        for (int ks = 0; ks < KS; ++ks) {
+                            const uint64_t ad = oz::sdesc(su32(As + (size_t)ks * 2 * LBO), LBO, SBO);
+                            const uint64_t bd = oz::sdesc(su32(B + t * sb + (size_t)ks * 2 * LBO), LBO, SBO);
+                            oz::mma(tmem + (unsigned)(L * DCOL), ad, bd, idesc, acc);
+                            acc = 1;
+                        }
+                    }
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar_m)
+                             : "memory");
+            }
+            *dok = good;
+        }
+    }
+
     // ---- phase 4: Dv and the compensated D2 v, 2-row x 1-complex-column tasks
     // on every thread; the v planes
     {
         const float* VH = PH;
         const float* VL = KV;
-        const float* D2S = OPS + 2 * mat;
-        const float* D2LS = OPS + 3 * mat;
+        const float* D2S = OPS + 2 * slot;
+        const float* D2LS = OPS + 3 * slot;
         const int RB2 = (Ny + 1) / 2, ntask2 = RB2 * c.C;
         for (int t = tid; t < ntask2; t += THREADS) {
             const int rb = t / c.C, j = t - rb * c.C, r0 = 2 * rb;
@@ -552,12 +697,64 @@ __global__ void __launch_bounds__(THREADS, 2) k_spec(GroupView g, int s) {
             }
         }
     }
+
+    // ---- fused D2 v: wait for the MMAs (bounded), rows 0..63 read back by
+    // warps 0, 1, 4, 5 (TMEM lanes 32 (w & 3) .., real columns 8 (w >> 2) ..),
+    // the levels combined and scaled exactly as the D2 v kernel does
+    if (fuse) {
+        __syncthreads();
+        if (tid == 0) {
+            int good = *dok;
+            if (good) {
+                good = waitp(bar_m, 0) ? 1 : 0;
+                if (!good) waitp(bar_m, 0);               // do not release TMEM under running MMAs
+            }
+            *dok = good;
+        }
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const unsigned tmem = *tslot;
+        const bool ok = *dok != 0;
+        if (ok && (warp & 3) < 2) {
+            const int y = 32 * (warp & 3) + lane;
+            const int c0 = 8 * (warp >> 2);
+            float hi[8], lo[8];
+            oz::combine_levels<8>(tmem + ((unsigned)(32 * (warp & 3)) << 16) + (unsigned)c0, DCOL, hi, lo);
+            if (y < Ny) {
+                const float sr = oz::p2f(g.D2ozexp[y] - 14);
+#pragma unroll
+                for (int i = 0; i < 8; i += 2) {
+                    const int cr = c0 + i, j = cr >> 1;
+                    if (j >= c.C) break;
+                    const int q = col_q(c, j), e = col_e(c, j);
+                    if (!in_range(g, q, y, e)) continue;
+                    // 2^(e_r + f_c) 2^-14 in two exact steps (each in the float range)
+                    const float re = __fadd_rn(hi[i], lo[i]) * sr * oz::p2f(dcexp[cr] - 1022);
+                    const float im = __fadd_rn(hi[i + 1], lo[i + 1]) * sr * oz::p2f(dcexp[cr + 1] - 1022);
+                    P5[2 * fs5 + ((size_t)y * E + e) * NM + q] = make_float2(re, im);
+                }
+            }
+        }
+        if (!ok && tid == 0) atomicExch(g.status, 5);
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        if (warp == 0)
+            asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(DTCOLS) : "memory");
+    }
 }
 
 }  // namespace spc
 
 bool spec_supported(const GroupView& g) {
     return !g.lin && g.npairs > 1 && spc::smem_bytes(g) + 1024 <= 227 * 1024;
+}
+
+// The fused D2 v for a group whose stage runs with d2fuse set (callers set it
+// before asking): the digit image exists (d2tc), the CTA's columns fit the MMA's
+// N, and every slice with the rows that follow it lies inside shared memory.
+bool spec_d2fuse_supported(const GroupView& g) {
+    return g.d2fuse && g.d2tc && !g.lin && g.ny <= 64 && g.kp % 16 == 0 && 4 * spc::chunk_members(g) <= spc::DCOL &&
+           spc::fused_d2_fits(g) && spec_supported(g);
 }
 
 size_t spec_smem_bytes(const GroupView& g) {
@@ -567,9 +764,13 @@ size_t spec_smem_bytes(const GroupView& g) {
 
 void launch_spec(const GroupView& g, int s, cudaStream_t st) {
     const int ctas = mean_row_ctas(g) + (g.npairs - 1) * spc::chunks(g);
-    spc::k_spec<<<ctas, spc::THREADS, spec_smem_bytes(g), st>>>(g, s);
+    if (g.d2fuse) spc::k_spec<true><<<ctas, spc::THREADS, spec_smem_bytes(g), st>>>(g, s);
+    else spc::k_spec<false><<<ctas, spc::THREADS, spec_smem_bytes(g), st>>>(g, s);
 }
 
-void set_attributes_spec() { allow_max_dynamic_smem(spc::k_spec); }
+void set_attributes_spec() {
+    allow_max_dynamic_smem(spc::k_spec<false>);
+    allow_max_dynamic_smem(spc::k_spec<true>);
+}
 
 }  // namespace dnsk

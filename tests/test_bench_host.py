@@ -62,6 +62,17 @@ def test_byte_and_work_models_are_the_documented_counts():
     bound, flops, unit = bench.kernel_work("plane", g, "mixed")
     per = 15 * 2.5 * 4096 * 12 + 22 * 4096
     assert (bound, unit) == ("alu", "flop") and flops == pytest.approx(4 * 63 * per)
+    # the fused stage: N in, the FP64 state, the RK accumulators, the operators of
+    # 22 x 22 - 1 wavenumber pairs (4 + 4 + 2 matrices over three sub-steps; the
+    # mean mode's pair has none), and four P-layout fields out, five when it
+    # computes D2 v itself
+    ops = 483 * (10 / 3) * 63 * 64 * 4
+    base = ops + 24 * S + 2 * S * (16 * 2 / 3 + 16 + 8 * 2 / 3) + 16 * S * 4 / 3
+    assert bench.kernel_bytes("spec", g, "mixed") == pytest.approx(base + 32 * S)
+    assert bench.kernel_bytes("spec", dict(g, _stage="fused_d2v"), "mixed") == pytest.approx(base + 40 * S)
+    _, w4, _ = bench.kernel_work("spec", g, "mixed")
+    _, w5, _ = bench.kernel_work("spec", dict(g, _stage="fused_d2v"), "mixed")
+    assert w5 - w4 == pytest.approx(S * 4 * 63)
 
 
 def test_alu_peak_scales_with_the_sm_count_and_clock():

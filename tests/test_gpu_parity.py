@@ -369,8 +369,8 @@ def test_autotuner_picks_a_variant_caches_it_and_matches_that_variant(tmp_path):
     choice = dns.dns_kernel_choice(ens.h, 0)
     plane = dns.dns_kernel_choice(ens.h, 0, "plane")
     helm = dns.dns_kernel_choice(ens.h, 0, "helm")
-    assert choice in ("simt", "tc") and plane in ("cta", "lines") and helm in ("simt", "tc", "fused")
-    assert helm != "fused" or choice == "simt"
+    assert choice in ("simt", "tc") and plane in ("cta", "lines") and helm in ("simt", "tc", "fused", "fused_d2v")
+    assert helm not in ("fused", "fused_d2v") or choice == "simt"
     ens.set_state(0, st["v"], st["eta"], st["U"], st["W"])
     ens.step(3)
     got = ens.get_state(0)
@@ -381,7 +381,7 @@ def test_autotuner_picks_a_variant_caches_it_and_matches_that_variant(tmp_path):
     # the tile shapes: the fused stage's members per CTA, the y-derivative tile
     assert all(ln.split()[1:5] == ["32", "33", "32", "4"] for ln in lines)
     want = {"helm", "plane", "ygemm"} | ({"ytile"} if choice == "simt" else set()) | \
-        ({"spec_ec"} if helm == "fused" else set())
+        ({"spec_ec"} if helm in ("fused", "fused_d2v") else set())
     assert sorted(keys) == sorted(want)
     ens2 = dns.Ensemble([g], precision="mixed", autotune_cache=cache)   # read back, no new timing
     assert dns.dns_kernel_choice(ens2.h, 0) == choice
@@ -725,3 +725,39 @@ def test_fused_stage_member_alone_equals_member_in_batch_and_resumes_bitwise():
     again = _run(g, dict(zip(FIELDS, half)), 3, "mixed", **pin)
     err = mixed_errors(again, whole)
     assert np.all(err[:, :3] < 1e-6), err
+
+
+@pytest.mark.parametrize("flow,mx,my,mz,E,extra", [
+    ("poiseuille", 64, 65, 64, 8, {}),                        # the benchmarked case: two blocks of 4
+    ("couette", 16, 21, 48, 3, {}),                           # Ny = 19: K padded to 32
+    ("poiseuille", 32, 49, 32, 5, {}),                        # member chunks of 4 and 1
+    ("couette", 48, 33, 48, 1, {}),
+    ("poiseuille", 32, 33, 16, 6, dict(member_block=6)),      # chunks of 4 and 2
+    ("couette", 64, 65, 64, 4, dict(form="rotational")),
+])
+def test_fused_d2v_is_bitwise_the_separate_digit_kernel(flow, mx, my, mz, E, extra):
+    """The fused stage with the tensor-core D2 v inside it (digits of the new
+    state, the MMAs and the TMEM read-back in the same launch) runs the digit
+    arithmetic of the separate D2 v kernel: each level is an exact integer sum,
+    so the state after 4 steps (CUDA graph) is bit for bit the one of the fused
+    stage followed by the separate kernel."""
+    g = dict(group(flow, mx, my, mz, 2 * np.pi, np.pi, 1650.0 if flow == "poiseuille" else 400.0, 0.005, E), **extra)
+    st = _state(g, 97, 5e-2)
+    ens = dns.Ensemble([g], precision="mixed", helm="fused_d2v", plane="lines")
+    assert dns.dns_kernel_choice(ens.h, 0, "helm") == "fused_d2v"
+    ens.close()
+    sep = _run(g, st, 4, "mixed", use_graph=True, helm="fused", plane="lines")
+    inside = _run(g, st, 4, "mixed", use_graph=True, helm="fused_d2v", plane="lines")
+    for a, b, name in zip(sep, inside, FIELDS):
+        assert np.array_equal(a, b), name
+
+
+def test_fused_d2v_request_falls_back_where_it_cannot_run():
+    """Above Ny = 64 the stage sums D2 v in float-float and has no digit image:
+    a request for the fused D2 v runs the plain fused stage there."""
+    g = group("poiseuille", 32, 97, 16, 2 * np.pi, np.pi, 1650.0, 0.005, 2)
+    ens = dns.Ensemble([g], precision="mixed", helm="fused_d2v")
+    try:
+        assert dns.dns_kernel_choice(ens.h, 0, "helm") == "fused"
+    finally:
+        ens.close()
