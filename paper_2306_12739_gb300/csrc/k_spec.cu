@@ -289,7 +289,22 @@ __device__ __forceinline__ void apply_epilogue(const GroupView& g, int s, int f,
     }
 }
 
-template <bool FUSE>
+// t / C for the CTA's column count C, which is EC or 2 EC (pairs with one
+// mode, or both): with a compile-time EC both divisions are by constants
+template <int ECC>
+__device__ __forceinline__ int div_cols(int t, int C) {
+    if (ECC > 0) {
+        if (C == 2 * ECC) return t / (2 * ECC);
+        if (C == ECC) return t / ECC;
+    }
+    return t / C;
+}
+
+// NYC, ECC: compile-time Ny and members per chunk of the most used group
+// shapes (0: read from the group), so that the operator and vector strides of
+// the products and the task divisions are constants; the arithmetic and its
+// order are the same in every instantiation.
+template <bool FUSE, int NYC, int ECC>
 __global__ void __launch_bounds__(THREADS, 2) k_spec(GroupView g, int s) {
     extern __shared__ __align__(16) unsigned char sm[];
     const int nrow = mean_row_ctas(g);
@@ -297,7 +312,10 @@ __global__ void __launch_bounds__(THREADS, 2) k_spec(GroupView g, int s) {
         mean_cta(g, s, blockIdx.x, sm);
         return;
     }
-    const int Ny = g.ny, RP = g.rp, E = g.E, NM = g.nmodes, NKX = g.nkx, VS = vec_stride(g);
+    const int Ny = NYC ? NYC : g.ny, RP = NYC ? (NYC + 3) / 4 * 4 : g.rp;
+    const int E = g.E, NM = g.nmodes, NKX = g.nkx;
+    const int EC = ECC ? ECC : chunk_members(g), VS = 4 * EC;   // (= vec_stride(g))
+    const size_t VF = (size_t)Ny * VS;                           // (= vec_floats(g))
     const int b = blockIdx.x - nrow;
     const int np1 = g.npairs - 1;                 // pair 0 is the mean mode: no CTA
     Cols c;
@@ -308,7 +326,6 @@ __global__ void __launch_bounds__(THREADS, 2) k_spec(GroupView g, int s) {
     c.nq = c.am > 0 ? 2 : 1;
     c.q1 = (g.kz + c.am) * NKX + c.n;
     c.q2 = (g.kz - c.am) * NKX + c.n;
-    const int EC = chunk_members(g);
     c.e0 = ch * EC;
     c.ec = min(EC, E - c.e0);
     c.C = c.nq * c.ec;
@@ -318,13 +335,13 @@ __global__ void __launch_bounds__(THREADS, 2) k_spec(GroupView g, int s) {
                                                   // (or, with d2fuse, D2's digit image in 0, 2, 3)
     float* D1S = OPS + 4 * slot;                  // D1^T [Ny][RP]
     float* PH = D1S + mat;                        // phi, then v+ (hi)
-    float* KV = PH + vec_floats(g);               // -k^2 Nv (+ noise), then v+ (lo)
-    float* GT = KV + vec_floats(g);               // G~
-    float* XV = GT + vec_floats(g);               // x_t of v (single precision)
-    float* XE = XV + vec_floats(g);               // x_t of eta
-    float* FT = XE + vec_floats(g);               // F~
-    float* EN = FT + vec_floats(g);               // eta+ (single precision)
-    unsigned long long* bar = (unsigned long long*)(EN + vec_floats(g));
+    float* KV = PH + VF;                          // -k^2 Nv (+ noise), then v+ (lo)
+    float* GT = KV + VF;                          // G~
+    float* XV = GT + VF;                          // x_t of v (single precision)
+    float* XE = XV + VF;                          // x_t of eta
+    float* FT = XE + VF;                          // F~
+    float* EN = FT + VF;                          // eta+ (single precision)
+    unsigned long long* bar = (unsigned long long*)(EN + VF);
     const unsigned bar_a = su32(bar), bar_d = su32(bar + 1), bar_m = su32(bar + 2);
     constexpr bool fuse = FUSE;                   // D2 v by the digit product below
     int* dcexp = (int*)(bar + 4);                 // fused D2 v: column exponent maxima [DCOL],
@@ -368,10 +385,11 @@ __global__ void __launch_bounds__(THREADS, 2) k_spec(GroupView g, int s) {
         const float kx = g.kxtf[c.n];
         const bool forced = g.fn > 0 && c.n == g.fn;
         for (int i = tid; i < total; i += THREADS) {
-            const int y = i / c.C, j = i - y * c.C;
+            const int y = div_cols<ECC>(i, c.C), j = i - y * c.C;
             const int q = col_q(c, j), e = col_e(c, j);
             if (!in_range(g, q, y, e) || !DNS_CK(g.status, 2 * j + 1 < VS, CK_SPEC_SMEM, y * VS + 2 * j)) continue;
-            const float kz = g.kztf[q / NKX];
+            const int mz = j < c.ec ? g.kz + c.am : g.kz - c.am;    // = q / NKX
+            const float kz = g.kztf[mz];
             const size_t op = ((size_t)y * E + e) * NM + q;
             const size_t oh = ((size_t)q * Ny + y) * E + e;
             const float2 nu = N3[op], nv = N3[fs + op], nw = N3[2 * fs + op];
@@ -387,8 +405,8 @@ __global__ void __launch_bounds__(THREADS, 2) k_spec(GroupView g, int s) {
             const float bx = kz * nu.x - kx * nw.x, by = kz * nu.y - kx * nw.y;   // i kz Nu - i kx Nw
             float2 kv = make_float2(-k2 * nv.x, -k2 * nv.y);
             float2 G = make_float2(-by, bx);
-            if (forced && DNS_CK(g.status, q / NKX < g.nkz, CK_SPEC, q)) {
-                const size_t o = ((size_t)(q / NKX) * Ny + y) * E + e, half = (size_t)g.nkz * Ny * E;
+            if (forced && DNS_CK(g.status, mz < g.nkz, CK_SPEC, q)) {
+                const size_t o = ((size_t)mz * Ny + y) * E + e, half = (size_t)g.nkz * Ny * E;
                 kv.x += (float)g.noise[o].x; kv.y += (float)g.noise[o].y;
                 G.x += (float)g.noise[half + o].x; G.y += (float)g.noise[half + o].y;
             }
@@ -430,7 +448,7 @@ __global__ void __launch_bounds__(THREADS, 2) k_spec(GroupView g, int s) {
     if (tid < HALF) {
         float2* Av = (float2*)g.Av;
         for (int t = tid; t < ntask; t += HALF) {
-            const int rb = t / c.C, j = t - rb * c.C, r0 = 4 * rb;
+            const int rb = div_cols<ECC>(t, c.C), j = t - rb * c.C, r0 = 4 * rb;
             const int q = col_q(c, j), e = col_e(c, j);
             float2 pav[4];
 #pragma unroll
@@ -478,7 +496,7 @@ __global__ void __launch_bounds__(THREADS, 2) k_spec(GroupView g, int s) {
         }
     } else {
         for (int t = tid - HALF; t < ntask; t += HALF) {
-            const int rb = t / c.C, j = t - rb * c.C, r0 = 4 * rb;
+            const int rb = div_cols<ECC>(t, c.C), j = t - rb * c.C, r0 = 4 * rb;
             double2 x[4];
             float2 m1[4];
             apply_prefetch(g, s, 1, c, r0, j, x, m1);
@@ -513,7 +531,7 @@ __global__ void __launch_bounds__(THREADS, 2) k_spec(GroupView g, int s) {
     // ---- phase 3: v+ (P_v F~, threads 0..127) | D eta and the eta planes (threads 128..255)
     if (tid < HALF) {
         for (int t = tid; t < ntask; t += HALF) {
-            const int rb = t / c.C, j = t - rb * c.C, r0 = 4 * rb;
+            const int rb = div_cols<ECC>(t, c.C), j = t - rb * c.C, r0 = 4 * rb;
             double2 x[4];
             float2 m1[4];
             apply_prefetch(g, s, 0, c, r0, j, x, m1);
@@ -533,7 +551,7 @@ __global__ void __launch_bounds__(THREADS, 2) k_spec(GroupView g, int s) {
         }
     } else {
         for (int t = tid - HALF; t < ntask; t += HALF) {
-            const int rb = t / c.C, j = t - rb * c.C, r0 = 4 * rb;
+            const int rb = div_cols<ECC>(t, c.C), j = t - rb * c.C, r0 = 4 * rb;
             float a[2][4];
             d1mm(D1S, EN, Ny, RP, VS, r0, 2 * j, a);
             const int q = col_q(c, j), e = col_e(c, j);
@@ -658,7 +676,7 @@ __global__ void __launch_bounds__(THREADS, 2) k_spec(GroupView g, int s) {
         const float* D2LS = OPS + 3 * slot;
         const int RB2 = (Ny + 1) / 2, ntask2 = RB2 * c.C;
         for (int t = tid; t < ntask2; t += THREADS) {
-            const int rb = t / c.C, j = t - rb * c.C, r0 = 2 * rb;
+            const int rb = div_cols<ECC>(t, c.C), j = t - rb * c.C, r0 = 2 * rb;
             float d1[2][2] = {{0.f, 0.f}, {0.f, 0.f}};    // [row][re/im]
             float sh[2][2] = {{0.f, 0.f}, {0.f, 0.f}}, sl[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
             if (!d2here) {
@@ -762,15 +780,33 @@ size_t spec_smem_bytes(const GroupView& g) {
     return b > m ? b : m;
 }
 
+// the shapes with their own instantiation: (Ny, members per chunk)
+#define DNS_SPEC_SHAPES(X) X(63, 4) X(63, 2) X(63, 8)
+
 void launch_spec(const GroupView& g, int s, cudaStream_t st) {
     const int ctas = mean_row_ctas(g) + (g.npairs - 1) * spc::chunks(g);
-    if (g.d2fuse) spc::k_spec<true><<<ctas, spc::THREADS, spec_smem_bytes(g), st>>>(g, s);
-    else spc::k_spec<false><<<ctas, spc::THREADS, spec_smem_bytes(g), st>>>(g, s);
+    const size_t sm = spec_smem_bytes(g);
+    if (g.d2fuse) {
+        spc::k_spec<true, 0, 0><<<ctas, spc::THREADS, sm, st>>>(g, s);
+        return;
+    }
+    const int ec = spc::chunk_members(g);
+#define DNS_CASE(a, b)                                                      \
+    if (g.ny == a && ec == b) {                                             \
+        spc::k_spec<false, a, b><<<ctas, spc::THREADS, sm, st>>>(g, s);     \
+        return;                                                             \
+    }
+    DNS_SPEC_SHAPES(DNS_CASE)
+#undef DNS_CASE
+    spc::k_spec<false, 0, 0><<<ctas, spc::THREADS, sm, st>>>(g, s);
 }
 
 void set_attributes_spec() {
-    allow_max_dynamic_smem(spc::k_spec<false>);
-    allow_max_dynamic_smem(spc::k_spec<true>);
+    allow_max_dynamic_smem(spc::k_spec<false, 0, 0>);
+    allow_max_dynamic_smem(spc::k_spec<true, 0, 0>);
+#define DNS_CASE(a, b) allow_max_dynamic_smem(spc::k_spec<false, a, b>);
+    DNS_SPEC_SHAPES(DNS_CASE)
+#undef DNS_CASE
 }
 
 }  // namespace dnsk

@@ -761,3 +761,20 @@ def test_fused_d2v_request_falls_back_where_it_cannot_run():
         assert dns.dns_kernel_choice(ens.h, 0, "helm") == "fused"
     finally:
         ens.close()
+
+
+def test_fused_stage_shape_specialisations_are_bitwise_the_generic_kernel():
+    """At Ny = 63 the fused stage has instantiations with the wall-normal size
+    and the members per CTA as compile-time constants (4 and 2 here); three
+    members run the generic kernel.  Members evolve independently, so the
+    first members of the four- and two-member runs equal the three-member run's
+    bit for bit after 3 steps."""
+    g4 = group("poiseuille", 64, 65, 64, 2 * np.pi, np.pi, 1650.0, 0.005, 4)
+    st = _state(g4, 99, 5e-2)
+    pin = dict(helm="fused", plane="lines")
+    four = _run(g4, st, 3, "mixed", **pin)
+    three = _run(dict(g4, members=3), {k: st[k][:3] for k in FIELDS}, 3, "mixed", **pin)
+    two = _run(dict(g4, members=2), {k: st[k][:2] for k in FIELDS}, 3, "mixed", **pin)
+    for a, b, c, name in zip(four, three, two, FIELDS):
+        assert np.array_equal(a[:3], b), name
+        assert np.array_equal(a[:2], c), name
