@@ -62,7 +62,8 @@ __global__ void __launch_bounds__(THREADS, 2) k_d2v_tc(GroupView g, const double
     if (tid < NCOL) cexp[tid] = 0;
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_a) : "memory");
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_m) : "memory");
+        // one arrival per issuing lane (one lane per level, below)
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar_m), "r"(NLEV) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
@@ -136,32 +137,40 @@ __global__ void __launch_bounds__(THREADS, 2) k_d2v_tc(GroupView g, const double
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 
-    // ---- the MMAs: level L into TMEM columns [L NCOL, (L + 1) NCOL)
+    // ---- the MMAs: level L into TMEM columns [L NCOL, (L + 1) NCOL), issued by
+    // lane L of warp 0 (tcgen05.mma has single-thread semantics: each lane
+    // issues its own sequence; a level's MMAs stay in one lane, in order, and
+    // each lane's commit arrives once on bar_m)
     __shared__ int ok_flag;
-    if (tid == 0) {
-        int good = waitp(bar_a, 0) ? 1 : 0;
-        if (!good) waitp(bar_a, 0);               // one more bounded wait: no copy left in flight
-        if (good) {
+    if (warp == 0) {
+        int mine = 1;
+        if (lane < NLEV) mine = waitp(bar_a, 0) ? 1 : 0;
+        int good = __all_sync(0xffffffffu, mine);
+        if (!good && lane == 0) waitp(bar_a, 0);   // one more bounded wait: no copy left in flight
+        if (good && lane < NLEV) {
             const unsigned idesc = idesc_bf16(MROWS, NCOL);
-            const int KS = KP / 16;
-            for (int L = 0; L < NLEV; ++L) {
-                unsigned acc = 0;
-                for (int s = 0; s <= L; ++s) {
-                    const int t = L - s;
-                    for (int ks = 0; ks < KS; ++ks) {
-                        const uint64_t ad = sdesc(su32(A + s * sa + (size_t)ks * 2 * LBO), LBO, SBO);
-                        const uint64_t bd = sdesc(su32(B + t * sb + (size_t)ks * 2 * LBO), LBO, SBO);
-                        mma(tmem + (unsigned)(L * NCOL), ad, bd, idesc, acc);
-                        acc = 1;
-                    }
+            const int KS = KP / 16, L = lane;
+            unsigned acc = 0;
+            for (int s = 0; s <= L; ++s) {
+                const int t = L - s;
+                for (int ks = 0; ks < KS; ++ks) {
+                    const uint64_t ad = sdesc(su32(A + s * sa + (size_t)ks * 2 * LBO), LBO, SBO);
+                    const uint64_t bd = sdesc(su32(B + t * sb + (size_t)ks * 2 * LBO), LBO, SBO);
+                    mma(tmem + (unsigned)(L * NCOL), ad, bd, idesc, acc);
+                    acc = 1;
                 }
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar_m)
                          : "memory");
-            good = waitp(bar_m, 0) ? 1 : 0;
-            if (!good) waitp(bar_m, 0);           // do not release TMEM under running MMAs
         }
-        ok_flag = good;
+        __syncwarp();
+        if (lane == 0) {
+            if (good) {
+                good = waitp(bar_m, 0) ? 1 : 0;
+                if (!good) waitp(bar_m, 0);       // do not release TMEM under running MMAs
+            }
+            ok_flag = good;
+        }
     }
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
