@@ -238,7 +238,9 @@ def kernel_work(cls, g, precision):
         # computes it); 2 ny flops per output value of each
         npairs = nkx * (nkz // 2 + 1)
         apply = 2 * npairs * 2 * 2 * ny * ny * 4 * E * (5.0 / 6.0)
-        return "alu", S * 2 * 2 * ny * (4 if spec_computes_d2v(g) else 3) + apply, "flop"
+        work = S * 2 * 2 * ny * (4 if spec_computes_d2v(g) else 3) + apply
+        # in parity blocks every product is two half-size blocks: half the flops
+        return "alu", work / 2 if g.get("_stage") == "fused_eo" else work, "flop"
     return "alu", E * 4.0 * (g["my"]) ** 2, "flop"
 
 
@@ -283,7 +285,10 @@ def kernel_bytes(cls, g, precision):
         # out (v, Dv, eta, D eta, and D2 v where this stage computes it)
         rp = (ny + 3) // 4 * 4
         npairs = nkx * (nkz // 2 + 1) - 1              # the mean mode's pair has no CTA
-        ops = member_blocks(g) * npairs * ((4 + 4 + 2) / 3.0) * ny * rp * 4
+        # in parity blocks (per-wavenumber stage "fused_eo") a matrix is its even
+        # and odd halves, ny x 2 ceil(ceil(ny / 2) / 2) floats
+        mat = ny * 2 * (((ny + 1) // 2 + 1) // 2) if g.get("_stage") == "fused_eo" else ny * rp
+        ops = member_blocks(g) * npairs * ((4 + 4 + 2) / 3.0) * mat * 4
         state = 2 * S * (16 * (2.0 / 3.0) + 16 + 8 * (2.0 / 3.0))
         acc = 2 * 8 * S * (4.0 / 3.0)
         return ops + 3 * 8 * S + state + acc + (5 if spec_computes_d2v(g) else 4) * 8 * S
@@ -844,7 +849,7 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparator run")
     ap.add_argument("--plane", choices=["default", "cta", "cluster", "lines"], default="default",
                     help="plane-stage kernel (default: autotuned among those the grid supports)")
-    ap.add_argument("--helm", choices=["default", "simt", "tc", "persist", "fused", "fused_d2v"], default="default",
+    ap.add_argument("--helm", choices=["default", "simt", "tc", "persist", "fused", "fused_d2v", "fused_eo"], default="default",
                     help="per-wavenumber stage of the mixed path (default: the fused stage where the group "
                          "supports it, else the autotuned implicit apply)")
     ap.add_argument("--ygemm", choices=["default", "simt", "tc"], default="default",

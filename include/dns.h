@@ -127,10 +127,11 @@ typedef struct {
     unsigned long long barrier_timeout_ns;  /* reserved, 0 */
     const char* autotune_cache;    /* optional text file: autotuner decisions are read from it
                                       and appended to it ("ygemm|plane|helm Mx My Mz E choice" for
-                                      kernel variants, "spec_ec|ytile Mx My Mz E value" for the
-                                      tile shapes: members per CTA of the fused stage, first
-                                      column-tile cap of the register-tiled y-derivatives; the
-                                      shapes never change a result); NULL = none */
+                                      kernel variants, "spec_ec|spec_cta|ytile Mx My Mz E value"
+                                      for the tile shapes: members per CTA of the fused stage,
+                                      CTAs per SM of its parity-block form, first column-tile cap
+                                      of the register-tiled y-derivatives; the shapes never change
+                                      a result); NULL = none */
     int ygemm;                     /* mixed path y-derivatives of the step-by-step stage
                                       (helm 1-3): 0 autotuned at dns_bind_workspace, 1
                                       register-tiled FP32 with D2 v summed in float-float, 2
@@ -149,7 +150,7 @@ typedef struct {
                                       variant the group's size lacks is ignored */
     int helm;                      /* mixed path per-wavenumber stage: 0 autotuned at
                                       dns_bind_workspace (DNS groups: 1 and 2, each timed with the
-                                      y-derivatives and the forcing, against 4 and 5; linear
+                                      y-derivatives and the forcing, against 4, 5 and 6; linear
                                       groups: 1 against 2),
                                       1 register-tiled FP32 implicit apply (one CTA per
                                       wavenumber pair and field), 2 tcgen05 tensor cores with
@@ -165,7 +166,12 @@ typedef struct {
                                       with D2 v of the new state computed inside the same launch
                                       (the tensor-core digit product of the separate D2 v
                                       kernel, bit for bit the same result; groups with
-                                      My <= 66, at most 4 members per CTA; others run 4) */
+                                      My <= 66, at most 4 members per CTA; others run 4), 6 the
+                                      fused stage in parity blocks: every operator (centro-
+                                      symmetric M - I and P, anti-centro-symmetric D1 on the
+                                      symmetric grid) applied as its even and odd halves, half
+                                      the operator bytes and multiply-adds (groups whose D2 v
+                                      comes from the tensor-core kernel; others run 4) */
 } dns_config;
 
 /* One-point statistics of one member (paper Sec. 4), computed from the current
@@ -303,7 +309,8 @@ const char* dns_last_error(const dns_handle* h);
  * plane 1 one CTA per plane / 2 a thread-block cluster per plane / 3 line-owned
  * single CTA per plane; helm 1 register-tiled FP32 / 2 tcgen05 implicit apply /
  * 3 persistent register-tiled FP32 / 4 the fused per-wavenumber stage / 5 the
- * fused stage with D2 v inside it.  Any output may be NULL. */
+ * fused stage with D2 v inside it / 6 the fused stage in parity blocks.  Any
+ * output may be NULL. */
 int dns_kernel_choice(const dns_handle* h, int group, int* ygemm, int* plane, int* helm);
 
 /* Number of kernel launches enqueued by the last dns_step call (all steps). */

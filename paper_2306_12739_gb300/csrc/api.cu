@@ -40,7 +40,7 @@ struct HostGroup {
     dnsb::GridOps grid;
     dnsb::CnOps ops[2];
     std::vector<double> kxt, kzt, k2t, k2inv, twx, twz, opsdev[2], mopsdev[2], D1i, D2i;
-    std::vector<float> kxtf, kztf, k2invf, twxf, twzf, opsf[2], opsfT[2], D1T, D2T, D2Tl;
+    std::vector<float> kxtf, kztf, k2invf, twxf, twzf, opsf[2], opsfT[2], D1T, D2T, D2Tl, opsEO[2], D1EO;
     std::vector<uint16_t> Atc, Htc[2], D2oz;
     std::vector<int> D2ozexp;
     std::vector<double> fstruct, flam;   // stochastic forcing: structures [NKZ][2][n][Ny], decay rates
@@ -126,12 +126,40 @@ bool d2fuse_ok(GroupView v) {
     v.d2fuse = 1;
     return dnsk::spec_d2fuse_supported(v);
 }
+// the fused stage can run in parity blocks (helm request 6)
+bool eo_ok(GroupView v) {
+    v.spec_eo = 1;
+    v.d2fuse = 0;
+    return dnsk::spec_eo_supported(v);
+}
+// ... and its operator images are wanted (a request for it, or the autotuner)
+bool eo_candidate(const GroupView& v) { return (v.helm == 4 || v.helm == 0) && v.d2tc && eo_ok(v); }
 
 // Largest My at which DNS groups may take the FP32-accumulated tensor-core
 // y-derivatives (see choose_variants)
 constexpr int FP32_D2_MAX_MY = 49;
 
 // Assign workspace offsets for every device array of group g (base = 0).
+// The parity-block images of the fused stage in parity blocks: per h index and
+// wavenumber pair, M_v - I, P_v, M_eta - I, P_eta (from the FP64 operators),
+// and D1 (interior block).
+void build_eo_images(HostGroup& G) {
+    const GroupView& v = G.v;
+    const size_t nn = (size_t)v.ny * v.ny, mat = dnsk::spec_eo_mat_floats(v.ny);
+    std::vector<double> a(nn);
+    for (int hi = 0; hi < 2; ++hi) {
+        G.opsEO[hi].assign((size_t)v.npairs * 4 * mat, 0.f);
+        for (size_t blk = 0; blk < (size_t)v.npairs * 4; ++blk) {
+            memcpy(a.data(), &G.opsdev[hi][blk * nn], nn * sizeof(double));
+            if (blk % 4 == 0 || blk % 4 == 2)
+                for (int i = 0; i < v.ny; ++i) a[(size_t)i * v.ny + i] -= 1.0;
+            dnsk::spec_eo_image(a.data(), v.ny, false, &G.opsEO[hi][blk * mat]);
+        }
+    }
+    G.D1EO.assign(mat, 0.f);
+    dnsk::spec_eo_image(G.D1i.data(), v.ny, true, G.D1EO.data());
+}
+
 size_t layout_group(dns_handle* h, HostGroup& G, size_t cur) {
     GroupView& v = G.v;
     G.slots.clear();
@@ -148,6 +176,7 @@ size_t layout_group(dns_handle* h, HostGroup& G, size_t cur) {
     add((void**)&v.D1T, sizeof(float) * (size_t)v.ny * v.rp);
     add((void**)&v.D2T, sizeof(float) * (size_t)v.ny * v.rp);
     add((void**)&v.D2Tl, sizeof(float) * (size_t)v.ny * v.rp);
+    if (precision_mixed(h) && eo_candidate(v)) add((void**)&v.D1EO, sizeof(float) * dnsk::spec_eo_mat_floats(v.ny));
     add((void**)&v.status, 256);
     if (v.ygemm != 1) add((void**)&v.Atc, 3 * 128 * (size_t)v.kp * sizeof(uint16_t));
     if (v.d2tc) {
@@ -171,6 +200,7 @@ size_t layout_group(dns_handle* h, HostGroup& G, size_t cur) {
         if (precision_mixed(h)) {
             add((void**)&v.opsfT[hi], sizeof(float) * (size_t)v.npairs * 4 * v.ny * v.rp);
             if (helm_tc_candidate(v)) add((void**)&v.Htc[hi], (size_t)v.npairs * 2 * 3 * 64 * 2 * v.kp * sizeof(uint16_t));
+            if (eo_candidate(v)) add((void**)&v.opsEO[hi], sizeof(float) * (size_t)v.npairs * 4 * dnsk::spec_eo_mat_floats(v.ny));
         }
         add((void**)&v.mops[hi], sizeof(double) * (2 * nn + 3 * (size_t)v.ny + (size_t)v.ny * v.my));
     }
@@ -462,7 +492,7 @@ int cache_lookup(const char* path, const std::string& key) {
         std::string ln(line);
         if (ln.compare(0, key.size(), key) == 0 && ln.size() > key.size() + 1) {
             int c = atoi(ln.c_str() + key.size() + 1);
-            if (c >= 1 && c <= 5) found = c;
+            if (c >= 1 && c <= 6) found = c;
         }
     }
     fclose(f);
@@ -505,7 +535,7 @@ int choose_variants(dns_handle* h, const dns_config* cfg, GroupView& v, int gi) 
     // forcing) and 4
     v.helm = 1;
     if (precision_mixed(h)) {
-        if (cfg->helm == 4 || cfg->helm == 5) v.helm = dnsk::spec_supported(v) ? 4 : 0;
+        if (cfg->helm >= 4 && cfg->helm <= 6) v.helm = dnsk::spec_supported(v) ? 4 : 0;
         else if (cfg->helm == 0) v.helm = 0;
         else if (cfg->helm == 2 && dnsk::helm_tc_supported(v)) v.helm = 2;
         else if (cfg->helm == 3) v.helm = 3;
@@ -515,6 +545,9 @@ int choose_variants(dns_handle* h, const dns_config* cfg, GroupView& v, int gi) 
     v.d2tc = ((v.helm == 4 || v.helm == 0) && dnsk::spec_supported(v) && dnsk::d2v_tc_supported(v)) ? 1 : 0;
     // and, on request (helm 5) or by the autotuner, that digit product inside the fused launch
     v.d2fuse = (cfg->helm == 5 && v.helm == 4 && d2fuse_ok(v)) ? 1 : 0;
+    // or the fused stage in parity blocks (helm 6)
+    v.spec_eo = (cfg->helm == 6 && v.helm == 4 && eo_ok(v)) ? 1 : 0;
+    v.spec_minb = 2;
     // plane-stage kernel: single CTA per plane where it fits, a thread-block
     // cluster (distributed shared memory) where it does not; where both exist
     // the autotuner decides at bind time
@@ -622,6 +655,7 @@ int dns_create(const dns_config* cfg, void* cuda_stream, dns_handle** out) {
             if (rcv) return rcv;
             if (G.v.ygemm != 1 && G.Atc.empty()) G.Atc = dnsk::yderiv_tc_a_image(G.D1i, G.D2i, G.v.ny, G.v.kp);
             if (G.v.d2tc && G.D2oz.empty()) dnsk::d2v_tc_image(G.D2i, G.v.ny, G.v.kp, G.D2oz, G.D2ozexp);
+            if (precision_mixed(h) && eo_candidate(G.v) && G.opsEO[0].empty()) build_eo_images(G);
             if (precision_mixed(h) && helm_tc_candidate(G.v) && G.Htc[0].empty())
                 for (int hi = 0; hi < 2; ++hi)
                     G.Htc[hi] = dnsk::helm_tc_a_images(G.opsdev[hi], G.v.npairs, G.v.ny, G.v.kp);
@@ -754,6 +788,7 @@ int dns_create(const dns_config* cfg, void* cuda_stream, dns_handle** out) {
             }
         if (v.ygemm != 1) G.Atc = dnsk::yderiv_tc_a_image(G.D1i, G.D2i, v.ny, v.kp);
         if (v.d2tc) dnsk::d2v_tc_image(G.D2i, v.ny, v.kp, G.D2oz, G.D2ozexp);
+        if (precision_mixed(h) && eo_candidate(v)) build_eo_images(G);
         if (precision_mixed(h) && helm_tc_candidate(v))
             for (int hi = 0; hi < 2; ++hi) G.Htc[hi] = dnsk::helm_tc_a_images(G.opsdev[hi], v.npairs, v.ny, v.kp);
         if (!lin) G.twx = dnsb::twiddles(d.mx);
@@ -858,6 +893,9 @@ int dns_bind_workspace(dns_handle* h, void* dev_ptr, size_t bytes) {
             {v.D2T, G.D2T.data(), G.D2T.size() * 4},
             {v.D2Tl, G.D2Tl.data(), G.D2Tl.size() * 4},
             {v.D2oz, G.D2oz.data(), G.D2oz.size() * 2},
+            {v.opsEO[0], G.opsEO[0].data(), G.opsEO[0].size() * 4},
+            {v.opsEO[1], G.opsEO[1].data(), G.opsEO[1].size() * 4},
+            {v.D1EO, G.D1EO.data(), G.D1EO.size() * 4},
             {v.D2ozexp, G.D2ozexp.data(), G.D2ozexp.size() * 4},
             {v.mops[0], G.mopsdev[0].data(), G.mopsdev[0].size() * 8},
             {v.mops[1], G.mopsdev[1].data(), G.mopsdev[1].size() * 8},
@@ -959,23 +997,29 @@ int dns_bind_workspace(dns_handle* h, void* dev_ptr, size_t bytes) {
         const std::string key = tune_helm_key(v0);
         int choice = decided.count(key) ? decided[key] : cache_lookup(h->cfg.autotune_cache, key);
         // 5: the fused stage with its D2 v inside (every block of the group must allow it)
-        bool fuse_ok = dnsk::spec_supported(v0);
-        for (const auto& P : h->parts[gi]) fuse_ok = fuse_ok && d2fuse_ok(h->groups[P.ig].v);
+        // 6: the fused stage in parity blocks (its images were laid out for every block)
+        bool fuse_ok = dnsk::spec_supported(v0), par_ok = dnsk::spec_supported(v0);
+        for (const auto& P : h->parts[gi]) {
+            const GroupView& vb = h->groups[P.ig].v;
+            fuse_ok = fuse_ok && d2fuse_ok(vb);
+            par_ok = par_ok && eo_candidate(vb) && vb.opsEO[0] != nullptr && vb.D1EO != nullptr;
+        }
         if ((choice == 2 && !dnsk::helm_tc_supported(v0)) || (choice == 4 && !dnsk::spec_supported(v0)) ||
-            (choice == 5 && !fuse_ok) || choice == 3)
+            (choice == 5 && !fuse_ok) || (choice == 6 && !par_ok) || choice == 3)
             choice = 0;
         if (!choice) {
-            float best[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            float best[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             cudaEvent_t e0, e1;
             cudaEventCreate(&e0);
             cudaEventCreate(&e1);
-            for (int cand = 1; cand <= 5 && !rc; ++cand) {
+            for (int cand = 1; cand <= 6 && !rc; ++cand) {
                 if (cand == 3 || (cand == 2 && !dnsk::helm_tc_supported(v0)) ||
-                    (cand == 4 && !dnsk::spec_supported(v0)) || (cand == 5 && !fuse_ok))
+                    (cand == 4 && !dnsk::spec_supported(v0)) || (cand == 5 && !fuse_ok) || (cand == 6 && !par_ok))
                     continue;
                 for (const auto& P : h->parts[gi]) {
-                    h->groups[P.ig].v.helm = cand == 5 ? 4 : cand;
+                    h->groups[P.ig].v.helm = cand >= 4 ? 4 : cand;
                     h->groups[P.ig].v.d2fuse = cand == 5 ? 1 : 0;
+                    h->groups[P.ig].v.spec_eo = cand == 6 ? 1 : 0;
                 }
                 for (int w = 0; w < 2; ++w) enqueue_step(h);
                 cudaEventRecord(e0, st);
@@ -991,15 +1035,16 @@ int dns_bind_workspace(dns_handle* h, void* dev_ptr, size_t bytes) {
             if (rc) return rc;
             if ((rc = device_status(h))) return rc;
             choice = 0;
-            for (int cand = 1; cand <= 5; ++cand)
+            for (int cand = 1; cand <= 6; ++cand)
                 if (best[cand] > 0.f && (choice == 0 || best[cand] < best[choice])) choice = cand;
-            cache_store(h->cfg.autotune_cache, key, choice, best, 5);
+            cache_store(h->cfg.autotune_cache, key, choice, best, 6);
         }
         decided[key] = choice;
         for (const auto& P : h->parts[gi]) {
             GroupView& v = h->groups[P.ig].v;
-            v.helm = choice == 5 ? 4 : choice;
+            v.helm = choice >= 4 ? 4 : choice;
             v.d2fuse = choice == 5 ? 1 : 0;
+            v.spec_eo = choice == 6 ? 1 : 0;
             if (v.helm == 4) v.ygemm = 1;
         }
     }
@@ -1077,6 +1122,7 @@ int dns_bind_workspace(dns_handle* h, void* dev_ptr, size_t bytes) {
         for (int ec : {std::min(v.E, 8), (std::min(v.E, 8) + 1) / 2, 2}) {
             v.spec_ec = ec;
             if (v.d2fuse && (ec > 4 || !dnsk::spec_d2fuse_supported(v))) continue;   // its N holds 4 members
+            if (v.spec_eo && !dnsk::spec_eo_supported(v)) continue;
             if (ec >= 1 && dnsk::spec_supported(v) && std::find(cands.begin(), cands.end(), ec) == cands.end())
                 cands.push_back(ec);
         }
@@ -1114,6 +1160,48 @@ int dns_bind_workspace(dns_handle* h, void* dev_ptr, size_t bytes) {
         }
         decided[key] = choice;
         v.spec_ec = choice;
+    }
+    // CTAs per SM of the fused stage in parity blocks (the registers budgeted
+    // for 2 or for 3): by timing whole steps, every block of the group on the
+    // candidate (a third CTA per SM helps the concurrent member blocks more
+    // than it costs the kernel alone)
+    for (size_t gi = 0; gi < h->parts.size(); ++gi) {
+        GroupView& v0 = h->groups[h->parts[gi][0].ig].v;
+        if (!precision_mixed(h) || v0.helm != 4 || !v0.spec_eo) continue;
+        char kb[96];
+        snprintf(kb, sizeof kb, "spec_cta %d %d %d %d", v0.mx, v0.my, v0.mz, v0.E);
+        const std::string key = kb;
+        const std::vector<int> cands = {2, 3};
+        int choice = decided.count(key) ? decided[key] : cache_lookup_value(h->cfg.autotune_cache, key);
+        if (std::find(cands.begin(), cands.end(), choice) == cands.end()) choice = 0;
+        if (!choice) {
+            std::vector<float> ms(cands.size(), 0.f);
+            cudaEvent_t e0, e1;
+            cudaEventCreate(&e0);
+            cudaEventCreate(&e1);
+            for (size_t ci = 0; ci < cands.size() && !rc; ++ci) {
+                for (const auto& P : h->parts[gi]) h->groups[P.ig].v.spec_minb = cands[ci];
+                for (int w = 0; w < 2; ++w) enqueue_step(h);
+                cudaEventRecord(e0, st);
+                for (int r = 0; r < 3; ++r) enqueue_step(h);
+                cudaEventRecord(e1, st);
+                rc = check(h, cudaEventSynchronize(e1), "autotune fused-stage CTAs per SM");
+                if (!rc) cudaEventElapsedTime(&ms[ci], e0, e1);
+            }
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            h->launches = 0;
+            if (rc) return rc;
+            if ((rc = device_status(h))) return rc;
+            size_t best = 0;
+            for (size_t ci = 1; ci < cands.size(); ++ci)
+                if (ms[ci] < ms[best]) best = ci;
+            choice = cands[best];
+            for (auto& m : ms) m /= 3.f;
+            cache_store_shape(h->cfg.autotune_cache, key, choice, cands, ms);
+        }
+        decided[key] = choice;
+        for (const auto& P : h->parts[gi]) h->groups[P.ig].v.spec_minb = choice;
     }
     // First column-tile cap of the register-tiled y-derivatives (in the
     // step-by-step stage every sub-step, with the fused stage for every newly
@@ -2014,7 +2102,7 @@ int dns_kernel_choice(const dns_handle* h, int group, int* ygemm, int* plane, in
     const GroupView& v = h->groups[h->parts[group][0].ig].v;
     if (ygemm) *ygemm = v.ygemm;
     if (plane) *plane = v.plane;
-    if (helm) *helm = (v.helm == 4 && v.d2fuse) ? 5 : v.helm;
+    if (helm) *helm = v.helm != 4 ? v.helm : v.d2fuse ? 5 : v.spec_eo ? 6 : 4;
     return DNS_OK;
 }
 

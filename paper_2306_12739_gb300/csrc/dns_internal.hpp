@@ -59,6 +59,11 @@ struct GroupView {
     const float* D2Tl;    // D2T's residual: D2i - (double) D2T in single precision (compensated D2 v)
     int d2tc;             // fused stage: 1 = D2 v of the new state by the tensor-core digit kernel
     int d2fuse;           // fused stage: 1 = that digit product inside the fused launch (no D2 v launch)
+    int spec_eo;          // fused stage: 1 = in parity blocks (even / odd parts in y; with d2tc)
+    int spec_minb;        // fused stage in parity blocks: CTAs per SM of its register budget (2 or 3)
+    const float* opsEO[2];  // mixed path, per h index: [npairs][4] matrices (M - I, P of v and eta) in
+                            // parity blocks, each eo_mat(Ny) floats (see k_spec.cu)
+    const float* D1EO;      // D1 in parity blocks
     int spec_ec;          // fused stage: members per CTA (0 = up to 8), set by the autotuner
     int yd_cap;           // register-tiled y-derivatives: first column-tile cap (0 = 64, or 32 above
                           //    Ny = 96), halved while the grid is short of 3 CTAs per SM; autotuned
@@ -165,6 +170,11 @@ void set_attributes_d2v_tc();
 // fused per-wavenumber stage of the mixed path (k_spec.cu)
 bool spec_supported(const GroupView& g);
 bool spec_d2fuse_supported(const GroupView& g);   // with g.d2fuse set: the fused D2 v can run
+bool spec_eo_supported(const GroupView& g);       // the fused stage in parity blocks can run
+size_t spec_eo_mat_floats(int ny);                // floats of one matrix in parity blocks
+// one Ny x Ny row-major matrix (centro-symmetric, or anti-centro-symmetric when
+// anti) as its two parity blocks, transposed and row-padded (out: spec_eo_mat_floats)
+void spec_eo_image(const double* A, int ny, bool anti, float* out);
 size_t spec_smem_bytes(const GroupView& g);
 void launch_spec(const GroupView& g, int s, cudaStream_t st);
 void set_attributes_spec();

@@ -293,7 +293,7 @@ __device__ __forceinline__ void apply_epilogue(const GroupView& g, int s, int f,
 // mode, or both): with a compile-time EC both divisions are by constants
 template <int ECC>
 __device__ __forceinline__ int div_cols(int t, int C) {
-    if (ECC > 0) {
+    if constexpr (ECC > 0) {
         if (C == 2 * ECC) return t / (2 * ECC);
         if (C == ECC) return t / ECC;
     }
@@ -761,6 +761,502 @@ __global__ void __launch_bounds__(THREADS, 2) k_spec(GroupView g, int s) {
     }
 }
 
+
+// ============================================================================
+// The fused stage in parity blocks (k_spec_eo).  On the symmetric Chebyshev
+// grid (y_j = -y_{Ny-1-j}) the per-wavenumber operators M - I and P of both
+// fields commute with the reflection y -> -y (centro-symmetric) and D1
+// anticommutes with it.  With every vector split into its even and odd parts,
+//   x_e[i] = x[i] + x[Ny-1-i],  x_o[i] = x[i] - x[Ny-1-i]   (i < Ny / 2),
+//   x_e[c] = x[c] at the centre c = (Ny-1)/2 when Ny is odd,
+// a centro-symmetric operator maps even parts to even parts and odd to odd,
+// and D1 maps odd to even and even to odd: each product becomes two blocks of
+// half the size (NE = ceil(Ny/2) and NO = floor(Ny/2) rows), half the
+// operator bytes and half the multiply-adds.  The host stores each matrix as
+// its two blocks, transposed and row-padded to RP2 (eo_block_image).  Vectors
+// in shared memory hold the even part in rows 0 .. NE-1 and the odd part in
+// rows NE .. Ny-1; the state, forcing accumulators and outputs stay in the
+// natural order in global memory, and every task converts the natural rows of
+// its pair-rows (i and Ny-1-i) on the way in and out.  Used where D2 v comes
+// from the tensor-core digit kernel.
+// ============================================================================
+
+__host__ __device__ inline int eo_ne(int ny) { return (ny + 1) / 2; }
+__host__ __device__ inline int eo_rp(int ny) { return 2 * ((eo_ne(ny) + 1) / 2); }
+// floats of one matrix in parity blocks (a multiple of 4: 16-byte copies)
+__host__ __device__ inline size_t eo_mat(int ny) { return ((size_t)ny * eo_rp(ny) + 3) / 4 * 4; }
+__host__ __device__ inline size_t eo_smem_bytes(const GroupView& g) {
+    return (5 * eo_mat(g.ny) + 7 * vec_floats(g)) * sizeof(float) + 32;
+}
+
+// Two pair-rows p0, p0 + 1 x one complex column (c2 its real column) of a
+// matrix in parity blocks B: the block of the even output rows [KE][RP2]
+// contracts XE, the block of the odd output rows [KO][RP2] (after it)
+// contracts XO.
+__device__ __forceinline__ void eo2(const float* B, int KE, int KO, int RP2, const float* XE, const float* XO, int VS,
+                                    int p0, int c2, float (&ye)[2][2], float (&yo)[2][2]) {
+#pragma unroll
+    for (int r = 0; r < 2; ++r) { ye[r][0] = ye[r][1] = yo[r][0] = yo[r][1] = 0.f; }
+#pragma unroll 4
+    for (int k = 0; k < KE; ++k) {
+        const float2 b = *(const float2*)&B[k * RP2 + p0];
+        const float2 x = *(const float2*)&XE[k * VS + c2];
+        ye[0][0] += b.x * x.x; ye[0][1] += b.x * x.y; ye[1][0] += b.y * x.x; ye[1][1] += b.y * x.y;
+    }
+    const float* BO = B + KE * RP2;
+#pragma unroll 4
+    for (int k = 0; k < KO; ++k) {
+        const float2 b = *(const float2*)&BO[k * RP2 + p0];
+        const float2 x = *(const float2*)&XO[k * VS + c2];
+        yo[0][0] += b.x * x.x; yo[0][1] += b.x * x.y; yo[1][0] += b.y * x.x; yo[1][1] += b.y * x.y;
+    }
+}
+
+// Two matrices A, B in parity blocks, the same pair-rows and column, with
+// their own inputs (the implicit apply of eta: (M - I) x + P G~)
+__device__ __forceinline__ void eo2x2(const float* A, const float* B, int KE, int KO, int RP2, const float* XAE,
+                                      const float* XAO, const float* XBE, const float* XBO, int VS, int p0, int c2,
+                                      bool needA, float (&ae)[2][2], float (&ao)[2][2], float (&be)[2][2],
+                                      float (&bo)[2][2]) {
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int c = 0; c < 2; ++c) ae[r][c] = ao[r][c] = be[r][c] = bo[r][c] = 0.f;
+#pragma unroll 4
+    for (int k = 0; k < KE; ++k) {
+        const float2 bb = *(const float2*)&B[k * RP2 + p0];
+        const float2 xb = *(const float2*)&XBE[k * VS + c2];
+        be[0][0] += bb.x * xb.x; be[0][1] += bb.x * xb.y; be[1][0] += bb.y * xb.x; be[1][1] += bb.y * xb.y;
+        if (needA) {
+            const float2 aa = *(const float2*)&A[k * RP2 + p0];
+            const float2 xa = *(const float2*)&XAE[k * VS + c2];
+            ae[0][0] += aa.x * xa.x; ae[0][1] += aa.x * xa.y; ae[1][0] += aa.y * xa.x; ae[1][1] += aa.y * xa.y;
+        }
+    }
+    const float* AO = A + KE * RP2;
+    const float* BO = B + KE * RP2;
+#pragma unroll 4
+    for (int k = 0; k < KO; ++k) {
+        const float2 bb = *(const float2*)&BO[k * RP2 + p0];
+        const float2 xb = *(const float2*)&XBO[k * VS + c2];
+        bo[0][0] += bb.x * xb.x; bo[0][1] += bb.x * xb.y; bo[1][0] += bb.y * xb.x; bo[1][1] += bb.y * xb.y;
+        if (needA) {
+            const float2 aa = *(const float2*)&AO[k * RP2 + p0];
+            const float2 xa = *(const float2*)&XAO[k * VS + c2];
+            ao[0][0] += aa.x * xa.x; ao[0][1] += aa.x * xa.y; ao[1][0] += aa.y * xa.x; ao[1][1] += aa.y * xa.y;
+        }
+    }
+}
+
+// one pair-row p (phase 4: every thread one pair-row of one column)
+__device__ __forceinline__ void eo1(const float* B, int KE, int KO, int RP2, const float* XE, const float* XO, int VS,
+                                    int p, int c2, float (&ye)[2], float (&yo)[2]) {
+    ye[0] = ye[1] = yo[0] = yo[1] = 0.f;
+#pragma unroll 4
+    for (int k = 0; k < KE; ++k) {
+        const float b = B[k * RP2 + p];
+        const float2 x = *(const float2*)&XE[k * VS + c2];
+        ye[0] += b * x.x; ye[1] += b * x.y;
+    }
+    const float* BO = B + KE * RP2;
+#pragma unroll 4
+    for (int k = 0; k < KO; ++k) {
+        const float b = BO[k * RP2 + p];
+        const float2 x = *(const float2*)&XO[k * VS + c2];
+        yo[0] += b * x.x; yo[1] += b * x.y;
+    }
+}
+
+// natural rows of pair-row p: y0 = p and, below the centre, y1 = Ny-1-p
+struct EoRows {
+    int y0, y1;
+    bool pair;
+};
+__device__ __forceinline__ EoRows eo_rows(int p, int Ny) {
+    EoRows r;
+    r.y0 = p;
+    r.y1 = Ny - 1 - p;
+    r.pair = p < Ny / 2;
+    return r;
+}
+
+// MINB: CTAs per SM the registers are budgeted for (2, or 3 at 80 registers;
+// shared memory allows 3): chosen by timing whole steps
+template <int NYC, int ECC, int MINB>
+__global__ void __launch_bounds__(THREADS, MINB) k_spec_eo(GroupView g, int s) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    const int nrow = mean_row_ctas(g);
+    if ((int)blockIdx.x < nrow) {
+        mean_cta(g, s, blockIdx.x, sm);
+        return;
+    }
+    const int Ny = NYC ? NYC : g.ny;
+    const int NE = (Ny + 1) / 2, NO = Ny / 2, RB2 = (NE + 1) / 2, RP2 = 2 * RB2;
+    const size_t MEO = eo_mat(Ny);
+    const int E = g.E, NM = g.nmodes, NKX = g.nkx;
+    const int EC = ECC ? ECC : chunk_members(g), VS = 4 * EC;
+    const size_t VF = (size_t)Ny * VS;
+    const int b = blockIdx.x - nrow;
+    const int np1 = g.npairs - 1;                 // pair 0 is the mean mode: no CTA
+    Cols c;
+    c.p = 1 + b % np1;
+    const int ch = b / np1;
+    c.n = c.p % NKX;
+    c.am = c.p / NKX;
+    c.nq = c.am > 0 ? 2 : 1;
+    c.q1 = (g.kz + c.am) * NKX + c.n;
+    c.q2 = (g.kz - c.am) * NKX + c.n;
+    c.e0 = ch * EC;
+    c.ec = min(EC, E - c.e0);
+    c.C = c.nq * c.ec;
+    float* OPS = (float*)sm;                      // 4 x MEO: (Mv-I), Pv, (Me-I), Pe in parity blocks
+    float* D1S = OPS + 4 * MEO;                   // D1 in parity blocks
+    float* PH = D1S + MEO;                        // phi, then v+
+    float* KV = PH + VF;                          // -k^2 Nv (+ noise), then (M_v - I) v_t
+    float* GT = KV + VF;                          // G~
+    float* XV = GT + VF;                          // v_t (single precision)
+    float* XE = XV + VF;                          // eta_t
+    float* FT = XE + VF;                          // F~
+    float* EN = FT + VF;                          // eta+
+    unsigned long long* bar = (unsigned long long*)(EN + VF);
+    const unsigned bar_a = su32(bar);
+    const int tid = threadIdx.x;
+    const bool needM = (s != 2);
+    const int hidx = (s == 0) ? 0 : 1;
+
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_a) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (tid == 0 && DNS_CK(g.status, c.p < g.npairs, CK_SPEC, c.p)) {
+        const float* src = g.opsEO[hidx] + (size_t)c.p * 4 * MEO;
+        const unsigned mb = (unsigned)(MEO * sizeof(float));
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_a),
+                     "r"(needM ? 5 * mb : 3 * mb) : "memory");
+        bulk(D1S, g.D1EO, mb, bar_a);
+        if (needM) {
+            bulk(OPS, src, 4 * mb, bar_a);
+        } else {
+            bulk(OPS + MEO, src + MEO, mb, bar_a);
+            bulk(OPS + 3 * MEO, src + 3 * MEO, mb, bar_a);
+        }
+    }
+
+    // ---- phase 1: the nonlinear terms of both natural rows of each pair-row
+    // -> phi, -k^2 Nv, G~ (with its RK accumulator, natural rows), x_t; their
+    // even and odd parts into shared memory
+    {
+        const size_t fs = (size_t)Ny * E * NM;
+        const float2* N3 = (const float2*)g.N3;
+        float2* Ae = (float2*)g.Ae;
+        const float kx = g.kxtf[c.n];
+        const bool forced = g.fn > 0 && c.n == g.fn;
+        const int total = NE * c.C;
+        for (int i = tid; i < total; i += THREADS) {
+            const int p = div_cols<ECC>(i, c.C), j = i - p * c.C;
+            const int q = col_q(c, j), e = col_e(c, j);
+            const int mz = j < c.ec ? g.kz + c.am : g.kz - c.am;    // = q / NKX
+            const float kz = g.kztf[mz];
+            const float k2 = kx * kx + kz * kz;
+            const EoRows R = eo_rows(p, Ny);
+            float2 ph[2], kvv[2], gt[2];
+            double2 xv[2], xe[2];
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                ph[r] = kvv[r] = gt[r] = make_float2(0.f, 0.f);
+                xv[r] = xe[r] = make_double2(0.0, 0.0);
+                const int y = r ? R.y1 : R.y0;
+                if ((r && !R.pair) || !in_range(g, q, y, e)) continue;
+                const size_t op = ((size_t)y * E + e) * NM + q;
+                const size_t oh = ((size_t)q * Ny + y) * E + e;
+                const float2 nu = N3[op], nv = N3[fs + op], nw = N3[2 * fs + op];
+                float2 ae = make_float2(0.f, 0.f);
+                if (s != 0) ae = Ae[oh];
+                if (needM) {
+                    xv[r] = g.v_t[oh];
+                    xe[r] = g.e_t[oh];
+                }
+                const float ax = kx * nu.x + kz * nw.x, ay = kx * nu.y + kz * nw.y;   // i kx Nu + i kz Nw
+                const float bx = kz * nu.x - kx * nw.x, by = kz * nu.y - kx * nw.y;   // i kz Nu - i kx Nw
+                float2 kv = make_float2(-k2 * nv.x, -k2 * nv.y);
+                float2 G = make_float2(-by, bx);
+                if (forced && DNS_CK(g.status, mz < g.nkz, CK_SPEC, q)) {
+                    const size_t o = ((size_t)mz * Ny + y) * E + e, half = (size_t)g.nkz * Ny * E;
+                    kv.x += (float)g.noise[o].x; kv.y += (float)g.noise[o].y;
+                    G.x += (float)g.noise[half + o].x; G.y += (float)g.noise[half + o].y;
+                }
+                float2 Gt;
+                if (s == 0) {
+                    Gt = G;
+                    Ae[oh] = G;
+                } else if (s == 1) {
+                    Gt = make_float2(2.f * G.x - ae.x, 2.f * G.y - ae.y);
+                    Ae[oh] = make_float2((1.f / 6.f) * ae.x + (4.f / 6.f) * G.x, (1.f / 6.f) * ae.y + (4.f / 6.f) * G.y);
+                } else {
+                    Gt = make_float2(ae.x + (1.f / 6.f) * G.x, ae.y + (1.f / 6.f) * G.y);
+                }
+                ph[r] = make_float2(-ay, ax);
+                kvv[r] = kv;
+                gt[r] = Gt;
+            }
+            if (!DNS_CK(g.status, 2 * j + 1 < VS && p < NE, CK_SPEC_SMEM, p * VS + 2 * j)) continue;
+            const int se = p * VS + 2 * j, so = (NE + p) * VS + 2 * j;
+            *(float2*)&PH[se] = make_float2(ph[0].x + ph[1].x, ph[0].y + ph[1].y);
+            *(float2*)&KV[se] = make_float2(kvv[0].x + kvv[1].x, kvv[0].y + kvv[1].y);
+            *(float2*)&GT[se] = make_float2(gt[0].x + gt[1].x, gt[0].y + gt[1].y);
+            if (needM) {
+                *(float2*)&XV[se] = make_float2(d2f(xv[0].x + xv[1].x), d2f(xv[0].y + xv[1].y));
+                *(float2*)&XE[se] = make_float2(d2f(xe[0].x + xe[1].x), d2f(xe[0].y + xe[1].y));
+            }
+            if (R.pair) {
+                *(float2*)&PH[so] = make_float2(ph[0].x - ph[1].x, ph[0].y - ph[1].y);
+                *(float2*)&KV[so] = make_float2(kvv[0].x - kvv[1].x, kvv[0].y - kvv[1].y);
+                *(float2*)&GT[so] = make_float2(gt[0].x - gt[1].x, gt[0].y - gt[1].y);
+                if (needM) {
+                    *(float2*)&XV[so] = make_float2(d2f(xv[0].x - xv[1].x), d2f(xv[0].y - xv[1].y));
+                    *(float2*)&XE[so] = make_float2(d2f(xe[0].x - xe[1].x), d2f(xe[0].y - xe[1].y));
+                }
+            }
+        }
+    }
+    __syncthreads();
+    // every thread waits for the operators (bounded); on a timeout the CTA
+    // latches the status word, waits once more for the copy and leaves
+    if (!__syncthreads_and(waitp(bar_a, 0))) {
+        if (tid == 0) {
+            atomicExch(g.status, 1);
+            waitp(bar_a, 0);
+        }
+        return;
+    }
+    const int ntask = RB2 * c.C;
+    const size_t fs5 = (size_t)Ny * E * NM;
+    float2* P5 = (float2*)g.P5;
+
+    // ---- phase 2: F~ and (M_v - I) v_t (threads 0..127) | eta+ (threads 128..255);
+    // tasks of two pair-rows x one complex column
+    if (tid < HALF) {
+        float2* Av = (float2*)g.Av;
+        for (int t = tid; t < ntask; t += HALF) {
+            const int rb = div_cols<ECC>(t, c.C), j = t - rb * c.C, p0 = 2 * rb;
+            const int q = col_q(c, j), e = col_e(c, j);
+            float2 pav[2][2];
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                pav[r][0] = pav[r][1] = make_float2(0.f, 0.f);
+                const EoRows R = eo_rows(p0 + r, Ny);
+                if (s == 0 || p0 + r >= NE) continue;
+                if (in_range(g, q, R.y0, e)) pav[r][0] = Av[((size_t)q * Ny + R.y0) * E + e];
+                if (R.pair && in_range(g, q, R.y1, e)) pav[r][1] = Av[((size_t)q * Ny + R.y1) * E + e];
+            }
+            // D1 phi: the even rows contract the odd part, the odd rows the even part
+            float ae[2][2], ao[2][2];
+            eo2(D1S, NO, NE, RP2, PH + NE * VS, PH, VS, p0, 2 * j, ae, ao);
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                const int p = p0 + r;
+                if (p >= NE) break;
+                const EoRows R = eo_rows(p, Ny);
+                const float2 kve = *(const float2*)&KV[p * VS + 2 * j];
+                const float2 kvo = R.pair ? *(const float2*)&KV[(NE + p) * VS + 2 * j] : make_float2(0.f, 0.f);
+                const float2 Fe = make_float2(kve.x - ae[r][0], kve.y - ae[r][1]);
+                const float2 Fo = make_float2(kvo.x - ao[r][0], kvo.y - ao[r][1]);
+                float2 Ftn[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+#pragma unroll
+                for (int k2 = 0; k2 < 2; ++k2) {
+                    const int y = k2 ? R.y1 : R.y0;
+                    if ((k2 && !R.pair) || !in_range(g, q, y, e)) continue;
+                    // the natural row's F: half the sum or difference of its parts
+                    const float2 F = !R.pair ? Fe
+                                   : k2 ? make_float2(0.5f * (Fe.x - Fo.x), 0.5f * (Fe.y - Fo.y))
+                                        : make_float2(0.5f * (Fe.x + Fo.x), 0.5f * (Fe.y + Fo.y));
+                    const size_t oh = ((size_t)q * Ny + y) * E + e;
+                    const float2 pa = pav[r][k2];
+                    float2 Ft;
+                    if (s == 0) {
+                        Ft = F;
+                        Av[oh] = F;
+                    } else if (s == 1) {
+                        Ft = make_float2(2.f * F.x - pa.x, 2.f * F.y - pa.y);
+                        Av[oh] = make_float2((1.f / 6.f) * pa.x + (4.f / 6.f) * F.x, (1.f / 6.f) * pa.y + (4.f / 6.f) * F.y);
+                    } else {
+                        Ft = make_float2(pa.x + (1.f / 6.f) * F.x, pa.y + (1.f / 6.f) * F.y);
+                    }
+                    Ftn[k2] = Ft;
+                }
+                *(float2*)&FT[p * VS + 2 * j] = make_float2(Ftn[0].x + Ftn[1].x, Ftn[0].y + Ftn[1].y);
+                if (R.pair)
+                    *(float2*)&FT[(NE + p) * VS + 2 * j] = make_float2(Ftn[0].x - Ftn[1].x, Ftn[0].y - Ftn[1].y);
+            }
+            // (M_v - I) v_t of the same pair-rows and column, kept in the KV slots
+            // this thread has just read, for phase 3
+            if (needM) {
+                float me[2][2], mo[2][2];
+                eo2(OPS, NE, NO, RP2, XV, XV + NE * VS, VS, p0, 2 * j, me, mo);
+#pragma unroll
+                for (int r = 0; r < 2; ++r) {
+                    const int p = p0 + r;
+                    if (p >= NE) break;
+                    *(float2*)&KV[p * VS + 2 * j] = make_float2(me[r][0], me[r][1]);
+                    if (p < NO) *(float2*)&KV[(NE + p) * VS + 2 * j] = make_float2(mo[r][0], mo[r][1]);
+                }
+            }
+        }
+    } else {
+        float2* M1 = (float2*)g.mx1_e;
+        double2* O = (s == 2) ? g.e_t : g.e_s;
+        for (int t = tid - HALF; t < ntask; t += HALF) {
+            const int rb = div_cols<ECC>(t, c.C), j = t - rb * c.C, p0 = 2 * rb;
+            const int q = col_q(c, j), e = col_e(c, j);
+            double2 x[2][2];
+            float2 m1s[2][2];
+#pragma unroll
+            for (int r = 0; r < 2; ++r)
+#pragma unroll
+                for (int k2 = 0; k2 < 2; ++k2) {
+                    const EoRows R = eo_rows(p0 + r, Ny);
+                    const int y = k2 ? R.y1 : R.y0;
+                    x[r][k2] = make_double2(0.0, 0.0);
+                    m1s[r][k2] = make_float2(0.f, 0.f);
+                    if (p0 + r >= NE || (k2 && !R.pair) || !in_range(g, q, y, e)) continue;
+                    const size_t oh = ((size_t)q * Ny + y) * E + e;
+                    x[r][k2] = g.e_t[oh];
+                    if (s == 2) m1s[r][k2] = M1[oh];
+                }
+            float mae[2][2], mao[2][2], pae[2][2], pao[2][2];
+            eo2x2(OPS + 2 * MEO, OPS + 3 * MEO, NE, NO, RP2, XE, XE + NE * VS, GT, GT + NE * VS, VS, p0, 2 * j,
+                  needM, mae, mao, pae, pao);
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                const int p = p0 + r;
+                if (p >= NE) break;
+                const EoRows R = eo_rows(p, Ny);
+                double2 xn[2] = {make_double2(0.0, 0.0), make_double2(0.0, 0.0)};
+#pragma unroll
+                for (int k2 = 0; k2 < 2; ++k2) {
+                    const int y = k2 ? R.y1 : R.y0;
+                    if ((k2 && !R.pair) || !in_range(g, q, y, e)) continue;
+                    const float sg = k2 ? -1.f : 1.f;
+                    const float2 ma = R.pair ? make_float2(0.5f * (mae[r][0] + sg * mao[r][0]), 0.5f * (mae[r][1] + sg * mao[r][1]))
+                                             : make_float2(mae[r][0], mae[r][1]);
+                    const float2 pa = R.pair ? make_float2(0.5f * (pae[r][0] + sg * pao[r][0]), 0.5f * (pae[r][1] + sg * pao[r][1]))
+                                             : make_float2(pae[r][0], pae[r][1]);
+                    const size_t oh = ((size_t)q * Ny + y) * E + e;
+                    const float2 m1 = (s == 2) ? m1s[r][k2] : ma;
+                    if (s == 1) M1[oh] = m1;
+                    xn[k2] = make_double2(x[r][k2].x + f2d(m1.x + pa.x), x[r][k2].y + f2d(m1.y + pa.y));
+                    O[oh] = xn[k2];
+                    P5[3 * fs5 + ((size_t)y * E + e) * NM + q] = make_float2(d2f(xn[k2].x), d2f(xn[k2].y));
+                }
+                *(float2*)&EN[p * VS + 2 * j] = make_float2(d2f(xn[0].x + xn[1].x), d2f(xn[0].y + xn[1].y));
+                if (R.pair)
+                    *(float2*)&EN[(NE + p) * VS + 2 * j] = make_float2(d2f(xn[0].x - xn[1].x), d2f(xn[0].y - xn[1].y));
+            }
+        }
+    }
+    __syncthreads();
+
+    // ---- phase 3: v+ (P_v F~, threads 0..127) | D eta (threads 128..255)
+    if (tid < HALF) {
+        float2* M1 = (float2*)g.mx1_v;
+        double2* O = (s == 2) ? g.v_t : g.v_s;
+        for (int t = tid; t < ntask; t += HALF) {
+            const int rb = div_cols<ECC>(t, c.C), j = t - rb * c.C, p0 = 2 * rb;
+            const int q = col_q(c, j), e = col_e(c, j);
+            double2 x[2][2];
+            float2 m1s[2][2];
+#pragma unroll
+            for (int r = 0; r < 2; ++r)
+#pragma unroll
+                for (int k2 = 0; k2 < 2; ++k2) {
+                    const EoRows R = eo_rows(p0 + r, Ny);
+                    const int y = k2 ? R.y1 : R.y0;
+                    x[r][k2] = make_double2(0.0, 0.0);
+                    m1s[r][k2] = make_float2(0.f, 0.f);
+                    if (p0 + r >= NE || (k2 && !R.pair) || !in_range(g, q, y, e)) continue;
+                    const size_t oh = ((size_t)q * Ny + y) * E + e;
+                    x[r][k2] = g.v_t[oh];
+                    if (s == 2) m1s[r][k2] = M1[oh];
+                }
+            float pe[2][2], po[2][2];
+            eo2(OPS + MEO, NE, NO, RP2, FT, FT + NE * VS, VS, p0, 2 * j, pe, po);
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                const int p = p0 + r;
+                if (p >= NE) break;
+                const EoRows R = eo_rows(p, Ny);
+                float2 me = make_float2(0.f, 0.f), mo = me;
+                if (needM) {
+                    me = *(const float2*)&KV[p * VS + 2 * j];
+                    if (R.pair) mo = *(const float2*)&KV[(NE + p) * VS + 2 * j];
+                }
+                double2 xn[2] = {make_double2(0.0, 0.0), make_double2(0.0, 0.0)};
+#pragma unroll
+                for (int k2 = 0; k2 < 2; ++k2) {
+                    const int y = k2 ? R.y1 : R.y0;
+                    if ((k2 && !R.pair) || !in_range(g, q, y, e)) continue;
+                    const float sg = k2 ? -1.f : 1.f;
+                    const float2 ma = R.pair ? make_float2(0.5f * (me.x + sg * mo.x), 0.5f * (me.y + sg * mo.y)) : me;
+                    const float2 pa = R.pair ? make_float2(0.5f * (pe[r][0] + sg * po[r][0]), 0.5f * (pe[r][1] + sg * po[r][1]))
+                                             : make_float2(pe[r][0], pe[r][1]);
+                    const size_t oh = ((size_t)q * Ny + y) * E + e;
+                    const float2 m1 = (s == 2) ? m1s[r][k2] : ma;
+                    if (s == 1) M1[oh] = m1;
+                    xn[k2] = make_double2(x[r][k2].x + f2d(m1.x + pa.x), x[r][k2].y + f2d(m1.y + pa.y));
+                    O[oh] = xn[k2];
+                    P5[((size_t)y * E + e) * NM + q] = make_float2(d2f(xn[k2].x), d2f(xn[k2].y));
+                }
+                // v+ in parity parts (over phi) for D v
+                *(float2*)&PH[p * VS + 2 * j] = make_float2(d2f(xn[0].x + xn[1].x), d2f(xn[0].y + xn[1].y));
+                if (R.pair)
+                    *(float2*)&PH[(NE + p) * VS + 2 * j] = make_float2(d2f(xn[0].x - xn[1].x), d2f(xn[0].y - xn[1].y));
+            }
+        }
+    } else {
+        for (int t = tid - HALF; t < ntask; t += HALF) {
+            const int rb = div_cols<ECC>(t, c.C), j = t - rb * c.C, p0 = 2 * rb;
+            const int q = col_q(c, j), e = col_e(c, j);
+            float de[2][2], dq[2][2];
+            eo2(D1S, NO, NE, RP2, EN + NE * VS, EN, VS, p0, 2 * j, de, dq);
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                const int p = p0 + r;
+                if (p >= NE) break;
+                const EoRows R = eo_rows(p, Ny);
+#pragma unroll
+                for (int k2 = 0; k2 < 2; ++k2) {
+                    const int y = k2 ? R.y1 : R.y0;
+                    if ((k2 && !R.pair) || !in_range(g, q, y, e)) continue;
+                    const float sg = k2 ? -1.f : 1.f;
+                    const float2 d = R.pair ? make_float2(0.5f * (de[r][0] + sg * dq[r][0]), 0.5f * (de[r][1] + sg * dq[r][1]))
+                                            : make_float2(de[r][0], de[r][1]);
+                    P5[4 * fs5 + ((size_t)y * E + e) * NM + q] = d;
+                }
+            }
+        }
+    }
+    __syncthreads();
+
+    // ---- phase 4: D v on every thread, one pair-row x one complex column each
+    for (int t = tid; t < NE * c.C; t += THREADS) {
+        const int p = div_cols<ECC>(t, c.C), j = t - p * c.C;
+        const int q = col_q(c, j), e = col_e(c, j);
+        const EoRows R = eo_rows(p, Ny);
+        float de[2], dq[2];
+        eo1(D1S, NO, NE, RP2, PH + NE * VS, PH, VS, p, 2 * j, de, dq);
+#pragma unroll
+        for (int k2 = 0; k2 < 2; ++k2) {
+            const int y = k2 ? R.y1 : R.y0;
+            if ((k2 && !R.pair) || !in_range(g, q, y, e)) continue;
+            const float sg = k2 ? -1.f : 1.f;
+            const float2 d = R.pair ? make_float2(0.5f * (de[0] + sg * dq[0]), 0.5f * (de[1] + sg * dq[1]))
+                                    : make_float2(de[0], de[1]);
+            P5[fs5 + ((size_t)y * E + e) * NM + q] = d;
+        }
+    }
+}
+
 }  // namespace spc
 
 bool spec_supported(const GroupView& g) {
@@ -776,8 +1272,47 @@ bool spec_d2fuse_supported(const GroupView& g) {
 }
 
 size_t spec_smem_bytes(const GroupView& g) {
-    const size_t b = spc::smem_bytes(g), m = mean_smem_bytes(g);
+    const size_t b = g.spec_eo ? spc::eo_smem_bytes(g) : spc::smem_bytes(g), m = mean_smem_bytes(g);
     return b > m ? b : m;
+}
+
+bool spec_eo_supported(const GroupView& g) {
+    return !g.lin && g.npairs > 1 && g.d2tc && !g.d2fuse && spc::eo_smem_bytes(g) + 1024 <= 227 * 1024;
+}
+
+size_t spec_eo_mat_floats(int ny) { return spc::eo_mat(ny); }
+
+// The parity blocks of a matrix A (Ny x Ny, row-major), R(j) = Ny-1-j, NO =
+// Ny/2, the centre c = NO when Ny is odd.  Centro-symmetric A (A[R i][R j] =
+// A[i][j]): even block Ae[i][k] = A[i][k] + A[i][R k] (k < NO), 2 A[i][c]
+// (k = c), with the centre row A[c][k], A[c][c]; odd block Ao[i][k] = A[i][k] -
+// A[i][R k].  Anti-centro-symmetric A (A[R i][R j] = -A[i][j], D1): even rows
+// from the odd part, Aeo[i][k] = A[i][k] - A[i][R k] (centre row A[c][k]); odd
+// rows from the even part, Aoe[i][k] = A[i][k] + A[i][R k], 2 A[i][c] (k = c).
+// Each block transposed [k][row], rows padded to RP2: the even output rows'
+// block first (KE inputs), then the odd output rows' block.
+void spec_eo_image(const double* A, int ny, bool anti, float* out) {
+    const int NE = spc::eo_ne(ny), NO = ny / 2, RP2 = spc::eo_rp(ny);
+    const size_t mat = spc::eo_mat(ny);
+    for (size_t i = 0; i < mat; ++i) out[i] = 0.f;
+    auto a = [&](int i, int j) { return A[(size_t)i * ny + j]; };
+    const int KE = anti ? NO : NE, KO = anti ? NE : NO;
+    float* be = out;
+    float* bo = out + (size_t)KE * RP2;
+    for (int i = 0; i < NE; ++i)
+        for (int k = 0; k < KE; ++k) {
+            double v;
+            if (i < NO) v = (!anti && k == NO) ? 2.0 * a(i, NO) : (anti ? a(i, k) - a(i, ny - 1 - k) : a(i, k) + a(i, ny - 1 - k));
+            else v = a(NO, k);                    // the centre row (odd Ny)
+            be[(size_t)k * RP2 + i] = (float)v;
+        }
+    for (int i = 0; i < NO; ++i)
+        for (int k = 0; k < KO; ++k) {
+            double v;
+            if (anti) v = (k == NO) ? 2.0 * a(i, NO) : a(i, k) + a(i, ny - 1 - k);
+            else v = a(i, k) - a(i, ny - 1 - k);
+            bo[(size_t)k * RP2 + i] = (float)v;
+        }
 }
 
 // the shapes with their own instantiation: (Ny, members per chunk)
@@ -786,6 +1321,21 @@ size_t spec_smem_bytes(const GroupView& g) {
 void launch_spec(const GroupView& g, int s, cudaStream_t st) {
     const int ctas = mean_row_ctas(g) + (g.npairs - 1) * spc::chunks(g);
     const size_t sm = spec_smem_bytes(g);
+    if (g.spec_eo) {
+        const int ec = spc::chunk_members(g);
+        const bool three = g.spec_minb == 3;
+#define DNS_CASE(a, b)                                                                       \
+        if (g.ny == a && ec == b) {                                                          \
+            if (three) spc::k_spec_eo<a, b, 3><<<ctas, spc::THREADS, sm, st>>>(g, s);        \
+            else spc::k_spec_eo<a, b, 2><<<ctas, spc::THREADS, sm, st>>>(g, s);              \
+            return;                                                                          \
+        }
+        DNS_SPEC_SHAPES(DNS_CASE)
+#undef DNS_CASE
+        if (three) spc::k_spec_eo<0, 0, 3><<<ctas, spc::THREADS, sm, st>>>(g, s);
+        else spc::k_spec_eo<0, 0, 2><<<ctas, spc::THREADS, sm, st>>>(g, s);
+        return;
+    }
     if (g.d2fuse) {
         spc::k_spec<true, 0, 0><<<ctas, spc::THREADS, sm, st>>>(g, s);
         return;
@@ -804,9 +1354,14 @@ void launch_spec(const GroupView& g, int s, cudaStream_t st) {
 void set_attributes_spec() {
     allow_max_dynamic_smem(spc::k_spec<false, 0, 0>);
     allow_max_dynamic_smem(spc::k_spec<true, 0, 0>);
-#define DNS_CASE(a, b) allow_max_dynamic_smem(spc::k_spec<false, a, b>);
+#define DNS_CASE(a, b)                                  \
+    allow_max_dynamic_smem(spc::k_spec<false, a, b>);   \
+    allow_max_dynamic_smem(spc::k_spec_eo<a, b, 2>);    \
+    allow_max_dynamic_smem(spc::k_spec_eo<a, b, 3>);
     DNS_SPEC_SHAPES(DNS_CASE)
 #undef DNS_CASE
+    allow_max_dynamic_smem(spc::k_spec_eo<0, 0, 2>);
+    allow_max_dynamic_smem(spc::k_spec_eo<0, 0, 3>);
 }
 
 }  // namespace dnsk
