@@ -240,15 +240,16 @@ def kernel_work(cls, g, precision):
         apply = 2 * npairs * 2 * 2 * ny * ny * 4 * E * (5.0 / 6.0)
         work = S * 2 * 2 * ny * (4 if spec_computes_d2v(g) else 3) + apply
         # in parity blocks every product is two half-size blocks: half the flops
-        return "alu", work / 2 if g.get("_stage") == "fused_eo" else work, "flop"
+        return "alu", work / 2 if g.get("_stage") in ("fused_eo", "fused_eo_ff") else work, "flop"
     return "alu", E * 4.0 * (g["my"]) ** 2, "flop"
 
 
 def spec_computes_d2v(g):
     """The fused stage writes D2 v itself: with the digit product inside it
-    (per-wavenumber stage "fused_d2v") or, above Ny = 64, in float-float; else
+    (per-wavenumber stage "fused_d2v"), in float-float (stage "fused_eo_ff", and
+    above Ny = 64); else
     the separate tensor-core D2 v kernel does."""
-    return g.get("_stage") == "fused_d2v" or g["my"] - 2 > 64
+    return g.get("_stage") in ("fused_d2v", "fused_eo_ff") or g["my"] - 2 > 64
 
 
 def member_blocks(g):
@@ -287,7 +288,7 @@ def kernel_bytes(cls, g, precision):
         npairs = nkx * (nkz // 2 + 1) - 1              # the mean mode's pair has no CTA
         # in parity blocks (per-wavenumber stage "fused_eo") a matrix is its even
         # and odd halves, ny x 2 ceil(ceil(ny / 2) / 2) floats
-        mat = ny * 2 * (((ny + 1) // 2 + 1) // 2) if g.get("_stage") == "fused_eo" else ny * rp
+        mat = ny * 2 * (((ny + 1) // 2 + 1) // 2) if g.get("_stage") in ("fused_eo", "fused_eo_ff") else ny * rp
         ops = member_blocks(g) * npairs * ((4 + 4 + 2) / 3.0) * mat * 4
         state = 2 * S * (16 * (2.0 / 3.0) + 16 + 8 * (2.0 / 3.0))
         acc = 2 * 8 * S * (4.0 / 3.0)
@@ -849,7 +850,7 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparator run")
     ap.add_argument("--plane", choices=["default", "cta", "cluster", "lines"], default="default",
                     help="plane-stage kernel (default: autotuned among those the grid supports)")
-    ap.add_argument("--helm", choices=["default", "simt", "tc", "persist", "fused", "fused_d2v", "fused_eo"], default="default",
+    ap.add_argument("--helm", choices=["default", "simt", "tc", "persist", "fused", "fused_d2v", "fused_eo", "fused_eo_ff"], default="default",
                     help="per-wavenumber stage of the mixed path (default: the fused stage where the group "
                          "supports it, else the autotuned implicit apply)")
     ap.add_argument("--ygemm", choices=["default", "simt", "tc"], default="default",

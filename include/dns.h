@@ -150,7 +150,7 @@ typedef struct {
                                       variant the group's size lacks is ignored */
     int helm;                      /* mixed path per-wavenumber stage: 0 autotuned at
                                       dns_bind_workspace (DNS groups: 1 and 2, each timed with the
-                                      y-derivatives and the forcing, against 4, 5 and 6; linear
+                                      y-derivatives and the forcing, against 4 to 7; linear
                                       groups: 1 against 2),
                                       1 register-tiled FP32 implicit apply (one CTA per
                                       wavenumber pair and field), 2 tcgen05 tensor cores with
@@ -171,7 +171,9 @@ typedef struct {
                                       symmetric M - I and P, anti-centro-symmetric D1 on the
                                       symmetric grid) applied as its even and odd halves, half
                                       the operator bytes and multiply-adds (groups whose D2 v
-                                      comes from the tensor-core kernel; others run 4) */
+                                      comes from the tensor-core kernel; others run 4), 7 the
+                                      same with D2 v summed inside it in float-float (D2 in
+                                      parity blocks; every size the fused stage takes) */
 } dns_config;
 
 /* One-point statistics of one member (paper Sec. 4), computed from the current
@@ -309,8 +311,8 @@ const char* dns_last_error(const dns_handle* h);
  * plane 1 one CTA per plane / 2 a thread-block cluster per plane / 3 line-owned
  * single CTA per plane; helm 1 register-tiled FP32 / 2 tcgen05 implicit apply /
  * 3 persistent register-tiled FP32 / 4 the fused per-wavenumber stage / 5 the
- * fused stage with D2 v inside it / 6 the fused stage in parity blocks.  Any
- * output may be NULL. */
+ * fused stage with D2 v inside it / 6 the fused stage in parity blocks / 7 the
+ * same with its float-float D2 v.  Any output may be NULL. */
 int dns_kernel_choice(const dns_handle* h, int group, int* ygemm, int* plane, int* helm);
 
 /* Number of kernel launches enqueued by the last dns_step call (all steps). */

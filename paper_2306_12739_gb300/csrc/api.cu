@@ -40,7 +40,7 @@ struct HostGroup {
     dnsb::GridOps grid;
     dnsb::CnOps ops[2];
     std::vector<double> kxt, kzt, k2t, k2inv, twx, twz, opsdev[2], mopsdev[2], D1i, D2i;
-    std::vector<float> kxtf, kztf, k2invf, twxf, twzf, opsf[2], opsfT[2], D1T, D2T, D2Tl, opsEO[2], D1EO;
+    std::vector<float> kxtf, kztf, k2invf, twxf, twzf, opsf[2], opsfT[2], D1T, D2T, D2Tl, opsEO[2], D1EO, D2EO, D2lEO;
     std::vector<uint16_t> Atc, Htc[2], D2oz;
     std::vector<int> D2ozexp;
     std::vector<double> fstruct, flam;   // stochastic forcing: structures [NKZ][2][n][Ny], decay rates
@@ -126,14 +126,16 @@ bool d2fuse_ok(GroupView v) {
     v.d2fuse = 1;
     return dnsk::spec_d2fuse_supported(v);
 }
-// the fused stage can run in parity blocks (helm request 6)
-bool eo_ok(GroupView v) {
+// the fused stage can run in parity blocks, with D2 v from the digit kernel
+// (helm request 6) or summed inside in float-float (ff, helm request 7)
+bool eo_ok(GroupView v, bool ff) {
     v.spec_eo = 1;
+    v.spec_eoff = ff ? 1 : 0;
     v.d2fuse = 0;
     return dnsk::spec_eo_supported(v);
 }
 // ... and its operator images are wanted (a request for it, or the autotuner)
-bool eo_candidate(const GroupView& v) { return (v.helm == 4 || v.helm == 0) && v.d2tc && eo_ok(v); }
+bool eo_candidate(const GroupView& v) { return (v.helm == 4 || v.helm == 0) && eo_ok(v, true); }
 
 // Largest My at which DNS groups may take the FP32-accumulated tensor-core
 // y-derivatives (see choose_variants)
@@ -158,6 +160,10 @@ void build_eo_images(HostGroup& G) {
     }
     G.D1EO.assign(mat, 0.f);
     dnsk::spec_eo_image(G.D1i.data(), v.ny, true, G.D1EO.data());
+    G.D2EO.assign(mat, 0.f);
+    G.D2lEO.assign(mat, 0.f);
+    dnsk::spec_eo_image(G.D2i.data(), v.ny, false, G.D2EO.data());
+    dnsk::spec_eo_image(G.D2i.data(), v.ny, false, G.D2lEO.data(), true);
 }
 
 size_t layout_group(dns_handle* h, HostGroup& G, size_t cur) {
@@ -176,7 +182,11 @@ size_t layout_group(dns_handle* h, HostGroup& G, size_t cur) {
     add((void**)&v.D1T, sizeof(float) * (size_t)v.ny * v.rp);
     add((void**)&v.D2T, sizeof(float) * (size_t)v.ny * v.rp);
     add((void**)&v.D2Tl, sizeof(float) * (size_t)v.ny * v.rp);
-    if (precision_mixed(h) && eo_candidate(v)) add((void**)&v.D1EO, sizeof(float) * dnsk::spec_eo_mat_floats(v.ny));
+    if (precision_mixed(h) && eo_candidate(v)) {
+        add((void**)&v.D1EO, sizeof(float) * dnsk::spec_eo_mat_floats(v.ny));
+        add((void**)&v.D2EO, sizeof(float) * dnsk::spec_eo_mat_floats(v.ny));
+        add((void**)&v.D2lEO, sizeof(float) * dnsk::spec_eo_mat_floats(v.ny));
+    }
     add((void**)&v.status, 256);
     if (v.ygemm != 1) add((void**)&v.Atc, 3 * 128 * (size_t)v.kp * sizeof(uint16_t));
     if (v.d2tc) {
@@ -337,7 +347,7 @@ void enqueue_group(dns_handle* h, HostGroup& G, cudaStream_t st, Timer* tm) {
             dnsk::launch_spec(g, s, st);
             mark(DNS_K_SPEC);
             h->launches += 2;
-            if (g.d2tc && !g.d2fuse) {
+            if (g.d2tc && !g.d2fuse && !g.spec_eoff) {
                 dnsk::launch_d2v_tc(g, s == 2 ? g.v_t : g.v_s, st);
                 mark(DNS_K_D2V);
                 h->launches += 1;
@@ -492,7 +502,7 @@ int cache_lookup(const char* path, const std::string& key) {
         std::string ln(line);
         if (ln.compare(0, key.size(), key) == 0 && ln.size() > key.size() + 1) {
             int c = atoi(ln.c_str() + key.size() + 1);
-            if (c >= 1 && c <= 6) found = c;
+            if (c >= 1 && c <= 7) found = c;
         }
     }
     fclose(f);
@@ -535,7 +545,7 @@ int choose_variants(dns_handle* h, const dns_config* cfg, GroupView& v, int gi) 
     // forcing) and 4
     v.helm = 1;
     if (precision_mixed(h)) {
-        if (cfg->helm >= 4 && cfg->helm <= 6) v.helm = dnsk::spec_supported(v) ? 4 : 0;
+        if (cfg->helm >= 4 && cfg->helm <= 7) v.helm = dnsk::spec_supported(v) ? 4 : 0;
         else if (cfg->helm == 0) v.helm = 0;
         else if (cfg->helm == 2 && dnsk::helm_tc_supported(v)) v.helm = 2;
         else if (cfg->helm == 3) v.helm = 3;
@@ -546,7 +556,12 @@ int choose_variants(dns_handle* h, const dns_config* cfg, GroupView& v, int gi) 
     // and, on request (helm 5) or by the autotuner, that digit product inside the fused launch
     v.d2fuse = (cfg->helm == 5 && v.helm == 4 && d2fuse_ok(v)) ? 1 : 0;
     // or the fused stage in parity blocks (helm 6)
-    v.spec_eo = (cfg->helm == 6 && v.helm == 4 && eo_ok(v)) ? 1 : 0;
+    v.spec_eo = 0;
+    v.spec_eoff = 0;
+    if (v.helm == 4 && ((cfg->helm == 6 && v.d2tc && eo_ok(v, false)) || (cfg->helm == 7 && eo_ok(v, true)))) {
+        v.spec_eo = 1;
+        v.spec_eoff = cfg->helm == 7 ? 1 : 0;
+    }
     v.spec_minb = 2;
     // plane-stage kernel: single CTA per plane where it fits, a thread-block
     // cluster (distributed shared memory) where it does not; where both exist
@@ -896,6 +911,8 @@ int dns_bind_workspace(dns_handle* h, void* dev_ptr, size_t bytes) {
             {v.opsEO[0], G.opsEO[0].data(), G.opsEO[0].size() * 4},
             {v.opsEO[1], G.opsEO[1].data(), G.opsEO[1].size() * 4},
             {v.D1EO, G.D1EO.data(), G.D1EO.size() * 4},
+            {v.D2EO, G.D2EO.data(), G.D2EO.size() * 4},
+            {v.D2lEO, G.D2lEO.data(), G.D2lEO.size() * 4},
             {v.D2ozexp, G.D2ozexp.data(), G.D2ozexp.size() * 4},
             {v.mops[0], G.mopsdev[0].data(), G.mopsdev[0].size() * 8},
             {v.mops[1], G.mopsdev[1].data(), G.mopsdev[1].size() * 8},
@@ -997,29 +1014,34 @@ int dns_bind_workspace(dns_handle* h, void* dev_ptr, size_t bytes) {
         const std::string key = tune_helm_key(v0);
         int choice = decided.count(key) ? decided[key] : cache_lookup(h->cfg.autotune_cache, key);
         // 5: the fused stage with its D2 v inside (every block of the group must allow it)
-        // 6: the fused stage in parity blocks (its images were laid out for every block)
-        bool fuse_ok = dnsk::spec_supported(v0), par_ok = dnsk::spec_supported(v0);
+        // 6, 7: the fused stage in parity blocks, D2 v by the digit kernel or
+        // inside in float-float (its images were laid out for every block)
+        bool fuse_ok = dnsk::spec_supported(v0), par_ok = dnsk::spec_supported(v0), ff_ok = par_ok;
         for (const auto& P : h->parts[gi]) {
             const GroupView& vb = h->groups[P.ig].v;
             fuse_ok = fuse_ok && d2fuse_ok(vb);
-            par_ok = par_ok && eo_candidate(vb) && vb.opsEO[0] != nullptr && vb.D1EO != nullptr;
+            const bool img = eo_candidate(vb) && vb.opsEO[0] != nullptr && vb.D1EO != nullptr && vb.D2EO != nullptr;
+            par_ok = par_ok && img && vb.d2tc && eo_ok(vb, false);
+            ff_ok = ff_ok && img;
         }
         if ((choice == 2 && !dnsk::helm_tc_supported(v0)) || (choice == 4 && !dnsk::spec_supported(v0)) ||
-            (choice == 5 && !fuse_ok) || (choice == 6 && !par_ok) || choice == 3)
+            (choice == 5 && !fuse_ok) || (choice == 6 && !par_ok) || (choice == 7 && !ff_ok) || choice == 3)
             choice = 0;
         if (!choice) {
-            float best[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            float best[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             cudaEvent_t e0, e1;
             cudaEventCreate(&e0);
             cudaEventCreate(&e1);
-            for (int cand = 1; cand <= 6 && !rc; ++cand) {
+            for (int cand = 1; cand <= 7 && !rc; ++cand) {
                 if (cand == 3 || (cand == 2 && !dnsk::helm_tc_supported(v0)) ||
-                    (cand == 4 && !dnsk::spec_supported(v0)) || (cand == 5 && !fuse_ok) || (cand == 6 && !par_ok))
+                    (cand == 4 && !dnsk::spec_supported(v0)) || (cand == 5 && !fuse_ok) || (cand == 6 && !par_ok) ||
+                    (cand == 7 && !ff_ok))
                     continue;
                 for (const auto& P : h->parts[gi]) {
                     h->groups[P.ig].v.helm = cand >= 4 ? 4 : cand;
                     h->groups[P.ig].v.d2fuse = cand == 5 ? 1 : 0;
-                    h->groups[P.ig].v.spec_eo = cand == 6 ? 1 : 0;
+                    h->groups[P.ig].v.spec_eo = cand >= 6 ? 1 : 0;
+                    h->groups[P.ig].v.spec_eoff = cand == 7 ? 1 : 0;
                 }
                 for (int w = 0; w < 2; ++w) enqueue_step(h);
                 cudaEventRecord(e0, st);
@@ -1035,16 +1057,17 @@ int dns_bind_workspace(dns_handle* h, void* dev_ptr, size_t bytes) {
             if (rc) return rc;
             if ((rc = device_status(h))) return rc;
             choice = 0;
-            for (int cand = 1; cand <= 6; ++cand)
+            for (int cand = 1; cand <= 7; ++cand)
                 if (best[cand] > 0.f && (choice == 0 || best[cand] < best[choice])) choice = cand;
-            cache_store(h->cfg.autotune_cache, key, choice, best, 6);
+            cache_store(h->cfg.autotune_cache, key, choice, best, 7);
         }
         decided[key] = choice;
         for (const auto& P : h->parts[gi]) {
             GroupView& v = h->groups[P.ig].v;
             v.helm = choice >= 4 ? 4 : choice;
             v.d2fuse = choice == 5 ? 1 : 0;
-            v.spec_eo = choice == 6 ? 1 : 0;
+            v.spec_eo = choice >= 6 ? 1 : 0;
+            v.spec_eoff = choice == 7 ? 1 : 0;
             if (v.helm == 4) v.ygemm = 1;
         }
     }
@@ -2102,7 +2125,7 @@ int dns_kernel_choice(const dns_handle* h, int group, int* ygemm, int* plane, in
     const GroupView& v = h->groups[h->parts[group][0].ig].v;
     if (ygemm) *ygemm = v.ygemm;
     if (plane) *plane = v.plane;
-    if (helm) *helm = v.helm != 4 ? v.helm : v.d2fuse ? 5 : v.spec_eo ? 6 : 4;
+    if (helm) *helm = v.helm != 4 ? v.helm : v.d2fuse ? 5 : v.spec_eoff ? 7 : v.spec_eo ? 6 : 4;
     return DNS_OK;
 }
 

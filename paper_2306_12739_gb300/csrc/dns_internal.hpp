@@ -61,9 +61,12 @@ struct GroupView {
     int d2fuse;           // fused stage: 1 = that digit product inside the fused launch (no D2 v launch)
     int spec_eo;          // fused stage: 1 = in parity blocks (even / odd parts in y; with d2tc)
     int spec_minb;        // fused stage in parity blocks: CTAs per SM of its register budget (2 or 3)
+    int spec_eoff;        // fused stage in parity blocks: 1 = D2 v summed inside in float-float
     const float* opsEO[2];  // mixed path, per h index: [npairs][4] matrices (M - I, P of v and eta) in
                             // parity blocks, each eo_mat(Ny) floats (see k_spec.cu)
     const float* D1EO;      // D1 in parity blocks
+    const float* D2EO;      // D2 in parity blocks and its residual D2 - (double) D2EO
+    const float* D2lEO;
     int spec_ec;          // fused stage: members per CTA (0 = up to 8), set by the autotuner
     int yd_cap;           // register-tiled y-derivatives: first column-tile cap (0 = 64, or 32 above
                           //    Ny = 96), halved while the grid is short of 3 CTAs per SM; autotuned
@@ -174,7 +177,7 @@ bool spec_eo_supported(const GroupView& g);       // the fused stage in parity b
 size_t spec_eo_mat_floats(int ny);                // floats of one matrix in parity blocks
 // one Ny x Ny row-major matrix (centro-symmetric, or anti-centro-symmetric when
 // anti) as its two parity blocks, transposed and row-padded (out: spec_eo_mat_floats)
-void spec_eo_image(const double* A, int ny, bool anti, float* out);
+void spec_eo_image(const double* A, int ny, bool anti, float* out, bool residual = false);
 size_t spec_smem_bytes(const GroupView& g);
 void launch_spec(const GroupView& g, int s, cudaStream_t st);
 void set_attributes_spec();

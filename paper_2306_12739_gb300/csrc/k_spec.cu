@@ -777,8 +777,11 @@ __global__ void __launch_bounds__(THREADS, 2) k_spec(GroupView g, int s) {
 // in shared memory hold the even part in rows 0 .. NE-1 and the odd part in
 // rows NE .. Ny-1; the state, forcing accumulators and outputs stay in the
 // natural order in global memory, and every task converts the natural rows of
-// its pair-rows (i and Ny-1-i) on the way in and out.  Used where D2 v comes
-// from the tensor-core digit kernel.
+// its pair-rows (i and Ny-1-i) on the way in and out.  D2 v of the new state
+// comes from the tensor-core digit kernel after the launch or (D2FF) is summed
+// here in float-float, D2 and its residual in parity blocks over the eta
+// operators once phase 2 is done (half the products of the natural-order
+// float-float sum).
 // ============================================================================
 
 __host__ __device__ inline int eo_ne(int ny) { return (ny + 1) / 2; }
@@ -787,6 +790,32 @@ __host__ __device__ inline int eo_rp(int ny) { return 2 * ((eo_ne(ny) + 1) / 2);
 __host__ __device__ inline size_t eo_mat(int ny) { return ((size_t)ny * eo_rp(ny) + 3) / 4 * 4; }
 __host__ __device__ inline size_t eo_smem_bytes(const GroupView& g) {
     return (5 * eo_mat(g.ny) + 7 * vec_floats(g)) * sizeof(float) + 32;
+}
+
+// float-float product of one pair-row p (phase 4 with D2FF): centro-symmetric D2
+// (hi part B, residual BL) in parity blocks with the even and odd parts of v
+// (hi XH, lo XL); sums (hi, lo) per output row and re/im
+__device__ __forceinline__ void eo1ff(const float* B, const float* BL, int NE, int NO, int RP2, const float* XH,
+                                      const float* XL, int VS, int p, int c2, float (&eh)[2], float (&el)[2],
+                                      float (&oh)[2], float (&ol)[2]) {
+    eh[0] = eh[1] = el[0] = el[1] = oh[0] = oh[1] = ol[0] = ol[1] = 0.f;
+#pragma unroll 2
+    for (int k = 0; k < NE; ++k) {
+        const float b = B[k * RP2 + p], bl = BL[k * RP2 + p];
+        const float2 x = *(const float2*)&XH[k * VS + c2];
+        const float2 xl = *(const float2*)&XL[k * VS + c2];
+        ff_add_prod2(eh[0], el[0], b, x.x, bl, xl.x);
+        ff_add_prod2(eh[1], el[1], b, x.y, bl, xl.y);
+    }
+    const size_t ob = (size_t)NE * RP2;
+#pragma unroll 2
+    for (int k = 0; k < NO; ++k) {
+        const float b = B[ob + k * RP2 + p], bl = BL[ob + k * RP2 + p];
+        const float2 x = *(const float2*)&XH[(NE + k) * VS + c2];
+        const float2 xl = *(const float2*)&XL[(NE + k) * VS + c2];
+        ff_add_prod2(oh[0], ol[0], b, x.x, bl, xl.x);
+        ff_add_prod2(oh[1], ol[1], b, x.y, bl, xl.y);
+    }
 }
 
 // Two pair-rows p0, p0 + 1 x one complex column (c2 its real column) of a
@@ -882,7 +911,7 @@ __device__ __forceinline__ EoRows eo_rows(int p, int Ny) {
 
 // MINB: CTAs per SM the registers are budgeted for (2, or 3 at 80 registers;
 // shared memory allows 3): chosen by timing whole steps
-template <int NYC, int ECC, int MINB>
+template <int NYC, int ECC, int MINB, bool D2FF>
 __global__ void __launch_bounds__(THREADS, MINB) k_spec_eo(GroupView g, int s) {
     extern __shared__ __align__(16) unsigned char sm[];
     const int nrow = mean_row_ctas(g);
@@ -919,13 +948,14 @@ __global__ void __launch_bounds__(THREADS, MINB) k_spec_eo(GroupView g, int s) {
     float* FT = XE + VF;                          // F~
     float* EN = FT + VF;                          // eta+
     unsigned long long* bar = (unsigned long long*)(EN + VF);
-    const unsigned bar_a = su32(bar);
+    const unsigned bar_a = su32(bar), bar_d = su32(bar + 1);
     const int tid = threadIdx.x;
     const bool needM = (s != 2);
     const int hidx = (s == 0) ? 0 : 1;
 
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_a) : "memory");
+        if (D2FF) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_d) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
@@ -1156,6 +1186,16 @@ __global__ void __launch_bounds__(THREADS, MINB) k_spec_eo(GroupView g, int s) {
         }
     }
     __syncthreads();
+    // D2FF: the eta operators are no longer read: D2 and its residual in parity
+    // blocks go there (the generic-proxy reads of phase 2 ordered before the
+    // async-proxy writes)
+    if (D2FF && tid == 0) {
+        const unsigned mb = (unsigned)(MEO * sizeof(float));
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_d), "r"(2 * mb) : "memory");
+        bulk(OPS + 2 * MEO, g.D2EO, mb, bar_d);
+        bulk(OPS + 3 * MEO, g.D2lEO, mb, bar_d);
+    }
 
     // ---- phase 3: v+ (P_v F~, threads 0..127) | D eta (threads 128..255)
     if (tid < HALF) {
@@ -1207,10 +1247,18 @@ __global__ void __launch_bounds__(THREADS, MINB) k_spec_eo(GroupView g, int s) {
                     O[oh] = xn[k2];
                     P5[((size_t)y * E + e) * NM + q] = make_float2(d2f(xn[k2].x), d2f(xn[k2].y));
                 }
-                // v+ in parity parts (over phi) for D v
-                *(float2*)&PH[p * VS + 2 * j] = make_float2(d2f(xn[0].x + xn[1].x), d2f(xn[0].y + xn[1].y));
-                if (R.pair)
-                    *(float2*)&PH[(NE + p) * VS + 2 * j] = make_float2(d2f(xn[0].x - xn[1].x), d2f(xn[0].y - xn[1].y));
+                // v+ in parity parts (over phi) for D v; with D2FF also the
+                // residuals (over the (M_v - I) v_t slots this thread has read)
+                const double2 ve = make_double2(xn[0].x + xn[1].x, xn[0].y + xn[1].y);
+                const double2 vo = make_double2(xn[0].x - xn[1].x, xn[0].y - xn[1].y);
+                const float2 he = make_float2(d2f(ve.x), d2f(ve.y)), ho = make_float2(d2f(vo.x), d2f(vo.y));
+                *(float2*)&PH[p * VS + 2 * j] = he;
+                if (R.pair) *(float2*)&PH[(NE + p) * VS + 2 * j] = ho;
+                if (D2FF) {
+                    *(float2*)&KV[p * VS + 2 * j] = make_float2(d2f(ve.x - f2d(he.x)), d2f(ve.y - f2d(he.y)));
+                    if (R.pair)
+                        *(float2*)&KV[(NE + p) * VS + 2 * j] = make_float2(d2f(vo.x - f2d(ho.x)), d2f(vo.y - f2d(ho.y)));
+                }
             }
         }
     } else {
@@ -1238,13 +1286,26 @@ __global__ void __launch_bounds__(THREADS, MINB) k_spec_eo(GroupView g, int s) {
     }
     __syncthreads();
 
-    // ---- phase 4: D v on every thread, one pair-row x one complex column each
+    if (D2FF) {
+        if (!__syncthreads_and(waitp(bar_d, 0))) {
+            if (tid == 0) {
+                atomicExch(g.status, 1);
+                waitp(bar_d, 0);
+            }
+            return;
+        }
+    }
+
+    // ---- phase 4: D v (and with D2FF the float-float D2 v) on every thread,
+    // one pair-row x one complex column each
     for (int t = tid; t < NE * c.C; t += THREADS) {
         const int p = div_cols<ECC>(t, c.C), j = t - p * c.C;
         const int q = col_q(c, j), e = col_e(c, j);
         const EoRows R = eo_rows(p, Ny);
         float de[2], dq[2];
         eo1(D1S, NO, NE, RP2, PH + NE * VS, PH, VS, p, 2 * j, de, dq);
+        float eh[2], el[2], oh[2], ol[2];
+        if (D2FF) eo1ff(OPS + 2 * MEO, OPS + 3 * MEO, NE, NO, RP2, PH, KV, VS, p, 2 * j, eh, el, oh, ol);
 #pragma unroll
         for (int k2 = 0; k2 < 2; ++k2) {
             const int y = k2 ? R.y1 : R.y0;
@@ -1252,7 +1313,13 @@ __global__ void __launch_bounds__(THREADS, MINB) k_spec_eo(GroupView g, int s) {
             const float sg = k2 ? -1.f : 1.f;
             const float2 d = R.pair ? make_float2(0.5f * (de[0] + sg * dq[0]), 0.5f * (de[1] + sg * dq[1]))
                                     : make_float2(de[0], de[1]);
-            P5[fs5 + ((size_t)y * E + e) * NM + q] = d;
+            const size_t o = ((size_t)y * E + e) * NM + q;
+            P5[fs5 + o] = d;
+            if (D2FF) {
+                const float e0 = __fadd_rn(eh[0], el[0]), e1 = __fadd_rn(eh[1], el[1]);
+                const float o0 = __fadd_rn(oh[0], ol[0]), o1 = __fadd_rn(oh[1], ol[1]);
+                P5[2 * fs5 + o] = R.pair ? make_float2(0.5f * (e0 + sg * o0), 0.5f * (e1 + sg * o1)) : make_float2(e0, e1);
+            }
         }
     }
 }
@@ -1276,8 +1343,9 @@ size_t spec_smem_bytes(const GroupView& g) {
     return b > m ? b : m;
 }
 
+// (D2 v from the digit kernel after the launch, or with spec_eoff summed inside)
 bool spec_eo_supported(const GroupView& g) {
-    return !g.lin && g.npairs > 1 && g.d2tc && !g.d2fuse && spc::eo_smem_bytes(g) + 1024 <= 227 * 1024;
+    return !g.lin && g.npairs > 1 && (g.d2tc || g.spec_eoff) && !g.d2fuse && spc::eo_smem_bytes(g) + 1024 <= 227 * 1024;
 }
 
 size_t spec_eo_mat_floats(int ny) { return spc::eo_mat(ny); }
@@ -1291,7 +1359,7 @@ size_t spec_eo_mat_floats(int ny) { return spc::eo_mat(ny); }
 // rows from the even part, Aoe[i][k] = A[i][k] + A[i][R k], 2 A[i][c] (k = c).
 // Each block transposed [k][row], rows padded to RP2: the even output rows'
 // block first (KE inputs), then the odd output rows' block.
-void spec_eo_image(const double* A, int ny, bool anti, float* out) {
+void spec_eo_image(const double* A, int ny, bool anti, float* out, bool residual) {
     const int NE = spc::eo_ne(ny), NO = ny / 2, RP2 = spc::eo_rp(ny);
     const size_t mat = spc::eo_mat(ny);
     for (size_t i = 0; i < mat; ++i) out[i] = 0.f;
@@ -1304,14 +1372,14 @@ void spec_eo_image(const double* A, int ny, bool anti, float* out) {
             double v;
             if (i < NO) v = (!anti && k == NO) ? 2.0 * a(i, NO) : (anti ? a(i, k) - a(i, ny - 1 - k) : a(i, k) + a(i, ny - 1 - k));
             else v = a(NO, k);                    // the centre row (odd Ny)
-            be[(size_t)k * RP2 + i] = (float)v;
+            be[(size_t)k * RP2 + i] = residual ? (float)(v - (double)(float)v) : (float)v;
         }
     for (int i = 0; i < NO; ++i)
         for (int k = 0; k < KO; ++k) {
             double v;
             if (anti) v = (k == NO) ? 2.0 * a(i, NO) : a(i, k) + a(i, ny - 1 - k);
             else v = a(i, k) - a(i, ny - 1 - k);
-            bo[(size_t)k * RP2 + i] = (float)v;
+            bo[(size_t)k * RP2 + i] = residual ? (float)(v - (double)(float)v) : (float)v;
         }
 }
 
@@ -1323,17 +1391,21 @@ void launch_spec(const GroupView& g, int s, cudaStream_t st) {
     const size_t sm = spec_smem_bytes(g);
     if (g.spec_eo) {
         const int ec = spc::chunk_members(g);
-        const bool three = g.spec_minb == 3;
+        const bool three = g.spec_minb == 3, ff = g.spec_eoff != 0;
+#define DNS_GO(a, b, m)                                                                      \
+        {                                                                                    \
+            if (ff) spc::k_spec_eo<a, b, m, true><<<ctas, spc::THREADS, sm, st>>>(g, s);     \
+            else spc::k_spec_eo<a, b, m, false><<<ctas, spc::THREADS, sm, st>>>(g, s);       \
+        }
 #define DNS_CASE(a, b)                                                                       \
         if (g.ny == a && ec == b) {                                                          \
-            if (three) spc::k_spec_eo<a, b, 3><<<ctas, spc::THREADS, sm, st>>>(g, s);        \
-            else spc::k_spec_eo<a, b, 2><<<ctas, spc::THREADS, sm, st>>>(g, s);              \
+            if (three) DNS_GO(a, b, 3) else DNS_GO(a, b, 2)                                  \
             return;                                                                          \
         }
         DNS_SPEC_SHAPES(DNS_CASE)
 #undef DNS_CASE
-        if (three) spc::k_spec_eo<0, 0, 3><<<ctas, spc::THREADS, sm, st>>>(g, s);
-        else spc::k_spec_eo<0, 0, 2><<<ctas, spc::THREADS, sm, st>>>(g, s);
+        if (three) DNS_GO(0, 0, 3) else DNS_GO(0, 0, 2)
+#undef DNS_GO
         return;
     }
     if (g.d2fuse) {
@@ -1354,14 +1426,16 @@ void launch_spec(const GroupView& g, int s, cudaStream_t st) {
 void set_attributes_spec() {
     allow_max_dynamic_smem(spc::k_spec<false, 0, 0>);
     allow_max_dynamic_smem(spc::k_spec<true, 0, 0>);
-#define DNS_CASE(a, b)                                  \
-    allow_max_dynamic_smem(spc::k_spec<false, a, b>);   \
-    allow_max_dynamic_smem(spc::k_spec_eo<a, b, 2>);    \
-    allow_max_dynamic_smem(spc::k_spec_eo<a, b, 3>);
+#define DNS_EO(a, b)                                        \
+    allow_max_dynamic_smem(spc::k_spec_eo<a, b, 2, false>);  \
+    allow_max_dynamic_smem(spc::k_spec_eo<a, b, 3, false>);  \
+    allow_max_dynamic_smem(spc::k_spec_eo<a, b, 2, true>);   \
+    allow_max_dynamic_smem(spc::k_spec_eo<a, b, 3, true>);
+#define DNS_CASE(a, b) allow_max_dynamic_smem(spc::k_spec<false, a, b>); DNS_EO(a, b)
     DNS_SPEC_SHAPES(DNS_CASE)
 #undef DNS_CASE
-    allow_max_dynamic_smem(spc::k_spec_eo<0, 0, 2>);
-    allow_max_dynamic_smem(spc::k_spec_eo<0, 0, 3>);
+    DNS_EO(0, 0)
+#undef DNS_EO
 }
 
 }  // namespace dnsk

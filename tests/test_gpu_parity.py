@@ -370,8 +370,8 @@ def test_autotuner_picks_a_variant_caches_it_and_matches_that_variant(tmp_path):
     plane = dns.dns_kernel_choice(ens.h, 0, "plane")
     helm = dns.dns_kernel_choice(ens.h, 0, "helm")
     assert choice in ("simt", "tc") and plane in ("cta", "lines") and helm in ("simt", "tc", "fused", "fused_d2v",
-                                                                                 "fused_eo")
-    assert helm not in ("fused", "fused_d2v", "fused_eo") or choice == "simt"
+                                                                                 "fused_eo", "fused_eo_ff")
+    assert helm not in ("fused", "fused_d2v", "fused_eo", "fused_eo_ff") or choice == "simt"
     ens.set_state(0, st["v"], st["eta"], st["U"], st["W"])
     ens.step(3)
     got = ens.get_state(0)
@@ -382,8 +382,8 @@ def test_autotuner_picks_a_variant_caches_it_and_matches_that_variant(tmp_path):
     # the tile shapes: the fused stage's members per CTA, the y-derivative tile
     assert all(ln.split()[1:5] == ["32", "33", "32", "4"] for ln in lines)
     want = {"helm", "plane", "ygemm"} | ({"ytile"} if choice == "simt" else set()) | \
-        ({"spec_ec"} if helm in ("fused", "fused_d2v", "fused_eo") else set()) | \
-        ({"spec_cta"} if helm == "fused_eo" else set())
+        ({"spec_ec"} if helm in ("fused", "fused_d2v", "fused_eo", "fused_eo_ff") else set()) | \
+        ({"spec_cta"} if helm in ("fused_eo", "fused_eo_ff") else set())
     assert sorted(keys) == sorted(want)
     ens2 = dns.Ensemble([g], precision="mixed", autotune_cache=cache)   # read back, no new timing
     assert dns.dns_kernel_choice(ens2.h, 0) == choice
@@ -782,6 +782,7 @@ def test_fused_stage_shape_specialisations_are_bitwise_the_generic_kernel():
         assert np.array_equal(a[:2], c), name
 
 
+@pytest.mark.parametrize("stage", ["fused_eo", "fused_eo_ff"])
 @pytest.mark.parametrize("flow,mx,my,mz,E,extra", [
     ("poiseuille", 32, 33, 32, 3, {}),
     ("couette", 48, 49, 48, 5, {}),
@@ -789,19 +790,26 @@ def test_fused_stage_shape_specialisations_are_bitwise_the_generic_kernel():
     ("couette", 64, 65, 64, 4, dict(form="rotational")),
     ("couette", 16, 7, 16, 3, {}),                              # Ny = 5: parity parts of 3 and 2 rows
     ("poiseuille", 32, 34, 16, 2, {}),                          # even Ny: no centre row
+    ("poiseuille", 32, 97, 16, 2, {}),                          # Ny = 95: float-float D2 v only
 ])
-def test_fused_stage_in_parity_blocks_matches_fp64_and_the_natural_order_stage(flow, mx, my, mz, E, extra):
+def test_fused_stage_in_parity_blocks_matches_fp64_and_the_natural_order_stage(stage, flow, mx, my, mz, E, extra):
     """The fused stage in parity blocks (every operator as its even and odd
-    halves) against the FP64 step over 20 steps (1e-6 per field and member,
-    W00 on its own scale at 3e-5) and against the fused stage in the natural
-    order (the same arithmetic regrouped: within the budget)."""
+    halves; D2 v from the digit kernel, or summed inside in float-float)
+    against the FP64 step over 20 steps (1e-6 per field and member, W00 on its
+    own scale at 3e-5) and against the fused stage in the natural order (the
+    same arithmetic regrouped: within the budget).  Above Ny = 64 there is no
+    digit kernel: only the float-float form runs."""
     g = dict(group(flow, mx, my, mz, 2 * np.pi, np.pi, 1650.0 if flow == "poiseuille" else 400.0, 0.005, E), **extra)
     st = _state(g, 91, 5e-2)
-    ens = dns.Ensemble([g], precision="mixed", helm="fused_eo")
-    assert dns.dns_kernel_choice(ens.h, 0, "helm") == "fused_eo"
+    ens = dns.Ensemble([g], precision="mixed", helm=stage)
+    got = dns.dns_kernel_choice(ens.h, 0, "helm")
     ens.close()
+    if stage == "fused_eo" and my - 2 > 64:
+        assert got == "fused"
+        return
+    assert got == stage
     ref = _run(g, st, 20, "fp64")
-    par = _run(g, st, 20, "mixed", use_graph=True, helm="fused_eo")
+    par = _run(g, st, 20, "mixed", use_graph=True, helm=stage)
     nat = _run(g, st, 20, "mixed", use_graph=True, helm="fused")
     err = mixed_errors(par, ref)
     assert np.all(err[:, :3] < 1e-6), err
@@ -809,12 +817,13 @@ def test_fused_stage_in_parity_blocks_matches_fp64_and_the_natural_order_stage(f
     assert np.all(mixed_errors(par, nat)[:, :3] < 1e-6)
 
 
-def test_headline_in_parity_blocks_matches_fp64_over_50_steps():
+@pytest.mark.parametrize("stage", ["fused_eo", "fused_eo_ff"])
+def test_headline_in_parity_blocks_matches_fp64_over_50_steps(stage):
     """The benchmarked configuration (64x65x64, 8 members in two blocks, graph)
     with the fused stage in parity blocks, mixed against FP64 after 50 steps."""
     st = _state(CFG2, 2000, 5e-2, n_max=4, m_max=4)
     ref = _run(CFG2, st, 50, "fp64", use_graph=True)
-    err = mixed_errors(_run(CFG2, st, 50, "mixed", use_graph=True, helm="fused_eo"), ref)
+    err = mixed_errors(_run(CFG2, st, 50, "mixed", use_graph=True, helm=stage), ref)
     assert err.shape[0] == 8
     assert np.all(err[:, :3] < 1e-6), err
     assert np.all(err[:, 3] < 3e-5), err
