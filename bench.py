@@ -674,7 +674,7 @@ def gpu_arm(args, rank, world, dist):
         peak, unit = apk, "TFLOP/s"
         achieved = work / (kt[dom][0] / 1e3) / 1e12
     variant = {"plane": choices[0]["plane"], "yderiv": choices[0]["ygemm"], "helm": choices[0]["helm"],
-               "spec": "fused", "d2v": "tc"}.get(dom, "simt")
+               "spec": choices[0]["helm"], "d2v": "tc"}.get(dom, "simt")
     traffic = (profiled_traffic(dom, variant)
                if (precision == "mixed" and args.workload == "poiseuille64") else None)
     # every class against the HBM roofline of its own algorithmic bytes (the

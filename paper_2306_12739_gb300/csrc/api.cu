@@ -1308,12 +1308,22 @@ static bool aligned_for_kernels(const void* v, const void* e, const void* U, con
 
 // After the pack kernel: a group on the fused stage keeps the y-derivatives of
 // its state at time t in the per-plane arrays (every fused launch writes those
-// of the state it produces), so a newly set state gets them here.
+// of the state it produces), so a newly set state gets them here: in parity
+// blocks as that stage computes them, else from the register-tiled kernel.
 static int new_state_derivatives(dns_handle* h, const GroupView& v, cudaStream_t st) {
     int rc = check(h, cudaGetLastError(), "pack state");
     if (rc || !precision_mixed(h) || v.helm != 4) return rc;
-    dnsk::launch_yderiv_t(v, v.v_t, v.e_t, st);
-    h->launches += 1;
+    if (v.spec_eo) {
+        dnsk::launch_eo_derivs(v, st);
+        h->launches += 1;
+        if (!v.spec_eoff) {
+            dnsk::launch_d2v_tc(v, v.v_t, st);
+            h->launches += 1;
+        }
+    } else {
+        dnsk::launch_yderiv_t(v, v.v_t, v.e_t, st);
+        h->launches += 1;
+    }
     return check(h, cudaGetLastError(), "derivatives of the new state");
 }
 

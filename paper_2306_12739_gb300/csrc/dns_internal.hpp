@@ -175,6 +175,9 @@ bool spec_supported(const GroupView& g);
 bool spec_d2fuse_supported(const GroupView& g);   // with g.d2fuse set: the fused D2 v can run
 bool spec_eo_supported(const GroupView& g);       // the fused stage in parity blocks can run
 size_t spec_eo_mat_floats(int ny);                // floats of one matrix in parity blocks
+// the y-derivatives (and planes) of a newly set state for a group on the fused
+// stage in parity blocks (D2 v with spec_eoff; else the digit kernel's)
+void launch_eo_derivs(const GroupView& g, cudaStream_t st);
 // one Ny x Ny row-major matrix (centro-symmetric, or anti-centro-symmetric when
 // anti) as its two parity blocks, transposed and row-padded (out: spec_eo_mat_floats)
 void spec_eo_image(const double* A, int ny, bool anti, float* out, bool residual = false);

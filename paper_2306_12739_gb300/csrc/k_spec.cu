@@ -1324,6 +1324,124 @@ __global__ void __launch_bounds__(THREADS, MINB) k_spec_eo(GroupView g, int s) {
     }
 }
 
+// Derivatives of a newly set state (after the upload of dns_set_state or
+// dns_advance) for a group on the fused stage in parity blocks: the v and eta
+// planes, D v, D eta and (D2FF) the float-float D2 v in the per-plane layout,
+// computed as the fused stage computes them for the state it produces (the
+// same parity parts, products and order), so a state set from outside enters
+// the next sub-step as one the stage produced itself.  One CTA per (pair,
+// member chunk); D2 v comes from the digit kernel where D2FF is off.
+template <bool D2FF>
+__global__ void __launch_bounds__(THREADS, 2) k_eo_derivs(GroupView g) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    const int Ny = g.ny;
+    const int NE = (Ny + 1) / 2, NO = Ny / 2, RB2 = (NE + 1) / 2, RP2 = 2 * RB2;
+    const size_t MEO = eo_mat(Ny);
+    const int E = g.E, NM = g.nmodes, NKX = g.nkx;
+    const int EC = chunk_members(g), VS = 4 * EC;
+    const size_t VF = (size_t)Ny * VS;
+    const int np1 = g.npairs - 1;
+    Cols c;
+    c.p = 1 + (int)blockIdx.x % np1;
+    const int ch = (int)blockIdx.x / np1;
+    c.n = c.p % NKX;
+    c.am = c.p / NKX;
+    c.nq = c.am > 0 ? 2 : 1;
+    c.q1 = (g.kz + c.am) * NKX + c.n;
+    c.q2 = (g.kz - c.am) * NKX + c.n;
+    c.e0 = ch * EC;
+    c.ec = min(EC, E - c.e0);
+    c.C = c.nq * c.ec;
+    float* D1S = (float*)sm;                      // D1, D2, its residual in parity blocks
+    float* D2S = D1S + MEO;
+    float* D2L = D2S + MEO;
+    float* PH = D1S + (D2FF ? 3 : 1) * MEO;       // v (hi), v (lo), eta in parity parts
+    float* KV = PH + VF;
+    float* EN = KV + VF;
+    unsigned long long* bar = (unsigned long long*)(EN + VF);
+    const unsigned bar_a = su32(bar);
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_a) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (tid == 0) {
+        const unsigned mb = (unsigned)(MEO * sizeof(float));
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_a), "r"((D2FF ? 3 : 1) * mb)
+                     : "memory");
+        bulk(D1S, g.D1EO, mb, bar_a);
+        if (D2FF) {
+            bulk(D2S, g.D2EO, mb, bar_a);
+            bulk(D2L, g.D2lEO, mb, bar_a);
+        }
+    }
+    const size_t fs5 = (size_t)Ny * E * NM;
+    float2* P5 = (float2*)g.P5;
+    for (int i = tid; i < NE * c.C; i += THREADS) {
+        const int p = i / c.C, j = i - p * c.C;
+        const int q = col_q(c, j), e = col_e(c, j);
+        const EoRows R = eo_rows(p, Ny);
+        double2 v[2] = {make_double2(0.0, 0.0), make_double2(0.0, 0.0)}, et[2] = {v[0], v[1]};
+#pragma unroll
+        for (int k2 = 0; k2 < 2; ++k2) {
+            const int y = k2 ? R.y1 : R.y0;
+            if ((k2 && !R.pair) || !in_range(g, q, y, e)) continue;
+            const size_t oh = ((size_t)q * Ny + y) * E + e, o = ((size_t)y * E + e) * NM + q;
+            v[k2] = g.v_t[oh];
+            et[k2] = g.e_t[oh];
+            P5[o] = make_float2(d2f(v[k2].x), d2f(v[k2].y));
+            P5[3 * fs5 + o] = make_float2(d2f(et[k2].x), d2f(et[k2].y));
+        }
+        if (!DNS_CK(g.status, 2 * j + 1 < VS && p < NE, CK_SPEC_SMEM, p * VS + 2 * j)) continue;
+        const double2 ve = make_double2(v[0].x + v[1].x, v[0].y + v[1].y);
+        const double2 vo = make_double2(v[0].x - v[1].x, v[0].y - v[1].y);
+        const float2 he = make_float2(d2f(ve.x), d2f(ve.y)), ho = make_float2(d2f(vo.x), d2f(vo.y));
+        *(float2*)&PH[p * VS + 2 * j] = he;
+        *(float2*)&KV[p * VS + 2 * j] = make_float2(d2f(ve.x - f2d(he.x)), d2f(ve.y - f2d(he.y)));
+        *(float2*)&EN[p * VS + 2 * j] = make_float2(d2f(et[0].x + et[1].x), d2f(et[0].y + et[1].y));
+        if (R.pair) {
+            *(float2*)&PH[(NE + p) * VS + 2 * j] = ho;
+            *(float2*)&KV[(NE + p) * VS + 2 * j] = make_float2(d2f(vo.x - f2d(ho.x)), d2f(vo.y - f2d(ho.y)));
+            *(float2*)&EN[(NE + p) * VS + 2 * j] = make_float2(d2f(et[0].x - et[1].x), d2f(et[0].y - et[1].y));
+        }
+    }
+    __syncthreads();
+    if (!__syncthreads_and(waitp(bar_a, 0))) {
+        if (tid == 0) {
+            atomicExch(g.status, 1);
+            waitp(bar_a, 0);
+        }
+        return;
+    }
+    for (int t = tid; t < NE * c.C; t += THREADS) {
+        const int p = t / c.C, j = t - p * c.C;
+        const int q = col_q(c, j), e = col_e(c, j);
+        const EoRows R = eo_rows(p, Ny);
+        float de[2], dq[2], fe[2], fq[2];
+        eo1(D1S, NO, NE, RP2, PH + NE * VS, PH, VS, p, 2 * j, de, dq);
+        eo1(D1S, NO, NE, RP2, EN + NE * VS, EN, VS, p, 2 * j, fe, fq);
+        float eh[2], el[2], oh[2], ol[2];
+        if (D2FF) eo1ff(D2S, D2L, NE, NO, RP2, PH, KV, VS, p, 2 * j, eh, el, oh, ol);
+#pragma unroll
+        for (int k2 = 0; k2 < 2; ++k2) {
+            const int y = k2 ? R.y1 : R.y0;
+            if ((k2 && !R.pair) || !in_range(g, q, y, e)) continue;
+            const float sg = k2 ? -1.f : 1.f;
+            const size_t o = ((size_t)y * E + e) * NM + q;
+            P5[fs5 + o] = R.pair ? make_float2(0.5f * (de[0] + sg * dq[0]), 0.5f * (de[1] + sg * dq[1]))
+                                 : make_float2(de[0], de[1]);
+            P5[4 * fs5 + o] = R.pair ? make_float2(0.5f * (fe[0] + sg * fq[0]), 0.5f * (fe[1] + sg * fq[1]))
+                                     : make_float2(fe[0], fe[1]);
+            if (D2FF) {
+                const float e0 = __fadd_rn(eh[0], el[0]), e1 = __fadd_rn(eh[1], el[1]);
+                const float o0 = __fadd_rn(oh[0], ol[0]), o1 = __fadd_rn(oh[1], ol[1]);
+                P5[2 * fs5 + o] = R.pair ? make_float2(0.5f * (e0 + sg * o0), 0.5f * (e1 + sg * o1)) : make_float2(e0, e1);
+            }
+        }
+    }
+}
+
 }  // namespace spc
 
 bool spec_supported(const GroupView& g) {
@@ -1349,6 +1467,16 @@ bool spec_eo_supported(const GroupView& g) {
 }
 
 size_t spec_eo_mat_floats(int ny) { return spc::eo_mat(ny); }
+
+static size_t eo_derivs_smem_bytes(const GroupView& g) {
+    return ((g.spec_eoff ? 3 : 1) * spc::eo_mat(g.ny) + 3 * spc::vec_floats(g)) * sizeof(float) + 32;
+}
+
+void launch_eo_derivs(const GroupView& g, cudaStream_t st) {
+    const int ctas = (g.npairs - 1) * spc::chunks(g);
+    if (g.spec_eoff) spc::k_eo_derivs<true><<<ctas, spc::THREADS, eo_derivs_smem_bytes(g), st>>>(g);
+    else spc::k_eo_derivs<false><<<ctas, spc::THREADS, eo_derivs_smem_bytes(g), st>>>(g);
+}
 
 // The parity blocks of a matrix A (Ny x Ny, row-major), R(j) = Ny-1-j, NO =
 // Ny/2, the centre c = NO when Ny is odd.  Centro-symmetric A (A[R i][R j] =
@@ -1436,6 +1564,8 @@ void set_attributes_spec() {
 #undef DNS_CASE
     DNS_EO(0, 0)
 #undef DNS_EO
+    allow_max_dynamic_smem(spc::k_eo_derivs<false>);
+    allow_max_dynamic_smem(spc::k_eo_derivs<true>);
 }
 
 }  // namespace dnsk

@@ -32,6 +32,10 @@ CASES = [
                            members=20, member_block=20)], "mixed", dict(helm="fused"), 3, None),
     ("fused_d2v_inside", [dict(flow="poiseuille", mx=32, my=33, mz=32, lx=2 * np.pi, lz=np.pi, re=1650.0, dt=0.005,
                                members=6, member_block=6)], "mixed", dict(helm="fused_d2v"), 3, None),
+    ("fused_parity_ff", [dict(flow="poiseuille", mx=32, my=33, mz=32, lx=2 * np.pi, lz=np.pi, re=1650.0, dt=0.005,
+                              members=6, member_block=6)], "mixed", dict(helm="fused_eo_ff"), 3, None),
+    ("fused_parity", [dict(flow="couette", mx=16, my=21, mz=16, lx=2 * np.pi, lz=np.pi, re=400.0, dt=0.005,
+                           members=3)], "mixed", dict(helm="fused_eo"), 3, None),
     ("fused_floatfloat", [dict(flow="poiseuille", mx=32, my=97, mz=16, lx=2 * np.pi, lz=np.pi, re=1650.0, dt=0.005,
                                members=2)], "mixed", dict(helm="fused"), 3, None),
     ("chain_tc", [dict(flow="couette", mx=32, my=49, mz=32, lx=1.75 * np.pi, lz=1.2 * np.pi, re=500.0, dt=0.01,

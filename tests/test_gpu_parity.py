@@ -846,3 +846,22 @@ def test_parity_block_stage_ctas_per_sm_do_not_change_the_result(tmp_path):
         ens.close()
     for a, b, name in zip(out[0], out[1], FIELDS):
         assert np.array_equal(a, b), name
+
+
+@pytest.mark.parametrize("stage", ["fused_eo", "fused_eo_ff"])
+def test_parity_block_stage_resumes_through_get_and_set(stage):
+    """3 + 3 steps through get/set (the derivatives of the set state then come
+    from the parity-block derivative kernel, as the stage computes them) = 6
+    steps within the mixed budget, and a member alone = the same member in a
+    batch, bitwise."""
+    g = group("poiseuille", 64, 65, 64, 2 * np.pi, np.pi, 1650.0, 0.005, 4)
+    st = _state(g, 103, 5e-2)
+    pin = dict(helm=stage, plane="lines")
+    whole = _run(g, st, 6, "mixed", **pin)
+    half = _run(g, st, 3, "mixed", **pin)
+    again = _run(g, dict(zip(FIELDS, half)), 3, "mixed", **pin)
+    err = mixed_errors(again, whole)
+    assert np.all(err[:, :3] < 1e-6), err
+    one = _run(dict(g, members=1), {k: st[k][1:2] for k in FIELDS}, 6, "mixed", **pin)
+    for a, b in zip(whole, one):
+        assert np.array_equal(a[1:2], b)
