@@ -909,6 +909,21 @@ __device__ __forceinline__ EoRows eo_rows(int p, int Ny) {
     return r;
 }
 
+// The even and odd parts of two FP64 values as float-float pairs (h, l), from
+// their single-precision splits (x = h + l to 2^-48): a TwoSum (Knuth) of the
+// high parts, the low parts added to its error; the FP64 pipe is not used.
+__device__ __forceinline__ void eo_ff(double x0, double x1, float& eh, float& el, float& oh, float& ol) {
+    const float h0 = d2f(x0), h1 = d2f(x1);
+    const float l0 = d2f(x0 - f2d(h0)), l1 = d2f(x1 - f2d(h1));
+    float s = h0 + h1, bb = s - h0;
+    eh = s;
+    el = ((h0 - (s - bb)) + (h1 - bb)) + (l0 + l1);
+    s = h0 - h1;
+    bb = s - h0;
+    oh = s;
+    ol = ((h0 - (s - bb)) + (-h1 - bb)) + (l0 - l1);
+}
+
 // MINB: CTAs per SM the registers are budgeted for (2, or 3 at 80 registers;
 // shared memory allows 3): chosen by timing whole steps
 template <int NYC, int ECC, int MINB, bool D2FF>
@@ -1035,17 +1050,22 @@ __global__ void __launch_bounds__(THREADS, MINB) k_spec_eo(GroupView g, int s) {
             *(float2*)&PH[se] = make_float2(ph[0].x + ph[1].x, ph[0].y + ph[1].y);
             *(float2*)&KV[se] = make_float2(kvv[0].x + kvv[1].x, kvv[0].y + kvv[1].y);
             *(float2*)&GT[se] = make_float2(gt[0].x + gt[1].x, gt[0].y + gt[1].y);
+            // x_t in single precision, its parts summed in single precision (the
+            // increment (M - I) x_t is O(dt) x_t: one more rounding there is far below
+            // the budget)
+            const float2 v0 = make_float2(d2f(xv[0].x), d2f(xv[0].y)), v1 = make_float2(d2f(xv[1].x), d2f(xv[1].y));
+            const float2 e0 = make_float2(d2f(xe[0].x), d2f(xe[0].y)), e1 = make_float2(d2f(xe[1].x), d2f(xe[1].y));
             if (needM) {
-                *(float2*)&XV[se] = make_float2(d2f(xv[0].x + xv[1].x), d2f(xv[0].y + xv[1].y));
-                *(float2*)&XE[se] = make_float2(d2f(xe[0].x + xe[1].x), d2f(xe[0].y + xe[1].y));
+                *(float2*)&XV[se] = make_float2(v0.x + v1.x, v0.y + v1.y);
+                *(float2*)&XE[se] = make_float2(e0.x + e1.x, e0.y + e1.y);
             }
             if (R.pair) {
                 *(float2*)&PH[so] = make_float2(ph[0].x - ph[1].x, ph[0].y - ph[1].y);
                 *(float2*)&KV[so] = make_float2(kvv[0].x - kvv[1].x, kvv[0].y - kvv[1].y);
                 *(float2*)&GT[so] = make_float2(gt[0].x - gt[1].x, gt[0].y - gt[1].y);
                 if (needM) {
-                    *(float2*)&XV[so] = make_float2(d2f(xv[0].x - xv[1].x), d2f(xv[0].y - xv[1].y));
-                    *(float2*)&XE[so] = make_float2(d2f(xe[0].x - xe[1].x), d2f(xe[0].y - xe[1].y));
+                    *(float2*)&XV[so] = make_float2(v0.x - v1.x, v0.y - v1.y);
+                    *(float2*)&XE[so] = make_float2(e0.x - e1.x, e0.y - e1.y);
                 }
             }
         }
@@ -1162,7 +1182,7 @@ __global__ void __launch_bounds__(THREADS, MINB) k_spec_eo(GroupView g, int s) {
                 const int p = p0 + r;
                 if (p >= NE) break;
                 const EoRows R = eo_rows(p, Ny);
-                double2 xn[2] = {make_double2(0.0, 0.0), make_double2(0.0, 0.0)};
+                float2 hn[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
 #pragma unroll
                 for (int k2 = 0; k2 < 2; ++k2) {
                     const int y = k2 ? R.y1 : R.y0;
@@ -1175,13 +1195,14 @@ __global__ void __launch_bounds__(THREADS, MINB) k_spec_eo(GroupView g, int s) {
                     const size_t oh = ((size_t)q * Ny + y) * E + e;
                     const float2 m1 = (s == 2) ? m1s[r][k2] : ma;
                     if (s == 1) M1[oh] = m1;
-                    xn[k2] = make_double2(x[r][k2].x + f2d(m1.x + pa.x), x[r][k2].y + f2d(m1.y + pa.y));
-                    O[oh] = xn[k2];
-                    P5[3 * fs5 + ((size_t)y * E + e) * NM + q] = make_float2(d2f(xn[k2].x), d2f(xn[k2].y));
+                    const double2 xn = make_double2(x[r][k2].x + f2d(m1.x + pa.x), x[r][k2].y + f2d(m1.y + pa.y));
+                    O[oh] = xn;
+                    hn[k2] = make_float2(d2f(xn.x), d2f(xn.y));
+                    P5[3 * fs5 + ((size_t)y * E + e) * NM + q] = hn[k2];
                 }
-                *(float2*)&EN[p * VS + 2 * j] = make_float2(d2f(xn[0].x + xn[1].x), d2f(xn[0].y + xn[1].y));
-                if (R.pair)
-                    *(float2*)&EN[(NE + p) * VS + 2 * j] = make_float2(d2f(xn[0].x - xn[1].x), d2f(xn[0].y - xn[1].y));
+                // eta+ parts in single precision (D eta is a single-precision product)
+                *(float2*)&EN[p * VS + 2 * j] = make_float2(hn[0].x + hn[1].x, hn[0].y + hn[1].y);
+                if (R.pair) *(float2*)&EN[(NE + p) * VS + 2 * j] = make_float2(hn[0].x - hn[1].x, hn[0].y - hn[1].y);
             }
         }
     }
@@ -1247,17 +1268,16 @@ __global__ void __launch_bounds__(THREADS, MINB) k_spec_eo(GroupView g, int s) {
                     O[oh] = xn[k2];
                     P5[((size_t)y * E + e) * NM + q] = make_float2(d2f(xn[k2].x), d2f(xn[k2].y));
                 }
-                // v+ in parity parts (over phi) for D v; with D2FF also the
-                // residuals (over the (M_v - I) v_t slots this thread has read)
-                const double2 ve = make_double2(xn[0].x + xn[1].x, xn[0].y + xn[1].y);
-                const double2 vo = make_double2(xn[0].x - xn[1].x, xn[0].y - xn[1].y);
-                const float2 he = make_float2(d2f(ve.x), d2f(ve.y)), ho = make_float2(d2f(vo.x), d2f(vo.y));
+                // v+ in parity parts (over phi) for D v; with D2FF as float-float
+                // pairs, the low parts over the (M_v - I) v_t slots this thread has read
+                float2 he, le, ho, lo;
+                eo_ff(xn[0].x, xn[1].x, he.x, le.x, ho.x, lo.x);
+                eo_ff(xn[0].y, xn[1].y, he.y, le.y, ho.y, lo.y);
                 *(float2*)&PH[p * VS + 2 * j] = he;
                 if (R.pair) *(float2*)&PH[(NE + p) * VS + 2 * j] = ho;
                 if (D2FF) {
-                    *(float2*)&KV[p * VS + 2 * j] = make_float2(d2f(ve.x - f2d(he.x)), d2f(ve.y - f2d(he.y)));
-                    if (R.pair)
-                        *(float2*)&KV[(NE + p) * VS + 2 * j] = make_float2(d2f(vo.x - f2d(ho.x)), d2f(vo.y - f2d(ho.y)));
+                    *(float2*)&KV[p * VS + 2 * j] = le;
+                    if (R.pair) *(float2*)&KV[(NE + p) * VS + 2 * j] = lo;
                 }
             }
         }
@@ -1394,16 +1414,17 @@ __global__ void __launch_bounds__(THREADS, 2) k_eo_derivs(GroupView g) {
             P5[3 * fs5 + o] = make_float2(d2f(et[k2].x), d2f(et[k2].y));
         }
         if (!DNS_CK(g.status, 2 * j + 1 < VS && p < NE, CK_SPEC_SMEM, p * VS + 2 * j)) continue;
-        const double2 ve = make_double2(v[0].x + v[1].x, v[0].y + v[1].y);
-        const double2 vo = make_double2(v[0].x - v[1].x, v[0].y - v[1].y);
-        const float2 he = make_float2(d2f(ve.x), d2f(ve.y)), ho = make_float2(d2f(vo.x), d2f(vo.y));
+        float2 he, le, ho, lo;
+        eo_ff(v[0].x, v[1].x, he.x, le.x, ho.x, lo.x);
+        eo_ff(v[0].y, v[1].y, he.y, le.y, ho.y, lo.y);
+        const float2 h0 = make_float2(d2f(et[0].x), d2f(et[0].y)), h1 = make_float2(d2f(et[1].x), d2f(et[1].y));
         *(float2*)&PH[p * VS + 2 * j] = he;
-        *(float2*)&KV[p * VS + 2 * j] = make_float2(d2f(ve.x - f2d(he.x)), d2f(ve.y - f2d(he.y)));
-        *(float2*)&EN[p * VS + 2 * j] = make_float2(d2f(et[0].x + et[1].x), d2f(et[0].y + et[1].y));
+        *(float2*)&KV[p * VS + 2 * j] = le;
+        *(float2*)&EN[p * VS + 2 * j] = make_float2(h0.x + h1.x, h0.y + h1.y);
         if (R.pair) {
             *(float2*)&PH[(NE + p) * VS + 2 * j] = ho;
-            *(float2*)&KV[(NE + p) * VS + 2 * j] = make_float2(d2f(vo.x - f2d(ho.x)), d2f(vo.y - f2d(ho.y)));
-            *(float2*)&EN[(NE + p) * VS + 2 * j] = make_float2(d2f(et[0].x - et[1].x), d2f(et[0].y - et[1].y));
+            *(float2*)&KV[(NE + p) * VS + 2 * j] = lo;
+            *(float2*)&EN[(NE + p) * VS + 2 * j] = make_float2(h0.x - h1.x, h0.y - h1.y);
         }
     }
     __syncthreads();
