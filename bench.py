@@ -223,11 +223,13 @@ def kernel_work(cls, g, precision):
         return "alu", E * ny * per_plane, "flop"
     if cls == "yderiv":
         return "alu", S * 3 * 2 * 2 * ny, "flop"
+    # the step-by-step forcing and apply in parity blocks ("simt_eo"): half the flops
+    half = 0.5 if g.get("_stage") == "simt_eo" else 1.0
     if cls == "forcing":
-        return "alu", S * 2 * 2 * ny, "flop"
+        return "alu", S * 2 * 2 * ny * half, "flop"
     if cls == "helm":
         npairs = nkx * (nkz // 2 + 1)
-        return "alu", 2 * npairs * 2 * 2 * ny * ny * 4 * E, "flop"
+        return "alu", 2 * npairs * 2 * 2 * ny * ny * 4 * E * half, "flop"
     if cls == "d2v":
         # D2 v of the new state: 2 ny flops per real output value
         return "alu", S * 2 * 2 * ny, "flop"
@@ -298,7 +300,8 @@ def kernel_bytes(cls, g, precision):
         npairs = nkx * (nkz // 2 + 1)
         opb = 4 if precision == "mixed" else 8
         mats = (2 + 2 + 1) / 3.0                         # M and P, M reused in the third sub-step
-        ops = member_blocks(g) * npairs * 2 * mats * ny * (rp if precision == "mixed" else ny) * opb
+        width = 2 * (((ny + 1) // 2 + 1) // 2) if g.get("_stage") == "simt_eo" else rp   # parity blocks
+        ops = member_blocks(g) * npairs * 2 * mats * ny * (width if precision == "mixed" else ny) * opb
         m1 = (c if precision == "mixed" else 16) * (2.0 / 3.0)
         return ops + 2 * S * (16 * (2.0 / 3.0) + c + 16 + m1)   # x_t, F~ in, x+ out, M1 x_t
     return 0.0
@@ -850,7 +853,7 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparator run")
     ap.add_argument("--plane", choices=["default", "cta", "cluster", "lines"], default="default",
                     help="plane-stage kernel (default: autotuned among those the grid supports)")
-    ap.add_argument("--helm", choices=["default", "simt", "tc", "persist", "fused", "fused_d2v", "fused_eo", "fused_eo_ff"], default="default",
+    ap.add_argument("--helm", choices=["default", "simt", "tc", "persist", "fused", "fused_d2v", "fused_eo", "fused_eo_ff", "simt_eo"], default="default",
                     help="per-wavenumber stage of the mixed path (default: the fused stage where the group "
                          "supports it, else the autotuned implicit apply)")
     ap.add_argument("--ygemm", choices=["default", "simt", "tc"], default="default",

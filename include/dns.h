@@ -149,8 +149,8 @@ typedef struct {
                                       threads (mixed precision, sizes <= 64); a request for a
                                       variant the group's size lacks is ignored */
     int helm;                      /* mixed path per-wavenumber stage: 0 autotuned at
-                                      dns_bind_workspace (DNS groups: 1 and 2, each timed with the
-                                      y-derivatives and the forcing, against 4 to 7; linear
+                                      dns_bind_workspace (DNS groups: 1, 2 and 8, each timed with
+                                      the y-derivatives and the forcing, against 4 to 7; linear
                                       groups: 1 against 2),
                                       1 register-tiled FP32 implicit apply (one CTA per
                                       wavenumber pair and field), 2 tcgen05 tensor cores with
@@ -173,7 +173,10 @@ typedef struct {
                                       the operator bytes and multiply-adds (groups whose D2 v
                                       comes from the tensor-core kernel; others run 4), 7 the
                                       same with D2 v summed inside it in float-float (D2 in
-                                      parity blocks; every size the fused stage takes) */
+                                      parity blocks; every size the fused stage takes), 8 the
+                                      step-by-step stage of 1 with its forcing (D1) and implicit
+                                      apply (M - I, P) in parity blocks (DNS groups; linear
+                                      groups and tiles that do not fit run 1) */
 } dns_config;
 
 /* One-point statistics of one member (paper Sec. 4), computed from the current
@@ -312,7 +315,8 @@ const char* dns_last_error(const dns_handle* h);
  * single CTA per plane; helm 1 register-tiled FP32 / 2 tcgen05 implicit apply /
  * 3 persistent register-tiled FP32 / 4 the fused per-wavenumber stage / 5 the
  * fused stage with D2 v inside it / 6 the fused stage in parity blocks / 7 the
- * same with its float-float D2 v.  Any output may be NULL. */
+ * same with its float-float D2 v / 8 the register-tiled FP32 stage with its
+ * forcing and apply in parity blocks.  Any output may be NULL. */
 int dns_kernel_choice(const dns_handle* h, int group, int* ygemm, int* plane, int* helm);
 
 /* Number of kernel launches enqueued by the last dns_step call (all steps). */

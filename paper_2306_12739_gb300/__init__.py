@@ -235,13 +235,14 @@ def convert_selftest(d_in, f_in):
 
 def dns_kernel_choice(h, group, which="ygemm"):
     """'ygemm' -> 'simt' | 'tc'; 'plane' -> 'cta' | 'cluster' | 'lines' | 'linear';
-    'helm' -> 'simt' | 'tc' | 'persist' | 'fused' | 'fused_d2v' | 'fused_eo' | 'fused_eo_ff'."""
+    'helm' -> 'simt' | 'tc' | 'persist' | 'fused' | 'fused_d2v' | 'fused_eo' | 'fused_eo_ff' | 'simt_eo'."""
     c, p, m = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
     _ck(h, _lib.dns_kernel_choice(h, group, ctypes.byref(c), ctypes.byref(p), ctypes.byref(m)))
     if which == "plane":
         return {1: "cta", 2: "cluster", 3: "lines", 4: "linear"}.get(p.value, p.value)
     if which == "helm":
-        return {1: "simt", 2: "tc", 3: "persist", 4: "fused", 5: "fused_d2v", 6: "fused_eo", 7: "fused_eo_ff"}.get(m.value, m.value)
+        return {1: "simt", 2: "tc", 3: "persist", 4: "fused", 5: "fused_d2v", 6: "fused_eo", 7: "fused_eo_ff",
+                8: "simt_eo"}.get(m.value, m.value)
     return {1: "simt", 2: "tc"}.get(c.value, c.value)
 
 
@@ -310,7 +311,7 @@ _YGEMM = {"default": 0, "auto": 0, "simt": 1, "tc": 2}
 _PLANE = {"default": 0, "auto": 0, "cta": 1, "cluster": 2, "lines": 3}
 
 
-_HELM = {"default": 0, "auto": 0, "simt": 1, "tc": 2, "persist": 3, "fused": 4, "fused_d2v": 5, "fused_eo": 6, "fused_eo_ff": 7}
+_HELM = {"default": 0, "auto": 0, "simt": 1, "tc": 2, "persist": 3, "fused": 4, "fused_d2v": 5, "fused_eo": 6, "fused_eo_ff": 7, "simt_eo": 8}
 
 
 def _pick(table, name, what):

@@ -22,7 +22,7 @@ NVFLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler"
            "--expt-relaxed-constexpr", "-I" + os.path.join(ROOT, "include")]
 CXXFLAGS = ["-O2", "-std=c++17", "-fPIC", "-ffp-contract=off", "-I" + os.path.join(ROOT, "include")]
 
-CU = ["api.cu", "k_spectral.cu", "k_plane.cu", "k_plane_f32.cu", "k_gemm_f32.cu", "k_noalloc.cu", "k_yderiv_tc.cu", "k_plane_cl.cu", "k_plane_lines.cu", "k_helm_tc.cu", "k_linear.cu", "k_stoch.cu", "k_spec.cu", "k_d2v_tc.cu"]
+CU = ["api.cu", "k_spectral.cu", "k_plane.cu", "k_plane_f32.cu", "k_gemm_f32.cu", "k_noalloc.cu", "k_yderiv_tc.cu", "k_plane_cl.cu", "k_plane_lines.cu", "k_helm_tc.cu", "k_linear.cu", "k_stoch.cu", "k_spec.cu", "k_d2v_tc.cu", "k_step_eo.cu"]
 CPP = ["builder.cpp"]
 
 

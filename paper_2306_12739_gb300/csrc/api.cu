@@ -136,6 +136,12 @@ bool eo_ok(GroupView v, bool ff) {
 }
 // ... and its operator images are wanted (a request for it, or the autotuner)
 bool eo_candidate(const GroupView& v) { return (v.helm == 4 || v.helm == 0) && eo_ok(v, true); }
+// the step-by-step forcing and apply in parity blocks may run (a request, helm
+// 8, or the autotuner): they read the pair operators and D1 in parity blocks
+bool step_eo_candidate(const GroupView& v) {
+    return (v.helm == 0 || (v.helm == 1 && v.step_eo)) && dnsk::step_eo_supported(v);
+}
+bool eo_images(const GroupView& v) { return eo_candidate(v) || step_eo_candidate(v); }
 
 // Largest My at which DNS groups may take the FP32-accumulated tensor-core
 // y-derivatives (see choose_variants)
@@ -182,7 +188,7 @@ size_t layout_group(dns_handle* h, HostGroup& G, size_t cur) {
     add((void**)&v.D1T, sizeof(float) * (size_t)v.ny * v.rp);
     add((void**)&v.D2T, sizeof(float) * (size_t)v.ny * v.rp);
     add((void**)&v.D2Tl, sizeof(float) * (size_t)v.ny * v.rp);
-    if (precision_mixed(h) && eo_candidate(v)) {
+    if (precision_mixed(h) && eo_images(v)) {
         add((void**)&v.D1EO, sizeof(float) * dnsk::spec_eo_mat_floats(v.ny));
         add((void**)&v.D2EO, sizeof(float) * dnsk::spec_eo_mat_floats(v.ny));
         add((void**)&v.D2lEO, sizeof(float) * dnsk::spec_eo_mat_floats(v.ny));
@@ -210,7 +216,7 @@ size_t layout_group(dns_handle* h, HostGroup& G, size_t cur) {
         if (precision_mixed(h)) {
             add((void**)&v.opsfT[hi], sizeof(float) * (size_t)v.npairs * 4 * v.ny * v.rp);
             if (helm_tc_candidate(v)) add((void**)&v.Htc[hi], (size_t)v.npairs * 2 * 3 * 64 * 2 * v.kp * sizeof(uint16_t));
-            if (eo_candidate(v)) add((void**)&v.opsEO[hi], sizeof(float) * (size_t)v.npairs * 4 * dnsk::spec_eo_mat_floats(v.ny));
+            if (eo_images(v)) add((void**)&v.opsEO[hi], sizeof(float) * (size_t)v.npairs * 4 * dnsk::spec_eo_mat_floats(v.ny));
         }
         add((void**)&v.mops[hi], sizeof(double) * (2 * nn + 3 * (size_t)v.ny + (size_t)v.ny * v.my));
     }
@@ -366,7 +372,8 @@ void enqueue_group(dns_handle* h, HostGroup& G, cudaStream_t st, Timer* tm) {
             if (g.shared_mean && g.E > 1) { dnsk::launch_shared_mean(g, false, st); h->launches += 1; }
             if (s == 0 && g.fn > 0 && !side_noise) { dnsk::launch_stoch_noise(g, st); h->launches += 1; }
             if (s == 0 && side_noise) cudaStreamWaitEvent(st, G.njoin, 0);
-            dnsk::launch_forcing_t(g, s, st);
+            if (g.helm == 1 && g.step_eo) dnsk::launch_forcing_eo(g, s, st);
+            else dnsk::launch_forcing_t(g, s, st);
         } else {
             dnsk::launch_yderiv<double>(g, cv, ce, g.P5, st, sprev);
             mark(DNS_K_YDERIV);
@@ -384,6 +391,7 @@ void enqueue_group(dns_handle* h, HostGroup& G, cudaStream_t st, Timer* tm) {
         if (precision_mixed(h)) {
             if (g.helm == 2) dnsk::launch_helm_tc(g, s, st);
             else if (g.helm == 3) dnsk::launch_helm_tp(g, s, st);
+            else if (g.step_eo) dnsk::launch_helm_eo(g, s, st);
             else dnsk::launch_helm_t(g, s, st);
         } else {
             dnsk::launch_helm(g, s, st);
@@ -502,7 +510,7 @@ int cache_lookup(const char* path, const std::string& key) {
         std::string ln(line);
         if (ln.compare(0, key.size(), key) == 0 && ln.size() > key.size() + 1) {
             int c = atoi(ln.c_str() + key.size() + 1);
-            if (c >= 1 && c <= 7) found = c;
+            if (c >= 1 && c <= 8) found = c;
         }
     }
     fclose(f);
@@ -541,11 +549,14 @@ int choose_variants(dns_handle* h, const dns_config* cfg, GroupView& v, int gi) 
     }
     // per-wavenumber stage: 1 register-tiled FP32 apply, 2 tcgen05, 3 persistent
     // register-tiled FP32 with double-buffered operator copies, 4 the fused
-    // stage; 0 = autotuned among 1, 2 (each after the y-derivatives and the
-    // forcing) and 4
+    // stage (5 to 7 its forms), 8 = 1 with the forcing and apply in parity
+    // blocks; 0 = autotuned among 1, 2, 8 (each after the y-derivatives and the
+    // forcing) and 4 to 7
     v.helm = 1;
+    v.step_eo = 0;
     if (precision_mixed(h)) {
         if (cfg->helm >= 4 && cfg->helm <= 7) v.helm = dnsk::spec_supported(v) ? 4 : 0;
+        else if (cfg->helm == 8) v.step_eo = dnsk::step_eo_supported(v) ? 1 : 0;   // 1 in parity blocks
         else if (cfg->helm == 0) v.helm = 0;
         else if (cfg->helm == 2 && dnsk::helm_tc_supported(v)) v.helm = 2;
         else if (cfg->helm == 3) v.helm = 3;
@@ -670,7 +681,7 @@ int dns_create(const dns_config* cfg, void* cuda_stream, dns_handle** out) {
             if (rcv) return rcv;
             if (G.v.ygemm != 1 && G.Atc.empty()) G.Atc = dnsk::yderiv_tc_a_image(G.D1i, G.D2i, G.v.ny, G.v.kp);
             if (G.v.d2tc && G.D2oz.empty()) dnsk::d2v_tc_image(G.D2i, G.v.ny, G.v.kp, G.D2oz, G.D2ozexp);
-            if (precision_mixed(h) && eo_candidate(G.v) && G.opsEO[0].empty()) build_eo_images(G);
+            if (precision_mixed(h) && eo_images(G.v) && G.opsEO[0].empty()) build_eo_images(G);
             if (precision_mixed(h) && helm_tc_candidate(G.v) && G.Htc[0].empty())
                 for (int hi = 0; hi < 2; ++hi)
                     G.Htc[hi] = dnsk::helm_tc_a_images(G.opsdev[hi], G.v.npairs, G.v.ny, G.v.kp);
@@ -803,7 +814,7 @@ int dns_create(const dns_config* cfg, void* cuda_stream, dns_handle** out) {
             }
         if (v.ygemm != 1) G.Atc = dnsk::yderiv_tc_a_image(G.D1i, G.D2i, v.ny, v.kp);
         if (v.d2tc) dnsk::d2v_tc_image(G.D2i, v.ny, v.kp, G.D2oz, G.D2ozexp);
-        if (precision_mixed(h) && eo_candidate(v)) build_eo_images(G);
+        if (precision_mixed(h) && eo_images(v)) build_eo_images(G);
         if (precision_mixed(h) && helm_tc_candidate(v))
             for (int hi = 0; hi < 2; ++hi) G.Htc[hi] = dnsk::helm_tc_a_images(G.opsdev[hi], v.npairs, v.ny, v.kp);
         if (!lin) G.twx = dnsb::twiddles(d.mx);
@@ -866,6 +877,7 @@ int dns_bind_workspace(dns_handle* h, void* dev_ptr, size_t bytes) {
     dnsk::set_attributes_helm_tc();
     dnsk::set_attributes_linear();
     dnsk::set_attributes_spec();
+    dnsk::set_attributes_step_eo();
     dnsk::set_attributes_d2v_tc();
     {
         int rc0 = check(h, cudaGetLastError(), "kernel attributes");
@@ -1016,32 +1028,37 @@ int dns_bind_workspace(dns_handle* h, void* dev_ptr, size_t bytes) {
         // 5: the fused stage with its D2 v inside (every block of the group must allow it)
         // 6, 7: the fused stage in parity blocks, D2 v by the digit kernel or
         // inside in float-float (its images were laid out for every block)
-        bool fuse_ok = dnsk::spec_supported(v0), par_ok = dnsk::spec_supported(v0), ff_ok = par_ok;
+        // 8: the step-by-step stage with its forcing and apply in parity blocks
+        bool fuse_ok = dnsk::spec_supported(v0), par_ok = dnsk::spec_supported(v0), ff_ok = par_ok, seo_ok = true;
         for (const auto& P : h->parts[gi]) {
             const GroupView& vb = h->groups[P.ig].v;
             fuse_ok = fuse_ok && d2fuse_ok(vb);
             const bool img = eo_candidate(vb) && vb.opsEO[0] != nullptr && vb.D1EO != nullptr && vb.D2EO != nullptr;
             par_ok = par_ok && img && vb.d2tc && eo_ok(vb, false);
             ff_ok = ff_ok && img;
+            seo_ok = seo_ok && step_eo_candidate(vb) && vb.opsEO[0] != nullptr && vb.D1EO != nullptr;
         }
         if ((choice == 2 && !dnsk::helm_tc_supported(v0)) || (choice == 4 && !dnsk::spec_supported(v0)) ||
-            (choice == 5 && !fuse_ok) || (choice == 6 && !par_ok) || (choice == 7 && !ff_ok) || choice == 3)
+            (choice == 5 && !fuse_ok) || (choice == 6 && !par_ok) || (choice == 7 && !ff_ok) ||
+            (choice == 8 && !seo_ok) || choice == 3)
             choice = 0;
         if (!choice) {
-            float best[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            float best[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             cudaEvent_t e0, e1;
             cudaEventCreate(&e0);
             cudaEventCreate(&e1);
-            for (int cand = 1; cand <= 7 && !rc; ++cand) {
+            for (int cand = 1; cand <= 8 && !rc; ++cand) {
                 if (cand == 3 || (cand == 2 && !dnsk::helm_tc_supported(v0)) ||
                     (cand == 4 && !dnsk::spec_supported(v0)) || (cand == 5 && !fuse_ok) || (cand == 6 && !par_ok) ||
-                    (cand == 7 && !ff_ok))
+                    (cand == 7 && !ff_ok) || (cand == 8 && !seo_ok))
                     continue;
                 for (const auto& P : h->parts[gi]) {
-                    h->groups[P.ig].v.helm = cand >= 4 ? 4 : cand;
-                    h->groups[P.ig].v.d2fuse = cand == 5 ? 1 : 0;
-                    h->groups[P.ig].v.spec_eo = cand >= 6 ? 1 : 0;
-                    h->groups[P.ig].v.spec_eoff = cand == 7 ? 1 : 0;
+                    GroupView& vb = h->groups[P.ig].v;
+                    vb.helm = cand == 8 ? 1 : cand >= 4 ? 4 : cand;
+                    vb.d2fuse = cand == 5 ? 1 : 0;
+                    vb.spec_eo = (cand == 6 || cand == 7) ? 1 : 0;
+                    vb.spec_eoff = cand == 7 ? 1 : 0;
+                    vb.step_eo = cand == 8 ? 1 : 0;
                 }
                 for (int w = 0; w < 2; ++w) enqueue_step(h);
                 cudaEventRecord(e0, st);
@@ -1057,17 +1074,18 @@ int dns_bind_workspace(dns_handle* h, void* dev_ptr, size_t bytes) {
             if (rc) return rc;
             if ((rc = device_status(h))) return rc;
             choice = 0;
-            for (int cand = 1; cand <= 7; ++cand)
+            for (int cand = 1; cand <= 8; ++cand)
                 if (best[cand] > 0.f && (choice == 0 || best[cand] < best[choice])) choice = cand;
-            cache_store(h->cfg.autotune_cache, key, choice, best, 7);
+            cache_store(h->cfg.autotune_cache, key, choice, best, 8);
         }
         decided[key] = choice;
         for (const auto& P : h->parts[gi]) {
             GroupView& v = h->groups[P.ig].v;
-            v.helm = choice >= 4 ? 4 : choice;
+            v.helm = choice == 8 ? 1 : choice >= 4 ? 4 : choice;
             v.d2fuse = choice == 5 ? 1 : 0;
-            v.spec_eo = choice >= 6 ? 1 : 0;
+            v.spec_eo = (choice == 6 || choice == 7) ? 1 : 0;
             v.spec_eoff = choice == 7 ? 1 : 0;
+            v.step_eo = choice == 8 ? 1 : 0;
             if (v.helm == 4) v.ygemm = 1;
         }
     }
@@ -2135,7 +2153,7 @@ int dns_kernel_choice(const dns_handle* h, int group, int* ygemm, int* plane, in
     const GroupView& v = h->groups[h->parts[group][0].ig].v;
     if (ygemm) *ygemm = v.ygemm;
     if (plane) *plane = v.plane;
-    if (helm) *helm = v.helm != 4 ? v.helm : v.d2fuse ? 5 : v.spec_eoff ? 7 : v.spec_eo ? 6 : 4;
+    if (helm) *helm = v.helm == 1 && v.step_eo ? 8 : v.helm != 4 ? v.helm : v.d2fuse ? 5 : v.spec_eoff ? 7 : v.spec_eo ? 6 : 4;
     return DNS_OK;
 }
 

@@ -62,6 +62,7 @@ struct GroupView {
     int spec_eo;          // fused stage: 1 = in parity blocks (even / odd parts in y; with d2tc)
     int spec_minb;        // fused stage in parity blocks: CTAs per SM of its register budget (2 or 3)
     int spec_eoff;        // fused stage in parity blocks: 1 = D2 v summed inside in float-float
+    int step_eo;          // step-by-step stage (helm 1): 1 = forcing and implicit apply in parity blocks
     const float* opsEO[2];  // mixed path, per h index: [npairs][4] matrices (M - I, P of v and eta) in
                             // parity blocks, each eo_mat(Ny) floats (see k_spec.cu)
     const float* D1EO;      // D1 in parity blocks
@@ -184,6 +185,13 @@ void spec_eo_image(const double* A, int ny, bool anti, float* out, bool residual
 size_t spec_smem_bytes(const GroupView& g);
 void launch_spec(const GroupView& g, int s, cudaStream_t st);
 void set_attributes_spec();
+// the step-by-step forcing and implicit apply in parity blocks (k_step_eo.cu)
+bool step_eo_supported(const GroupView& g);
+size_t forcing_eo_smem_bytes(const GroupView& g);
+size_t helm_eo_smem_bytes(const GroupView& g);
+void launch_forcing_eo(const GroupView& g, int s, cudaStream_t st);
+void launch_helm_eo(const GroupView& g, int s, cudaStream_t st);
+void set_attributes_step_eo();
 void launch_stats(const GroupView& g, cudaStream_t st);
 // the statistics without profiles and CFL: per-plane sums into part [E][Ny][6],
 // packed values into out [E][8]

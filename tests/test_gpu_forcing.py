@@ -100,7 +100,8 @@ def test_fp64_forced_shared_mean_ensemble_matches_the_oracle():
 
 
 @pytest.mark.parametrize("precision,pin", [("fp64", {}), ("mixed", dict(ygemm="tc", plane="lines", helm="simt")),
-                                           ("mixed", dict(plane="lines", helm="fused"))])
+                                           ("mixed", dict(plane="lines", helm="fused")),
+                                           ("mixed", dict(ygemm="tc", plane="lines", helm="simt_eo"))])
 def test_forced_graph_replay_and_member_blocks_are_bitwise_invisible(precision, pin):
     g = group("couette", 16, 33, 16, 400.0, 0.01, 40)
     st = _state(g, 60)
@@ -111,7 +112,8 @@ def test_forced_graph_replay_and_member_blocks_are_bitwise_invisible(precision, 
         assert np.array_equal(a, b)
 
 
-@pytest.mark.parametrize("pin", [dict(ygemm="tc", plane="lines", helm="simt"), dict(helm="fused")])
+@pytest.mark.parametrize("pin", [dict(ygemm="tc", plane="lines", helm="simt"), dict(helm="fused"),
+                                 dict(ygemm="tc", plane="lines", helm="simt_eo")])
 def test_mixed_forced_run_matches_fp64_over_50_steps(pin):
     """Every step draws new noise (the step counter advances once per step in
     the step-by-step and in the fused stage alike)."""

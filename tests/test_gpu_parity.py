@@ -817,6 +817,49 @@ def test_fused_stage_in_parity_blocks_matches_fp64_and_the_natural_order_stage(s
     assert np.all(mixed_errors(par, nat)[:, :3] < 1e-6)
 
 
+@pytest.mark.parametrize("flow,mx,my,mz,E,extra", [
+    ("couette", 32, 33, 32, 5, {}),
+    ("poiseuille", 64, 65, 64, 4, {}),
+    ("poiseuille", 16, 21, 48, 20, dict(member_block=20)),      # one block of 20: member chunks
+    ("couette", 48, 49, 48, 3, dict(form="rotational")),
+    ("couette", 16, 7, 16, 3, {}),                              # Ny = 5: parity parts of 3 and 2 rows
+    ("poiseuille", 32, 34, 16, 2, {}),                          # even Ny: no centre row
+    ("poiseuille", 32, 97, 16, 2, {}),                          # Ny = 95
+])
+def test_step_by_step_stage_in_parity_blocks_matches_fp64_and_the_natural_order_stage(flow, mx, my, mz, E, extra):
+    """The step-by-step stage with its forcing (D1) and implicit apply (M - I,
+    P) in parity blocks against the FP64 step over 20 steps (1e-6 per field and
+    member, W00 on its own scale at 3e-5) and against the same stage in the
+    natural order (the same products regrouped: within the budget)."""
+    g = dict(group(flow, mx, my, mz, 2 * np.pi, np.pi, 1650.0 if flow == "poiseuille" else 400.0, 0.005, E), **extra)
+    st = _state(g, 93, 5e-2)
+    ens = dns.Ensemble([g], precision="mixed", helm="simt_eo")
+    got = dns.dns_kernel_choice(ens.h, 0, "helm")
+    ens.close()
+    assert got == "simt_eo"
+    ref = _run(g, st, 20, "fp64")
+    par = _run(g, st, 20, "mixed", use_graph=True, helm="simt_eo")
+    nat = _run(g, st, 20, "mixed", use_graph=True, helm="simt")
+    err = mixed_errors(par, ref)
+    assert np.all(err[:, :3] < 1e-6), err
+    assert np.all(err[:, 3] < 3e-5), err
+    assert np.all(mixed_errors(par, nat)[:, :3] < 1e-6)
+
+
+def test_step_by_step_stage_in_parity_blocks_keeps_members_independent():
+    """Members evolve independently in the parity-block forcing and apply as
+    anywhere else: the first members of a 5-member run (one block; the
+    forcing's column tiles and the apply's CTAs hold other member counts) equal
+    a 3-member run bit for bit after 3 steps, eager and graph replay alike."""
+    g = group("couette", 32, 33, 32, 2 * np.pi, np.pi, 400.0, 0.005, 5)
+    st = _state(g, 97, 5e-2)
+    five = _run(dict(g, member_block=5), st, 3, "mixed", helm="simt_eo", plane="lines")
+    three = _run(dict(g, members=3), {k: st[k][:3] for k in FIELDS}, 3, "mixed", use_graph=True, helm="simt_eo",
+                 plane="lines")
+    for a, b, name in zip(five, three, FIELDS):
+        assert np.array_equal(a[:3], b), name
+
+
 @pytest.mark.parametrize("stage", ["fused_eo", "fused_eo_ff"])
 def test_headline_in_parity_blocks_matches_fp64_over_50_steps(stage):
     """The benchmarked configuration (64x65x64, 8 members in two blocks, graph)
