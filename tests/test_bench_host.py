@@ -124,3 +124,24 @@ def test_roofline_bound_follows_the_ridge_point():
     w = bench.kernel_work("plane", g, "mixed")[1]
     b = bench.kernel_bytes("plane", g, "mixed")
     assert bench.roofline_bound(w, b, 80.5, 6799.3) == "alu"
+
+
+def test_parity_block_models_halve_the_operator_bytes_and_the_flops():
+    """In parity blocks a matrix is its even and odd halves, Ny x 2 ceil(ceil(Ny/2)/2)
+    floats (63 x 32 at Ny = 63 against 63 x 64 row-padded), and every product
+    half the multiply-adds: the fused stage (fused_eo, fused_eo_ff) and the
+    step-by-step forcing and apply (simt_eo)."""
+    g = dict(bench.WORKLOADS["poiseuille64"]["groups"][0], members=4)
+    S = 22 * 43 * 63 * 4
+    nat = bench.kernel_bytes("spec", dict(g, _stage="fused_eo_ff"), "mixed")
+    assert nat == pytest.approx(bench.kernel_bytes("spec", dict(g, _stage="fused_d2v"), "mixed")
+                                - 483 * (10 / 3) * 63 * 32 * 4)
+    h_nat = bench.kernel_bytes("helm", dict(g, _stage="simt"), "mixed")
+    h_eo = bench.kernel_bytes("helm", dict(g, _stage="simt_eo"), "mixed")
+    assert h_nat - h_eo == pytest.approx(484 * 2 * (5 / 3) * 63 * 32 * 4)
+    for cls in ("forcing", "helm"):
+        _, a, _ = bench.kernel_work(cls, dict(g, _stage="simt"), "mixed")
+        _, b, _ = bench.kernel_work(cls, dict(g, _stage="simt_eo"), "mixed")
+        assert b == pytest.approx(a / 2)
+    assert bench.kernel_bytes("forcing", dict(g, _stage="simt_eo"), "mixed") == \
+        bench.kernel_bytes("forcing", g, "mixed") == pytest.approx((40 + 16 * 4 / 3) * S)
