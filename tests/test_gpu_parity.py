@@ -370,7 +370,7 @@ def test_autotuner_picks_a_variant_caches_it_and_matches_that_variant(tmp_path):
     plane = dns.dns_kernel_choice(ens.h, 0, "plane")
     helm = dns.dns_kernel_choice(ens.h, 0, "helm")
     assert choice in ("simt", "tc") and plane in ("cta", "lines") and helm in ("simt", "tc", "fused", "fused_d2v",
-                                                                                 "fused_eo", "fused_eo_ff")
+                                                                                 "fused_eo", "fused_eo_ff", "simt_eo")
     assert helm not in ("fused", "fused_d2v", "fused_eo", "fused_eo_ff") or choice == "simt"
     ens.set_state(0, st["v"], st["eta"], st["U"], st["W"])
     ens.step(3)
