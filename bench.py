@@ -222,7 +222,8 @@ def kernel_work(cls, g, precision):
             per_plane = 15 * 2.5 * MM * np.log2(MM) + 9 * 2 * MM + 2 * 2 * MM
         return "alu", E * ny * per_plane, "flop"
     if cls == "yderiv":
-        return "alu", S * 3 * 2 * 2 * ny, "flop"
+        # in parity blocks ("simt_eo" y-derivatives) half the flops
+        return "alu", S * 3 * 2 * 2 * ny * (0.5 if g.get("_ygemm") == "simt_eo" else 1.0), "flop"
     # the step-by-step forcing and apply in parity blocks ("simt_eo"): half the flops
     half = 0.5 if g.get("_stage") == "simt_eo" else 1.0
     if cls == "forcing":
@@ -645,6 +646,7 @@ def gpu_arm(args, rank, world, dist):
                     helm=dns.dns_kernel_choice(ens.h, gi, "helm")) for gi in range(len(groups))]
     for g, ch in zip(groups, choices):
         g["_stage"] = ch["helm"]            # the byte and flop models of the fused stage depend on it
+        g["_ygemm"] = ch["ygemm"]
     total_ms = reduce_max(total_ms, dist, dev)
     ms_step = total_ms / args.steps
     value = aggregate(members * args.steps, total_ms / 1e3, world)
@@ -856,7 +858,7 @@ def main():
     ap.add_argument("--helm", choices=["default", "simt", "tc", "persist", "fused", "fused_d2v", "fused_eo", "fused_eo_ff", "simt_eo"], default="default",
                     help="per-wavenumber stage of the mixed path (default: the fused stage where the group "
                          "supports it, else the autotuned implicit apply)")
-    ap.add_argument("--ygemm", choices=["default", "simt", "tc"], default="default",
+    ap.add_argument("--ygemm", choices=["default", "simt", "tc", "simt_eo"], default="default",
                     help="y-contraction variant of the mixed path")
     ap.add_argument("--member-block", type=int, default=0,
                     help="members per block of every independent-member group (0: the library's rule)")

@@ -133,14 +133,17 @@ typedef struct {
                                       of the register-tiled y-derivatives; the shapes never change
                                       a result); NULL = none */
     int ygemm;                     /* mixed path y-derivatives of the step-by-step stage
-                                      (helm 1-3): 0 autotuned at dns_bind_workspace, 1
+                                      (helm 1-3, 8): 0 autotuned at dns_bind_workspace, 1
                                       register-tiled FP32 with D2 v summed in float-float, 2
                                       tcgen05 tensor cores with split-BF16 operands and FP32
-                                      accumulation (groups with My <= 66 and <= 64 members).
-                                      The FP32 accumulation loses about 1e-5 of |D2 v| to the
-                                      cancellation in D2's rows at My = 65, over the 1e-6 budget
-                                      of the mixed step, so DNS groups time 2 against 1 only up
-                                      to My = 49 (linear groups at every size) */
+                                      accumulation (groups with My <= 66 and <= 64 members), 3
+                                      the register-tiled kernel of 1 in parity blocks (D1 and
+                                      D2 as their even and odd halves; the same float-float
+                                      D2 v).  The FP32 accumulation of 2 loses about 1e-5 of
+                                      |D2 v| to the cancellation in D2's rows at My = 65, over
+                                      the 1e-6 budget of the mixed step, so DNS groups time it
+                                      against 1 and 3 only up to My = 49 (linear groups at every
+                                      size); 1 and 3 are timed against each other at every size */
     int plane;                     /* plane stage: 0 autotuned where several kernels exist (else
                                       the only one; FP64 defaults to 1), 1 one CTA per plane
                                       (sizes <= 64), 2 a thread-block cluster per plane (64x64
@@ -310,7 +313,8 @@ int dns_destroy(dns_handle* h);
 const char* dns_last_error(const dns_handle* h);
 
 /* Kernel variants `group` uses, after the autotuner ran (i.e. after
- * dns_bind_workspace): ygemm 1 register-tiled FP32 / 2 tcgen05 y-contraction;
+ * dns_bind_workspace): ygemm 1 register-tiled FP32 / 2 tcgen05 y-contraction /
+ * 3 register-tiled FP32 in parity blocks;
  * plane 1 one CTA per plane / 2 a thread-block cluster per plane / 3 line-owned
  * single CTA per plane; helm 1 register-tiled FP32 / 2 tcgen05 implicit apply /
  * 3 persistent register-tiled FP32 / 4 the fused per-wavenumber stage / 5 the

@@ -234,7 +234,7 @@ def convert_selftest(d_in, f_in):
 
 
 def dns_kernel_choice(h, group, which="ygemm"):
-    """'ygemm' -> 'simt' | 'tc'; 'plane' -> 'cta' | 'cluster' | 'lines' | 'linear';
+    """'ygemm' -> 'simt' | 'tc' | 'simt_eo'; 'plane' -> 'cta' | 'cluster' | 'lines' | 'linear';
     'helm' -> 'simt' | 'tc' | 'persist' | 'fused' | 'fused_d2v' | 'fused_eo' | 'fused_eo_ff' | 'simt_eo'."""
     c, p, m = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
     _ck(h, _lib.dns_kernel_choice(h, group, ctypes.byref(c), ctypes.byref(p), ctypes.byref(m)))
@@ -243,7 +243,7 @@ def dns_kernel_choice(h, group, which="ygemm"):
     if which == "helm":
         return {1: "simt", 2: "tc", 3: "persist", 4: "fused", 5: "fused_d2v", 6: "fused_eo", 7: "fused_eo_ff",
                 8: "simt_eo"}.get(m.value, m.value)
-    return {1: "simt", 2: "tc"}.get(c.value, c.value)
+    return {1: "simt", 2: "tc", 3: "simt_eo"}.get(c.value, c.value)
 
 
 def dns_set_base_flow(h, group, U, V, W, ptr_kind):
@@ -305,7 +305,7 @@ _FLOWS = {"couette": DNS_COUETTE, "poiseuille": DNS_POISEUILLE}
 _PRECS = {"fp64": DNS_PREC_FP64, "mixed": DNS_PREC_MIXED}
 
 
-_YGEMM = {"default": 0, "auto": 0, "simt": 1, "tc": 2}
+_YGEMM = {"default": 0, "auto": 0, "simt": 1, "tc": 2, "simt_eo": 3}
 
 
 _PLANE = {"default": 0, "auto": 0, "cta": 1, "cluster": 2, "lines": 3}

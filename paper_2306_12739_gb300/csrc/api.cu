@@ -147,15 +147,27 @@ bool eo_images(const GroupView& v) { return eo_candidate(v) || step_eo_candidate
 // y-derivatives (see choose_variants)
 constexpr int FP32_D2_MAX_MY = 49;
 
+// the tcgen05 y-derivatives may run (a request, or the autotuner: DNS groups up
+// to FP32_D2_MAX_MY, linear groups at every size): their operator image is needed
+bool ygemm_tc_candidate(const GroupView& v) {
+    return v.ygemm == 2 || (v.ygemm == 0 && dnsk::yderiv_tc_supported(v) && (v.lin || v.my <= FP32_D2_MAX_MY));
+}
+// the y-derivatives in parity blocks may run (a request, ygemm 3, or the
+// autotuner): D1, D2 and its residual in parity blocks are needed
+bool ygemm_eo_candidate(const GroupView& v) {
+    return (v.ygemm == 0 || v.ygemm == 3) && dnsk::yderiv_eo_supported(v);
+}
+
 // Assign workspace offsets for every device array of group g (base = 0).
 // The parity-block images of the fused stage in parity blocks: per h index and
 // wavenumber pair, M_v - I, P_v, M_eta - I, P_eta (from the FP64 operators),
 // and D1 (interior block).
-void build_eo_images(HostGroup& G) {
+// ops false: D1, D2 and its residual only (the y-derivatives in parity blocks).
+void build_eo_images(HostGroup& G, bool ops) {
     const GroupView& v = G.v;
     const size_t nn = (size_t)v.ny * v.ny, mat = dnsk::spec_eo_mat_floats(v.ny);
     std::vector<double> a(nn);
-    for (int hi = 0; hi < 2; ++hi) {
+    for (int hi = 0; hi < 2 && ops; ++hi) {
         G.opsEO[hi].assign((size_t)v.npairs * 4 * mat, 0.f);
         for (size_t blk = 0; blk < (size_t)v.npairs * 4; ++blk) {
             memcpy(a.data(), &G.opsdev[hi][blk * nn], nn * sizeof(double));
@@ -188,13 +200,13 @@ size_t layout_group(dns_handle* h, HostGroup& G, size_t cur) {
     add((void**)&v.D1T, sizeof(float) * (size_t)v.ny * v.rp);
     add((void**)&v.D2T, sizeof(float) * (size_t)v.ny * v.rp);
     add((void**)&v.D2Tl, sizeof(float) * (size_t)v.ny * v.rp);
-    if (precision_mixed(h) && eo_images(v)) {
+    if (precision_mixed(h) && (eo_images(v) || ygemm_eo_candidate(v))) {
         add((void**)&v.D1EO, sizeof(float) * dnsk::spec_eo_mat_floats(v.ny));
         add((void**)&v.D2EO, sizeof(float) * dnsk::spec_eo_mat_floats(v.ny));
         add((void**)&v.D2lEO, sizeof(float) * dnsk::spec_eo_mat_floats(v.ny));
     }
     add((void**)&v.status, 256);
-    if (v.ygemm != 1) add((void**)&v.Atc, 3 * 128 * (size_t)v.kp * sizeof(uint16_t));
+    if (ygemm_tc_candidate(v)) add((void**)&v.Atc, 3 * 128 * (size_t)v.kp * sizeof(uint16_t));
     if (v.d2tc) {
         add((void**)&v.D2oz, dnsk::d2v_tc_image_bytes(v));
         add((void**)&v.D2ozexp, 64 * sizeof(int));
@@ -362,6 +374,7 @@ void enqueue_group(dns_handle* h, HostGroup& G, cudaStream_t st, Timer* tm) {
         }
         if (precision_mixed(h)) {
             if (g.ygemm == 2) dnsk::launch_yderiv_tc(g, cv, ce, st, sprev);
+            else if (g.ygemm == 3) dnsk::launch_yderiv_eo(g, cv, ce, st, sprev);
             else dnsk::launch_yderiv_t(g, cv, ce, st, sprev);
             mark(DNS_K_YDERIV);
             if (g.lin) dnsk::launch_lin_plane(g, false, st);
@@ -535,17 +548,20 @@ void cache_store(const char* path, const std::string& key, int choice, const flo
 // config; 0 entries are decided by the autotuner at dns_bind_workspace.
 int choose_variants(dns_handle* h, const dns_config* cfg, GroupView& v, int gi) {
     const dns_group_desc& d = h->descs[gi];
-    // y-contraction variant: 1 register-tiled FP32, 2 tcgen05; 0 = decided by the
-    // autotuner when the workspace is bound
+    // y-contraction variant: 1 register-tiled FP32, 2 tcgen05, 3 register-tiled
+    // FP32 in parity blocks; 0 = decided by the autotuner when the workspace is
+    // bound (where more than one candidate can run)
     // The tensor-core one accumulates D2 v in FP32, which loses about 1e-5 of
     // |D2 v| to the cancellation in D2's rows at My = 65 (max row sum of |D2_int|
     // 1.2e6; eta 2.2e-6 after 50 steps, over the 1e-6 budget) but not at My = 49
     // (3.8e5; 4.2e-7): DNS groups time it against the float-float register-tiled
     // kernel up to My = 49 and use the latter above; linear groups time both.
     v.ygemm = 1;
-    if (precision_mixed(h) && dnsk::yderiv_tc_supported(v)) {
-        if (cfg->ygemm == 2) v.ygemm = 2;
-        else if (cfg->ygemm == 0 && (v.lin || v.my <= FP32_D2_MAX_MY)) v.ygemm = 0;
+    if (precision_mixed(h)) {
+        const bool tc = dnsk::yderiv_tc_supported(v), eo = dnsk::yderiv_eo_supported(v);
+        if (cfg->ygemm == 2 && tc) v.ygemm = 2;
+        else if (cfg->ygemm == 3 && eo) v.ygemm = 3;
+        else if (cfg->ygemm == 0 && ((tc && (v.lin || v.my <= FP32_D2_MAX_MY)) || eo)) v.ygemm = 0;
     }
     // per-wavenumber stage: 1 register-tiled FP32 apply, 2 tcgen05, 3 persistent
     // register-tiled FP32 with double-buffered operator copies, 4 the fused
@@ -679,9 +695,11 @@ int dns_create(const dns_config* cfg, void* cuda_stream, dns_handle** out) {
             G.v.E = d.members;
             int rcv = choose_variants(h, cfg, G.v, gi);
             if (rcv) return rcv;
-            if (G.v.ygemm != 1 && G.Atc.empty()) G.Atc = dnsk::yderiv_tc_a_image(G.D1i, G.D2i, G.v.ny, G.v.kp);
+            if (ygemm_tc_candidate(G.v) && G.Atc.empty()) G.Atc = dnsk::yderiv_tc_a_image(G.D1i, G.D2i, G.v.ny, G.v.kp);
             if (G.v.d2tc && G.D2oz.empty()) dnsk::d2v_tc_image(G.D2i, G.v.ny, G.v.kp, G.D2oz, G.D2ozexp);
-            if (precision_mixed(h) && eo_images(G.v) && G.opsEO[0].empty()) build_eo_images(G);
+            if (precision_mixed(h) && ((eo_images(G.v) && G.opsEO[0].empty()) ||
+                                       (ygemm_eo_candidate(G.v) && G.D1EO.empty())))
+                build_eo_images(G, eo_images(G.v));
             if (precision_mixed(h) && helm_tc_candidate(G.v) && G.Htc[0].empty())
                 for (int hi = 0; hi < 2; ++hi)
                     G.Htc[hi] = dnsk::helm_tc_a_images(G.opsdev[hi], G.v.npairs, G.v.ny, G.v.kp);
@@ -812,9 +830,9 @@ int dns_create(const dns_config* cfg, void* cuda_stream, dns_handle** out) {
                 G.D2T[(size_t)k * v.rp + r] = (float)d2;
                 G.D2Tl[(size_t)k * v.rp + r] = (float)(d2 - (double)(float)d2);
             }
-        if (v.ygemm != 1) G.Atc = dnsk::yderiv_tc_a_image(G.D1i, G.D2i, v.ny, v.kp);
+        if (ygemm_tc_candidate(v)) G.Atc = dnsk::yderiv_tc_a_image(G.D1i, G.D2i, v.ny, v.kp);
         if (v.d2tc) dnsk::d2v_tc_image(G.D2i, v.ny, v.kp, G.D2oz, G.D2ozexp);
-        if (precision_mixed(h) && eo_images(v)) build_eo_images(G);
+        if (precision_mixed(h) && (eo_images(v) || ygemm_eo_candidate(v))) build_eo_images(G, eo_images(v));
         if (precision_mixed(h) && helm_tc_candidate(v))
             for (int hi = 0; hi < 2; ++hi) G.Htc[hi] = dnsk::helm_tc_a_images(G.opsdev[hi], v.npairs, v.ny, v.kp);
         if (!lin) G.twx = dnsb::twiddles(d.mx);
@@ -983,15 +1001,21 @@ int dns_bind_workspace(dns_handle* h, void* dev_ptr, size_t bytes) {
         if (v.ygemm != 0) continue;
         const std::string key = tune_key(v);
         int choice = decided.count(key) ? decided[key] : cache_lookup(h->cfg.autotune_cache, key);
-        if (choice > 2) choice = 0;
+        // candidates: 1 always; 2 where its operator image was laid out; 3 where
+        // the parity-block images were
+        const bool tc_ok = ygemm_tc_candidate(v) && v.Atc != nullptr;
+        const bool eo_ok3 = ygemm_eo_candidate(v) && v.D1EO != nullptr && v.D2EO != nullptr && v.D2lEO != nullptr;
+        if (choice > 3 || (choice == 2 && !tc_ok) || (choice == 3 && !eo_ok3)) choice = 0;
         if (!choice) {
-            float best[3] = {0.f, 0.f, 0.f};
+            float best[4] = {0.f, 0.f, 0.f, 0.f};
             cudaEvent_t e0, e1;
             cudaEventCreate(&e0);
             cudaEventCreate(&e1);
-            for (int cand = 1; cand <= 2; ++cand) {
+            for (int cand = 1; cand <= 3; ++cand) {
+                if ((cand == 2 && !tc_ok) || (cand == 3 && !eo_ok3)) continue;
                 auto run = [&]() {
                     if (cand == 2) dnsk::launch_yderiv_tc(v, v.v_t, v.e_t, st);
+                    else if (cand == 3) dnsk::launch_yderiv_eo(v, v.v_t, v.e_t, st);
                     else dnsk::launch_yderiv_t(v, v.v_t, v.e_t, st);
                 };
                 for (int w = 0; w < 2; ++w) run();
@@ -1007,8 +1031,10 @@ int dns_bind_workspace(dns_handle* h, void* dev_ptr, size_t bytes) {
             cudaEventDestroy(e1);
             if (rc) return rc;
             if ((rc = device_status(h))) return rc;
-            choice = best[2] < best[1] ? 2 : 1;
-            cache_store(h->cfg.autotune_cache, key, choice, best, 2);
+            choice = 1;
+            for (int cand = 2; cand <= 3; ++cand)
+                if (best[cand] > 0.f && best[cand] < best[choice]) choice = cand;
+            cache_store(h->cfg.autotune_cache, key, choice, best, 3);
         }
         decided[key] = choice;
         v.ygemm = choice;
@@ -1122,6 +1148,7 @@ int dns_bind_workspace(dns_handle* h, void* dev_ptr, size_t bytes) {
                     }
                     if (whole) {
                         if (v.ygemm == 2) dnsk::launch_yderiv_tc(v, v.v_t, v.e_t, st);
+                        else if (v.ygemm == 3) dnsk::launch_yderiv_eo(v, v.v_t, v.e_t, st);
                         else dnsk::launch_yderiv_t(v, v.v_t, v.e_t, st);
                         dnsk::launch_forcing_t(v, 1, st);
                     }
@@ -1249,9 +1276,13 @@ int dns_bind_workspace(dns_handle* h, void* dev_ptr, size_t bytes) {
     // set state):
     for (auto& G : h->groups) {
         GroupView& v = G.v;
-        if (!precision_mixed(h) || v.ygemm != 1) continue;
+        if (!precision_mixed(h) || (v.ygemm != 1 && v.ygemm != 3)) continue;
         char kb[96];
         snprintf(kb, sizeof kb, "ytile %d %d %d %d", v.mx, v.my, v.mz, v.E);
+        auto yd = [&]() {
+            if (v.ygemm == 3) dnsk::launch_yderiv_eo(v, v.v_t, v.e_t, st);
+            else dnsk::launch_yderiv_t(v, v.v_t, v.e_t, st);
+        };
         const std::string key = kb;
         const std::vector<int> cands = {16, 32, 64};
         int choice = decided.count(key) ? decided[key] : cache_lookup_value(h->cfg.autotune_cache, key);
@@ -1263,9 +1294,9 @@ int dns_bind_workspace(dns_handle* h, void* dev_ptr, size_t bytes) {
             cudaEventCreate(&e1);
             for (size_t ci = 0; ci < cands.size() && !rc; ++ci) {
                 v.yd_cap = cands[ci];
-                for (int w = 0; w < 2; ++w) dnsk::launch_yderiv_t(v, v.v_t, v.e_t, st);
+                for (int w = 0; w < 2; ++w) yd();
                 cudaEventRecord(e0, st);
-                for (int r = 0; r < 5; ++r) dnsk::launch_yderiv_t(v, v.v_t, v.e_t, st);
+                for (int r = 0; r < 5; ++r) yd();
                 cudaEventRecord(e1, st);
                 rc = check(h, cudaEventSynchronize(e1), "autotune y-derivative tile");
                 if (!rc) cudaEventElapsedTime(&ms[ci], e0, e1);

@@ -19,7 +19,8 @@ struct GroupView {
     int mx, my, mz, kx, kz, nkx, nkz, nmodes, ny, E, npairs;
     int rp;               // Ny rounded up to a multiple of 4 (row padding of transposed operators)
     int kp;               // Ny rounded up to a multiple of 16 (K of the tensor-core y-contraction)
-    int ygemm;            // mixed path y-derivatives: 1 register-tiled FP32, 2 tcgen05 split-BF16
+    int ygemm;            // mixed path y-derivatives: 1 register-tiled FP32, 2 tcgen05 split-BF16,
+                          // 3 register-tiled FP32 in parity blocks; 0 = autotune
     int plane;            // plane stage: 1 single-CTA kernel, 2 cluster kernel, 3 line-owned
                           // single-CTA kernel (mixed path); 0 = autotune
     const void* Atc;      // tensor-core A image: [D1_int; D2_int] in 3 BF16 pieces
@@ -185,7 +186,10 @@ void spec_eo_image(const double* A, int ny, bool anti, float* out, bool residual
 size_t spec_smem_bytes(const GroupView& g);
 void launch_spec(const GroupView& g, int s, cudaStream_t st);
 void set_attributes_spec();
-// the step-by-step forcing and implicit apply in parity blocks (k_step_eo.cu)
+// the step-by-step y-derivatives, forcing and implicit apply in parity blocks (k_step_eo.cu)
+bool yderiv_eo_supported(const GroupView& g);
+size_t yderiv_eo_smem_bytes(const GroupView& g);
+void launch_yderiv_eo(const GroupView& g, const double2* v, const double2* e, cudaStream_t st, int sprev = -1);
 bool step_eo_supported(const GroupView& g);
 size_t forcing_eo_smem_bytes(const GroupView& g);
 size_t helm_eo_smem_bytes(const GroupView& g);

@@ -1,9 +1,10 @@
 // The step-by-step per-wavenumber stage of the mixed path in parity blocks
-// (eo.cuh): the forcing (Eqs. Dv, eta: D1 phi) and the implicit apply
-// (increment form of Eqs. CN1, CN2: (M - I) x_t + P F~), each product as the
-// even and odd halves of its operator, half the operator bytes and
-// multiply-adds of the natural-order kernels (k_gemm_f32.cu: k_forcing_t,
-// k_helm_t), whose tiles, work items and epilogues these follow.  The state,
+// (eo.cuh): the y-derivatives (Dv, D2v, D eta, Sec. 3.1), the forcing (Eqs.
+// Dv, eta: D1 phi) and the implicit apply (increment form of Eqs. CN1, CN2:
+// (M - I) x_t + P F~), each product as the even and odd halves of its
+// operator, half the operator bytes and multiply-adds of the natural-order
+// kernels (k_gemm_f32.cu: k_yderiv_t, k_forcing_t, k_helm_t), whose tiles,
+// work items and epilogues these follow.  The state,
 // forcings and accumulators stay in the natural order in global memory; the
 // staging converts the two natural rows of each pair-row into parity parts and
 // every task converts its products back.
@@ -36,6 +37,175 @@ __device__ __forceinline__ bool waitp(unsigned bar, unsigned parity) {
         if (done) return true;
     }
     return false;
+}
+
+// ----------------------------------------------------------- y-derivatives
+
+// Column tile of the y-derivatives in parity blocks: tile_of's, with fewer
+// columns while the shared memory (D1, D2 and its residual in parity blocks,
+// three vectors) would pass YDE_SMEM_MAX.
+constexpr size_t YDE_SMEM_MAX = 200 * 1024;
+__host__ __device__ inline size_t yde_bytes(int ny, int nc) {
+    return (3 * spc::eo_mat(ny) + 3 * (size_t)ny * 2 * nc) * sizeof(float);
+}
+__host__ __device__ inline gt::Tile yde_tile(int E, int ny, int nm, int cap0) {
+    gt::Tile t = gt::tile_of(E, ny, nm, cap0);
+    while (yde_bytes(ny, t.NC) > YDE_SMEM_MAX && t.NC > 4) {
+        if (t.QT > 1) t.QT /= 2;
+        else t.EBT = (t.EBT + 1) / 2;
+        t.NC = t.QT * t.EBT;
+    }
+    return t;
+}
+
+// Dv, D2v, D eta of a column tile (k_yderiv_t's tile and output): v staged as
+// the float-float even and odd parts of the FP64 state, eta as single-precision
+// sums; D1 (anti-centro-symmetric) maps the odd part to the even output rows
+// and the even part to the odd ones, D2 (centro-symmetric, float-float with its
+// residual) maps each part to its own.  Tasks: two pair-rows x one complex
+// column.  Grid rows from (E + EBT - 1) / EBT on finish the previous sub-step's
+// mean flow (one CTA per member).
+__global__ void __launch_bounds__(THREADS) k_yderiv_eo(GroupView g, const double2* __restrict__ V,
+                                                      const double2* __restrict__ H, int sprev) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    const int Ny = g.ny, E = g.E, NM = g.nmodes;
+    const gt::Tile T = yde_tile(E, Ny, NM, g.yd_cap);
+    if (mean_finish_rows(g, sprev, (E + T.EBT - 1) / T.EBT, sm)) return;
+    const int NE = (Ny + 1) / 2, NO = Ny / 2, RP2 = spc::eo_rp(Ny), RB2 = (NE + 1) / 2;
+    const size_t MEO = spc::eo_mat(Ny);
+    const int q0 = blockIdx.x * T.QT, e0 = blockIdx.y * T.EBT;
+    const int NCR = 2 * T.NC;
+    float* D1 = (float*)sm;                       // D1 in parity blocks
+    float* D2 = D1 + MEO;                         // D2
+    float* D2l = D2 + MEO;                        // its residual
+    float* Xh = D2l + MEO;                        // v parts, high [Ny][NCR]
+    float* Xl = Xh + (size_t)Ny * NCR;            // v parts, low
+    float* Xe = Xl + (size_t)Ny * NCR;            // eta parts
+    const size_t fs = (size_t)Ny * E * NM;
+    float2* P = (float2*)g.P5;
+    {
+        const float4* s1 = (const float4*)g.D1EO;
+        const float4* s2 = (const float4*)g.D2EO;
+        const float4* s3 = (const float4*)g.D2lEO;
+        for (int i = threadIdx.x; i < (int)(MEO / 4); i += THREADS) {
+            ((float4*)D1)[i] = s1[i];
+            ((float4*)D2)[i] = s2[i];
+            ((float4*)D2l)[i] = s3[i];
+        }
+        // state tile, read in H order [q][y][e] (consecutive threads: consecutive
+        // members), both natural rows of a pair-row per thread; v and eta in single
+        // precision into their planes of the P layout
+        const int per_q = NE * T.EBT;
+        const FastDiv dPQ((unsigned)per_q), dEB((unsigned)T.EBT);
+        for (int i = threadIdx.x; i < T.QT * per_q; i += THREADS) {
+            const int qq = (int)dPQ.div((unsigned)i), r = i - qq * per_q;
+            const int p = (int)dEB.div((unsigned)r), el = r - p * T.EBT;
+            const int q = q0 + qq, e = e0 + el;
+            const EoRows R = eo_rows(p, Ny);
+            double2 a[2] = {make_double2(0.0, 0.0), make_double2(0.0, 0.0)}, b[2] = {a[0], a[1]};
+            if (q < NM && e < E && DNS_CK(g.status, R.y1 < Ny, CK_YDERIV_T, i)) {
+#pragma unroll
+                for (int k2 = 0; k2 < 2; ++k2) {
+                    if (k2 && !R.pair) continue;
+                    const int y = k2 ? R.y1 : R.y0;
+                    const size_t oh = ((size_t)q * Ny + y) * E + e, op = ((size_t)y * E + e) * NM + q;
+                    a[k2] = V[oh];
+                    b[k2] = H[oh];
+                    P[op] = make_float2(d2f(a[k2].x), d2f(a[k2].y));
+                    P[3 * fs + op] = make_float2(d2f(b[k2].x), d2f(b[k2].y));
+                }
+            }
+            const int c = 2 * (el * T.QT + qq);
+            float2 he, le, ho, lo;
+            spc::eo_ff(a[0].x, a[1].x, he.x, le.x, ho.x, lo.x);
+            spc::eo_ff(a[0].y, a[1].y, he.y, le.y, ho.y, lo.y);
+            const float2 h0 = make_float2(d2f(b[0].x), d2f(b[0].y)), h1 = make_float2(d2f(b[1].x), d2f(b[1].y));
+            *(float2*)&Xh[p * NCR + c] = he;
+            *(float2*)&Xl[p * NCR + c] = le;
+            *(float2*)&Xe[p * NCR + c] = make_float2(h0.x + h1.x, h0.y + h1.y);
+            if (R.pair) {
+                *(float2*)&Xh[(NE + p) * NCR + c] = ho;
+                *(float2*)&Xl[(NE + p) * NCR + c] = lo;
+                *(float2*)&Xe[(NE + p) * NCR + c] = make_float2(h0.x - h1.x, h0.y - h1.y);
+            }
+        }
+    }
+    __syncthreads();
+    const FastDiv dNC((unsigned)T.NC), dQT((unsigned)T.QT);
+    // the odd-output block of D1 (after its NO even-output rows), the odd-output
+    // block of D2 and its residual (after their NE even-output rows)
+    const float* D1o = D1 + (size_t)NO * RP2;
+    const float* D2o = D2 + (size_t)NE * RP2;
+    const float* D2lo = D2l + (size_t)NE * RP2;
+    for (int m = threadIdx.x; m < RB2 * T.NC; m += THREADS) {
+        const int rb = (int)dNC.div((unsigned)m), j = m - rb * T.NC;   // consecutive threads: consecutive q
+        const int p0 = 2 * rb, c2 = 2 * j;
+        float d1o[2][2] = {{0.f, 0.f}, {0.f, 0.f}}, f1o[2][2] = {{0.f, 0.f}, {0.f, 0.f}};   // D1 v, D1 eta: odd rows
+        float d1e[2][2] = {{0.f, 0.f}, {0.f, 0.f}}, f1e[2][2] = {{0.f, 0.f}, {0.f, 0.f}};   // even rows
+        float beh[2][2] = {{0.f, 0.f}, {0.f, 0.f}}, bel[2][2] = {{0.f, 0.f}, {0.f, 0.f}};   // D2 v even rows
+        float boh[2][2] = {{0.f, 0.f}, {0.f, 0.f}}, bol[2][2] = {{0.f, 0.f}, {0.f, 0.f}};   // D2 v odd rows
+        // the even parts: D1's odd-output block, D2's even-output block
+#pragma unroll 2
+        for (int k = 0; k < NE; ++k) {
+            const float2 b1 = *(const float2*)&D1o[k * RP2 + p0];
+            const float2 b2 = *(const float2*)&D2[k * RP2 + p0];
+            const float2 b2l = *(const float2*)&D2l[k * RP2 + p0];
+            const float2 x = *(const float2*)&Xh[k * NCR + c2];
+            const float2 xl = *(const float2*)&Xl[k * NCR + c2];
+            const float2 h = *(const float2*)&Xe[k * NCR + c2];
+            const float bb1[2] = {b1.x, b1.y}, bb2[2] = {b2.x, b2.y}, bbl[2] = {b2l.x, b2l.y};
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                d1o[r][0] += bb1[r] * x.x; d1o[r][1] += bb1[r] * x.y;
+                f1o[r][0] += bb1[r] * h.x; f1o[r][1] += bb1[r] * h.y;
+                ff_add_prod2(beh[r][0], bel[r][0], bb2[r], x.x, bbl[r], xl.x);
+                ff_add_prod2(beh[r][1], bel[r][1], bb2[r], x.y, bbl[r], xl.y);
+            }
+        }
+        // the odd parts: D1's even-output block, D2's odd-output block
+#pragma unroll 2
+        for (int k = 0; k < NO; ++k) {
+            const float2 b1 = *(const float2*)&D1[k * RP2 + p0];
+            const float2 b2 = *(const float2*)&D2o[k * RP2 + p0];
+            const float2 b2l = *(const float2*)&D2lo[k * RP2 + p0];
+            const float2 x = *(const float2*)&Xh[(NE + k) * NCR + c2];
+            const float2 xl = *(const float2*)&Xl[(NE + k) * NCR + c2];
+            const float2 h = *(const float2*)&Xe[(NE + k) * NCR + c2];
+            const float bb1[2] = {b1.x, b1.y}, bb2[2] = {b2.x, b2.y}, bbl[2] = {b2l.x, b2l.y};
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                d1e[r][0] += bb1[r] * x.x; d1e[r][1] += bb1[r] * x.y;
+                f1e[r][0] += bb1[r] * h.x; f1e[r][1] += bb1[r] * h.y;
+                ff_add_prod2(boh[r][0], bol[r][0], bb2[r], x.x, bbl[r], xl.x);
+                ff_add_prod2(boh[r][1], bol[r][1], bb2[r], x.y, bbl[r], xl.y);
+            }
+        }
+        const int el = (int)dQT.div((unsigned)j), qq = j - el * T.QT;
+        const int q = q0 + qq, e = e0 + el;
+        if (q >= NM || e >= E) continue;
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            const int p = p0 + r;
+            if (p >= NE) break;
+            const EoRows R = eo_rows(p, Ny);
+            const float ve[2] = {__fadd_rn(beh[r][0], bel[r][0]), __fadd_rn(beh[r][1], bel[r][1])};
+            const float vo[2] = {__fadd_rn(boh[r][0], bol[r][0]), __fadd_rn(boh[r][1], bol[r][1])};
+#pragma unroll
+            for (int k2 = 0; k2 < 2; ++k2) {
+                if (k2 && !R.pair) continue;
+                const int y = k2 ? R.y1 : R.y0;
+                if (!DNS_CK(g.status, 2 * j + 1 < NCR, CK_YDERIV_T, q)) continue;
+                const float sg = k2 ? -1.f : 1.f;
+                const size_t o = ((size_t)y * E + e) * NM + q;
+                P[fs + o] = R.pair ? make_float2(0.5f * (d1e[r][0] + sg * d1o[r][0]), 0.5f * (d1e[r][1] + sg * d1o[r][1]))
+                                   : make_float2(d1e[r][0], d1e[r][1]);
+                P[2 * fs + o] = R.pair ? make_float2(0.5f * (ve[0] + sg * vo[0]), 0.5f * (ve[1] + sg * vo[1]))
+                                       : make_float2(ve[0], ve[1]);
+                P[4 * fs + o] = R.pair ? make_float2(0.5f * (f1e[r][0] + sg * f1o[r][0]), 0.5f * (f1e[r][1] + sg * f1o[r][1]))
+                                       : make_float2(f1e[r][0], f1e[r][1]);
+            }
+        }
+    }
 }
 
 // ---------------------------------------------------------------- forcing
@@ -346,7 +516,25 @@ void launch_helm_eo(const GroupView& g, int s, cudaStream_t st) {
                      st>>>(g, s);
 }
 
+size_t yderiv_eo_smem_bytes(const GroupView& g) {
+    const gt::Tile t = sto::yde_tile(g.E, g.ny, g.nmodes, g.yd_cap);
+    const size_t b = sto::yde_bytes(g.ny, t.NC), m = mean_smem_bytes(g);
+    return b > m ? b : m;
+}
+
+// the y-derivatives in parity blocks (D1 and D2 have the reflection symmetry on
+// every group's interior grid, linear groups included)
+bool yderiv_eo_supported(const GroupView& g) { return g.ny >= 3 && yderiv_eo_smem_bytes(g) <= 227 * 1024; }
+
+void launch_yderiv_eo(const GroupView& g, const double2* v, const double2* e, cudaStream_t st, int sprev) {
+    const gt::Tile t = sto::yde_tile(g.E, g.ny, g.nmodes, g.yd_cap);
+    dim3 grid((g.nmodes + t.QT - 1) / t.QT, (g.E + t.EBT - 1) / t.EBT);
+    grid.y += mean_finish_extra_rows(g, grid.x, sprev);
+    sto::k_yderiv_eo<<<grid, sto::THREADS, yderiv_eo_smem_bytes(g), st>>>(g, v, e, sprev);
+}
+
 void set_attributes_step_eo() {
+    allow_max_dynamic_smem(sto::k_yderiv_eo);
     allow_max_dynamic_smem(sto::k_forcing_eo);
     allow_max_dynamic_smem(sto::k_helm_eo);
 }

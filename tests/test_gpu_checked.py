@@ -38,6 +38,8 @@ CASES = [
                            members=3)], "mixed", dict(helm="fused_eo"), 3, None),
     ("fused_floatfloat", [dict(flow="poiseuille", mx=32, my=97, mz=16, lx=2 * np.pi, lz=np.pi, re=1650.0, dt=0.005,
                                members=2)], "mixed", dict(helm="fused"), 3, None),
+    ("yderiv_parity", [dict(flow="poiseuille", mx=32, my=34, mz=16, lx=2 * np.pi, lz=np.pi, re=1650.0, dt=0.005,
+                            members=5)], "mixed", dict(helm="simt", ygemm="simt_eo"), 3, None),
     ("step_parity", [dict(flow="couette", mx=16, my=21, mz=16, lx=2 * np.pi, lz=np.pi, re=400.0, dt=0.005,
                           members=3)], "mixed", dict(helm="simt_eo"), 3, (1, 2, 1e-3, 5)),
     ("chain_tc", [dict(flow="couette", mx=32, my=49, mz=32, lx=1.75 * np.pi, lz=1.2 * np.pi, re=500.0, dt=0.01,

@@ -17,7 +17,7 @@ if not torch.cuda.is_available():  # pragma: no cover
 import paper_2306_12739_gb300 as dns  # noqa: E402
 
 PINS = (dict(ygemm="simt", helm="simt"), dict(ygemm="tc", helm="simt"), dict(ygemm="simt", helm="tc"),
-        dict(ygemm="tc", helm="tc"), dict(ygemm="tc", helm="persist"))
+        dict(ygemm="tc", helm="tc"), dict(ygemm="tc", helm="persist"), dict(ygemm="simt_eo", helm="simt"))
 
 
 def lgroup(my, mz, lz, re, dt, n, E):
@@ -149,7 +149,7 @@ def test_optimal_sweeps_of_two_wavenumbers_match_the_oracle(use_graph):
         ens.close()
 
 
-@pytest.mark.parametrize("pin", PINS, ids=["simt", "tc_ygemm", "tc_helm", "tc_both", "persist_helm"])
+@pytest.mark.parametrize("pin", PINS, ids=["simt", "tc_ygemm", "tc_helm", "tc_both", "persist_helm", "eo_ygemm"])
 def test_linear_mixed_matches_fp64_over_50_steps(pin):
     my, mz, lz, re, dt, n, E = 65, 64, np.pi, 3000.0, 0.04, 1, 6
     b, d = _case(my, mz, lz, n, E, 5)

@@ -369,7 +369,7 @@ def test_autotuner_picks_a_variant_caches_it_and_matches_that_variant(tmp_path):
     choice = dns.dns_kernel_choice(ens.h, 0)
     plane = dns.dns_kernel_choice(ens.h, 0, "plane")
     helm = dns.dns_kernel_choice(ens.h, 0, "helm")
-    assert choice in ("simt", "tc") and plane in ("cta", "lines") and helm in ("simt", "tc", "fused", "fused_d2v",
+    assert choice in ("simt", "tc", "simt_eo") and plane in ("cta", "lines") and helm in ("simt", "tc", "fused", "fused_d2v",
                                                                                  "fused_eo", "fused_eo_ff", "simt_eo")
     assert helm not in ("fused", "fused_d2v", "fused_eo", "fused_eo_ff") or choice == "simt"
     ens.set_state(0, st["v"], st["eta"], st["U"], st["W"])
@@ -381,7 +381,7 @@ def test_autotuner_picks_a_variant_caches_it_and_matches_that_variant(tmp_path):
     # keyed by the member block's size: 8 members run as 2 blocks of 4, tuned once;
     # the tile shapes: the fused stage's members per CTA, the y-derivative tile
     assert all(ln.split()[1:5] == ["32", "33", "32", "4"] for ln in lines)
-    want = {"helm", "plane", "ygemm"} | ({"ytile"} if choice == "simt" else set()) | \
+    want = {"helm", "plane", "ygemm"} | ({"ytile"} if choice in ("simt", "simt_eo") else set()) | \
         ({"spec_ec"} if helm in ("fused", "fused_d2v", "fused_eo", "fused_eo_ff") else set()) | \
         ({"spec_cta"} if helm in ("fused_eo", "fused_eo_ff") else set())
     assert sorted(keys) == sorted(want)
@@ -844,6 +844,35 @@ def test_step_by_step_stage_in_parity_blocks_matches_fp64_and_the_natural_order_
     assert np.all(err[:, :3] < 1e-6), err
     assert np.all(err[:, 3] < 3e-5), err
     assert np.all(mixed_errors(par, nat)[:, :3] < 1e-6)
+
+
+@pytest.mark.parametrize("flow,mx,my,mz,E,extra", [
+    ("couette", 32, 49, 32, 6, {}),
+    ("poiseuille", 16, 21, 48, 20, dict(member_block=20)),      # one block of 20
+    ("couette", 48, 49, 48, 3, dict(form="rotational")),
+    ("couette", 16, 7, 16, 3, {}),                              # Ny = 5
+    ("poiseuille", 32, 34, 16, 2, {}),                          # even Ny: no centre row
+    ("poiseuille", 32, 97, 16, 4, {}),                          # Ny = 95
+])
+def test_y_derivatives_in_parity_blocks_match_fp64_and_the_natural_order_kernel(flow, mx, my, mz, E, extra):
+    """The register-tiled y-derivatives in parity blocks (D1 and D2 as their
+    even and odd halves, D2 v in float-float from the float-float parts of the
+    FP64 state), in the step-by-step stage with either apply, against the FP64
+    step over 20 steps (1e-6 per field and member, W00 on its own scale at
+    3e-5) and against the natural-order kernel (within the budget)."""
+    g = dict(group(flow, mx, my, mz, 2 * np.pi, np.pi, 1650.0 if flow == "poiseuille" else 400.0, 0.005, E), **extra)
+    st = _state(g, 95, 5e-2)
+    ens = dns.Ensemble([g], precision="mixed", ygemm="simt_eo", helm="simt")
+    assert dns.dns_kernel_choice(ens.h, 0, "ygemm") == "simt_eo"
+    ens.close()
+    ref = _run(g, st, 20, "fp64")
+    nat = _run(g, st, 20, "mixed", use_graph=True, ygemm="simt", helm="simt")
+    for helm in ("simt", "simt_eo"):
+        par = _run(g, st, 20, "mixed", use_graph=True, ygemm="simt_eo", helm=helm)
+        err = mixed_errors(par, ref)
+        assert np.all(err[:, :3] < 1e-6), (helm, err)
+        assert np.all(err[:, 3] < 3e-5), (helm, err)
+        assert np.all(mixed_errors(par, nat)[:, :3] < 1e-6), helm
 
 
 def test_step_by_step_stage_in_parity_blocks_keeps_members_independent():
