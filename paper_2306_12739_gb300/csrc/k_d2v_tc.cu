@@ -144,9 +144,9 @@ __global__ void __launch_bounds__(THREADS, 2) k_d2v_tc(GroupView g, const double
     __shared__ int ok_flag;
     if (warp == 0) {
         int mine = 1;
-        if (lane < NLEV) mine = waitp(bar_a, 0) ? 1 : 0;
+        if (lane < NLEV) mine = mbar_wait(bar_a, 0) ? 1 : 0;
         int good = __all_sync(0xffffffffu, mine);
-        if (!good && lane == 0) waitp(bar_a, 0);   // one more bounded wait: no copy left in flight
+        if (!good && lane == 0) mbar_wait(bar_a, 0);   // one more bounded wait: no copy left in flight
         if (good && lane < NLEV) {
             const unsigned idesc = idesc_bf16(MROWS, NCOL);
             const int KS = KP / 16, L = lane;
@@ -166,8 +166,8 @@ __global__ void __launch_bounds__(THREADS, 2) k_d2v_tc(GroupView g, const double
         __syncwarp();
         if (lane == 0) {
             if (good) {
-                good = waitp(bar_m, 0) ? 1 : 0;
-                if (!good) waitp(bar_m, 0);       // do not release TMEM under running MMAs
+                good = mbar_wait(bar_m, 0) ? 1 : 0;
+                if (!good) mbar_wait(bar_m, 0);       // do not release TMEM under running MMAs
             }
             ok_flag = good;
         }

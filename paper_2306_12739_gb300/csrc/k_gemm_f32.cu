@@ -10,6 +10,7 @@
 //               (increment form of Eqs. CN1, CN2); the pair's operators arrive
 //               by one TMA bulk copy (cp.async.bulk + mbarrier) per CTA.
 #include "dns_internal.hpp"
+#include "mbar.cuh"
 #include "cvt.cuh"
 #include "ff.cuh"
 #include "mean.cuh"
@@ -269,23 +270,6 @@ __global__ void __launch_bounds__(THREADS) k_forcing_t(GroupView g, int s) {
 
 // ------------------------------------------------------------------- helm
 
-__device__ __forceinline__ unsigned smem_u32(const void* p) {
-    return (unsigned)__cvta_generic_to_shared(p);
-}
-
-// Bounded wait on phase 0 of an mbarrier; false if it did not complete.
-__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
-    for (int it = 0; it < (1 << 22); ++it) {
-        unsigned done;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(done) : "r"(bar), "r"(parity) : "memory");
-        if (done) return true;
-    }
-    return false;
-}
-__device__ __forceinline__ bool mbar_wait0(unsigned bar) { return mbar_wait(bar, 0); }
-
 // x_t (single precision, needM only) and F~ of the item's modes and members
 // into shared memory, [Ny][NC]
 __device__ __forceinline__ void helm_stage(const GroupView& g, const HelmItem& it, bool needM, float* Xs, float* Fs) {
@@ -404,7 +388,7 @@ __device__ __forceinline__ void helm_issue(const GroupView& g, int s, const Helm
     float* to = needM ? dst : dst + mat;
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                 ::"r"(smem_u32(to)), "l"(from), "r"(bytes), "r"(bar) : "memory");
+                 ::"r"(su32(to)), "l"(from), "r"(bytes), "r"(bar) : "memory");
 }
 
 // one CTA per (pair, field, member chunk)
@@ -428,7 +412,7 @@ __global__ void __launch_bounds__(THREADS, 3) k_helm_t(GroupView g, int s) {
     float* Xs = PT + mat;                         // [Ny][NC]
     float* Fs = Xs + (size_t)Ny * it.NC;          // [Ny][NC]
     unsigned long long* bar = (unsigned long long*)(Fs + (size_t)Ny * it.NC + 2);
-    const unsigned bar_a = smem_u32(bar);
+    const unsigned bar_a = su32(bar);
     if (threadIdx.x == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_a) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -471,7 +455,7 @@ __global__ void __launch_bounds__(THREADS, 3) k_helm_tp(GroupView g, int s) {
     float* Xs = OP1 + 2 * mat;
     float* Fs = Xs + (size_t)Ny * 4 * helm_member_chunk(g);
     unsigned long long* bars = (unsigned long long*)(Fs + (size_t)Ny * 4 * helm_member_chunk(g) + 2);
-    const unsigned bar0 = smem_u32(bars), bar1 = smem_u32(bars + 1);
+    const unsigned bar0 = su32(bars), bar1 = su32(bars + 1);
     auto decode = [&](int t) {
         const int p = p0 + t % npv, f = (t / npv) & 1, ch = t / (2 * npv);
         return helm_item(g, p, f, ch);
@@ -513,13 +497,13 @@ __global__ void __launch_bounds__(THREADS, 3) k_helm_tp(GroupView g, int s) {
 // never comes.  The wait gives up after its iteration limit and latches status.
 __global__ void k_wait_selftest(int* status) {
     __shared__ unsigned long long bar;
-    const unsigned b = smem_u32(&bar);
+    const unsigned b = su32(&bar);
     if (threadIdx.x == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    if (!mbar_wait0(b) && threadIdx.x == 0) atomicExch(status, 2);
+    if (!mbar_wait(b, 0) && threadIdx.x == 0) atomicExch(status, 2);
 }
 
 }  // namespace gt

@@ -19,6 +19,7 @@
 // mbarrier wait is bounded; on a timeout the CTA latches the status word,
 // waits once more for what it issued, releases its TMEM and leaves.
 #include "dns_internal.hpp"
+#include "mbar.cuh"
 #include "cvt.cuh"
 #include "mean.cuh"
 #include <cuda_bf16.h>
@@ -32,19 +33,6 @@ namespace htc {
 constexpr int THREADS = 256;
 constexpr int MROWS = 128;     // MMA rows (64 used)
 constexpr int NPMAX = 128;     // columns per pass
-
-__device__ __forceinline__ unsigned su32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ bool waitp(unsigned bar, unsigned parity) {
-    for (int it = 0; it < (1 << 22); ++it) {
-        unsigned done;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(done) : "r"(bar), "r"(parity) : "memory");
-        if (done) return true;
-    }
-    return false;
-}
 
 // Shared-memory matrix descriptor, no swizzle, K-major core matrices (8 rows x
 // 16 bytes): LBO = distance between core matrices along K, SBO = between
@@ -237,8 +225,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_helm_tc(GroupView g, int s) {
         if (threadIdx.x == 0) {
             int good = 1;
             if (pass == 0) {
-                good = waitp(bar_a, 0) ? 1 : 0;
-                if (!good) waitp(bar_a, 0);           // one more bounded wait: no copy left in flight
+                good = mbar_wait(bar_a, 0) ? 1 : 0;
+                if (!good) mbar_wait(bar_a, 0);           // one more bounded wait: no copy left in flight
             }
             if (good) {
                 const unsigned idesc = idesc_bf16(MROWS, G.NP);
@@ -266,8 +254,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_helm_tc(GroupView g, int s) {
                              ::"r"(bar_m) : "memory");
                 // thread 0 waits for the MMAs; the barrier below hands the result
                 // (and the completed accumulators) to every thread
-                good = waitp(bar_m, (unsigned)(pass & 1)) ? 1 : 0;
-                if (!good) waitp(bar_m, (unsigned)(pass & 1));   // do not touch B or TMEM under running MMAs
+                good = mbar_wait(bar_m, (unsigned)(pass & 1)) ? 1 : 0;
+                if (!good) mbar_wait(bar_m, (unsigned)(pass & 1));   // do not touch B or TMEM under running MMAs
             }
             ok_flag = good;
         }

@@ -34,6 +34,7 @@
 // computes D v, and four warps read the six levels back from TMEM.  A sub-step
 // is then two launches per member block (plane stage, this one).
 #include "dns_internal.hpp"
+#include "mbar.cuh"
 #include "cvt.cuh"
 #include "ff.cuh"
 #include "mean.cuh"
@@ -89,19 +90,6 @@ __host__ __device__ inline size_t smem_bytes(const GroupView& g) {
 __host__ __device__ inline bool fused_d2_fits(const GroupView& g) {
     const size_t slot = slot_floats(g) * sizeof(float), sa = (size_t)64 * g.kp * 2;
     return 3 * slot + 3 * sa <= smem_bytes(g) && 6 * (size_t)DCOL * g.kp * 2 <= slot;
-}
-
-__device__ __forceinline__ unsigned su32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ bool waitp(unsigned bar, unsigned parity) {
-    for (int it = 0; it < (1 << 22); ++it) {
-        unsigned done;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(done) : "r"(bar), "r"(parity) : "memory");
-        if (done) return true;
-    }
-    return false;
 }
 
 __device__ __forceinline__ void bulk(void* dst, const void* src, unsigned bytes, unsigned bar) {
@@ -434,10 +422,10 @@ __global__ void __launch_bounds__(THREADS, 2) k_spec(GroupView g, int s) {
     __syncthreads();
     // every thread waits for the operators (bounded); on a timeout the CTA
     // latches the status word, waits once more for the copy and leaves
-    if (!__syncthreads_and(waitp(bar_a, 0))) {
+    if (!__syncthreads_and(mbar_wait(bar_a, 0))) {
         if (tid == 0) {
             atomicExch(g.status, 1);
-            waitp(bar_a, 0);
+            mbar_wait(bar_a, 0);
         }
         return;
     }
@@ -569,10 +557,10 @@ __global__ void __launch_bounds__(THREADS, 2) k_spec(GroupView g, int s) {
     }
     __syncthreads();
 
-    if (!__syncthreads_and(!d2here || waitp(bar_d, 0))) {
+    if (!__syncthreads_and(!d2here || mbar_wait(bar_d, 0))) {
         if (tid == 0) {
             atomicExch(g.status, 1);
-            waitp(bar_d, 0);
+            mbar_wait(bar_d, 0);
         }
         return;
     }
@@ -638,8 +626,8 @@ __global__ void __launch_bounds__(THREADS, 2) k_spec(GroupView g, int s) {
         __syncthreads();
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         if (tid == 0) {
-            int good = waitp(bar_d, 0) ? 1 : 0;
-            if (!good) waitp(bar_d, 0);                   // one more bounded wait: no copy left in flight
+            int good = mbar_wait(bar_d, 0) ? 1 : 0;
+            if (!good) mbar_wait(bar_d, 0);                   // one more bounded wait: no copy left in flight
             if (good) {
                 const unsigned tmem = *tslot;
                 const unsigned idesc = oz::idesc_bf16(oz::MROWS, DCOL);
@@ -725,8 +713,8 @@ __global__ void __launch_bounds__(THREADS, 2) k_spec(GroupView g, int s) {
         if (tid == 0) {
             int good = *dok;
             if (good) {
-                good = waitp(bar_m, 0) ? 1 : 0;
-                if (!good) waitp(bar_m, 0);               // do not release TMEM under running MMAs
+                good = mbar_wait(bar_m, 0) ? 1 : 0;
+                if (!good) mbar_wait(bar_m, 0);               // do not release TMEM under running MMAs
             }
             *dok = good;
         }
@@ -761,7 +749,6 @@ __global__ void __launch_bounds__(THREADS, 2) k_spec(GroupView g, int s) {
             asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(DTCOLS) : "memory");
     }
 }
-
 
 // ============================================================================
 // The fused stage in parity blocks (k_spec_eo).  On the symmetric Chebyshev
@@ -936,10 +923,10 @@ __global__ void __launch_bounds__(THREADS, MINB) k_spec_eo(GroupView g, int s) {
     __syncthreads();
     // every thread waits for the operators (bounded); on a timeout the CTA
     // latches the status word, waits once more for the copy and leaves
-    if (!__syncthreads_and(waitp(bar_a, 0))) {
+    if (!__syncthreads_and(mbar_wait(bar_a, 0))) {
         if (tid == 0) {
             atomicExch(g.status, 1);
-            waitp(bar_a, 0);
+            mbar_wait(bar_a, 0);
         }
         return;
     }
@@ -1170,10 +1157,10 @@ __global__ void __launch_bounds__(THREADS, MINB) k_spec_eo(GroupView g, int s) {
     __syncthreads();
 
     if (D2FF) {
-        if (!__syncthreads_and(waitp(bar_d, 0))) {
+        if (!__syncthreads_and(mbar_wait(bar_d, 0))) {
             if (tid == 0) {
                 atomicExch(g.status, 1);
-                waitp(bar_d, 0);
+                mbar_wait(bar_d, 0);
             }
             return;
         }
@@ -1291,10 +1278,10 @@ __global__ void __launch_bounds__(THREADS, 2) k_eo_derivs(GroupView g) {
         }
     }
     __syncthreads();
-    if (!__syncthreads_and(waitp(bar_a, 0))) {
+    if (!__syncthreads_and(mbar_wait(bar_a, 0))) {
         if (tid == 0) {
             atomicExch(g.status, 1);
-            waitp(bar_a, 0);
+            mbar_wait(bar_a, 0);
         }
         return;
     }

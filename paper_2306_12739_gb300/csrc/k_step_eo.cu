@@ -9,6 +9,7 @@
 // staging converts the two natural rows of each pair-row into parity parts and
 // every task converts its products back.
 #include "dns_internal.hpp"
+#include "mbar.cuh"
 #include "cvt.cuh"
 #include "ff.cuh"
 #include "mean.cuh"
@@ -25,19 +26,6 @@ using spc::eo_rows;
 using spc::EoRows;
 
 constexpr int THREADS = 256;
-
-__device__ __forceinline__ unsigned su32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ bool waitp(unsigned bar, unsigned parity) {
-    for (int it = 0; it < (1 << 22); ++it) {
-        unsigned done;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(done) : "r"(bar), "r"(parity) : "memory");
-        if (done) return true;
-    }
-    return false;
-}
 
 // ----------------------------------------------------------- y-derivatives
 
@@ -473,11 +461,11 @@ __global__ void __launch_bounds__(THREADS, 3) k_helm_eo(GroupView g, int s) {
     }
     stage_eo(g, it, needM, Xs, Fs);
     __syncthreads();
-    if (!waitp(bar_a, 0)) {
+    if (!mbar_wait(bar_a, 0)) {
         // the operator copy did not land: flag it, give the copy one more bounded
         // wait so no write into this CTA's shared memory is left in flight, leave
         if (threadIdx.x == 0) atomicExch(g.status, 1);
-        waitp(bar_a, 0);
+        mbar_wait(bar_a, 0);
         return;
     }
     compute_eo(g, s, it, MS, PS, Xs, Fs);

@@ -16,6 +16,7 @@
 // a timeout the kernel latches the status word, still releases its TMEM, and
 // leaves.
 #include "dns_internal.hpp"
+#include "mbar.cuh"
 #include "mean.cuh"
 #include <cuda_bf16.h>
 #include <cstring>
@@ -30,19 +31,6 @@ constexpr int THREADS = 256;          // 8 warps; warp w reads TMEM lanes 32 (w 
 // half of v, half of eta; NCOL / 4 complex columns per field.  The narrow tile
 // doubles the CTAs where the wide one would leave most SMs idle.
 constexpr int MROWS = 128;
-
-__device__ __forceinline__ unsigned su32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ bool wait0(unsigned bar) {
-    for (int it = 0; it < (1 << 22); ++it) {
-        unsigned done;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(done) : "r"(bar), "r"(0) : "memory");
-        if (done) return true;
-    }
-    return false;
-}
 
 // Shared-memory matrix descriptor, no swizzle, K-major core matrices
 // (8 rows x 16 bytes each, rows 16 bytes apart): LBO = distance between core
@@ -203,8 +191,8 @@ __global__ void __launch_bounds__(THREADS, 2) k_yderiv_tc(GroupView g, const dou
     const unsigned tmem = *tslot;
     __shared__ int ok_flag;
     if (threadIdx.x == 0) {
-        int ok = wait0(bar_a) ? 1 : 0;
-        if (!ok) wait0(bar_a);          // one more bounded wait: no copy left in flight
+        int ok = mbar_wait(bar_a, 0) ? 1 : 0;
+        if (!ok) mbar_wait(bar_a, 0);          // one more bounded wait: no copy left in flight
         if (ok) {
             const unsigned idesc = idesc_bf16(MROWS, NCOL);
             // piece pairs (a, b) by increasing magnitude: l h, h l, m m, m h, h m, h h
@@ -225,8 +213,8 @@ __global__ void __launch_bounds__(THREADS, 2) k_yderiv_tc(GroupView g, const dou
     __syncthreads();
     bool ok = ok_flag != 0;
     if (ok) {
-        ok = wait0(bar_m);
-        if (!ok) wait0(bar_m);          // do not release TMEM under running MMAs
+        ok = mbar_wait(bar_m, 0);
+        if (!ok) mbar_wait(bar_m, 0);          // do not release TMEM under running MMAs
     }
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (ok) {

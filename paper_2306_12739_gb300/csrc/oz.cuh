@@ -13,6 +13,7 @@
 #pragma once
 #include <cstdint>
 #include "ff.cuh"
+#include "mbar.cuh"
 
 namespace dnsk {
 namespace oz {
@@ -24,19 +25,6 @@ constexpr int MROWS = 128;          // MMA M: 64 rows of D2 used, the rest never
 
 // one digit slice of D2's image: 64 rows x KP, BF16 (bytes)
 __host__ __device__ inline size_t slice_a(int KP) { return (size_t)64 * KP * 2; }
-
-__device__ __forceinline__ unsigned su32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ bool waitp(unsigned bar, unsigned parity) {
-    for (int it = 0; it < (1 << 22); ++it) {
-        unsigned done;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(done) : "r"(bar), "r"(parity) : "memory");
-        if (done) return true;
-    }
-    return false;
-}
 
 // shared-memory matrix descriptor, no swizzle, K-major core matrices (8 rows x
 // 16 bytes): LBO between core matrices along K, SBO between 8-row groups
