@@ -278,7 +278,16 @@ typedef struct {
  * nsteps CN/RK3 steps run, and
  * the result is written to out[group] (out == NULL: nothing is read back).
  * Same results, bit for bit, as dns_set_state for every group, dns_step and
- * dns_get_state for every group; the difference is scheduling.  When every
+ * dns_get_state for every group; the difference is scheduling.  One exception:
+ * on a member block whose stage the autotuner set to the fused per-wavenumber
+ * stage (helm 0 in the config, decided 4-7), a call of at most 2 steps on the
+ * direct path (captured whole, or eager) runs the block's step-by-step stage in
+ * parity blocks (helm 8 with the tuned ygemm), which needs no derivatives of the
+ * uploaded state, where the group's measured whole-step time on that stage
+ * exceeds the fused one's by less, over the call's steps, than those
+ * derivatives cost (timed at dns_bind_workspace); its results equal that
+ * stage's, within the mixed budget of the fused one, and the block's next fused
+ * step first computes the derivatives of its current state.  When every
  * buffer takes the direct path (device memory, mapped page-locked host memory;
  * see dns_set_state) each member block uploads, steps and downloads on its own
  * stream, the uploads one after another, so the link transfers of one block

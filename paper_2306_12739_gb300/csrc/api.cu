@@ -49,6 +49,20 @@ struct HostGroup {
     cudaStream_t nstream = nullptr;
     cudaEvent_t nfork = nullptr, njoin = nullptr;
     cudaEvent_t uploaded = nullptr;   // this block's input is on the device (dns_advance)
+    // dns_advance's short calls (at most ADVANCE_SBS_STEPS steps) on a block
+    // whose autotuned stage is the fused one: the step-by-step stage in parity
+    // blocks (vsbs: the same arrays, those variant flags), which needs no
+    // derivatives of the uploaded state.  ygemm_sbs: the tuned y-derivative
+    // variant the fused stage does not use.  p5_stale: such a call left the
+    // per-plane arrays without the derivatives of the current state, which the
+    // fused stage expects; the next fused step computes them first.
+    GroupView vsbs{};
+    bool has_sbs = false, p5_stale = false;
+    int ygemm_sbs = 1;
+    // whole-step times (ms per step of the handle) of the block's group on its
+    // fused choice and on the step-by-step stage in parity blocks (0: unknown),
+    // and the time of the derivatives of a newly set state of all its blocks
+    float t_fused = 0.f, t_sbs = 0.f, t_derivs = 0.f;
 
     // byte offsets inside the workspace
     struct Off { size_t off, bytes; };
@@ -90,6 +104,12 @@ struct dns_handle {
 
 // dns_advance calls of at most this many steps are captured whole
 constexpr int ADVANCE_GRAPH_STEPS = 16;
+// dns_advance calls of at most this many steps may run a fused-stage block on
+// the step-by-step stage in parity blocks, where the group's measured step-time
+// gap over the call's steps is below the derivatives of the uploaded state that
+// the fused stage needs first (64x65x64 blocks of 4, one call per 0, 1, 2, 4
+// steps: 171, 494, 844, 1538 us against 221, 545, 870, 1523 on the fused stage)
+constexpr int ADVANCE_SBS_STEPS = 2;
 
 namespace {
 
@@ -495,7 +515,8 @@ int cache_lookup_value(const char* path, const std::string& key) {
     int found = 0;
     while (fgets(line, sizeof line, f)) {
         std::string ln(line);
-        if (ln.compare(0, key.size(), key) == 0 && ln.size() > key.size() + 1) found = atoi(ln.c_str() + key.size() + 1);
+        if (ln.compare(0, key.size(), key) == 0 && ln.size() > key.size() + 1 && ln[key.size()] == ' ')
+            found = atoi(ln.c_str() + key.size() + 1);
     }
     fclose(f);
     return found;
@@ -521,10 +542,29 @@ int cache_lookup(const char* path, const std::string& key) {
     int found = 0;
     while (fgets(line, sizeof line, f)) {
         std::string ln(line);
-        if (ln.compare(0, key.size(), key) == 0 && ln.size() > key.size() + 1) {
+        if (ln.compare(0, key.size(), key) == 0 && ln.size() > key.size() + 1 && ln[key.size()] == ' ') {
             int c = atoi(ln.c_str() + key.size() + 1);
             if (c >= 1 && c <= 8) found = c;
         }
+    }
+    fclose(f);
+    return found;
+}
+
+// the time recorded for variant c on key's last line in the cache (0: none)
+float cache_lookup_time(const char* path, const std::string& key, int c) {
+    if (!path) return 0.f;
+    FILE* f = fopen(path, "r");
+    if (!f) return 0.f;
+    char line[512];
+    float found = 0.f;
+    char tag[32];
+    snprintf(tag, sizeof tag, "variant %d ", c);
+    while (fgets(line, sizeof line, f)) {
+        std::string ln(line);
+        if (ln.compare(0, key.size(), key) != 0 || ln.size() <= key.size() + 1 || ln[key.size()] != ' ') continue;
+        const size_t at = ln.find(tag);
+        found = at == std::string::npos ? 0.f : (float)atof(ln.c_str() + at + strlen(tag));
     }
     fclose(f);
     return found;
@@ -865,6 +905,8 @@ static void drop_graphs(dns_handle* h) {
     h->akey.clear();
 }
 
+static int new_state_derivatives(dns_handle* h, const GroupView& v, cudaStream_t st);
+
 int dns_bind_workspace(dns_handle* h, void* dev_ptr, size_t bytes) {
     NvtxRange range_("dns_bind_workspace");
     if (!h) return DNS_ERR_INVALID;
@@ -958,6 +1000,7 @@ int dns_bind_workspace(dns_handle* h, void* dev_ptr, size_t bytes) {
     // decisions of this call by key: the member blocks of a group (and equal
     // groups) are tuned once and share the choice
     std::map<std::string, int> decided;
+    std::map<std::string, std::pair<float, float>> decided_t;   // per-stage key: (chosen, step-by-step in parity) ms
     for (auto& G : h->groups) {
         GroupView& v = G.v;
         if (v.plane != 0) continue;
@@ -1068,6 +1111,7 @@ int dns_bind_workspace(dns_handle* h, void* dev_ptr, size_t bytes) {
             (choice == 5 && !fuse_ok) || (choice == 6 && !par_ok) || (choice == 7 && !ff_ok) ||
             (choice == 8 && !seo_ok) || choice == 3)
             choice = 0;
+        float t_choice = 0.f, t_sbs = 0.f;
         if (!choice) {
             float best[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             cudaEvent_t e0, e1;
@@ -1103,8 +1147,17 @@ int dns_bind_workspace(dns_handle* h, void* dev_ptr, size_t bytes) {
             for (int cand = 1; cand <= 8; ++cand)
                 if (best[cand] > 0.f && (choice == 0 || best[cand] < best[choice])) choice = cand;
             cache_store(h->cfg.autotune_cache, key, choice, best, 8);
+            t_choice = best[choice];
+            t_sbs = best[8];
+        } else if (decided_t.count(key)) {
+            t_choice = decided_t[key].first;
+            t_sbs = decided_t[key].second;
+        } else {
+            t_choice = cache_lookup_time(h->cfg.autotune_cache, key, choice);
+            t_sbs = cache_lookup_time(h->cfg.autotune_cache, key, 8);
         }
         decided[key] = choice;
+        decided_t[key] = {t_choice, t_sbs};
         for (const auto& P : h->parts[gi]) {
             GroupView& v = h->groups[P.ig].v;
             v.helm = choice == 8 ? 1 : choice >= 4 ? 4 : choice;
@@ -1112,6 +1165,9 @@ int dns_bind_workspace(dns_handle* h, void* dev_ptr, size_t bytes) {
             v.spec_eo = (choice == 6 || choice == 7) ? 1 : 0;
             v.spec_eoff = choice == 7 ? 1 : 0;
             v.step_eo = choice == 8 ? 1 : 0;
+            h->groups[P.ig].ygemm_sbs = v.ygemm;
+            h->groups[P.ig].t_fused = t_choice;
+            h->groups[P.ig].t_sbs = t_sbs;
             if (v.helm == 4) v.ygemm = 1;
         }
     }
@@ -1315,6 +1371,53 @@ int dns_bind_workspace(dns_handle* h, void* dev_ptr, size_t bytes) {
         decided[key] = choice;
         v.yd_cap = choice;
     }
+    // the step-by-step stage in parity blocks for dns_advance's short calls, on
+    // every block the autotuner put on the fused stage (not on a requested one)
+    for (auto& G : h->groups) {
+        G.has_sbs = false;
+        G.p5_stale = false;
+        const GroupView& v = G.v;
+        if (!precision_mixed(h) || h->cfg.helm != 0 || v.lin || v.helm != 4) continue;
+        GroupView a = v;
+        a.helm = 1;
+        a.d2fuse = 0;
+        a.spec_eo = 0;
+        a.spec_eoff = 0;
+        a.step_eo = 1;
+        a.ygemm = G.ygemm_sbs;
+        const bool imgs = v.opsEO[0] != nullptr && v.opsEO[1] != nullptr && v.D1EO != nullptr &&
+                          (a.ygemm != 3 || (v.D2EO != nullptr && v.D2lEO != nullptr)) &&
+                          (a.ygemm != 2 || v.Atc != nullptr);
+        if (!imgs || !dnsk::step_eo_supported(a) || (a.ygemm == 3 && !dnsk::yderiv_eo_supported(a))) continue;
+        if (!(G.t_fused > 0.f && G.t_sbs > 0.f)) continue;   // no whole-step times for this group
+        G.vsbs = a;
+        G.has_sbs = true;
+    }
+    // what a short call saves on such a group: the derivatives of its uploaded
+    // state (every block's, back to back), timed here on the workspace's contents
+    for (size_t gi = 0; gi < h->parts.size() && !rc; ++gi) {
+        if (!h->groups[h->parts[gi][0].ig].has_sbs) continue;
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        auto derivs = [&]() {
+            for (const auto& P : h->parts[gi])
+                if (!rc) rc = new_state_derivatives(h, h->groups[P.ig].v, st);
+        };
+        derivs();
+        cudaEventRecord(e0, st);
+        for (int r = 0; r < 3; ++r) derivs();
+        cudaEventRecord(e1, st);
+        float ms = 0.f;
+        if (!rc) rc = check(h, cudaEventSynchronize(e1), "time the derivatives of a new state");
+        if (!rc) cudaEventElapsedTime(&ms, e0, e1);
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        for (const auto& P : h->parts[gi]) h->groups[P.ig].t_derivs = ms / 3.f;
+    }
+    h->launches = 0;
+    if (rc) return rc;
+    if ((rc = device_status(h))) return rc;
     h->bound = true;
     return DNS_OK;
 }
@@ -1388,6 +1491,7 @@ static int set_state_block(dns_handle* h, int group, int member0, int count, con
     if (direct) {
         dnsk::launch_pack(v, member0, count, (const double2*)v_hat, (const double2*)eta_hat, v.lin ? nullptr : U00,
                           v.lin ? nullptr : W00, st);
+        if (v.helm == 4) h->groups[group].p5_stale = false;
         return new_state_derivatives(h, v, st);
     }
     const size_t per = (size_t)count * v.ny * v.nmodes;
@@ -1402,6 +1506,7 @@ static int set_state_block(dns_handle* h, int group, int member0, int count, con
             return rc;
     }
     dnsk::launch_pack(v, member0, count, v.stage, v.stage + per, nullptr, nullptr, st);
+    if (v.helm == 4) h->groups[group].p5_stale = false;
     return new_state_derivatives(h, v, st);
 }
 
@@ -1495,8 +1600,21 @@ int dns_get_state(const dns_handle* hc, int group, int member0, int count, doubl
 // nsteps steps of every group on the handle's stream: the captured step graph
 // (captured on first use) or the kernels enqueued directly; adds the launches
 // to h->launches.
+// The derivatives of the current state for every fused-stage block whose
+// per-plane arrays a short dns_advance call left without them.
+static int refresh_stale(dns_handle* h) {
+    for (auto& G : h->groups) {
+        if (!G.p5_stale) continue;
+        G.p5_stale = false;
+        int rc = new_state_derivatives(h, G.v, h->stream);
+        if (rc) return rc;
+    }
+    return DNS_OK;
+}
+
 static int run_steps(dns_handle* h, int nsteps) {
     int rc;
+    if (nsteps > 0 && (rc = refresh_stale(h))) return rc;
     if (h->cfg.use_graph) {
         if (h->stream == nullptr)
             return fail(h, DNS_ERR_INVALID, "graph capture needs a non-default stream (got the legacy NULL stream)");
@@ -1540,7 +1658,14 @@ int dns_step(dns_handle* h, int nsteps) {
 // buffers and step count.  Staged transfers (pageable memory, which a graph
 // cannot hold) and long runs take the plain sequence: uploads, the step graph,
 // downloads.  Per block the kernels and their order are those of
-// dns_set_state + dns_step + dns_get_state, so the results are bitwise the same.
+// dns_set_state + dns_step + dns_get_state, so the results are bitwise the same,
+// except on a block the autotuner put on the fused stage in a call of at most
+// ADVANCE_SBS_STEPS steps (captured whole, or eager) where the group's measured
+// step-time gap over the call's steps is below what the derivatives of the
+// uploaded state cost: that call runs the block's step-by-step stage in parity
+// blocks, which needs none (the results are those of that stage, within the
+// mixed step's budget of the fused one), and the next fused step of the block
+// first computes the derivatives of its state.
 int dns_advance(dns_handle* h, int nsteps, const dns_state_in* in, const dns_state_out* out, int ptr_kind) {
     NvtxRange range_("dns_advance");
     if (!h) return DNS_ERR_INVALID;
@@ -1583,6 +1708,25 @@ int dns_advance(dns_handle* h, int nsteps, const dns_state_in* in, const dns_sta
             return rc;
     const cudaMemcpyKind kin = ptr_kind ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     const cudaMemcpyKind kout = ptr_kind ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    bool all_direct = true;
+    for (int gi = 0; gi < ng; ++gi) all_direct = all_direct && (!in || din[gi]) && (!out || dout[gi]);
+    const bool whole = graph && all_direct && nsteps <= ADVANCE_GRAPH_STEPS;   // one captured graph
+    // short calls (captured whole, or eager) run a fused-stage block on its
+    // step-by-step stage in parity blocks where the group's step-time gap over
+    // the call's steps is below the derivatives of the uploaded state
+    const bool sbs_window = nsteps <= ADVANCE_SBS_STEPS && (whole || !graph);
+    auto alt = [&](const HostGroup& G) {
+        return sbs_window && G.has_sbs && (float)nsteps * (G.t_sbs - G.t_fused) < G.t_derivs;
+    };
+    bool sbs = false;
+    for (const auto& G : h->groups) sbs = sbs || alt(G);
+    // a block's view swapped for its short-call one while its work is enqueued
+    struct SbsView {
+        HostGroup& G;
+        bool on;
+        SbsView(HostGroup& g, bool o) : G(g), on(o) { if (on) std::swap(G.v, G.vsbs); }
+        ~SbsView() { if (on) std::swap(G.v, G.vsbs); }
+    };
     // Fork, per block: upload (after the previous block's), nsteps steps,
     // download; join.
     auto enqueue_advance = [&]() -> int {
@@ -1594,6 +1738,7 @@ int dns_advance(dns_handle* h, int nsteps, const dns_state_in* in, const dns_sta
             const size_t pm = (size_t)v0.ny * v0.nmodes * 2, pu = (size_t)v0.my;
             for (const auto& P : h->parts[gi]) {
                 HostGroup& G = h->groups[P.ig];
+                SbsView sw(G, alt(G));
                 cudaStream_t sb = bstream(P.ig);
                 const size_t o = (size_t)P.m0;
                 if (multi) cudaStreamWaitEvent(sb, h->fork_ev, 0);
@@ -1625,13 +1770,18 @@ int dns_advance(dns_handle* h, int nsteps, const dns_state_in* in, const dns_sta
             for (size_t ig = 0; ig < h->groups.size(); ++ig) cudaStreamWaitEvent(h->stream, h->gevents[ig], 0);
         return DNS_OK;
     };
-    bool all_direct = true;
-    for (int gi = 0; gi < ng; ++gi) all_direct = all_direct && (!in || din[gi]) && (!out || dout[gi]);
-    if (graph && all_direct && nsteps <= ADVANCE_GRAPH_STEPS) {
+    // a fused-stage block continuing its current state needs its derivatives
+    if (!in)
+        for (auto& G : h->groups) {
+            if (!G.p5_stale || alt(G)) continue;
+            G.p5_stale = false;
+            if ((rc = new_state_derivatives(h, G.v, h->stream))) return rc;
+        }
+    if (whole) {
         // the whole call as one graph (one submission: every block starts at
         // once), kept for the next call with the same buffers and step count
         std::vector<uintptr_t> key = {(uintptr_t)nsteps, (uintptr_t)ptr_kind, (uintptr_t)(in != nullptr),
-                                      (uintptr_t)(out != nullptr)};
+                                      (uintptr_t)(out != nullptr), (uintptr_t)sbs};
         for (int gi = 0; gi < ng; ++gi) {
             if (in) for (const void* q : {in[gi].v_hat, in[gi].eta_hat, in[gi].U00, in[gi].W00}) key.push_back((uintptr_t)q);
             if (out) for (const void* q : {out[gi].v_hat, out[gi].eta_hat, out[gi].U00, out[gi].W00}) key.push_back((uintptr_t)q);
@@ -1691,6 +1841,7 @@ int dns_advance(dns_handle* h, int nsteps, const dns_state_in* in, const dns_sta
             }
         }
     }
+    for (auto& G : h->groups) G.p5_stale = G.p5_stale || alt(G);
     if ((rc = check(h, cudaGetLastError(), "advance launch"))) return rc;
     return sync_with_status(h, h->stream, "advance");
 }
@@ -1701,7 +1852,8 @@ int dns_step_timed(dns_handle* h, int nsteps, double* ms, int* launches) {
     if (nsteps < 0) return fail(h, DNS_ERR_INVALID, "nsteps < 0");
     for (int c = 0; c < DNS_K_NCLASS; ++c) { ms[c] = 0.0; launches[c] = 0; }
     h->launches = 0;
-    int rc = DNS_OK;
+    int rc = nsteps > 0 ? refresh_stale(h) : DNS_OK;
+    if (rc) return rc;
     for (int i = 0; i < nsteps && rc == DNS_OK; ++i) {
         Timer tm;
         enqueue_step(h, &tm);

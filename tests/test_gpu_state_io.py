@@ -245,3 +245,73 @@ def test_advance_with_stochastic_forcing_and_a_linear_group():
         for x, y in zip(a[:2], b2[:2]):
             assert np.array_equal(x, y)
     assert np.array_equal(out[0][0][2], out[1][0][2]) and np.array_equal(out[0][0][3], out[1][0][3])
+
+
+def _fused_cache(tmp_path):
+    """An autotune cache that puts G's member blocks of 4 on the fused stage in
+    parity blocks (helm 7) with the y-derivatives in parity blocks tuned (3) and
+    the tile shapes fixed, so that every handle below runs the same kernels; its
+    whole-step times put the step-by-step stage in parity blocks (helm 8) 1 us
+    per step behind, less than the derivatives of a new state cost."""
+    p = tmp_path / "tune.txt"
+    p.write_text("plane 32 33 32 4 3\nygemm 32 33 32 4 3\n"
+                 "helm 32 33 32 4 7   # variant 7 0.2000 ms variant 8 0.2010 ms\nspec_ec 32 33 32 4 4\n"
+                 "spec_cta 32 33 32 4 3\nytile 32 33 32 4 16\n")
+    return str(p)
+
+
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_short_advance_calls_run_the_step_by_step_stage_of_a_fused_block(tmp_path, use_graph):
+    """A block the autotuner put on the fused stage runs, in dns_advance calls of
+    one or two steps with page-locked buffers, its step-by-step stage in parity
+    blocks (no derivatives of the uploaded state needed): the call equals
+    set_state + step + get_state on that stage bit for bit.  The next fused
+    step first computes the derivatives of its state (as setting that state
+    and stepping does), and a four-step call runs the fused stage."""
+    cache = _fused_cache(tmp_path)
+    st = _state()
+    keys = ("v", "eta", "U", "W")
+
+    def run(nsteps, **kw):
+        e = dns.Ensemble([G], precision="mixed", use_graph=use_graph, autotune_cache=cache, **kw)
+        try:
+            e.set_state(0, *(st[k] for k in keys))
+            e.step(nsteps)
+            return e.get_state(0)
+        finally:
+            e.close()
+
+    ens = dns.Ensemble([G], precision="mixed", use_graph=use_graph, autotune_cache=cache)
+    try:
+        assert dns.dns_kernel_choice(ens.h, 0, "helm") == "fused_eo_ff"
+        keep_in = [_pinned(st[k]) for k in keys]
+        for nsteps, kw in ((1, dict(helm="simt_eo", ygemm="simt_eo", plane="lines")),
+                           (2, dict(helm="simt_eo", ygemm="simt_eo", plane="lines")),
+                           (4, {})):
+            ref = run(nsteps, **kw)
+            keep_out = [_pinned(np.zeros_like(x)) for x in ref]
+            dns.dns_advance(ens.h, nsteps, [tuple(_ptr(t) for _, t in keep_in)],
+                            [tuple(_ptr(t) for _, t in keep_out)], 0)
+            got = [_host(t, x).copy() for (_, t), x in zip(keep_out, ref)]
+            for a, b in zip(got, ref):
+                assert np.array_equal(a, b), nsteps
+        # continue on the fused stage from the state a one-step call left: its
+        # derivatives are computed first, as setting that state computes them (a
+        # state read back and set again differs from the device's only by the
+        # Hermitian projection of the n = 0 column, at rounding level; derivatives
+        # of the wrong state would be off by far more)
+        dns.dns_advance(ens.h, 1, [tuple(_ptr(t) for _, t in keep_in)], None, 0)
+        mid = ens.get_state(0)
+        ens.step(2)
+        cont = ens.get_state(0)
+        e2 = dns.Ensemble([G], precision="mixed", use_graph=use_graph, autotune_cache=cache)
+        try:
+            e2.set_state(0, *mid)
+            e2.step(2)
+            want = e2.get_state(0)
+        finally:
+            e2.close()
+        for a, b in zip(cont, want):
+            assert np.max(np.abs(a - b)) <= 1e-12 * np.max(np.abs(b))
+    finally:
+        ens.close()
