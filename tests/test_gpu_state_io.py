@@ -296,10 +296,12 @@ def test_short_advance_calls_run_the_step_by_step_stage_of_a_fused_block(tmp_pat
             for a, b in zip(got, ref):
                 assert np.array_equal(a, b), nsteps
         # continue on the fused stage from the state a one-step call left: its
-        # derivatives are computed first, as setting that state computes them (a
-        # state read back and set again differs from the device's only by the
-        # Hermitian projection of the n = 0 column, at rounding level; derivatives
-        # of the wrong state would be off by far more)
+        # derivatives are computed first, as setting that state computes them.  A
+        # state read back and set again differs from the device's by the Hermitian
+        # projection of the n = 0 column, at FP64 rounding level, which can flip
+        # single-precision roundings downstream (measured 7e-9 of the field after
+        # two steps); the derivatives of the previous sub-stage's state, which the
+        # per-plane arrays held, would be off at O(dt) = 5e-3 of the field.
         dns.dns_advance(ens.h, 1, [tuple(_ptr(t) for _, t in keep_in)], None, 0)
         mid = ens.get_state(0)
         ens.step(2)
@@ -312,6 +314,6 @@ def test_short_advance_calls_run_the_step_by_step_stage_of_a_fused_block(tmp_pat
         finally:
             e2.close()
         for a, b in zip(cont, want):
-            assert np.max(np.abs(a - b)) <= 1e-12 * np.max(np.abs(b))
+            assert np.max(np.abs(a - b)) <= 1e-6 * np.max(np.abs(b))
     finally:
         ens.close()
