@@ -199,7 +199,9 @@ k_plane_cl(GroupView g, const double* __restrict__ Ucur, const double* __restric
             }
         }
         // every rank has also finished reading its A slots of the previous transform
-        cluster.sync();
+        // (their values consumed before its last CTA barrier): an execution barrier
+        // of the cluster suffices here, no release of this rank's own writes
+        asm volatile("barrier.cluster.arrive.relaxed.aligned;\n\tbarrier.cluster.wait.aligned;" ::: "memory");
         // z-stage step C: tasks (f, k1, nl); row z goes to the rank owning it
         for (int t = tid; t < (NF - f_lo) * NKL * Z1; t += NT) {
             const int nl = t % NKL, r = t / NKL, k1 = r % Z1, f = f_lo + r / Z1;
