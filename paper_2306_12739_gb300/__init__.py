@@ -330,7 +330,11 @@ def make_config(groups, precision="fp64", use_graph=False, ygemm="default", auto
     concurrently run member blocks), linear (True: a linearised disturbance
     ensemble of one streamwise wavenumber) and kx_index (its n >= 1).
     autotune_cache: file of kernel-variant decisions read and appended at bind
-    time (None: the DNS_AUTOTUNE_CACHE environment variable, if set)."""
+    time (None: the DNS_AUTOTUNE_CACHE environment variable, if set).
+    ygemm, plane, helm: kernel-variant requests of the mixed path ("default":
+    autotuned at bind time; dns_config in include/dns.h describes each):
+    ygemm simt | tc | simt_eo; plane cta | cluster | lines; helm simt | tc |
+    persist | fused | fused_d2v | fused_eo | fused_eo_ff | simt_eo."""
     arr = (dns_group_desc * len(groups))()
     for i, g in enumerate(groups):
         arr[i] = dns_group_desc(_pick(_FLOWS, g["flow"], "flow"), g["mx"], g["my"], g["mz"], g["lx"], g["lz"], g["re"],
