@@ -129,8 +129,8 @@ def test_roofline_bound_follows_the_ridge_point():
 def test_parity_block_models_halve_the_operator_bytes_and_the_flops():
     """In parity blocks a matrix is its even and odd halves, Ny x 2 ceil(ceil(Ny/2)/2)
     floats (63 x 32 at Ny = 63 against 63 x 64 row-padded), and every product
-    half the multiply-adds: the fused stage (fused_eo, fused_eo_ff) and the
-    step-by-step forcing and apply (simt_eo)."""
+    half the multiply-adds: the fused stage (fused_eo, fused_eo_ff), the
+    step-by-step forcing and apply (simt_eo) and the y-derivatives (ygemm simt_eo)."""
     g = dict(bench.WORKLOADS["poiseuille64"]["groups"][0], members=4)
     S = 22 * 43 * 63 * 4
     nat = bench.kernel_bytes("spec", dict(g, _stage="fused_eo_ff"), "mixed")
@@ -145,3 +145,8 @@ def test_parity_block_models_halve_the_operator_bytes_and_the_flops():
         assert b == pytest.approx(a / 2)
     assert bench.kernel_bytes("forcing", dict(g, _stage="simt_eo"), "mixed") == \
         bench.kernel_bytes("forcing", g, "mixed") == pytest.approx((40 + 16 * 4 / 3) * S)
+    # the y-derivatives in parity blocks: half the flops, the same bytes
+    _, a, _ = bench.kernel_work("yderiv", dict(g, _ygemm="simt"), "mixed")
+    _, b, _ = bench.kernel_work("yderiv", dict(g, _ygemm="simt_eo"), "mixed")
+    assert b == pytest.approx(a / 2) and a == pytest.approx(S * 3 * 2 * 2 * 63)
+    assert bench.kernel_bytes("yderiv", dict(g, _ygemm="simt_eo"), "mixed") == bench.kernel_bytes("yderiv", g, "mixed")
