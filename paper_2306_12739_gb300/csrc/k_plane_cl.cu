@@ -198,9 +198,13 @@ k_plane_cl(GroupView g, const double* __restrict__ Ucur, const double* __restric
                 S[k1 * (Z2 * NKLP)] = k1 == 0 ? v[0] : mul(v[k1], mk<C>(w.x, -w.y));
             }
         }
-        // every rank has also finished reading its A slots of the previous transform
-        // (their values consumed before its last CTA barrier): an execution barrier
-        // of the cluster suffices here, no release of this rank's own writes
+        // The scratch rows just written are read by other threads of this CTA in
+        // step C: a CTA barrier orders them.  Across the cluster, every rank has
+        // also finished reading its A slots of the previous transform (their values
+        // consumed before its last CTA barrier) and, in the first transform, has
+        // started: an execution barrier of the cluster suffices for that, without
+        // the release of this rank's writes that a default cluster barrier costs.
+        __syncthreads();
         asm volatile("barrier.cluster.arrive.relaxed.aligned;\n\tbarrier.cluster.wait.aligned;" ::: "memory");
         // z-stage step C: tasks (f, k1, nl); row z goes to the rank owning it
         for (int t = tid; t < (NF - f_lo) * NKL * Z1; t += NT) {
