@@ -238,12 +238,18 @@ def dns_kernel_choice(h, group, which="ygemm"):
     'helm' -> 'simt' | 'tc' | 'persist' | 'fused' | 'fused_d2v' | 'fused_eo' | 'fused_eo_ff' | 'simt_eo'."""
     c, p, m = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
     _ck(h, _lib.dns_kernel_choice(h, group, ctypes.byref(c), ctypes.byref(p), ctypes.byref(m)))
+    # the names of the request tables (one source for both directions); plane 4,
+    # the linearised groups' own kernel, is never requested
     if which == "plane":
-        return {1: "cta", 2: "cluster", 3: "lines", 4: "linear"}.get(p.value, p.value)
+        return {**_names(_PLANE), 4: "linear"}.get(p.value, p.value)
     if which == "helm":
-        return {1: "simt", 2: "tc", 3: "persist", 4: "fused", 5: "fused_d2v", 6: "fused_eo", 7: "fused_eo_ff",
-                8: "simt_eo"}.get(m.value, m.value)
-    return {1: "simt", 2: "tc", 3: "simt_eo"}.get(c.value, c.value)
+        return _names(_HELM).get(m.value, m.value)
+    return _names(_YGEMM).get(c.value, c.value)
+
+
+def _names(table):
+    """number -> name of a request table, without the autotune aliases."""
+    return {v: k for k, v in table.items() if v != 0}
 
 
 def dns_set_base_flow(h, group, U, V, W, ptr_kind):

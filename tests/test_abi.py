@@ -283,3 +283,29 @@ def test_autotune_cache_path_may_come_from_the_environment(dns, monkeypatch, tmp
     assert dns.make_config([_g()], autotune_cache="other").autotune_cache == b"other"
     monkeypatch.delenv("DNS_AUTOTUNE_CACHE")
     assert dns.make_config([_g()]).autotune_cache is None
+
+
+def test_kernel_choice_names_are_the_request_names(dns, monkeypatch):
+    """Every kernel variant a caller can request reads back under the same name
+    (the C call faked: it reports the requested numbers)."""
+    import ctypes
+
+    class Fake:
+        value = (0, 0, 0)
+
+        def dns_kernel_choice(self, h, group, c, p, m):
+            for ref, v in zip((c, p, m), self.value):
+                ctypes.cast(ref, ctypes.POINTER(ctypes.c_int))[0] = v
+            return 0
+
+    fake = Fake()
+    monkeypatch.setattr(dns, "_lib", fake)
+    for which, table in (("ygemm", dns._YGEMM), ("plane", dns._PLANE), ("helm", dns._HELM)):
+        for name, num in table.items():
+            if num == 0:
+                continue
+            fake.value = tuple(num if w == which else 1 for w in ("ygemm", "plane", "helm"))
+            assert dns.dns_kernel_choice(None, 0, which) == name, (which, name)
+    fake.value = (1, 4, 1)
+    assert dns.dns_kernel_choice(None, 0, "plane") == "linear"
+
