@@ -1,6 +1,9 @@
 """The N > 1 path of bench.py on CPU: two gloo ranks, each advancing its own
 replica ensemble (members are independent, so nothing but a barrier and the
-max of the timed durations crosses ranks)."""
+max of the timed durations crosses ranks), and each building the library's
+handle for its replica on the host (the same operators and workspace on every
+rank, so replicas need no exchange of either)."""
+import hashlib
 import os
 import queue
 import socket
@@ -29,6 +32,20 @@ def _replica(rank):
     return ch.stats(x)["e_total"]
 
 
+def _library_replica():
+    """The host side of a replica's handle: workspace bytes and a digest of the
+    operators of one wavenumber pair (no GPU: dns_create builds them on the host)."""
+    import paper_2306_12739_gb300 as dns
+    h = dns.dns_create(dns.make_config([G], precision="mixed"), 0)
+    try:
+        nbytes = dns.dns_workspace_size(h)
+        ops = dns.dns_export_operators(h, 0, 1, 1, G["my"] - 2)
+        digest = hashlib.sha256(b"".join(np.ascontiguousarray(a).tobytes() for a in ops)).hexdigest()
+    finally:
+        dns.dns_destroy(h)
+    return int(nbytes), digest
+
+
 def _worker(rank, world, port, q):
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
                       WORLD_SIZE=str(world), LOCAL_RANK=str(rank))
@@ -39,18 +56,23 @@ def _worker(rank, world, port, q):
         t0 = time.perf_counter()
         energy = _replica(rank)
         dt = time.perf_counter() - t0 + 0.05 * rank      # ranks finish at different times
+        lib = _library_replica()
         tmax = bench.reduce_max(dt, dist)
         value = bench.aggregate(G["members"] * 2, tmax, w)
         gathered = [None] * w
         dist.all_gather_object(gathered, energy.tolist())
+        libs = [None] * w
+        dist.all_gather_object(libs, lib)
         dist.barrier()
         dist.destroy_process_group()
-        q.put((rank, dt, tmax, value, gathered))
+        q.put((rank, dt, tmax, value, gathered, libs))
     except Exception as exc:  # pragma: no cover - reported to the parent
         q.put((rank, "error", repr(exc)))
 
 
 def test_two_gloo_ranks_run_replicas_and_report_whole_job_throughput():
+    import __graft_entry__
+    __graft_entry__.build()          # the ranks load the library built here
     import multiprocessing as mp
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
@@ -73,11 +95,13 @@ def test_two_gloo_ranks_run_replicas_and_report_whole_job_throughput():
                 p.terminate()
     dts = [results[r][1] for r in range(2)]
     for r in range(2):
-        _, dt, tmax, value, gathered = results[r]
+        _, dt, tmax, value, gathered, libs = results[r]
         assert tmax == pytest.approx(max(dts))                      # max over ranks
         assert value == pytest.approx(G["members"] * 2 * 2 / max(dts))   # all ranks' member-steps / slowest
         # each rank advanced a distinct replica, identical to running it alone
         assert not np.allclose(gathered[0], gathered[1])
+        # and built the same handle: workspace size and operators
+        assert libs[0] == libs[1] and libs[0][0] > 0
     alone = [_replica(r) for r in range(2)]
     for r in range(2):
         assert np.allclose(results[0][4][r], alone[r], rtol=1e-13, atol=0)
